@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a hand-worked
+example, the paper's matrix form of the serialization, a library routine
+(scipy's extremum finder and natural cubic spline), closed forms and invariants
+(Eq. 1 reconstruction, the IMF condition), and tone separation.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_15319_gb300 import synth
+
+scipy_signal = pytest.importorskip("scipy.signal")
+scipy_interp = pytest.importorskip("scipy.interpolate")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = np.finfo(np.float64).eps
+
+
+# ------------------------------------------------------------------ Sec. 3.2 / 3.3
+
+def _read_golden_serialize():
+    vals = {}
+    with open(os.path.join(GOLDEN, "serialize_M5_N3_D2.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *rest = line.split()
+            vals[key] = rest
+    M, N, D = int(vals["M"][0]), int(vals["N"][0]), int(vals["D"][0])
+    X = np.array([float(v) for v in vals["X"]]).reshape(N, M)
+    x = np.array([float(Fraction(v)) for v in vals["x"]])
+    return M, N, D, X, x
+
+
+def test_serialize_hand_example():
+    M, N, D, X, x = _read_golden_serialize()
+    got = O.serialize(X, D)
+    assert got.size == O.serial_length(M, N, D) == x.size
+    np.testing.assert_allclose(got, x, rtol=0, atol=4 * EPS * 34)
+
+
+def _serialize_matrix_form(X, D):
+    """Sec. 3.2 written with the paper's matrix operations (paper matrix X is M x N)."""
+    Xp = X.T  # M x N, signals as columns
+    M, N = Xp.shape
+    a = np.arange(1, D + 1) / (D + 1)
+    af = a[::-1]
+    XA = Xp[0:D, 1:N]
+    XB = Xp[M - D:M, 0:N - 1]
+    u = np.ones(N - 1)
+    E = np.flipud(XA) * np.outer(a, u) + np.flipud(XB) * np.outer(af, u)
+    z = np.zeros((D, 1))
+    T = np.vstack([Xp, np.hstack([E, z])])
+    t = T.reshape(-1, order="F")  # vec() stacks columns
+    return t[:(M + D) * N - D]
+
+
+@pytest.mark.parametrize("M,N,D", [(5, 3, 2), (7, 1, 3), (16, 4, 0), (9, 5, 9), (12, 6, 1),
+                                   (40, 3, 8)])
+def test_serialize_matches_matrix_form(M, N, D):
+    X = synth.rng(M * 100 + N * 10 + D).standard_normal((N, M))
+    got = O.serialize(X, D)
+    ref = _serialize_matrix_form(X, D)
+    assert got.size == M * N + D * N - D
+    np.testing.assert_allclose(got, ref, rtol=0, atol=8 * EPS * np.abs(X).max())
+
+
+def test_serialize_transition_continuity():
+    """h(0) = f(T), h(D) = g(0) of Eq. (transition), in the discrete limit."""
+    M, N, D = 200, 2, 150
+    t = np.linspace(0, 1, M)
+    X = np.vstack([np.cos(3 * t) + 2.0, np.sin(5 * t) - 1.0])
+    x = O.serialize(X, D)
+    first, last = x[M], x[M + D - 1]
+    assert abs(first - X[0, -1]) <= abs(X[1, D - 1] - X[0, -1]) / (D + 1) + 1e-12
+    assert abs(last - X[1, 0]) <= abs(X[0, M - D] - X[1, 0]) / (D + 1) + 1e-12
+    # constant signals: the transition weights sum to one
+    Xc = np.full((3, 10), 2.5)
+    np.testing.assert_allclose(O.serialize(Xc, 4), 2.5, rtol=4 * EPS)
+
+
+@pytest.mark.parametrize("M,N,D", [(5, 3, 2), (33, 7, 6), (10, 1, 0), (8, 8, 8)])
+def test_deserialize_round_trip_bit_exact(M, N, D):
+    X = synth.rng(7 + M).standard_normal((N, M))
+    x = O.serialize(X, D)
+    back = O.deserialize(x[None, :], M, N, D)[0]
+    assert np.array_equal(back, X)
+
+
+# ------------------------------------------------------------------ Sec. 2.1 Step 1
+
+def test_extrema_vs_scipy_tie_free():
+    for seed in range(20):
+        h = synth.rng(seed).standard_normal(257 + seed)
+        tmax, tmin = O.extrema(h)
+        smax = scipy_signal.argrelextrema(h, np.greater)[0]
+        smin = scipy_signal.argrelextrema(h, np.less)[0]
+        assert np.array_equal(tmax, smax)
+        assert np.array_equal(tmin, smin)
+
+
+def test_extrema_ties_golden():
+    with open(os.path.join(GOLDEN, "extrema_ties.txt")) as f:
+        rows = [ln for ln in f if ln.strip() and not ln.startswith("#")]
+    for ln in rows:
+        hs, mx, mn = [p.strip() for p in ln.split("|")]
+        h = np.array([float(v) for v in hs.split()])
+        emax = [] if mx == "-" else [int(v) for v in mx.split()]
+        emin = [] if mn == "-" else [int(v) for v in mn.split()]
+        tmax, tmin = O.extrema(h)
+        assert list(tmax) == emax, ln
+        assert list(tmin) == emin, ln
+
+
+def test_extrema_count_on_sinusoid():
+    # f full periods over L samples, phase chosen so no sample sits on a peak
+    for f in (3, 17, 64):
+        L = 4096
+        t = np.arange(L) / L
+        h = np.sin(2 * np.pi * f * t + 0.1234)
+        tmax, tmin = O.extrema(h)
+        assert tmax.size == f and tmin.size == f
+
+
+# ------------------------------------------------------------------ Sec. 2.1 Step 2
+
+@pytest.mark.parametrize("n", [3, 4, 5, 8, 12])
+def test_spline_vs_scipy_and_dense(n):
+    g = synth.rng(1000 + n)
+    s = np.cumsum(g.integers(1, 9, n)).astype(np.float64) - 3.0
+    v = g.standard_normal(n)
+    Mj = O.spline_second_derivs(s, v)
+    cs = scipy_interp.CubicSpline(s, v, bc_type="natural")
+    np.testing.assert_allclose(Mj, cs(s, 2), rtol=1e-12, atol=1e-12)
+    # dense solve of the same tridiagonal system
+    A = np.zeros((n, n))
+    d = np.zeros(n)
+    A[0, 0] = A[-1, -1] = 1.0
+    for j in range(1, n - 1):
+        hl, hr = s[j] - s[j - 1], s[j + 1] - s[j]
+        A[j, j - 1], A[j, j], A[j, j + 1] = hl, 2 * (hl + hr), hr
+        d[j] = 6 * ((v[j + 1] - v[j]) / hr - (v[j] - v[j - 1]) / hl)
+    np.testing.assert_allclose(Mj, np.linalg.solve(A, d), rtol=1e-13, atol=1e-13)
+
+
+def test_spline_linear_data_is_exact():
+    s = np.array([-4.0, -1.0, 2.0, 3.0, 7.0, 11.0])
+    v = 0.5 * s - 2.0
+    np.testing.assert_allclose(O.spline_second_derivs(s, v), 0.0, atol=1e-14)
+
+
+def _mirror_knots(h, t, P=2):
+    L = h.size
+    p = min(P, t.size)
+    left = [(-float(t[j]), h[t[j]]) for j in range(p - 1, -1, -1)]
+    mid = [(float(tj), h[tj]) for tj in t]
+    right = [(2.0 * (L - 1) - t[j], h[t[j]]) for j in range(t.size - 1, t.size - p - 1, -1)]
+    k = np.array(left + mid + right)
+    return k[:, 0], k[:, 1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_envelope_vs_scipy_mirror(seed):
+    g = synth.rng(50 + seed)
+    L = int(g.integers(20, 300))
+    h = np.cumsum(g.standard_normal(L)) + np.sin(np.arange(L) / 3.0)
+    tmax, tmin = O.extrema(h)
+    for t in (tmax, tmin):
+        if t.size == 0:
+            continue
+        s, v = _mirror_knots(h, t)
+        ref = scipy_interp.CubicSpline(s, v, bc_type="natural")(np.arange(L))
+        got = O.envelope(h, t)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-11 * max(1.0, np.abs(v).max()))
+
+
+def test_envelope_endpoints_rule_vs_scipy():
+    h = synth.rng(3).standard_normal(64)
+    tmax, _ = O.extrema(h)
+    s = np.concatenate([[0.0], tmax.astype(float), [63.0]])
+    v = np.concatenate([[h[0]], h[tmax], [h[63]]])
+    ref = scipy_interp.CubicSpline(s, v, bc_type="natural")(np.arange(64))
+    got = O.envelope(h, tmax, boundary=O.BOUNDARY_ENDPOINTS)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_envelope_single_knot():
+    h = np.array([0.0, 1.0, 3.0, 2.0, 1.5, 1.0])
+    tmax, _ = O.extrema(h)
+    assert list(tmax) == [2]
+    # knots (-2, 3), (2, 3), (8, 3): a constant envelope
+    np.testing.assert_allclose(O.envelope(h, tmax), 3.0, rtol=1e-15)
+
+
+# ------------------------------------------------------------- Sec. 2.1 Steps 3-4
+
+@pytest.mark.parametrize("seed", range(5))
+def test_one_sift_vs_scipy_composition(seed):
+    g = synth.rng(77 + seed)
+    L = int(g.integers(30, 500))
+    h = g.standard_normal(L) + np.sin(np.arange(L) / 5.0)
+    out = O.sift(h)
+    assert out is not None
+    hs, num, den = out
+    tmax = scipy_signal.argrelextrema(h, np.greater)[0]
+    tmin = scipy_signal.argrelextrema(h, np.less)[0]
+    envs = []
+    for t in (tmax, tmin):
+        s, v = _mirror_knots(h, t)
+        envs.append(scipy_interp.CubicSpline(s, v, bc_type="natural")(np.arange(L)))
+    m = (envs[0] + envs[1]) / 2
+    ref = h - m
+    np.testing.assert_allclose(hs, ref, rtol=0, atol=1e-11 * np.abs(h).max())
+    np.testing.assert_allclose(num, np.sum((h - ref) ** 2), rtol=1e-9)
+    np.testing.assert_allclose(den, np.sum(h * h), rtol=1e-12)
+
+
+# ------------------------------------------------------------- Sec. 2.1, Eq. (1)
+
+def _n_zero_crossings(c):
+    s = c < 0
+    return int(np.count_nonzero(s[1:] != s[:-1]))
+
+
+def test_emd_reconstruction_and_tone_separation():
+    L = 4096
+    t = np.arange(L) / L
+    hi, lo = np.sin(2 * np.pi * 64 * t), np.sin(2 * np.pi * 8 * t)
+    x = hi + lo
+    K = 8
+    imfs, res, n, sifts = O.emd(x, K, fixed_sifts=10)
+    assert n >= 2
+    assert list(sifts[:n]) == [10] * n and np.all(imfs[n:] == 0)
+    recon = imfs.sum(0) + res
+    assert np.abs(recon - x).max() <= 4 * K * EPS * (np.abs(x).max() + np.abs(imfs).max())
+    mid = slice(L // 20, 19 * L // 20)
+    rel = lambda a, b: np.linalg.norm(a[mid] - b[mid]) / np.linalg.norm(b[mid])
+    assert rel(imfs[0], hi) <= 0.05
+    assert rel(imfs[1], lo) <= 0.1
+    # IMF condition (Sec. 1 / Sec. 2.1): extrema and zero crossings differ by at most one
+    for c in imfs[:2]:
+        cm = c[mid]
+        a, b = O.extrema(cm)
+        assert abs((a.size + b.size) - _n_zero_crossings(cm)) <= 1
+
+
+def test_emd_reconstruction_noisy_series():
+    X = synth.workload_series_3x1024()
+    x = O.serialize(X, 0)
+    K = 8
+    imfs, res, n, _ = O.emd(x, K)
+    assert 3 <= n <= K
+    assert np.abs(imfs.sum(0) + res - x).max() <= 4 * K * EPS * (np.abs(x).max()
+                                                                 + np.abs(imfs).max())
+
+
+def test_emd_no_extrema_gives_residue_only():
+    x = np.linspace(-1, 3, 100)
+    imfs, res, n, _ = O.emd(x, 5)
+    assert n == 0 and np.all(imfs == 0) and np.array_equal(res, x)
+
+
+def test_emd_sd_stop_limits():
+    x = synth.workload_series_3x1024()[0]
+    _, _, n1, s1 = O.emd(x, 6, stop=O.STOP_SD, sd_threshold=1e30, max_sifts=50)
+    assert n1 > 0 and np.all(s1[:n1] == 1)
+    _, _, n2, s2 = O.emd(x, 2, stop=O.STOP_SD, sd_threshold=0.0, max_sifts=7)
+    assert n2 == 2 and np.all(s2[:n2] == 7)
+    _, _, n3, s3 = O.emd(x, 4, stop=O.STOP_SD, sd_threshold=0.2, max_sifts=50)
+    assert n3 == 4 and np.all((s3[:n3] >= 1) & (s3[:n3] <= 50))
+
+
+def test_emd_fixed_sifts_equals_repeated_sift():
+    """A fixed sift count is exactly the sift step applied S times (Sec. 2.1 Step 5)."""
+    x = synth.workload_series_3x1024()[1]
+    imfs, res, n, _ = O.emd(x, 1, fixed_sifts=4)
+    h = x.copy()
+    for _ in range(4):
+        h = O.sift(h)[0]
+    assert np.array_equal(imfs[0], h)
+    assert np.array_equal(res, x - h)
+
+
+# ------------------------------------------------------------------ Sec. 2.2 EEMD
+
+def test_eemd_zero_noise_equals_emd():
+    x = synth.workload_series_3x1024()[2]
+    w = synth.white_noise(4, x.size, 5)
+    imfs_e, res_e, n_e = O.eemd(x, w, 0.0, 6)
+    imfs, res, n, _ = O.emd(x, 6)
+    assert n_e == n
+    assert np.array_equal(imfs_e, imfs) and np.array_equal(res_e, res)
+
+
+def test_eemd_average_and_reconstruction():
+    x = synth.grating_image(24, 9).reshape(-1)
+    T = 3
+    w = synth.white_noise(T, x.size, 11)
+    beta = 0.2 * O.std(x)
+    np.testing.assert_allclose(O.std(x), np.std(x), rtol=1e-12)
+    imfs, res, n = O.eemd(x, w, beta, 6)
+    acc = np.zeros((6, x.size))
+    accr = np.zeros(x.size)
+    nmax = 0
+    for m in range(T):
+        c, r, nn, _ = O.emd(x + beta * w[m], 6)
+        acc += c
+        accr += r
+        nmax = max(nmax, nn)
+    assert n == nmax
+    np.testing.assert_allclose(imfs, acc / T, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(res, accr / T, rtol=0, atol=1e-14)
+    recon = imfs.sum(0) + res
+    np.testing.assert_allclose(recon, x + beta * w.mean(0), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ Sec. 3 end to end
+
+def test_serial_emd_single_signal_is_plain_emd():
+    X = synth.workload_series_3x1024()[:1]
+    imfs, res, n, _ = O.serial_emd(X, D=0, K=6)
+    imfs2, res2, n2, _ = O.emd(X[0], 6)
+    assert n == n2 and np.array_equal(imfs[:, 0, :], imfs2) and np.array_equal(res[0], res2)
+
+
+def test_serial_emd_transitions_removed():
+    X = synth.workload_series_3x1024()
+    D = 205
+    imfs, res, n, _ = O.serial_emd(X, D=D, K=8)
+    x = O.serialize(X, D)
+    R, r, n2, _ = O.emd(x, 8)
+    assert n == n2
+    M = X.shape[1]
+    for i in range(3):
+        seg = slice(i * (M + D), i * (M + D) + M)
+        assert np.array_equal(imfs[:, i, :], R[:, seg])
+        assert np.array_equal(res[i], r[seg])
+    assert np.abs(imfs.sum(0) + res - X).max() <= 1e-12
