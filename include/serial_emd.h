@@ -1,0 +1,232 @@
+/*
+ * serial_emd.h -- C ABI of the GB300 Serial-EMD library (libserial_emd.so).
+ *
+ * Serial-EMD (Zhang et al., arXiv 2106.15319) decomposes a multivariate series
+ * or a 2D image by (1) serializing its N signals of length M into one 1D signal
+ * of length L = MN + DN - D, joined by D-sample linear-blend transitions
+ * (Sec. 3.1-3.2), (2) running 1D empirical mode decomposition on it: extrema,
+ * cubic-spline envelopes, mean subtraction and a stop test, repeated per IMF
+ * (Sec. 2.1, Eq. 1; EEMD Sec. 2.2), and (3) de-serializing the IMFs back to the
+ * input's shape, dropping the transitions (Sec. 3.3).
+ *
+ * Every step runs in this library's CUDA kernels on one GPU. There is no CPU
+ * fallback: when no usable GPU is present the calls return SEMD_ECUDA.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers; everything else is host memory.
+ *  - Arrays are dense and row-major. An input of shape rows x cols holds its N
+ *    signals as rows (SEMD_ORDER_ROWS: M = cols, N = rows; a channels x samples
+ *    series or an image read row after row) or as columns (SEMD_ORDER_COLS:
+ *    M = rows, N = cols).
+ *  - The element type of inputs and IMF outputs follows the plan's precision:
+ *    double for SEMD_FP64, float for SEMD_FP32_MIXED. Residues are always double.
+ *  - IMF outputs are K x rows x cols (K = max_imfs); slots past the number of
+ *    IMFs produced are zero-filled (the paper pads missing IMFs with zeros,
+ *    Sec. 4.3, table of IMF counts).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - The caller owns every buffer it passes and keeps it alive until the call's
+ *    work has finished on the stream (or, for the server, until poll reports a
+ *    final status). The library owns plans, servers and their workspaces.
+ *  - No call aborts or exits. Each returns a semd_status; the text of the last
+ *    error on a plan or server is returned by serial_emd_last_error().
+ */
+#ifndef SERIAL_EMD_H
+#define SERIAL_EMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum semd_status {
+    SEMD_OK = 0,
+    SEMD_PENDING = 1,      /* poll: the request is queued or running */
+    SEMD_EINVAL = -1,      /* an argument is out of range or inconsistent */
+    SEMD_ENOMEM = -2,      /* a device or host allocation failed */
+    SEMD_EBUDGET = -3,     /* the work does not fit the plan's or server's byte budget */
+    SEMD_ECUDA = -4,       /* a CUDA call failed (no device, launch error, ...) */
+    SEMD_ETIMEOUT = -5,    /* a bounded wait ran out */
+    SEMD_ECANCELED = -6,   /* the server was destroyed before the request finished */
+    SEMD_EUNSUPPORTED = -7 /* a valid option this build does not implement */
+} semd_status;
+
+typedef enum semd_order { SEMD_ORDER_ROWS = 0, SEMD_ORDER_COLS = 1 } semd_order;
+typedef enum semd_stop { SEMD_STOP_FIXED = 0, SEMD_STOP_SD = 1 } semd_stop;
+typedef enum semd_boundary { SEMD_BOUNDARY_MIRROR = 0, SEMD_BOUNDARY_ENDPOINTS = 1 } semd_boundary;
+typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precision;
+
+/*
+ * Parameters of the method, following the paper's statement of the problem:
+ *  rows, cols       shape of one input (the plan's capacity unit, see serial_emd_plan).
+ *  order            which axis holds the N signals (see conventions above).
+ *  transition_len   D of Sec. 3.2, 0 <= D <= M; -1 selects round(0.2 M), the
+ *                   20 % rule of Sec. 4.1.
+ *  max_imfs         K, 1 <= K <= 32 (Sec. 3.3; the paper caps at 10 in Sec. 4.3).
+ *  stop             SEMD_STOP_FIXED: exactly fixed_sifts sifts per IMF (>= 1).
+ *                   SEMD_STOP_SD: sift until sum (h_prev - h)^2 / sum h_prev^2 <
+ *                   sd_threshold, at most max_sifts sifts. Sec. 2.1 Step 5 leaves the
+ *                   criterion open ("some predefined stopping criterion").
+ *  boundary         envelope end rule (the paper is silent): MIRROR reflects the
+ *                   first and last mirror_knots (1 or 2) extrema about the ends;
+ *                   ENDPOINTS adds the two end samples as knots.
+ *  precision        SEMD_FP64: FP64 end to end. SEMD_FP32_MIXED: sifting in FP32,
+ *                   FP64 in the cross-tile spline interface solve, the stop
+ *                   reductions, the residue and the EEMD average.
+ *  ensemble_trials  <= 1: EMD. > 1: EEMD with that many noise realizations (Sec. 2.2).
+ *  noise_rel_std    EEMD beta = noise_rel_std * population std of the serialized x.
+ */
+typedef struct semd_params {
+    int64_t rows;
+    int64_t cols;
+    int32_t order;
+    int32_t transition_len;
+    int32_t max_imfs;
+    int32_t stop;
+    int32_t fixed_sifts;
+    int32_t max_sifts;
+    double sd_threshold;
+    int32_t boundary;
+    int32_t mirror_knots;
+    int32_t precision;
+    int32_t ensemble_trials;
+    double noise_rel_std;
+} semd_params;
+
+/* Fills p with the defaults: ROWS order, D = -1 (20 % rule), K = 10, fixed 10 sifts,
+ * SD threshold 0.2 with at most 50 sifts, MIRROR with 2 knots, FP32_MIXED, EMD. */
+void serial_emd_default_params(semd_params *p);
+
+typedef struct semd_plan_s *semd_plan_t;
+
+/*
+ * Creates a plan: validates params and reserves every device workspace up front,
+ * so that the decompose calls allocate nothing. Capacity: up to max_batch inputs
+ * of at most params->rows x params->cols elements each (for EEMD, one input and
+ * ensemble_trials realizations). mem_budget > 0 caps the workspace bytes
+ * (SEMD_EBUDGET if it does not fit); 0 means no cap. On success *out owns the
+ * plan until serial_emd_destroy. Errors: EINVAL, EBUDGET, ENOMEM, ECUDA.
+ */
+semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem_budget,
+                            semd_plan_t *out);
+
+/* Bytes of device workspace the plan holds. */
+size_t serial_emd_plan_bytes(semd_plan_t plan);
+
+/*
+ * Serial-EMD of one input of the plan's shape (Sec. 3: serialize, EMD or EEMD,
+ * de-serialize), enqueued on `stream`.
+ *  d_x        input, rows x cols (plan precision).
+ *  d_noise    EEMD only: ensemble_trials x L white-noise realizations w^(m)
+ *             (plan precision, L = MN + DN - D); ignored for EMD.
+ *  d_imfs     output, K x rows x cols (plan precision); for EEMD the trial average.
+ *  d_residue  output, rows x cols doubles; may be NULL.
+ *  n_imfs     host; if not NULL the call waits for the stream and stores the IMF
+ *             count (for EEMD the largest count over the trials). If NULL the call
+ *             returns without waiting and serial_emd_plan_counts() gives the counts
+ *             after the stream has finished.
+ * The plan may not be used by two calls at once. Errors: EINVAL, ECUDA.
+ */
+semd_status serial_emd_decompose(semd_plan_t plan, const void *d_x, const void *d_noise,
+                                 void *d_imfs, double *d_residue, int *n_imfs, void *stream);
+
+/* One input of a batch: its own shape (within the plan's capacity) and buffers. */
+typedef struct semd_instance {
+    const void *d_x;   /* rows x cols input (plan precision) */
+    int64_t rows;
+    int64_t cols;
+    void *d_imfs;      /* K x rows x cols output (plan precision) */
+    double *d_residue; /* rows x cols doubles, or NULL */
+} semd_instance;
+
+/*
+ * Serial-EMD of `count` independent inputs of different shapes in one batched run:
+ * every pass over the signals covers all inputs at once. Each input's result is
+ * bit-identical to decomposing it alone. count <= max_batch and the summed
+ * serialized lengths must fit the plan (EBUDGET otherwise). EMD plans only
+ * (EINVAL for EEMD plans). n_imfs: host array of `count`, or NULL (see decompose).
+ */
+semd_status serial_emd_decompose_batch(semd_plan_t plan, int count, const semd_instance *inst,
+                                       int *n_imfs, void *stream);
+
+/* After the stream has finished: IMF counts (count entries) and sifts per IMF
+ * (count x K entries, may be NULL) of the plan's last decompose call. */
+semd_status serial_emd_plan_counts(semd_plan_t plan, int count, int *n_imfs, int *sifts);
+
+/*
+ * Step-level entry points (Sec. 2.1 Step 1 and Steps 1-4 on an already
+ * serialized signal), for unit tests and for callers that sift themselves.
+ * serial_emd_extrema: d_h has L elements (plan precision); writes the ascending
+ * indices of the maxima to d_tmax and of the minima to d_tmin (int32, capacity L/2+1
+ * each) and their counts to the host ints n_max / n_min (waits for the stream).
+ * Rule: maximum at k iff h[k-1] < h[k] >= h[k+1], minimum iff h[k-1] > h[k] <=
+ * h[k+1], for 1 <= k <= L-2.
+ * serial_emd_sift: one sift of d_h into d_out (L elements each); returns through
+ * the host pointers the sums (h - h')^2 and h^2. SEMD_EINVAL if either kind of
+ * extremum is missing. L must not exceed the plan's serialized length.
+ */
+semd_status serial_emd_extrema(semd_plan_t plan, const void *d_h, int64_t L, int32_t *d_tmax,
+                               int32_t *d_tmin, int64_t *n_max, int64_t *n_min, void *stream);
+semd_status serial_emd_sift(semd_plan_t plan, const void *d_h, int64_t L, void *d_out,
+                            double *sd_num, double *sd_den, void *stream);
+
+/* Releases a plan and its workspaces (after its work on any stream has finished). */
+void serial_emd_destroy(semd_plan_t plan);
+
+/* Text of the last error on a plan (or of the last failed plan creation if NULL). */
+const char *serial_emd_last_error(semd_plan_t plan);
+
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * A server decomposes requests of different shapes as they arrive (continuous
+ * batching): a host thread admits queued requests whenever slots and the byte
+ * budget allow, runs one pass of the sifting loop over every admitted request at
+ * once, and retires requests as they finish, so new ones join while others are on
+ * the GPU. Per-request results are identical to decomposing the request alone.
+ *  defaults     method parameters; rows/cols give the largest accepted request
+ *               (its serialized length must not exceed that of rows x cols).
+ *  mem_budget   device bytes the server may hold for request state (> 0).
+ *  max_inflight most requests on the GPU at once (>= 1).
+ * EEMD is not served (EUNSUPPORTED). Errors: EINVAL, ENOMEM, ECUDA.
+ */
+typedef struct semd_server_s *semd_server_t;
+
+semd_status serial_emd_server_create(const semd_params *defaults, size_t mem_budget,
+                                     int max_inflight, semd_server_t *out);
+
+typedef struct semd_request {
+    const void *d_x;   /* rows x cols input (server precision) */
+    int64_t rows;
+    int64_t cols;
+    int32_t order;     /* SEMD_ORDER_ROWS / SEMD_ORDER_COLS */
+    int32_t _reserved;
+    void *d_imfs;      /* K x rows x cols output (server precision) */
+    double *d_residue; /* rows x cols doubles, or NULL */
+} semd_request;
+
+typedef struct semd_result {
+    int32_t status;     /* SEMD_OK, or the error that ended the request */
+    int32_t n_imfs;
+    int64_t sifts;      /* total sifts over all IMFs */
+    double queue_ms;    /* submit -> admission */
+    double run_ms;      /* admission -> outputs written */
+} semd_result;
+
+/* Queues a request; *ticket identifies it. EBUDGET if it could never fit. */
+semd_status serial_emd_submit(semd_server_t server, const semd_request *req, uint64_t *ticket);
+
+/* Non-blocking: SEMD_PENDING while the request is queued or running; otherwise
+ * fills *out (once) and returns SEMD_OK. EINVAL for an unknown ticket. */
+semd_status serial_emd_poll(semd_server_t server, uint64_t ticket, semd_result *out);
+
+/* Stops the server thread; unfinished requests end with SEMD_ECANCELED. */
+void serial_emd_server_destroy(semd_server_t server);
+
+const char *serial_emd_server_last_error(semd_server_t server);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SERIAL_EMD_H */

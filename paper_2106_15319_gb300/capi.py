@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libserial_emd.so (the C ABI in include/serial_emd.h).
+
+Argument marshalling only: every step of Serial-EMD runs in the library's CUDA
+kernels. Functions keep the C names; tensors are torch CUDA tensors whose data
+pointers are passed through. There is no CPU fallback: loading fails loudly if
+the library is missing, and the calls raise when the C ABI returns an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SEMD_OK, SEMD_PENDING = 0, 1
+SEMD_EINVAL, SEMD_ENOMEM, SEMD_EBUDGET, SEMD_ECUDA = -1, -2, -3, -4
+SEMD_ETIMEOUT, SEMD_ECANCELED, SEMD_EUNSUPPORTED = -5, -6, -7
+ORDER_ROWS, ORDER_COLS = 0, 1
+STOP_FIXED, STOP_SD = 0, 1
+BOUNDARY_MIRROR, BOUNDARY_ENDPOINTS = 0, 1
+FP64, FP32_MIXED = 0, 1
+
+_STATUS = {0: "OK", 1: "PENDING", -1: "EINVAL", -2: "ENOMEM", -3: "EBUDGET", -4: "ECUDA",
+           -5: "ETIMEOUT", -6: "ECANCELED", -7: "EUNSUPPORTED"}
+
+
+class SemdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class semd_params(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("order", ctypes.c_int32),
+                ("transition_len", ctypes.c_int32), ("max_imfs", ctypes.c_int32),
+                ("stop", ctypes.c_int32), ("fixed_sifts", ctypes.c_int32),
+                ("max_sifts", ctypes.c_int32), ("sd_threshold", ctypes.c_double),
+                ("boundary", ctypes.c_int32), ("mirror_knots", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("ensemble_trials", ctypes.c_int32),
+                ("noise_rel_std", ctypes.c_double)]
+
+
+class semd_instance(ctypes.Structure):
+    _fields_ = [("d_x", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("d_imfs", ctypes.c_void_p), ("d_residue", ctypes.c_void_p)]
+
+
+class semd_request(ctypes.Structure):
+    _fields_ = [("d_x", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("order", ctypes.c_int32), ("_reserved", ctypes.c_int32),
+                ("d_imfs", ctypes.c_void_p), ("d_residue", ctypes.c_void_p)]
+
+
+class semd_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_imfs", ctypes.c_int32),
+                ("sifts", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "serial_emd_default_params": (None, [ctypes.POINTER(semd_params)]),
+    "serial_emd_plan": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_int, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "serial_emd_plan_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "serial_emd_decompose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "serial_emd_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.POINTER(semd_instance),
+                                                  ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "serial_emd_plan_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
+    "serial_emd_extrema": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "serial_emd_sift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "serial_emd_destroy": (None, [ctypes.c_void_p]),
+    "serial_emd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "serial_emd_server_create": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_size_t,
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "serial_emd_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_request),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "serial_emd_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.POINTER(semd_result)]),
+    "serial_emd_server_destroy": (None, [ctypes.c_void_p]),
+    "serial_emd_server_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads the in-tree library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libserial_emd.so not found at {path}; run build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc: int, handle, err_fn="serial_emd_last_error"):
+    if rc < 0:
+        msg = getattr(load(), err_fn)(handle)
+        raise SemdError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ------------------------------------------------------------------ C-named wrappers
+
+def serial_emd_default_params(**overrides) -> semd_params:
+    p = semd_params()
+    load().serial_emd_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def serial_emd_plan(params: semd_params, max_batch: int = 1, mem_budget: int = 0) -> int:
+    h = ctypes.c_void_p()
+    rc = load().serial_emd_plan(ctypes.byref(params), max_batch, mem_budget, ctypes.byref(h))
+    _check(rc, None)
+    return h.value
+
+
+def serial_emd_plan_bytes(plan: int) -> int:
+    return int(load().serial_emd_plan_bytes(plan))
+
+
+def serial_emd_decompose(plan: int, x, noise, imfs, residue, stream=None, wait: bool = True):
+    n = ctypes.c_int(-1)
+    rc = load().serial_emd_decompose(plan, _ptr(x), _ptr(noise), _ptr(imfs), _ptr(residue),
+                                     ctypes.byref(n) if wait else None, _stream(stream))
+    _check(rc, plan)
+    return n.value if wait else None
+
+
+def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True):
+    """items: list of (x, imfs, residue) CUDA tensors, x 2D (rows, cols)."""
+    arr = (semd_instance * len(items))()
+    for i, (x, imfs, res) in enumerate(items):
+        arr[i] = semd_instance(_ptr(x), x.shape[0], x.shape[1], _ptr(imfs), _ptr(res))
+    n = (ctypes.c_int * len(items))()
+    rc = load().serial_emd_decompose_batch(plan, len(items), arr, n if wait else None,
+                                           _stream(stream))
+    _check(rc, plan)
+    return list(n) if wait else None
+
+
+def serial_emd_plan_counts(plan: int, count: int, max_imfs: int):
+    n = (ctypes.c_int * count)()
+    s = (ctypes.c_int * (count * max_imfs))()
+    _check(load().serial_emd_plan_counts(plan, count, n, s), plan)
+    return list(n), [list(s[i * max_imfs:(i + 1) * max_imfs]) for i in range(count)]
+
+
+def serial_emd_extrema(plan: int, h, tmax, tmin, stream=None):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    rc = load().serial_emd_extrema(plan, _ptr(h), h.numel(), _ptr(tmax), _ptr(tmin),
+                                   ctypes.byref(a), ctypes.byref(b), _stream(stream))
+    _check(rc, plan)
+    return a.value, b.value
+
+
+def serial_emd_sift(plan: int, h, out, stream=None):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = load().serial_emd_sift(plan, _ptr(h), h.numel(), _ptr(out), ctypes.byref(a),
+                                ctypes.byref(b), _stream(stream))
+    _check(rc, plan)
+    return a.value, b.value
+
+
+def serial_emd_destroy(plan: int) -> None:
+    if plan:
+        load().serial_emd_destroy(plan)
+
+
+def serial_emd_last_error(plan) -> str:
+    m = load().serial_emd_last_error(plan)
+    return m.decode() if m else ""
+
+
+def serial_emd_server_create(params: semd_params, mem_budget: int, max_inflight: int) -> int:
+    h = ctypes.c_void_p()
+    rc = load().serial_emd_server_create(ctypes.byref(params), mem_budget, max_inflight,
+                                         ctypes.byref(h))
+    if rc < 0:
+        raise SemdError(rc, serial_emd_server_last_error(None))
+    return h.value
+
+
+def serial_emd_submit(server: int, x, imfs, residue, order: int = ORDER_ROWS) -> int:
+    req = semd_request(_ptr(x), x.shape[0], x.shape[1], order, 0, _ptr(imfs), _ptr(residue))
+    t = ctypes.c_uint64()
+    rc = load().serial_emd_submit(server, ctypes.byref(req), ctypes.byref(t))
+    _check(rc, server, "serial_emd_server_last_error")
+    return t.value
+
+
+def serial_emd_poll(server: int, ticket: int):
+    """Returns None while pending, else the semd_result."""
+    r = semd_result()
+    rc = load().serial_emd_poll(server, ticket, ctypes.byref(r))
+    if rc == SEMD_PENDING:
+        return None
+    _check(rc, server, "serial_emd_server_last_error")
+    return r
+
+
+def serial_emd_server_destroy(server: int) -> None:
+    if server:
+        load().serial_emd_server_destroy(server)
+
+
+def serial_emd_server_last_error(server) -> str:
+    m = load().serial_emd_server_last_error(server)
+    return m.decode() if m else ""

@@ -1,0 +1,841 @@
+// Host runtime and C ABI of the GB300 Serial-EMD library: plans, workspaces, the
+// pass loop, serialization (Sec. 3.2), de-serialization (Sec. 3.3) and the EEMD
+// ensemble (Sec. 2.2). See semd_device.cuh for the sifting kernels.
+#include "semd_runtime.h"
+#include "semd_device.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace semd {
+
+static thread_local std::string g_plan_create_error;
+
+// ----------------------------------------------------------------- helper kernels
+
+// Sec. 3.2 serialization, one CTA per tile: x[i(M+D)+m] = X(i, m) for m < M and, for
+// the D transition samples between signal i and i+1 (0-based r),
+// x = (r+1)/(D+1) * X(i+1, D-1-r) + (D-r)/(D+1) * X(i, M-1-r). Written in FP64 to r0.
+template <typename R>
+__global__ void k_serialize(const Inst *inst, const int32_t *tile_inst, double *r0, int tile,
+                            int only_first)
+{
+    const int gt = blockIdx.x, ii = tile_inst[gt];
+    if (only_first && ii != 0)
+        return;
+    const Inst &in = inst[ii];
+    const int64_t ts = (int64_t)(gt - in.tile0) * tile;
+    const int64_t cnt = min((int64_t)tile, in.L - ts);
+    const R *X = (const R *)in.x;
+    const int64_t M = in.M, N = in.N, D = in.D;
+    for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+        const int64_t p = ts + idx;
+        const int64_t i = p / (M + D), m = p - i * (M + D);
+        double v;
+        if (m < M) {
+            v = (double)X[in.order == 0 ? i * M + m : m * N + i];
+        } else {
+            const int64_t r = m - M;
+            const int64_t ma = D - 1 - r, mb = M - 1 - r;
+            const double xa = (double)X[in.order == 0 ? (i + 1) * M + ma : ma * N + (i + 1)];
+            const double xb = (double)X[in.order == 0 ? i * M + mb : mb * N + i];
+            const double a = (double)(r + 1) / (double)(D + 1);
+            const double af = (double)(D - r) / (double)(D + 1);
+            v = __dadd_rn(__dmul_rn(xa, a), __dmul_rn(xb, af));
+        }
+        r0[in.off + p] = v;
+    }
+}
+
+// EEMD beta = rel * population std of the serialized x (Sec. 2.2 Step 1), one CTA.
+__global__ void k_std(const double *x, int64_t L, double rel, double *beta)
+{
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
+        s += x[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double mean = sh[0] / (double)L;
+    __syncthreads();
+    double v = 0.0;
+    for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
+        v += (x[k] - mean) * (x[k] - mean);
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *beta = rel * sqrt(sh[0] / (double)L);
+}
+
+// x^(m) = x + beta w^(m) for every trial (Sec. 2.2 Step 1); trial 0 holds x on entry.
+template <typename R>
+__global__ void k_add_noise(const Inst *inst, int trials, const R *w, const double *beta,
+                            double *r0)
+{
+    const int64_t L = inst[0].L;
+    const double b = *beta;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double x = r0[inst[0].off + p];
+        for (int m = trials - 1; m >= 0; --m)
+            r0[inst[m].off + p] = __dadd_rn(x, __dmul_rn(b, (double)w[(int64_t)m * L + p]));
+    }
+}
+
+// Sec. 3.3 for the residue, and zero-fill of the IMF slots past the produced count.
+template <typename R>
+__global__ void k_finalize(const Inst *inst, const State *state, const int32_t *tile_inst,
+                           const double *r0, const double *r1, int tile, int K)
+{
+    const int gt = blockIdx.x, ii = tile_inst[gt];
+    const Inst &in = inst[ii];
+    if (in.imf_serialized)
+        return;
+    const int n = state[ii].imf_count;
+    const double *r = (state[ii].rpar ? r1 : r0) + in.off;
+    const int64_t ts = (int64_t)(gt - in.tile0) * tile;
+    const int64_t cnt = min((int64_t)tile, in.L - ts);
+    R *imf = (R *)in.imf;
+    for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+        const int64_t p = ts + idx;
+        int64_t dst;
+        if (!deser_index(p, in.M, in.N, in.D, in.order, dst))
+            continue;
+        if (in.res)
+            in.res[dst] = r[p];
+        for (int k = n; k < K; ++k)
+            imf[(int64_t)k * in.imf_stride + dst] = R(0);
+    }
+}
+
+// EEMD Step 3: average the trials' IMFs (zeros where a trial has fewer) and residues,
+// in FP64 and in trial order, then de-serialize (Sec. 3.3).
+template <typename R>
+__global__ void k_eemd_average(const Inst *inst, const State *state, int trials, int K,
+                               const R *scratch, const double *r0, const double *r1, R *out,
+                               double *res, int tile)
+{
+    const Inst &in = inst[0];
+    const int64_t L = in.L;
+    const int64_t ts = (int64_t)blockIdx.x * tile;
+    const int64_t cnt = min((int64_t)tile, L - ts);
+    const int64_t outstride = in.M * in.N;
+    for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+        const int64_t p = ts + idx;
+        int64_t dst;
+        if (!deser_index(p, in.M, in.N, in.D, in.order, dst))
+            continue;
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int m = 0; m < trials; ++m)
+                if (k < state[m].imf_count)
+                    acc += (double)scratch[((int64_t)m * K + k) * L + p];
+            out[(int64_t)k * outstride + dst] = (R)(acc / (double)trials);
+        }
+        if (res) {
+            double acc = 0.0;
+            for (int m = 0; m < trials; ++m)
+                acc += (state[m].rpar ? r1 : r0)[inst[m].off + p];
+            res[dst] = acc / (double)trials;
+        }
+    }
+}
+
+// Standalone extrema (Sec. 2.1 Step 1): per-tile counts, then ordered writes.
+template <typename R>
+__global__ void k_extrema_tiles(const R *h, int64_t L, int tile, const int32_t *base,
+                                int32_t *counts, int32_t *tmax, int32_t *tmin)
+{
+    const int64_t ts = (int64_t)blockIdx.x * tile;
+    const int64_t cnt = min((int64_t)tile, L - ts);
+    if (threadIdx.x != 0)
+        return;
+    int a = 0, b = 0;
+    int oa = base ? base[2 * blockIdx.x] : 0, ob = base ? base[2 * blockIdx.x + 1] : 0;
+    for (int64_t k = ts; k < ts + cnt; ++k) {
+        if (k < 1 || k > L - 2)
+            continue;
+        const R l = h[k - 1], c = h[k], r = h[k + 1];
+        if (l < c && c >= r) {
+            if (base)
+                tmax[oa + a] = (int32_t)k;
+            ++a;
+        }
+        if (l > c && c <= r) {
+            if (base)
+                tmin[ob + b] = (int32_t)k;
+            ++b;
+        }
+    }
+    if (!base) {
+        counts[2 * blockIdx.x] = a;
+        counts[2 * blockIdx.x + 1] = b;
+    }
+}
+
+template <typename R>
+__global__ void k_to_double(const R *h, int64_t L, double *r)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L;
+         p += (int64_t)gridDim.x * blockDim.x)
+        r[p] = (double)h[p];
+}
+
+// ------------------------------------------------------------------ plan helpers
+
+template <typename R>
+static cudaError_t set_smem_attr()
+{
+    return cudaFuncSetAttribute(k_pass<R, kTile, kThreads>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(PassSmem<R, kTile, kThreads>));
+}
+
+int64_t serial_length(int64_t M, int64_t N, int64_t D) { return M * N + D * N - D; }
+
+bool geometry(const semd_params &p, int64_t rows, int64_t cols, int order, int64_t &M,
+              int64_t &N, int64_t &D, std::string &err)
+{
+    if (rows < 1 || cols < 1) {
+        err = "rows and cols must be >= 1";
+        return false;
+    }
+    M = order == SEMD_ORDER_ROWS ? cols : rows;
+    N = order == SEMD_ORDER_ROWS ? rows : cols;
+    D = p.transition_len < 0 ? (int64_t)std::llround(0.2 * (double)M) : p.transition_len;
+    if (N == 1)
+        D = 0; // one signal: there is nothing to join
+    if (D > M) {
+        err = "transition_len must be <= M (X_A needs D rows, Sec. 3.2)";
+        return false;
+    }
+    if (serial_length(M, N, D) >= (int64_t)1 << 30) {
+        err = "serialized length must be < 2^30";
+        return false;
+    }
+    return true;
+}
+
+bool validate(const semd_params &p, std::string &err)
+{
+    if (p.order != SEMD_ORDER_ROWS && p.order != SEMD_ORDER_COLS)
+        return err = "order must be ROWS or COLS", false;
+    if (p.max_imfs < 1 || p.max_imfs > KMAX)
+        return err = "max_imfs must be in [1, 32]", false;
+    if (p.stop != SEMD_STOP_FIXED && p.stop != SEMD_STOP_SD)
+        return err = "stop must be FIXED or SD", false;
+    if (p.stop == SEMD_STOP_FIXED && (p.fixed_sifts < 1 || p.fixed_sifts > 1000))
+        return err = "fixed_sifts must be in [1, 1000]", false;
+    if (p.stop == SEMD_STOP_SD && (p.max_sifts < 1 || p.max_sifts > 1000 || !(p.sd_threshold >= 0)))
+        return err = "max_sifts must be in [1, 1000] and sd_threshold >= 0", false;
+    if (p.boundary != SEMD_BOUNDARY_MIRROR && p.boundary != SEMD_BOUNDARY_ENDPOINTS)
+        return err = "boundary must be MIRROR or ENDPOINTS", false;
+    if (p.boundary == SEMD_BOUNDARY_MIRROR && (p.mirror_knots < 1 || p.mirror_knots > 2))
+        return err = "mirror_knots must be 1 or 2", false;
+    if (p.precision != SEMD_FP64 && p.precision != SEMD_FP32_MIXED)
+        return err = "precision must be FP64 or FP32_MIXED", false;
+    if (p.ensemble_trials > 1 && !(p.noise_rel_std >= 0))
+        return err = "noise_rel_std must be >= 0", false;
+    if (p.transition_len < -1)
+        return err = "transition_len must be >= -1", false;
+    return true;
+}
+
+int max_iterations(const semd_params &p)
+{
+    return p.stop == SEMD_STOP_FIXED ? 1 + p.max_imfs * p.fixed_sifts
+                                     : 1 + p.max_imfs * (p.max_sifts + 1);
+}
+
+#define SEMD_CU(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                      \
+            return SEMD_ECUDA;                                                             \
+        }                                                                                  \
+    } while (0)
+
+semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64_t rentries,
+                                int iters, size_t elem, int64_t eemd_elems, size_t budget,
+                                std::string &err)
+{
+    cap_samples = samples;
+    cap_inst = insts;
+    cap_tiles = tiles;
+    cap_rentries = rentries;
+    cap_iters = iters;
+    elem_size = elem;
+    struct Req {
+        void **p;
+        size_t bytes;
+    };
+    std::vector<Req> reqs = {
+        {&h0, (size_t)samples * elem},
+        {&h1, (size_t)samples * elem},
+        {(void **)&r0, (size_t)samples * 8},
+        {(void **)&r1, (size_t)samples * 8},
+        {(void **)&d_inst, (size_t)insts * sizeof(Inst)},
+        {(void **)&d_state, (size_t)insts * sizeof(State)},
+        {(void **)&d_tile_inst, (size_t)tiles * 4},
+        {(void **)&d_tex, (size_t)tiles * 2 * sizeof(TileExport)},
+        {(void **)&d_tsol, (size_t)tiles * 2 * sizeof(TileSolve)},
+        {(void **)&d_taux, (size_t)tiles * sizeof(TileAux)},
+        {(void **)&d_rbase, (size_t)insts * 8},
+        {(void **)&d_rent, (size_t)rentries * sizeof(REntry)},
+        {(void **)&d_rA, (size_t)rentries * 8},
+        {(void **)&d_rB, (size_t)rentries * 8},
+        {(void **)&d_rC, (size_t)rentries * 8},
+        {(void **)&d_rD, (size_t)rentries * 8},
+        {(void **)&d_rcp, (size_t)rentries * 8},
+        {(void **)&d_rdp, (size_t)rentries * 8},
+        {(void **)&d_rbp, (size_t)rentries * 8},
+        {(void **)&d_rM, (size_t)rentries * 8},
+        {(void **)&d_active, (size_t)iters * 4},
+        {(void **)&d_beta, 8},
+        {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
+    };
+    if (eemd_elems > 0)
+        reqs.push_back({&eemd_scratch, (size_t)eemd_elems * elem});
+    size_t total = 0;
+    for (auto &r : reqs)
+        total += (r.bytes + 255) & ~(size_t)255;
+    if (budget > 0 && total > budget) {
+        err = "workspace of " + std::to_string(total) + " bytes exceeds the budget of " +
+              std::to_string(budget);
+        return SEMD_EBUDGET;
+    }
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc of the workspace: ") + cudaGetErrorString(e);
+        base = nullptr;
+        return e == cudaErrorMemoryAllocation ? SEMD_ENOMEM : SEMD_ECUDA;
+    }
+    bytes = total;
+    char *cur = (char *)base;
+    for (auto &r : reqs) {
+        *r.p = cur;
+        cur += (r.bytes + 255) & ~(size_t)255;
+    }
+    e = cudaMallocHost((void **)&h_inst, (size_t)insts * sizeof(Inst));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h_tile_inst, (size_t)tiles * 4);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h_rbase, (size_t)insts * 8);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h_state, (size_t)insts * sizeof(State));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h_misc, (size_t)tiles * 2 * 4 + 64);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&staging_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        err = std::string("pinned host staging: ") + cudaGetErrorString(e);
+        return SEMD_ENOMEM;
+    }
+    if (elem == 8)
+        e = set_smem_attr<double>();
+    else
+        e = set_smem_attr<float>();
+    if (e != cudaSuccess) {
+        err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return SEMD_ECUDA;
+    }
+    return SEMD_OK;
+}
+
+void Workspace::release()
+{
+    if (staging_done) {
+        cudaEventSynchronize(staging_done);
+        cudaEventDestroy(staging_done);
+    }
+    if (base)
+        cudaFree(base);
+    if (h_inst)
+        cudaFreeHost(h_inst);
+    if (h_tile_inst)
+        cudaFreeHost(h_tile_inst);
+    if (h_rbase)
+        cudaFreeHost(h_rbase);
+    if (h_state)
+        cudaFreeHost(h_state);
+    if (h_misc)
+        cudaFreeHost(h_misc);
+    *this = Workspace();
+}
+
+// Lays out n instances (host descriptors in ws.h_inst must have L, geometry and
+// output pointers set); fills offsets, tiles and scratch bases; uploads.
+semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::string &err)
+{
+    int64_t off = 0, tiles = 0, rent = 0;
+    for (int i = 0; i < n; ++i) {
+        Inst &in = h_inst[i];
+        in.off = off;
+        in.tile0 = (int32_t)tiles;
+        in.ntiles = (int32_t)((in.L + kTile - 1) / kTile);
+        h_rbase[i] = rent;
+        off += (in.L + 31) & ~(int64_t)31;
+        tiles += in.ntiles;
+        rent += 2 * skew_len(reduce_entries(in.ntiles));
+    }
+    if (off > cap_samples || tiles > cap_tiles || rent > cap_rentries || n > cap_inst) {
+        err = "batch exceeds the plan's capacity";
+        return SEMD_EBUDGET;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int t = 0; t < h_inst[i].ntiles; ++t)
+            h_tile_inst[h_inst[i].tile0 + t] = i;
+    ntiles = tiles;
+    SEMD_CU(cudaMemcpyAsync(d_inst, h_inst, (size_t)n * sizeof(Inst), cudaMemcpyHostToDevice, s));
+    SEMD_CU(cudaMemcpyAsync(d_tile_inst, h_tile_inst, (size_t)tiles * 4, cudaMemcpyHostToDevice,
+                            s));
+    SEMD_CU(cudaMemcpyAsync(d_rbase, h_rbase, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    SEMD_CU(cudaEventRecord(staging_done, s));
+    return SEMD_OK;
+}
+
+template <typename R>
+static void launch_pass(Workspace &ws, int64_t ntiles, cudaStream_t s)
+{
+    PassArgs pa;
+    pa.inst = ws.d_inst;
+    pa.state = ws.d_state;
+    pa.tile_inst = ws.d_tile_inst;
+    pa.h0 = ws.h0;
+    pa.h1 = ws.h1;
+    pa.r0 = ws.r0;
+    pa.r1 = ws.r1;
+    pa.tex = ws.d_tex;
+    pa.tsol = ws.d_tsol;
+    pa.taux = ws.d_taux;
+    k_pass<R, kTile, kThreads>
+        <<<(unsigned)ntiles, kThreads, sizeof(PassSmem<R, kTile, kThreads>), s>>>(pa);
+}
+
+static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
+{
+    ReduceArgs ra;
+    ra.inst = ws.d_inst;
+    ra.state = ws.d_state;
+    ra.tex = ws.d_tex;
+    ra.tsol = ws.d_tsol;
+    ra.taux = ws.d_taux;
+    ra.rbase = ws.d_rbase;
+    ra.rent = ws.d_rent;
+    ra.rA = ws.d_rA;
+    ra.rB = ws.d_rB;
+    ra.rC = ws.d_rC;
+    ra.rD = ws.d_rD;
+    ra.rcp = ws.d_rcp;
+    ra.rdp = ws.d_rdp;
+    ra.rbp = ws.d_rbp;
+    ra.rM = ws.d_rM;
+    ra.active = ws.d_active;
+    ra.K = p.max_imfs;
+    ra.stop = p.stop;
+    ra.fixed_sifts = p.fixed_sifts;
+    ra.max_sifts = p.max_sifts;
+    ra.sd_threshold = p.sd_threshold;
+    ra.boundary = p.boundary;
+    ra.mirror_knots = p.mirror_knots;
+    return ra;
+}
+
+// Runs passes until every instance is done (the state of each instance must be
+// initialised to MODE_INIT with r0 holding its serialized signal).
+template <typename R>
+static semd_status run_passes(Workspace &ws, const semd_params &p, int ninst, int64_t ntiles,
+                              cudaStream_t s, std::string &err)
+{
+    const int iters = max_iterations(p);
+    SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
+    ReduceArgs ra = reduce_args(ws, p);
+    for (int it = 0; it < iters; ++it) {
+        launch_pass<R>(ws, ntiles, s);
+        ra.active = ws.d_active + it;
+        k_reduce<<<ninst, 64, 0, s>>>(ra);
+        if (p.stop == SEMD_STOP_SD && (it % 8) == 7) {
+            SEMD_CU(cudaMemcpyAsync(ws.h_misc, ws.d_active + it, 4, cudaMemcpyDeviceToHost, s));
+            SEMD_CU(cudaStreamSynchronize(s));
+            if (((int32_t *)ws.h_misc)[0] == 0)
+                break;
+        }
+    }
+    SEMD_CU(cudaGetLastError());
+    return SEMD_OK;
+}
+
+template <typename R>
+semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *insts,
+                           const void *d_noise, int *n_imfs, cudaStream_t s)
+{
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    const semd_params &p = pl.p;
+    const bool eemd = p.ensemble_trials > 1;
+    const int ninst = eemd ? p.ensemble_trials : count;
+    SEMD_CU(cudaEventSynchronize(ws.staging_done)); // staging buffers are free again
+    for (int i = 0; i < ninst; ++i) {
+        const semd_instance &q = insts[eemd ? 0 : i];
+        Inst in{};
+        int64_t M, N, D;
+        if (!geometry(p, q.rows, q.cols, p.order, M, N, D, err))
+            return SEMD_EINVAL;
+        in.L = serial_length(M, N, D);
+        in.M = M;
+        in.N = N;
+        in.D = D;
+        in.order = p.order;
+        in.x = q.d_x;
+        if (eemd) {
+            in.imf = (char *)ws.eemd_scratch + (size_t)i * p.max_imfs * in.L * sizeof(R);
+            in.imf_stride = in.L;
+            in.imf_serialized = 1;
+            in.res = nullptr;
+        } else {
+            in.imf = q.d_imfs;
+            in.imf_stride = q.rows * q.cols;
+            in.imf_serialized = 0;
+            in.res = q.d_residue;
+        }
+        ws.h_inst[i] = in;
+    }
+    int64_t ntiles;
+    semd_status st = ws.layout(ninst, ntiles, s, err);
+    if (st != SEMD_OK)
+        return st;
+    SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)ninst * sizeof(State), s));
+    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_tile_inst, ws.r0, kTile,
+                                                      eemd ? 1 : 0);
+    if (eemd) {
+        k_std<<<1, 1024, 0, s>>>(ws.r0 + ws.h_inst[0].off, ws.h_inst[0].L, p.noise_rel_std,
+                                 ws.d_beta);
+        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, (const R *)d_noise, ws.d_beta,
+                                           ws.r0);
+    }
+    st = run_passes<R>(ws, p, ninst, ntiles, s, err);
+    if (st != SEMD_OK)
+        return st;
+    if (eemd) {
+        const Inst &in0 = ws.h_inst[0];
+        k_eemd_average<R><<<in0.ntiles, 256, 0, s>>>(
+            ws.d_inst, ws.d_state, ninst, p.max_imfs, (const R *)ws.eemd_scratch, ws.r0, ws.r1,
+            (R *)insts[0].d_imfs, insts[0].d_residue, kTile);
+    } else {
+        k_finalize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
+                                                         ws.r0, ws.r1, kTile, p.max_imfs);
+    }
+    SEMD_CU(cudaGetLastError());
+    SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, (size_t)ninst * sizeof(State),
+                            cudaMemcpyDeviceToHost, s));
+    pl.last_ninst = ninst;
+    pl.last_count = eemd ? 1 : count;
+    if (n_imfs) {
+        SEMD_CU(cudaStreamSynchronize(s));
+        pl.counts(pl.last_count, n_imfs, nullptr);
+    }
+    return SEMD_OK;
+}
+
+template <typename R>
+semd_status extrema_impl(semd_plan_s &pl, const void *d_h, int64_t L, int32_t *tmax,
+                         int32_t *tmin, int64_t *nmax, int64_t *nmin, cudaStream_t s)
+{
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    const int ntiles = (int)((L + kTile - 1) / kTile);
+    if (L < 1 || ntiles > ws.cap_tiles) {
+        err = "L out of range for this plan";
+        return SEMD_EINVAL;
+    }
+    int32_t *d_cnt = ws.d_misc;
+    k_extrema_tiles<R><<<ntiles, 32, 0, s>>>((const R *)d_h, L, kTile, nullptr, d_cnt, nullptr,
+                                             nullptr);
+    SEMD_CU(cudaMemcpyAsync(ws.h_misc, d_cnt, (size_t)ntiles * 8, cudaMemcpyDeviceToHost, s));
+    SEMD_CU(cudaStreamSynchronize(s));
+    int32_t *c = (int32_t *)ws.h_misc;
+    int64_t a = 0, b = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        const int32_t ca = c[2 * t], cb = c[2 * t + 1];
+        c[2 * t] = (int32_t)a;
+        c[2 * t + 1] = (int32_t)b;
+        a += ca;
+        b += cb;
+    }
+    SEMD_CU(cudaMemcpyAsync(d_cnt, ws.h_misc, (size_t)ntiles * 8, cudaMemcpyHostToDevice, s));
+    k_extrema_tiles<R><<<ntiles, 32, 0, s>>>((const R *)d_h, L, kTile, d_cnt, nullptr, tmax, tmin);
+    SEMD_CU(cudaGetLastError());
+    SEMD_CU(cudaStreamSynchronize(s));
+    *nmax = a;
+    *nmin = b;
+    return SEMD_OK;
+}
+
+template <typename R>
+semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, double *sd_num,
+                      double *sd_den, cudaStream_t s)
+{
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    if (L < 1 || L > ws.cap_samples) {
+        err = "L out of range for this plan";
+        return SEMD_EINVAL;
+    }
+    SEMD_CU(cudaEventSynchronize(ws.staging_done));
+    Inst in{};
+    in.L = L;
+    in.M = L;
+    in.N = 1;
+    in.D = 0;
+    ws.h_inst[0] = in;
+    int64_t ntiles;
+    semd_status st = ws.layout(1, ntiles, s, err);
+    if (st != SEMD_OK)
+        return st;
+    SEMD_CU(cudaMemsetAsync(ws.d_state, 0, sizeof(State), s));
+    k_to_double<R><<<152, 256, 0, s>>>((const R *)d_h, L, ws.r0);
+    semd_params p = pl.p;
+    p.stop = SEMD_STOP_FIXED;
+    p.fixed_sifts = 1000; // stay in SIFT mode
+    p.max_imfs = 1;
+    ReduceArgs ra = reduce_args(ws, p);
+    SEMD_CU(cudaMemsetAsync(ws.d_active, 0, 8, s));
+    launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
+    k_reduce<<<1, 64, 0, s>>>(ra);
+    launch_pass<R>(ws, ntiles, s); // SIFT
+    SEMD_CU(cudaGetLastError());
+    SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
+    SEMD_CU(cudaStreamSynchronize(s));
+    if (ws.h_state[0].mode != MODE_SIFT) {
+        err = "the signal lacks maxima or minima; it cannot be sifted";
+        return SEMD_EINVAL;
+    }
+    // the SIFT pass read h from buffer hpar = 1 and wrote buffer 0
+    SEMD_CU(cudaMemcpyAsync(d_out, ws.h0, (size_t)L * sizeof(R), cudaMemcpyDeviceToDevice, s));
+    std::vector<TileAux> aux(ntiles);
+    SEMD_CU(cudaMemcpyAsync(aux.data(), ws.d_taux, (size_t)ntiles * sizeof(TileAux),
+                            cudaMemcpyDeviceToHost, s));
+    SEMD_CU(cudaStreamSynchronize(s));
+    double a = 0.0, b = 0.0;
+    for (auto &x : aux) {
+        a += x.sd_num;
+        b += x.sd_den;
+    }
+    *sd_num = a;
+    *sd_den = b;
+    return SEMD_OK;
+}
+
+template semd_status decompose_impl<float>(semd_plan_s &, int, const semd_instance *,
+                                           const void *, int *, cudaStream_t);
+template semd_status decompose_impl<double>(semd_plan_s &, int, const semd_instance *,
+                                            const void *, int *, cudaStream_t);
+
+} // namespace semd
+
+void semd_plan_s::counts(int count, int *n_imfs, int *sifts) const
+{
+    using namespace semd;
+    const bool eemd = p.ensemble_trials > 1;
+    for (int i = 0; i < count; ++i) {
+        int n = 0;
+        if (eemd) {
+            for (int m = 0; m < last_ninst; ++m)
+                n = std::max(n, (int)ws.h_state[m].imf_count);
+        } else {
+            n = ws.h_state[i].imf_count;
+        }
+        if (n_imfs)
+            n_imfs[i] = n;
+        if (sifts)
+            for (int k = 0; k < p.max_imfs; ++k)
+                sifts[(int64_t)i * p.max_imfs + k] =
+                    eemd ? 0 : (k < n ? ws.h_state[i].sifts[k] : 0);
+    }
+}
+
+// ======================================================================= C ABI
+using namespace semd;
+
+extern "C" {
+
+void serial_emd_default_params(semd_params *p)
+{
+    std::memset(p, 0, sizeof(*p));
+    p->rows = 1;
+    p->cols = 1;
+    p->order = SEMD_ORDER_ROWS;
+    p->transition_len = -1;
+    p->max_imfs = 10;
+    p->stop = SEMD_STOP_FIXED;
+    p->fixed_sifts = 10;
+    p->max_sifts = 50;
+    p->sd_threshold = 0.2;
+    p->boundary = SEMD_BOUNDARY_MIRROR;
+    p->mirror_knots = 2;
+    p->precision = SEMD_FP32_MIXED;
+    p->ensemble_trials = 1;
+    p->noise_rel_std = 0.2;
+}
+
+semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem_budget,
+                            semd_plan_t *out)
+{
+    std::string &err = g_plan_create_error;
+    err.clear();
+    if (!params || !out || max_batch < 1) {
+        err = "null argument or max_batch < 1";
+        return SEMD_EINVAL;
+    }
+    *out = nullptr;
+    if (!validate(*params, err))
+        return SEMD_EINVAL;
+    int64_t M, N, D;
+    if (!geometry(*params, params->rows, params->cols, params->order, M, N, D, err))
+        return SEMD_EINVAL;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        err = "no CUDA device is available";
+        return SEMD_ECUDA;
+    }
+    const bool eemd = params->ensemble_trials > 1;
+    if (eemd && max_batch != 1) {
+        err = "EEMD plans take one input (max_batch = 1)";
+        return SEMD_EINVAL;
+    }
+    const int64_t L = serial_length(M, N, D);
+    const int ninst = eemd ? params->ensemble_trials : max_batch;
+    const int64_t tiles_per = (L + kTile - 1) / kTile;
+    const int64_t samples = (int64_t)ninst * ((L + 31) & ~(int64_t)31);
+    const int64_t tiles = (int64_t)ninst * tiles_per;
+    const int64_t rent = (int64_t)ninst * 2 * skew_len(reduce_entries((int)tiles_per));
+    const size_t elem = params->precision == SEMD_FP64 ? 8 : 4;
+    const int64_t eemd_elems = eemd ? (int64_t)ninst * params->max_imfs * L : 0;
+    semd_plan_s *pl = new (std::nothrow) semd_plan_s();
+    if (!pl) {
+        err = "out of host memory";
+        return SEMD_ENOMEM;
+    }
+    pl->p = *params;
+    pl->L = L;
+    semd_status st = pl->ws.allocate(samples, ninst, tiles, rent, max_iterations(*params), elem,
+                                      eemd_elems, mem_budget, err);
+    if (st != SEMD_OK) {
+        pl->ws.release();
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return SEMD_OK;
+}
+
+size_t serial_emd_plan_bytes(semd_plan_t plan) { return plan ? plan->ws.bytes : 0; }
+
+semd_status serial_emd_decompose(semd_plan_t plan, const void *d_x, const void *d_noise,
+                                 void *d_imfs, double *d_residue, int *n_imfs, void *stream)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (!d_x || !d_imfs || (plan->p.ensemble_trials > 1 && !d_noise)) {
+        plan->err = "null input, output or (EEMD) noise pointer";
+        return SEMD_EINVAL;
+    }
+    semd_instance in{d_x, plan->p.rows, plan->p.cols, d_imfs, d_residue};
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->p.precision == SEMD_FP64
+               ? decompose_impl<double>(*plan, 1, &in, d_noise, n_imfs, s)
+               : decompose_impl<float>(*plan, 1, &in, d_noise, n_imfs, s);
+}
+
+semd_status serial_emd_decompose_batch(semd_plan_t plan, int count, const semd_instance *inst,
+                                       int *n_imfs, void *stream)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (plan->p.ensemble_trials > 1) {
+        plan->err = "batched decomposition takes EMD plans only";
+        return SEMD_EINVAL;
+    }
+    if (count < 1 || count > plan->ws.cap_inst || !inst) {
+        plan->err = "count must be in [1, max_batch]";
+        return SEMD_EINVAL;
+    }
+    const int64_t Lp = plan->L;
+    for (int i = 0; i < count; ++i) {
+        int64_t M, N, D;
+        if (!inst[i].d_x || !inst[i].d_imfs) {
+            plan->err = "null input or output pointer in the batch";
+            return SEMD_EINVAL;
+        }
+        if (!geometry(plan->p, inst[i].rows, inst[i].cols, plan->p.order, M, N, D, plan->err))
+            return SEMD_EINVAL;
+        if (serial_length(M, N, D) > Lp) {
+            plan->err = "an input is larger than the plan's shape";
+            return SEMD_EBUDGET;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->p.precision == SEMD_FP64
+               ? decompose_impl<double>(*plan, count, inst, nullptr, n_imfs, s)
+               : decompose_impl<float>(*plan, count, inst, nullptr, n_imfs, s);
+}
+
+semd_status serial_emd_plan_counts(semd_plan_t plan, int count, int *n_imfs, int *sifts)
+{
+    if (!plan || count < 0 || count > plan->last_count)
+        return SEMD_EINVAL;
+    plan->counts(count, n_imfs, sifts);
+    return SEMD_OK;
+}
+
+semd_status serial_emd_extrema(semd_plan_t plan, const void *d_h, int64_t L, int32_t *d_tmax,
+                               int32_t *d_tmin, int64_t *n_max, int64_t *n_min, void *stream)
+{
+    if (!plan || !d_h || !d_tmax || !d_tmin || !n_max || !n_min)
+        return SEMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->p.precision == SEMD_FP64
+               ? extrema_impl<double>(*plan, d_h, L, d_tmax, d_tmin, n_max, n_min, s)
+               : extrema_impl<float>(*plan, d_h, L, d_tmax, d_tmin, n_max, n_min, s);
+}
+
+semd_status serial_emd_sift(semd_plan_t plan, const void *d_h, int64_t L, void *d_out,
+                            double *sd_num, double *sd_den, void *stream)
+{
+    if (!plan || !d_h || !d_out || !sd_num || !sd_den)
+        return SEMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->p.precision == SEMD_FP64
+               ? sift_impl<double>(*plan, d_h, L, d_out, sd_num, sd_den, s)
+               : sift_impl<float>(*plan, d_h, L, d_out, sd_num, sd_den, s);
+}
+
+void serial_emd_destroy(semd_plan_t plan)
+{
+    if (!plan)
+        return;
+    plan->ws.release();
+    delete plan;
+}
+
+const char *serial_emd_last_error(semd_plan_t plan)
+{
+    return plan ? plan->err.c_str() : g_plan_create_error.c_str();
+}
+
+} // extern "C"

@@ -1,0 +1,104 @@
+// Data layout shared by the host runtime and the kernels of the GB300 Serial-EMD
+// library (instances, per-instance state, per-tile records of the spline solve).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace semd {
+
+constexpr int KMAX = 32;
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+enum Mode : int32_t {
+    MODE_INIT = 0,        // h <- (working precision) r; export h
+    MODE_SIFT = 1,        // h <- sift(h); export
+    MODE_SIFT_COMMIT = 2, // c <- sift(h); commit c; h <- r_new; export
+    MODE_COMMIT = 3,      // c <- h; commit c; h <- r_new; export
+    MODE_DONE = 4
+};
+
+enum Boundary : int32_t { BND_MIRROR = 0, BND_ENDPOINTS = 1 };
+enum Stop : int32_t { STOP_FIXED = 0, STOP_SD = 1 };
+
+// Read-only description of one instance (one serialized signal).
+struct Inst {
+    int64_t L;            // serialized length, Sec. 3.2: MN + DN - D
+    int64_t off;          // offset of the instance in the flat work arrays
+    int32_t tile0;        // first global tile
+    int32_t ntiles;
+    int64_t M, N, D;      // signal length, number of signals, transition length
+    int32_t order;        // 0: signal i is row i of the input, 1: column i
+    int32_t imf_serialized; // 1: IMFs are written in serialized order (EEMD trials)
+    const void *x;        // input (rows x cols, row-major), or null
+    void *imf;            // IMF output base
+    double *res;          // residue output (input shape), or null
+    int64_t imf_stride;   // elements between IMF slots
+};
+
+// Mutable per-instance state of the sifting state machine.
+struct State {
+    int32_t mode, hpar, rpar, imf_count, sift_count, nmax, nmin, pad;
+    double sd;
+    int32_t sifts[KMAX];
+};
+
+// Per tile and envelope (0 = maxima, 1 = minima): what k_reduce needs of the tile.
+struct TileExport {
+    int32_t n;     // knots of this kind in the tile
+    int32_t t[4];  // instance positions of knots 0, 1, n-2, n-1
+    int32_t pad;
+    double y[4];   // their values
+    double xa[3];  // M at knot 1   = xa[0] + xa[1] * M_0 + xa[2] * M_{n-1}  (n >= 3)
+    double xb[3];  // M at knot n-2 = xb[0] + xb[1] * M_0 + xb[2] * M_{n-1}  (n >= 3)
+};
+
+// Per tile and envelope: the tile-boundary values solved by k_reduce.
+struct TileSolve {
+    double MF, ML;          // M at the tile's first and last knot
+    int32_t tp, tn;         // outside bracket knots: last knot before the tile,
+    double yp, Mp, yn, Mn;  // first knot after it (instance positions)
+};
+
+struct TileAux {
+    double sd_num, sd_den;  // sum (h - h')^2, sum h^2 over the tile
+    double h_first, h_last; // h[0] / h[L-1] of the new signal (first / last tile)
+};
+
+struct PassArgs {
+    const Inst *inst;
+    const State *state;
+    const int32_t *tile_inst;
+    void *h0, *h1;
+    double *r0, *r1;
+    TileExport *tex;
+    const TileSolve *tsol;
+    TileAux *taux;
+};
+
+enum RKind : int32_t { RK_FIXED = 0, RK_FREE = 1, RK_F = 2, RK_L = 3, RK_FL = 4 };
+struct REntry {
+    int32_t t, tile, kind, pad;
+    double y;
+};
+
+struct ReduceArgs {
+    const Inst *inst;
+    State *state;
+    const TileExport *tex;
+    TileSolve *tsol;
+    const TileAux *taux;
+    const int64_t *rbase; // per instance: first scratch entry (2 envelopes follow)
+    REntry *rent;
+    double *rA, *rB, *rC, *rD, *rcp, *rdp, *rbp, *rM;
+    int32_t *active;      // incremented once per instance still running
+    int32_t K, stop, fixed_sifts, max_sifts;
+    double sd_threshold;
+    int32_t boundary, mirror_knots;
+};
+
+// Entries of the reduced system of an instance with nt tiles (per envelope).
+__host__ __device__ inline int64_t reduce_entries(int nt) { return 2 * (int64_t)nt + 4; }
+// Scratch length for n entries addressed through sk().
+__host__ __device__ inline int64_t skew_len(int64_t n) { return n + n / 32 + 2; }
+
+} // namespace semd

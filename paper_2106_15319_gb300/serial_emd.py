@@ -1,0 +1,105 @@
+"""Python front end of the GB300 Serial-EMD library.
+
+`Plan` owns a C-ABI plan (device workspaces reserved once); `decompose` is the
+one-call convenience form. Tensors are torch CUDA tensors; every computation runs
+in libserial_emd.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import capi
+
+_DTYPE = {capi.FP64: torch.float64, capi.FP32_MIXED: torch.float32}
+
+
+def make_params(rows: int, cols: int, *, order: int = capi.ORDER_ROWS, transition_len: int = -1,
+                max_imfs: int = 10, stop: int = capi.STOP_FIXED, fixed_sifts: int = 10,
+                sd_threshold: float = 0.2, max_sifts: int = 50,
+                boundary: int = capi.BOUNDARY_MIRROR, mirror_knots: int = 2,
+                precision: int = capi.FP32_MIXED, ensemble_trials: int = 1,
+                noise_rel_std: float = 0.2) -> capi.semd_params:
+    return capi.serial_emd_default_params(
+        rows=rows, cols=cols, order=order, transition_len=transition_len, max_imfs=max_imfs,
+        stop=stop, fixed_sifts=fixed_sifts, sd_threshold=sd_threshold, max_sifts=max_sifts,
+        boundary=boundary, mirror_knots=mirror_knots, precision=precision,
+        ensemble_trials=ensemble_trials, noise_rel_std=noise_rel_std)
+
+
+def serialized_length(rows: int, cols: int, order: int = capi.ORDER_ROWS,
+                      transition_len: int = -1) -> int:
+    M, N = (cols, rows) if order == capi.ORDER_ROWS else (rows, cols)
+    D = round(0.2 * M) if transition_len < 0 else transition_len
+    if N == 1:
+        D = 0
+    return M * N + D * N - D
+
+
+class Plan:
+    def __init__(self, params: capi.semd_params, max_batch: int = 1, mem_budget: int = 0):
+        self.params = params
+        self.handle = capi.serial_emd_plan(params, max_batch, mem_budget)
+        self.dtype = _DTYPE[params.precision]
+        self.max_batch = max_batch
+
+    @property
+    def nbytes(self) -> int:
+        return capi.serial_emd_plan_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            capi.serial_emd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, rows: int, cols: int, device="cuda"):
+        imfs = torch.empty((self.params.max_imfs, rows, cols), dtype=self.dtype, device=device)
+        res = torch.empty((rows, cols), dtype=torch.float64, device=device)
+        return imfs, res
+
+    def decompose(self, x: torch.Tensor, noise: torch.Tensor | None = None, imfs=None,
+                  residue=None, stream=None, wait: bool = True):
+        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous()
+        if imfs is None:
+            imfs, residue = self.outputs(*x.shape, device=x.device)
+        n = capi.serial_emd_decompose(self.handle, x, noise, imfs, residue, stream, wait)
+        return imfs, residue, n
+
+    def decompose_batch(self, xs, outs=None, stream=None, wait: bool = True):
+        if outs is None:
+            outs = [self.outputs(*x.shape, device=x.device) for x in xs]
+        items = [(x, o[0], o[1]) for x, o in zip(xs, outs)]
+        n = capi.serial_emd_decompose_batch(self.handle, items, stream, wait)
+        return outs, n
+
+    def counts(self, count: int = 1):
+        return capi.serial_emd_plan_counts(self.handle, count, self.params.max_imfs)
+
+    def extrema(self, h: torch.Tensor, stream=None):
+        L = h.numel()
+        tmax = torch.empty(L // 2 + 1, dtype=torch.int32, device=h.device)
+        tmin = torch.empty(L // 2 + 1, dtype=torch.int32, device=h.device)
+        a, b = capi.serial_emd_extrema(self.handle, h, tmax, tmin, stream)
+        return tmax[:a], tmin[:b]
+
+    def sift(self, h: torch.Tensor, stream=None):
+        out = torch.empty_like(h)
+        num, den = capi.serial_emd_sift(self.handle, h, out, stream)
+        return out, num, den
+
+
+def decompose(x: torch.Tensor, noise: torch.Tensor | None = None, **kw):
+    """One-shot Serial-EMD of a 2D CUDA tensor (rows, cols). Returns (imfs, residue, n)."""
+    prec = capi.FP64 if x.dtype == torch.float64 else capi.FP32_MIXED
+    kw.setdefault("precision", prec)
+    p = make_params(x.shape[0], x.shape[1], **kw)
+    plan = Plan(p)
+    try:
+        return plan.decompose(x.contiguous(), noise)
+    finally:
+        plan.close()

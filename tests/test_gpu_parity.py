@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 per-IMF relative L2 <= 1e-10; FP32-mixed per-IMF relative L2
+<= 1e-4 (the denominator has a floor of 1e-6 * ||x||); knot indices bit-exact.
+Inputs for the FP32 form are rounded to float32 first, and the oracle decomposes
+the rounded values, so both sides start from the same numbers.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2106_15319_gb300 import capi, synth  # noqa: E402
+from paper_2106_15319_gb300.serial_emd import Plan, make_params  # noqa: E402
+
+TOL = {capi.FP64: 1e-10, capi.FP32_MIXED: 1e-4}
+NP = {capi.FP64: np.float64, capi.FP32_MIXED: np.float32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    capi.load()
+
+
+def _rel(a, b, floor):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), floor)
+
+
+def _check_imfs(imfs_g, res_g, n_g, imfs_o, res_o, n_o, x, prec, what=""):
+    assert n_g == n_o, f"{what}: IMF count {n_g} vs {n_o}"
+    floor = 1e-6 * np.linalg.norm(x)
+    errs = [_rel(imfs_g[k], imfs_o[k], floor) for k in range(imfs_o.shape[0])]
+    assert max(errs) <= TOL[prec], f"{what}: per-IMF rel L2 {errs}"
+    assert _rel(res_g, res_o, floor) <= TOL[prec], what
+    return errs
+
+
+def _run(X, prec, order=capi.ORDER_ROWS, **kw):
+    Xr = np.asarray(X, NP[prec])
+    rows, cols = Xr.shape
+    p = make_params(rows, cols, precision=prec, order=order, **kw)
+    plan = Plan(p)
+    x = torch.from_numpy(Xr).cuda()
+    imfs, res, n = plan.decompose(x)
+    torch.cuda.synchronize()
+    out = imfs.double().cpu().numpy(), res.cpu().numpy(), n, plan.counts(1)[1][0]
+    plan.close()
+    return out
+
+
+def _oracle(X, prec, order=capi.ORDER_ROWS, transition_len=-1, max_imfs=10,
+            stop=capi.STOP_FIXED, fixed_sifts=10, sd_threshold=0.2, max_sifts=50,
+            boundary=capi.BOUNDARY_MIRROR, mirror_knots=2):
+    Xd = np.asarray(np.asarray(X, NP[prec]), np.float64)
+    Xs = Xd if order == capi.ORDER_ROWS else Xd.T
+    N, M = Xs.shape
+    D = round(0.2 * M) if transition_len < 0 else transition_len
+    if N == 1:
+        D = 0
+    imfs, res, n, sifts = O.serial_emd(Xs, D, max_imfs, stop=stop, fixed_sifts=fixed_sifts,
+                                       sd_threshold=sd_threshold, max_sifts=max_sifts,
+                                       boundary=boundary, mirror_knots=mirror_knots)
+    if order == capi.ORDER_COLS:
+        imfs = imfs.transpose(0, 2, 1)
+        res = res.T
+    return imfs, res, n, sifts, Xd
+
+
+# ---------------------------------------------------------------- step-level parity
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+@pytest.mark.parametrize("L", [3, 5, 64, 1023, 1024, 1025, 5000])
+def test_extrema_bit_exact(prec, L):
+    h = synth.rng(L).standard_normal(L).astype(NP[prec])
+    h[L // 3: L // 3 + 3] = h[L // 3]  # a flat run
+    plan = Plan(make_params(1, max(L, 8), precision=prec))
+    tmax, tmin = plan.extrema(torch.from_numpy(h).cuda())
+    omax, omin = O.extrema(h.astype(np.float64))
+    assert np.array_equal(tmax.cpu().numpy(), omax)
+    assert np.array_equal(tmin.cpu().numpy(), omin)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+@pytest.mark.parametrize("L", [40, 1000, 1024, 3001, 20000])
+def test_one_sift(prec, L):
+    g = synth.rng(100 + L)
+    t = np.arange(L)
+    h = (np.sin(t / 7.0) + 0.3 * g.standard_normal(L) + 0.5 * np.sin(t / 151.0)).astype(NP[prec])
+    plan = Plan(make_params(1, L, precision=prec))
+    out, num, den = plan.sift(torch.from_numpy(h).cuda())
+    ref, rnum, rden = O.sift(h.astype(np.float64))
+    got = out.double().cpu().numpy()
+    tol = 1e-12 if prec == capi.FP64 else 2e-5
+    assert _rel(got, ref, 1e-30) <= tol
+    assert abs(num - rnum) <= tol * 10 * rnum and abs(den - rden) <= tol * 10 * rden
+    plan.close()
+
+
+# ------------------------------------------------------------ end-to-end parity
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+@pytest.mark.parametrize("D", [0, 205])
+def test_series_3x1024(prec, D):
+    X = synth.workload_series_3x1024()
+    g = _run(X, prec, transition_len=D, max_imfs=8)
+    o = _oracle(X, prec, transition_len=D, max_imfs=8)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, f"series D={D}")
+    assert list(g[3]) == list(o[3])
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_texture_256(prec):
+    X = synth.workload_texture_256()
+    g = _run(X, prec, transition_len=0, max_imfs=10)
+    o = _oracle(X, prec, transition_len=0, max_imfs=10)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, "texture 256")
+
+
+def test_texture_256_with_transitions_fp64():
+    X = synth.workload_texture_256()
+    g = _run(X, capi.FP64, transition_len=-1, max_imfs=10)
+    o = _oracle(X, capi.FP64, transition_len=-1, max_imfs=10)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, "texture 256 D=51")
+
+
+@pytest.mark.parametrize("shape", [(1, 5), (1, 17), (1, 1023), (1, 1025), (3, 700), (2, 2049),
+                                   (7, 333)])
+def test_ragged_sizes_fp64(shape):
+    g0 = synth.rng(shape[0] * 10007 + shape[1])
+    t = np.arange(shape[1])
+    X = np.sin(t[None, :] / (3.0 + np.arange(shape[0])[:, None])) + 0.2 * g0.standard_normal(shape)
+    g = _run(X, capi.FP64, max_imfs=6)
+    o = _oracle(X, capi.FP64, max_imfs=6)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, f"ragged {shape}")
+
+
+@pytest.mark.parametrize("kw", [dict(boundary=capi.BOUNDARY_ENDPOINTS),
+                                dict(mirror_knots=1),
+                                dict(order=capi.ORDER_COLS),
+                                dict(fixed_sifts=1),
+                                dict(stop=capi.STOP_SD, sd_threshold=0.2, max_sifts=50)])
+def test_options_fp64(kw):
+    X = synth.tone_chirp_series(4, 900, 77)
+    if kw.get("order") == capi.ORDER_COLS:
+        X = np.ascontiguousarray(X.T)
+    g = _run(X, capi.FP64, max_imfs=7, **kw)
+    o = _oracle(X, capi.FP64, max_imfs=7, **kw)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, str(kw))
+    assert list(g[3]) == list(o[3]), (g[3], o[3])
+
+
+def test_reconstruction_on_gpu():
+    X = synth.workload_texture_256()
+    imfs, res, n, _ = _run(X, capi.FP64, transition_len=0)
+    assert np.abs(imfs.sum(0) + res - X).max() <= 1e-12
+
+
+# ------------------------------------------------------------------------- batching
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_batch_uneven_images_match_oracle_and_alone(prec):
+    imgs = synth.uneven_images(12, 4242, side_range=(32, 96))
+    imgs = [np.asarray(im, NP[prec]) for im in imgs]
+    side = max(im.shape[0] for im in imgs)
+    p = make_params(side, side, precision=prec, transition_len=0, max_imfs=8)
+    plan = Plan(p, max_batch=len(imgs))
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    outs, ns = plan.decompose_batch(xs)
+    torch.cuda.synchronize()
+    for i, im in enumerate(imgs):
+        o = _oracle(im, prec, transition_len=0, max_imfs=8)
+        _check_imfs(outs[i][0].double().cpu().numpy(), outs[i][1].cpu().numpy(), ns[i],
+                    o[0], o[1], o[2], o[4], prec, f"batch item {i}")
+    # alone == in the batch, bit for bit
+    for i in (0, 5, 11):
+        alone, n1 = plan.decompose_batch([xs[i]])
+        torch.cuda.synchronize()
+        assert n1[0] == ns[i]
+        assert torch.equal(alone[0][0], outs[i][0]) and torch.equal(alone[0][1], outs[i][1])
+    plan.close()
+
+
+# ----------------------------------------------------------------------------- EEMD
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_eemd_small(prec):
+    img = synth.grating_image(48, 5).astype(NP[prec])
+    trials = 6
+    L = img.size
+    w = synth.white_noise(trials, L, 6).astype(NP[prec])
+    p = make_params(48, 48, precision=prec, transition_len=0, max_imfs=8, ensemble_trials=trials,
+                    noise_rel_std=0.2)
+    plan = Plan(p)
+    imfs, res, n = plan.decompose(torch.from_numpy(img).cuda(), torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    x = img.astype(np.float64).reshape(-1)
+    beta = 0.2 * O.std(x)
+    oi, orr, on = O.eemd(x, w.astype(np.float64), beta, 8)
+    assert n == on
+    floor = 1e-6 * np.linalg.norm(x)
+    gi = imfs.double().cpu().numpy().reshape(8, -1)
+    errs = [_rel(gi[k], oi[k], floor) for k in range(8)]
+    assert max(errs) <= TOL[prec], errs
+    assert _rel(res.cpu().numpy().reshape(-1), orr, floor) <= TOL[prec]
+    plan.close()
