@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Serial-EMD hot path.
+
+One step = one full Serial-EMD decomposition (serialize, all sifting passes of all
+IMFs, de-serialize) of the workload's synthetic input, resident in HBM. The metric
+is serialized samples sifted per second (sum over instances of L x sifts, divided
+by the device time of the step). Default workload: the 256 x 256 texture image
+(gratings of period 4, 16 and 64 px plus noise), row-serialized without
+transitions (L = 65536), 10 sifts per IMF, at most 10 IMFs, mirror boundary; the
+FP32-mixed form gives `value`, the plain FP64 form is timed beside it, and the
+batched FP32 form is also measured on the EEMD workload (512 x 512 image, 256
+noise realizations in one batched run). The CPU oracle is timed on a bounded
+sample of the same workload on the host cores (`cpu_baseline`), and
+`--impl reference` times only the oracle.
+
+N > 1 (torchrun): every rank runs its own replica of the workload (the method has
+no cross-instance exchange), timing is max over ranks, `value` sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "serialized samples sifted/s: batched FP32 vs plain FP64 on GB300; p99 request latency"
+UNIT = "samples*sifts/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def workload_inputs(name: str, trials: int = 256):
+    from paper_2106_15319_gb300 import synth
+    if name == "texture256":
+        return {"X": synth.workload_texture_256(), "K": 10, "S": 10, "D": 0, "trials": 1,
+                "desc": "256x256 texture (gratings 4/16/64 px + N(0,0.05^2)), row-serialized, "
+                        "D=0, L=65536, 10 sifts/IMF, <=10 IMFs, mirror boundary"}
+    if name == "eemd512":
+        img, w = synth.workload_eemd_512(trials)
+        return {"X": img, "W": w, "K": 10, "S": 10, "D": 0, "trials": trials,
+                "desc": f"EEMD of a 512x512 grating image (L=262144), {trials} noise realizations "
+                        "(beta = 0.2 std), one batched run, 10 sifts/IMF, <=10 IMFs"}
+    if name == "series3x1024":
+        return {"X": synth.workload_series_3x1024(), "K": 8, "S": 10, "D": 0, "trials": 1,
+                "desc": "3-channel series x 1024 samples (tones + chirp + noise), D=0, L=3072, "
+                        "10 sifts/IMF, <=8 IMFs"}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _flush_l2(buf):
+    buf.add_(1)
+
+
+def run_ours(wl, precision, steps, warmup, device, flush):
+    import torch
+    from paper_2106_15319_gb300 import capi
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    dt = np.float64 if precision == capi.FP64 else np.float32
+    X = np.ascontiguousarray(wl["X"], dt)
+    rows, cols = X.shape
+    p = make_params(rows, cols, precision=precision, transition_len=wl["D"], max_imfs=wl["K"],
+                    fixed_sifts=wl["S"], ensemble_trials=wl["trials"])
+    plan = Plan(p)
+    x = torch.from_numpy(X).to(device)
+    noise = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).to(device) if wl["trials"] > 1 \
+        else None
+    imfs, res = plan.outputs(rows, cols, device=device)
+    stream = torch.cuda.Stream(device)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
+        stream.synchronize()
+        times = []
+        for _ in range(steps):
+            if flush is not None:
+                _flush_l2(flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
+            b.record(stream)
+            times.append((a, b))
+        stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in times]
+    st = plan.stats()
+    out = {"ms": ms, "sample_sifts": st.sample_sifts, "launches": st.kernel_launches,
+           "graph": st.used_graph, "plan": plan, "x": x, "noise": noise, "imfs": imfs, "res": res,
+           "stream": stream}
+    return out
+
+
+def profile_pass(run, steps, flush):
+    """Replays the steps with events around every pass and reduce launch (no graph)."""
+    import torch
+    plan, stream = run["plan"], run["stream"]
+    plan.set_options(use_graphs=False, profile=True)
+    tot = {"pass_ms": 0.0, "pass_n": 0, "reduce_ms": 0.0, "reduce_n": 0, "bytes": 0}
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            if flush is not None:
+                _flush_l2(flush)
+            plan.decompose(run["x"], run["noise"], run["imfs"], run["res"], stream=stream,
+                           wait=False)
+            stream.synchronize()
+            st = plan.stats()
+            tot["pass_ms"] += st.pass_ms
+            tot["pass_n"] += st.pass_launches
+            tot["reduce_ms"] += st.reduce_ms
+            tot["reduce_n"] += st.reduce_launches
+            tot["bytes"] += st.pass_bytes
+    plan.set_options(use_graphs=True, profile=False)
+    return tot
+
+
+def e2e_ours(wl, precision, steps, warmup, device):
+    """Same metric through the public API with host buffers (H2D of the input, D2H of IMFs
+    and residue inside the timed region)."""
+    import torch
+    from paper_2106_15319_gb300 import capi
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    dt = np.float64 if precision == capi.FP64 else np.float32
+    X = np.ascontiguousarray(wl["X"], dt)
+    rows, cols = X.shape
+    p = make_params(rows, cols, precision=precision, transition_len=wl["D"], max_imfs=wl["K"],
+                    fixed_sifts=wl["S"], ensemble_trials=wl["trials"])
+    plan = Plan(p)
+    hx = torch.from_numpy(X).pin_memory()
+    hn = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).pin_memory() if wl["trials"] > 1 \
+        else None
+    x = torch.empty_like(hx, device=device)
+    noise = torch.empty_like(hn, device=device) if hn is not None else None
+    imfs, res = plan.outputs(rows, cols, device=device)
+    h_imfs = torch.empty(imfs.shape, dtype=imfs.dtype).pin_memory()
+    h_res = torch.empty(res.shape, dtype=res.dtype).pin_memory()
+    stream = torch.cuda.Stream(device)
+    bi = hx.numel() * hx.element_size() + (hn.numel() * hn.element_size() if hn is not None else 0)
+    bo = h_imfs.numel() * h_imfs.element_size() + h_res.numel() * h_res.element_size()
+
+    def step():
+        x.copy_(hx, non_blocking=True)
+        if noise is not None:
+            noise.copy_(hn, non_blocking=True)
+        plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
+        h_imfs.copy_(imfs, non_blocking=True)
+        h_res.copy_(res, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        stream.synchronize()
+    ms = a.elapsed_time(b) / steps
+    ss = plan.stats().sample_sifts
+    plan.close()
+    return ms, ss, bi, bo
+
+
+def fp32_imf_errors(wl, run):
+    """Per-IMF relative L2 of the FP32 result against the FP64 oracle (untimed)."""
+    from oracle import oracle as O
+    X = np.asarray(np.asarray(wl["X"], np.float32), np.float64)
+    oi, orr, on, _ = O.serial_emd(X, wl["D"], wl["K"], fixed_sifts=wl["S"])
+    g = run["imfs"].double().cpu().numpy()
+    floor = 1e-6 * np.linalg.norm(X)
+    return [float(np.linalg.norm(g[k] - oi[k]) / max(np.linalg.norm(oi[k]), floor))
+            for k in range(wl["K"])]
+
+
+def cpu_baseline(wl, budget_s: float = 12.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    X = np.asarray(wl["X"], np.float64)
+    if wl["trials"] > 1:
+        x = O.serialize(X, wl["D"])
+        beta = 0.2 * O.std(x)
+        t0 = time.perf_counter()
+        done, ss = 0, 0
+        while time.perf_counter() - t0 < budget_s and done < wl["trials"]:
+            _, _, n, sifts = O.emd(x + beta * wl["W"][done], wl["K"], fixed_sifts=wl["S"])
+            ss += int(np.sum(sifts)) * x.size
+            done += 1
+        el = time.perf_counter() - t0
+        return {"value": ss / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{done} of {wl['trials']} EEMD trials, FP64, single thread"}
+    t0 = time.perf_counter()
+    done, ss = 0, 0
+    while time.perf_counter() - t0 < budget_s or done == 0:
+        _, _, n, sifts = O.serial_emd(X, wl["D"], wl["K"], fixed_sifts=wl["S"])
+        ss += int(np.sum(sifts)) * O.serial_length(X.shape[1], X.shape[0], wl["D"])
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": ss / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} full decompositions of the workload, FP64, single thread"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def arm_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload_inputs(args.workload, args.trials)
+    from oracle import oracle as O
+    X = np.asarray(wl["X"], np.float64)
+    per_step_budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, budget_s=per_step_budget)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = v
+    L = O.serial_length(X.shape[1], X.shape[0], wl["D"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": L * wl["S"] * wl["K"] / v * 1e3 * max(1, wl["trials"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"], "L": L},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def arm_ours(args):
+    import torch
+    from paper_2106_15319_gb300 import capi
+    world, rank, local = dist_setup(args)
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    capi.load()
+    wl = workload_inputs(args.workload, args.trials)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    peak, peak_kind = _peaks()
+
+    barrier(world)
+    with ClockSampler(local) as clk:
+        r32 = run_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device, flush)
+    barrier(world)
+    ms32 = statistics.mean(r32["ms"])
+    ms32_max = max_over_ranks(ms32, world)
+    value = world * r32["sample_sifts"] / (ms32_max * 1e-3)
+
+    r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush)
+    ms64 = max_over_ranks(statistics.mean(r64["ms"]), world)
+    v64 = world * r64["sample_sifts"] / (ms64 * 1e-3)
+
+    prof = profile_pass(r32, args.steps, flush)
+    pass_avg_ms = prof["pass_ms"] / max(1, prof["pass_n"])
+    bytes_per_launch = prof["bytes"] / max(1, prof["pass_n"])
+    achieved = bytes_per_launch / (pass_avg_ms * 1e-3) / 1e9
+
+    e2e_ms, e2e_ss, bi, bo = e2e_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device)
+    e2e_ms = max_over_ranks(e2e_ms, world)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; stands in for the paper's texture images)",
+        "config": {"workload": wl["desc"], "form": "FP32-mixed (FP64 interface solve, "
+                   "stop reductions and residue)", "L": int(r32["x"].numel()),
+                   "sample_sifts_per_step": r32["sample_sifts"], "cuda_graph": bool(r32["graph"]),
+                   "l2": "flushed between timed steps (512 MB write); "
+                         "the 65536-sample working set is L2-resident within a step",
+                   "parallelism": f"replicas x{world}"},
+        "plain_fp64": {"value": v64, "ms_per_step": ms64, "dtype": "f64"},
+        "speedup_fp32_vs_fp64": value / v64,
+        "fp32_imf_rel_l2": None,
+        "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "traffic": None,
+                     "avg_launch_us": pass_avg_ms * 1e3, "bytes_per_launch": bytes_per_launch,
+                     "launches": prof["pass_n"], "reduce_avg_us":
+                         prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
+                     "note": "events around every pass launch over a replay of the timed steps "
+                             "(graphs off); working set L2-resident"},
+        "e2e": {"value": world * e2e_ss / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms},
+        "gpu_launches": int(r32["launches"]) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        line["fp32_imf_rel_l2"] = fp32_imf_errors(wl, r32)
+        if not args.no_batched:
+            line["batched"] = batched_eemd(args, device, flush, peak, peak_kind, world)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    elif not args.no_batched:
+        batched_eemd(args, device, flush, peak, peak_kind, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def batched_eemd(args, device, flush, peak, peak_kind, world):
+    """The batched FP32 form on the EEMD workload (256 realizations in one run)."""
+    from paper_2106_15319_gb300 import capi
+    wl = workload_inputs("eemd512", args.trials)
+    steps = max(1, min(args.steps, 5))
+    r = run_ours(wl, capi.FP32_MIXED, steps, min(args.warmup, 3), device, flush)
+    ms = max_over_ranks(statistics.mean(r["ms"]), world)
+    prof = profile_pass(r, 1, flush)
+    pass_avg_ms = prof["pass_ms"] / max(1, prof["pass_n"])
+    bpl = prof["bytes"] / max(1, prof["pass_n"])
+    ach = bpl / (pass_avg_ms * 1e-3) / 1e9
+    out = {"workload": wl["desc"], "value": world * r["sample_sifts"] / (ms * 1e-3),
+           "unit": UNIT, "ms_per_step": ms, "steps": steps, "dtype": "f32",
+           "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": ach,
+                        "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "peak_source": peak_kind, "avg_launch_us": pass_avg_ms * 1e3,
+                        "bytes_per_launch": bpl, "launches": prof["pass_n"],
+                        "reduce_avg_us": prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3}}
+    r["plan"].close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="texture256",
+                    choices=["texture256", "eemd512", "series3x1024"])
+    ap.add_argument("--trials", type=int, default=256, help="EEMD realizations (eemd512)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        arm_reference(args)
+    else:
+        arm_ours(args)
+
+
+if __name__ == "__main__":
+    main()

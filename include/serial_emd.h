@@ -171,6 +171,33 @@ semd_status serial_emd_extrema(semd_plan_t plan, const void *d_h, int64_t L, int
 semd_status serial_emd_sift(semd_plan_t plan, const void *d_h, int64_t L, void *d_out,
                             double *sd_num, double *sd_den, void *stream);
 
+/*
+ * Execution options of a plan. use_graphs (default 1): a decomposition with a fixed
+ * sift count is captured once into a CUDA graph (per batch layout) and replayed on
+ * the plan's own stream, joined to the caller's stream by events; the first call for
+ * a new layout must not itself be under stream capture. profile (default 0): the
+ * pass and reduce kernels are bracketed by CUDA events (graphs are then not used),
+ * and serial_emd_plan_stats() reports their summed device time.
+ */
+semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int profile);
+
+/* Statistics of the plan's last decompose call; valid once its stream has finished. */
+typedef struct semd_stats {
+    int64_t kernel_launches; /* kernels the call ran (inside the graph when used_graph) */
+    int64_t pass_launches;   /* profiled pass-kernel launches (0 unless profiling) */
+    double pass_ms;          /* their summed device time */
+    int64_t reduce_launches; /* profiled interface-solve launches */
+    double reduce_ms;
+    int64_t sample_sifts;    /* serialized samples x sifts performed */
+    int64_t pass_bytes;      /* algorithmic HBM bytes of the pass kernel: per sample, the
+                                signal in and out (2w), plus w + 16 for a commit (IMF out,
+                                FP64 residue in and out); 8 + w for the first pass */
+    int32_t used_graph;
+    int32_t _reserved;
+} semd_stats;
+
+semd_status serial_emd_plan_stats(semd_plan_t plan, semd_stats *out);
+
 /* Releases a plan and its workspaces (after its work on any stream has finished). */
 void serial_emd_destroy(semd_plan_t plan);
 

@@ -64,18 +64,19 @@ def lib():
             L.oracle_emd.restype = ctypes.c_int
             L.oracle_emd.argtypes = [_dp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     _dp, _dp, _ipint]
+                                     _dp, _dp, _ipint, ctypes.c_int]
             L.oracle_std.restype = ctypes.c_double
             L.oracle_std.argtypes = [_dp, _i64]
             L.oracle_eemd.restype = ctypes.c_int
             L.oracle_eemd.argtypes = [_dp, _i64, _dp, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                      ctypes.c_int]
             L.oracle_serial_emd.restype = ctypes.c_int
             L.oracle_serial_emd.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_double, _dp, _dp, _dp, _ipint]
+                                            ctypes.c_double, _dp, _dp, _dp, _ipint, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -155,8 +156,12 @@ def sift(h, boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2):
 
 
 def emd(x, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10, sd_threshold: float = 0.2,
-        max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2):
-    """Sec. 2.1: returns (imfs (K, L) zero-filled, residue (L,), n_imfs, sifts per IMF)."""
+        max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2,
+        store_f32: bool = False):
+    """Sec. 2.1: returns (imfs (K, L) zero-filled, residue (L,), n_imfs, sifts per IMF).
+
+    store_f32 rounds the sifted signal to single precision where the FP32 form stores it.
+    """
     x = _f64(x)
     L = x.size
     imfs = np.empty((K, L), np.float64)
@@ -164,7 +169,7 @@ def emd(x, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10, sd_threshold: 
     sifts = np.zeros(K, np.int32)
     n = lib().oracle_emd(_d(x), L, K, stop, fixed_sifts, sd_threshold, max_sifts, boundary,
                          mirror_knots, _d(imfs), _d(res),
-                         sifts.ctypes.data_as(_ipint))
+                         sifts.ctypes.data_as(_ipint), int(store_f32))
     return imfs, res, int(n), sifts
 
 
@@ -175,7 +180,7 @@ def std(x) -> float:
 
 def eemd(x, w, beta: float, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
          sd_threshold: float = 0.2, max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR,
-         mirror_knots: int = 2):
+         mirror_knots: int = 2, store_f32: bool = False):
     """Sec. 2.2: w is (trials, L). Returns (mean imfs (K, L), mean residue, max n_imfs)."""
     x, w = _f64(x), _f64(w)
     trials, L = w.shape
@@ -183,13 +188,14 @@ def eemd(x, w, beta: float, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 1
     imfs = np.empty((K, L), np.float64)
     res = np.empty(L, np.float64)
     n = lib().oracle_eemd(_d(x), L, _d(w), trials, beta, K, stop, fixed_sifts, sd_threshold,
-                          max_sifts, boundary, mirror_knots, _d(imfs), _d(res))
+                          max_sifts, boundary, mirror_knots, _d(imfs), _d(res), int(store_f32))
     return imfs, res, int(n)
 
 
 def serial_emd(X, D: int, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
                sd_threshold: float = 0.2, max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR,
-               mirror_knots: int = 2, trials: int = 1, noise_rel_std: float = 0.0, w=None):
+               mirror_knots: int = 2, trials: int = 1, noise_rel_std: float = 0.0, w=None,
+               store_f32: bool = False):
     """Sec. 3: serialize, EMD/EEMD, de-serialize. X is (N, M).
 
     Returns (imfs (K, N, M), residue (N, M), n_imfs, sifts per IMF (EMD only)).
@@ -208,5 +214,5 @@ def serial_emd(X, D: int, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
         wp = None
     n = lib().oracle_serial_emd(_d(X), M, N, D, K, stop, fixed_sifts, sd_threshold, max_sifts,
                                 boundary, mirror_knots, trials, noise_rel_std, wp, _d(imfs),
-                                _d(res), sifts.ctypes.data_as(_ipint))
+                                _d(res), sifts.ctypes.data_as(_ipint), int(store_f32))
     return imfs, res, int(n), sifts

@@ -35,6 +35,12 @@
  *   Reading 11 EEMD noise is added to the serialized signal; beta is
  *              noise_rel_std times the population std of x; trials with fewer
  *              IMFs contribute zeros to the average.
+ *
+ * store_f32 (off for the reference decomposition): rounds the sifted signal to
+ * single precision at IMF start and after every sift, the two points where the
+ * FP32 form of the method stores it. All arithmetic stays FP64. Running the
+ * oracle both ways measures how far single-precision storage alone moves each
+ * IMF, which bounds what any FP32-storage implementation can match.
  */
 #include <math.h>
 #include <stdint.h>
@@ -269,11 +275,18 @@ static int has_enough_extrema(const double *h, int64_t L, int32_t *scratch_a,
  * (slots past the produced count are zero-filled), residue is L. The stop rule
  * is a fixed sift count (stop = OR_STOP_FIXED, fixed_sifts) or the SD rule of
  * Reading 8. sifts_per_imf (length K, may be NULL) receives each IMF's sift
- * count. Returns the number of IMFs produced.
+ * count. store_f32: see the header. Returns the number of IMFs produced.
  */
+static void round_to_single(double *h, int64_t L)
+{
+    int64_t k;
+    for (k = 0; k < L; ++k)
+        h[k] = (double)(float)h[k];
+}
+
 int oracle_emd(const double *x, int64_t L, int K, int stop, int fixed_sifts,
                double sd_threshold, int max_sifts, int boundary, int mirror_knots,
-               double *imfs, double *residue, int *sifts_per_imf)
+               double *imfs, double *residue, int *sifts_per_imf, int store_f32)
 {
     double *r = (double *)malloc((size_t)(L > 0 ? L : 1) * sizeof(double));
     double *h = (double *)malloc((size_t)(L > 0 ? L : 1) * sizeof(double));
@@ -292,6 +305,8 @@ int oracle_emd(const double *x, int64_t L, int K, int stop, int fixed_sifts,
         if (!has_enough_extrema(r, L, sa, sb))
             break; /* Reading 9: r is the residue */
         memcpy(h, r, (size_t)L * sizeof(double));
+        if (store_f32)
+            round_to_single(h, L);
         for (;;) {
             double num, den, *tmp;
             if (stop == OR_STOP_FIXED && sifts >= fixed_sifts)
@@ -304,6 +319,8 @@ int oracle_emd(const double *x, int64_t L, int K, int stop, int fixed_sifts,
             tmp = h;
             h = hn;
             hn = tmp;
+            if (store_f32)
+                round_to_single(h, L);
             if (stop == OR_STOP_SD) {
                 if (num / den < sd_threshold || sifts >= max_sifts)
                     break; /* Reading 8 */
@@ -349,7 +366,7 @@ double oracle_std(const double *x, int64_t L)
  */
 int oracle_eemd(const double *x, int64_t L, const double *w, int trials, double beta,
                 int K, int stop, int fixed_sifts, double sd_threshold, int max_sifts,
-                int boundary, int mirror_knots, double *imfs, double *residue)
+                int boundary, int mirror_knots, double *imfs, double *residue, int store_f32)
 {
     double *xm = (double *)malloc((size_t)L * sizeof(double));
     double *cm = (double *)malloc((size_t)K * (size_t)L * sizeof(double));
@@ -363,7 +380,7 @@ int oracle_eemd(const double *x, int64_t L, const double *w, int trials, double 
         for (q = 0; q < L; ++q)
             xm[q] = x[q] + beta * w[(int64_t)m * L + q]; /* Step 1 */
         n = oracle_emd(xm, L, K, stop, fixed_sifts, sd_threshold, max_sifts, boundary,
-                       mirror_knots, cm, rm, NULL); /* Step 2 */
+                       mirror_knots, cm, rm, NULL, store_f32); /* Step 2 */
         if (n > nmax)
             nmax = n;
         for (q = 0; q < (int64_t)K * L; ++q)
@@ -392,7 +409,7 @@ int oracle_eemd(const double *x, int64_t L, const double *w, int trials, double 
 int oracle_serial_emd(const double *X, int64_t M, int64_t N, int64_t D, int K, int stop,
                       int fixed_sifts, double sd_threshold, int max_sifts, int boundary,
                       int mirror_knots, int trials, double noise_rel_std, const double *w,
-                      double *imfs_out, double *residue_out, int *sifts_per_imf)
+                      double *imfs_out, double *residue_out, int *sifts_per_imf, int store_f32)
 {
     int64_t L = oracle_serial_length(M, N, D);
     double *x = (double *)malloc((size_t)L * sizeof(double));
@@ -402,11 +419,11 @@ int oracle_serial_emd(const double *X, int64_t M, int64_t N, int64_t D, int K, i
     oracle_serialize(X, M, N, D, x);
     if (trials <= 1) {
         n = oracle_emd(x, L, K, stop, fixed_sifts, sd_threshold, max_sifts, boundary,
-                       mirror_knots, R, r, sifts_per_imf);
+                       mirror_knots, R, r, sifts_per_imf, store_f32);
     } else {
         double beta = noise_rel_std * oracle_std(x, L);
         n = oracle_eemd(x, L, w, trials, beta, K, stop, fixed_sifts, sd_threshold,
-                        max_sifts, boundary, mirror_knots, R, r);
+                        max_sifts, boundary, mirror_knots, R, r, store_f32);
     }
     oracle_deserialize(R, K, M, N, D, imfs_out);
     oracle_deserialize(r, 1, M, N, D, residue_out);

@@ -51,6 +51,14 @@ class semd_request(ctypes.Structure):
                 ("d_imfs", ctypes.c_void_p), ("d_residue", ctypes.c_void_p)]
 
 
+class semd_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("pass_launches", ctypes.c_int64),
+                ("pass_ms", ctypes.c_double), ("reduce_launches", ctypes.c_int64),
+                ("reduce_ms", ctypes.c_double), ("sample_sifts", ctypes.c_int64),
+                ("pass_bytes", ctypes.c_int64), ("used_graph", ctypes.c_int32),
+                ("_reserved", ctypes.c_int32)]
+
+
 class semd_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n_imfs", ctypes.c_int32),
                 ("sifts", ctypes.c_int64), ("queue_ms", ctypes.c_double),
@@ -79,6 +87,8 @@ SIGNATURES = {
     "serial_emd_sift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "serial_emd_plan_set_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "serial_emd_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_stats)]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
     "serial_emd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "serial_emd_server_create": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_size_t,
@@ -200,6 +210,16 @@ def serial_emd_sift(plan: int, h, out, stream=None):
                                 ctypes.byref(b), _stream(stream))
     _check(rc, plan)
     return a.value, b.value
+
+
+def serial_emd_plan_set_options(plan: int, use_graphs: bool = True, profile: bool = False):
+    _check(load().serial_emd_plan_set_options(plan, int(use_graphs), int(profile)), plan)
+
+
+def serial_emd_plan_stats(plan: int) -> semd_stats:
+    st = semd_stats()
+    _check(load().serial_emd_plan_stats(plan, ctypes.byref(st)), plan)
+    return st
 
 
 def serial_emd_destroy(plan: int) -> None:

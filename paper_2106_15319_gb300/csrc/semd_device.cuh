@@ -605,6 +605,17 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
     }
     for (int idx = tid; idx < cnt; idx += NT)
         hdst[idx] = S.hn[idx + 1];
+    if (tid == 0 && pa.stats) {
+        // algorithmic bytes per sample: h in (w) unless INIT, h out (w), and for a commit
+        // the IMF out (w) and the residue in and out (16); INIT reads the residue (8)
+        const unsigned long long w = sizeof(R);
+        unsigned long long per = (mode == MODE_INIT) ? 8 + w : 2 * w;
+        if (commit)
+            per += w + 16;
+        atomicAdd(&pa.stats->pass_bytes, per * (unsigned long long)cnt);
+        if (sift)
+            atomicAdd(&pa.stats->sample_sifts, (unsigned long long)cnt);
+    }
 }
 
 // ---------------------------------------------------------------------------------

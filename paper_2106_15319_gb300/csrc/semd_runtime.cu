@@ -52,8 +52,10 @@ __global__ void k_serialize(const Inst *inst, const int32_t *tile_inst, double *
 }
 
 // EEMD beta = rel * population std of the serialized x (Sec. 2.2 Step 1), one CTA.
-__global__ void k_std(const double *x, int64_t L, double rel, double *beta)
+__global__ void k_std(const Inst *inst, const double *r0, double rel, double *beta)
 {
+    const double *x = r0 + inst[0].off;
+    const int64_t L = inst[0].L;
     __shared__ double sh[1024];
     double s = 0.0;
     for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
@@ -83,10 +85,10 @@ __global__ void k_std(const double *x, int64_t L, double rel, double *beta)
 
 // x^(m) = x + beta w^(m) for every trial (Sec. 2.2 Step 1); trial 0 holds x on entry.
 template <typename R>
-__global__ void k_add_noise(const Inst *inst, int trials, const R *w, const double *beta,
-                            double *r0)
+__global__ void k_add_noise(const Inst *inst, int trials, const double *beta, double *r0)
 {
     const int64_t L = inst[0].L;
+    const R *w = (const R *)inst[0].noise;
     const double b = *beta;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -126,10 +128,11 @@ __global__ void k_finalize(const Inst *inst, const State *state, const int32_t *
 // in FP64 and in trial order, then de-serialize (Sec. 3.3).
 template <typename R>
 __global__ void k_eemd_average(const Inst *inst, const State *state, int trials, int K,
-                               const R *scratch, const double *r0, const double *r1, R *out,
-                               double *res, int tile)
+                               const R *scratch, const double *r0, const double *r1, int tile)
 {
     const Inst &in = inst[0];
+    R *out = (R *)in.avg_imf;
+    double *res = in.avg_res;
     const int64_t L = in.L;
     const int64_t ts = (int64_t)blockIdx.x * tile;
     const int64_t cnt = min((int64_t)tile, L - ts);
@@ -308,6 +311,7 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {(void **)&d_active, (size_t)iters * 4},
         {(void **)&d_beta, 8},
         {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
+        {(void **)&d_stats, sizeof(Stats)},
     };
     if (eemd_elems > 0)
         reqs.push_back({&eemd_scratch, (size_t)eemd_elems * elem});
@@ -340,6 +344,8 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         e = cudaMallocHost((void **)&h_state, (size_t)insts * sizeof(State));
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&h_misc, (size_t)tiles * 2 * 4 + 64);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h_stats, sizeof(Stats));
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&staging_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -375,6 +381,8 @@ void Workspace::release()
         cudaFreeHost(h_state);
     if (h_misc)
         cudaFreeHost(h_misc);
+    if (h_stats)
+        cudaFreeHost(h_stats);
     *this = Workspace();
 }
 
@@ -423,6 +431,7 @@ static void launch_pass(Workspace &ws, int64_t ntiles, cudaStream_t s)
     pa.tex = ws.d_tex;
     pa.tsol = ws.d_tsol;
     pa.taux = ws.d_taux;
+    pa.stats = ws.d_stats;
     k_pass<R, kTile, kThreads>
         <<<(unsigned)ntiles, kThreads, sizeof(PassSmem<R, kTile, kThreads>), s>>>(pa);
 }
@@ -456,27 +465,79 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     return ra;
 }
 
-// Runs passes until every instance is done (the state of each instance must be
-// initialised to MODE_INIT with r0 holding its serialized signal).
+// Records an event pair around a launch when the plan is profiling.
+struct LaunchTimer {
+    Profiler *pr;
+    cudaStream_t s;
+    int kind; // 0 pass, 1 reduce
+    size_t slot = 0;
+    LaunchTimer(Profiler *p, cudaStream_t st, int k) : pr(p), s(st), kind(k)
+    {
+        if (pr && pr->on)
+            slot = pr->begin(kind, s);
+    }
+    ~LaunchTimer()
+    {
+        if (pr && pr->on)
+            pr->end(slot, s);
+    }
+};
+
+// All device work of one decomposition after the descriptors are uploaded. Everything
+// here is stream-ordered and, for the fixed sift count, free of host synchronization,
+// so it can be captured into a CUDA graph.
 template <typename R>
-static semd_status run_passes(Workspace &ws, const semd_params &p, int ninst, int64_t ntiles,
-                              cudaStream_t s, std::string &err)
+static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t ntiles,
+                                         int ntiles0, cudaStream_t s, bool capture)
 {
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    const semd_params &p = pl.p;
+    const bool eemd = p.ensemble_trials > 1;
+    Profiler *prof = capture ? nullptr : &pl.prof;
+    int64_t launches = 0;
     const int iters = max_iterations(p);
+    SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)ninst * sizeof(State), s));
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
+    SEMD_CU(cudaMemsetAsync(ws.d_stats, 0, sizeof(Stats), s));
+    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_tile_inst, ws.r0, kTile,
+                                                      eemd ? 1 : 0);
+    ++launches;
+    if (eemd) {
+        k_std<<<1, 1024, 0, s>>>(ws.d_inst, ws.r0, p.noise_rel_std, ws.d_beta);
+        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, ws.d_beta, ws.r0);
+        launches += 2;
+    }
     ReduceArgs ra = reduce_args(ws, p);
     for (int it = 0; it < iters; ++it) {
-        launch_pass<R>(ws, ntiles, s);
+        {
+            LaunchTimer t(prof, s, 0);
+            launch_pass<R>(ws, ntiles, s);
+        }
         ra.active = ws.d_active + it;
-        k_reduce<<<ninst, 64, 0, s>>>(ra);
-        if (p.stop == SEMD_STOP_SD && (it % 8) == 7) {
+        {
+            LaunchTimer t(prof, s, 1);
+            k_reduce<<<ninst, 64, 0, s>>>(ra);
+        }
+        launches += 2;
+        if (!capture && p.stop == SEMD_STOP_SD && (it % 8) == 7) {
             SEMD_CU(cudaMemcpyAsync(ws.h_misc, ws.d_active + it, 4, cudaMemcpyDeviceToHost, s));
             SEMD_CU(cudaStreamSynchronize(s));
             if (((int32_t *)ws.h_misc)[0] == 0)
                 break;
         }
     }
+    if (eemd) {
+        k_eemd_average<R><<<ntiles0, 256, 0, s>>>(ws.d_inst, ws.d_state, ninst, p.max_imfs,
+                                                  (const R *)ws.eemd_scratch, ws.r0, ws.r1,
+                                                  kTile);
+    } else {
+        k_finalize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
+                                                         ws.r0, ws.r1, kTile, p.max_imfs);
+    }
+    ++launches;
     SEMD_CU(cudaGetLastError());
+    pl.stat_launches = launches;
     return SEMD_OK;
 }
 
@@ -507,6 +568,11 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
             in.imf_stride = in.L;
             in.imf_serialized = 1;
             in.res = nullptr;
+            if (i == 0) {
+                in.noise = d_noise;
+                in.avg_imf = q.d_imfs;
+                in.avg_res = q.d_residue;
+            }
         } else {
             in.imf = q.d_imfs;
             in.imf_stride = q.rows * q.cols;
@@ -519,30 +585,50 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     semd_status st = ws.layout(ninst, ntiles, s, err);
     if (st != SEMD_OK)
         return st;
-    SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)ninst * sizeof(State), s));
-    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_tile_inst, ws.r0, kTile,
-                                                      eemd ? 1 : 0);
-    if (eemd) {
-        k_std<<<1, 1024, 0, s>>>(ws.r0 + ws.h_inst[0].off, ws.h_inst[0].L, p.noise_rel_std,
-                                 ws.d_beta);
-        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, (const R *)d_noise, ws.d_beta,
-                                           ws.r0);
-    }
-    st = run_passes<R>(ws, p, ninst, ntiles, s, err);
-    if (st != SEMD_OK)
-        return st;
-    if (eemd) {
-        const Inst &in0 = ws.h_inst[0];
-        k_eemd_average<R><<<in0.ntiles, 256, 0, s>>>(
-            ws.d_inst, ws.d_state, ninst, p.max_imfs, (const R *)ws.eemd_scratch, ws.r0, ws.r1,
-            (R *)insts[0].d_imfs, insts[0].d_residue, kTile);
+    const int ntiles0 = ws.h_inst[0].ntiles;
+    const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
+    pl.prof.reset();
+    if (use_graph) {
+        const GraphKey key{ninst, ntiles, ntiles0};
+        if (!pl.graph_exec || !(pl.graph_key == key)) {
+            if (pl.graph_exec) {
+                cudaGraphExecDestroy(pl.graph_exec);
+                pl.graph_exec = nullptr;
+            }
+            // capture on the plan's own stream so that any caller stream (including the
+            // legacy default stream) can be used
+            cudaGraph_t g = nullptr;
+            SEMD_CU(cudaStreamBeginCapture(pl.gstream, cudaStreamCaptureModeThreadLocal));
+            st = enqueue_decomposition<R>(pl, ninst, ntiles, ntiles0, pl.gstream, true);
+            cudaError_t ce = cudaStreamEndCapture(pl.gstream, &g);
+            if (st != SEMD_OK) {
+                if (g)
+                    cudaGraphDestroy(g);
+                return st;
+            }
+            SEMD_CU(ce);
+            ce = cudaGraphInstantiate(&pl.graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            SEMD_CU(ce);
+            pl.graph_key = key;
+            pl.graph_launches = pl.stat_launches;
+        }
+        SEMD_CU(cudaEventRecord(pl.ev_in, s));
+        SEMD_CU(cudaStreamWaitEvent(pl.gstream, pl.ev_in, 0));
+        SEMD_CU(cudaGraphLaunch(pl.graph_exec, pl.gstream));
+        SEMD_CU(cudaEventRecord(pl.ev_out, pl.gstream));
+        SEMD_CU(cudaStreamWaitEvent(s, pl.ev_out, 0));
+        pl.stat_launches = pl.graph_launches;
+        pl.stat_graph = 1;
     } else {
-        k_finalize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
-                                                         ws.r0, ws.r1, kTile, p.max_imfs);
+        st = enqueue_decomposition<R>(pl, ninst, ntiles, ntiles0, s, false);
+        if (st != SEMD_OK)
+            return st;
+        pl.stat_graph = 0;
     }
-    SEMD_CU(cudaGetLastError());
     SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, (size_t)ninst * sizeof(State),
                             cudaMemcpyDeviceToHost, s));
+    SEMD_CU(cudaMemcpyAsync(ws.h_stats, ws.d_stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
     pl.last_ninst = ninst;
     pl.last_count = eemd ? 1 : count;
     if (n_imfs) {
@@ -735,9 +821,16 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     pl->L = L;
     semd_status st = pl->ws.allocate(samples, ninst, tiles, rent, max_iterations(*params), elem,
                                       eemd_elems, mem_budget, err);
+    if (st == SEMD_OK) {
+        if (cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            err = "stream or event creation failed";
+            st = SEMD_ECUDA;
+        }
+    }
     if (st != SEMD_OK) {
-        pl->ws.release();
-        delete pl;
+        serial_emd_destroy(pl);
         return st;
     }
     *out = pl;
@@ -829,8 +922,47 @@ void serial_emd_destroy(semd_plan_t plan)
 {
     if (!plan)
         return;
+    if (plan->gstream)
+        cudaStreamSynchronize(plan->gstream);
+    if (plan->graph_exec)
+        cudaGraphExecDestroy(plan->graph_exec);
+    if (plan->ev_in)
+        cudaEventDestroy(plan->ev_in);
+    if (plan->ev_out)
+        cudaEventDestroy(plan->ev_out);
+    if (plan->gstream)
+        cudaStreamDestroy(plan->gstream);
+    plan->prof.destroy();
     plan->ws.release();
     delete plan;
+}
+
+semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int profile)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    plan->graphs = use_graphs != 0;
+    plan->prof.on = profile != 0;
+    return SEMD_OK;
+}
+
+semd_status serial_emd_plan_stats(semd_plan_t plan, semd_stats *out)
+{
+    if (!plan || !out)
+        return SEMD_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->kernel_launches = plan->stat_launches;
+    out->used_graph = plan->stat_graph;
+    out->sample_sifts = (int64_t)plan->ws.h_stats->sample_sifts;
+    out->pass_bytes = (int64_t)plan->ws.h_stats->pass_bytes;
+    double ms[2];
+    int64_t cnt[2];
+    plan->prof.totals(ms, cnt);
+    out->pass_launches = cnt[0];
+    out->pass_ms = ms[0];
+    out->reduce_launches = cnt[1];
+    out->reduce_ms = ms[1];
+    return SEMD_OK;
 }
 
 const char *serial_emd_last_error(semd_plan_t plan)

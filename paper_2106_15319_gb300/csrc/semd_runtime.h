@@ -1,6 +1,8 @@
 // Internal host-side declarations shared by the runtime and the server.
 #pragma once
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "semd_types.h"
 #include "serial_emd.h"
@@ -33,6 +35,7 @@ struct Workspace {
     int32_t *d_active = nullptr;
     double *d_beta = nullptr;
     int32_t *d_misc = nullptr;
+    Stats *d_stats = nullptr;
     void *eemd_scratch = nullptr;
     // pinned host staging
     Inst *h_inst = nullptr;
@@ -40,6 +43,7 @@ struct Workspace {
     int64_t *h_rbase = nullptr;
     State *h_state = nullptr;
     void *h_misc = nullptr;
+    Stats *h_stats = nullptr;
     cudaEvent_t staging_done = nullptr;
 
     semd_status allocate(int64_t samples, int insts, int64_t tiles, int64_t rentries, int iters,
@@ -54,6 +58,68 @@ bool geometry(const semd_params &p, int64_t rows, int64_t cols, int order, int64
 bool validate(const semd_params &p, std::string &err);
 int max_iterations(const semd_params &p);
 
+// Optional per-launch timing of the pass and reduce kernels (CUDA events on the
+// launching stream), used by the benchmark's roofline figures.
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<std::pair<int, size_t>> rec; // (kind, index of the start event)
+    size_t used = 0;
+    void reset()
+    {
+        rec.clear();
+        used = 0;
+    }
+    size_t begin(int kind, cudaStream_t s)
+    {
+        while (ev.size() < used + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess)
+                return (size_t)-1;
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[used], s);
+        rec.push_back({kind, used});
+        used += 2;
+        return rec.size() - 1;
+    }
+    void end(size_t slot, cudaStream_t s)
+    {
+        if (slot != (size_t)-1)
+            cudaEventRecord(ev[rec[slot].second + 1], s);
+    }
+    void totals(double ms[2], int64_t cnt[2]) const
+    {
+        ms[0] = ms[1] = 0.0;
+        cnt[0] = cnt[1] = 0;
+        for (auto &r : rec) {
+            float t = 0.f;
+            cudaEventSynchronize(ev[r.second + 1]);
+            if (cudaEventElapsedTime(&t, ev[r.second], ev[r.second + 1]) == cudaSuccess) {
+                ms[r.first] += t;
+                cnt[r.first] += 1;
+            }
+        }
+    }
+    void destroy()
+    {
+        for (auto e : ev)
+            cudaEventDestroy(e);
+        ev.clear();
+        reset();
+    }
+};
+
+struct GraphKey {
+    int ninst = 0;
+    int64_t ntiles = 0;
+    int ntiles0 = 0;
+    bool operator==(const GraphKey &o) const
+    {
+        return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0;
+    }
+};
+
 } // namespace semd
 
 struct semd_plan_s {
@@ -62,5 +128,16 @@ struct semd_plan_s {
     semd::Workspace ws;
     std::string err;
     int last_ninst = 0, last_count = 0;
+    // CUDA graph of the fixed-sift-count decomposition, replayed on the plan's stream
+    bool graphs = true;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    semd::GraphKey graph_key;
+    int64_t graph_launches = 0;
+    // statistics of the last decomposition
+    semd::Profiler prof;
+    int64_t stat_launches = 0;
+    int stat_graph = 0;
     void counts(int count, int *n_imfs, int *sifts) const;
 };

@@ -33,6 +33,15 @@ struct Inst {
     void *imf;            // IMF output base
     double *res;          // residue output (input shape), or null
     int64_t imf_stride;   // elements between IMF slots
+    const void *noise;    // EEMD (instance 0): trials x L noise realizations
+    void *avg_imf;        // EEMD (instance 0): averaged IMF output
+    double *avg_res;      // EEMD (instance 0): averaged residue output, or null
+};
+
+// Device counters of one decomposition (summed by the pass kernel, one atomic per CTA).
+struct Stats {
+    unsigned long long sample_sifts; // serialized samples times sifts
+    unsigned long long pass_bytes;   // algorithmic HBM bytes of the pass kernel
 };
 
 // Mutable per-instance state of the sifting state machine.
@@ -73,6 +82,7 @@ struct PassArgs {
     TileExport *tex;
     const TileSolve *tsol;
     TileAux *taux;
+    Stats *stats;
 };
 
 enum RKind : int32_t { RK_FIXED = 0, RK_FREE = 1, RK_F = 2, RK_L = 3, RK_FL = 4 };

@@ -77,6 +77,12 @@ class Plan:
         n = capi.serial_emd_decompose_batch(self.handle, items, stream, wait)
         return outs, n
 
+    def set_options(self, use_graphs: bool = True, profile: bool = False):
+        capi.serial_emd_plan_set_options(self.handle, use_graphs, profile)
+
+    def stats(self) -> capi.semd_stats:
+        return capi.serial_emd_plan_stats(self.handle)
+
     def counts(self, count: int = 1):
         return capi.serial_emd_plan_counts(self.handle, count, self.params.max_imfs)
 
