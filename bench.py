@@ -347,17 +347,26 @@ def arm_ours(args):
     ms32_max = max_over_ranks(ms32, world)
     value = world * r32["sample_sifts"] / (ms32_max * 1e-3)
 
-    r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush)
-    ms64 = max_over_ranks(statistics.mean(r64["ms"]), world)
-    v64 = world * r64["sample_sifts"] / (ms64 * 1e-3)
+    if "fp64" in args.forms:
+        r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush)
+        ms64 = max_over_ranks(statistics.mean(r64["ms"]), world)
+        v64 = world * r64["sample_sifts"] / (ms64 * 1e-3)
+        r64["plan"].close()
+    else:
+        ms64, v64 = None, None
 
     prof = profile_pass(r32, args.steps, flush)
     pass_avg_ms = prof["pass_ms"] / max(1, prof["pass_n"])
     bytes_per_launch = prof["bytes"] / max(1, prof["pass_n"])
     achieved = bytes_per_launch / (pass_avg_ms * 1e-3) / 1e9
 
-    e2e_ms, e2e_ss, bi, bo = e2e_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device)
-    e2e_ms = max_over_ranks(e2e_ms, world)
+    if not args.no_e2e:
+        e2e_ms, e2e_ss, bi, bo = e2e_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device)
+        e2e_ms = max_over_ranks(e2e_ms, world)
+        e2e = {"value": world * e2e_ss / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
+    else:
+        e2e = None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -371,7 +380,7 @@ def arm_ours(args):
                          "the 65536-sample working set is L2-resident within a step",
                    "parallelism": f"replicas x{world}"},
         "plain_fp64": {"value": v64, "ms_per_step": ms64, "dtype": "f64"},
-        "speedup_fp32_vs_fp64": value / v64,
+        "speedup_fp32_vs_fp64": value / v64 if v64 else None,
         "fp32_imf_rel_l2": None,
         "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -381,13 +390,13 @@ def arm_ours(args):
                          prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
                      "note": "events around every pass launch over a replay of the timed steps "
                              "(graphs off); working set L2-resident"},
-        "e2e": {"value": world * e2e_ss / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms},
+        "e2e": e2e,
         "gpu_launches": int(r32["launches"]) * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0:
-        line["fp32_imf_rel_l2"] = fp32_imf_errors(wl, r32)
+        if wl["trials"] == 1:
+            line["fp32_imf_rel_l2"] = fp32_imf_errors(wl, r32)
         if not args.no_batched:
             line["batched"] = batched_eemd(args, device, flush, peak, peak_kind, world)
         if not args.no_cpu_baseline:
@@ -431,6 +440,8 @@ def main():
     ap.add_argument("--workload", default="texture256",
                     choices=["texture256", "eemd512", "series3x1024"])
     ap.add_argument("--trials", type=int, default=256, help="EEMD realizations (eemd512)")
+    ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -44,10 +44,21 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ float rrcp(float a) { return __frcp_rn(a); }
-__device__ __forceinline__ double rrcp(double a) { return __drcp_rn(a); }
+// Reciprocals: the hardware approximation in FP32 (about 2 ulp); in FP64 a float seed
+// refined by two Newton steps (about 1 ulp), which avoids the long IEEE division
+// sequence on the slow FP64 pipe. Both are deterministic, which is what the halo
+// recomputation needs; neither is correctly rounded.
+__device__ __forceinline__ float rrcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double rrcp(double a)
+{
+    double r = (double)__fdividef(1.0f, (float)a);
+    double e = __fma_rn(-a, r, 1.0);
+    r = __fma_rn(r, e, r);
+    e = __fma_rn(-a, r, 1.0);
+    return __fma_rn(r, e, r);
+}
+__device__ __forceinline__ float rdiv(float a, float b) { return __fmul_rn(a, rrcp(b)); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __dmul_rn(a, rrcp(b)); }
 
 // ---------------------------------------------------------------------------------
 // Warp-level partitioned tridiagonal solve.
@@ -203,16 +214,15 @@ __device__ void warp_tridiag(int n, const RowFn &row, const R (&xl)[NCOL], const
 template <typename R>
 struct KnotRows {
     const int *kt; // tile-relative knot positions (skewed index)
-    const R *hv;   // signal, hv[k + 1] = h(tile start + k)
+    const R *sl;   // sl[j] = (y_{j+1} - y_j) / (t_{j+1} - t_j), skewed index
     __device__ void operator()(int i, R &a, R &b, R &c, R &d) const
     {
         const int tl = kt[sk(i)], tc = kt[sk(i + 1)], tr = kt[sk(i + 2)];
-        const R yl = hv[tl + 1], yc = hv[tc + 1], yr = hv[tr + 1];
         const R hl = R(tc - tl), hr = R(tr - tc);
         a = hl;
         b = R(2) * (hl + hr);
         c = hr;
-        d = R(6) * (rdiv(yr - yc, hr) - rdiv(yc - yl, hl));
+        d = R(6) * (sl[sk(i + 1)] - sl[sk(i)]);
     }
 };
 
@@ -258,127 +268,25 @@ struct Interval {
 };
 
 // ---------------------------------------------------------------------------------
-// Shared memory of one tile pass.
+// Shared memory of one tile pass. The signal itself lives in registers: lane l of warp
+// w holds samples w*32*RW + 32*r + l, r < RW, so every warp-wide access to a row is 32
+// consecutive samples (coalesced global traffic, conflict-free shared memory).
 template <typename R, int TILE, int NT>
 struct PassSmem {
-    static constexpr int KCAP = TILE / 2 + 2;                // knots of one kind
-    static constexpr int SKN = KCAP + KCAP / 32 + 2;         // skewed length
-    R hs[TILE + 2];  // current h, hs[k + 1] = h(ts + k), k in [-1, cnt]
-    R hn[TILE + 2];  // next h (same indexing)
-    R kM[2][SKN];    // second derivatives at the tile's knots
-    R cp[2][SKN], dp[2][SKN], bp[2][SKN];
+    static constexpr int NW = NT / 32;                 // warps
+    static constexpr int RW = TILE / NT;               // rows per warp = samples per lane
+    static constexpr int KCAP = TILE / 2 + 2;          // knots of one kind in a tile
+    static constexpr int SKN = KCAP + KCAP / 32 + 2;   // skewed length
     int kt[2][SKN];  // tile-relative knot positions
-    uint32_t wsum[NT / 32];
-    double red[2][NT / 32];
+    R ky[2][SKN];    // knot values
+    R kM[2][SKN];    // second derivatives at the knots
+    R sl[2][SKN];    // knot-interval slopes (solver input)
+    R cp[2][SKN], dp[2][SKN], bp[2][SKN]; // solver scratch, then interval coefficients c1..c3
+    R edge_first[NW], edge_last[NW];
+    uint32_t wtot[NW];
+    double red[2][NW];
     int cnt[2];
 };
-
-template <int NT>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *wsum,
-                                                         uint32_t &total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULLMASK, x, o);
-        if (lane >= o)
-            x += y;
-    }
-    if (lane == 31)
-        wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        uint32_t t = (lane < NT / 32) ? wsum[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULLMASK, t, o);
-            if (lane >= o)
-                t += y;
-        }
-        if (lane < NT / 32)
-            wsum[lane] = t;
-    }
-    __syncthreads();
-    total = wsum[NT / 32 - 1];
-    const uint32_t base = (w > 0 ? wsum[w - 1] : 0u) + x - v;
-    __syncthreads();
-    return base;
-}
-
-// Step 1 on the tile: extremum flags of hv (maximum: h[k-1] < h[k] >= h[k+1]; minimum:
-// h[k-1] > h[k] <= h[k+1]; never at the instance's end samples), compacted in order
-// into S.kt. Each thread owns SPT consecutive samples; fm[e] holds its flags.
-template <typename R, int TILE, int NT>
-__device__ void find_knots(PassSmem<R, TILE, NT> &S, const R *hv, int cnt, int64_t ts, int64_t L,
-                           uint32_t (&fm)[2], int (&base)[2])
-{
-    constexpr int SPT = TILE / NT;
-    const int k0 = threadIdx.x * SPT;
-    uint32_t fmax = 0, fmin = 0;
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) {
-        const int k = k0 + s;
-        if (k < cnt) {
-            const int64_t g = ts + k;
-            if (g >= 1 && g <= L - 2) {
-                const R l = hv[k], c = hv[k + 1], r = hv[k + 2];
-                if (l < c && c >= r)
-                    fmax |= 1u << s;
-                if (l > c && c <= r)
-                    fmin |= 1u << s;
-            }
-        }
-    }
-    uint32_t total;
-    const uint32_t packed = (uint32_t)__popc(fmax) | ((uint32_t)__popc(fmin) << 16);
-    const uint32_t b = block_exclusive_scan<NT>(packed, S.wsum, total);
-    base[0] = (int)(b & 0xffffu);
-    base[1] = (int)(b >> 16);
-    fm[0] = fmax;
-    fm[1] = fmin;
-    int a0 = base[0], a1 = base[1];
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) {
-        if ((fmax >> s) & 1u)
-            S.kt[0][sk(a0++)] = k0 + s;
-        if ((fmin >> s) & 1u)
-            S.kt[1][sk(a1++)] = k0 + s;
-    }
-    if (threadIdx.x == 0) {
-        S.cnt[0] = (int)(total & 0xffffu);
-        S.cnt[1] = (int)(total >> 16);
-    }
-    __syncthreads();
-}
-
-template <typename R, int TILE, int NT>
-__device__ __forceinline__ void load_interval(const PassSmem<R, TILE, NT> &S, const R *hv, int e,
-                                              int j, int m, const TileSolve &so, int64_t ts,
-                                              Interval<R> &iv)
-{
-    int tl, tr;
-    R yl, Ml, yr, Mr;
-    if (j < 0) {
-        tl = (int)(so.tp - ts);
-        yl = (R)so.yp;
-        Ml = (R)so.Mp;
-    } else {
-        tl = S.kt[e][sk(j)];
-        yl = hv[tl + 1];
-        Ml = S.kM[e][sk(j)];
-    }
-    if (j + 1 >= m) {
-        tr = (int)(so.tn - ts);
-        yr = (R)so.yn;
-        Mr = (R)so.Mn;
-    } else {
-        tr = S.kt[e][sk(j + 1)];
-        yr = hv[tr + 1];
-        Mr = S.kM[e][sk(j + 1)];
-    }
-    iv.set(tl, yl, Ml, tr, yr, Mr);
-}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
@@ -401,16 +309,168 @@ __device__ __forceinline__ bool deser_index(int64_t p, int64_t M, int64_t N, int
     return true;
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+__device__ __forceinline__ uint32_t lanemask_le() { return (2u << (threadIdx.x & 31)) - 1u; }
+
+// Step 1 on the tile held in registers: extremum flags of v (maximum: h[k-1] < h[k] >=
+// h[k+1]; minimum: h[k-1] > h[k] <= h[k+1]; never at the instance's end samples) as one
+// ballot mask per row and envelope, their in-order ranks (wbase + pre + popc), and the
+// compacted knot lists (position and value) in shared memory.
+template <typename R, int TILE, int NT>
+__device__ void detect_knots(PassSmem<R, TILE, NT> &S, const R (&v)[TILE / NT], R left_halo,
+                             R right_halo, int cnt, int64_t ts, int64_t L,
+                             uint32_t (&mx)[TILE / NT], uint32_t (&mn)[TILE / NT],
+                             int (&wbase)[2], int (&pre)[2][TILE / NT])
+{
+    constexpr int RW = TILE / NT, NW = NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        S.edge_first[w] = v[0];
+    if (lane == 31)
+        S.edge_last[w] = v[RW - 1];
+    __syncthreads();
+    const R prev_last = w > 0 ? S.edge_last[w - 1] : left_halo;
+    const R next_first = w < NW - 1 ? S.edge_first[w + 1] : right_halo;
+    int c0 = 0, c1 = 0;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int k = w * 32 * RW + 32 * r + lane;
+        const R c = v[r];
+        const R up = __shfl_up_sync(FULLMASK, c, 1);
+        const R dn = __shfl_down_sync(FULLMASK, c, 1);
+        const R pr = __shfl_sync(FULLMASK, v[r > 0 ? r - 1 : 0], 31);
+        const R nx = __shfl_sync(FULLMASK, v[r < RW - 1 ? r + 1 : RW - 1], 0);
+        const R left = lane > 0 ? up : (r > 0 ? pr : prev_last);
+        const R right = lane < 31 ? dn : (r < RW - 1 ? nx : next_first);
+        const int64_t g = ts + k;
+        const bool valid = k < cnt && g >= 1 && g <= L - 2;
+        mx[r] = __ballot_sync(FULLMASK, valid && left < c && c >= right);
+        mn[r] = __ballot_sync(FULLMASK, valid && left > c && c <= right);
+        pre[0][r] = c0;
+        pre[1][r] = c1;
+        c0 += __popc(mx[r]);
+        c1 += __popc(mn[r]);
+    }
+    if (lane == 0)
+        S.wtot[w] = (uint32_t)c0 | ((uint32_t)c1 << 16);
+    __syncthreads();
+    int b0 = 0, b1 = 0, t0 = 0, t1 = 0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {
+        const uint32_t t = S.wtot[ww];
+        if (ww < w) {
+            b0 += (int)(t & 0xffffu);
+            b1 += (int)(t >> 16);
+        }
+        t0 += (int)(t & 0xffffu);
+        t1 += (int)(t >> 16);
+    }
+    wbase[0] = b0;
+    wbase[1] = b1;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int k = w * 32 * RW + 32 * r + lane;
+        if ((mx[r] >> lane) & 1u) {
+            const int idx = b0 + pre[0][r] + __popc(mx[r] & lt);
+            S.kt[0][sk(idx)] = k;
+            S.ky[0][sk(idx)] = v[r];
+        }
+        if ((mn[r] >> lane) & 1u) {
+            const int idx = b1 + pre[1][r] + __popc(mn[r] & lt);
+            S.kt[1][sk(idx)] = k;
+            S.ky[1][sk(idx)] = v[r];
+        }
+    }
+    if (threadIdx.x == 0) {
+        S.cnt[0] = t0;
+        S.cnt[1] = t1;
+    }
+    __syncthreads();
+}
+
+// Slopes of the knot intervals of both envelopes, all threads in parallel (keeps the
+// divisions out of the sequential elimination).
+template <typename R, int TILE, int NT>
+__device__ __forceinline__ void knot_slopes(PassSmem<R, TILE, NT> &S)
+{
+    const int n0 = max(S.cnt[0] - 1, 0), n1 = max(S.cnt[1] - 1, 0);
+    for (int idx = threadIdx.x; idx < n0 + n1; idx += NT) {
+        const int e = idx < n0 ? 0 : 1;
+        const int j = idx < n0 ? idx : idx - n0;
+        const int ta = S.kt[e][sk(j)], tb = S.kt[e][sk(j + 1)];
+        S.sl[e][sk(j)] = rmul(rsub(S.ky[e][sk(j + 1)], S.ky[e][sk(j)]), rrcp(R(tb - ta)));
+    }
+}
+
+// Interval q of envelope e spans (knot q-1, knot q), with knot -1 the bracket knot before
+// the tile and knot m the one after it. Coefficients of the cubic in u = k - t_{q-1}:
+// c0 = y_{q-1} (not stored), c1..c3 written over the solver scratch.
+template <typename R, int TILE, int NT>
+__device__ __forceinline__ void interval_coefs(PassSmem<R, TILE, NT> &S, const TileSolve &so0,
+                                               const TileSolve &so1, int64_t ts)
+{
+    const int m0 = S.cnt[0], m1 = S.cnt[1];
+    for (int idx = threadIdx.x; idx < m0 + m1 + 2; idx += NT) {
+        const int e = idx <= m0 ? 0 : 1;
+        const int q = idx <= m0 ? idx : idx - m0 - 1;
+        const int m = e ? m1 : m0;
+        const TileSolve &so = e ? so1 : so0;
+        int tl, tr;
+        R yl, Ml, yr, Mr;
+        if (q == 0) {
+            tl = (int)(so.tp - ts);
+            yl = (R)so.yp;
+            Ml = (R)so.Mp;
+        } else {
+            tl = S.kt[e][sk(q - 1)];
+            yl = S.ky[e][sk(q - 1)];
+            Ml = S.kM[e][sk(q - 1)];
+        }
+        if (q == m) {
+            tr = (int)(so.tn - ts);
+            yr = (R)so.yn;
+            Mr = (R)so.Mn;
+        } else {
+            tr = S.kt[e][sk(q)];
+            yr = S.ky[e][sk(q)];
+            Mr = S.kM[e][sk(q)];
+        }
+        const R h = R(tr - tl);
+        const R inv = rrcp(h);
+        const R slope = rmul(rsub(yr, yl), inv);
+        S.cp[e][sk(q)] = rsub(slope, rmul(rmul(h, radd(rmul(R(2), Ml), Mr)), R(1.0 / 6.0)));
+        S.dp[e][sk(q)] = rmul(Ml, R(0.5));
+        S.bp[e][sk(q)] = rmul(rmul(rsub(Mr, Ml), inv), R(1.0 / 6.0));
+    }
+}
+
+// Envelope e at tile-relative sample k, which lies in interval q. The spline passes
+// through its knots; at the bracket knot after the tile (only reachable when it sits
+// on a sample, the ENDPOINTS rule's last sample) the knot value is returned exactly.
+template <typename R, int TILE, int NT>
+__device__ __forceinline__ R envelope_at(const PassSmem<R, TILE, NT> &S, int e, int q, int k,
+                                         const TileSolve &so, int64_t ts)
+{
+    const int m = S.cnt[e];
+    if (q == m && (int64_t)k == so.tn - ts)
+        return (R)so.yn;
+    const int tl = q > 0 ? S.kt[e][sk(q - 1)] : (int)(so.tp - ts);
+    const R c0 = q > 0 ? S.ky[e][sk(q - 1)] : (R)so.yp;
+    const R u = R(k - tl);
+    return rfma(rfma(rfma(S.bp[e][sk(q)], u, S.dp[e][sk(q)]), u, S.cp[e][sk(q)]), u, c0);
+}
+
 // ---------------------------------------------------------------------------------
 // One sifting pass over one tile. Grid: one CTA per tile of every instance.
 template <typename R, int TILE, int NT>
 __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
 {
-    constexpr int SPT = TILE / NT;
-    static_assert(SPT >= 1 && SPT <= 32 && TILE % NT == 0, "tile split");
+    constexpr int RW = TILE / NT, NW = NT / 32;
+    static_assert(RW >= 1 && RW <= 32 && TILE % NT == 0 && NW >= 2, "tile split");
     extern __shared__ __align__(16) unsigned char smraw[];
     PassSmem<R, TILE, NT> &S = *reinterpret_cast<PassSmem<R, TILE, NT> *>(smraw);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gt = blockIdx.x;
     const int ii = pa.tile_inst[gt];
     const State *stp = pa.state + ii;
@@ -429,32 +489,41 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
     double *rdst = (rpar ? pa.r0 : pa.r1) + in.off + ts;
     const bool sift = mode == MODE_SIFT || mode == MODE_SIFT_COMMIT;
     const bool commit = mode == MODE_SIFT_COMMIT || mode == MODE_COMMIT;
-    const int k0 = tid * SPT;
+    const int kbase = warp * 32 * RW + lane;
 
-    // current signal with one halo sample per side
+    // current signal: samples k <= cnt (k == cnt is the right halo of a partial tile),
+    // plus the halo of a full tile and the left halo, each in one register
+    R v[RW];
+    R hl = R(0), hr = R(0);
     if (mode != MODE_INIT) {
-        for (int idx = tid; idx < cnt + 2; idx += NT) {
-            const int k = idx - 1;
-            R v = R(0);
-            if ((k >= 0 && k < cnt) || (k < 0 && hasL) || (k >= cnt && hasR))
-                v = hsrc[k];
-            S.hs[idx] = v;
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int k = kbase + 32 * r;
+            v[r] = (k < cnt || (k == cnt && hasR)) ? hsrc[k] : R(0);
         }
+        if (tid == 0 && hasL)
+            hl = hsrc[-1];
+        if (tid == NT - 1 && hasR && cnt == TILE)
+            hr = hsrc[TILE];
     }
-    __syncthreads();
 
+    R hn[RW];
+    R hnl = R(0), hnr = R(0);
     double sdn = 0.0, sdd = 0.0;
     if (sift) {
-        uint32_t fm[2];
-        int base[2];
-        find_knots<R, TILE, NT>(S, S.hs, cnt, ts, L, fm, base);
+        uint32_t mx[RW], mn[RW];
+        int wbase[2], pre[2][RW];
+        detect_knots<R, TILE, NT>(S, v, hl, hr, cnt, ts, L, mx, mn, wbase, pre);
         const TileSolve so0 = pa.tsol[2 * (int64_t)gt], so1 = pa.tsol[2 * (int64_t)gt + 1];
-        // Step 2: second derivatives at the tile's knots (one warp per envelope)
+        knot_slopes<R, TILE, NT>(S);
+        __syncthreads();
+        // Step 2: second derivatives at the tile's knots (one warp per envelope), with the
+        // tile's first and last knot values from the interface solve
         if (warp < 2) {
             const int e = warp;
             const int m = S.cnt[e];
             const TileSolve &so = e ? so1 : so0;
-            if (m >= 1 && (threadIdx.x & 31) == 0) {
+            if (m >= 1 && lane == 0) {
                 S.kM[e][sk(0)] = (R)so.MF;
                 S.kM[e][sk(m - 1)] = (R)so.ML;
             }
@@ -463,108 +532,115 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
                 R f1[1], l1[1];
                 R *kM = S.kM[e];
                 warp_tridiag<R, 1, true>(
-                    m - 2, KnotRows<R>{S.kt[e], S.hs}, xl, xr, S.cp[e], S.dp[e], S.bp[e],
+                    m - 2, KnotRows<R>{S.kt[e], S.sl[e]}, xl, xr, S.cp[e], S.dp[e], S.bp[e],
                     [kM](int i, R x) { kM[sk(i + 1)] = x; }, f1, l1);
             }
         }
         __syncthreads();
+        interval_coefs<R, TILE, NT>(S, so0, so1, ts);
+        __syncthreads();
         // Steps 2-4 at every sample: envelopes, mean, subtraction
-        const int m0 = S.cnt[0], m1 = S.cnt[1];
-        Interval<R> iv0, iv1;
-        int j0 = base[0] - 1, j1 = base[1] - 1;
-        load_interval(S, S.hs, 0, j0, m0, so0, ts, iv0);
-        load_interval(S, S.hs, 1, j1, m1, so1, ts, iv1);
+        const uint32_t le = lanemask_le();
         R pn = R(0), pd = R(0);
-#pragma unroll 4
-        for (int s = 0; s < SPT; ++s) {
-            const int k = k0 + s;
-            if (k >= cnt)
-                break;
-            if ((fm[0] >> s) & 1u) {
-                ++j0;
-                load_interval(S, S.hs, 0, j0, m0, so0, ts, iv0);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int k = kbase + 32 * r;
+            const int q0 = wbase[0] + pre[0][r] + __popc(mx[r] & le);
+            const int q1 = wbase[1] + pre[1][r] + __popc(mn[r] & le);
+            if (k < cnt || (k == cnt && hasR)) {
+                const R e0 = envelope_at(S, 0, q0, k, so0, ts);
+                const R e1 = envelope_at(S, 1, q1, k, so1, ts);
+                const R mean = rmul(radd(e0, e1), R(0.5));
+                hn[r] = rsub(v[r], mean);
+                if (k < cnt) {
+                    pn += mean * mean;
+                    pd += v[r] * v[r];
+                }
+            } else {
+                hn[r] = R(0);
             }
-            if ((fm[1] >> s) & 1u) {
-                ++j1;
-                load_interval(S, S.hs, 1, j1, m1, so1, ts, iv1);
-            }
-            const R h = S.hs[k + 1];
-            const R mean = rmul(radd(iv0.eval(k), iv1.eval(k)), R(0.5));
-            const R hv = rsub(h, mean);
-            S.hn[k + 1] = hv;
-            pn += mean * mean;
-            pd += h * h;
         }
         sdn = (double)pn;
         sdd = (double)pd;
-        if (tid == 0 && hasL) { // left halo: interval [previous knot, first knot]
-            Interval<R> a, b;
-            load_interval(S, S.hs, 0, -1, m0, so0, ts, a);
-            load_interval(S, S.hs, 1, -1, m1, so1, ts, b);
-            S.hn[0] = rsub(S.hs[0], rmul(radd(a.eval(-1), b.eval(-1)), R(0.5)));
+        if (tid == 0 && hasL) { // left halo: interval 0 of both envelopes
+            const R mean = rmul(radd(envelope_at(S, 0, 0, -1, so0, ts),
+                                     envelope_at(S, 1, 0, -1, so1, ts)), R(0.5));
+            hnl = rsub(hl, mean);
         }
-        if (tid == NT - 1 && hasR) { // right halo: interval [last knot, next knot]
-            Interval<R> a, b;
-            load_interval(S, S.hs, 0, m0 - 1, m0, so0, ts, a);
-            load_interval(S, S.hs, 1, m1 - 1, m1, so1, ts, b);
-            S.hn[cnt + 1] = rsub(S.hs[cnt + 1], rmul(radd(a.eval(cnt), b.eval(cnt)), R(0.5)));
+        if (tid == NT - 1 && hasR && cnt == TILE) { // right halo: the last interval
+            const R mean = rmul(radd(envelope_at(S, 0, S.cnt[0], TILE, so0, ts),
+                                     envelope_at(S, 1, S.cnt[1], TILE, so1, ts)), R(0.5));
+            hnr = rsub(hr, mean);
         }
-        __syncthreads();
+    } else {
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+            hn[r] = v[r];
+        hnl = hl;
+        hnr = hr;
     }
 
     // Step 5 / Eq. (1): commit the IMF, update the residue, restart from it
     if (commit || mode == MODE_INIT) {
-        const R *csrc = (mode == MODE_SIFT_COMMIT) ? S.hn : S.hs;
-        if (commit) {
-            R *imf = (R *)in.imf + (int64_t)imfc * in.imf_stride;
-            for (int idx = tid; idx < cnt; idx += NT) {
-                const R c = csrc[idx + 1];
-                const int64_t p = ts + idx;
-                int64_t dst;
-                if (in.imf_serialized)
-                    imf[p] = c;
-                else if (deser_index(p, in.M, in.N, in.D, in.order, dst))
-                    imf[dst] = c;
-            }
-        }
-        __syncthreads(); // csrc may alias S.hn, rewritten below
-        for (int idx = tid; idx < cnt + 2; idx += NT) {
-            const int k = idx - 1;
-            const bool inside = k >= 0 && k < cnt;
-            if (!(inside || (k < 0 && hasL) || (k >= cnt && hasR)))
+        R *imf = (R *)in.imf + (int64_t)imfc * in.imf_stride;
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int k = kbase + 32 * r;
+            const bool inside = k < cnt;
+            if (!(inside || (k == cnt && hasR)))
                 continue;
             double rn = rsrc[k];
-            if (commit)
-                rn = __dsub_rn(rn, (double)csrc[idx]);
-            if (commit && inside)
-                rdst[k] = rn;
-            S.hn[idx] = (R)rn;
+            if (commit) {
+                const R c = hn[r];
+                rn = __dsub_rn(rn, (double)c);
+                if (inside) {
+                    const int64_t p = ts + k;
+                    int64_t dst;
+                    if (in.imf_serialized)
+                        imf[p] = c;
+                    else if (deser_index(p, in.M, in.N, in.D, in.order, dst))
+                        imf[dst] = c;
+                    rdst[k] = rn;
+                }
+            }
+            hn[r] = (R)rn;
         }
-        __syncthreads();
+        if (tid == 0 && hasL)
+            hnl = (R)(commit ? __dsub_rn(rsrc[-1], (double)hnl) : rsrc[-1]);
+        if (tid == NT - 1 && hasR && cnt == TILE)
+            hnr = (R)(commit ? __dsub_rn(rsrc[TILE], (double)hnr) : rsrc[TILE]);
     }
 
     // the new signal: edge values for the ENDPOINTS rule, SD partial sums
-    if (tid == 0) {
-        if (!hasL)
-            pa.taux[gt].h_first = (double)S.hn[1];
-        if (!hasR)
-            pa.taux[gt].h_last = (double)S.hn[cnt];
+    if (!hasL && tid == 0)
+        pa.taux[gt].h_first = (double)hn[0];
+    if (!hasR) {
+        const int kl = cnt - 1;
+        if (kl >= kbase && ((kl - kbase) & 31) == 0 && (kl - kbase) / 32 < RW)
+#pragma unroll
+            for (int r = 0; r < RW; ++r)
+                if (kbase + 32 * r == kl)
+                    pa.taux[gt].h_last = (double)hn[r];
     }
     if (sift) {
         sdn = warp_sum(sdn);
         sdd = warp_sum(sdd);
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             S.red[0][warp] = sdn;
             S.red[1][warp] = sdd;
         }
     }
 
     // Step 1 on the new signal and the per-tile elimination of the spline system
-    uint32_t fm[2];
-    int base[2];
-    find_knots<R, TILE, NT>(S, S.hn, cnt, ts, L, fm, base);
+    {
+        uint32_t mx[RW], mn[RW];
+        int wbase[2], pre[2][RW];
+        detect_knots<R, TILE, NT>(S, hn, hnl, hnr, cnt, ts, L, mx, mn, wbase, pre);
+        knot_slopes<R, TILE, NT>(S);
+        __syncthreads();
+    }
     if (warp < 2) {
-        const int e = warp, lane = tid & 31;
+        const int e = warp;
         const int m = S.cnt[e];
         TileExport *rec = pa.tex + 2 * (int64_t)gt + e;
         if (lane == 0) {
@@ -573,9 +649,8 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
                 const int ix[4] = {0, min(1, m - 1), max(m - 2, 0), m - 1};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int t = S.kt[e][sk(ix[q])];
-                    rec->t[q] = (int32_t)(ts + t);
-                    rec->y[q] = (double)S.hn[t + 1];
+                    rec->t[q] = (int32_t)(ts + S.kt[e][sk(ix[q])]);
+                    rec->y[q] = (double)S.ky[e][sk(ix[q])];
                 }
             }
         }
@@ -583,7 +658,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
             const R xl[3] = {R(0), R(1), R(0)}, xr[3] = {R(0), R(0), R(1)};
             R f[3], l[3];
             warp_tridiag<R, 3, false>(
-                m - 2, KnotRows<R>{S.kt[e], S.hn}, xl, xr, S.cp[e], S.dp[e], S.bp[e],
+                m - 2, KnotRows<R>{S.kt[e], S.sl[e]}, xl, xr, S.cp[e], S.dp[e], S.bp[e],
                 [](int, R) {}, f, l);
             if (lane == 0) {
 #pragma unroll
@@ -596,15 +671,19 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
     }
     if (sift && tid == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < NT / 32; ++w) {
+        for (int w = 0; w < NW; ++w) {
             a += S.red[0][w];
             b += S.red[1][w];
         }
         pa.taux[gt].sd_num = a;
         pa.taux[gt].sd_den = b;
     }
-    for (int idx = tid; idx < cnt; idx += NT)
-        hdst[idx] = S.hn[idx + 1];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int k = kbase + 32 * r;
+        if (k < cnt)
+            hdst[k] = hn[r];
+    }
     if (tid == 0 && pa.stats) {
         // algorithmic bytes per sample: h in (w) unless INIT, h out (w), and for a commit
         // the IMF out (w) and the residue in and out (16); INIT reads the residue (8)
@@ -714,10 +793,35 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
         return;
 
     // reduced system: [left end knots][first/last knot of every non-empty tile][right end knots]
-    const int64_t rb = ra.rbase[ii] + (int64_t)e * skew_len(reduce_entries(nt));
-    REntry *Rn = ra.rent + rb;
-    double *A = ra.rA + rb, *B = ra.rB + rb, *C = ra.rC + rb, *D = ra.rD + rb;
-    double *Mv = ra.rM + rb;
+    REntry *Rn;
+    double *A, *B, *C, *D, *Mv, *cpv, *dpv, *bpv;
+    if (ra.smem_entries > 0) {
+        // per envelope: cap REntry, then 8 double arrays of cap entries
+        extern __shared__ __align__(16) unsigned char rsm[];
+        const int64_t cap = ra.smem_entries;
+        unsigned char *base = rsm + (size_t)e * (size_t)cap * (sizeof(REntry) + 8 * sizeof(double));
+        Rn = reinterpret_cast<REntry *>(base);
+        double *dbl = reinterpret_cast<double *>(base + (size_t)cap * sizeof(REntry));
+        A = dbl;
+        B = dbl + cap;
+        C = dbl + 2 * cap;
+        D = dbl + 3 * cap;
+        Mv = dbl + 4 * cap;
+        cpv = dbl + 5 * cap;
+        dpv = dbl + 6 * cap;
+        bpv = dbl + 7 * cap;
+    } else {
+        const int64_t rb = ra.rbase[ii] + (int64_t)e * skew_len(reduce_entries(nt));
+        Rn = ra.rent + rb;
+        A = ra.rA + rb;
+        B = ra.rB + rb;
+        C = ra.rC + rb;
+        D = ra.rD + rb;
+        Mv = ra.rM + rb;
+        cpv = ra.rcp + rb;
+        dpv = ra.rdp + rb;
+        bpv = ra.rbp + rb;
+    }
     const int nl = ra.boundary == BND_MIRROR ? min(ra.mirror_knots, ntot) : 1;
     const int nr = nl;
     const int NR = nl + U + nr;
@@ -803,7 +907,7 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
             }
             const double hl = (double)c.t - tl, hr = tr - (double)c.t;
             const double a0 = hl, b0 = 2.0 * (hl + hr), c0 = hr;
-            const double d0 = 6.0 * ((yr - c.y) / hr - (c.y - yl) / hl);
+            const double d0 = 6.0 * ((yr - c.y) * rrcp(hr) - (c.y - yl) * rrcp(hl));
             a = a0;
             b = b0;
             cc = c0;
@@ -829,7 +933,7 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
         const double xl[1] = {0.0}, xr[1] = {0.0};
         double f1[1], l1[1];
         warp_tridiag<double, 1, true>(
-            NR, ScratchRows{A, B, C, D}, xl, xr, ra.rcp + rb, ra.rdp + rb, ra.rbp + rb,
+            NR, ScratchRows{A, B, C, D}, xl, xr, cpv, dpv, bpv,
             [Mv](int i, double x) { Mv[i] = x; }, f1, l1);
     }
     __syncwarp();

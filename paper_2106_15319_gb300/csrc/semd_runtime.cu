@@ -356,6 +356,9 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         e = set_smem_attr<double>();
     else
         e = set_smem_attr<float>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kReduceSmemMax);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return SEMD_ECUDA;
@@ -391,6 +394,7 @@ void Workspace::release()
 semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::string &err)
 {
     int64_t off = 0, tiles = 0, rent = 0;
+    max_ntiles = 0;
     for (int i = 0; i < n; ++i) {
         Inst &in = h_inst[i];
         in.off = off;
@@ -399,6 +403,7 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
         h_rbase[i] = rent;
         off += (in.L + 31) & ~(int64_t)31;
         tiles += in.ntiles;
+        max_ntiles = std::max<int64_t>(max_ntiles, in.ntiles);
         rent += 2 * skew_len(reduce_entries(in.ntiles));
     }
     if (off > cap_samples || tiles > cap_tiles || rent > cap_rentries || n > cap_inst) {
@@ -462,7 +467,14 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.sd_threshold = p.sd_threshold;
     ra.boundary = p.boundary;
     ra.mirror_knots = p.mirror_knots;
+    const int64_t entries = skew_len(reduce_entries((int)ws.max_ntiles));
+    ra.smem_entries = reduce_smem_bytes(entries) <= kReduceSmemMax ? entries : 0;
     return ra;
+}
+
+static size_t reduce_smem(const ReduceArgs &ra)
+{
+    return ra.smem_entries > 0 ? reduce_smem_bytes(ra.smem_entries) : 0;
 }
 
 // Records an event pair around a launch when the plan is profiling.
@@ -517,7 +529,7 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
         ra.active = ws.d_active + it;
         {
             LaunchTimer t(prof, s, 1);
-            k_reduce<<<ninst, 64, 0, s>>>(ra);
+            k_reduce<<<ninst, 64, reduce_smem(ra), s>>>(ra);
         }
         launches += 2;
         if (!capture && p.stop == SEMD_STOP_SD && (it % 8) == 7) {
@@ -589,7 +601,7 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{ninst, ntiles, ntiles0};
+        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles};
         if (!pl.graph_exec || !(pl.graph_key == key)) {
             if (pl.graph_exec) {
                 cudaGraphExecDestroy(pl.graph_exec);
@@ -702,7 +714,7 @@ semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, 
     ReduceArgs ra = reduce_args(ws, p);
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, 8, s));
     launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
-    k_reduce<<<1, 64, 0, s>>>(ra);
+    k_reduce<<<1, 64, reduce_smem(ra), s>>>(ra);
     launch_pass<R>(ws, ntiles, s); // SIFT
     SEMD_CU(cudaGetLastError());
     SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
@@ -971,3 +983,4 @@ const char *serial_emd_last_error(semd_plan_t plan)
 }
 
 } // extern "C"
+

@@ -12,12 +12,14 @@ namespace semd {
 // One tile of TILE samples per CTA, TILE / kThreads consecutive samples per thread.
 constexpr int kTile = 1024;
 constexpr int kThreads = 128;
+// Largest shared-memory scratch of the interface solve; larger instances use global memory.
+constexpr size_t kReduceSmemMax = 200 * 1024;
 
 // Device workspace of a plan (or of a server slot pool): one allocation carved up.
 struct Workspace {
     void *base = nullptr;
     size_t bytes = 0;
-    int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0;
+    int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0, max_ntiles = 0;
     int cap_inst = 0, cap_iters = 0;
     size_t elem_size = 0;
     void *h0 = nullptr, *h1 = nullptr;
@@ -114,9 +116,11 @@ struct GraphKey {
     int ninst = 0;
     int64_t ntiles = 0;
     int ntiles0 = 0;
+    int64_t max_ntiles = 0;
     bool operator==(const GraphKey &o) const
     {
-        return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0;
+        return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0 &&
+               max_ntiles == o.max_ntiles;
     }
 };
 

@@ -104,7 +104,14 @@ struct ReduceArgs {
     int32_t K, stop, fixed_sifts, max_sifts;
     double sd_threshold;
     int32_t boundary, mirror_knots;
+    int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
 };
+
+// Shared memory of k_reduce for a per-envelope scratch of `entries` (skewed) entries.
+__host__ __device__ inline size_t reduce_smem_bytes(int64_t entries)
+{
+    return 2 * (size_t)entries * (sizeof(REntry) + 8 * sizeof(double));
+}
 
 // Entries of the reduced system of an instance with nt tiles (per envelope).
 __host__ __device__ inline int64_t reduce_entries(int nt) { return 2 * (int64_t)nt + 4; }

@@ -5,12 +5,18 @@ Tolerances: FP64 per-IMF relative L2 <= 1e-10 (the denominator has a floor of
 float32 first, and the oracle decomposes the rounded values, so both sides start
 from the same numbers.
 
-FP32-mixed: the signal is stored in single precision between sifts, and the
-rounding it adds at every sift grows through the chain of IMFs (the same growth
-appears in the oracle run with single-precision storage, store_f32=True). The
-bar: equal IMF and sift counts, per-IMF relative L2 <= 1e-4 on the two leading
-IMFs, and every IMF and the residue within 1e-2 * ||x|| in L2. The measured
-per-IMF errors are reported in the assertion messages and in the benchmark.
+FP32-mixed: the signal is stored in single precision between sifts. The oracle's
+own store_f32 mode (FP64 arithmetic, single-precision storage at the same points)
+shows what that storage alone does: the leading IMFs move by ~1e-7 of their norm,
+but once the remainder is slow, near-ties between neighbouring samples flip some
+extremum decisions, and later IMFs move by up to ~2e-4 of their own norm (~1e-5 of
+||x||). Whether a last, nearly flat remainder still has enough extrema for one
+more IMF is decided the same way, so the IMF count may differ by one, while the
+sum of that tail (last common IMF onward plus the residue) is reproducible. The
+bar: IMF counts equal or one apart; the two leading IMFs within 1e-4 of their own
+norm; every other IMF before the tail, and the tail sum, within 1e-4 * ||x||.
+The measured per-IMF errors are reported in the assertion messages and in the
+benchmark.
 """
 import numpy as np
 import pytest
@@ -38,20 +44,23 @@ def _rel(a, b, floor):
 
 
 def _check_imfs(imfs_g, res_g, n_g, imfs_o, res_o, n_o, x, prec, what=""):
-    assert n_g == n_o, f"{what}: IMF count {n_g} vs {n_o}"
     nx = np.linalg.norm(x)
     floor = 1e-6 * nx
     K = imfs_o.shape[0]
     errs = [_rel(imfs_g[k], imfs_o[k], floor) for k in range(K)]
     rerr = _rel(res_g, res_o, floor)
     if prec == capi.FP64:
+        assert n_g == n_o, f"{what}: IMF count {n_g} vs {n_o}"
         assert max(errs) <= TOL[prec] and rerr <= TOL[prec], f"{what}: {errs} res {rerr}"
-    else:
-        lead = errs[:2]
-        assert max(lead) <= TOL[prec], f"{what}: leading IMFs {lead} (all {errs})"
-        absn = [np.linalg.norm(imfs_g[k] - imfs_o[k]) / nx for k in range(K)]
-        absn.append(np.linalg.norm(res_g - res_o) / nx)
-        assert max(absn) <= 1e-2, f"{what}: |dc|/|x| {absn} (rel {errs})"
+        return errs
+    assert abs(n_g - n_o) <= 1, f"{what}: IMF count {n_g} vs {n_o}"
+    tail0 = max(min(n_g, n_o) - 1, 0)
+    lead = errs[:min(2, tail0)]
+    assert max(lead, default=0.0) <= TOL[prec], f"{what}: leading IMFs {lead} (all {errs})"
+    absn = [np.linalg.norm(imfs_g[k] - imfs_o[k]) / nx for k in range(tail0)]
+    tail = imfs_g[tail0:].sum(0) + res_g - imfs_o[tail0:].sum(0) - res_o
+    absn.append(np.linalg.norm(tail) / nx)
+    assert max(absn) <= TOL[prec], f"{what}: |dc|/|x| {absn} (rel {errs}; n {n_g} vs {n_o})"
     return errs
 
 
@@ -126,7 +135,8 @@ def test_series_3x1024(prec, D):
     g = _run(X, prec, transition_len=D, max_imfs=8)
     o = _oracle(X, prec, transition_len=D, max_imfs=8)
     _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, f"series D={D}")
-    assert list(g[3]) == list(o[3])
+    common = min(g[2], o[2]) - (0 if prec == capi.FP64 else 1)
+    assert list(g[3][:common]) == list(o[3][:common])
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
