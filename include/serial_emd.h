@@ -172,6 +172,31 @@ semd_status serial_emd_sift(semd_plan_t plan, const void *d_h, int64_t L, void *
                             double *sd_num, double *sd_den, void *stream);
 
 /*
+ * Allocation-free form of serial_emd_sift, for callers that cannot reserve device
+ * memory: code that runs while a CUDA graph is being captured into or replayed on a
+ * pool it does not own, plug-ins hosted by a framework whose caching allocator owns
+ * the device memory, or real-time paths that forbid allocation after start-up. The
+ * paper has no counterpart; it is a packaging of the same sift.
+ * It performs exactly the sift of serial_emd_sift (same kernels, same results) on
+ * d_h (L elements of the precision in params->precision) into d_out (L elements),
+ * with the envelope rule of params->boundary / params->mirror_knots; the other
+ * fields of params are ignored. The sums (h - h')^2 and h^2 are returned through the
+ * host pointers, after the call has waited for the stream.
+ * Scratch: one static device array of about 2.1 MB, compiled into the library, which
+ * every GPU that loads the library holds until the process exits; nothing is
+ * allocated per call (no cudaMalloc, cudaFree or allocating library routine). L
+ * must be in [1, 65536]: a larger L returns SEMD_EINVAL with a message naming the
+ * limit. The first call on a device looks up the array's device address and sets
+ * kernel attributes for that device; make that first call outside any stream
+ * capture. All calls share the one array and each call clears what it needs, so two
+ * calls whose work overlaps on the GPU (different streams or threads) race and
+ * give wrong results: serialize them. Errors (EINVAL, ECUDA) are described by
+ * serial_emd_last_error(NULL).
+ */
+semd_status serial_emd_sift_noalloc(const semd_params *params, const void *d_h, int64_t L,
+                                    void *d_out, double *sd_num, double *sd_den, void *stream);
+
+/*
  * Execution options of a plan. use_graphs (default 1): a decomposition with a fixed
  * sift count is captured once into a CUDA graph (per batch layout) and replayed on
  * the plan's own stream, joined to the caller's stream by events; the first call for

@@ -87,6 +87,10 @@ SIGNATURES = {
     "serial_emd_sift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "serial_emd_sift_noalloc": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_void_p,
+                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "serial_emd_plan_set_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "serial_emd_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_stats)]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
@@ -209,6 +213,15 @@ def serial_emd_sift(plan: int, h, out, stream=None):
     rc = load().serial_emd_sift(plan, _ptr(h), h.numel(), _ptr(out), ctypes.byref(a),
                                 ctypes.byref(b), _stream(stream))
     _check(rc, plan)
+    return a.value, b.value
+
+
+def serial_emd_sift_noalloc(params: semd_params, h, out, stream=None):
+    """Allocation-free single sift (no plan); returns (sum (h - h')^2, sum h^2)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = load().serial_emd_sift_noalloc(ctypes.byref(params), _ptr(h), h.numel(), _ptr(out),
+                                        ctypes.byref(a), ctypes.byref(b), _stream(stream))
+    _check(rc, None)
     return a.value, b.value
 
 

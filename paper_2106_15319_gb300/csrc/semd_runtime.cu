@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -984,3 +985,206 @@ const char *serial_emd_last_error(semd_plan_t plan)
 
 } // extern "C"
 
+// ================================================================= allocation-free sift
+//
+// serial_emd_sift_noalloc: the single sift of serial_emd_sift without a plan. Its
+// scratch (signal and residue buffers, per-tile records of the spline solve, the
+// instance descriptor and state) lives in one file-scope __device__ array, so a call
+// reserves no device memory. Every GPU that loads this library holds the array
+// (kNoAllocBytes, about 2.1 MB) until the process exits. All calls share it: calls
+// that overlap on the GPU (concurrent streams, threads or devices sharing a context)
+// race on it, and each call clears what it needs before use.
+namespace semd {
+
+constexpr int64_t kNoAllocMaxL = 65536;                  // largest accepted L
+constexpr int kNoAllocTiles = (int)(kNoAllocMaxL / kTile);
+constexpr int64_t kNoAllocRent = 2 * skew_len(reduce_entries(kNoAllocTiles));
+constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kNoAllocBytes =
+    4 * na_round(kNoAllocMaxL * 8) +                        // h0, h1 (sized for FP64), r0, r1
+    na_round(sizeof(Inst)) + na_round(sizeof(State)) + na_round(kNoAllocTiles * 4) +
+    na_round(kNoAllocTiles * 2 * sizeof(TileExport)) +
+    na_round(kNoAllocTiles * 2 * sizeof(TileSolve)) + na_round(kNoAllocTiles * sizeof(TileAux)) +
+    na_round(8) +                                           // reduce scratch base
+    na_round(kNoAllocRent * sizeof(REntry)) + 8 * na_round(kNoAllocRent * 8) +
+    na_round(8) + na_round(sizeof(Stats)) + na_round(4 * 8); // active flags, stats, result
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_base[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the device address of the scratch array
+// (its host-side name is only a stand-in) and the shared-memory limits of the kernels.
+static semd_status noalloc_setup(void *&base, std::string &err)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return SEMD_ECUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        err = "device ordinal out of range for the allocation-free sift";
+        return SEMD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("cudaGetSymbolAddress of the static scratch: ") +
+                  cudaGetErrorString(e);
+            return SEMD_ECUDA;
+        }
+        e = set_smem_attr<float>();
+        if (e == cudaSuccess)
+            e = set_smem_attr<double>();
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kReduceSmemMax);
+        if (e != cudaSuccess) {
+            err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return SEMD_ECUDA;
+        }
+        g_noalloc_base[dev] = p;
+    }
+    base = g_noalloc_base[dev];
+    return SEMD_OK;
+}
+
+// Clears the per-call state and writes the instance descriptor (passed by value, so
+// no host staging buffer is needed).
+__global__ void k_noalloc_setup(Inst in, Inst *d_inst, State *d_state, int32_t *tile_inst,
+                                int ntiles, int64_t *rbase, int32_t *active, Stats *stats)
+{
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        tile_inst[t] = 0;
+    if (threadIdx.x == 0) {
+        *d_inst = in;
+        *d_state = State{};
+        rbase[0] = 0;
+        active[0] = 0;
+        active[1] = 0;
+        *stats = Stats{};
+    }
+}
+
+// The sums (h - h')^2 and h^2 over the tiles, in tile order, and the state's mode.
+__global__ void k_noalloc_result(const State *st, const TileAux *taux, int ntiles, double *out)
+{
+    if (threadIdx.x != 0)
+        return;
+    double a = 0.0, b = 0.0;
+    for (int t = 0; t < ntiles; ++t) {
+        a += taux[t].sd_num;
+        b += taux[t].sd_den;
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = (double)st->mode;
+}
+
+template <typename R>
+static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int64_t L,
+                                     void *d_out, double *sd_num, double *sd_den,
+                                     cudaStream_t s, std::string &err)
+{
+    void *base = nullptr;
+    semd_status st = noalloc_setup(base, err);
+    if (st != SEMD_OK)
+        return st;
+    const int ntiles = (int)((L + kTile - 1) / kTile);
+    Workspace ws; // views into the static scratch; never allocated or released
+    char *cur = (char *)base;
+    auto take = [&cur](size_t bytes) {
+        void *q = cur;
+        cur += na_round(bytes);
+        return q;
+    };
+    ws.h0 = take(kNoAllocMaxL * 8);
+    ws.h1 = take(kNoAllocMaxL * 8);
+    ws.r0 = (double *)take(kNoAllocMaxL * 8);
+    ws.r1 = (double *)take(kNoAllocMaxL * 8);
+    ws.d_inst = (Inst *)take(sizeof(Inst));
+    ws.d_state = (State *)take(sizeof(State));
+    ws.d_tile_inst = (int32_t *)take(kNoAllocTiles * 4);
+    ws.d_tex = (TileExport *)take(kNoAllocTiles * 2 * sizeof(TileExport));
+    ws.d_tsol = (TileSolve *)take(kNoAllocTiles * 2 * sizeof(TileSolve));
+    ws.d_taux = (TileAux *)take(kNoAllocTiles * sizeof(TileAux));
+    ws.d_rbase = (int64_t *)take(8);
+    ws.d_rent = (REntry *)take(kNoAllocRent * sizeof(REntry));
+    double **dbl[8] = {&ws.d_rA, &ws.d_rB, &ws.d_rC, &ws.d_rD,
+                       &ws.d_rcp, &ws.d_rdp, &ws.d_rbp, &ws.d_rM};
+    for (double **d : dbl)
+        *d = (double *)take(kNoAllocRent * 8);
+    ws.d_active = (int32_t *)take(8);
+    ws.d_stats = (Stats *)take(sizeof(Stats));
+    double *d_result = (double *)take(4 * 8);
+    ws.max_ntiles = ntiles;
+
+    Inst in{};
+    in.L = L;
+    in.off = 0;
+    in.tile0 = 0;
+    in.ntiles = ntiles;
+    in.M = L;
+    in.N = 1;
+    in.D = 0;
+    k_noalloc_setup<<<1, 64, 0, s>>>(in, ws.d_inst, ws.d_state, ws.d_tile_inst, ntiles,
+                                     ws.d_rbase, ws.d_active, ws.d_stats);
+    k_to_double<R><<<152, 256, 0, s>>>((const R *)d_h, L, ws.r0);
+    semd_params q = p;
+    q.stop = SEMD_STOP_FIXED;
+    q.fixed_sifts = 1000; // stay in SIFT mode
+    q.max_imfs = 1;
+    ReduceArgs ra = reduce_args(ws, q);
+    launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
+    k_reduce<<<1, 64, reduce_smem(ra), s>>>(ra);
+    launch_pass<R>(ws, ntiles, s); // SIFT
+    k_noalloc_result<<<1, 32, 0, s>>>(ws.d_state, ws.d_taux, ntiles, d_result);
+    SEMD_CU(cudaGetLastError());
+    double res[3];
+    SEMD_CU(cudaMemcpyAsync(res, d_result, sizeof(res), cudaMemcpyDeviceToHost, s));
+    SEMD_CU(cudaStreamSynchronize(s));
+    if ((int)res[2] != MODE_SIFT) {
+        err = "the signal lacks maxima or minima; it cannot be sifted";
+        return SEMD_EINVAL;
+    }
+    // the SIFT pass read h from buffer hpar = 1 and wrote buffer 0
+    SEMD_CU(cudaMemcpyAsync(d_out, ws.h0, (size_t)L * sizeof(R), cudaMemcpyDeviceToDevice, s));
+    *sd_num = res[0];
+    *sd_den = res[1];
+    return SEMD_OK;
+}
+
+} // namespace semd
+
+extern "C" semd_status serial_emd_sift_noalloc(const semd_params *params, const void *d_h,
+                                               int64_t L, void *d_out, double *sd_num,
+                                               double *sd_den, void *stream)
+{
+    std::string &err = semd::g_plan_create_error;
+    err.clear();
+    if (!params || !d_h || !d_out || !sd_num || !sd_den) {
+        err = "null argument";
+        return SEMD_EINVAL;
+    }
+    if (params->precision != SEMD_FP64 && params->precision != SEMD_FP32_MIXED)
+        return err = "precision must be FP64 or FP32_MIXED", SEMD_EINVAL;
+    if (params->boundary != SEMD_BOUNDARY_MIRROR && params->boundary != SEMD_BOUNDARY_ENDPOINTS)
+        return err = "boundary must be MIRROR or ENDPOINTS", SEMD_EINVAL;
+    if (params->boundary == SEMD_BOUNDARY_MIRROR &&
+        (params->mirror_knots < 1 || params->mirror_knots > 2))
+        return err = "mirror_knots must be 1 or 2", SEMD_EINVAL;
+    if (L < 1 || L > semd::kNoAllocMaxL) {
+        err = "L = " + std::to_string(L) + " is outside [1, " +
+              std::to_string(semd::kNoAllocMaxL) + "], the size of the allocation-free scratch";
+        return SEMD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return params->precision == SEMD_FP64
+               ? semd::sift_noalloc_impl<double>(*params, d_h, L, d_out, sd_num, sd_den, s, err)
+               : semd::sift_noalloc_impl<float>(*params, d_h, L, d_out, sd_num, sd_den, s, err);
+}

@@ -114,8 +114,8 @@ __host__ __device__ inline size_t reduce_smem_bytes(int64_t entries)
 }
 
 // Entries of the reduced system of an instance with nt tiles (per envelope).
-__host__ __device__ inline int64_t reduce_entries(int nt) { return 2 * (int64_t)nt + 4; }
+__host__ __device__ constexpr int64_t reduce_entries(int nt) { return 2 * (int64_t)nt + 4; }
 // Scratch length for n entries addressed through sk().
-__host__ __device__ inline int64_t skew_len(int64_t n) { return n + n / 32 + 2; }
+__host__ __device__ constexpr int64_t skew_len(int64_t n) { return n + n / 32 + 2; }
 
 } // namespace semd
