@@ -121,7 +121,7 @@ def _flush_l2(buf):
     buf.add_(1)
 
 
-def run_ours(wl, precision, steps, warmup, device, flush):
+def run_ours(wl, precision, steps, warmup, device, flush, tile=0):
     import torch
     from paper_2106_15319_gb300 import capi
     from paper_2106_15319_gb300.serial_emd import Plan, make_params
@@ -131,6 +131,8 @@ def run_ours(wl, precision, steps, warmup, device, flush):
     p = make_params(rows, cols, precision=precision, transition_len=wl["D"], max_imfs=wl["K"],
                     fixed_sifts=wl["S"], ensemble_trials=wl["trials"])
     plan = Plan(p)
+    if tile:
+        plan.tile = tile
     x = torch.from_numpy(X).to(device)
     noise = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).to(device) if wl["trials"] > 1 \
         else None
@@ -242,6 +244,25 @@ def fp32_imf_errors(wl, run):
             for k in range(wl["K"])]
 
 
+def fp32_imf_errors_given_input(wl, run):
+    """Per-IMF relative L2 of the FP32 result against the oracle's IMF of the same input
+    remainder (x minus the GPU's earlier IMFs, rounded to single precision), untimed."""
+    from oracle import oracle as O
+    x = np.asarray(np.asarray(wl["X"], np.float32), np.float64).reshape(-1)
+    g = run["imfs"].double().cpu().numpy().reshape(wl["K"], -1)
+    floor = 1e-6 * np.linalg.norm(x)
+    r, errs = x.copy(), []
+    for k in range(wl["K"]):
+        if not np.any(g[k]):
+            break
+        oi, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, fixed_sifts=wl["S"])
+        if on < 1:
+            break
+        errs.append(float(np.linalg.norm(g[k] - oi[0]) / max(np.linalg.norm(oi[0]), floor)))
+        r = r - g[k]
+    return errs
+
+
 def cpu_baseline(wl, budget_s: float = 12.0):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -341,14 +362,14 @@ def arm_ours(args):
 
     barrier(world)
     with ClockSampler(local) as clk:
-        r32 = run_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device, flush)
+        r32 = run_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device, flush, args.tile)
     barrier(world)
     ms32 = statistics.mean(r32["ms"])
     ms32_max = max_over_ranks(ms32, world)
     value = world * r32["sample_sifts"] / (ms32_max * 1e-3)
 
     if "fp64" in args.forms:
-        r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush)
+        r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush, args.tile)
         ms64 = max_over_ranks(statistics.mean(r64["ms"]), world)
         v64 = world * r64["sample_sifts"] / (ms64 * 1e-3)
         r64["plan"].close()
@@ -395,8 +416,9 @@ def arm_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0:
-        if wl["trials"] == 1:
+        if wl["trials"] == 1 and wl["D"] == 0:
             line["fp32_imf_rel_l2"] = fp32_imf_errors(wl, r32)
+            line["fp32_imf_rel_l2_given_input"] = fp32_imf_errors_given_input(wl, r32)
         if not args.no_batched:
             line["batched"] = batched_eemd(args, device, flush, peak, peak_kind, world)
         if not args.no_cpu_baseline:
@@ -442,6 +464,7 @@ def main():
     ap.add_argument("--trials", type=int, default=256, help="EEMD realizations (eemd512)")
     ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="pass-kernel tile (0: the plan's)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

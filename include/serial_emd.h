@@ -206,6 +206,18 @@ semd_status serial_emd_sift_noalloc(const semd_params *params, const void *d_h, 
  */
 semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int profile);
 
+/*
+ * Tile of the sifting pass kernel: every pass cuts each serialized signal into tiles of
+ * `tile` samples (512, 1024 or 2048; one thread block each, 8 samples per thread), and
+ * the spline system is partitioned at tile edges. 0 restores the plan's own choice. The
+ * tile changes rounding only (results agree to the precision's tolerance), and the
+ * speed: small tiles spread short signals over more SMs, large ones shrink the
+ * interface system. Takes effect at the next decompose call. Errors: EINVAL.
+ */
+semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile);
+/* The plan's current tile (0 for a NULL plan). */
+int serial_emd_plan_get_tile(semd_plan_t plan);
+
 /* Statistics of the plan's last decompose call; valid once its stream has finished. */
 typedef struct semd_stats {
     int64_t kernel_launches; /* kernels the call ran (inside the graph when used_graph) */

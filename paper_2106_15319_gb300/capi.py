@@ -91,6 +91,8 @@ SIGNATURES = {
                                                ctypes.c_int64, ctypes.c_void_p,
                                                ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "serial_emd_plan_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "serial_emd_plan_get_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "serial_emd_plan_set_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "serial_emd_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_stats)]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
@@ -223,6 +225,14 @@ def serial_emd_sift_noalloc(params: semd_params, h, out, stream=None):
                                         ctypes.byref(a), ctypes.byref(b), _stream(stream))
     _check(rc, None)
     return a.value, b.value
+
+
+def serial_emd_plan_set_tile(plan: int, tile: int) -> None:
+    _check(load().serial_emd_plan_set_tile(plan, tile), plan)
+
+
+def serial_emd_plan_get_tile(plan: int) -> int:
+    return int(load().serial_emd_plan_get_tile(plan))
 
 
 def serial_emd_plan_set_options(plan: int, use_graphs: bool = True, profile: bool = False):

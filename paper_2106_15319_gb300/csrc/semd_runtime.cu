@@ -22,8 +22,7 @@ static thread_local std::string g_plan_create_error;
 // the D transition samples between signal i and i+1 (0-based r),
 // x = (r+1)/(D+1) * X(i+1, D-1-r) + (D-r)/(D+1) * X(i, M-1-r). Written in FP64 to r0.
 template <typename R>
-__global__ void k_serialize(const Inst *inst, const int32_t *tile_inst, double *r0, int tile,
-                            int only_first)
+__global__ void k_serialize(const Inst *inst, const int32_t *tile_inst, int tile, int only_first)
 {
     const int gt = blockIdx.x, ii = tile_inst[gt];
     if (only_first && ii != 0)
@@ -48,14 +47,14 @@ __global__ void k_serialize(const Inst *inst, const int32_t *tile_inst, double *
             const double af = (double)(D - r) / (double)(D + 1);
             v = __dadd_rn(__dmul_rn(xa, a), __dmul_rn(xb, af));
         }
-        r0[in.off + p] = v;
+        in.r[0][p] = v;
     }
 }
 
 // EEMD beta = rel * population std of the serialized x (Sec. 2.2 Step 1), one CTA.
-__global__ void k_std(const Inst *inst, const double *r0, double rel, double *beta)
+__global__ void k_std(const Inst *inst, double rel, double *beta)
 {
-    const double *x = r0 + inst[0].off;
+    const double *x = inst[0].r[0];
     const int64_t L = inst[0].L;
     __shared__ double sh[1024];
     double s = 0.0;
@@ -86,30 +85,30 @@ __global__ void k_std(const Inst *inst, const double *r0, double rel, double *be
 
 // x^(m) = x + beta w^(m) for every trial (Sec. 2.2 Step 1); trial 0 holds x on entry.
 template <typename R>
-__global__ void k_add_noise(const Inst *inst, int trials, const double *beta, double *r0)
+__global__ void k_add_noise(const Inst *inst, int trials, const double *beta)
 {
     const int64_t L = inst[0].L;
     const R *w = (const R *)inst[0].noise;
     const double b = *beta;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const double x = r0[inst[0].off + p];
+        const double x = inst[0].r[0][p];
         for (int m = trials - 1; m >= 0; --m)
-            r0[inst[m].off + p] = __dadd_rn(x, __dmul_rn(b, (double)w[(int64_t)m * L + p]));
+            inst[m].r[0][p] = __dadd_rn(x, __dmul_rn(b, (double)w[(int64_t)m * L + p]));
     }
 }
 
 // Sec. 3.3 for the residue, and zero-fill of the IMF slots past the produced count.
 template <typename R>
 __global__ void k_finalize(const Inst *inst, const State *state, const int32_t *tile_inst,
-                           const double *r0, const double *r1, int tile, int K)
+                           int tile, int K)
 {
     const int gt = blockIdx.x, ii = tile_inst[gt];
     const Inst &in = inst[ii];
     if (in.imf_serialized)
         return;
     const int n = state[ii].imf_count;
-    const double *r = (state[ii].rpar ? r1 : r0) + in.off;
+    const double *r = in.r[state[ii].rpar];
     const int64_t ts = (int64_t)(gt - in.tile0) * tile;
     const int64_t cnt = min((int64_t)tile, in.L - ts);
     R *imf = (R *)in.imf;
@@ -129,7 +128,7 @@ __global__ void k_finalize(const Inst *inst, const State *state, const int32_t *
 // in FP64 and in trial order, then de-serialize (Sec. 3.3).
 template <typename R>
 __global__ void k_eemd_average(const Inst *inst, const State *state, int trials, int K,
-                               const R *scratch, const double *r0, const double *r1, int tile)
+                               const R *scratch, int tile)
 {
     const Inst &in = inst[0];
     R *out = (R *)in.avg_imf;
@@ -147,13 +146,13 @@ __global__ void k_eemd_average(const Inst *inst, const State *state, int trials,
             double acc = 0.0;
             for (int m = 0; m < trials; ++m)
                 if (k < state[m].imf_count)
-                    acc += (double)scratch[((int64_t)m * K + k) * L + p];
+                    acc += (double)scratch[((int64_t)m * K + k) * in.imf_stride + p];
             out[(int64_t)k * outstride + dst] = (R)(acc / (double)trials);
         }
         if (res) {
             double acc = 0.0;
             for (int m = 0; m < trials; ++m)
-                acc += (state[m].rpar ? r1 : r0)[inst[m].off + p];
+                acc += inst[m].r[state[m].rpar][p];
             res[dst] = acc / (double)trials;
         }
     }
@@ -201,12 +200,43 @@ __global__ void k_to_double(const R *h, int64_t L, double *r)
 
 // ------------------------------------------------------------------ plan helpers
 
+// The pass kernel for each supported tile: 512 / 1024 / 2048 samples, 64 / 128 / 256
+// threads, 8 consecutive samples per thread.
+template <typename R, int TILE>
+static cudaError_t pass_attr_one()
+{
+    return cudaFuncSetAttribute(k_pass<R, TILE, TILE / 8>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(PassSmem<R, TILE, TILE / 8>));
+}
+
 template <typename R>
 static cudaError_t set_smem_attr()
 {
-    return cudaFuncSetAttribute(k_pass<R, kTile, kThreads>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(PassSmem<R, kTile, kThreads>));
+    cudaError_t e = pass_attr_one<R, 512>();
+    if (e == cudaSuccess)
+        e = pass_attr_one<R, 1024>();
+    if (e == cudaSuccess)
+        e = pass_attr_one<R, 2048>();
+    return e;
+}
+
+template <typename R, int TILE>
+static void launch_pass_t(const PassArgs &pa, int64_t ntiles, cudaStream_t s)
+{
+    k_pass<R, TILE, TILE / 8>
+        <<<(unsigned)ntiles, TILE / 8, sizeof(PassSmem<R, TILE, TILE / 8>), s>>>(pa);
+}
+
+template <typename R>
+static void launch_pass_tiles(int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
+{
+    if (tile == 512)
+        launch_pass_t<R, 512>(pa, ntiles, s);
+    else if (tile == 2048)
+        launch_pass_t<R, 2048>(pa, ntiles, s);
+    else
+        launch_pass_t<R, 1024>(pa, ntiles, s);
 }
 
 int64_t serial_length(int64_t M, int64_t N, int64_t D) { return M * N + D * N - D; }
@@ -259,6 +289,9 @@ bool validate(const semd_params &p, std::string &err)
     return true;
 }
 
+// Tile of the pass kernel for a plan: 1024 samples (128 threads).
+int choose_tile(const semd_params &, int64_t, int) { return kTile; }
+
 int max_iterations(const semd_params &p)
 {
     return p.stop == SEMD_STOP_FIXED ? 1 + p.max_imfs * p.fixed_sifts
@@ -299,16 +332,8 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {(void **)&d_tex, (size_t)tiles * 2 * sizeof(TileExport)},
         {(void **)&d_tsol, (size_t)tiles * 2 * sizeof(TileSolve)},
         {(void **)&d_taux, (size_t)tiles * sizeof(TileAux)},
-        {(void **)&d_rbase, (size_t)insts * 8},
         {(void **)&d_rent, (size_t)rentries * sizeof(REntry)},
-        {(void **)&d_rA, (size_t)rentries * 8},
-        {(void **)&d_rB, (size_t)rentries * 8},
-        {(void **)&d_rC, (size_t)rentries * 8},
-        {(void **)&d_rD, (size_t)rentries * 8},
-        {(void **)&d_rcp, (size_t)rentries * 8},
-        {(void **)&d_rdp, (size_t)rentries * 8},
-        {(void **)&d_rbp, (size_t)rentries * 8},
-        {(void **)&d_rM, (size_t)rentries * 8},
+        {(void **)&d_rscr, (size_t)rentries * 8 * 8},
         {(void **)&d_active, (size_t)iters * 4},
         {(void **)&d_beta, 8},
         {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
@@ -339,8 +364,6 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
     e = cudaMallocHost((void **)&h_inst, (size_t)insts * sizeof(Inst));
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&h_tile_inst, (size_t)tiles * 4);
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&h_rbase, (size_t)insts * 8);
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&h_state, (size_t)insts * sizeof(State));
     if (e == cudaSuccess)
@@ -379,8 +402,6 @@ void Workspace::release()
         cudaFreeHost(h_inst);
     if (h_tile_inst)
         cudaFreeHost(h_tile_inst);
-    if (h_rbase)
-        cudaFreeHost(h_rbase);
     if (h_state)
         cudaFreeHost(h_state);
     if (h_misc)
@@ -390,22 +411,37 @@ void Workspace::release()
     *this = Workspace();
 }
 
-// Lays out n instances (host descriptors in ws.h_inst must have L, geometry and
-// output pointers set); fills offsets, tiles and scratch bases; uploads.
+// Points instance i at its own slices of the workspace buffers (samples from `off`,
+// tiles from `tiles`, interface scratch from `rent`).
+static void bind_instance(Workspace &ws, Inst &in, int64_t off, int64_t tiles, int64_t rent)
+{
+    in.tile0 = (int32_t)tiles;
+    in.ntiles = (int32_t)((in.L + ws.tile - 1) / ws.tile);
+    in.h[0] = (char *)ws.h0 + off * (int64_t)ws.elem_size;
+    in.h[1] = (char *)ws.h1 + off * (int64_t)ws.elem_size;
+    in.r[0] = ws.r0 + off;
+    in.r[1] = ws.r1 + off;
+    in.tex = ws.d_tex + 2 * tiles;
+    in.tsol = ws.d_tsol + 2 * tiles;
+    in.taux = ws.d_taux + tiles;
+    in.rlen = reduce_len(in.ntiles);
+    in.rent = ws.d_rent + rent;
+    in.rscr = ws.d_rscr + 8 * rent;
+}
+
+// Lays out n instances (host descriptors in ws.h_inst must have L, geometry and output
+// pointers set): buffer slices, tiles, then the upload of descriptors and tile map.
 semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::string &err)
 {
     int64_t off = 0, tiles = 0, rent = 0;
     max_ntiles = 0;
     for (int i = 0; i < n; ++i) {
         Inst &in = h_inst[i];
-        in.off = off;
-        in.tile0 = (int32_t)tiles;
-        in.ntiles = (int32_t)((in.L + kTile - 1) / kTile);
-        h_rbase[i] = rent;
+        bind_instance(*this, in, off, tiles, rent);
         off += (in.L + 31) & ~(int64_t)31;
         tiles += in.ntiles;
+        rent += 2 * in.rlen;
         max_ntiles = std::max<int64_t>(max_ntiles, in.ntiles);
-        rent += 2 * skew_len(reduce_entries(in.ntiles));
     }
     if (off > cap_samples || tiles > cap_tiles || rent > cap_rentries || n > cap_inst) {
         err = "batch exceeds the plan's capacity";
@@ -418,7 +454,6 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
     SEMD_CU(cudaMemcpyAsync(d_inst, h_inst, (size_t)n * sizeof(Inst), cudaMemcpyHostToDevice, s));
     SEMD_CU(cudaMemcpyAsync(d_tile_inst, h_tile_inst, (size_t)tiles * 4, cudaMemcpyHostToDevice,
                             s));
-    SEMD_CU(cudaMemcpyAsync(d_rbase, h_rbase, (size_t)n * 8, cudaMemcpyHostToDevice, s));
     SEMD_CU(cudaEventRecord(staging_done, s));
     return SEMD_OK;
 }
@@ -430,16 +465,8 @@ static void launch_pass(Workspace &ws, int64_t ntiles, cudaStream_t s)
     pa.inst = ws.d_inst;
     pa.state = ws.d_state;
     pa.tile_inst = ws.d_tile_inst;
-    pa.h0 = ws.h0;
-    pa.h1 = ws.h1;
-    pa.r0 = ws.r0;
-    pa.r1 = ws.r1;
-    pa.tex = ws.d_tex;
-    pa.tsol = ws.d_tsol;
-    pa.taux = ws.d_taux;
     pa.stats = ws.d_stats;
-    k_pass<R, kTile, kThreads>
-        <<<(unsigned)ntiles, kThreads, sizeof(PassSmem<R, kTile, kThreads>), s>>>(pa);
+    launch_pass_tiles<R>(ws.tile, pa, ntiles, s);
 }
 
 static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
@@ -447,19 +474,7 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ReduceArgs ra;
     ra.inst = ws.d_inst;
     ra.state = ws.d_state;
-    ra.tex = ws.d_tex;
-    ra.tsol = ws.d_tsol;
-    ra.taux = ws.d_taux;
-    ra.rbase = ws.d_rbase;
-    ra.rent = ws.d_rent;
-    ra.rA = ws.d_rA;
-    ra.rB = ws.d_rB;
-    ra.rC = ws.d_rC;
-    ra.rD = ws.d_rD;
-    ra.rcp = ws.d_rcp;
-    ra.rdp = ws.d_rdp;
-    ra.rbp = ws.d_rbp;
-    ra.rM = ws.d_rM;
+    ra.inst_list = nullptr;
     ra.active = ws.d_active;
     ra.K = p.max_imfs;
     ra.stop = p.stop;
@@ -468,7 +483,9 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.sd_threshold = p.sd_threshold;
     ra.boundary = p.boundary;
     ra.mirror_knots = p.mirror_knots;
-    const int64_t entries = skew_len(reduce_entries((int)ws.max_ntiles));
+    ra.single = ws.elem_size == 4 ? 1 : 0;
+    ra.pad = 0;
+    const int64_t entries = reduce_len(ws.max_ntiles);
     ra.smem_entries = reduce_smem_bytes(entries) <= kReduceSmemMax ? entries : 0;
     return ra;
 }
@@ -513,12 +530,12 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
     SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)ninst * sizeof(State), s));
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
     SEMD_CU(cudaMemsetAsync(ws.d_stats, 0, sizeof(Stats), s));
-    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_tile_inst, ws.r0, kTile,
+    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_tile_inst, ws.tile,
                                                       eemd ? 1 : 0);
     ++launches;
     if (eemd) {
-        k_std<<<1, 1024, 0, s>>>(ws.d_inst, ws.r0, p.noise_rel_std, ws.d_beta);
-        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, ws.d_beta, ws.r0);
+        k_std<<<1, 1024, 0, s>>>(ws.d_inst, p.noise_rel_std, ws.d_beta);
+        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, ws.d_beta);
         launches += 2;
     }
     ReduceArgs ra = reduce_args(ws, p);
@@ -542,11 +559,10 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
     }
     if (eemd) {
         k_eemd_average<R><<<ntiles0, 256, 0, s>>>(ws.d_inst, ws.d_state, ninst, p.max_imfs,
-                                                  (const R *)ws.eemd_scratch, ws.r0, ws.r1,
-                                                  kTile);
+                                                  (const R *)ws.eemd_scratch, ws.tile);
     } else {
         k_finalize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
-                                                         ws.r0, ws.r1, kTile, p.max_imfs);
+                                                         ws.tile, p.max_imfs);
     }
     ++launches;
     SEMD_CU(cudaGetLastError());
@@ -577,8 +593,9 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
         in.order = p.order;
         in.x = q.d_x;
         if (eemd) {
-            in.imf = (char *)ws.eemd_scratch + (size_t)i * p.max_imfs * in.L * sizeof(R);
-            in.imf_stride = in.L;
+            const int64_t slot = (in.L + 31) & ~(int64_t)31; // keeps every slot 128-byte aligned
+            in.imf = (char *)ws.eemd_scratch + (size_t)i * p.max_imfs * slot * sizeof(R);
+            in.imf_stride = slot;
             in.imf_serialized = 1;
             in.res = nullptr;
             if (i == 0) {
@@ -602,7 +619,7 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles};
+        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile};
         if (!pl.graph_exec || !(pl.graph_key == key)) {
             if (pl.graph_exec) {
                 cudaGraphExecDestroy(pl.graph_exec);
@@ -657,13 +674,13 @@ semd_status extrema_impl(semd_plan_s &pl, const void *d_h, int64_t L, int32_t *t
 {
     Workspace &ws = pl.ws;
     std::string &err = pl.err;
-    const int ntiles = (int)((L + kTile - 1) / kTile);
+    const int ntiles = (int)((L + ws.tile - 1) / ws.tile);
     if (L < 1 || ntiles > ws.cap_tiles) {
         err = "L out of range for this plan";
         return SEMD_EINVAL;
     }
     int32_t *d_cnt = ws.d_misc;
-    k_extrema_tiles<R><<<ntiles, 32, 0, s>>>((const R *)d_h, L, kTile, nullptr, d_cnt, nullptr,
+    k_extrema_tiles<R><<<ntiles, 32, 0, s>>>((const R *)d_h, L, ws.tile, nullptr, d_cnt, nullptr,
                                              nullptr);
     SEMD_CU(cudaMemcpyAsync(ws.h_misc, d_cnt, (size_t)ntiles * 8, cudaMemcpyDeviceToHost, s));
     SEMD_CU(cudaStreamSynchronize(s));
@@ -677,7 +694,8 @@ semd_status extrema_impl(semd_plan_s &pl, const void *d_h, int64_t L, int32_t *t
         b += cb;
     }
     SEMD_CU(cudaMemcpyAsync(d_cnt, ws.h_misc, (size_t)ntiles * 8, cudaMemcpyHostToDevice, s));
-    k_extrema_tiles<R><<<ntiles, 32, 0, s>>>((const R *)d_h, L, kTile, d_cnt, nullptr, tmax, tmin);
+    k_extrema_tiles<R><<<ntiles, 32, 0, s>>>((const R *)d_h, L, ws.tile, d_cnt, nullptr, tmax,
+                                             tmin);
     SEMD_CU(cudaGetLastError());
     SEMD_CU(cudaStreamSynchronize(s));
     *nmax = a;
@@ -819,12 +837,15 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     }
     const int64_t L = serial_length(M, N, D);
     const int ninst = eemd ? params->ensemble_trials : max_batch;
-    const int64_t tiles_per = (L + kTile - 1) / kTile;
+    const int tile = choose_tile(*params, L, ninst);
+    // capacity for the smallest tile, so that the tile can be changed per plan
+    const int64_t tiles_per = (L + kMinTile - 1) / kMinTile;
     const int64_t samples = (int64_t)ninst * ((L + 31) & ~(int64_t)31);
     const int64_t tiles = (int64_t)ninst * tiles_per;
-    const int64_t rent = (int64_t)ninst * 2 * skew_len(reduce_entries((int)tiles_per));
+    const int64_t rent = (int64_t)ninst * 2 * reduce_len(tiles_per);
     const size_t elem = params->precision == SEMD_FP64 ? 8 : 4;
-    const int64_t eemd_elems = eemd ? (int64_t)ninst * params->max_imfs * L : 0;
+    const int64_t eemd_elems =
+        eemd ? (int64_t)ninst * params->max_imfs * ((L + 31) & ~(int64_t)31) : 0;
     semd_plan_s *pl = new (std::nothrow) semd_plan_s();
     if (!pl) {
         err = "out of host memory";
@@ -832,6 +853,7 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     }
     pl->p = *params;
     pl->L = L;
+    pl->ws.tile = tile;
     semd_status st = pl->ws.allocate(samples, ninst, tiles, rent, max_iterations(*params), elem,
                                       eemd_elems, mem_budget, err);
     if (st == SEMD_OK) {
@@ -950,6 +972,22 @@ void serial_emd_destroy(semd_plan_t plan)
     delete plan;
 }
 
+semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (tile == 0)
+        tile = choose_tile(plan->p, plan->L, plan->ws.cap_inst);
+    if (tile != 512 && tile != 1024 && tile != 2048) {
+        plan->err = "tile must be 0, 512, 1024 or 2048";
+        return SEMD_EINVAL;
+    }
+    plan->ws.tile = tile;
+    return SEMD_OK;
+}
+
+int serial_emd_plan_get_tile(semd_plan_t plan) { return plan ? plan->ws.tile : 0; }
+
 semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int profile)
 {
     if (!plan)
@@ -1005,8 +1043,7 @@ constexpr size_t kNoAllocBytes =
     na_round(sizeof(Inst)) + na_round(sizeof(State)) + na_round(kNoAllocTiles * 4) +
     na_round(kNoAllocTiles * 2 * sizeof(TileExport)) +
     na_round(kNoAllocTiles * 2 * sizeof(TileSolve)) + na_round(kNoAllocTiles * sizeof(TileAux)) +
-    na_round(8) +                                           // reduce scratch base
-    na_round(kNoAllocRent * sizeof(REntry)) + 8 * na_round(kNoAllocRent * 8) +
+    na_round(kNoAllocRent * sizeof(REntry)) + na_round(kNoAllocRent * 8 * 8) +
     na_round(8) + na_round(sizeof(Stats)) + na_round(4 * 8); // active flags, stats, result
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1057,14 +1094,13 @@ static semd_status noalloc_setup(void *&base, std::string &err)
 // Clears the per-call state and writes the instance descriptor (passed by value, so
 // no host staging buffer is needed).
 __global__ void k_noalloc_setup(Inst in, Inst *d_inst, State *d_state, int32_t *tile_inst,
-                                int ntiles, int64_t *rbase, int32_t *active, Stats *stats)
+                                int ntiles, int32_t *active, Stats *stats)
 {
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
         tile_inst[t] = 0;
     if (threadIdx.x == 0) {
         *d_inst = in;
         *d_state = State{};
-        rbase[0] = 0;
         active[0] = 0;
         active[1] = 0;
         *stats = Stats{};
@@ -1113,27 +1149,23 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     ws.d_tex = (TileExport *)take(kNoAllocTiles * 2 * sizeof(TileExport));
     ws.d_tsol = (TileSolve *)take(kNoAllocTiles * 2 * sizeof(TileSolve));
     ws.d_taux = (TileAux *)take(kNoAllocTiles * sizeof(TileAux));
-    ws.d_rbase = (int64_t *)take(8);
     ws.d_rent = (REntry *)take(kNoAllocRent * sizeof(REntry));
-    double **dbl[8] = {&ws.d_rA, &ws.d_rB, &ws.d_rC, &ws.d_rD,
-                       &ws.d_rcp, &ws.d_rdp, &ws.d_rbp, &ws.d_rM};
-    for (double **d : dbl)
-        *d = (double *)take(kNoAllocRent * 8);
+    ws.d_rscr = (double *)take(kNoAllocRent * 8 * 8);
     ws.d_active = (int32_t *)take(8);
     ws.d_stats = (Stats *)take(sizeof(Stats));
     double *d_result = (double *)take(4 * 8);
     ws.max_ntiles = ntiles;
+    ws.tile = kTile;
+    ws.elem_size = sizeof(R);
 
     Inst in{};
     in.L = L;
-    in.off = 0;
-    in.tile0 = 0;
-    in.ntiles = ntiles;
     in.M = L;
     in.N = 1;
     in.D = 0;
+    bind_instance(ws, in, 0, 0, 0);
     k_noalloc_setup<<<1, 64, 0, s>>>(in, ws.d_inst, ws.d_state, ws.d_tile_inst, ntiles,
-                                     ws.d_rbase, ws.d_active, ws.d_stats);
+                                     ws.d_active, ws.d_stats);
     k_to_double<R><<<152, 256, 0, s>>>((const R *)d_h, L, ws.r0);
     semd_params q = p;
     q.stop = SEMD_STOP_FIXED;

@@ -9,16 +9,18 @@
 
 namespace semd {
 
-// One tile of TILE samples per CTA, TILE / kThreads consecutive samples per thread.
+// One tile of TILE samples per CTA and 8 consecutive samples per thread. Supported
+// tiles: 512, 1024, 2048 (64, 128, 256 threads); the plan picks one.
 constexpr int kTile = 1024;
-constexpr int kThreads = 128;
+constexpr int kMinTile = 512;
 // Largest shared-memory scratch of the interface solve; larger instances use global memory.
 constexpr size_t kReduceSmemMax = 200 * 1024;
 
-// Device workspace of a plan (or of a server slot pool): one allocation carved up.
+// Device workspace of a plan: one allocation carved up, plus pinned host staging.
 struct Workspace {
     void *base = nullptr;
     size_t bytes = 0;
+    int tile = kTile;
     int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0, max_ntiles = 0;
     int cap_inst = 0, cap_iters = 0;
     size_t elem_size = 0;
@@ -30,10 +32,8 @@ struct Workspace {
     TileExport *d_tex = nullptr;
     TileSolve *d_tsol = nullptr;
     TileAux *d_taux = nullptr;
-    int64_t *d_rbase = nullptr;
-    REntry *d_rent = nullptr;
-    double *d_rA = nullptr, *d_rB = nullptr, *d_rC = nullptr, *d_rD = nullptr;
-    double *d_rcp = nullptr, *d_rdp = nullptr, *d_rbp = nullptr, *d_rM = nullptr;
+    REntry *d_rent = nullptr; // interface-solve scratch: 2 x rlen entries per instance
+    double *d_rscr = nullptr; //   and 16 x rlen doubles per instance
     int32_t *d_active = nullptr;
     double *d_beta = nullptr;
     int32_t *d_misc = nullptr;
@@ -42,7 +42,6 @@ struct Workspace {
     // pinned host staging
     Inst *h_inst = nullptr;
     int32_t *h_tile_inst = nullptr;
-    int64_t *h_rbase = nullptr;
     State *h_state = nullptr;
     void *h_misc = nullptr;
     Stats *h_stats = nullptr;
@@ -54,11 +53,15 @@ struct Workspace {
     void release();
 };
 
+// Per-instance scratch length of the interface solve (entries per envelope).
+inline int64_t reduce_len(int64_t ntiles) { return skew_len(reduce_entries((int)ntiles)); }
+
 int64_t serial_length(int64_t M, int64_t N, int64_t D);
 bool geometry(const semd_params &p, int64_t rows, int64_t cols, int order, int64_t &M,
               int64_t &N, int64_t &D, std::string &err);
 bool validate(const semd_params &p, std::string &err);
 int max_iterations(const semd_params &p);
+int choose_tile(const semd_params &p, int64_t L, int ninst);
 
 // Optional per-launch timing of the pass and reduce kernels (CUDA events on the
 // launching stream), used by the benchmark's roofline figures.
@@ -117,10 +120,11 @@ struct GraphKey {
     int64_t ntiles = 0;
     int ntiles0 = 0;
     int64_t max_ntiles = 0;
+    int tile = 0;
     bool operator==(const GraphKey &o) const
     {
         return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0 &&
-               max_ntiles == o.max_ntiles;
+               max_ntiles == o.max_ntiles && tile == o.tile;
     }
 };
 

@@ -77,6 +77,14 @@ class Plan:
         n = capi.serial_emd_decompose_batch(self.handle, items, stream, wait)
         return outs, n
 
+    @property
+    def tile(self) -> int:
+        return capi.serial_emd_plan_get_tile(self.handle)
+
+    @tile.setter
+    def tile(self, value: int):
+        capi.serial_emd_plan_set_tile(self.handle, value)
+
     def set_options(self, use_graphs: bool = True, profile: bool = False):
         capi.serial_emd_plan_set_options(self.handle, use_graphs, profile)
 
