@@ -317,3 +317,27 @@ def test_eemd_small(prec):
     _check_imfs(imfs.double().cpu().numpy().reshape(8, -1), res.cpu().numpy().reshape(-1), n,
                 oi, orr, on, x, prec, "eemd")
     plan.close()
+
+
+# ------------------------------------------------------------------- tile independence
+
+@pytest.mark.parametrize("D", [0, -1])
+def test_tile_sizes_agree_fp64(D):
+    """The spline system is partitioned at tile edges exactly, so every tile size gives
+    the oracle's decomposition (ragged last tile included: 300 x 301 samples)."""
+    X = np.ascontiguousarray(synth.grating_image(301, 17)[:300, :])
+    o = _oracle(X, capi.FP64, transition_len=D, max_imfs=8)
+    res = {}
+    for tile in (512, 1024, 2048):
+        p = make_params(*X.shape, precision=capi.FP64, transition_len=D, max_imfs=8)
+        plan = Plan(p)
+        plan.tile = tile
+        assert plan.tile == tile
+        imfs, r, n = plan.decompose(torch.from_numpy(np.ascontiguousarray(X)).cuda())
+        torch.cuda.synchronize()
+        res[tile] = imfs.cpu().numpy()
+        _check_imfs(res[tile], r.cpu().numpy(), n, o[0], o[1], o[2], o[4], capi.FP64,
+                    f"tile {tile}")
+        plan.close()
+    for tile in (512, 2048):
+        assert np.abs(res[tile] - res[1024]).max() <= 1e-12 * np.abs(X).max()
