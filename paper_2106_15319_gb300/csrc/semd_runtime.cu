@@ -21,11 +21,13 @@ static thread_local std::string g_plan_create_error;
 // Sec. 3.2 serialization, one CTA per tile: x[i(M+D)+m] = X(i, m) for m < M and, for
 // the D transition samples between signal i and i+1 (0-based r),
 // x = (r+1)/(D+1) * X(i+1, D-1-r) + (D-r)/(D+1) * X(i, M-1-r). Written in FP64 to r0.
+// Only instances that have not started (state MODE_INIT) are serialized.
 template <typename R>
-__global__ void k_serialize(const Inst *inst, const int32_t *tile_inst, int tile, int only_first)
+__global__ void k_serialize(const Inst *inst, const State *state, const int32_t *tile_inst,
+                            int tile, int only_first)
 {
     const int gt = blockIdx.x, ii = tile_inst[gt];
-    if (only_first && ii != 0)
+    if ((only_first && ii != 0) || state[ii].mode != MODE_INIT)
         return;
     const Inst &in = inst[ii];
     const int64_t ts = (int64_t)(gt - in.tile0) * tile;
@@ -98,14 +100,15 @@ __global__ void k_add_noise(const Inst *inst, int trials, const double *beta)
     }
 }
 
-// Sec. 3.3 for the residue, and zero-fill of the IMF slots past the produced count.
+// Sec. 3.3 for the residue, and zero-fill of the IMF slots past the produced count, for
+// instances whose decomposition has ended (state MODE_DONE).
 template <typename R>
 __global__ void k_finalize(const Inst *inst, const State *state, const int32_t *tile_inst,
                            int tile, int K)
 {
     const int gt = blockIdx.x, ii = tile_inst[gt];
     const Inst &in = inst[ii];
-    if (in.imf_serialized)
+    if (in.imf_serialized || state[ii].mode != MODE_DONE)
         return;
     const int n = state[ii].imf_count;
     const double *r = in.r[state[ii].rpar];
@@ -530,8 +533,8 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
     SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)ninst * sizeof(State), s));
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
     SEMD_CU(cudaMemsetAsync(ws.d_stats, 0, sizeof(Stats), s));
-    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_tile_inst, ws.tile,
-                                                      eemd ? 1 : 0);
+    k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
+                                                      ws.tile, eemd ? 1 : 0);
     ++launches;
     if (eemd) {
         k_std<<<1, 1024, 0, s>>>(ws.d_inst, p.noise_rel_std, ws.d_beta);
@@ -756,6 +759,72 @@ semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, 
     *sd_num = a;
     *sd_den = b;
     return SEMD_OK;
+}
+
+// ------------------------------------------------- launch helpers for other translation units
+
+cudaError_t setup_kernel_attrs(size_t elem)
+{
+    cudaError_t e = elem == 8 ? set_smem_attr<double>() : set_smem_attr<float>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kReduceSmemMax);
+    return e;
+}
+
+void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
+{
+    if (elem == 8)
+        launch_pass_tiles<double>(tile, pa, ntiles, s);
+    else
+        launch_pass_tiles<float>(tile, pa, ntiles, s);
+}
+
+void launch_reduce_any(const ReduceArgs &ra, int nblocks, cudaStream_t s)
+{
+    k_reduce<<<nblocks, 64, reduce_smem(ra), s>>>(ra);
+}
+
+void launch_serialize_any(size_t elem, const Inst *d_inst, const State *d_state,
+                          const int32_t *tile_inst, int64_t ntiles, int tile, cudaStream_t s)
+{
+    if (elem == 8)
+        k_serialize<double><<<(unsigned)ntiles, 256, 0, s>>>(d_inst, d_state, tile_inst, tile, 0);
+    else
+        k_serialize<float><<<(unsigned)ntiles, 256, 0, s>>>(d_inst, d_state, tile_inst, tile, 0);
+}
+
+void launch_finalize_any(size_t elem, const Inst *d_inst, const State *d_state,
+                         const int32_t *tile_inst, int64_t ntiles, int tile, int K,
+                         cudaStream_t s)
+{
+    if (elem == 8)
+        k_finalize<double><<<(unsigned)ntiles, 256, 0, s>>>(d_inst, d_state, tile_inst, tile, K);
+    else
+        k_finalize<float><<<(unsigned)ntiles, 256, 0, s>>>(d_inst, d_state, tile_inst, tile, K);
+}
+
+ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_state,
+                            const int32_t *inst_list, int32_t *active, size_t elem,
+                            int64_t max_ntiles)
+{
+    ReduceArgs ra;
+    ra.inst = d_inst;
+    ra.state = d_state;
+    ra.inst_list = inst_list;
+    ra.active = active;
+    ra.K = p.max_imfs;
+    ra.stop = p.stop;
+    ra.fixed_sifts = p.fixed_sifts;
+    ra.max_sifts = p.max_sifts;
+    ra.sd_threshold = p.sd_threshold;
+    ra.boundary = p.boundary;
+    ra.mirror_knots = p.mirror_knots;
+    ra.single = elem == 4 ? 1 : 0;
+    ra.pad = 0;
+    const int64_t entries = reduce_len(max_ntiles);
+    ra.smem_entries = reduce_smem_bytes(entries) <= kReduceSmemMax ? entries : 0;
+    return ra;
 }
 
 template semd_status decompose_impl<float>(semd_plan_s &, int, const semd_instance *,

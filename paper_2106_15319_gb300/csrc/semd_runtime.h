@@ -61,6 +61,20 @@ bool geometry(const semd_params &p, int64_t rows, int64_t cols, int order, int64
               int64_t &N, int64_t &D, std::string &err);
 bool validate(const semd_params &p, std::string &err);
 int max_iterations(const semd_params &p);
+
+// Kernel launches for other translation units (the kernels are instantiated once, in the
+// runtime's). elem is the working precision's size: 4 (FP32-mixed) or 8 (FP64).
+cudaError_t setup_kernel_attrs(size_t elem);
+void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s);
+void launch_reduce_any(const ReduceArgs &ra, int nblocks, cudaStream_t s);
+void launch_serialize_any(size_t elem, const Inst *d_inst, const State *d_state,
+                          const int32_t *tile_inst, int64_t ntiles, int tile, cudaStream_t s);
+void launch_finalize_any(size_t elem, const Inst *d_inst, const State *d_state,
+                         const int32_t *tile_inst, int64_t ntiles, int tile, int K,
+                         cudaStream_t s);
+ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_state,
+                            const int32_t *inst_list, int32_t *active, size_t elem,
+                            int64_t max_ntiles);
 int choose_tile(const semd_params &p, int64_t L, int ninst);
 
 // Optional per-launch timing of the pass and reduce kernels (CUDA events on the

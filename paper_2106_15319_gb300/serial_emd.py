@@ -117,3 +117,41 @@ def decompose(x: torch.Tensor, noise: torch.Tensor | None = None, **kw):
         return plan.decompose(x.contiguous(), noise)
     finally:
         plan.close()
+
+
+class Server:
+    """Continuous-batching server (serial_emd_server_*): requests of different shapes are
+    admitted as slots and the memory budget allow, and sifted together."""
+
+    def __init__(self, params: capi.semd_params, mem_budget: int, max_inflight: int):
+        self.params = params
+        self.handle = capi.serial_emd_server_create(params, mem_budget, max_inflight)
+        self.dtype = _DTYPE[params.precision]
+
+    def outputs(self, rows: int, cols: int, device="cuda"):
+        imfs = torch.empty((self.params.max_imfs, rows, cols), dtype=self.dtype, device=device)
+        res = torch.empty((rows, cols), dtype=torch.float64, device=device)
+        return imfs, res
+
+    def submit(self, x: torch.Tensor, imfs=None, residue=None, order: int = capi.ORDER_ROWS):
+        """Queues x (rows, cols); returns (ticket, imfs, residue). The tensors must stay
+        alive until poll() returns the ticket's result."""
+        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous()
+        if imfs is None:
+            imfs, residue = self.outputs(*x.shape, device=x.device)
+        t = capi.serial_emd_submit(self.handle, x, imfs, residue, order)
+        return t, imfs, residue
+
+    def poll(self, ticket: int):
+        return capi.serial_emd_poll(self.handle, ticket)
+
+    def close(self):
+        if self.handle:
+            capi.serial_emd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

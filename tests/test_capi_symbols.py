@@ -60,3 +60,16 @@ def test_invalid_params_rejected_before_device_use():
     with pytest.raises(capi.SemdError) as ei:
         capi.serial_emd_plan(p, 1, 0)
     assert ei.value.status == capi.SEMD_EINVAL
+
+
+def test_server_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = capi.serial_emd_default_params(rows=4, cols=64)
+    with pytest.raises(capi.SemdError) as ei:
+        capi.serial_emd_server_create(p, 1 << 20, 2)
+    assert ei.value.status == capi.SEMD_ECUDA
+    with pytest.raises(capi.SemdError) as ei:
+        capi.serial_emd_server_create(p, 0, 2)
+    assert ei.value.status == capi.SEMD_EINVAL

@@ -1,0 +1,131 @@
+"""Continuous-batching server (serial_emd_server_create / _submit / _poll).
+
+Requests of different shapes are admitted as slots and the memory budget allow, while
+others are mid-decomposition; each result must be bit-identical to decomposing the same
+input alone with a plan (FP64 and FP32), and FP64 results must match the oracle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2106_15319_gb300 import capi, synth  # noqa: E402
+from paper_2106_15319_gb300.serial_emd import Plan, Server, make_params  # noqa: E402
+
+NP = {capi.FP64: np.float64, capi.FP32_MIXED: np.float32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    capi.load()
+
+
+def _mix(seed):
+    """Series and images of different shapes; one column-ordered."""
+    g = synth.rng(seed)
+    items = []
+    for k in range(5):
+        ch, n = int(g.integers(2, 6)), int(g.integers(700, 3000))
+        items.append((synth.tone_chirp_series(ch, n, seed + k), capi.ORDER_ROWS))
+    for k in range(4):
+        side = int(g.integers(32, 90))
+        items.append((synth.grating_image(side, seed + 10 + k), capi.ORDER_ROWS))
+    items.append((np.ascontiguousarray(synth.tone_chirp_series(3, 900, seed + 20).T),
+                  capi.ORDER_COLS))
+    return items
+
+
+def _wait(server, tickets, timeout=120.0):
+    out, t0 = {}, time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = server.poll(t)
+                if r is not None:
+                    out[t] = r
+        assert time.time() - t0 < timeout, "server did not finish in time"
+        time.sleep(0.002)
+    return out
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_server_results_equal_alone(prec):
+    items = _mix(31)
+    K = 8
+    base = make_params(64, 4096, precision=prec, transition_len=-1, max_imfs=K)
+    # a small budget and 3 slots: requests must queue and join while others run
+    server = Server(base, 24 << 20, 3)
+    xs = [torch.from_numpy(np.asarray(X, NP[prec])).cuda() for X, _ in items]
+    subs = []
+    for i, ((X, order), x) in enumerate(zip(items, xs)):
+        subs.append((server.submit(x, order=order), order))
+        if i == 4:
+            time.sleep(0.01)  # the second half arrives while the first is on the GPU
+    res = _wait(server, [s[0][0] for s in subs])
+    server.close()
+    for (X, order), x, ((t, imfs, r), _) in zip(items, xs, subs):
+        out = res[t]
+        assert out.status == capi.SEMD_OK
+        p = make_params(*X.shape, precision=prec, transition_len=-1, max_imfs=K, order=order)
+        plan = Plan(p)
+        ai, ar, an = plan.decompose(x)
+        torch.cuda.synchronize()
+        plan.close()
+        assert out.n_imfs == an
+        assert torch.equal(imfs, ai) and torch.equal(r, ar), (X.shape, order)
+        assert out.queue_ms >= 0.0 and out.run_ms > 0.0 and out.sifts >= 10 * an
+    # FP64 against the oracle, for two of the requests
+    if prec == capi.FP64:
+        for j in (0, 6):
+            X, order = items[j]
+            Xs = X if order == capi.ORDER_ROWS else X.T
+            D = round(0.2 * Xs.shape[1]) if Xs.shape[0] > 1 else 0
+            oi, orr, on, _ = O.serial_emd(np.asarray(Xs, np.float64), D, K)
+            g = subs[j][0][1].cpu().numpy()
+            assert res[subs[j][0][0]].n_imfs == on
+            for k in range(K):
+                den = max(np.linalg.norm(oi[k]), 1e-6 * np.linalg.norm(Xs))
+                assert np.linalg.norm(g[k] - oi[k]) / den <= 1e-10
+
+
+def test_server_rejects_and_reports():
+    base = make_params(16, 1024, precision=capi.FP32_MIXED, max_imfs=4)
+    server = Server(base, 8 << 20, 2)
+    too_long = torch.zeros((32, 1024), dtype=torch.float32, device="cuda")
+    with pytest.raises(capi.SemdError) as ei:
+        server.submit(too_long)
+    assert ei.value.status == capi.SEMD_EBUDGET
+    with pytest.raises(capi.SemdError) as ei:
+        server.submit(torch.zeros((4, 64), dtype=torch.float32, device="cuda"), order=7)
+    assert ei.value.status == capi.SEMD_EINVAL
+    with pytest.raises(capi.SemdError) as ei:
+        server.poll(123456)
+    assert ei.value.status == capi.SEMD_EINVAL
+    x = torch.from_numpy(synth.tone_chirp_series(2, 500, 3).astype(np.float32)).cuda()
+    t, imfs, r = server.submit(x)
+    out = _wait(server, [t])[t]
+    assert out.status == capi.SEMD_OK and out.n_imfs >= 1
+    with pytest.raises(capi.SemdError):
+        server.poll(t)  # a result is returned once
+    server.close()
+
+
+def test_server_destroy_while_busy_leaves_gpu_usable():
+    base = make_params(8, 4096, precision=capi.FP32_MIXED, max_imfs=6)
+    server = Server(base, 16 << 20, 2)
+    xs = [torch.from_numpy(synth.tone_chirp_series(4, 3000, s).astype(np.float32)).cuda()
+          for s in range(8)]
+    keep = [server.submit(x) for x in xs]
+    server.close()  # cancels what is queued or running
+    del keep
+    X = synth.workload_series_3x1024().astype(np.float32)
+    plan = Plan(make_params(3, 1024, precision=capi.FP32_MIXED, transition_len=0, max_imfs=8))
+    _, _, n = plan.decompose(torch.from_numpy(X).cuda())
+    plan.close()
+    assert n >= 3
