@@ -5,21 +5,25 @@
 // signal (Sec. 2.1 Steps 1-5: extrema, cubic-spline envelopes, mean, subtract, stop
 // test), commit IMFs (Eq. 1) and de-serialize (Sec. 3.3).
 //
-// Pass structure. Every instance's serialized signal is cut into tiles of TILE samples;
-// one CTA owns one tile and each thread 8 consecutive samples. A pass reads the current
-// signal h once and writes the next one once:
-//   k_pass   (per tile)     - extrema of h as bit masks (Step 1), compaction of the knot
-//                             positions, the tile's spline second derivatives given the
-//                             tile-boundary values from the previous k_reduce, the
-//                             interval cubics, envelope evaluation, mean and subtraction
-//                             (Steps 2-4), SD partial sums, IMF commit (Step 5 / Eq. 1);
-//                             then extrema of the new signal and elimination of the
-//                             tile's interior knots (the per-chunk part of the
-//                             partitioned spline solve), exported as a short record.
-//   k_reduce (per instance) - assembles the reduced interface system (two unknowns per
-//                             tile and envelope, plus the end knots), solves it in
-//                             FP64, writes the tile-boundary values back, and runs the
-//                             stop test / IMF state machine for the next pass.
+// Pass structure. Every instance's serialized signal is cut into tiles of TW = 32 * SPL
+// samples; one warp owns one tile and each lane SPL consecutive samples. Warps never
+// wait for one another: a CTA is only a group of independent warps. A pass reads the
+// current signal h once and writes the next one once:
+//   k_pass   (per tile)     - extrema of h as bit masks (Step 1), compaction of the knots
+//                             into the warp's shared-memory pool, the tile's spline second
+//                             derivatives given the tile-boundary values from the previous
+//                             k_reduce (lanes 0-15 solve the maxima, lanes 16-31 the
+//                             minima), envelope evaluation, mean and subtraction (Steps
+//                             2-4), SD partial sums, IMF commit (Step 5 / Eq. 1); then the
+//                             extrema of the new signal and the elimination of the tile's
+//                             interior knots (the per-chunk part of the partitioned spline
+//                             solve), exported as a short record.
+//   k_reduce (per instance) - stop test and IMF state machine; then per envelope the
+//                             reduced interface system (two unknowns per tile plus the end
+//                             knots) in three levels: contiguous row segments eliminated in
+//                             the working precision, the 32 segment-end unknowns solved in
+//                             FP64 by cyclic reduction, the segments back-substituted;
+//                             writes the tile-boundary values.
 // Knot lists never leave shared memory: besides the signal, only ~100 bytes per tile
 // and envelope cross HBM.
 #pragma once
@@ -29,10 +33,6 @@
 #include "semd_types.h"
 
 namespace semd {
-
-// Skewed index for the interface solve's scratch (lanes walking contiguous segments hit
-// distinct shared-memory banks).
-__device__ __forceinline__ int sk(int j) { return j + (j >> 5); }
 
 // Rounded arithmetic that the compiler may not contract into FMAs. Samples next to a
 // tile edge are evaluated by two tiles (as a sample and as the neighbour's halo); both
@@ -81,36 +81,37 @@ __device__ __forceinline__ bool deser_index(int64_t p, int64_t M, int64_t N, int
 }
 
 // ---------------------------------------------------------------------------------
-// Warp-level partitioned tridiagonal solve.
+// Partitioned tridiagonal solve.
 //
 // Unknowns x_0..x_{n-1}; row i: a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i, with the
 // outside values x_{-1} = xl[col] and x_n = xr[col] given per right-hand-side column.
 // Column 0 carries d; columns 1.. have d = 0 (they give the response to the outside
-// values). Lane l owns rows [s, e); it eliminates rows s..e-2 with the Thomas algorithm
-// in terms of x_{s-1} (last unknown of lane l-1) and x_{e-1} (its own last unknown
-// Z_l), which leaves one reduced row per lane coupling Z_{l-1}, Z_l, Z_{l+1}. That
-// 32-unknown system is solved by parallel cyclic reduction over shuffles. The matrix is
-// diagonally dominant (spline rows: b = 2(a + c)), so no pivoting is needed.
+// values). Worker l owns rows [s, e); it eliminates rows s..e-2 with the Thomas
+// algorithm in terms of x_{s-1} (last unknown of worker l-1) and x_{e-1} (its own last
+// unknown Z_l), which leaves one reduced row per worker coupling Z_{l-1}, Z_l, Z_{l+1}.
+// The matrix is diagonally dominant (spline rows: b = 2(a + c)), so no pivoting is
+// needed.
 
-// Per-lane result of the segment elimination: x_s = alS + beS x_{s-1} + gaS Z_l,
-// x_{e-2} = alE + beE x_{s-1} + gaE Z_l, and the lane's last row (al, bl, cl, dl).
+// Per-worker result of the segment elimination: x_s = alS + beS x_{s-1} + gaS Z_l,
+// x_{e-2} = alE + beE x_{s-1} + gaE Z_l, and the worker's last row (al, bl, cl, dl).
 template <typename R>
 struct SegElim {
     R alS = R(0), beS = R(0), gaS = R(1), alE = R(0), beE = R(1), gaE = R(0);
     R al = R(0), bl = R(1), cl = R(0), dl = R(0);
 };
 
-// The reduced 32-unknown system and its solution by parallel cyclic reduction; returns
-// Z_l per column (dummy 0 for lanes without rows, q == 0).
-template <typename R, int NCOL>
+// The reduced system of W lanes (W = 16: the two half-warps solve two independent
+// systems in the same instructions; W = 32: one system) solved by parallel cyclic
+// reduction over shuffles; returns Z_l per column (dummy 0 for lanes without rows).
+template <typename R, int NCOL, int W>
 __device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, bool has_next,
                                                    const R (&xl)[NCOL], const R (&xr)[NCOL],
                                                    R (&Z)[NCOL])
 {
-    const int lane = threadIdx.x & 31;
-    const R nalS = __shfl_down_sync(FULLMASK, g.alS, 1);
-    const R nbeS = __shfl_down_sync(FULLMASK, g.beS, 1);
-    const R ngaS = __shfl_down_sync(FULLMASK, g.gaS, 1);
+    const int wl = threadIdx.x & (W - 1);
+    const R nalS = __shfl_down_sync(FULLMASK, g.alS, 1, W);
+    const R nbeS = __shfl_down_sync(FULLMASK, g.beS, 1, W);
+    const R ngaS = __shfl_down_sync(FULLMASK, g.gaS, 1, W);
     R A = R(0), B = R(1), C = R(0), D[NCOL];
 #pragma unroll
     for (int k = 0; k < NCOL; ++k)
@@ -120,7 +121,7 @@ __device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, b
         B = g.bl + g.al * g.gaE + (has_next ? g.cl * nbeS : R(0));
         C = has_next ? g.cl * ngaS : R(0);
         D[0] = g.dl - g.al * g.alE - (has_next ? g.cl * nalS : R(0));
-        if (lane == 0) {
+        if (wl == 0) {
 #pragma unroll
             for (int k = 0; k < NCOL; ++k)
                 D[k] -= A * xl[k];
@@ -133,34 +134,36 @@ __device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, b
         }
     }
 #pragma unroll
-    for (int st = 1; st < 32; st <<= 1) {
-        R Am = __shfl_up_sync(FULLMASK, A, st), Bm = __shfl_up_sync(FULLMASK, B, st);
-        R Cm = __shfl_up_sync(FULLMASK, C, st);
-        R Ap = __shfl_down_sync(FULLMASK, A, st), Bp = __shfl_down_sync(FULLMASK, B, st);
-        R Cp = __shfl_down_sync(FULLMASK, C, st);
+    for (int st = 1; st < W; st <<= 1) {
+        // the neighbours' diagonals enter only through their reciprocals: one per lane
+        const R iB = rrcp(B);
+        R Am = __shfl_up_sync(FULLMASK, A, st, W), iBm = __shfl_up_sync(FULLMASK, iB, st, W);
+        R Cm = __shfl_up_sync(FULLMASK, C, st, W);
+        R Ap = __shfl_down_sync(FULLMASK, A, st, W), iBp = __shfl_down_sync(FULLMASK, iB, st, W);
+        R Cp = __shfl_down_sync(FULLMASK, C, st, W);
         R Dm[NCOL], Dp[NCOL];
 #pragma unroll
         for (int k = 0; k < NCOL; ++k) {
-            Dm[k] = __shfl_up_sync(FULLMASK, D[k], st);
-            Dp[k] = __shfl_down_sync(FULLMASK, D[k], st);
+            Dm[k] = __shfl_up_sync(FULLMASK, D[k], st, W);
+            Dp[k] = __shfl_down_sync(FULLMASK, D[k], st, W);
         }
-        if (lane < st) {
+        if (wl < st) {
             Am = R(0);
-            Bm = R(1);
+            iBm = R(1);
             Cm = R(0);
 #pragma unroll
             for (int k = 0; k < NCOL; ++k)
                 Dm[k] = R(0);
         }
-        if (lane + st >= 32) {
+        if (wl + st >= W) {
             Ap = R(0);
-            Bp = R(1);
+            iBp = R(1);
             Cp = R(0);
 #pragma unroll
             for (int k = 0; k < NCOL; ++k)
                 Dp[k] = R(0);
         }
-        const R k1 = A * rrcp(Bm), k2 = C * rrcp(Bp);
+        const R k1 = A * iBm, k2 = C * iBp;
         const R nA = -k1 * Am, nC = -k2 * Cp, nB = B - k1 * Cm - k2 * Ap;
 #pragma unroll
         for (int k = 0; k < NCOL; ++k)
@@ -174,78 +177,6 @@ __device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, b
     for (int k = 0; k < NCOL; ++k)
         Z[k] = D[k] * invB;
 }
-
-// General form used by the interface solve: rows from a functor, per-row scratch
-// cp/dp/bp (skewed index), full back-substitution through `out`.
-template <typename R, class RowFn, class OutFn>
-__device__ void warp_tridiag(int n, const RowFn &row, R xl0, R xr0, R *cp, R *dp, R *bp,
-                             const OutFn &out)
-{
-    const int lane = threadIdx.x & 31;
-    const int Q = (n + 31) >> 5;
-    const int s = min(lane * Q, n), e = min(s + Q, n), q = e - s;
-    SegElim<R> g;
-    if (q >= 2) {
-        R cprev = R(0), dprev = R(0), bprev = R(0);
-        for (int j = s; j <= e - 2; ++j) {
-            R a, b, c, d;
-            row(j, a, b, c, d);
-            const R den = (j == s) ? b : b - a * cprev;
-            const R inv = rrcp(den);
-            const R cpj = c * inv;
-            const R dpj = (d - a * dprev) * inv;
-            const R bpj = ((j == s) ? -a : -a * bprev) * inv;
-            cp[sk(j)] = cpj;
-            dp[sk(j)] = dpj;
-            bp[sk(j)] = bpj;
-            cprev = cpj;
-            dprev = dpj;
-            bprev = bpj;
-        }
-        g.alE = dprev;
-        g.beE = bprev;
-        g.gaE = -cprev;
-        R xa = g.alE, xb = g.beE, xg = g.gaE;
-        for (int j = e - 3; j >= s; --j) {
-            const R c = cp[sk(j)];
-            xa = dp[sk(j)] - c * xa;
-            xb = bp[sk(j)] - c * xb;
-            xg = -c * xg;
-        }
-        g.alS = xa;
-        g.beS = xb;
-        g.gaS = xg;
-    }
-    if (q >= 1)
-        row(e - 1, g.al, g.bl, g.cl, g.dl);
-    const R xl[1] = {xl0}, xr[1] = {xr0};
-    R Z[1];
-    warp_reduced_solve<R, 1>(g, q, (q >= 1) && (e < n), xl, xr, Z);
-    R Zp = __shfl_up_sync(FULLMASK, Z[0], 1);
-    if (lane == 0)
-        Zp = xl0;
-    if (q >= 1) {
-        out(e - 1, Z[0]);
-        R xn = Z[0];
-        for (int j = e - 2; j >= s; --j) {
-            const R x = dp[sk(j)] + bp[sk(j)] * Zp - cp[sk(j)] * xn;
-            out(j, x);
-            xn = x;
-        }
-    }
-}
-
-// Rows of the reduced interface system, read from (shared or global) scratch.
-struct ScratchRows {
-    const double *A, *B, *C, *D;
-    __device__ void operator()(int i, double &a, double &b, double &c, double &d) const
-    {
-        a = A[i];
-        b = B[i];
-        c = C[i];
-        d = D[i];
-    }
-};
 
 // ---------------------------------------------------------------------------------
 // Envelope cubics. Interval (tl, tr) with values (yl, yr) and second derivatives
@@ -284,34 +215,23 @@ __device__ __forceinline__ R horner(const Coef<R> &c, R u)
 }
 
 // ---------------------------------------------------------------------------------
-// Shared memory of one tile pass.
-//
-// Per envelope: the knot positions (tile-relative), kte[0] = bracket knot before the
-// tile, kte[j + 1] = knot j, kte[m + 1] = bracket knot after the tile; the interval
-// cubics cf[q], q = 0..m (interval q runs from knot q-1 to knot q), which during the
-// solve hold the interval's slope, 1/length, length and left value; per-row
-// elimination scratch rw (cp, dp, bp). A lane of the solving warp walks a contiguous
-// run of Q rows with Q odd, so the 32 lanes always touch distinct banks.
-template <typename R, int TILE>
-struct EnvSmem {
-    static constexpr int KC = TILE / 2 + 2; // knots of one kind in a tile, with room
-    Coef<R> cf[KC + 2];
-    Coef<R> rw[KC];
-    int kte[KC + 4];
-};
-
-template <typename R, int TILE, int NT>
-struct PassSmem {
-    static constexpr int NW = NT / 32;
-    EnvSmem<R, TILE> env[2];
-    R hs[TILE + 8];   // hs[4 + k]: signal at tile-relative k, k in [-1, TILE]
-    uint32_t wcnt[NW];
-    R red[2][NW];
-    int cnt[2];
+// Shared memory of one warp tile: a pool of knot slots shared by both envelopes.
+// Maxima use slots [0, m0 + 2), minima [m0 + 2, m0 + m1 + 4). Within an envelope's range,
+// slot 0 is the bracket knot before the tile, slot j + 1 knot j, slot m + 1 the bracket
+// knot after it; cf[q] is the interval whose left knot sits in slot q (interval q =
+// knot q-1 -> knot q); rw holds the elimination of row i (knot i + 1) at slot i. Every
+// sample is at most one kind of extremum, so m0 + m1 <= TW.
+template <typename R, int TW>
+struct WarpPool {
+    static constexpr int KP = TW + 4;
+    Coef<R> cf[KP];
+    Coef<R> rw[KP];
+    R y[KP];
+    int t[KP];
 };
 
 // The interface solution of one tile and envelope in the working precision (FP32 pass
-// kernels read the single-precision copy, so they issue no FP64 conversions).
+// kernels read the single-precision values, so they issue no FP64 conversions).
 template <typename R>
 struct SolveVals {
     R MF, ML, yp, Mp, yn, Mn;
@@ -325,103 +245,96 @@ __device__ __forceinline__ SolveVals<double> solve_vals(const TileSolve &so, dou
     return {so.MF, so.ML, so.yp, so.Mp, so.yn, so.Mn};
 }
 
-// Stores v in an 8-byte record slot: as a double, or as a float in the slot's first half.
-__device__ __forceinline__ void put_slot(double *slot, double v) { *slot = v; }
-__device__ __forceinline__ void put_slot(double *slot, float v)
+// N consecutive values through 16-byte vector accesses (p 16-byte aligned).
+template <int N>
+__device__ __forceinline__ void vload(const float *p, float (&v)[N])
 {
-    *reinterpret_cast<float *>(slot) = v;
+    static_assert(N % 4 == 0, "whole float4s");
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[i];
+        v[4 * i] = a.x;
+        v[4 * i + 1] = a.y;
+        v[4 * i + 2] = a.z;
+        v[4 * i + 3] = a.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void vload(const double *p, double (&v)[N])
+{
+    static_assert(N % 2 == 0, "whole double2s");
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[i];
+        v[2 * i] = a.x;
+        v[2 * i + 1] = a.y;
+    }
+}
+template <int N>
+__device__ __forceinline__ void vstore(float *p, const float (&v)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+        reinterpret_cast<float4 *>(p)[i] =
+            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+template <int N>
+__device__ __forceinline__ void vstore(double *p, const double (&v)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i)
+        reinterpret_cast<double2 *>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
 }
 
-template <typename R>
-struct Vec8;
-template <>
-struct Vec8<float> {
-    __device__ static void load(const float *p, float (&v)[8])
-    {
-        const float4 a = *reinterpret_cast<const float4 *>(p);
-        const float4 b = *reinterpret_cast<const float4 *>(p + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    }
-    __device__ static void store(float *p, const float (&v)[8])
-    {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
-    }
-};
-template <>
-struct Vec8<double> {
-    __device__ static void load(const double *p, double (&v)[8])
-    {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const double2 a = *reinterpret_cast<const double2 *>(p + 2 * i);
-            v[2 * i] = a.x;
-            v[2 * i + 1] = a.y;
-        }
-    }
-    __device__ static void store(double *p, const double (&v)[8])
-    {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<double2 *>(p + 2 * i) = make_double2(v[2 * i], v[2 * i + 1]);
-    }
-};
-
-// 8 consecutive samples starting at k0 (< cnt), zero past cnt. p is 16-byte aligned at k0.
-template <typename T>
-__device__ __forceinline__ void load8(const T *p, int k0, int cnt, T (&v)[8])
+// N consecutive samples starting at k0, zero at and past cnt. p + k0 is 16-byte aligned.
+template <typename T, int N>
+__device__ __forceinline__ void loadn(const T *p, int k0, int cnt, T (&v)[N])
 {
-    if (k0 + 8 <= cnt) {
-        Vec8<T>::load(p + k0, v);
+    if (k0 + N <= cnt) {
+        vload<N>(p + k0, v);
     } else {
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
+        for (int s = 0; s < N; ++s)
             v[s] = (k0 + s < cnt) ? p[k0 + s] : T(0);
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void store8(T *p, int k0, int cnt, const T (&v)[8])
+template <typename T, int N>
+__device__ __forceinline__ void storen(T *p, int k0, int cnt, const T (&v)[N])
 {
-    if (k0 + 8 <= cnt) {
-        Vec8<T>::store(p + k0, v);
+    if (k0 + N <= cnt) {
+        vstore<N>(p + k0, v);
     } else {
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
+        for (int s = 0; s < N; ++s)
             if (k0 + s < cnt)
                 p[k0 + s] = v[s];
     }
 }
 
-// Step 1 on the tile in S.hs: extremum masks of this thread's 8 samples (maximum:
+// Step 1 on one warp tile: extremum masks of this lane's SPL samples (maximum:
 // h[k-1] < h[k] >= h[k+1]; minimum: h[k-1] > h[k] <= h[k+1]; never at the instance's
-// end samples), their block-wide exclusive ranks, and the compacted knot positions
-// env[e].kte[1 + rank]. Then, by all threads, the length, 1/length, slope and left value
-// of every interval between two knots of the tile (cf[1..m-1]). Ends with the knot
-// counts in S.cnt and a barrier.
-template <typename R, int TILE, int NT>
-__device__ __forceinline__ void find_knots(PassSmem<R, TILE, NT> &S, const R (&v)[8], int k0,
-                                           int ts, int L, int cnt, uint32_t &MX, uint32_t &MN,
-                                           int &bx, int &bn)
+// end samples), their warp-wide exclusive ranks (bx, bn), the counts (m0, m1), and the
+// knots (tile position and value) compacted into the pool: maxima at slots 1.., minima
+// at slots m0 + 3... `left` / `right` are the samples next to this lane's run.
+template <typename R, int SPL, int TW>
+__device__ __forceinline__ void warp_knots(WarpPool<R, TW> &P, const R (&v)[SPL], R left, R right,
+                                           int k0, int g0, int cnt, int L, uint32_t &MX,
+                                           uint32_t &MN, int &bx, int &bn, int &m0, int &m1)
 {
-    constexpr int NW = NT / 32;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const R *hs = S.hs + 4;
-    const R left = hs[k0 - 1], right = hs[k0 + 8];
+    const int lane = threadIdx.x & 31;
     uint32_t up = 0, dn = 0; // bit s: h[k0+s] < h[k0+s+1] / h[k0+s] > h[k0+s+1]
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const R nx = s < 7 ? v[s + 1] : right;
+    for (int s = 0; s < SPL; ++s) {
+        const R nx = s < SPL - 1 ? v[s + 1] : right;
         up |= (uint32_t)(v[s] < nx) << s;
         dn |= (uint32_t)(v[s] > nx) << s;
     }
     const uint32_t upl = (up << 1) | (uint32_t)(left < v[0]);
     const uint32_t dnl = (dn << 1) | (uint32_t)(left > v[0]);
-    // valid samples: inside the tile's count and 1 <= global index <= L-2
-    const int g0 = ts + k0;
-    const int lo = max(0, 1 - g0), hi = min(min(8, cnt - k0), L - 1 - g0);
-    const uint32_t valid = hi > lo ? (((1u << hi) - 1u) & ~((1u << lo) - 1u)) : 0u;
+    // valid samples: inside the tile's count and 1 <= instance index <= L-2
+    const int lo = max(0, 1 - g0), hi = min(min(SPL, cnt - k0), L - 1 - g0);
+    const uint32_t valid = hi > lo ? (((2u << (hi - 1)) - 1u) & ~((1u << lo) - 1u)) : 0u;
     MX = upl & ~up & valid;
     MN = dnl & ~dn & valid;
     const uint32_t packed = (uint32_t)__popc(MX) | ((uint32_t)__popc(MN) << 16);
@@ -432,176 +345,229 @@ __device__ __forceinline__ void find_knots(PassSmem<R, TILE, NT> &S, const R (&v
         if (lane >= o)
             incl += y;
     }
-    if (lane == 31)
-        S.wcnt[w] = incl;
-    __syncthreads();
-    uint32_t before = incl - packed, total = 0;
-#pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
-        const uint32_t t = S.wcnt[ww];
-        before += ww < w ? t : 0u;
-        total += t;
-    }
+    const uint32_t total = __shfl_sync(FULLMASK, incl, 31);
+    const uint32_t before = incl - packed;
     bx = (int)(before & 0xffffu);
     bn = (int)(before >> 16);
-    int ix = bx + 1, in = bn + 1;
-    int *kx = S.env[0].kte, *kn = S.env[1].kte;
+    m0 = (int)(total & 0xffffu);
+    m1 = (int)(total >> 16);
+    int ix = 1 + bx, in = m0 + 3 + bn;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        if ((MX >> s) & 1u)
-            kx[ix++] = k0 + s;
-        if ((MN >> s) & 1u)
-            kn[in++] = k0 + s;
-    }
-    const int m0 = (int)(total & 0xffffu), m1 = (int)(total >> 16);
-    if (threadIdx.x == 0) {
-        S.cnt[0] = m0;
-        S.cnt[1] = m1;
-    }
-    __syncthreads();
-    const int n0 = max(m0 - 1, 0), n1 = max(m1 - 1, 0);
-    for (int idx = threadIdx.x; idx < n0 + n1; idx += NT) {
-        const int e = idx < n0 ? 0 : 1;
-        const int q = (idx < n0 ? idx : idx - n0) + 1;
-        EnvSmem<R, TILE> &E = S.env[e];
-        const int tl = E.kte[q], tr = E.kte[q + 1];
-        const R yl = hs[tl];
-        const R h = R(tr - tl), inv = rrcp(h);
-        E.cf[q] = Coef<R>{(hs[tr] - yl) * inv, inv, h, yl};
-    }
-    __syncthreads();
-}
-
-// Step 2 for one envelope of the tile (one warp): natural-spline second derivatives M_j
-// of the interior knots 1..m-2 given M_0 = MF and M_{m-1} = ML from the interface
-// solve; row j: h_j M_{j-1} + 2 (h_j + h_{j+1}) M_j + h_{j+1} M_{j+1} = 6 (S_{j+1} - S_j),
-// h_j and S_j the length and slope of interval j (precomputed in cf[j]). Writes the
-// halved cubic of every interval q = 0..m to E.cf[q]. With EXPORT, instead eliminates
-// the interior in terms of the unknown M_0 and M_{m-1} and returns M_1 (first) and
-// M_{m-2} (last) as affine functions of them (m >= 3 required).
-template <typename R, int TILE, bool EXPORT>
-__device__ void envelope_solve(EnvSmem<R, TILE> &E, const R *hv, int m, const SolveVals<R> &sv,
-                               R (&first)[3], R (&last)[3])
-{
-    const int lane = threadIdx.x & 31;
-    const R MF = EXPORT ? R(0) : sv.MF, ML = EXPORT ? R(0) : sv.ML;
-    const int n = m - 2; // interior unknowns; row i is knot i + 1
-    if (!EXPORT && lane == 0) {
-        // the intervals at the tile's ends: bracket knot -> knot 0, knot m-1 -> bracket
-        auto T = [&](int j) { return E.kte[j + 1]; };
-        auto Y = [&](int j) { return hv[E.kte[j + 1]]; };
-        if (m == 0) {
-            E.cf[0] = half_cubic<R>(T(-1), sv.yp, sv.Mp, T(0), sv.yn, sv.Mn);
-        } else {
-            E.cf[0] = half_cubic<R>(T(-1), sv.yp, sv.Mp, T(0), Y(0), MF);
-            E.cf[m] = half_cubic<R>(T(m - 1), Y(m - 1), ML, T(m), sv.yn, sv.Mn);
-            if (m == 2)
-                E.cf[1] = half_cubic<R>(T(0), Y(0), MF, T(1), Y(1), ML);
+    for (int s = 0; s < SPL; ++s) {
+        if ((MX >> s) & 1u) {
+            P.t[ix] = k0 + s;
+            P.y[ix] = v[s];
+            ++ix;
+        }
+        if ((MN >> s) & 1u) {
+            P.t[in] = k0 + s;
+            P.y[in] = v[s];
+            ++in;
         }
     }
-    if (n <= 0)
+}
+
+// Forward elimination of the interior spline rows s..e-1 of one envelope (row i: knot
+// i + 1, pool slot i + 2; h_q, S_q length and slope of interval q):
+//   h_{i+1} M_i + 2 (h_{i+1} + h_{i+2}) M_{i+1} + h_{i+2} M_{i+2} = 6 (S_{i+2} - S_{i+1}),
+// rows s..e-2 in terms of x_{s-1} and the segment's last unknown x_{e-1} (kept as the
+// lane's last row), then the backward sweep to the segment's first unknown.
+// With IV, also stores every interval's (slope, 1/length, length, left value) in IV[q],
+// for the cubics of the back-substitution.
+template <typename R, bool STORE_IV>
+__device__ __forceinline__ void seg_forward(const int *T, const R *Y, Coef<R> *RW, Coef<R> *IV,
+                                            int s, int e, SegElim<R> &g)
+{
+    if (e <= s)
         return;
-    int Q = (n + 31) >> 5;
-    Q |= 1;
-    const int s = min(lane * Q, n), e = min(s + Q, n), q = e - s;
-    SegElim<R> g;
-    if (q >= 1) {
-        // forward elimination of rows s..e-2 (knots s+1..e-1), the next interval's data
-        // fetched one row ahead; the lane's last row (knot e) is kept for the reduction
-        Coef<R> iv = E.cf[s + 1];
-        R hA = iv.c2, SA = iv.c0;
-        iv = E.cf[s + 2];
-        R cprev = R(0), dprev = R(0), bprev = R(0);
-        for (int j = s + 1; j < e; ++j) {
-            const Coef<R> nxt = E.cf[j + 2];
-            const R hB = iv.c2, SB = iv.c0;
-            const R a = hA, c = hB, b = R(2) * (a + c), d = R(6) * (SB - SA);
-            const bool f = j == s + 1;
+    // length and slope of interval s + 1 (slots s + 1 -> s + 2)
+    const int t0 = T[s + 1];
+    const R y0 = Y[s + 1];
+    int tB = T[s + 2];
+    R yB = Y[s + 2];
+    R hA = R(tB - t0);
+    R iA = rrcp(hA);
+    R SA = (yB - y0) * iA;
+    if (STORE_IV)
+        IV[s + 1] = Coef<R>{SA, iA, hA, y0};
+    R cprev = R(0), dprev = R(0), bprev = R(0);
+    for (int j = s; j < e; ++j) {
+        const int tN = T[j + 3];
+        const R yN = Y[j + 3];
+        const R hB = R(tN - tB);
+        const R iB = rrcp(hB);
+        const R SB = (yN - yB) * iB;
+        if (STORE_IV)
+            IV[j + 2] = Coef<R>{SB, iB, hB, yB};
+        const R a = hA, c = hB, b = R(2) * (a + c), d = R(6) * (SB - SA);
+        if (j < e - 1) {
+            const bool f = j == s;
             const R den = f ? b : b - a * cprev;
             const R inv = rrcp(den);
             cprev = c * inv;
             dprev = (f ? d : d - a * dprev) * inv;
             bprev = (f ? -a : -a * bprev) * inv;
-            E.rw[j - 1] = Coef<R>{cprev, dprev, bprev, R(0)};
-            hA = hB;
-            SA = SB;
-            iv = nxt;
+            RW[j] = Coef<R>{cprev, dprev, bprev, R(0)};
+        } else {
+            g.al = a;
+            g.bl = b;
+            g.cl = c;
+            g.dl = d;
         }
-        g.al = hA;
-        g.cl = iv.c2;
-        g.bl = R(2) * (g.al + g.cl);
-        g.dl = R(6) * (iv.c0 - SA);
-        if (q >= 2) {
-            g.alE = dprev;
-            g.beE = bprev;
-            g.gaE = -cprev;
-            R xa = g.alE, xb = g.beE, xg = g.gaE;
-            Coef<R> w = E.rw[max(e - 3, s)];
-            for (int r = e - 3; r >= s; --r) {
-                const Coef<R> wn = E.rw[max(r - 1, s)];
-                xa = w.c1 - w.c0 * xa;
-                xb = w.c2 - w.c0 * xb;
-                xg = -w.c0 * xg;
-                w = wn;
-            }
-            g.alS = xa;
-            g.beS = xb;
-            g.gaS = xg;
-        }
+        tB = tN;
+        yB = yN;
+        hA = hB;
+        SA = SB;
     }
-    const bool has_next = (q >= 1) && (e < n);
-    if constexpr (EXPORT) {
-        const R xl[3] = {R(0), R(1), R(0)}, xr[3] = {R(0), R(0), R(1)};
-        R Z[3];
-        warp_reduced_solve<R, 3>(g, q, has_next, xl, xr, Z);
-        const int last_lane = (n - 1) / Q;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const R f = (k == 0 ? g.alS : R(0)) + g.beS * xl[k] + g.gaS * Z[k];
-            first[k] = __shfl_sync(FULLMASK, f, 0);
-            last[k] = __shfl_sync(FULLMASK, Z[k], last_lane);
+    if (e - s >= 2) {
+        g.alE = dprev;
+        g.beE = bprev;
+        g.gaE = -cprev;
+        R xa = g.alE, xb = g.beE, xg = g.gaE;
+        for (int r = e - 3; r >= s; --r) {
+            const Coef<R> w = RW[r];
+            xa = w.c1 - w.c0 * xa;
+            xb = w.c2 - w.c0 * xb;
+            xg = -w.c0 * xg;
         }
-    } else {
-        const R xl[1] = {MF}, xr[1] = {ML};
-        R Z[1];
-        warp_reduced_solve<R, 1>(g, q, has_next, xl, xr, Z);
-        R Zp = __shfl_up_sync(FULLMASK, Z[0], 1);
-        if (lane == 0)
-            Zp = MF;
-        if (q >= 1) {
-            // back-substitution, descending, with the cubic of each interval as soon as
-            // both of its second derivatives are known (interval j+1: knot j -> j+1)
-            R xn = Z[0];
-            if (e == n) {
-                const Coef<R> st = E.cf[n + 1];
-                E.cf[n + 1] = half_cubic_from(st.c3, xn, ML, st.c2, st.c1, st.c0);
-            }
-            Coef<R> w = E.rw[max(e - 2, 0)], st = E.cf[e];
-            for (int j = e - 1; j >= s + 1; --j) {
-                const Coef<R> wn = E.rw[max(j - 2, 0)], stn = E.cf[j];
-                const R x = w.c1 + w.c2 * Zp - w.c0 * xn;
-                E.cf[j + 1] = half_cubic_from(st.c3, x, xn, st.c2, st.c1, st.c0);
-                xn = x;
-                w = wn;
-                st = stn;
-            }
-            const Coef<R> s1 = E.cf[s + 1];
-            E.cf[s + 1] = half_cubic_from(s1.c3, Zp, xn, s1.c2, s1.c1, s1.c0);
-        }
+        g.alS = xa;
+        g.beS = xb;
+        g.gaS = xg;
     }
 }
 
-// ---------------------------------------------------------------------------------
-// One sifting pass over one tile. Grid: one CTA per tile of every running instance.
-template <typename R, int TILE, int NT>
-__global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
+// Halved cubic of the interval whose left knot is slot q.
+template <typename R>
+__device__ __forceinline__ Coef<R> slot_cubic(const int *T, const R *Y, int q, R Ml, R Mr)
 {
-    constexpr int NW = NT / 32;
-    static_assert(TILE == 8 * NT && NW >= 2 && NW <= 32, "8 samples per thread, >= 2 warps");
+    return half_cubic<R>(T[q], Y[q], Ml, T[q + 1], Y[q + 1], Mr);
+}
+
+// Step 2 for one envelope of the tile (one half-warp, lane hl of 16): natural-spline
+// second derivatives of the interior knots 1..m-2 given M_0 = MF and M_{m-1} = ML from
+// the interface solve, then the halved cubic of every interval q = 0..m into cf. The
+// end intervals (to the bracket knots) use half_cubic on values both neighbouring tiles
+// hold bit for bit, so a sample next to a tile edge evaluates identically in both.
+// Called by all 32 lanes (the shuffles span the warp); any_interior (warp-uniform) tells
+// whether either envelope has interior knots.
+template <typename R, int TW>
+__device__ __forceinline__ void env_solve(WarpPool<R, TW> &P, int base, int m, int hl,
+                                          const SolveVals<R> &sv, bool any_interior)
+{
+    const int *T = P.t + base;
+    const R *Y = P.y + base;
+    Coef<R> *CF = P.cf + base;
+    Coef<R> *RW = P.rw + base;
+    const R MF = sv.MF, ML = sv.ML;
+    if (hl == 0) {
+        if (m == 0) {
+            CF[0] = slot_cubic(T, Y, 0, sv.Mp, sv.Mn);
+        } else {
+            CF[0] = slot_cubic(T, Y, 0, sv.Mp, MF);
+            CF[m] = slot_cubic(T, Y, m, ML, sv.Mn);
+            if (m == 2)
+                CF[1] = slot_cubic(T, Y, 1, MF, ML);
+        }
+    }
+    const int n = max(m - 2, 0); // interior unknowns; row i is knot i + 1 (slot i + 2)
+    if (!any_interior)
+        return;
+    const int Q = ((n + 15) >> 4) | 1; // odd: 16 lanes walking runs of Q rows hit distinct banks
+    const int s = min(hl * Q, n), e = min(s + Q, n), q = e - s;
+    SegElim<R> g;
+    seg_forward<R, true>(T, Y, RW, CF, s, e, g);
+    __syncwarp(); // a neighbour's forward sweep wrote interval data this lane reads below
+    const R xl[1] = {MF}, xr[1] = {ML};
+    R Z[1];
+    warp_reduced_solve<R, 1, 16>(g, q, (q >= 1) && (e < n), xl, xr, Z);
+    R Zp = __shfl_up_sync(FULLMASK, Z[0], 1, 16);
+    if (hl == 0)
+        Zp = MF;
+    if (q >= 1) {
+        // back-substitution, descending; the interval with left slot j + 2 (knot j + 1 ->
+        // j + 2) is written as soon as both of its second derivatives are known
+        auto cubic = [&](int qq, R Ml, R Mr) {
+            const Coef<R> iv = CF[qq];
+            CF[qq] = half_cubic_from(iv.c3, Ml, Mr, iv.c2, iv.c1, iv.c0);
+        };
+        R xn = Z[0];
+        if (e == n)
+            cubic(n + 1, xn, ML);
+        for (int j = e - 2; j >= s; --j) {
+            const Coef<R> w = RW[j];
+            const R x = w.c1 + w.c2 * Zp - w.c0 * xn;
+            cubic(j + 2, x, xn);
+            xn = x;
+        }
+        cubic(s + 1, Zp, xn);
+    }
+}
+
+// Elimination of the interior of one envelope of the tile (one half-warp) in terms of the
+// unknown M_0 and M_{m-1}: M_1 = first[0] + first[1] M_0 + first[2] M_{m-1} and M_{m-2}
+// likewise (last). Meaningful for m >= 3; called by all 32 lanes (or by none).
+template <typename R, int TW>
+__device__ __forceinline__ void env_export(WarpPool<R, TW> &P, int base, int m, int hl,
+                                           R (&first)[3], R (&last)[3])
+{
+    const int n = max(m - 2, 0);
+    const int Q = ((n + 15) >> 4) | 1;
+    const int s = min(hl * Q, n), e = min(s + Q, n), q = e - s;
+    SegElim<R> g;
+    seg_forward<R, false>(P.t + base, P.y + base, P.rw + base, nullptr, s, e, g);
+    const R xl[3] = {R(0), R(1), R(0)}, xr[3] = {R(0), R(0), R(1)};
+    R Z[3];
+    warp_reduced_solve<R, 3, 16>(g, q, (q >= 1) && (e < n), xl, xr, Z);
+    const int last_lane = n > 0 ? (n - 1) / Q : 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const R f = (k == 0 ? g.alS : R(0)) + g.beS * xl[k] + g.gaS * Z[k];
+        first[k] = __shfl_sync(FULLMASK, f, 0, 16);
+        last[k] = __shfl_sync(FULLMASK, Z[k], last_lane, 16);
+    }
+}
+
+// Whole-record 16-byte accesses to the tile records.
+template <typename R>
+union RecWords {
+    int4 v[sizeof(TileRec<R>) / 16];
+    TileRec<R> r;
+};
+template <typename R>
+__device__ __forceinline__ void store_rec(TileRec<R> *p, const TileRec<R> &r)
+{
+    RecWords<R> u;
+    u.r = r;
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(TileRec<R>) / 16); ++i)
+        reinterpret_cast<int4 *>(p)[i] = u.v[i];
+}
+template <typename R>
+__device__ __forceinline__ TileRec<R> load_rec(const TileRec<R> *p)
+{
+    RecWords<R> u;
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(TileRec<R>) / 16); ++i)
+        u.v[i] = reinterpret_cast<const int4 *>(p)[i];
+    return u.r;
+}
+
+// ---------------------------------------------------------------------------------
+// One sifting pass over warp tiles. Grid: NWARP tiles per CTA over every running
+// instance's tiles; warps are independent (no block barrier).
+// The FP32 kernel of 256-sample tiles is shared-memory-limited to 5 CTAs per SM; its
+// register budget is held to that occupancy.
+template <typename R, int SPL, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 : 1)
+    k_pass(PassArgs pa)
+{
+    constexpr int TW = 32 * SPL;
     extern __shared__ __align__(16) unsigned char smraw[];
-    PassSmem<R, TILE, NT> &S = *reinterpret_cast<PassSmem<R, TILE, NT> *>(smraw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gt = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gt = (int64_t)blockIdx.x * NWARP + warp;
+    if (gt >= pa.ntiles)
+        return;
+    WarpPool<R, TW> &P = reinterpret_cast<WarpPool<R, TW> *>(smraw)[warp];
     const int ii = pa.tile_inst[gt];
     const State *stp = pa.state + ii;
     const int mode = stp->mode;
@@ -610,65 +576,74 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
     const int hpar = stp->hpar, rpar = stp->rpar, imfc = stp->imf_count;
     const Inst &in = pa.inst[ii];
     const int L = (int)in.L;
-    const int lt = gt - in.tile0;
-    const int ts = lt * TILE;
-    const int cnt = min(TILE, L - ts);
-    const bool hasL = ts > 0, hasR = ts + TILE < L;
+    const int lt = (int)(gt - in.tile0);
+    const int ts = lt * TW;
+    const int cnt = min(TW, L - ts);
+    const bool hasL = ts > 0, hasR = ts + TW < L;
     const R *hsrc = (const R *)in.h[hpar] + ts;
     R *hdst = (R *)in.h[hpar ^ 1] + ts;
     const double *rsrc = in.r[rpar] + ts;
     double *rdst = in.r[rpar ^ 1] + ts;
     const bool sift = mode == MODE_SIFT || mode == MODE_SIFT_COMMIT;
     const bool commit = mode == MODE_SIFT_COMMIT || mode == MODE_COMMIT;
-    const int k0 = tid * 8;
-    R *hs = S.hs + 4;
+    const int k0 = lane * SPL;
+    const int eh = lane >> 4, hl = lane & 15; // half-warp = envelope in the spline phases
 
-    R v[8], hn[8];
-    R hcl = R(0), hcr = R(0); // current signal at the halo samples -1 and TILE
+    R v[SPL], hn[SPL];
+    R hcl = R(0), hcr = R(0); // current signal at the halo samples -1 and TW
     if (mode != MODE_INIT) {
-        load8(hsrc, k0, cnt, v);
-        if (tid == 0 && hasL)
+        loadn<R, SPL>(hsrc, k0, cnt, v);
+        if (lane == 0 && hasL)
             hcl = hsrc[-1];
-        if (tid == NT - 1 && hasR)
-            hcr = hsrc[TILE];
+        if (lane == 31 && hasR)
+            hcr = hsrc[TW];
+    }
+    // the residue of a commit (or INIT) pass, fetched together with h
+    const bool use_r = commit || mode == MODE_INIT;
+    double r[SPL], rl = 0.0, rr = 0.0;
+    if (use_r) {
+        loadn<double, SPL>(rsrc, k0, cnt, r);
+        if (lane == 0 && hasL)
+            rl = rsrc[-1];
+        if (lane == 31 && hasR)
+            rr = rsrc[TW];
     }
 
     R pn = R(0), pd = R(0);
     R hnl = hcl, hnr = hcr; // the new signal at the halo samples
     if (sift) {
-        Vec8<R>::store(hs + k0, v);
-        if (tid == 0)
-            hs[-1] = hcl;
-        if (tid == NT - 1)
-            hs[TILE] = hcr;
-        __syncthreads();
+        R left = __shfl_up_sync(FULLMASK, v[SPL - 1], 1);
+        R right = __shfl_down_sync(FULLMASK, v[0], 1);
+        if (lane == 0)
+            left = hcl;
+        if (lane == 31)
+            right = hcr;
         uint32_t MX, MN;
-        int bx, bn;
-        find_knots<R, TILE, NT>(S, v, k0, ts, L, cnt, MX, MN, bx, bn);
-        const TileSolve *so = in.tsol + 2 * lt;
-        if (tid < 2) {
-            EnvSmem<R, TILE> &E = S.env[tid];
-            E.kte[0] = so[tid].tp - ts;
-            E.kte[S.cnt[tid] + 1] = so[tid].tn - ts;
+        int bx, bn, m0, m1;
+        warp_knots<R, SPL, TW>(P, v, left, right, k0, ts + k0, cnt, L, MX, MN, bx, bn, m0, m1);
+        const TileSolve &so = in.tsol[2 * lt + eh];
+        const SolveVals<R> sv = solve_vals(so, R(0));
+        const int b1 = m0 + 2;
+        const int base = eh ? b1 : 0, m = eh ? m1 : m0;
+        if (hl == 0) {
+            P.t[base] = so.tp - ts;
+            P.y[base] = sv.yp;
+            P.t[base + m + 1] = so.tn - ts;
+            P.y[base + m + 1] = sv.yn;
         }
-        __syncthreads();
-        if (warp < 2) {
-            R f[3], l[3];
-            envelope_solve<R, TILE, false>(S.env[warp], hs, S.cnt[warp],
-                                           solve_vals(so[warp], R(0)), f, l);
-        }
-        __syncthreads();
+        __syncwarp();
+        env_solve<R, TW>(P, base, m, hl, sv, max(m0, m1) >= 3);
+        __syncwarp();
         // Steps 2-4 at every sample: both envelopes (interval = knots at or before k),
         // their mean, the subtraction, and the SD partial sums
-        const EnvSmem<R, TILE> &E0 = S.env[0], &E1 = S.env[1];
-        int q0 = bx, q1 = bn;
+        int q0 = bx, q1 = b1 + bn;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
+        for (int s = 0; s < SPL; ++s) {
             q0 += (MX >> s) & 1u;
             q1 += (MN >> s) & 1u;
             const int k = k0 + s;
-            const R e0 = horner(E0.cf[q0], R(k - E0.kte[q0]));
-            const R e1 = horner(E1.cf[q1], R(k - E1.kte[q1]));
+            const R e0 = horner(P.cf[q0], R(k - P.t[q0]));
+            const R e1 = horner(P.cf[q1], R(k - P.t[q1]));
             const R mean = radd(e0, e1);
             hn[s] = rsub(v[s], mean);
             if (k < cnt) {
@@ -676,47 +651,43 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
                 pd += v[s] * v[s];
             }
         }
-        // halo samples: interval 0 before the tile, interval m after it (where a knot on
-        // the sample itself gives the knot value, as the neighbour computes it)
-        if (tid == 0 && hasL) {
-            const R mean = radd(horner(E0.cf[0], R(-1 - E0.kte[0])),
-                                horner(E1.cf[0], R(-1 - E1.kte[0])));
+        // halo samples: interval 0 before the tile, interval m after it (where the
+        // bracket knot is the sample itself, the knot value, as the neighbour computes it)
+        if (lane == 0 && hasL) {
+            const R mean = radd(horner(P.cf[0], R(-1 - P.t[0])), horner(P.cf[b1], R(-1 - P.t[b1])));
             hnl = rsub(hcl, mean);
         }
-        if (tid == NT - 1 && hasR) {
-            const int m0 = S.cnt[0], m1 = S.cnt[1];
-            const R e0 = E0.kte[m0 + 1] == TILE ? rmul(solve_vals(so[0], R(0)).yn, R(0.5))
-                                                  : horner(E0.cf[m0], R(TILE - E0.kte[m0]));
-            const R e1 = E1.kte[m1 + 1] == TILE ? rmul(solve_vals(so[1], R(0)).yn, R(0.5))
-                                                  : horner(E1.cf[m1], R(TILE - E1.kte[m1]));
+        if (lane == 31 && hasR) {
+            const R e0 = P.t[m0 + 1] == TW ? rmul(P.y[m0 + 1], R(0.5))
+                                           : horner(P.cf[m0], R(TW - P.t[m0]));
+            const int q = b1 + m1;
+            const R e1 = P.t[q + 1] == TW ? rmul(P.y[q + 1], R(0.5)) : horner(P.cf[q], R(TW - P.t[q]));
             hnr = rsub(hcr, radd(e0, e1));
         }
+        __syncwarp(); // the pool is reused for the new signal's knots
     } else {
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
+        for (int s = 0; s < SPL; ++s)
             hn[s] = v[s];
     }
 
     // Step 5 / Eq. (1): commit the IMF c, update the FP64 residue, restart from it
-    if (commit || mode == MODE_INIT) {
-        double r[8];
-        load8(rsrc, k0, cnt, r);
+    if (use_r) {
         if (commit) {
-            double rn[8];
+            double rn[SPL];
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
+            for (int s = 0; s < SPL; ++s)
                 rn[s] = __dsub_rn(r[s], (double)hn[s]);
-            }
-            store8(rdst, k0, cnt, rn);
+            storen<double, SPL>(rdst, k0, cnt, rn);
             R *imf = (R *)in.imf + (int64_t)imfc * in.imf_stride;
             if (in.imf_serialized) {
-                store8(imf + ts, k0, cnt, hn);
+                storen<R, SPL>(imf + ts, k0, cnt, hn);
             } else {
                 const int64_t MD = in.M + in.D;
                 const int p0 = ts + k0;
                 int64_t i = p0 / MD, mm = p0 - i * MD;
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
+                for (int s = 0; s < SPL; ++s) {
                     if (k0 + s < cnt && mm < in.M)
                         imf[in.order == 0 ? i * in.M + mm : mm * in.N + i] = hn[s];
                     if (++mm == MD) {
@@ -726,65 +697,58 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
                 }
             }
 #pragma unroll
-            for (int s = 0; s < 8; ++s)
+            for (int s = 0; s < SPL; ++s)
                 hn[s] = (R)rn[s];
         } else {
 #pragma unroll
-            for (int s = 0; s < 8; ++s)
+            for (int s = 0; s < SPL; ++s)
                 hn[s] = (R)r[s];
         }
-        if (tid == 0 && hasL)
-            hnl = (R)(commit ? __dsub_rn(rsrc[-1], (double)hnl) : rsrc[-1]);
-        if (tid == NT - 1 && hasR)
-            hnr = (R)(commit ? __dsub_rn(rsrc[TILE], (double)hnr) : rsrc[TILE]);
+        if (lane == 0 && hasL)
+            hnl = (R)(commit ? __dsub_rn(rl, (double)hnl) : rl);
+        if (lane == 31 && hasR)
+            hnr = (R)(commit ? __dsub_rn(rr, (double)hnr) : rr);
     }
 
     // Step 1 on the new signal and the per-tile elimination of its spline system
-    if (sift)
-        __syncthreads(); // the solve and the evaluation are done with hs and env
-    Vec8<R>::store(hs + k0, hn);
-    if (tid == 0)
-        hs[-1] = hnl;
-    if (tid == NT - 1)
-        hs[TILE] = hnr;
-    __syncthreads();
     {
+        R left = __shfl_up_sync(FULLMASK, hn[SPL - 1], 1);
+        R right = __shfl_down_sync(FULLMASK, hn[0], 1);
+        if (lane == 0)
+            left = hnl;
+        if (lane == 31)
+            right = hnr;
         uint32_t MX, MN;
-        int bx, bn;
-        find_knots<R, TILE, NT>(S, hn, k0, ts, L, cnt, MX, MN, bx, bn);
-    }
-    if (warp < 2) {
-        const int e = warp;
-        const int m = S.cnt[e];
-        const EnvSmem<R, TILE> &E = S.env[e];
-        TileExport *rec = in.tex + 2 * lt + e;
+        int bx, bn, m0, m1;
+        warp_knots<R, SPL, TW>(P, hn, left, right, k0, ts + k0, cnt, L, MX, MN, bx, bn, m0, m1);
+        __syncwarp();
+        const int base = eh ? m0 + 2 : 0, m = eh ? m1 : m0;
         R f[3] = {R(0), R(0), R(0)}, l[3] = {R(0), R(0), R(0)};
-        if (m >= 3)
-            envelope_solve<R, TILE, true>(S.env[e], hs, m, SolveVals<R>{}, f, l);
-        if (lane == 0) {
-            rec->n = m;
-            if (m >= 1) {
-                const int ix[4] = {0, min(1, m - 1), max(m - 2, 0), m - 1};
+        if (max(m0, m1) >= 3)
+            env_export<R, TW>(P, base, m, hl, f, l);
+        if (hl == 0) {
+            TileRec<R> rec;
+            rec.n = m;
+            const int ix[4] = {0, min(1, m - 1), max(m - 2, 0), m - 1};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = E.kte[ix[q] + 1];
-                    rec->t[q] = ts + t;
-                    put_slot(&rec->y[q], hs[t]);
-                }
+            for (int q = 0; q < 4; ++q) {
+                rec.t[q] = m >= 1 ? ts + P.t[base + 1 + ix[q]] : 0;
+                rec.y[q] = m >= 1 ? P.y[base + 1 + ix[q]] : R(0);
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                put_slot(&rec->xa[q], f[q]);
-                put_slot(&rec->xb[q], l[q]);
+                rec.xa[q] = m >= 3 ? f[q] : R(0);
+                rec.xb[q] = m >= 3 ? l[q] : R(0);
             }
+            store_rec(reinterpret_cast<TileRec<R> *>(in.tex) + 2 * lt + eh, rec);
         }
     }
-    store8(hdst, k0, cnt, hn);
-    if (tid == 0 && !hasL)
+    storen<R, SPL>(hdst, k0, cnt, hn);
+    if (lane == 0 && !hasL)
         in.taux[lt].h_first = (double)hn[0];
-    if (!hasR && k0 <= cnt - 1 && cnt - 1 < k0 + 8) {
+    if (!hasR && k0 <= cnt - 1 && cnt - 1 < k0 + SPL) {
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
+        for (int s = 0; s < SPL; ++s)
             if (k0 + s == cnt - 1)
                 in.taux[lt].h_last = (double)hn[s];
     }
@@ -792,55 +756,109 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs pa)
         pn = warp_sum(pn);
         pd = warp_sum(pd);
         if (lane == 0) {
-            S.red[0][warp] = pn;
-            S.red[1][warp] = pd;
+            in.taux[lt].sd_num = (double)pn;
+            in.taux[lt].sd_den = (double)pd;
         }
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0, b = 0.0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                a += (double)S.red[0][w];
-                b += (double)S.red[1][w];
-            }
-            in.taux[lt].sd_num = a;
-            in.taux[lt].sd_den = b;
-        }
-    }
-    if (tid == 0 && pa.stats) {
-        // algorithmic bytes per sample: h in (w) unless INIT, h out (w), and for a commit
-        // the IMF out (w) and the residue in and out (16); INIT reads the residue (8)
-        const unsigned long long w = sizeof(R);
-        unsigned long long per = (mode == MODE_INIT) ? 8 + w : 2 * w;
-        if (commit)
-            per += w + 16;
-        atomicAdd(&pa.stats->pass_bytes, per * (unsigned long long)cnt);
-        if (sift)
-            atomicAdd(&pa.stats->sample_sifts, (unsigned long long)cnt);
     }
 }
 
 // ---------------------------------------------------------------------------------
 // Per instance: stop test and state machine, then the reduced interface system of the
-// spline solve for each envelope (warp 0: maxima, warp 1: minima), in FP64.
-__global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
+// spline solve for each envelope (threads 0-127: maxima, 128-255: minima).
+//
+// Rows of the reduced system are the tile-edge knots in order, [mirrored or end knots]
+// [first/last knot of every non-empty tile][mirrored or end knots]; a tile's interior
+// knots next to its first/last knot are substituted by the tile's elimination
+// (M = x0 + x1 M_first + x2 M_last), which keeps the system tridiagonal. The tile
+// records are read once into a shared (or, for very long instances, global) scratch;
+// every row is then built from the scratch alone. The solve has three levels, one warp
+// per envelope: lane l eliminates its contiguous segment of rows in the working
+// precision, the 32 segment-end unknowns are solved in FP64 by cyclic reduction, and
+// the segments are back-substituted. FP64 work is O(32) per envelope: GB300's FP64 pipe
+// is narrow (a warp-wide FP64 instruction, conversions included, occupies it for many
+// cycles), so the working precision carries everything else.
+
+// Entry kinds of the reduced system.
+enum EKind : int32_t {
+    EK_FIXED = 0, // natural end: M = 0
+    EK_FREE = 1,  // mirrored knot: plain row
+    EK_F = 2,     // first knot of a tile with 2 knots (its right neighbour is the next entry)
+    EK_FS = 3,    // first knot of a tile with >= 3 knots (right neighbour substituted)
+    EK_L = 4,     // last knot of a tile with 2 knots
+    EK_LS = 5,    // last knot of a tile with >= 3 knots (left neighbour substituted)
+    EK_FL = 6     // the only knot of a tile
+};
+
+// Per-envelope scratch of k_reduce, structure of arrays of `cap` entries.
+//   Et, Ey   - entry position and value
+//   Ek       - entry kind
+//   St, A..D - substituted neighbour (position St, value A) and the tile's elimination
+//              (B, C, D = x0, x1, x2); then the row (a, b, c, d); then, for the rows a
+//              segment eliminates, (bp, b, cp, dp)
+//   MV       - solved second derivative
+//   Tu       - per tile: its number of entries (0, 1 or 2)
+template <typename R>
+struct RedScratch {
+    R *Ey, *A, *B, *C, *D, *MV;
+    int *Et, *Ek, *St;
+    unsigned char *Tu;
+    __device__ void carve(unsigned char *p, int64_t cap)
+    {
+        R *r = reinterpret_cast<R *>(p);
+        Ey = r;
+        A = r + cap;
+        B = r + 2 * cap;
+        C = r + 3 * cap;
+        D = r + 4 * cap;
+        MV = r + 5 * cap;
+        int *q = reinterpret_cast<int *>(r + 6 * cap);
+        Et = q;
+        Ek = q + cap;
+        St = q + 2 * cap;
+        Tu = reinterpret_cast<unsigned char *>(q + 3 * cap);
+    }
+};
+
+struct RedShared {
+    double sd[kRedThreads / 32][2];
+    int wsu[kRedThreads / 32], wsn[kRedThreads / 32];
+    int next;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
 {
+    __shared__ RedShared S;
     const int ii = ra.inst_list ? ra.inst_list[blockIdx.x] : (int)blockIdx.x;
     State *st = ra.state + ii;
     const int pm = st->mode;
     if (pm == MODE_DONE)
         return;
     const Inst &in = ra.inst[ii];
-    const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int e = tid / kRedSeg, te = tid % kRedSeg;
+    constexpr int WPE = kRedSeg / 32; // warps per envelope
     const int nt = in.ntiles;
-    const int TQ = (nt + 31) / 32;
-    const int ta = min(lane * TQ, nt), tb = min(ta + TQ, nt);
-    const TileExport *tex = in.tex + e;
+    const int TQ = (nt + kRedSeg - 1) / kRedSeg;
+    const int ta = min(te * TQ, nt), tb = min(ta + TQ, nt);
+    // this envelope's record of tile t: tex[2 t]
+    const TileRec<R> *tex = reinterpret_cast<const TileRec<R> *>(in.tex) + e;
+
+    // counts: knots and reduced-system entries (first/last knot) of this thread's tiles
     int sn = 0, su = 0;
+#pragma unroll 4
     for (int t = ta; t < tb; ++t) {
         const int n = tex[2 * t].n;
         sn += n;
         su += min(n, 2);
+    }
+    double a = 0.0, b = 0.0;
+    if (e == 0 && pm == MODE_SIFT) {
+#pragma unroll 4
+        for (int t = ta; t < tb; ++t) {
+            a += in.taux[t].sd_num;
+            b += in.taux[t].sd_den;
+        }
     }
     int incl = su;
 #pragma unroll
@@ -849,30 +867,34 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
         if (lane >= o)
             incl += y;
     }
-    const int ubase = incl - su;
-    const int U = __shfl_sync(FULLMASK, incl, 31);
-    const int ntot = warp_sum(sn);
-    __shared__ int s_ntot[2], s_next;
-    __shared__ double s_sd[2];
-    if (lane == 0)
-        s_ntot[e] = ntot;
-    if (e == 0) {
-        double a = 0.0, b = 0.0;
-        if (pm == MODE_SIFT)
-            for (int t = ta; t < tb; ++t) {
-                a += in.taux[t].sd_num;
-                b += in.taux[t].sd_den;
-            }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (lane == 0) {
-            s_sd[0] = a;
-            s_sd[1] = b;
-        }
+    const int snw = warp_sum(sn);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 31)
+        S.wsu[warp] = incl;
+    if (lane == 0) {
+        S.wsn[warp] = snw;
+        S.sd[warp][0] = a;
+        S.sd[warp][1] = b;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nmax = s_ntot[0], nmin = s_ntot[1];
+    int ubase = incl - su, U = 0, ntot = 0;
+#pragma unroll
+    for (int w = 0; w < WPE; ++w) {
+        const int ww = e * WPE + w;
+        ubase += ww < warp ? S.wsu[ww] : 0;
+        U += S.wsu[ww];
+        ntot += S.wsn[ww];
+    }
+    if (tid == 0) {
+        int nmax = 0, nmin = 0;
+        double sdn = 0.0, sdd = 0.0;
+        for (int w = 0; w < WPE; ++w) {
+            nmax += S.wsn[w];
+            nmin += S.wsn[WPE + w];
+            sdn += S.sd[w][0];
+            sdd += S.sd[w][1];
+        }
         const bool ok = nmax >= 1 && nmin >= 1 && nmax + nmin >= 3;
         State s = *st;
         s.hpar ^= 1;
@@ -897,7 +919,7 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
             } else if (ra.stop == STOP_FIXED) {
                 nm = (s.sift_count >= ra.fixed_sifts - 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
             } else {
-                const double sd = s_sd[0] / s_sd[1];
+                const double sd = sdn / sdd;
                 s.sd = sd;
                 nm = (sd < ra.sd_threshold || s.sift_count >= ra.max_sifts) ? MODE_COMMIT
                                                                             : MODE_SIFT;
@@ -907,183 +929,274 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs ra)
         s.nmin = nmin;
         s.mode = nm;
         *st = s;
-        s_next = nm;
+        S.next = nm;
         if (nm != MODE_DONE)
             atomicAdd(ra.active, 1);
+        if (ra.stats) {
+            // algorithmic bytes per sample of the pass that just ran: h in (w) unless
+            // INIT, h out (w), and for a commit the IMF out (w) and the residue in and
+            // out (16); INIT reads the residue (8)
+            const unsigned long long w = sizeof(R);
+            unsigned long long per = (pm == MODE_INIT) ? 8 + w : 2 * w;
+            if (pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
+                per += w + 16;
+            atomicAdd(&ra.stats->pass_bytes, per * (unsigned long long)in.L);
+            if (pm == MODE_SIFT || pm == MODE_SIFT_COMMIT)
+                atomicAdd(&ra.stats->sample_sifts, (unsigned long long)in.L);
+        }
     }
     __syncthreads();
-    const int nm = s_next;
+    const int nm = S.next;
     if (nm != MODE_SIFT && nm != MODE_SIFT_COMMIT)
         return;
 
-    // reduced system: [left end knots][first/last knot of every non-empty tile][right end knots]
-    REntry *Rn;
-    double *A, *B, *C, *D, *Mv, *cpv, *dpv, *bpv;
-    if (ra.smem_entries > 0) {
-        // per envelope: cap REntry, then 8 double arrays of cap entries
+    RedScratch<R> X;
+    {
         extern __shared__ __align__(16) unsigned char rsm[];
-        const int64_t cap = ra.smem_entries;
-        unsigned char *base = rsm + (size_t)e * (size_t)cap * (sizeof(REntry) + 8 * sizeof(double));
-        Rn = reinterpret_cast<REntry *>(base);
-        double *dbl = reinterpret_cast<double *>(base + (size_t)cap * sizeof(REntry));
-        A = dbl;
-        B = dbl + cap;
-        C = dbl + 2 * cap;
-        D = dbl + 3 * cap;
-        Mv = dbl + 4 * cap;
-        cpv = dbl + 5 * cap;
-        dpv = dbl + 6 * cap;
-        bpv = dbl + 7 * cap;
-    } else {
-        const int64_t cap = in.rlen;
-        Rn = in.rent + (int64_t)e * cap;
-        double *dbl = in.rscr + (int64_t)e * 8 * cap;
-        A = dbl;
-        B = dbl + cap;
-        C = dbl + 2 * cap;
-        D = dbl + 3 * cap;
-        Mv = dbl + 4 * cap;
-        cpv = dbl + 5 * cap;
-        dpv = dbl + 6 * cap;
-        bpv = dbl + 7 * cap;
+        const bool shm = ra.smem_entries > 0;
+        const int64_t cap = shm ? ra.smem_entries : in.rlen;
+        unsigned char *p0 = shm ? rsm + (size_t)e * red_env_bytes(cap, sizeof(R))
+                                : reinterpret_cast<unsigned char *>(in.rscr + (int64_t)e * 8 * cap);
+        X.carve(p0, cap);
     }
-    // tile-record values in the pass kernel's precision, widened to FP64
-    const bool single = ra.single != 0;
-    auto W = [single](const double &v) {
-        return single ? (double)*reinterpret_cast<const float *>(&v) : v;
-    };
     const int nl = ra.boundary == BND_MIRROR ? min(ra.mirror_knots, ntot) : 1;
     const int nr = nl;
     const int NR = nl + U + nr;
+    // entries of this thread's tiles, with the substitution data of their rows; records
+    // are fetched four at a time (all loads in flight before any is used)
     {
         int p = nl + ubase;
-        for (int t = ta; t < tb; ++t) {
-            const TileExport &rc = tex[2 * t];
-            if (rc.n == 1) {
-                Rn[p++] = REntry{rc.t[0], t, RK_FL, 0, W(rc.y[0])};
-            } else if (rc.n >= 2) {
-                Rn[p++] = REntry{rc.t[0], t, RK_F, 0, W(rc.y[0])};
-                Rn[p++] = REntry{rc.t[3], t, RK_L, 0, W(rc.y[3])};
+        for (int t0 = ta; t0 < tb; t0 += 4) {
+            TileRec<R> rb[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (t0 + k < tb)
+                    rb[k] = load_rec(tex + 2 * (t0 + k));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (t0 + k >= tb)
+                    break;
+                const TileRec<R> &rc = rb[k];
+                const int n = rc.n;
+                X.Tu[t0 + k] = (unsigned char)min(n, 2);
+                if (n == 1) {
+                    X.Et[p] = rc.t[0];
+                    X.Ey[p] = rc.y[0];
+                    X.Ek[p] = EK_FL;
+                    ++p;
+                } else if (n >= 2) {
+                    X.Et[p] = rc.t[0];
+                    X.Ey[p] = rc.y[0];
+                    X.Et[p + 1] = rc.t[3];
+                    X.Ey[p + 1] = rc.y[3];
+                    if (n >= 3) {
+                        X.Ek[p] = EK_FS;
+                        X.St[p] = rc.t[1];
+                        X.A[p] = rc.y[1];
+                        X.B[p] = rc.xa[0];
+                        X.C[p] = rc.xa[1];
+                        X.D[p] = rc.xa[2];
+                        X.Ek[p + 1] = EK_LS;
+                        X.St[p + 1] = rc.t[2];
+                        X.A[p + 1] = rc.y[2];
+                        X.B[p + 1] = rc.xb[0];
+                        X.C[p + 1] = rc.xb[1];
+                        X.D[p + 1] = rc.xb[2];
+                    } else {
+                        X.Ek[p] = EK_F;
+                        X.Ek[p + 1] = EK_L;
+                    }
+                    p += 2;
+                }
             }
         }
     }
-    __syncwarp();
-    if (lane == 0) {
+    __syncthreads();
+    if (te == 0) {
         const int64_t L = in.L;
         if (ra.boundary == BND_MIRROR) {
             // first two and last two knots of the whole signal, reflected about the ends
-            const REntry k0 = Rn[nl];
-            const TileExport &r0 = tex[2 * k0.tile];
+            const int f = nl, l = nl + U - 1;
             if (nl == 2) {
-                int t1;
-                double y1;
-                if (r0.n >= 2) {
-                    t1 = r0.t[1];
-                    y1 = W(r0.y[1]);
-                } else {
-                    t1 = Rn[nl + 1].t;
-                    y1 = Rn[nl + 1].y;
-                }
-                Rn[0] = REntry{-t1, -1, RK_FIXED, 0, y1};
-                Rn[1] = REntry{-k0.t, -1, RK_FREE, 0, k0.y};
+                // the signal's second knot: substituted neighbour of a first knot, else
+                // the next entry
+                const bool sub = X.Ek[f] == EK_FS;
+                const int t1 = sub ? X.St[f] : X.Et[f + 1];
+                const R y1 = sub ? X.A[f] : X.Ey[f + 1];
+                X.Et[0] = -t1;
+                X.Ey[0] = y1;
+                X.Ek[0] = EK_FIXED;
+                X.Et[1] = -X.Et[f];
+                X.Ey[1] = X.Ey[f];
+                X.Ek[1] = EK_FREE;
             } else {
-                Rn[0] = REntry{-k0.t, -1, RK_FIXED, 0, k0.y};
+                X.Et[0] = -X.Et[f];
+                X.Ey[0] = X.Ey[f];
+                X.Ek[0] = EK_FIXED;
             }
-            const REntry kl = Rn[nl + U - 1];
-            const TileExport &rl = tex[2 * kl.tile];
             const int Lm = (int)(2 * (L - 1));
             if (nr == 2) {
-                int t2;
-                double y2;
-                if (rl.n >= 2) {
-                    t2 = rl.t[2];
-                    y2 = W(rl.y[2]);
-                } else {
-                    t2 = Rn[nl + U - 2].t;
-                    y2 = Rn[nl + U - 2].y;
-                }
-                Rn[nl + U] = REntry{Lm - kl.t, -1, RK_FREE, 0, kl.y};
-                Rn[nl + U + 1] = REntry{Lm - t2, -1, RK_FIXED, 0, y2};
+                const bool sub = X.Ek[l] == EK_LS;
+                const int t2 = sub ? X.St[l] : X.Et[l - 1];
+                const R y2 = sub ? X.A[l] : X.Ey[l - 1];
+                X.Et[l + 1] = Lm - X.Et[l];
+                X.Ey[l + 1] = X.Ey[l];
+                X.Ek[l + 1] = EK_FREE;
+                X.Et[l + 2] = Lm - t2;
+                X.Ey[l + 2] = y2;
+                X.Ek[l + 2] = EK_FIXED;
             } else {
-                Rn[nl + U] = REntry{Lm - kl.t, -1, RK_FIXED, 0, kl.y};
+                X.Et[l + 1] = Lm - X.Et[l];
+                X.Ey[l + 1] = X.Ey[l];
+                X.Ek[l + 1] = EK_FIXED;
             }
         } else {
-            Rn[0] = REntry{0, -1, RK_FIXED, 0, in.taux[0].h_first};
-            Rn[nl + U] = REntry{(int)(L - 1), -1, RK_FIXED, 0, in.taux[nt - 1].h_last};
+            X.Et[0] = 0;
+            X.Ey[0] = (R)in.taux[0].h_first;
+            X.Ek[0] = EK_FIXED;
+            X.Et[nl + U] = (int)(L - 1);
+            X.Ey[nl + U] = (R)in.taux[nt - 1].h_last;
+            X.Ek[nl + U] = EK_FIXED;
         }
     }
-    __syncwarp();
-    // rows; a tile's interior knots next to its first/last knot are substituted by the
-    // tile's elimination (M = x0 + u M_first + v M_last)
-    for (int p = lane; p < NR; p += 32) {
-        const REntry c = Rn[p];
-        double a = 0.0, b = 1.0, cc = 0.0, d = 0.0;
-        if (c.kind != RK_FIXED) {
-            const REntry lf = Rn[p - 1], rg = Rn[p + 1];
-            double tl = lf.t, yl = lf.y, tr = rg.t, yr = rg.y;
-            const TileExport *rc = nullptr;
-            if (c.kind == RK_F || c.kind == RK_L)
-                rc = &tex[2 * c.tile];
-            const bool subR = c.kind == RK_F && rc->n >= 3;
-            const bool subL = c.kind == RK_L && rc->n >= 3;
-            if (subR) {
-                tr = rc->t[1];
-                yr = W(rc->y[1]);
+    __syncthreads();
+    // rows, every thread a strided share (reads the scratch only; writes its own rows)
+    for (int p = te; p < NR; p += kRedSeg) {
+        const int k = X.Ek[p];
+        R ra_ = R(0), rb = R(1), rc_ = R(0), rd = R(0);
+        if (k != EK_FIXED) {
+            const int tc = X.Et[p];
+            const R yc = X.Ey[p];
+            int tl = X.Et[p - 1], tr = X.Et[p + 1];
+            R yl = X.Ey[p - 1], yr = X.Ey[p + 1];
+            R x0 = R(0), x1 = R(0), x2 = R(0);
+            if (k == EK_FS || k == EK_LS) {
+                x0 = X.B[p];
+                x1 = X.C[p];
+                x2 = X.D[p];
+                if (k == EK_FS) {
+                    tr = X.St[p];
+                    yr = X.A[p];
+                } else {
+                    tl = X.St[p];
+                    yl = X.A[p];
+                }
             }
-            if (subL) {
-                tl = rc->t[2];
-                yl = W(rc->y[2]);
-            }
-            const double hl = (double)c.t - tl, hr = tr - (double)c.t;
-            const double a0 = hl, b0 = 2.0 * (hl + hr), c0 = hr;
-            const double d0 = 6.0 * ((yr - c.y) * rrcp(hr) - (c.y - yl) * rrcp(hl));
-            a = a0;
-            b = b0;
-            cc = c0;
-            d = d0;
-            if (subR) {
-                b = b0 + c0 * W(rc->xa[1]);
-                cc = c0 * W(rc->xa[2]);
-                d = d0 - c0 * W(rc->xa[0]);
-            }
-            if (subL) {
-                a = a0 * W(rc->xb[1]);
-                b = b0 + a0 * W(rc->xb[2]);
-                d = d0 - a0 * W(rc->xb[0]);
+            const R hl = R(tc - tl), hr = R(tr - tc);
+            const R d0 = R(6) * ((yr - yc) * rrcp(hr) - (yc - yl) * rrcp(hl));
+            ra_ = hl;
+            rb = R(2) * (hl + hr);
+            rc_ = hr;
+            rd = d0;
+            if (k == EK_FS) {
+                rb = rb + hr * x1;
+                rc_ = hr * x2;
+                rd = d0 - hr * x0;
+            } else if (k == EK_LS) {
+                rb = rb + hl * x2;
+                ra_ = hl * x1;
+                rd = d0 - hl * x0;
             }
         }
-        A[p] = a;
-        B[p] = b;
-        C[p] = cc;
-        D[p] = d;
+        X.A[p] = ra_;
+        X.B[p] = rb;
+        X.C[p] = rc_;
+        X.D[p] = rd;
     }
-    __syncwarp();
-    warp_tridiag<double>(NR, ScratchRows{A, B, C, D}, 0.0, 0.0, cpv, dpv, bpv,
-                         [Mv](int i, double x) { Mv[i] = x; });
-    __syncwarp();
+    __syncthreads();
+    if (te < 32) {
+        // level 1: lane segments of Q1 rows (odd, so the lanes hit distinct banks)
+        const int Q1 = ((NR + 31) >> 5) | 1;
+        const int rs = min(lane * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
+        SegElim<R> g;
+        if (rq >= 1) {
+            R cprev = R(0), dprev = R(0), bprev = R(0);
+            for (int j = rs; j < re - 1; ++j) {
+                const R A = X.A[j], B = X.B[j], C = X.C[j], D = X.D[j];
+                const bool f = j == rs;
+                const R den = f ? B : B - A * cprev;
+                const R inv = rrcp(den);
+                cprev = C * inv;
+                dprev = (f ? D : D - A * dprev) * inv;
+                bprev = (f ? -A : -A * bprev) * inv;
+                X.A[j] = bprev;
+                X.C[j] = cprev;
+                X.D[j] = dprev;
+            }
+            g.al = X.A[re - 1];
+            g.bl = X.B[re - 1];
+            g.cl = X.C[re - 1];
+            g.dl = X.D[re - 1];
+            if (rq >= 2) {
+                g.alE = dprev;
+                g.beE = bprev;
+                g.gaE = -cprev;
+                R xa = g.alE, xb = g.beE, xg = g.gaE;
+                for (int j = re - 3; j >= rs; --j) {
+                    const R c = X.C[j];
+                    xa = X.D[j] - c * xa;
+                    xb = X.A[j] - c * xb;
+                    xg = -c * xg;
+                }
+                g.alS = xa;
+                g.beS = xb;
+                g.gaS = xg;
+            }
+        }
+        // level 2: the 32 segment-end unknowns in FP64 (no outside values: the first and
+        // last rows are natural ends)
+        SegElim<double> gd;
+        gd.alS = (double)g.alS;
+        gd.beS = (double)g.beS;
+        gd.gaS = (double)g.gaS;
+        gd.alE = (double)g.alE;
+        gd.beE = (double)g.beE;
+        gd.gaE = (double)g.gaE;
+        gd.al = (double)g.al;
+        gd.bl = (double)g.bl;
+        gd.cl = (double)g.cl;
+        gd.dl = (double)g.dl;
+        const double zl[1] = {0.0}, zr[1] = {0.0};
+        double Z[1];
+        warp_reduced_solve<double, 1, 32>(gd, rq, (rq >= 1) && (re < NR), zl, zr, Z);
+        // level 3: back-substitution of the segment
+        const R z = (R)Z[0];
+        R Zp = __shfl_up_sync(FULLMASK, z, 1);
+        if (lane == 0)
+            Zp = R(0);
+        if (rq >= 1) {
+            X.MV[re - 1] = z;
+            R xn = z;
+            for (int j = re - 2; j >= rs; --j) {
+                const R x = X.D[j] + X.A[j] * Zp - X.C[j] * xn;
+                X.MV[j] = x;
+                xn = x;
+            }
+        }
+    }
+    __syncthreads();
     {
         int p = nl + ubase;
         for (int t = ta; t < tb; ++t) {
-            const int n = tex[2 * t].n;
-            const int u = min(n, 2);
-            TileSolve so;
-            const REntry pv = Rn[p - 1], nx = Rn[p + u];
-            so.tp = pv.t;
-            so.yp = pv.y;
-            so.Mp = Mv[p - 1];
-            so.tn = nx.t;
-            so.yn = nx.y;
-            so.Mn = Mv[p + u];
-            so.MF = u >= 1 ? Mv[p] : 0.0;
-            so.ML = u >= 1 ? Mv[p + u - 1] : 0.0;
-            so.f[0] = (float)so.MF;
-            so.f[1] = (float)so.ML;
-            so.f[2] = (float)so.yp;
-            so.f[3] = (float)so.Mp;
-            so.f[4] = (float)so.yn;
-            so.f[5] = (float)so.Mn;
-            so.pad[0] = so.pad[1] = 0;
-            in.tsol[2 * t + e] = so;
+            const int u = X.Tu[t];
+            TileSolve *so = in.tsol + 2 * t + e;
+            const R yp = X.Ey[p - 1], Mp = X.MV[p - 1], yn = X.Ey[p + u], Mn = X.MV[p + u];
+            const R MF = u >= 1 ? X.MV[p] : R(0), ML = u >= 1 ? X.MV[p + u - 1] : R(0);
+            so->tp = X.Et[p - 1];
+            so->tn = X.Et[p + u];
+            if (sizeof(R) == 4) {
+                // FP32 pass kernels read the single-precision values only
+                *reinterpret_cast<float4 *>(&so->f[0]) =
+                    make_float4((float)MF, (float)ML, (float)yp, (float)Mp);
+                *reinterpret_cast<float2 *>(&so->f[4]) = make_float2((float)yn, (float)Mn);
+            } else {
+                so->MF = (double)MF;
+                so->ML = (double)ML;
+                so->yp = (double)yp;
+                so->Mp = (double)Mp;
+                so->yn = (double)yn;
+                so->Mn = (double)Mn;
+            }
             p += u;
         }
     }

@@ -203,43 +203,61 @@ __global__ void k_to_double(const R *h, int64_t L, double *r)
 
 // ------------------------------------------------------------------ plan helpers
 
-// The pass kernel for each supported tile: 512 / 1024 / 2048 samples, 64 / 128 / 256
-// threads, 8 consecutive samples per thread.
+// The pass kernel for each supported tile: 128 / 256 / 512 samples per warp (4, 8, 16 per
+// lane), kPassWarps warps per CTA.
+template <typename R, int TILE>
+static constexpr size_t pass_smem() { return kPassWarps * sizeof(WarpPool<R, TILE>); }
+
 template <typename R, int TILE>
 static cudaError_t pass_attr_one()
 {
-    return cudaFuncSetAttribute(k_pass<R, TILE, TILE / 8>,
+    return cudaFuncSetAttribute(k_pass<R, TILE / 32, kPassWarps>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(PassSmem<R, TILE, TILE / 8>));
+                                (int)pass_smem<R, TILE>());
 }
 
 template <typename R>
 static cudaError_t set_smem_attr()
 {
-    cudaError_t e = pass_attr_one<R, 512>();
+    cudaError_t e = pass_attr_one<R, 128>();
     if (e == cudaSuccess)
-        e = pass_attr_one<R, 1024>();
+        e = pass_attr_one<R, 256>();
     if (e == cudaSuccess)
-        e = pass_attr_one<R, 2048>();
+        e = pass_attr_one<R, 512>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kReduceSmemMax);
     return e;
 }
 
 template <typename R, int TILE>
-static void launch_pass_t(const PassArgs &pa, int64_t ntiles, cudaStream_t s)
+static void launch_pass_t(PassArgs pa, int64_t ntiles, cudaStream_t s)
 {
-    k_pass<R, TILE, TILE / 8>
-        <<<(unsigned)ntiles, TILE / 8, sizeof(PassSmem<R, TILE, TILE / 8>), s>>>(pa);
+    pa.ntiles = ntiles;
+    const int64_t grid = (ntiles + kPassWarps - 1) / kPassWarps;
+    k_pass<R, TILE / 32, kPassWarps><<<(unsigned)grid, 32 * kPassWarps, pass_smem<R, TILE>(), s>>>(pa);
 }
 
 template <typename R>
 static void launch_pass_tiles(int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
 {
-    if (tile == 512)
+    if (tile == 128)
+        launch_pass_t<R, 128>(pa, ntiles, s);
+    else if (tile == 512)
         launch_pass_t<R, 512>(pa, ntiles, s);
-    else if (tile == 2048)
-        launch_pass_t<R, 2048>(pa, ntiles, s);
     else
-        launch_pass_t<R, 1024>(pa, ntiles, s);
+        launch_pass_t<R, 256>(pa, ntiles, s);
+}
+
+static size_t reduce_smem(const ReduceArgs &ra)
+{
+    return ra.smem_entries > 0 ? reduce_smem_bytes(ra.smem_entries, ra.single ? 4 : 8) : 0;
+}
+
+template <typename R>
+static void launch_reduce(const ReduceArgs &ra, int nblocks, cudaStream_t s)
+{
+    k_reduce<R><<<nblocks, kRedThreads, reduce_smem(ra), s>>>(ra);
 }
 
 int64_t serial_length(int64_t M, int64_t N, int64_t D) { return M * N + D * N - D; }
@@ -332,10 +350,9 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {(void **)&d_inst, (size_t)insts * sizeof(Inst)},
         {(void **)&d_state, (size_t)insts * sizeof(State)},
         {(void **)&d_tile_inst, (size_t)tiles * 4},
-        {(void **)&d_tex, (size_t)tiles * 2 * sizeof(TileExport)},
+        {&d_tex, (size_t)tiles * 2 * tile_rec_bytes(elem)},
         {(void **)&d_tsol, (size_t)tiles * 2 * sizeof(TileSolve)},
         {(void **)&d_taux, (size_t)tiles * sizeof(TileAux)},
-        {(void **)&d_rent, (size_t)rentries * sizeof(REntry)},
         {(void **)&d_rscr, (size_t)rentries * 8 * 8},
         {(void **)&d_active, (size_t)iters * 4},
         {(void **)&d_beta, 8},
@@ -383,9 +400,6 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         e = set_smem_attr<double>();
     else
         e = set_smem_attr<float>();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kReduceSmemMax);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return SEMD_ECUDA;
@@ -424,11 +438,10 @@ static void bind_instance(Workspace &ws, Inst &in, int64_t off, int64_t tiles, i
     in.h[1] = (char *)ws.h1 + off * (int64_t)ws.elem_size;
     in.r[0] = ws.r0 + off;
     in.r[1] = ws.r1 + off;
-    in.tex = ws.d_tex + 2 * tiles;
+    in.tex = (char *)ws.d_tex + 2 * tiles * (int64_t)tile_rec_bytes(ws.elem_size);
     in.tsol = ws.d_tsol + 2 * tiles;
     in.taux = ws.d_taux + tiles;
     in.rlen = reduce_len(in.ntiles);
-    in.rent = ws.d_rent + rent;
     in.rscr = ws.d_rscr + 8 * rent;
 }
 
@@ -468,7 +481,7 @@ static void launch_pass(Workspace &ws, int64_t ntiles, cudaStream_t s)
     pa.inst = ws.d_inst;
     pa.state = ws.d_state;
     pa.tile_inst = ws.d_tile_inst;
-    pa.stats = ws.d_stats;
+    pa.ntiles = ntiles;
     launch_pass_tiles<R>(ws.tile, pa, ntiles, s);
 }
 
@@ -479,6 +492,7 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.state = ws.d_state;
     ra.inst_list = nullptr;
     ra.active = ws.d_active;
+    ra.stats = ws.d_stats;
     ra.K = p.max_imfs;
     ra.stop = p.stop;
     ra.fixed_sifts = p.fixed_sifts;
@@ -489,13 +503,8 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.single = ws.elem_size == 4 ? 1 : 0;
     ra.pad = 0;
     const int64_t entries = reduce_len(ws.max_ntiles);
-    ra.smem_entries = reduce_smem_bytes(entries) <= kReduceSmemMax ? entries : 0;
+    ra.smem_entries = reduce_smem_bytes(entries, ws.elem_size) <= kReduceSmemMax ? entries : 0;
     return ra;
-}
-
-static size_t reduce_smem(const ReduceArgs &ra)
-{
-    return ra.smem_entries > 0 ? reduce_smem_bytes(ra.smem_entries) : 0;
 }
 
 // Records an event pair around a launch when the plan is profiling.
@@ -550,7 +559,7 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
         ra.active = ws.d_active + it;
         {
             LaunchTimer t(prof, s, 1);
-            k_reduce<<<ninst, 64, reduce_smem(ra), s>>>(ra);
+            launch_reduce<R>(ra, ninst, s);
         }
         launches += 2;
         if (!capture && p.stop == SEMD_STOP_SD && (it % 8) == 7) {
@@ -736,7 +745,7 @@ semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, 
     ReduceArgs ra = reduce_args(ws, p);
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, 8, s));
     launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
-    k_reduce<<<1, 64, reduce_smem(ra), s>>>(ra);
+    launch_reduce<R>(ra, 1, s);
     launch_pass<R>(ws, ntiles, s); // SIFT
     SEMD_CU(cudaGetLastError());
     SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
@@ -765,11 +774,7 @@ semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, 
 
 cudaError_t setup_kernel_attrs(size_t elem)
 {
-    cudaError_t e = elem == 8 ? set_smem_attr<double>() : set_smem_attr<float>();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kReduceSmemMax);
-    return e;
+    return elem == 8 ? set_smem_attr<double>() : set_smem_attr<float>();
 }
 
 void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
@@ -780,9 +785,12 @@ void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, 
         launch_pass_tiles<float>(tile, pa, ntiles, s);
 }
 
-void launch_reduce_any(const ReduceArgs &ra, int nblocks, cudaStream_t s)
+void launch_reduce_any(size_t elem, const ReduceArgs &ra, int nblocks, cudaStream_t s)
 {
-    k_reduce<<<nblocks, 64, reduce_smem(ra), s>>>(ra);
+    if (elem == 8)
+        launch_reduce<double>(ra, nblocks, s);
+    else
+        launch_reduce<float>(ra, nblocks, s);
 }
 
 void launch_serialize_any(size_t elem, const Inst *d_inst, const State *d_state,
@@ -813,6 +821,7 @@ ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_s
     ra.state = d_state;
     ra.inst_list = inst_list;
     ra.active = active;
+    ra.stats = nullptr;
     ra.K = p.max_imfs;
     ra.stop = p.stop;
     ra.fixed_sifts = p.fixed_sifts;
@@ -823,7 +832,7 @@ ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_s
     ra.single = elem == 4 ? 1 : 0;
     ra.pad = 0;
     const int64_t entries = reduce_len(max_ntiles);
-    ra.smem_entries = reduce_smem_bytes(entries) <= kReduceSmemMax ? entries : 0;
+    ra.smem_entries = reduce_smem_bytes(entries, elem) <= kReduceSmemMax ? entries : 0;
     return ra;
 }
 
@@ -1047,8 +1056,8 @@ semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile)
         return SEMD_EINVAL;
     if (tile == 0)
         tile = choose_tile(plan->p, plan->L, plan->ws.cap_inst);
-    if (tile != 512 && tile != 1024 && tile != 2048) {
-        plan->err = "tile must be 0, 512, 1024 or 2048";
+    if (tile != 128 && tile != 256 && tile != 512) {
+        plan->err = "tile must be 0, 128, 256 or 512";
         return SEMD_EINVAL;
     }
     plan->ws.tile = tile;
@@ -1098,21 +1107,21 @@ const char *serial_emd_last_error(semd_plan_t plan)
 // scratch (signal and residue buffers, per-tile records of the spline solve, the
 // instance descriptor and state) lives in one file-scope __device__ array, so a call
 // reserves no device memory. Every GPU that loads this library holds the array
-// (kNoAllocBytes, about 2.1 MB) until the process exits. All calls share it: calls
+// (kNoAllocBytes, about 2.3 MB) until the process exits. All calls share it: calls
 // that overlap on the GPU (concurrent streams, threads or devices sharing a context)
 // race on it, and each call clears what it needs before use.
 namespace semd {
 
 constexpr int64_t kNoAllocMaxL = 65536;                  // largest accepted L
 constexpr int kNoAllocTiles = (int)(kNoAllocMaxL / kTile);
-constexpr int64_t kNoAllocRent = 2 * skew_len(reduce_entries(kNoAllocTiles));
+constexpr int64_t kNoAllocRent = 2 * reduce_len(kNoAllocTiles);
 constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kNoAllocBytes =
     4 * na_round(kNoAllocMaxL * 8) +                        // h0, h1 (sized for FP64), r0, r1
     na_round(sizeof(Inst)) + na_round(sizeof(State)) + na_round(kNoAllocTiles * 4) +
-    na_round(kNoAllocTiles * 2 * sizeof(TileExport)) +
+    na_round(kNoAllocTiles * 2 * tile_rec_bytes(8)) +
     na_round(kNoAllocTiles * 2 * sizeof(TileSolve)) + na_round(kNoAllocTiles * sizeof(TileAux)) +
-    na_round(kNoAllocRent * sizeof(REntry)) + na_round(kNoAllocRent * 8 * 8) +
+    na_round(kNoAllocRent * 8 * 8) +
     na_round(8) + na_round(sizeof(Stats)) + na_round(4 * 8); // active flags, stats, result
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1147,9 +1156,6 @@ static semd_status noalloc_setup(void *&base, std::string &err)
         e = set_smem_attr<float>();
         if (e == cudaSuccess)
             e = set_smem_attr<double>();
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kReduceSmemMax);
         if (e != cudaSuccess) {
             err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
             return SEMD_ECUDA;
@@ -1215,10 +1221,9 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     ws.d_inst = (Inst *)take(sizeof(Inst));
     ws.d_state = (State *)take(sizeof(State));
     ws.d_tile_inst = (int32_t *)take(kNoAllocTiles * 4);
-    ws.d_tex = (TileExport *)take(kNoAllocTiles * 2 * sizeof(TileExport));
+    ws.d_tex = take(kNoAllocTiles * 2 * tile_rec_bytes(8));
     ws.d_tsol = (TileSolve *)take(kNoAllocTiles * 2 * sizeof(TileSolve));
     ws.d_taux = (TileAux *)take(kNoAllocTiles * sizeof(TileAux));
-    ws.d_rent = (REntry *)take(kNoAllocRent * sizeof(REntry));
     ws.d_rscr = (double *)take(kNoAllocRent * 8 * 8);
     ws.d_active = (int32_t *)take(8);
     ws.d_stats = (Stats *)take(sizeof(Stats));
@@ -1242,7 +1247,7 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     q.max_imfs = 1;
     ReduceArgs ra = reduce_args(ws, q);
     launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
-    k_reduce<<<1, 64, reduce_smem(ra), s>>>(ra);
+    launch_reduce<R>(ra, 1, s);
     launch_pass<R>(ws, ntiles, s); // SIFT
     k_noalloc_result<<<1, 32, 0, s>>>(ws.d_state, ws.d_taux, ntiles, d_result);
     SEMD_CU(cudaGetLastError());

@@ -9,11 +9,14 @@
 
 namespace semd {
 
-// One tile of TILE samples per CTA and 8 consecutive samples per thread. Supported
-// tiles: 512, 1024, 2048 (64, 128, 256 threads); the plan picks one.
-constexpr int kTile = 1024;
-constexpr int kMinTile = 512;
-// Largest shared-memory scratch of the interface solve; larger instances use global memory.
+// One tile of TILE samples per warp, TILE / 32 consecutive samples per lane, kPassWarps
+// independent warps per CTA. Supported tiles: 128, 256, 512; the plan picks one.
+constexpr int kTile = 256;
+constexpr int kMinTile = 128;
+constexpr int kMaxTile = 512;
+constexpr int kPassWarps = 4;
+// Largest dynamic shared-memory scratch of the interface solve; larger instances use
+// global memory.
 constexpr size_t kReduceSmemMax = 200 * 1024;
 
 // Device workspace of a plan: one allocation carved up, plus pinned host staging.
@@ -29,11 +32,10 @@ struct Workspace {
     Inst *d_inst = nullptr;
     State *d_state = nullptr;
     int32_t *d_tile_inst = nullptr;
-    TileExport *d_tex = nullptr;
+    void *d_tex = nullptr;
     TileSolve *d_tsol = nullptr;
     TileAux *d_taux = nullptr;
-    REntry *d_rent = nullptr; // interface-solve scratch: 2 x rlen entries per instance
-    double *d_rscr = nullptr; //   and 16 x rlen doubles per instance
+    double *d_rscr = nullptr; // interface-solve scratch: 16 x rlen doubles per instance
     int32_t *d_active = nullptr;
     double *d_beta = nullptr;
     int32_t *d_misc = nullptr;
@@ -53,8 +55,10 @@ struct Workspace {
     void release();
 };
 
-// Per-instance scratch length of the interface solve (entries per envelope).
-inline int64_t reduce_len(int64_t ntiles) { return skew_len(reduce_entries((int)ntiles)); }
+// Per-instance scratch length of the interface solve (entries per envelope), a multiple
+// of 4 so that every array of the scratch (8- and 4-byte elements, two envelopes) stays
+// naturally aligned.
+constexpr int64_t reduce_len(int64_t ntiles) { return (reduce_entries(ntiles) + 3) & ~(int64_t)3; }
 
 int64_t serial_length(int64_t M, int64_t N, int64_t D);
 bool geometry(const semd_params &p, int64_t rows, int64_t cols, int order, int64_t &M,
@@ -66,7 +70,7 @@ int max_iterations(const semd_params &p);
 // runtime's). elem is the working precision's size: 4 (FP32-mixed) or 8 (FP64).
 cudaError_t setup_kernel_attrs(size_t elem);
 void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s);
-void launch_reduce_any(const ReduceArgs &ra, int nblocks, cudaStream_t s);
+void launch_reduce_any(size_t elem, const ReduceArgs &ra, int nblocks, cudaStream_t s);
 void launch_serialize_any(size_t elem, const Inst *d_inst, const State *d_state,
                           const int32_t *tile_inst, int64_t ntiles, int tile, cudaStream_t s);
 void launch_finalize_any(size_t elem, const Inst *d_inst, const State *d_state,

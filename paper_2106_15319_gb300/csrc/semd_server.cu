@@ -80,7 +80,7 @@ class PoolAlloc {
 // Per-request device buffers, carved from one pool range.
 struct ReqLayout {
     int64_t Lp = 0, nt = 0, rlen = 0;
-    size_t h = 0, r = 0, tex = 0, tsol = 0, taux = 0, rent = 0, rscr = 0, total = 0;
+    size_t h = 0, r = 0, tex = 0, tsol = 0, taux = 0, rscr = 0, total = 0;
 };
 
 static ReqLayout req_layout(int64_t L, size_t elem, int tile)
@@ -92,12 +92,11 @@ static ReqLayout req_layout(int64_t L, size_t elem, int tile)
     auto R = PoolAlloc::round;
     q.h = R((size_t)q.Lp * elem);
     q.r = R((size_t)q.Lp * 8);
-    q.tex = R((size_t)q.nt * 2 * sizeof(TileExport));
+    q.tex = R((size_t)q.nt * 2 * tile_rec_bytes(elem));
     q.tsol = R((size_t)q.nt * 2 * sizeof(TileSolve));
     q.taux = R((size_t)q.nt * sizeof(TileAux));
-    q.rent = R((size_t)q.rlen * 2 * sizeof(REntry));
     q.rscr = R((size_t)q.rlen * 16 * 8);
-    q.total = 2 * q.h + 2 * q.r + q.tex + q.tsol + q.taux + q.rent + q.rscr;
+    q.total = 2 * q.h + 2 * q.r + q.tex + q.tsol + q.taux + q.rscr;
     return q;
 }
 
@@ -223,11 +222,10 @@ bool semd_server_s::round(std::string &e)
         in.r[0] = (double *)(b + 2 * q.h);
         in.r[1] = (double *)(b + 2 * q.h + q.r);
         char *c = b + 2 * q.h + 2 * q.r;
-        in.tex = (TileExport *)c;
+        in.tex = c;
         in.tsol = (TileSolve *)(c + q.tex);
         in.taux = (TileAux *)(c + q.tex + q.tsol);
-        in.rent = (REntry *)(c + q.tex + q.tsol + q.taux);
-        in.rscr = (double *)(c + q.tex + q.tsol + q.taux + q.rent);
+        in.rscr = (double *)(c + q.tex + q.tsol + q.taux);
         in.rlen = q.rlen;
         in.x = rq.req.d_x;
         in.imf = rq.req.d_imfs;
@@ -261,11 +259,11 @@ bool semd_server_s::round(std::string &e)
         waiting = !queue.empty();
     }
     const int passes = waiting ? 2 : 8;
-    PassArgs pa{d_inst, d_state, d_tiles, nullptr};
+    PassArgs pa{d_inst, d_state, d_tiles, ntiles};
     ReduceArgs ra = make_reduce_args(p, d_inst, d_state, d_list, d_active, elem, max_nt);
     for (int it = 0; it < passes; ++it) {
         launch_pass_any(elem, tile, pa, ntiles, stream);
-        launch_reduce_any(ra, nact, stream);
+        launch_reduce_any(elem, ra, nact, stream);
     }
     SV_CU(cudaGetLastError());
     SV_CU(cudaMemcpyAsync(h_state, d_state, (size_t)max_inflight * sizeof(State),

@@ -21,38 +21,37 @@ enum Boundary : int32_t { BND_MIRROR = 0, BND_ENDPOINTS = 1 };
 enum Stop : int32_t { STOP_FIXED = 0, STOP_SD = 1 };
 
 // Per tile and envelope (0 = maxima, 1 = minima): what the interface solve needs of the
-// tile's knots, after the tile has eliminated its interior knots.
-// Values are in the pass kernel's working precision: double for FP64 plans, float (in
-// the first half of each 8-byte slot) for FP32 ones; the interface solve widens them.
-struct TileExport {
-    int32_t n;     // knots of this kind in the tile
-    int32_t t[4];  // instance positions of knots 0, 1, n-2, n-1
-    int32_t pad;
-    double y[4];   // their values
-    double xa[3];  // M at knot 1   = xa[0] + xa[1] * M_0 + xa[2] * M_{n-1}  (n >= 3)
-    double xb[3];  // M at knot n-2 = xb[0] + xb[1] * M_0 + xb[2] * M_{n-1}  (n >= 3)
+// tile's knots, after the tile has eliminated its interior knots, in the pass kernel's
+// working precision R (64 bytes for FP32, 112 for FP64; read with 16-byte loads).
+template <typename R>
+struct __align__(16) TileRec {
+    int32_t n;    // knots of this kind in the tile
+    int32_t t[4]; // instance positions of knots 0, 1, n-2, n-1
+    R y[4];       // their values
+    R xa[3];      // M at knot 1   = xa[0] + xa[1] * M_0 + xa[2] * M_{n-1}  (n >= 3)
+    R xb[3];      // M at knot n-2 = xb[0] + xb[1] * M_0 + xb[2] * M_{n-1}  (n >= 3)
 };
+// Bytes of one record in a plan of element size `elem`.
+__host__ __device__ constexpr size_t tile_rec_bytes(size_t elem)
+{
+    return elem == 4 ? sizeof(TileRec<float>) : sizeof(TileRec<double>);
+}
 
-// Per tile and envelope: the tile-boundary values solved by the interface solve.
-// The FP64 solution, with a single-precision copy of every value for FP32 pass kernels.
-struct TileSolve {
-    double MF, ML;          // M at the tile's first and last knot
-    int32_t tp, tn;         // outside bracket knots: last knot before the tile,
-    double yp, Mp, yn, Mn;  // first knot after it (instance positions)
+// Per tile and envelope: the tile-boundary values solved by the interface solve. FP32
+// plans fill the single-precision values (read by the FP32 pass kernel), FP64 plans the
+// double ones.
+struct __align__(16) TileSolve {
     float f[6];             // MF, ML, yp, Mp, yn, Mn in single precision
-    int32_t pad[2];
+    int32_t tp, tn;         // outside bracket knots: last knot before the tile, first knot
+                            // after it (instance positions)
+    double MF, ML;          // M at the tile's first and last knot
+    double yp, Mp, yn, Mn;  // values and M at the bracket knots
 };
 
 // Working precision, like TileExport.
 struct TileAux {
     double sd_num, sd_den;  // sum (h - h')^2, sum h^2 over the tile
     double h_first, h_last; // h[0] / h[L-1] of the new signal (first / last tile)
-};
-
-enum RKind : int32_t { RK_FIXED = 0, RK_FREE = 1, RK_F = 2, RK_L = 3, RK_FL = 4 };
-struct REntry {
-    int32_t t, tile, kind, pad;
-    double y;
 };
 
 // Read-only description of one instance (one serialized signal) and its buffers. Every
@@ -66,12 +65,11 @@ struct Inst {
     int32_t imf_serialized; // 1: IMFs are written in serialized order (EEMD trials)
     void *h[2];             // working-precision signal, ping-pong (L elements each)
     double *r[2];           // FP64 residue, ping-pong (L elements each)
-    TileExport *tex;        // 2 per tile
+    void *tex;              // TileRec<R>, 2 per tile
     TileSolve *tsol;        // 2 per tile
     TileAux *taux;          // 1 per tile
-    REntry *rent;           // interface-solve scratch when it does not fit shared memory:
-    double *rscr;           //   2 x rlen entries and 8 double arrays of 2 x rlen
-    int64_t rlen;
+    double *rscr;           // interface-solve scratch when it does not fit shared memory:
+    int64_t rlen;           //   8 doubles per entry, rlen entries per envelope
     const void *x;          // input (rows x cols, row-major), or null
     void *imf;              // IMF output base
     double *res;            // residue output (input shape), or null
@@ -98,7 +96,7 @@ struct PassArgs {
     const Inst *inst;
     const State *state;
     const int32_t *tile_inst; // launch tile -> instance index
-    Stats *stats;
+    int64_t ntiles;           // tiles in the launch (the grid is rounded up to whole CTAs)
 };
 
 struct ReduceArgs {
@@ -106,6 +104,7 @@ struct ReduceArgs {
     State *state;
     const int32_t *inst_list; // block -> instance index (null: identity)
     int32_t *active;          // incremented once per instance still running
+    Stats *stats;             // per-decomposition counters, or null
     int32_t K, stop, fixed_sifts, max_sifts;
     double sd_threshold;
     int32_t boundary, mirror_knots;
@@ -114,15 +113,23 @@ struct ReduceArgs {
     int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
 };
 
-// Shared memory of k_reduce for a per-envelope scratch of `entries` (skewed) entries.
-__host__ __device__ inline size_t reduce_smem_bytes(int64_t entries)
+// Threads of the interface-solve kernel: half per envelope.
+constexpr int kRedThreads = 256;
+constexpr int kRedSeg = kRedThreads / 2;
+
+// Scratch of k_reduce for one envelope of `entries` entries: six arrays in the working
+// precision, three of 32-bit integers and one of bytes, rounded to 16 bytes.
+__host__ __device__ constexpr size_t red_env_bytes(int64_t entries, size_t elem)
 {
-    return 2 * (size_t)entries * (sizeof(REntry) + 8 * sizeof(double));
+    return ((size_t)entries * (6 * elem + 13) + 15) & ~(size_t)15;
+}
+// Shared memory of k_reduce when both envelopes' scratch lives there.
+__host__ __device__ constexpr size_t reduce_smem_bytes(int64_t entries, size_t elem)
+{
+    return 2 * red_env_bytes(entries, elem);
 }
 
 // Entries of the reduced system of an instance with nt tiles (per envelope).
-__host__ __device__ constexpr int64_t reduce_entries(int nt) { return 2 * (int64_t)nt + 4; }
-// Scratch length for n entries addressed through sk().
-__host__ __device__ constexpr int64_t skew_len(int64_t n) { return n + n / 32 + 2; }
+__host__ __device__ constexpr int64_t reduce_entries(int64_t nt) { return 2 * nt + 4; }
 
 } // namespace semd
