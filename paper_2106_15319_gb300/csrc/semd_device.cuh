@@ -100,39 +100,13 @@ struct SegElim {
     R al = R(0), bl = R(1), cl = R(0), dl = R(0);
 };
 
-// The reduced system of W lanes (W = 16: the two half-warps solve two independent
-// systems in the same instructions; W = 32: one system) solved by parallel cyclic
-// reduction over shuffles; returns Z_l per column (dummy 0 for lanes without rows).
+// Parallel cyclic reduction of one tridiagonal row per lane over groups of W lanes
+// (A Z_{l-1} + B Z_l + C Z_{l+1} = D[k]; A = 0 on a group's first lane, C = 0 on its
+// last): log2(W) steps of shuffles; returns Z per right-hand-side column.
 template <typename R, int NCOL, int W>
-__device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, bool has_next,
-                                                   const R (&xl)[NCOL], const R (&xr)[NCOL],
-                                                   R (&Z)[NCOL])
+__device__ __forceinline__ void pcr_solve(R A, R B, R C, R (&D)[NCOL], R (&Z)[NCOL])
 {
     const int wl = threadIdx.x & (W - 1);
-    const R nalS = __shfl_down_sync(FULLMASK, g.alS, 1, W);
-    const R nbeS = __shfl_down_sync(FULLMASK, g.beS, 1, W);
-    const R ngaS = __shfl_down_sync(FULLMASK, g.gaS, 1, W);
-    R A = R(0), B = R(1), C = R(0), D[NCOL];
-#pragma unroll
-    for (int k = 0; k < NCOL; ++k)
-        D[k] = R(0);
-    if (q >= 1) {
-        A = g.al * g.beE;
-        B = g.bl + g.al * g.gaE + (has_next ? g.cl * nbeS : R(0));
-        C = has_next ? g.cl * ngaS : R(0);
-        D[0] = g.dl - g.al * g.alE - (has_next ? g.cl * nalS : R(0));
-        if (wl == 0) {
-#pragma unroll
-            for (int k = 0; k < NCOL; ++k)
-                D[k] -= A * xl[k];
-            A = R(0);
-        }
-        if (!has_next) {
-#pragma unroll
-            for (int k = 0; k < NCOL; ++k)
-                D[k] -= g.cl * xr[k];
-        }
-    }
 #pragma unroll
     for (int st = 1; st < W; st <<= 1) {
         // the neighbours' diagonals enter only through their reciprocals: one per lane
@@ -178,6 +152,59 @@ __device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, b
         Z[k] = D[k] * invB;
 }
 
+// Reduced row of a worker from its segment elimination g and the next worker's
+// first-unknown expression (nalS, nbeS, ngaS): A Z_{l-1} + B Z_l + C Z_{l+1} = D.
+// Workers without rows (q == 0) get the dummy row Z = 0.
+template <typename R>
+__device__ __forceinline__ void reduced_row(const SegElim<R> &g, int q, bool has_next, R nalS,
+                                            R nbeS, R ngaS, R &A, R &B, R &C, R &D)
+{
+    A = R(0);
+    B = R(1);
+    C = R(0);
+    D = R(0);
+    if (q >= 1) {
+        A = g.al * g.beE;
+        B = g.bl + g.al * g.gaE + (has_next ? g.cl * nbeS : R(0));
+        C = has_next ? g.cl * ngaS : R(0);
+        D = g.dl - g.al * g.alE - (has_next ? g.cl * nalS : R(0));
+    }
+}
+
+// The reduced system of W lanes (W = 16: the two half-warps solve two independent
+// systems in the same instructions; W = 2, 4, 8 for small systems) with the outside
+// values xl (before the first lane's rows) and xr (after the last rows), solved by
+// cyclic reduction; returns Z_l per column (dummy 0 for lanes without rows).
+template <typename R, int NCOL, int W>
+__device__ __forceinline__ void warp_reduced_solve(const SegElim<R> &g, int q, bool has_next,
+                                                   const R (&xl)[NCOL], const R (&xr)[NCOL],
+                                                   R (&Z)[NCOL])
+{
+    const int wl = threadIdx.x & (W - 1);
+    const R nalS = __shfl_down_sync(FULLMASK, g.alS, 1, W);
+    const R nbeS = __shfl_down_sync(FULLMASK, g.beS, 1, W);
+    const R ngaS = __shfl_down_sync(FULLMASK, g.gaS, 1, W);
+    R A, B, C, D[NCOL];
+    reduced_row(g, q, has_next, nalS, nbeS, ngaS, A, B, C, D[0]);
+#pragma unroll
+    for (int k = 1; k < NCOL; ++k)
+        D[k] = R(0);
+    if (q >= 1) {
+        if (wl == 0) {
+#pragma unroll
+            for (int k = 0; k < NCOL; ++k)
+                D[k] -= A * xl[k];
+            A = R(0);
+        }
+        if (!has_next) {
+#pragma unroll
+            for (int k = 0; k < NCOL; ++k)
+                D[k] -= g.cl * xr[k];
+        }
+    }
+    pcr_solve<R, NCOL, W>(A, B, C, D, Z);
+}
+
 // ---------------------------------------------------------------------------------
 // Envelope cubics. Interval (tl, tr) with values (yl, yr) and second derivatives
 // (Ml, Mr) is stored as the local polynomial e(u) = c0 + c1 u + c2 u^2 + c3 u^3,
@@ -218,16 +245,26 @@ __device__ __forceinline__ R horner(const Coef<R> &c, R u)
 // Shared memory of one warp tile: a pool of knot slots shared by both envelopes.
 // Maxima use slots [0, m0 + 2), minima [m0 + 2, m0 + m1 + 4). Within an envelope's range,
 // slot 0 is the bracket knot before the tile, slot j + 1 knot j, slot m + 1 the bracket
-// knot after it; cf[q] is the interval whose left knot sits in slot q (interval q =
-// knot q-1 -> knot q); rw holds the elimination of row i (knot i + 1) at slot i. Every
-// sample is at most one kind of extremum, so m0 + m1 <= TW.
+// knot after it; ky holds each slot's position (tile-relative) and value, cf[q] the
+// interval whose left knot sits in slot q (interval q = knot q-1 -> knot q), rw the
+// elimination of row i (knot i + 1) at slot i. Every sample is at most one kind of
+// extremum, so m0 + m1 <= TW.
+template <typename R>
+struct __align__(8) KnotY {
+    int t;
+    R y;
+};
+template <>
+struct __align__(16) KnotY<double> {
+    int t;
+    double y;
+};
 template <typename R, int TW>
 struct WarpPool {
     static constexpr int KP = TW + 4;
     Coef<R> cf[KP];
     Coef<R> rw[KP];
-    R y[KP];
-    int t[KP];
+    KnotY<R> ky[KP];
 };
 
 // The interface solution of one tile and envelope in the working precision (FP32 pass
@@ -354,16 +391,10 @@ __device__ __forceinline__ void warp_knots(WarpPool<R, TW> &P, const R (&v)[SPL]
     int ix = 1 + bx, in = m0 + 3 + bn;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {
-        if ((MX >> s) & 1u) {
-            P.t[ix] = k0 + s;
-            P.y[ix] = v[s];
-            ++ix;
-        }
-        if ((MN >> s) & 1u) {
-            P.t[in] = k0 + s;
-            P.y[in] = v[s];
-            ++in;
-        }
+        if ((MX >> s) & 1u)
+            P.ky[ix++] = KnotY<R>{k0 + s, v[s]};
+        if ((MN >> s) & 1u)
+            P.ky[in++] = KnotY<R>{k0 + s, v[s]};
     }
 }
 
@@ -372,33 +403,30 @@ __device__ __forceinline__ void warp_knots(WarpPool<R, TW> &P, const R (&v)[SPL]
 //   h_{i+1} M_i + 2 (h_{i+1} + h_{i+2}) M_{i+1} + h_{i+2} M_{i+2} = 6 (S_{i+2} - S_{i+1}),
 // rows s..e-2 in terms of x_{s-1} and the segment's last unknown x_{e-1} (kept as the
 // lane's last row), then the backward sweep to the segment's first unknown.
-// With IV, also stores every interval's (slope, 1/length, length, left value) in IV[q],
-// for the cubics of the back-substitution.
+// With STORE_IV, also stores every interval's (slope, 1/length, length, left value) in
+// IV[q], for the cubics of the back-substitution.
 template <typename R, bool STORE_IV>
-__device__ __forceinline__ void seg_forward(const int *T, const R *Y, Coef<R> *RW, Coef<R> *IV,
-                                            int s, int e, SegElim<R> &g)
+__device__ __forceinline__ void seg_forward(const KnotY<R> *K, Coef<R> *RW, Coef<R> *IV, int s,
+                                            int e, SegElim<R> &g)
 {
     if (e <= s)
         return;
     // length and slope of interval s + 1 (slots s + 1 -> s + 2)
-    const int t0 = T[s + 1];
-    const R y0 = Y[s + 1];
-    int tB = T[s + 2];
-    R yB = Y[s + 2];
-    R hA = R(tB - t0);
+    const KnotY<R> k0 = K[s + 1];
+    KnotY<R> kB = K[s + 2];
+    R hA = R(kB.t - k0.t);
     R iA = rrcp(hA);
-    R SA = (yB - y0) * iA;
+    R SA = (kB.y - k0.y) * iA;
     if (STORE_IV)
-        IV[s + 1] = Coef<R>{SA, iA, hA, y0};
+        IV[s + 1] = Coef<R>{SA, iA, hA, k0.y};
     R cprev = R(0), dprev = R(0), bprev = R(0);
     for (int j = s; j < e; ++j) {
-        const int tN = T[j + 3];
-        const R yN = Y[j + 3];
-        const R hB = R(tN - tB);
+        const KnotY<R> kN = K[j + 3];
+        const R hB = R(kN.t - kB.t);
         const R iB = rrcp(hB);
-        const R SB = (yN - yB) * iB;
+        const R SB = (kN.y - kB.y) * iB;
         if (STORE_IV)
-            IV[j + 2] = Coef<R>{SB, iB, hB, yB};
+            IV[j + 2] = Coef<R>{SB, iB, hB, kB.y};
         const R a = hA, c = hB, b = R(2) * (a + c), d = R(6) * (SB - SA);
         if (j < e - 1) {
             const bool f = j == s;
@@ -414,8 +442,7 @@ __device__ __forceinline__ void seg_forward(const int *T, const R *Y, Coef<R> *R
             g.cl = c;
             g.dl = d;
         }
-        tB = tN;
-        yB = yN;
+        kB = kN;
         hA = hB;
         SA = SB;
     }
@@ -438,9 +465,17 @@ __device__ __forceinline__ void seg_forward(const int *T, const R *Y, Coef<R> *R
 
 // Halved cubic of the interval whose left knot is slot q.
 template <typename R>
-__device__ __forceinline__ Coef<R> slot_cubic(const int *T, const R *Y, int q, R Ml, R Mr)
+__device__ __forceinline__ Coef<R> slot_cubic(const KnotY<R> *K, int q, R Ml, R Mr)
 {
-    return half_cubic<R>(T[q], Y[q], Ml, T[q + 1], Y[q + 1], Mr);
+    const KnotY<R> a = K[q], b = K[q + 1];
+    return half_cubic<R>(a.t, a.y, Ml, b.t, b.y, Mr);
+}
+
+// Rows per lane of the half-warp solves: odd (16 lanes walking runs of Q rows hit
+// distinct banks) and common to both envelopes (the half-warps run in lock-step anyway).
+__device__ __forceinline__ int seg_rows(int m0, int m1)
+{
+    return ((max(max(m0, m1) - 2, 0) + 15) >> 4) | 1;
 }
 
 // Step 2 for one envelope of the tile (one half-warp, lane hl of 16): natural-spline
@@ -450,37 +485,35 @@ __device__ __forceinline__ Coef<R> slot_cubic(const int *T, const R *Y, int q, R
 // hold bit for bit, so a sample next to a tile edge evaluates identically in both.
 // Called by all 32 lanes (the shuffles span the warp); any_interior (warp-uniform) tells
 // whether either envelope has interior knots.
-template <typename R, int TW>
-__device__ __forceinline__ void env_solve(WarpPool<R, TW> &P, int base, int m, int hl,
+template <typename R, int TW, int W>
+__device__ __forceinline__ void env_solve(WarpPool<R, TW> &P, int base, int m, int hl, int Q,
                                           const SolveVals<R> &sv, bool any_interior)
 {
-    const int *T = P.t + base;
-    const R *Y = P.y + base;
+    const KnotY<R> *K = P.ky + base;
     Coef<R> *CF = P.cf + base;
     Coef<R> *RW = P.rw + base;
     const R MF = sv.MF, ML = sv.ML;
     if (hl == 0) {
         if (m == 0) {
-            CF[0] = slot_cubic(T, Y, 0, sv.Mp, sv.Mn);
+            CF[0] = slot_cubic(K, 0, sv.Mp, sv.Mn);
         } else {
-            CF[0] = slot_cubic(T, Y, 0, sv.Mp, MF);
-            CF[m] = slot_cubic(T, Y, m, ML, sv.Mn);
+            CF[0] = slot_cubic(K, 0, sv.Mp, MF);
+            CF[m] = slot_cubic(K, m, ML, sv.Mn);
             if (m == 2)
-                CF[1] = slot_cubic(T, Y, 1, MF, ML);
+                CF[1] = slot_cubic(K, 1, MF, ML);
         }
     }
-    const int n = max(m - 2, 0); // interior unknowns; row i is knot i + 1 (slot i + 2)
     if (!any_interior)
         return;
-    const int Q = ((n + 15) >> 4) | 1; // odd: 16 lanes walking runs of Q rows hit distinct banks
+    const int n = max(m - 2, 0); // interior unknowns; row i is knot i + 1 (slot i + 2)
     const int s = min(hl * Q, n), e = min(s + Q, n), q = e - s;
     SegElim<R> g;
-    seg_forward<R, true>(T, Y, RW, CF, s, e, g);
+    seg_forward<R, true>(K, RW, CF, s, e, g);
     __syncwarp(); // a neighbour's forward sweep wrote interval data this lane reads below
     const R xl[1] = {MF}, xr[1] = {ML};
     R Z[1];
-    warp_reduced_solve<R, 1, 16>(g, q, (q >= 1) && (e < n), xl, xr, Z);
-    R Zp = __shfl_up_sync(FULLMASK, Z[0], 1, 16);
+    warp_reduced_solve<R, 1, W>(g, q, (q >= 1) && (e < n), xl, xr, Z);
+    R Zp = __shfl_up_sync(FULLMASK, Z[0], 1, W);
     if (hl == 0)
         Zp = MF;
     if (q >= 1) {
@@ -506,25 +539,57 @@ __device__ __forceinline__ void env_solve(WarpPool<R, TW> &P, int base, int m, i
 // Elimination of the interior of one envelope of the tile (one half-warp) in terms of the
 // unknown M_0 and M_{m-1}: M_1 = first[0] + first[1] M_0 + first[2] M_{m-1} and M_{m-2}
 // likewise (last). Meaningful for m >= 3; called by all 32 lanes (or by none).
-template <typename R, int TW>
-__device__ __forceinline__ void env_export(WarpPool<R, TW> &P, int base, int m, int hl,
+template <typename R, int TW, int W>
+__device__ __forceinline__ void env_export(WarpPool<R, TW> &P, int base, int m, int hl, int Q,
                                            R (&first)[3], R (&last)[3])
 {
     const int n = max(m - 2, 0);
-    const int Q = ((n + 15) >> 4) | 1;
     const int s = min(hl * Q, n), e = min(s + Q, n), q = e - s;
     SegElim<R> g;
-    seg_forward<R, false>(P.t + base, P.y + base, P.rw + base, nullptr, s, e, g);
+    seg_forward<R, false>(P.ky + base, P.rw + base, nullptr, s, e, g);
     const R xl[3] = {R(0), R(1), R(0)}, xr[3] = {R(0), R(0), R(1)};
     R Z[3];
-    warp_reduced_solve<R, 3, 16>(g, q, (q >= 1) && (e < n), xl, xr, Z);
+    warp_reduced_solve<R, 3, W>(g, q, (q >= 1) && (e < n), xl, xr, Z);
     const int last_lane = n > 0 ? (n - 1) / Q : 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const R f = (k == 0 ? g.alS : R(0)) + g.beS * xl[k] + g.gaS * Z[k];
-        first[k] = __shfl_sync(FULLMASK, f, 0, 16);
-        last[k] = __shfl_sync(FULLMASK, Z[k], last_lane, 16);
+        first[k] = __shfl_sync(FULLMASK, f, 0, W);
+        last[k] = __shfl_sync(FULLMASK, Z[k], last_lane, W);
     }
+}
+
+// The solves with the narrowest lane group that covers the larger envelope's interior
+// with one row per lane (W = 2, 4, 8), else all 16 lanes of the half-warp: cyclic
+// reduction takes log2(W) steps, so tiles with few knots pay for few.
+template <typename R, int TW>
+__device__ __forceinline__ void env_solve_any(WarpPool<R, TW> &P, int base, int m, int hl, int m0,
+                                              int m1, const SolveVals<R> &sv)
+{
+    const int nmax = max(max(m0, m1) - 2, 0);
+    if (nmax <= 2)
+        env_solve<R, TW, 2>(P, base, m, hl, 1, sv, nmax > 0);
+    else if (nmax <= 4)
+        env_solve<R, TW, 4>(P, base, m, hl, 1, sv, true);
+    else if (nmax <= 8)
+        env_solve<R, TW, 8>(P, base, m, hl, 1, sv, true);
+    else
+        env_solve<R, TW, 16>(P, base, m, hl, seg_rows(m0, m1), sv, true);
+}
+
+template <typename R, int TW>
+__device__ __forceinline__ void env_export_any(WarpPool<R, TW> &P, int base, int m, int hl, int m0,
+                                               int m1, R (&first)[3], R (&last)[3])
+{
+    const int nmax = max(max(m0, m1) - 2, 0);
+    if (nmax <= 2)
+        env_export<R, TW, 2>(P, base, m, hl, 1, first, last);
+    else if (nmax <= 4)
+        env_export<R, TW, 4>(P, base, m, hl, 1, first, last);
+    else if (nmax <= 8)
+        env_export<R, TW, 8>(P, base, m, hl, 1, first, last);
+    else
+        env_export<R, TW, 16>(P, base, m, hl, seg_rows(m0, m1), first, last);
 }
 
 // Whole-record 16-byte accesses to the tile records.
@@ -552,24 +617,23 @@ __device__ __forceinline__ TileRec<R> load_rec(const TileRec<R> *p)
     return u.r;
 }
 
+// Asks L2 to fetch [p, p + bytes) ahead of use (p 16-byte aligned, bytes a multiple of
+// 16, the range inside one allocation). No completion is awaited.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------------------------
-// One sifting pass over warp tiles. Grid: NWARP tiles per CTA over every running
-// instance's tiles; warps are independent (no block barrier).
-// The FP32 kernel of 256-sample tiles is shared-memory-limited to 5 CTAs per SM; its
-// register budget is held to that occupancy.
-template <typename R, int SPL, int NWARP>
-__global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 : 1)
-    k_pass(PassArgs pa)
+// One sifting pass over one warp tile (the body of k_pass).
+template <typename R, int SPL>
+__device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * SPL> &P, int64_t gt,
+                                          bool first, bool prefetch_next)
 {
     constexpr int TW = 32 * SPL;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gt = (int64_t)blockIdx.x * NWARP + warp;
-    if (gt >= pa.ntiles)
-        return;
-    WarpPool<R, TW> &P = reinterpret_cast<WarpPool<R, TW> *>(smraw)[warp];
+    const int lane = threadIdx.x & 31;
     const int ii = pa.tile_inst[gt];
-    const State *stp = pa.state + ii;
+    State *stp = pa.state + ii;
     const int mode = stp->mode;
     if (mode == MODE_DONE)
         return;
@@ -577,6 +641,11 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
     const Inst &in = pa.inst[ii];
     const int L = (int)in.L;
     const int lt = (int)(gt - in.tile0);
+    if (lt == 0 && lane == 0) {
+        stp->pass_mode = mode;
+        stp->pass_sift = stp->sift_count;
+        stp->pass_imf = imfc;
+    }
     const int ts = lt * TW;
     const int cnt = min(TW, L - ts);
     const bool hasL = ts > 0, hasR = ts + TW < L;
@@ -586,6 +655,7 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
     double *rdst = in.r[rpar ^ 1] + ts;
     const bool sift = mode == MODE_SIFT || mode == MODE_SIFT_COMMIT;
     const bool commit = mode == MODE_SIFT_COMMIT || mode == MODE_COMMIT;
+    const bool use_r = commit || mode == MODE_INIT;
     const int k0 = lane * SPL;
     const int eh = lane >> 4, hl = lane & 15; // half-warp = envelope in the spline phases
 
@@ -598,15 +668,17 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
         if (lane == 31 && hasR)
             hcr = hsrc[TW];
     }
-    // the residue of a commit (or INIT) pass, fetched together with h
-    const bool use_r = commit || mode == MODE_INIT;
-    double r[SPL], rl = 0.0, rr = 0.0;
-    if (use_r) {
-        loadn<double, SPL>(rsrc, k0, cnt, r);
-        if (lane == 0 && hasL)
-            rl = rsrc[-1];
-        if (lane == 31 && hasR)
-            rr = rsrc[TW];
+    // the residue of a commit (or INIT) pass into L2 now (a warp's first tile; the others
+    // were prefetched by its previous tile), into registers when the sift is done
+    if (first && use_r && lane == 0)
+        prefetch_l2(rsrc, (uint32_t)(((cnt * 8) + 15) & ~15));
+    // the warp's next tile (the same instance and mode) into L2 while this one computes
+    if (prefetch_next && lane == 0 && lt + 1 < in.ntiles) {
+        const int ncnt = min(TW, L - ts - TW);
+        if (mode != MODE_INIT)
+            prefetch_l2(hsrc + TW, (uint32_t)(((ncnt * (int)sizeof(R)) + 15) & ~15));
+        if (use_r)
+            prefetch_l2(rsrc + TW, (uint32_t)(((ncnt * 8) + 15) & ~15));
     }
 
     R pn = R(0), pd = R(0);
@@ -626,27 +698,39 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
         const int b1 = m0 + 2;
         const int base = eh ? b1 : 0, m = eh ? m1 : m0;
         if (hl == 0) {
-            P.t[base] = so.tp - ts;
-            P.y[base] = sv.yp;
-            P.t[base + m + 1] = so.tn - ts;
-            P.y[base + m + 1] = sv.yn;
+            P.ky[base] = KnotY<R>{so.tp - ts, sv.yp};
+            P.ky[base + m + 1] = KnotY<R>{so.tn - ts, sv.yn};
         }
         __syncwarp();
-        env_solve<R, TW>(P, base, m, hl, sv, max(m0, m1) >= 3);
+        env_solve_any<R, TW>(P, base, m, hl, m0, m1, sv);
         __syncwarp();
         // Steps 2-4 at every sample: both envelopes (interval = knots at or before k),
-        // their mean, the subtraction, and the SD partial sums
-        int q0 = bx, q1 = b1 + bn;
+        // their mean, the subtraction, and the SD partial sums. A lane's samples share
+        // few intervals: an interval's cubic is read when a knot starts it, and the local
+        // coordinate u = k - t_left advances by exact integer steps in between.
+        int q0 = bx + (MX & 1u), q1 = b1 + bn + (MN & 1u);
+        Coef<R> c0 = P.cf[q0], c1 = P.cf[q1];
+        int t0 = P.ky[q0].t, t1 = P.ky[q1].t;
 #pragma unroll
         for (int s = 0; s < SPL; ++s) {
-            q0 += (MX >> s) & 1u;
-            q1 += (MN >> s) & 1u;
             const int k = k0 + s;
-            const R e0 = horner(P.cf[q0], R(k - P.t[q0]));
-            const R e1 = horner(P.cf[q1], R(k - P.t[q1]));
+            if (s > 0) {
+                if ((MX >> s) & 1u) { // the knot is the sample itself
+                    ++q0;
+                    c0 = P.cf[q0];
+                    t0 = k;
+                }
+                if ((MN >> s) & 1u) {
+                    ++q1;
+                    c1 = P.cf[q1];
+                    t1 = k;
+                }
+            }
+            const R e0 = horner(c0, R(k - t0));
+            const R e1 = horner(c1, R(k - t1));
             const R mean = radd(e0, e1);
             hn[s] = rsub(v[s], mean);
-            if (k < cnt) {
+            if (pa.need_sd && k < cnt) {
                 pn += mean * mean;
                 pd += v[s] * v[s];
             }
@@ -654,14 +738,16 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
         // halo samples: interval 0 before the tile, interval m after it (where the
         // bracket knot is the sample itself, the knot value, as the neighbour computes it)
         if (lane == 0 && hasL) {
-            const R mean = radd(horner(P.cf[0], R(-1 - P.t[0])), horner(P.cf[b1], R(-1 - P.t[b1])));
+            const R mean = radd(horner(P.cf[0], R(-1 - P.ky[0].t)),
+                                horner(P.cf[b1], R(-1 - P.ky[b1].t)));
             hnl = rsub(hcl, mean);
         }
         if (lane == 31 && hasR) {
-            const R e0 = P.t[m0 + 1] == TW ? rmul(P.y[m0 + 1], R(0.5))
-                                           : horner(P.cf[m0], R(TW - P.t[m0]));
+            const KnotY<R> a0 = P.ky[m0 + 1];
+            const R e0 = a0.t == TW ? rmul(a0.y, R(0.5)) : horner(P.cf[m0], R(TW - P.ky[m0].t));
             const int q = b1 + m1;
-            const R e1 = P.t[q + 1] == TW ? rmul(P.y[q + 1], R(0.5)) : horner(P.cf[q], R(TW - P.t[q]));
+            const KnotY<R> a1 = P.ky[q + 1];
+            const R e1 = a1.t == TW ? rmul(a1.y, R(0.5)) : horner(P.cf[q], R(TW - P.ky[q].t));
             hnr = rsub(hcr, radd(e0, e1));
         }
         __syncwarp(); // the pool is reused for the new signal's knots
@@ -673,6 +759,12 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
 
     // Step 5 / Eq. (1): commit the IMF c, update the FP64 residue, restart from it
     if (use_r) {
+        double r[SPL], rl = 0.0, rr = 0.0;
+        loadn<double, SPL>(rsrc, k0, cnt, r);
+        if (lane == 0 && hasL)
+            rl = rsrc[-1];
+        if (lane == 31 && hasR)
+            rr = rsrc[TW];
         if (commit) {
             double rn[SPL];
 #pragma unroll
@@ -725,15 +817,16 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
         const int base = eh ? m0 + 2 : 0, m = eh ? m1 : m0;
         R f[3] = {R(0), R(0), R(0)}, l[3] = {R(0), R(0), R(0)};
         if (max(m0, m1) >= 3)
-            env_export<R, TW>(P, base, m, hl, f, l);
+            env_export_any<R, TW>(P, base, m, hl, m0, m1, f, l);
         if (hl == 0) {
             TileRec<R> rec;
             rec.n = m;
             const int ix[4] = {0, min(1, m - 1), max(m - 2, 0), m - 1};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                rec.t[q] = m >= 1 ? ts + P.t[base + 1 + ix[q]] : 0;
-                rec.y[q] = m >= 1 ? P.y[base + 1 + ix[q]] : R(0);
+                const KnotY<R> kq = P.ky[base + 1 + ix[q]];
+                rec.t[q] = m >= 1 ? ts + kq.t : 0;
+                rec.y[q] = m >= 1 ? kq.y : R(0);
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -742,6 +835,7 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
             }
             store_rec(reinterpret_cast<TileRec<R> *>(in.tex) + 2 * lt + eh, rec);
         }
+        __syncwarp(); // the pool is reused by the warp's next tile
     }
     storen<R, SPL>(hdst, k0, cnt, hn);
     if (lane == 0 && !hasL)
@@ -752,7 +846,7 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
             if (k0 + s == cnt - 1)
                 in.taux[lt].h_last = (double)hn[s];
     }
-    if (sift) {
+    if (sift && pa.need_sd) {
         pn = warp_sum(pn);
         pd = warp_sum(pd);
         if (lane == 0) {
@@ -762,21 +856,48 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
     }
 }
 
+// One sifting pass over all tiles of every running instance. Persistent grid: warp w
+// takes the contiguous tile range [w C, w C + C) of the launch (C = tiles / warps,
+// rounded up), so its next tile is usually the next tile of the same instance, which
+// it prefetches into L2. Warps are independent (no block barrier).
+// The FP32 kernel of 256-sample tiles is shared-memory-limited to 5 CTAs per SM; its
+// register budget is held to that occupancy.
+template <typename R, int SPL, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 : 1)
+    k_pass(PassArgs pa)
+{
+    constexpr int TW = 32 * SPL;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int warp = threadIdx.x >> 5;
+    WarpPool<R, TW> &P = reinterpret_cast<WarpPool<R, TW> *>(smraw)[warp];
+    const int64_t nw = (int64_t)gridDim.x * NWARP;
+    const int64_t wid = (int64_t)blockIdx.x * NWARP + warp;
+    const int64_t C = (pa.ntiles + nw - 1) / nw;
+    const int64_t g0 = wid * C, g1 = min(g0 + C, pa.ntiles);
+    for (int64_t gt = g0; gt < g1; ++gt)
+        pass_tile<R, SPL>(pa, P, gt, gt == g0, gt + 1 < g1);
+}
+
+
 // ---------------------------------------------------------------------------------
-// Per instance: stop test and state machine, then the reduced interface system of the
-// spline solve for each envelope (threads 0-127: maxima, 128-255: minima).
+// Interface solve: one CTA per instance and envelope (blockIdx.x = 2 instance +
+// envelope). Both CTAs of an instance take the stop test and state-machine step from
+// the same inputs (the pass's snapshot in State and the knot counts of both envelopes);
+// the maxima CTA writes the state. Then the envelope's reduced interface system.
 //
 // Rows of the reduced system are the tile-edge knots in order, [mirrored or end knots]
 // [first/last knot of every non-empty tile][mirrored or end knots]; a tile's interior
 // knots next to its first/last knot are substituted by the tile's elimination
 // (M = x0 + x1 M_first + x2 M_last), which keeps the system tridiagonal. The tile
 // records are read once into a shared (or, for very long instances, global) scratch;
-// every row is then built from the scratch alone. The solve has three levels, one warp
-// per envelope: lane l eliminates its contiguous segment of rows in the working
-// precision, the 32 segment-end unknowns are solved in FP64 by cyclic reduction, and
-// the segments are back-substituted. FP64 work is O(32) per envelope: GB300's FP64 pipe
-// is narrow (a warp-wide FP64 instruction, conversions included, occupies it for many
-// cycles), so the working precision carries everything else.
+// every row is then built from the scratch alone. The solve has three levels in one
+// warp: lane l eliminates its contiguous segment of rows in the working precision, the
+// 32 segment-end unknowns are solved to FP64 accuracy, and the segments are
+// back-substituted. GB300's FP64 pipe is narrow (a warp-wide FP64 instruction,
+// conversions included, occupies it for many cycles), so FP64 work is kept to O(1)
+// instructions per lane: FP32 plans solve the 32-unknown system by FP32 cyclic
+// reduction refined once with its residual evaluated in FP64; FP64 plans run the
+// cyclic reduction in FP64.
 
 // Entry kinds of the reduced system.
 enum EKind : int32_t {
@@ -821,41 +942,96 @@ struct RedScratch {
 
 struct RedShared {
     double sd[kRedThreads / 32][2];
-    int wsu[kRedThreads / 32], wsn[kRedThreads / 32];
+    int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2];
     int next;
 };
+
+// Level 2: the 32 segment-end unknowns (one reduced row per lane, no outside values: the
+// first and last rows are natural ends). FP64 plans: cyclic reduction in FP64.
+__device__ __forceinline__ double level2_solve(const SegElim<double> &g, int q, bool has_next)
+{
+    const double zl[1] = {0.0}, zr[1] = {0.0};
+    double Z[1];
+    warp_reduced_solve<double, 1, 32>(g, q, has_next, zl, zr, Z);
+    return Z[0];
+}
+// FP32 plans: cyclic reduction in FP32, the residual of the reduced rows formed and
+// evaluated in FP64, one FP32 correction solve: the FP64-accurate solution of the
+// system (it is diagonally dominant, condition number a few units).
+__device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, bool has_next)
+{
+    const int lane = threadIdx.x & 31;
+    const float nalS = __shfl_down_sync(FULLMASK, g.alS, 1);
+    const float nbeS = __shfl_down_sync(FULLMASK, g.beS, 1);
+    const float ngaS = __shfl_down_sync(FULLMASK, g.gaS, 1);
+    float A, B, C, D[1], Z[1];
+    reduced_row(g, q, has_next, nalS, nbeS, ngaS, A, B, C, D[0]);
+    pcr_solve<float, 1, 32>(A, B, C, D, Z);
+    SegElim<double> gd;
+    gd.alE = g.alE;
+    gd.beE = g.beE;
+    gd.gaE = g.gaE;
+    gd.al = g.al;
+    gd.bl = g.bl;
+    gd.cl = g.cl;
+    gd.dl = g.dl;
+    double Ad, Bd, Cd, Dd;
+    reduced_row(gd, q, has_next, (double)nalS, (double)nbeS, (double)ngaS, Ad, Bd, Cd, Dd);
+    const double z = (double)Z[0];
+    double zm = __shfl_up_sync(FULLMASK, z, 1), zp = __shfl_down_sync(FULLMASK, z, 1);
+    if (lane == 0)
+        zm = 0.0;
+    if (lane == 31)
+        zp = 0.0;
+    const double res = Dd - (Ad * zm + Bd * z + Cd * zp);
+    float Dr[1] = {(float)res}, dZ[1];
+    pcr_solve<float, 1, 32>(A, B, C, Dr, dZ);
+    return z + (double)dZ[0];
+}
 
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
 {
     __shared__ RedShared S;
-    const int ii = ra.inst_list ? ra.inst_list[blockIdx.x] : (int)blockIdx.x;
+    const int e = blockIdx.x & 1;
+    const int ii = ra.inst_list ? ra.inst_list[blockIdx.x >> 1] : (int)(blockIdx.x >> 1);
     State *st = ra.state + ii;
-    const int pm = st->mode;
-    if (pm == MODE_DONE)
+    if (st->mode == MODE_DONE)
         return;
+    const int pm = st->pass_mode, psift = st->pass_sift, pimf = st->pass_imf;
     const Inst &in = ra.inst[ii];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int e = tid / kRedSeg, te = tid % kRedSeg;
-    constexpr int WPE = kRedSeg / 32; // warps per envelope
+    constexpr int NW = kRedThreads / 32;
     const int nt = in.ntiles;
-    const int TQ = (nt + kRedSeg - 1) / kRedSeg;
-    const int ta = min(te * TQ, nt), tb = min(ta + TQ, nt);
-    // this envelope's record of tile t: tex[2 t]
-    const TileRec<R> *tex = reinterpret_cast<const TileRec<R> *>(in.tex) + e;
+    const int TQ = (nt + kRedThreads - 1) / kRedThreads;
+    const int ta = min(tid * TQ, nt), tb = min(ta + TQ, nt);
+    const TileRec<R> *tex = reinterpret_cast<const TileRec<R> *>(in.tex); // tile t: tex[2 t + e]
 
-    // counts: knots and reduced-system entries (first/last knot) of this thread's tiles
-    int sn = 0, su = 0;
+    // counts: knots of both envelopes and reduced-system entries (first/last knot) of this
+    // envelope over the thread's tiles, and the SD sums of the pass that just ran; the
+    // records of the thread's first two tiles stay in registers for the entries
+    TileRec<R> rk[2];
+    int sn = 0, so_ = 0, su = 0;
+    double a = 0.0, b = 0.0;
+    const bool want_sd = pm == MODE_SIFT && ra.stop == STOP_SD;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (ta + k < tb) {
+            rk[k] = load_rec(tex + 2 * (ta + k) + e);
+            sn += rk[k].n;
+            su += min(rk[k].n, 2);
+        }
+    }
 #pragma unroll 4
-    for (int t = ta; t < tb; ++t) {
-        const int n = tex[2 * t].n;
+    for (int t = ta + 2; t < tb; ++t) {
+        const int n = tex[2 * t + e].n;
         sn += n;
         su += min(n, 2);
     }
-    double a = 0.0, b = 0.0;
-    if (e == 0 && pm == MODE_SIFT) {
 #pragma unroll 4
-        for (int t = ta; t < tb; ++t) {
+    for (int t = ta; t < tb; ++t) {
+        so_ += tex[2 * t + (e ^ 1)].n;
+        if (want_sd) {
             a += in.taux[t].sd_num;
             b += in.taux[t].sd_den;
         }
@@ -867,82 +1043,90 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         if (lane >= o)
             incl += y;
     }
-    const int snw = warp_sum(sn);
+    sn = warp_sum(sn);
+    so_ = warp_sum(so_);
     a = warp_sum(a);
     b = warp_sum(b);
     if (lane == 31)
         S.wsu[warp] = incl;
     if (lane == 0) {
-        S.wsn[warp] = snw;
+        S.wsn[warp][0] = sn;
+        S.wsn[warp][1] = so_;
         S.sd[warp][0] = a;
         S.sd[warp][1] = b;
     }
     __syncthreads();
-    int ubase = incl - su, U = 0, ntot = 0;
+    int ubase = incl - su, U = 0, ntot = 0, nother = 0;
 #pragma unroll
-    for (int w = 0; w < WPE; ++w) {
-        const int ww = e * WPE + w;
-        ubase += ww < warp ? S.wsu[ww] : 0;
-        U += S.wsu[ww];
-        ntot += S.wsn[ww];
+    for (int w = 0; w < NW; ++w) {
+        ubase += w < warp ? S.wsu[w] : 0;
+        U += S.wsu[w];
+        ntot += S.wsn[w][0];
+        nother += S.wsn[w][1];
     }
     if (tid == 0) {
-        int nmax = 0, nmin = 0;
+        const int nmax = e == 0 ? ntot : nother, nmin = e == 0 ? nother : ntot;
         double sdn = 0.0, sdd = 0.0;
-        for (int w = 0; w < WPE; ++w) {
-            nmax += S.wsn[w];
-            nmin += S.wsn[WPE + w];
+        for (int w = 0; w < NW; ++w) {
             sdn += S.sd[w][0];
             sdd += S.sd[w][1];
         }
         const bool ok = nmax >= 1 && nmin >= 1 && nmax + nmin >= 3;
-        State s = *st;
-        s.hpar ^= 1;
-        if (pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT)
-            s.rpar ^= 1;
-        int nm;
+        int imf_count = pimf, sift_count = psift, nm;
+        int committed = -1; // IMF slot whose sift count is recorded
+        double sd = 0.0;
         if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
             if (pm != MODE_INIT) {
-                s.sifts[s.imf_count] = s.sift_count + (pm == MODE_SIFT_COMMIT ? 1 : 0);
-                s.imf_count += 1;
+                committed = imf_count;
+                imf_count += 1;
             }
-            if (s.imf_count >= ra.K || !ok) {
+            if (imf_count >= ra.K || !ok) {
                 nm = MODE_DONE;
             } else {
-                s.sift_count = 0;
                 nm = (ra.stop == STOP_FIXED && ra.fixed_sifts == 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
             }
         } else {
-            s.sift_count += 1;
+            sift_count += 1;
             if (!ok) {
                 nm = MODE_COMMIT;
             } else if (ra.stop == STOP_FIXED) {
-                nm = (s.sift_count >= ra.fixed_sifts - 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
+                nm = (sift_count >= ra.fixed_sifts - 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
             } else {
-                const double sd = sdn / sdd;
-                s.sd = sd;
-                nm = (sd < ra.sd_threshold || s.sift_count >= ra.max_sifts) ? MODE_COMMIT
-                                                                            : MODE_SIFT;
+                sd = sdn / sdd;
+                nm = (sd < ra.sd_threshold || sift_count >= ra.max_sifts) ? MODE_COMMIT
+                                                                          : MODE_SIFT;
             }
         }
-        s.nmax = nmax;
-        s.nmin = nmin;
-        s.mode = nm;
-        *st = s;
         S.next = nm;
-        if (nm != MODE_DONE)
-            atomicAdd(ra.active, 1);
-        if (ra.stats) {
-            // algorithmic bytes per sample of the pass that just ran: h in (w) unless
-            // INIT, h out (w), and for a commit the IMF out (w) and the residue in and
-            // out (16); INIT reads the residue (8)
-            const unsigned long long w = sizeof(R);
-            unsigned long long per = (pm == MODE_INIT) ? 8 + w : 2 * w;
-            if (pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
-                per += w + 16;
-            atomicAdd(&ra.stats->pass_bytes, per * (unsigned long long)in.L);
-            if (pm == MODE_SIFT || pm == MODE_SIFT_COMMIT)
-                atomicAdd(&ra.stats->sample_sifts, (unsigned long long)in.L);
+        if (e == 0) {
+            if (committed >= 0)
+                st->sifts[committed] = sift_count + (pm == MODE_SIFT_COMMIT ? 1 : 0);
+            if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
+                sift_count = 0;
+            st->hpar ^= 1;
+            if (pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT)
+                st->rpar ^= 1;
+            if (pm == MODE_SIFT && ra.stop == STOP_SD)
+                st->sd = sd;
+            st->imf_count = imf_count;
+            st->sift_count = sift_count;
+            st->nmax = nmax;
+            st->nmin = nmin;
+            st->mode = nm;
+            if (nm != MODE_DONE)
+                atomicAdd(ra.active, 1);
+            if (ra.stats) {
+                // algorithmic bytes per sample of the pass that just ran: h in (w) unless
+                // INIT, h out (w), and for a commit the IMF out (w) and the residue in
+                // and out (16); INIT reads the residue (8)
+                const unsigned long long w = sizeof(R);
+                unsigned long long per = (pm == MODE_INIT) ? 8 + w : 2 * w;
+                if (pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
+                    per += w + 16;
+                atomicAdd(&ra.stats->pass_bytes, per * (unsigned long long)in.L);
+                if (pm == MODE_SIFT || pm == MODE_SIFT_COMMIT)
+                    atomicAdd(&ra.stats->sample_sifts, (unsigned long long)in.L);
+            }
         }
     }
     __syncthreads();
@@ -955,7 +1139,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         extern __shared__ __align__(16) unsigned char rsm[];
         const bool shm = ra.smem_entries > 0;
         const int64_t cap = shm ? ra.smem_entries : in.rlen;
-        unsigned char *p0 = shm ? rsm + (size_t)e * red_env_bytes(cap, sizeof(R))
+        unsigned char *p0 = shm ? rsm
                                 : reinterpret_cast<unsigned char *>(in.rscr + (int64_t)e * 8 * cap);
         X.carve(p0, cap);
     }
@@ -963,56 +1147,60 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     const int nr = nl;
     const int NR = nl + U + nr;
     // entries of this thread's tiles, with the substitution data of their rows; records
-    // are fetched four at a time (all loads in flight before any is used)
+    // past the first two are fetched four at a time (all loads in flight before use)
     {
         int p = nl + ubase;
-        for (int t0 = ta; t0 < tb; t0 += 4) {
+        auto put = [&](int t, const TileRec<R> &rc) {
+            const int n = rc.n;
+            X.Tu[t] = (unsigned char)min(n, 2);
+            if (n == 1) {
+                X.Et[p] = rc.t[0];
+                X.Ey[p] = rc.y[0];
+                X.Ek[p] = EK_FL;
+                ++p;
+            } else if (n >= 2) {
+                X.Et[p] = rc.t[0];
+                X.Ey[p] = rc.y[0];
+                X.Et[p + 1] = rc.t[3];
+                X.Ey[p + 1] = rc.y[3];
+                if (n >= 3) {
+                    X.Ek[p] = EK_FS;
+                    X.St[p] = rc.t[1];
+                    X.A[p] = rc.y[1];
+                    X.B[p] = rc.xa[0];
+                    X.C[p] = rc.xa[1];
+                    X.D[p] = rc.xa[2];
+                    X.Ek[p + 1] = EK_LS;
+                    X.St[p + 1] = rc.t[2];
+                    X.A[p + 1] = rc.y[2];
+                    X.B[p + 1] = rc.xb[0];
+                    X.C[p + 1] = rc.xb[1];
+                    X.D[p + 1] = rc.xb[2];
+                } else {
+                    X.Ek[p] = EK_F;
+                    X.Ek[p + 1] = EK_L;
+                }
+                p += 2;
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (ta + k < tb)
+                put(ta + k, rk[k]);
+        for (int t0 = ta + 2; t0 < tb; t0 += 4) {
             TileRec<R> rb[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (t0 + k < tb)
-                    rb[k] = load_rec(tex + 2 * (t0 + k));
+                    rb[k] = load_rec(tex + 2 * (t0 + k) + e);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (t0 + k >= tb)
-                    break;
-                const TileRec<R> &rc = rb[k];
-                const int n = rc.n;
-                X.Tu[t0 + k] = (unsigned char)min(n, 2);
-                if (n == 1) {
-                    X.Et[p] = rc.t[0];
-                    X.Ey[p] = rc.y[0];
-                    X.Ek[p] = EK_FL;
-                    ++p;
-                } else if (n >= 2) {
-                    X.Et[p] = rc.t[0];
-                    X.Ey[p] = rc.y[0];
-                    X.Et[p + 1] = rc.t[3];
-                    X.Ey[p + 1] = rc.y[3];
-                    if (n >= 3) {
-                        X.Ek[p] = EK_FS;
-                        X.St[p] = rc.t[1];
-                        X.A[p] = rc.y[1];
-                        X.B[p] = rc.xa[0];
-                        X.C[p] = rc.xa[1];
-                        X.D[p] = rc.xa[2];
-                        X.Ek[p + 1] = EK_LS;
-                        X.St[p + 1] = rc.t[2];
-                        X.A[p + 1] = rc.y[2];
-                        X.B[p + 1] = rc.xb[0];
-                        X.C[p + 1] = rc.xb[1];
-                        X.D[p + 1] = rc.xb[2];
-                    } else {
-                        X.Ek[p] = EK_F;
-                        X.Ek[p + 1] = EK_L;
-                    }
-                    p += 2;
-                }
-            }
+            for (int k = 0; k < 4; ++k)
+                if (t0 + k < tb)
+                    put(t0 + k, rb[k]);
         }
     }
     __syncthreads();
-    if (te == 0) {
+    if (tid == 0) {
         const int64_t L = in.L;
         if (ra.boundary == BND_MIRROR) {
             // first two and last two knots of the whole signal, reflected about the ends
@@ -1061,7 +1249,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     }
     __syncthreads();
     // rows, every thread a strided share (reads the scratch only; writes its own rows)
-    for (int p = te; p < NR; p += kRedSeg) {
+    for (int p = tid; p < NR; p += kRedThreads) {
         const int k = X.Ek[p];
         R ra_ = R(0), rb = R(1), rc_ = R(0), rd = R(0);
         if (k != EK_FIXED) {
@@ -1104,7 +1292,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         X.D[p] = rd;
     }
     __syncthreads();
-    if (te < 32) {
+    if (warp == 0) {
         // level 1: lane segments of Q1 rows (odd, so the lanes hit distinct banks)
         const int Q1 = ((NR + 31) >> 5) | 1;
         const int rs = min(lane * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
@@ -1143,24 +1331,10 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 g.gaS = xg;
             }
         }
-        // level 2: the 32 segment-end unknowns in FP64 (no outside values: the first and
-        // last rows are natural ends)
-        SegElim<double> gd;
-        gd.alS = (double)g.alS;
-        gd.beS = (double)g.beS;
-        gd.gaS = (double)g.gaS;
-        gd.alE = (double)g.alE;
-        gd.beE = (double)g.beE;
-        gd.gaE = (double)g.gaE;
-        gd.al = (double)g.al;
-        gd.bl = (double)g.bl;
-        gd.cl = (double)g.cl;
-        gd.dl = (double)g.dl;
-        const double zl[1] = {0.0}, zr[1] = {0.0};
-        double Z[1];
-        warp_reduced_solve<double, 1, 32>(gd, rq, (rq >= 1) && (re < NR), zl, zr, Z);
+        // level 2: the segment-end unknowns to FP64 accuracy
+        const double Zd = level2_solve(g, rq, (rq >= 1) && (re < NR));
         // level 3: back-substitution of the segment
-        const R z = (R)Z[0];
+        const R z = (R)Zd;
         R Zp = __shfl_up_sync(FULLMASK, z, 1);
         if (lane == 0)
             Zp = R(0);

@@ -230,11 +230,34 @@ static cudaError_t set_smem_attr()
     return e;
 }
 
+// CTAs of the pass kernel that fit on the current device at once (the persistent grid),
+// computed once per device.
+template <typename R, int TILE>
+static int64_t pass_resident_ctas()
+{
+    constexpr int kMaxDev = 64;
+    static int64_t cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return 152;
+    if (cache[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R, TILE / 32, kPassWarps>,
+                                                          32 * kPassWarps,
+                                                          pass_smem<R, TILE>()) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 152;
+        cache[dev] = (int64_t)std::max(per_sm, 1) * std::max(sms, 1);
+    }
+    return cache[dev];
+}
+
 template <typename R, int TILE>
 static void launch_pass_t(PassArgs pa, int64_t ntiles, cudaStream_t s)
 {
     pa.ntiles = ntiles;
-    const int64_t grid = (ntiles + kPassWarps - 1) / kPassWarps;
+    const int64_t grid =
+        std::min((ntiles + kPassWarps - 1) / kPassWarps, pass_resident_ctas<R, TILE>());
     k_pass<R, TILE / 32, kPassWarps><<<(unsigned)grid, 32 * kPassWarps, pass_smem<R, TILE>(), s>>>(pa);
 }
 
@@ -254,10 +277,11 @@ static size_t reduce_smem(const ReduceArgs &ra)
     return ra.smem_entries > 0 ? reduce_smem_bytes(ra.smem_entries, ra.single ? 4 : 8) : 0;
 }
 
+// One CTA per instance and envelope.
 template <typename R>
-static void launch_reduce(const ReduceArgs &ra, int nblocks, cudaStream_t s)
+static void launch_reduce(const ReduceArgs &ra, int ninst, cudaStream_t s)
 {
-    k_reduce<R><<<nblocks, kRedThreads, reduce_smem(ra), s>>>(ra);
+    k_reduce<R><<<2 * ninst, kRedThreads, reduce_smem(ra), s>>>(ra);
 }
 
 int64_t serial_length(int64_t M, int64_t N, int64_t D) { return M * N + D * N - D; }
@@ -475,13 +499,15 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
 }
 
 template <typename R>
-static void launch_pass(Workspace &ws, int64_t ntiles, cudaStream_t s)
+static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, cudaStream_t s)
 {
     PassArgs pa;
     pa.inst = ws.d_inst;
     pa.state = ws.d_state;
     pa.tile_inst = ws.d_tile_inst;
     pa.ntiles = ntiles;
+    pa.need_sd = need_sd ? 1 : 0;
+    pa.pad = 0;
     launch_pass_tiles<R>(ws.tile, pa, ntiles, s);
 }
 
@@ -554,7 +580,7 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
     for (int it = 0; it < iters; ++it) {
         {
             LaunchTimer t(prof, s, 0);
-            launch_pass<R>(ws, ntiles, s);
+            launch_pass<R>(ws, ntiles, p.stop == SEMD_STOP_SD, s);
         }
         ra.active = ws.d_active + it;
         {
@@ -744,9 +770,9 @@ semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, 
     p.max_imfs = 1;
     ReduceArgs ra = reduce_args(ws, p);
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, 8, s));
-    launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
+    launch_pass<R>(ws, ntiles, true, s); // INIT: h = r, export
     launch_reduce<R>(ra, 1, s);
-    launch_pass<R>(ws, ntiles, s); // SIFT
+    launch_pass<R>(ws, ntiles, true, s); // SIFT
     SEMD_CU(cudaGetLastError());
     SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
     SEMD_CU(cudaStreamSynchronize(s));
@@ -1246,9 +1272,9 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     q.fixed_sifts = 1000; // stay in SIFT mode
     q.max_imfs = 1;
     ReduceArgs ra = reduce_args(ws, q);
-    launch_pass<R>(ws, ntiles, s); // INIT: h = r, export
+    launch_pass<R>(ws, ntiles, true, s); // INIT: h = r, export
     launch_reduce<R>(ra, 1, s);
-    launch_pass<R>(ws, ntiles, s); // SIFT
+    launch_pass<R>(ws, ntiles, true, s); // SIFT
     k_noalloc_result<<<1, 32, 0, s>>>(ws.d_state, ws.d_taux, ntiles, d_result);
     SEMD_CU(cudaGetLastError());
     double res[3];

@@ -90,13 +90,19 @@ struct State {
     int32_t mode, hpar, rpar, imf_count, sift_count, nmax, nmin, pad;
     double sd;
     int32_t sifts[KMAX];
+    // written by the pass kernel (the instance's first tile): the mode, sift and IMF
+    // counts the pass ran with, so that both interface-solve CTAs of an instance read
+    // the same inputs while one of them updates the fields above
+    int32_t pass_mode, pass_sift, pass_imf, pad2;
 };
 
 struct PassArgs {
     const Inst *inst;
-    const State *state;
+    State *state;
     const int32_t *tile_inst; // launch tile -> instance index
-    int64_t ntiles;           // tiles in the launch (the grid is rounded up to whole CTAs)
+    int64_t ntiles;           // tiles in the launch
+    int32_t need_sd;          // 1: accumulate the SD sums (SD stop rule, single-sift calls)
+    int32_t pad;
 };
 
 struct ReduceArgs {
@@ -113,9 +119,8 @@ struct ReduceArgs {
     int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
 };
 
-// Threads of the interface-solve kernel: half per envelope.
+// Threads of the interface-solve kernel (one CTA per instance and envelope).
 constexpr int kRedThreads = 256;
-constexpr int kRedSeg = kRedThreads / 2;
 
 // Scratch of k_reduce for one envelope of `entries` entries: six arrays in the working
 // precision, three of 32-bit integers and one of bytes, rounded to 16 bytes.
@@ -123,10 +128,10 @@ __host__ __device__ constexpr size_t red_env_bytes(int64_t entries, size_t elem)
 {
     return ((size_t)entries * (6 * elem + 13) + 15) & ~(size_t)15;
 }
-// Shared memory of k_reduce when both envelopes' scratch lives there.
+// Shared memory of one k_reduce CTA when its scratch lives there.
 __host__ __device__ constexpr size_t reduce_smem_bytes(int64_t entries, size_t elem)
 {
-    return 2 * red_env_bytes(entries, elem);
+    return red_env_bytes(entries, elem);
 }
 
 // Entries of the reduced system of an instance with nt tiles (per envelope).
