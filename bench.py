@@ -421,11 +421,16 @@ def arm_ours(args):
             line["fp32_imf_rel_l2_given_input"] = fp32_imf_errors_given_input(wl, r32)
         if not args.no_batched:
             line["batched"] = batched_eemd(args, device, flush, peak, peak_kind, world)
+            line["batched_images"] = batched_images(args, device, flush, peak, peak_kind,
+                                                    world)
+        if not args.no_serving:
+            line["serving"] = serving(args, device)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
     elif not args.no_batched:
         batched_eemd(args, device, flush, peak, peak_kind, world)
+        batched_images(args, device, flush, peak, peak_kind, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -453,6 +458,121 @@ def batched_eemd(args, device, flush, peak, peak_kind, world):
     return out
 
 
+def batched_images(args, device, flush, peak, peak_kind, world):
+    """The batched uneven-images workload: 2048 blob-field images (side U{32..128}),
+    row-serialized (D = 0), FP32-mixed, SD stop 0.2 (at most 50 sifts), <= 8 IMFs, every
+    instance in each pass launch; the host checks for completion every 8 passes."""
+    import torch
+    from paper_2106_15319_gb300 import capi, synth
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    imgs = synth.workload_uneven_images(args.images)
+    side = max(im.shape[0] for im in imgs)
+    p = make_params(side, side, precision=capi.FP32_MIXED, transition_len=0, max_imfs=8,
+                    stop=capi.STOP_SD, sd_threshold=0.2, max_sifts=50)
+    plan = Plan(p, max_batch=len(imgs))
+    xs = [torch.from_numpy(np.ascontiguousarray(im, np.float32)).to(device) for im in imgs]
+    outs = [plan.outputs(*x.shape, device=device) for x in xs]
+    stream = torch.cuda.Stream(device)
+    steps = max(1, min(args.steps, 5))
+    with torch.cuda.stream(stream):
+        for _ in range(min(args.warmup, 3)):
+            plan.decompose_batch(xs, outs, stream=stream, wait=False)
+        stream.synchronize()
+        ms = []
+        for _ in range(steps):
+            _flush_l2(flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.decompose_batch(xs, outs, stream=stream, wait=False)
+            b.record(stream)
+            stream.synchronize()
+            ms.append(a.elapsed_time(b))
+    st = plan.stats()
+    ms_step = max_over_ranks(statistics.mean(ms), world)
+    samples = sum(int(x.numel()) for x in xs)
+    plan.set_options(use_graphs=True, profile=True)
+    with torch.cuda.stream(stream):
+        _flush_l2(flush)
+        plan.decompose_batch(xs, outs, stream=stream, wait=False)
+        stream.synchronize()
+    pr = plan.stats()
+    pass_avg_ms = pr.pass_ms / max(1, pr.pass_launches)
+    bpl = pr.pass_bytes / max(1, pr.pass_launches)
+    ach = bpl / (pass_avg_ms * 1e-3) / 1e9
+    n_imfs, sifts = plan.counts(len(xs))
+    plan.close()
+    return {"workload": f"{len(xs)} uneven blob-field images, side U{{32..128}} "
+                        f"({samples} samples), row-serialized D=0, SD stop 0.2 (max 50 "
+                        "sifts), <=8 IMFs, all instances in every pass launch",
+            "value": world * st.sample_sifts / (ms_step * 1e-3), "unit": UNIT,
+            "ms_per_step": ms_step, "steps": steps, "dtype": "f32",
+            "sifts_per_imf_mean": float(np.sum(sifts)) / max(1, int(np.sum(n_imfs))),
+            "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": ach,
+                         "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "peak_source": peak_kind, "avg_launch_us": pass_avg_ms * 1e3,
+                         "bytes_per_launch": bpl, "launches": pr.pass_launches,
+                         "reduce_avg_us": pr.reduce_ms / max(1, pr.reduce_launches) * 1e3}}
+
+
+def serving(args, device):
+    """The serving mix: Poisson arrivals of requests, half tone+chirp series (2..16
+    channels x 1k..64k samples), half grating images (side 32..1024 px, plus a 2 % tail
+    of 2048^2 images), transitions D = round(0.2 M), FP32-mixed, 10 sifts/IMF, <= 10
+    IMFs, one server with a 40 GB device budget and 64 slots. Each rate's requests are
+    submitted at their arrival times; latency is the server's submit -> outputs-written
+    time (queue + run)."""
+    import time as _t
+    import torch
+    from paper_2106_15319_gb300 import capi, synth
+    from paper_2106_15319_gb300.serial_emd import Server, make_params, serialized_length
+    base = make_params(2048, 2048, precision=capi.FP32_MIXED, transition_len=-1, max_imfs=10,
+                       fixed_sifts=10)
+    out = {"workload": "serving mix: Poisson arrivals; 50% series 2..16 ch x 1k..64k, 50% "
+                       "images 32..1024 px (+2% 2048^2), D=round(0.2 M), FP32-mixed, 10 "
+                       "sifts/IMF, <=10 IMFs, 40 GB budget, 64 slots",
+           "latency": "submit -> outputs written, measured by the server", "rates": []}
+    server = Server(base, 40 << 30, 64)
+    try:
+        for rate in args.serve_rates:
+            mix = synth.serving_mix(args.serve_requests, 20210629 + 5, rate)
+            xs = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+                  for _, _, a in mix]
+            outs = [server.outputs(*x.shape, device=device) for x in xs]
+            torch.cuda.synchronize()
+            pend, res = {}, {}
+            t0 = _t.perf_counter()
+            i = 0
+            while i < len(mix) or pend:
+                now = _t.perf_counter() - t0
+                while i < len(mix) and mix[i][0] <= now:
+                    t, _, _ = server.submit(xs[i], outs[i][0], outs[i][1])
+                    pend[t] = i
+                    i += 1
+                for t in list(pend):
+                    r = server.poll(t)
+                    if r is not None:
+                        res[pend.pop(t)] = (r, _t.perf_counter() - t0)
+                if i < len(mix) and not pend:
+                    _t.sleep(max(0.0, min(mix[i][0] - now, 0.002)))
+                elif pend:
+                    _t.sleep(0.0002)
+            wall = max(v[1] for v in res.values()) - mix[0][0]
+            lat = np.array([r.queue_ms + r.run_ms for r, _ in res.values()])
+            ss = sum(r.sifts * serialized_length(*xs[k].shape) for k, (r, _) in res.items())
+            ok = all(r.status == capi.SEMD_OK for r, _ in res.values())
+            out["rates"].append({
+                "rate_hz": rate, "requests": len(mix), "all_ok": bool(ok),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()),
+                "served_per_s": len(mix) / wall, "samples_sifts_per_s": ss / wall,
+                "samples": int(sum(serialized_length(*x.shape) for x in xs))})
+            del xs, outs
+    finally:
+        server.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +586,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="pass-kernel tile (0: the plan's)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--images", type=int, default=2048, help="batched uneven images")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 300.0, 1000.0])
+    ap.add_argument("--serve-requests", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
