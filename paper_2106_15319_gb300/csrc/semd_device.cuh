@@ -68,6 +68,12 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Programmatic dependent launch: let the stream's next kernel start its CTAs now (they
+// wait in pdl_wait), and wait until the previous kernel has completed and its writes are
+// visible. Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // De-serialized destination of serialized sample p (Sec. 3.3): returns false for
 // transition samples, which the de-serialization drops.
 __device__ __forceinline__ bool deser_index(int64_t p, int64_t M, int64_t N, int64_t D, int order,
@@ -631,6 +637,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         stp->pass_mode = mode;
         stp->pass_sift = stp->sift_count;
         stp->pass_imf = imfc;
+        stp->pass_par = hpar | (rpar << 1);
     }
     const int ts = lt * TW;
     const int cnt = min(TW, L - ts);
@@ -679,7 +686,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         uint32_t MX, MN;
         int bx, bn, m0, m1;
         warp_knots<R, SPL, TW>(P, v, left, right, k0, ts + k0, cnt, L, MX, MN, bx, bn, m0, m1);
-        const TileSolve &so = in.tsol[2 * lt + eh];
+        const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
         const SolveVals<R> sv = solve_vals(so, R(0));
         const int b1 = m0 + 2;
         const int base = eh ? b1 : 0, m = eh ? m1 : m0;
@@ -819,7 +826,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
                 rec.xa[q] = m >= 3 ? f[q] : R(0);
                 rec.xb[q] = m >= 3 ? l[q] : R(0);
             }
-            store_rec(reinterpret_cast<TileRec<R> *>(in.tex) + 2 * lt + eh, rec);
+            store_rec(reinterpret_cast<TileRec<R> *>(in.tex) + (int64_t)eh * in.ntiles + lt, rec);
         }
         __syncwarp(); // the pool is reused by the warp's next tile
     }
@@ -854,6 +861,8 @@ __global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 :
 {
     constexpr int TW = 32 * SPL;
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_trigger();
+    pdl_wait();
     const int warp = threadIdx.x >> 5;
     WarpPool<R, TW> &P = reinterpret_cast<WarpPool<R, TW> *>(smraw)[warp];
     const int64_t nw = (int64_t)gridDim.x * NWARP;
@@ -903,11 +912,12 @@ enum EKind : int32_t {
 //              (B, C, D = x0, x1, x2); then the row (a, b, c, d); then, for the rows a
 //              segment eliminates, (bp, b, cp, dp)
 //   MV       - solved second derivative
+//   To       - per tile: the index of its first entry
 //   Tu       - per tile: its number of entries (0, 1 or 2)
 template <typename R>
 struct RedScratch {
     R *Ey, *A, *B, *C, *D, *MV;
-    int *Et, *Ek, *St;
+    int *Et, *Ek, *St, *To;
     unsigned char *Tu;
     __device__ void carve(unsigned char *p, int64_t cap)
     {
@@ -922,7 +932,8 @@ struct RedScratch {
         Et = q;
         Ek = q + cap;
         St = q + 2 * cap;
-        Tu = reinterpret_cast<unsigned char *>(q + 3 * cap);
+        To = q + 3 * cap;
+        Tu = reinterpret_cast<unsigned char *>(q + 4 * cap);
     }
 };
 
@@ -979,62 +990,73 @@ template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
 {
     __shared__ RedShared S;
+    pdl_trigger();
     const int e = blockIdx.x & 1;
     const int ii = ra.inst_list ? ra.inst_list[blockIdx.x >> 1] : (int)(blockIdx.x >> 1);
+    // the instance descriptor does not change during a decomposition: read it while the
+    // pass kernel finishes
+    const Inst &in = ra.inst[ii];
+    const int nt = in.ntiles;
+    const TileRec<R> *texe = reinterpret_cast<const TileRec<R> *>(in.tex) + (int64_t)e * nt;
+    const TileRec<R> *texo = reinterpret_cast<const TileRec<R> *>(in.tex) + (int64_t)(e ^ 1) * nt;
+    TileSolve *tsol = in.tsol + (int64_t)e * nt;
+    const TileAux *taux = in.taux;
+    RedScratch<R> X;
+    {
+        extern __shared__ __align__(16) unsigned char rsm[];
+        const bool shm = ra.smem_entries > 0;
+        const int64_t cap = shm ? ra.smem_entries : in.rlen;
+        unsigned char *p0 = shm ? rsm
+                                : reinterpret_cast<unsigned char *>(in.rscr + (int64_t)e * 8 * cap);
+        X.carve(p0, cap);
+    }
+    pdl_wait();
     State *st = ra.state + ii;
     if (st->mode == MODE_DONE)
         return;
     const int pm = st->pass_mode, psift = st->pass_sift, pimf = st->pass_imf;
-    const Inst &in = ra.inst[ii];
+    const int ppar = st->pass_par;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int NW = kRedThreads / 32;
-    const int nt = in.ntiles;
-    const int TQ = (nt + kRedThreads - 1) / kRedThreads;
-    const int ta = min(tid * TQ, nt), tb = min(ta + TQ, nt);
-    const TileRec<R> *tex = reinterpret_cast<const TileRec<R> *>(in.tex); // tile t: tex[2 t + e]
 
-    // counts: knots of both envelopes and reduced-system entries (first/last knot) of this
-    // envelope over the thread's tiles, and the SD sums of the pass that just ran; the
-    // records of the thread's first two tiles stay in registers for the entries
-    TileRec<R> rk[2];
-    int sn = 0, so_ = 0, su = 0;
+    // counts: knots of both envelopes, this envelope's reduced-system entries per tile
+    // (first/last knot) and the SD sums of the pass that just ran. Tiles are taken in a
+    // stride of the block, four per thread at a time, every load in flight before use.
+    int sn = 0, so_ = 0;
     double a = 0.0, b = 0.0;
     const bool want_sd = pm == MODE_SIFT && ra.stop == STOP_SD;
+    for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+        int ne[4], no[4];
+        double sa[4], sb[4];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (ta + k < tb) {
-            rk[k] = load_rec(tex + 2 * (ta + k) + e);
-            sn += rk[k].n;
-            su += min(rk[k].n, 2);
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + tid + k * kRedThreads;
+            ne[k] = no[k] = 0;
+            sa[k] = sb[k] = 0.0;
+            if (t < nt) {
+                ne[k] = texe[t].n;
+                no[k] = texo[t].n;
+                if (want_sd) {
+                    sa[k] = taux[t].sd_num;
+                    sb[k] = taux[t].sd_den;
+                }
+            }
         }
-    }
-#pragma unroll 4
-    for (int t = ta + 2; t < tb; ++t) {
-        const int n = tex[2 * t + e].n;
-        sn += n;
-        su += min(n, 2);
-    }
-#pragma unroll 4
-    for (int t = ta; t < tb; ++t) {
-        so_ += tex[2 * t + (e ^ 1)].n;
-        if (want_sd) {
-            a += in.taux[t].sd_num;
-            b += in.taux[t].sd_den;
-        }
-    }
-    int incl = su;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULLMASK, incl, o);
-        if (lane >= o)
-            incl += y;
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + tid + k * kRedThreads;
+            if (t < nt)
+                X.Tu[t] = (unsigned char)min(ne[k], 2);
+            sn += ne[k];
+            so_ += no[k];
+            a += sa[k];
+            b += sb[k];
+        }
     }
     sn = warp_sum(sn);
     so_ = warp_sum(so_);
     a = warp_sum(a);
     b = warp_sum(b);
-    if (lane == 31)
-        S.wsu[warp] = incl;
     if (lane == 0) {
         S.wsn[warp][0] = sn;
         S.wsn[warp][1] = so_;
@@ -1042,11 +1064,25 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         S.sd[warp][1] = b;
     }
     __syncthreads();
-    int ubase = incl - su, U = 0, ntot = 0, nother = 0;
+    // entry offsets: each thread sums a contiguous chunk of tiles, a block scan of the
+    // chunk sums, then the chunk's per-tile offsets
+    const int CH = (nt + kRedThreads - 1) / kRedThreads;
+    const int ca = min(tid * CH, nt), cb = min(ca + CH, nt);
+    int su = 0;
+    for (int t = ca; t < cb; ++t)
+        su += X.Tu[t];
+    int incl = su;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        S.wsu[warp] = incl;
+    int ntot = 0, nother = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-        ubase += w < warp ? S.wsu[w] : 0;
-        U += S.wsu[w];
         ntot += S.wsn[w][0];
         nother += S.wsn[w][1];
     }
@@ -1089,9 +1125,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 st->sifts[committed] = sift_count + (pm == MODE_SIFT_COMMIT ? 1 : 0);
             if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
                 sift_count = 0;
-            st->hpar ^= 1;
-            if (pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT)
-                st->rpar ^= 1;
+            st->hpar = (ppar & 1) ^ 1;
+            st->rpar = ((ppar >> 1) & 1) ^ ((pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT) ? 1 : 0);
             if (pm == MODE_SIFT && ra.stop == STOP_SD)
                 st->sd = sd;
             st->imf_count = imf_count;
@@ -1116,34 +1151,48 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         }
     }
     __syncthreads();
+    int ubase = incl - su, U = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        ubase += w < warp ? S.wsu[w] : 0;
+        U += S.wsu[w];
+    }
     const int nm = S.next;
     if (nm != MODE_SIFT && nm != MODE_SIFT_COMMIT)
         return;
-
-    RedScratch<R> X;
-    {
-        extern __shared__ __align__(16) unsigned char rsm[];
-        const bool shm = ra.smem_entries > 0;
-        const int64_t cap = shm ? ra.smem_entries : in.rlen;
-        unsigned char *p0 = shm ? rsm
-                                : reinterpret_cast<unsigned char *>(in.rscr + (int64_t)e * 8 * cap);
-        X.carve(p0, cap);
-    }
     const int nl = ra.boundary == BND_MIRROR ? min(ra.mirror_knots, ntot) : 1;
     const int nr = nl;
     const int NR = nl + U + nr;
-    // entries of this thread's tiles, with the substitution data of their rows; records
-    // past the first two are fetched four at a time (all loads in flight before use)
     {
         int p = nl + ubase;
-        auto put = [&](int t, const TileRec<R> &rc) {
+        for (int t = ca; t < cb; ++t) {
+            X.To[t] = p;
+            p += X.Tu[t];
+        }
+    }
+    __syncthreads();
+    // entries, with the substitution data of their rows: tiles in a stride of the block,
+    // four records per thread in flight at a time
+    for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+        TileRec<R> rb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + tid + k * kRedThreads;
+            if (t < nt)
+                rb[k] = load_rec(texe + t);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + tid + k * kRedThreads;
+            if (t >= nt)
+                break;
+            const TileRec<R> &rc = rb[k];
             const int n = rc.n;
-            X.Tu[t] = (unsigned char)min(n, 2);
+            const int p = X.To[t];
             if (n == 1) {
                 X.Et[p] = rc.t[0];
                 X.Ey[p] = rc.y[0];
                 X.Ek[p] = EK_FL;
-                ++p;
             } else if (n >= 2) {
                 X.Et[p] = rc.t[0];
                 X.Ey[p] = rc.y[0];
@@ -1166,23 +1215,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                     X.Ek[p] = EK_F;
                     X.Ek[p + 1] = EK_L;
                 }
-                p += 2;
             }
-        };
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            if (ta + k < tb)
-                put(ta + k, rk[k]);
-        for (int t0 = ta + 2; t0 < tb; t0 += 4) {
-            TileRec<R> rb[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (t0 + k < tb)
-                    rb[k] = load_rec(tex + 2 * (t0 + k) + e);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (t0 + k < tb)
-                    put(t0 + k, rb[k]);
         }
     }
     __syncthreads();
@@ -1333,29 +1366,25 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         }
     }
     __syncthreads();
-    {
-        int p = nl + ubase;
-        for (int t = ta; t < tb; ++t) {
-            const int u = X.Tu[t];
-            TileSolve *so = in.tsol + 2 * t + e;
-            const R yp = X.Ey[p - 1], Mp = X.MV[p - 1], yn = X.Ey[p + u], Mn = X.MV[p + u];
-            const R MF = u >= 1 ? X.MV[p] : R(0), ML = u >= 1 ? X.MV[p + u - 1] : R(0);
-            so->tp = X.Et[p - 1];
-            so->tn = X.Et[p + u];
-            if (sizeof(R) == 4) {
-                // FP32 pass kernels read the single-precision values only
-                *reinterpret_cast<float4 *>(&so->f[0]) =
-                    make_float4((float)MF, (float)ML, (float)yp, (float)Mp);
-                *reinterpret_cast<float2 *>(&so->f[4]) = make_float2((float)yn, (float)Mn);
-            } else {
-                so->MF = (double)MF;
-                so->ML = (double)ML;
-                so->yp = (double)yp;
-                so->Mp = (double)Mp;
-                so->yn = (double)yn;
-                so->Mn = (double)Mn;
-            }
-            p += u;
+    for (int t = tid; t < nt; t += kRedThreads) {
+        const int u = X.Tu[t], p = X.To[t];
+        TileSolve *so = tsol + t;
+        const R yp = X.Ey[p - 1], Mp = X.MV[p - 1], yn = X.Ey[p + u], Mn = X.MV[p + u];
+        const R MF = u >= 1 ? X.MV[p] : R(0), ML = u >= 1 ? X.MV[p + u - 1] : R(0);
+        so->tp = X.Et[p - 1];
+        so->tn = X.Et[p + u];
+        if (sizeof(R) == 4) {
+            // FP32 pass kernels read the single-precision values only
+            *reinterpret_cast<float4 *>(&so->f[0]) =
+                make_float4((float)MF, (float)ML, (float)yp, (float)Mp);
+            *reinterpret_cast<float2 *>(&so->f[4]) = make_float2((float)yn, (float)Mn);
+        } else {
+            so->MF = (double)MF;
+            so->ML = (double)ML;
+            so->yp = (double)yp;
+            so->Mp = (double)Mp;
+            so->yn = (double)yn;
+            so->Mn = (double)Mn;
         }
     }
 }

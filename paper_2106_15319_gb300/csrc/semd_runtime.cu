@@ -252,13 +252,34 @@ static int64_t pass_resident_ctas()
     return cache[dev];
 }
 
+// Launches with programmatic stream serialization: the kernel's CTAs may start while the
+// previous kernel of the stream finishes (each waits in pdl_wait before reading its
+// results), which hides the launch gap between the passes and the interface solves.
+template <typename K, typename A>
+static void launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       const A &arg)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, arg);
+}
+
 template <typename R, int TILE>
 static void launch_pass_t(PassArgs pa, int64_t ntiles, cudaStream_t s)
 {
     pa.ntiles = ntiles;
     const int64_t grid =
         std::min((ntiles + kPassWarps - 1) / kPassWarps, pass_resident_ctas<R, TILE>());
-    k_pass<R, TILE / 32, kPassWarps><<<(unsigned)grid, 32 * kPassWarps, pass_smem<R, TILE>(), s>>>(pa);
+    launch_pdl(k_pass<R, TILE / 32, kPassWarps>, (unsigned)grid, 32 * kPassWarps,
+               pass_smem<R, TILE>(), s, pa);
 }
 
 template <typename R>
@@ -281,7 +302,7 @@ static size_t reduce_smem(const ReduceArgs &ra)
 template <typename R>
 static void launch_reduce(const ReduceArgs &ra, int ninst, cudaStream_t s)
 {
-    k_reduce<R><<<2 * ninst, kRedThreads, reduce_smem(ra), s>>>(ra);
+    launch_pdl(k_reduce<R>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s, ra);
 }
 
 int64_t serial_length(int64_t M, int64_t N, int64_t D) { return M * N + D * N - D; }

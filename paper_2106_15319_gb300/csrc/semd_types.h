@@ -93,7 +93,7 @@ struct State {
     // written by the pass kernel (the instance's first tile): the mode, sift and IMF
     // counts the pass ran with, so that both interface-solve CTAs of an instance read
     // the same inputs while one of them updates the fields above
-    int32_t pass_mode, pass_sift, pass_imf, pad2;
+    int32_t pass_mode, pass_sift, pass_imf, pass_par; // pass_par: hpar | rpar << 1
 };
 
 struct PassArgs {
@@ -123,10 +123,10 @@ struct ReduceArgs {
 constexpr int kRedThreads = 256;
 
 // Scratch of k_reduce for one envelope of `entries` entries: six arrays in the working
-// precision, three of 32-bit integers and one of bytes, rounded to 16 bytes.
+// precision, four of 32-bit integers and one of bytes, rounded to 16 bytes.
 __host__ __device__ constexpr size_t red_env_bytes(int64_t entries, size_t elem)
 {
-    return ((size_t)entries * (6 * elem + 13) + 15) & ~(size_t)15;
+    return ((size_t)entries * (6 * elem + 17) + 15) & ~(size_t)15;
 }
 // Shared memory of one k_reduce CTA when its scratch lives there.
 __host__ __device__ constexpr size_t reduce_smem_bytes(int64_t entries, size_t elem)
