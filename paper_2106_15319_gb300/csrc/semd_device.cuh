@@ -938,6 +938,8 @@ struct RedScratch {
 };
 
 struct RedShared {
+    double lev[14 * kRedThreads]; // level-1 results (10 arrays), level-1.5 scratch (4), in R
+    int segq[kRedThreads];        // rows per level-1 segment
     double sd[kRedThreads / 32][2];
     int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2];
     int next;
@@ -1311,13 +1313,18 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         X.D[p] = rd;
     }
     __syncthreads();
-    if (warp == 0) {
-        // level 1: lane segments of Q1 rows (odd, so the lanes hit distinct banks)
-        const int Q1 = ((NR + 31) >> 5) | 1;
-        const int rs = min(lane * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
+    // level 1: every thread eliminates a contiguous segment of Q1 rows (Q1 odd, so the
+    // lanes of a warp hit distinct banks); its result goes to shared memory
+    R *lev = reinterpret_cast<R *>(S.lev);
+    constexpr int NS = kRedThreads;      // level-1 segments
+    constexpr int G = kRedThreads / 32;  // segments per lane of the level-1.5 warp
+    {
+        const int Q1 = ((NR + NS - 1) / NS) | 1;
+        const int rs = min(tid * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
         SegElim<R> g;
         if (rq >= 1) {
             R cprev = R(0), dprev = R(0), bprev = R(1);
+#pragma unroll 4
             for (int j = rs; j < re - 1; ++j) {
                 const R A = X.A[j], B = X.B[j], C = X.C[j], D = X.D[j];
                 const R inv = rrcp(B - A * cprev);
@@ -1337,6 +1344,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 g.beE = bprev;
                 g.gaE = -cprev;
                 R xa = g.alE, xb = g.beE, xg = g.gaE;
+#pragma unroll 4
                 for (int j = re - 3; j >= rs; --j) {
                     const R c = X.C[j];
                     xa = X.D[j] - c * xa;
@@ -1348,16 +1356,87 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 g.gaS = xg;
             }
         }
-        // level 2: the segment-end unknowns to FP64 accuracy
-        const double Zd = level2_solve(g, rq, (rq >= 1) && (re < NR));
-        // level 3: back-substitution of the segment
+        const R gv[10] = {g.alS, g.beS, g.gaS, g.alE, g.beE, g.gaE, g.al, g.bl, g.cl, g.dl};
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+            lev[k * NS + tid] = gv[k];
+        S.segq[tid] = rq;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // level 1.5: the NS segment-end unknowns; lane l eliminates the reduced rows of
+        // segments G l .. G l + G - 1 (row j couples Z_{j-1}, Z_j, Z_{j+1})
+        R *cp2 = lev + 10 * NS, *dp2 = lev + 11 * NS, *bp2 = lev + 12 * NS, *Zs = lev + 13 * NS;
+        const int j0 = lane * G;
+        auto red_row = [&](int j, R &A, R &B, R &C, R &D) {
+            SegElim<R> gj;
+            gj.alE = lev[3 * NS + j];
+            gj.beE = lev[4 * NS + j];
+            gj.gaE = lev[5 * NS + j];
+            gj.al = lev[6 * NS + j];
+            gj.bl = lev[7 * NS + j];
+            gj.cl = lev[8 * NS + j];
+            gj.dl = lev[9 * NS + j];
+            const bool hn = j + 1 < NS && S.segq[j + 1] >= 1;
+            const R nalS = hn ? lev[j + 1] : R(0), nbeS = hn ? lev[NS + j + 1] : R(0);
+            const R ngaS = hn ? lev[2 * NS + j + 1] : R(0);
+            reduced_row(gj, S.segq[j], hn, nalS, nbeS, ngaS, A, B, C, D);
+        };
+        SegElim<R> g2;
+        R cprev = R(0), dprev = R(0), bprev = R(1);
+#pragma unroll
+        for (int k = 0; k < G - 1; ++k) {
+            R A, B, C, D;
+            red_row(j0 + k, A, B, C, D);
+            const R inv = rrcp(B - A * cprev);
+            cprev = C * inv;
+            dprev = (D - A * dprev) * inv;
+            bprev = -A * bprev * inv;
+            cp2[j0 + k] = cprev;
+            dp2[j0 + k] = dprev;
+            bp2[j0 + k] = bprev;
+        }
+        red_row(j0 + G - 1, g2.al, g2.bl, g2.cl, g2.dl);
+        g2.alE = dprev;
+        g2.beE = bprev;
+        g2.gaE = -cprev;
+        R xa = g2.alE, xb = g2.beE, xg = g2.gaE;
+#pragma unroll
+        for (int k = G - 3; k >= 0; --k) {
+            const R c = cp2[j0 + k];
+            xa = dp2[j0 + k] - c * xa;
+            xb = bp2[j0 + k] - c * xb;
+            xg = -c * xg;
+        }
+        g2.alS = xa;
+        g2.beS = xb;
+        g2.gaS = xg;
+        // level 2: the 32 group-end unknowns to FP64 accuracy
+        const double Zd = level2_solve(g2, G, lane < 31);
         const R z = (R)Zd;
         R Zp = __shfl_up_sync(FULLMASK, z, 1);
         if (lane == 0)
             Zp = R(0);
+        Zs[j0 + G - 1] = z;
+        R xn = z;
+#pragma unroll
+        for (int k = G - 2; k >= 0; --k) {
+            const R x = dp2[j0 + k] + bp2[j0 + k] * Zp - cp2[j0 + k] * xn;
+            Zs[j0 + k] = x;
+            xn = x;
+        }
+    }
+    __syncthreads();
+    {
+        // level 3: back-substitution of this thread's segment
+        const int Q1 = ((NR + NS - 1) / NS) | 1;
+        const int rs = min(tid * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
+        const R *Zs = lev + 13 * NS;
         if (rq >= 1) {
+            const R z = Zs[tid], Zp = tid > 0 ? Zs[tid - 1] : R(0);
             X.MV[re - 1] = z;
             R xn = z;
+#pragma unroll 4
             for (int j = re - 2; j >= rs; --j) {
                 const R x = X.D[j] + X.A[j] * Zp - X.C[j] * xn;
                 X.MV[j] = x;

@@ -17,7 +17,7 @@ constexpr int kMaxTile = 512;
 constexpr int kPassWarps = 4;
 // Largest dynamic shared-memory scratch of the interface solve; larger instances use
 // global memory.
-constexpr size_t kReduceSmemMax = 200 * 1024;
+constexpr size_t kReduceSmemMax = 184 * 1024;
 
 // Device workspace of a plan: one allocation carved up, plus pinned host staging.
 struct Workspace {
