@@ -182,7 +182,7 @@ semd_status serial_emd_sift(semd_plan_t plan, const void *d_h, int64_t L, void *
  * with the envelope rule of params->boundary / params->mirror_knots; the other
  * fields of params are ignored. The sums (h - h')^2 and h^2 are returned through the
  * host pointers, after the call has waited for the stream.
- * Scratch: one static device array of about 2.3 MB, compiled into the library, which
+ * Scratch: one static device array of about 2.4 MB, compiled into the library, which
  * every GPU that loads the library holds until the process exits; nothing is
  * allocated per call (no cudaMalloc, cudaFree or allocating library routine). L
  * must be in [1, 65536]: a larger L returns SEMD_EINVAL with a message naming the

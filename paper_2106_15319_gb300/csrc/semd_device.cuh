@@ -263,15 +263,25 @@ struct WarpPool {
 // kernels read the single-precision values, so they issue no FP64 conversions).
 template <typename R>
 struct SolveVals {
-    R MF, ML, yp, Mp, yn, Mn;
+    R MF, ML, yp, Mp, yn, Mn, M1, M2;
 };
 __device__ __forceinline__ SolveVals<float> solve_vals(const TileSolve &so, float)
 {
-    return {so.f[0], so.f[1], so.f[2], so.f[3], so.f[4], so.f[5]};
+    const float4 a = *reinterpret_cast<const float4 *>(&so.f[0]);
+    const float4 b = *reinterpret_cast<const float4 *>(&so.f[4]);
+    return {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 }
 __device__ __forceinline__ SolveVals<double> solve_vals(const TileSolve &so, double)
 {
-    return {so.MF, so.ML, so.yp, so.Mp, so.yn, so.Mn};
+    return {so.MF, so.ML, so.yp, so.Mp, so.yn, so.Mn, so.M1, so.M2};
+}
+
+// Second derivative of knot j of an envelope with m <= kSparseKnots knots, all of which
+// the interface solve determined.
+template <typename R>
+__device__ __forceinline__ R sparse_M(const SolveVals<R> &sv, int j, int m)
+{
+    return j == 0 ? sv.MF : (j == m - 1 ? sv.ML : (j == 1 ? sv.M1 : sv.M2));
 }
 
 // N consecutive values through 16-byte vector accesses (p 16-byte aligned).
@@ -463,41 +473,38 @@ __device__ __forceinline__ Coef<R> slot_cubic(const KnotY<R> *K, int q, R Ml, R 
     return half_cubic<R>(a.t, a.y, Ml, b.t, b.y, Mr);
 }
 
-// Rows per lane of the half-warp solves: odd (16 lanes walking runs of Q rows hit
-// distinct banks) and common to both envelopes (the half-warps run in lock-step anyway).
-__device__ __forceinline__ int seg_rows(int m0, int m1)
-{
-    return ((max(max(m0, m1) - 2, 0) + 15) >> 4) | 1;
-}
 
-// Step 2 for one envelope of the tile (one half-warp, lane hl of 16): natural-spline
-// second derivatives of the interior knots 1..m-2 given M_0 = MF and M_{m-1} = ML from
-// the interface solve, then the halved cubic of every interval q = 0..m into cf. The
-// end intervals (to the bracket knots) use half_cubic on values both neighbouring tiles
-// hold bit for bit, so a sample next to a tile edge evaluates identically in both.
-// Called by all 32 lanes (the shuffles span the warp); any_interior (warp-uniform) tells
-// whether either envelope has interior knots.
+// Step 2 for one envelope of the tile (one half-warp, lane hl of 16), then the halved
+// cubic of every interval q = 0..m into cf. An envelope with at most kSparseKnots knots
+// has every knot's second derivative from the interface solve (lane hl writes interval
+// hl). A denser one solves for its interior knots 1..m-2 given M_0 = MF and M_{m-1} = ML:
+// each lane eliminates a run of Q rows, cyclic reduction over W-lane groups joins the
+// runs, back-substitution writes the cubics. The end intervals (to the bracket knots)
+// use half_cubic on values both neighbouring tiles hold bit for bit, so a sample next to
+// a tile edge evaluates identically in both. Called by all 32 lanes (the shuffles span
+// the warp); run_pcr (warp-uniform) tells whether either envelope is dense.
 template <typename R, int TW, int W>
 __device__ __forceinline__ void env_solve(WarpPool<R, TW> &P, int base, int m, int hl, int Q,
-                                          const SolveVals<R> &sv, bool any_interior)
+                                          const SolveVals<R> &sv, bool run_pcr)
 {
     const KnotY<R> *K = P.ky + base;
     Coef<R> *CF = P.cf + base;
     Coef<R> *RW = P.rw + base;
     const R MF = sv.MF, ML = sv.ML;
-    if (hl == 0) {
-        if (m == 0) {
-            CF[0] = slot_cubic(K, 0, sv.Mp, sv.Mn);
-        } else {
-            CF[0] = slot_cubic(K, 0, sv.Mp, MF);
-            CF[m] = slot_cubic(K, m, ML, sv.Mn);
-            if (m == 2)
-                CF[1] = slot_cubic(K, 1, MF, ML);
+    const bool sparse = m <= kSparseKnots;
+    if (sparse) {
+        if (hl <= m) {
+            const R Ml = hl == 0 ? sv.Mp : sparse_M(sv, hl - 1, m);
+            const R Mr = hl == m ? sv.Mn : sparse_M(sv, hl, m);
+            CF[hl] = slot_cubic(K, hl, Ml, Mr);
         }
+    } else if (hl == 0) {
+        CF[0] = slot_cubic(K, 0, sv.Mp, MF);
+        CF[m] = slot_cubic(K, m, ML, sv.Mn);
     }
-    if (!any_interior)
+    if (!run_pcr)
         return;
-    const int n = max(m - 2, 0); // interior unknowns; row i is knot i + 1 (slot i + 2)
+    const int n = sparse ? 0 : m - 2; // interior unknowns; row i is knot i + 1 (slot i + 2)
     const int s = min(hl * Q, n), e = min(s + Q, n), q = e - s;
     SegElim<R> g;
     seg_forward<R, true>(K, RW, CF, s, e, g);
@@ -528,14 +535,15 @@ __device__ __forceinline__ void env_solve(WarpPool<R, TW> &P, int base, int m, i
     }
 }
 
-// Elimination of the interior of one envelope of the tile (one half-warp) in terms of the
-// unknown M_0 and M_{m-1}: M_1 = first[0] + first[1] M_0 + first[2] M_{m-1} and M_{m-2}
-// likewise (last). Meaningful for m >= 3; called by all 32 lanes (or by none).
+// Elimination of the interior of a dense envelope of the tile (one half-warp) in terms
+// of the unknown M_0 and M_{m-1}: M_1 = first[0] + first[1] M_0 + first[2] M_{m-1} and
+// M_{m-2} likewise (last). A sparse envelope takes part as empty rows. Called by all 32
+// lanes (or by none).
 template <typename R, int TW, int W>
 __device__ __forceinline__ void env_export(WarpPool<R, TW> &P, int base, int m, int hl, int Q,
                                            R (&first)[3], R (&last)[3])
 {
-    const int n = max(m - 2, 0);
+    const int n = m <= kSparseKnots ? 0 : m - 2;
     const int s = min(hl * Q, n), e = min(s + Q, n), q = e - s;
     SegElim<R> g;
     seg_forward<R, false>(P.ky + base, P.rw + base, nullptr, s, e, g);
@@ -551,37 +559,42 @@ __device__ __forceinline__ void env_export(WarpPool<R, TW> &P, int base, int m, 
     }
 }
 
-// The solves with the narrowest lane group that covers the larger envelope's interior
-// with one row per lane (W = 2, 4, 8), else all 16 lanes of the half-warp: cyclic
-// reduction takes log2(W) steps, so tiles with few knots pay for few.
+// Interior unknowns of the denser of the tile's two envelopes (0 when both are sparse).
+__device__ __forceinline__ int dense_rows(int m0, int m1)
+{
+    const int d0 = m0 > kSparseKnots ? m0 - 2 : 0, d1 = m1 > kSparseKnots ? m1 - 2 : 0;
+    return max(d0, d1);
+}
+
+// The solves with the narrowest lane group that covers the denser envelope's interior
+// with one row per lane (W = 4, 8), else all 16 lanes of the half-warp (Q rows per lane,
+// Q odd so the lanes hit distinct banks): cyclic reduction takes log2(W) steps.
 template <typename R, int TW>
 __device__ __forceinline__ void env_solve_any(WarpPool<R, TW> &P, int base, int m, int hl, int m0,
                                               int m1, const SolveVals<R> &sv)
 {
-    const int nmax = max(max(m0, m1) - 2, 0);
-    if (nmax <= 2)
-        env_solve<R, TW, 2>(P, base, m, hl, 1, sv, nmax > 0);
+    const int nmax = dense_rows(m0, m1);
+    if (nmax == 0)
+        env_solve<R, TW, 4>(P, base, m, hl, 1, sv, false);
     else if (nmax <= 4)
         env_solve<R, TW, 4>(P, base, m, hl, 1, sv, true);
     else if (nmax <= 8)
         env_solve<R, TW, 8>(P, base, m, hl, 1, sv, true);
     else
-        env_solve<R, TW, 16>(P, base, m, hl, seg_rows(m0, m1), sv, true);
+        env_solve<R, TW, 16>(P, base, m, hl, ((nmax + 15) >> 4) | 1, sv, true);
 }
 
 template <typename R, int TW>
 __device__ __forceinline__ void env_export_any(WarpPool<R, TW> &P, int base, int m, int hl, int m0,
                                                int m1, R (&first)[3], R (&last)[3])
 {
-    const int nmax = max(max(m0, m1) - 2, 0);
-    if (nmax <= 2)
-        env_export<R, TW, 2>(P, base, m, hl, 1, first, last);
-    else if (nmax <= 4)
+    const int nmax = dense_rows(m0, m1);
+    if (nmax <= 4)
         env_export<R, TW, 4>(P, base, m, hl, 1, first, last);
     else if (nmax <= 8)
         env_export<R, TW, 8>(P, base, m, hl, 1, first, last);
     else
-        env_export<R, TW, 16>(P, base, m, hl, seg_rows(m0, m1), first, last);
+        env_export<R, TW, 16>(P, base, m, hl, ((nmax + 15) >> 4) | 1, first, last);
 }
 
 // Whole-record 16-byte accesses to the tile records.
@@ -809,7 +822,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         __syncwarp();
         const int base = eh ? m0 + 2 : 0, m = eh ? m1 : m0;
         R f[3] = {R(0), R(0), R(0)}, l[3] = {R(0), R(0), R(0)};
-        if (max(m0, m1) >= 3)
+        if (max(m0, m1) > kSparseKnots)
             env_export_any<R, TW>(P, base, m, hl, m0, m1, f, l);
         if (hl == 0) {
             TileRec<R> rec;
@@ -823,8 +836,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                rec.xa[q] = m >= 3 ? f[q] : R(0);
-                rec.xb[q] = m >= 3 ? l[q] : R(0);
+                rec.xa[q] = m > kSparseKnots ? f[q] : R(0);
+                rec.xb[q] = m > kSparseKnots ? l[q] : R(0);
             }
             store_rec(reinterpret_cast<TileRec<R> *>(in.tex) + (int64_t)eh * in.ntiles + lt, rec);
         }
@@ -1009,7 +1022,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         const bool shm = ra.smem_entries > 0;
         const int64_t cap = shm ? ra.smem_entries : in.rlen;
         unsigned char *p0 = shm ? rsm
-                                : reinterpret_cast<unsigned char *>(in.rscr + (int64_t)e * 8 * cap);
+                                : reinterpret_cast<unsigned char *>(in.rscr + e * rscr_env_doubles(cap));
         X.carve(p0, cap);
     }
     pdl_wait();
@@ -1048,7 +1061,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         for (int k = 0; k < 4; ++k) {
             const int t = t0 + tid + k * kRedThreads;
             if (t < nt)
-                X.Tu[t] = (unsigned char)min(ne[k], 2);
+                X.Tu[t] = (unsigned char)(ne[k] <= kSparseKnots ? ne[k] : 2);
             sn += ne[k];
             so_ += no[k];
             a += sa[k];
@@ -1195,12 +1208,33 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 X.Et[p] = rc.t[0];
                 X.Ey[p] = rc.y[0];
                 X.Ek[p] = EK_FL;
-            } else if (n >= 2) {
+            } else if (n >= 2 && n <= kSparseKnots) {
+                // every knot an entry: t[0], t[1] (n >= 3), t[2] (n = 4), t[3]
+                X.Et[p] = rc.t[0];
+                X.Ey[p] = rc.y[0];
+                X.Ek[p] = EK_F;
+                int q = p + 1;
+                if (n >= 3) {
+                    X.Et[q] = rc.t[1];
+                    X.Ey[q] = rc.y[1];
+                    X.Ek[q] = EK_FREE;
+                    ++q;
+                }
+                if (n == 4) {
+                    X.Et[q] = rc.t[2];
+                    X.Ey[q] = rc.y[2];
+                    X.Ek[q] = EK_FREE;
+                    ++q;
+                }
+                X.Et[q] = rc.t[3];
+                X.Ey[q] = rc.y[3];
+                X.Ek[q] = EK_L;
+            } else if (n > kSparseKnots) {
                 X.Et[p] = rc.t[0];
                 X.Ey[p] = rc.y[0];
                 X.Et[p + 1] = rc.t[3];
                 X.Ey[p + 1] = rc.y[3];
-                if (n >= 3) {
+                {
                     X.Ek[p] = EK_FS;
                     X.St[p] = rc.t[1];
                     X.A[p] = rc.y[1];
@@ -1213,9 +1247,6 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                     X.B[p + 1] = rc.xb[0];
                     X.C[p + 1] = rc.xb[1];
                     X.D[p + 1] = rc.xb[2];
-                } else {
-                    X.Ek[p] = EK_F;
-                    X.Ek[p + 1] = EK_L;
                 }
             }
         }
@@ -1450,13 +1481,15 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         TileSolve *so = tsol + t;
         const R yp = X.Ey[p - 1], Mp = X.MV[p - 1], yn = X.Ey[p + u], Mn = X.MV[p + u];
         const R MF = u >= 1 ? X.MV[p] : R(0), ML = u >= 1 ? X.MV[p + u - 1] : R(0);
+        const R M1 = u >= 3 ? X.MV[p + 1] : R(0), M2 = u >= 4 ? X.MV[p + 2] : R(0);
         so->tp = X.Et[p - 1];
         so->tn = X.Et[p + u];
         if (sizeof(R) == 4) {
             // FP32 pass kernels read the single-precision values only
             *reinterpret_cast<float4 *>(&so->f[0]) =
                 make_float4((float)MF, (float)ML, (float)yp, (float)Mp);
-            *reinterpret_cast<float2 *>(&so->f[4]) = make_float2((float)yn, (float)Mn);
+            *reinterpret_cast<float4 *>(&so->f[4]) =
+                make_float4((float)yn, (float)Mn, (float)M1, (float)M2);
         } else {
             so->MF = (double)MF;
             so->ML = (double)ML;
@@ -1464,6 +1497,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
             so->Mp = (double)Mp;
             so->yn = (double)yn;
             so->Mn = (double)Mn;
+            so->M1 = (double)M1;
+            so->M2 = (double)M2;
         }
     }
 }

@@ -398,7 +398,7 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {&d_tex, (size_t)tiles * 2 * tile_rec_bytes(elem)},
         {(void **)&d_tsol, (size_t)tiles * 2 * sizeof(TileSolve)},
         {(void **)&d_taux, (size_t)tiles * sizeof(TileAux)},
-        {(void **)&d_rscr, (size_t)rentries * 8 * 8},
+        {(void **)&d_rscr, (size_t)rentries * 8},
         {(void **)&d_active, (size_t)iters * 4},
         {(void **)&d_beta, 8},
         {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
@@ -474,7 +474,7 @@ void Workspace::release()
 }
 
 // Points instance i at its own slices of the workspace buffers (samples from `off`,
-// tiles from `tiles`, interface scratch from `rent`).
+// tiles from `tiles`, interface scratch from double `rent`).
 static void bind_instance(Workspace &ws, Inst &in, int64_t off, int64_t tiles, int64_t rent)
 {
     in.tile0 = (int32_t)tiles;
@@ -487,7 +487,7 @@ static void bind_instance(Workspace &ws, Inst &in, int64_t off, int64_t tiles, i
     in.tsol = ws.d_tsol + 2 * tiles;
     in.taux = ws.d_taux + tiles;
     in.rlen = reduce_len(in.ntiles);
-    in.rscr = ws.d_rscr + 8 * rent;
+    in.rscr = ws.d_rscr + rent;
 }
 
 // Lays out n instances (host descriptors in ws.h_inst must have L, geometry and output
@@ -501,7 +501,7 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
         bind_instance(*this, in, off, tiles, rent);
         off += (in.L + 31) & ~(int64_t)31;
         tiles += in.ntiles;
-        rent += 2 * in.rlen;
+        rent += 2 * rscr_env_doubles(in.rlen);
         max_ntiles = std::max<int64_t>(max_ntiles, in.ntiles);
     }
     if (off > cap_samples || tiles > cap_tiles || rent > cap_rentries || n > cap_inst) {
@@ -967,7 +967,7 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     const int64_t tiles_per = (L + kMinTile - 1) / kMinTile;
     const int64_t samples = (int64_t)ninst * ((L + 31) & ~(int64_t)31);
     const int64_t tiles = (int64_t)ninst * tiles_per;
-    const int64_t rent = (int64_t)ninst * 2 * reduce_len(tiles_per);
+    const int64_t rent = (int64_t)ninst * 2 * rscr_env_doubles(reduce_len(tiles_per));
     const size_t elem = params->precision == SEMD_FP64 ? 8 : 4;
     const int64_t eemd_elems =
         eemd ? (int64_t)ninst * params->max_imfs * ((L + 31) & ~(int64_t)31) : 0;
@@ -1154,21 +1154,21 @@ const char *serial_emd_last_error(semd_plan_t plan)
 // scratch (signal and residue buffers, per-tile records of the spline solve, the
 // instance descriptor and state) lives in one file-scope __device__ array, so a call
 // reserves no device memory. Every GPU that loads this library holds the array
-// (kNoAllocBytes, about 2.3 MB) until the process exits. All calls share it: calls
+// (kNoAllocBytes, about 2.4 MB) until the process exits. All calls share it: calls
 // that overlap on the GPU (concurrent streams, threads or devices sharing a context)
 // race on it, and each call clears what it needs before use.
 namespace semd {
 
 constexpr int64_t kNoAllocMaxL = 65536;                  // largest accepted L
 constexpr int kNoAllocTiles = (int)(kNoAllocMaxL / kTile);
-constexpr int64_t kNoAllocRent = 2 * reduce_len(kNoAllocTiles);
+constexpr int64_t kNoAllocRent = 2 * rscr_env_doubles(reduce_len(kNoAllocTiles)); // doubles
 constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kNoAllocBytes =
     4 * na_round(kNoAllocMaxL * 8) +                        // h0, h1 (sized for FP64), r0, r1
     na_round(sizeof(Inst)) + na_round(sizeof(State)) + na_round(kNoAllocTiles * 4) +
     na_round(kNoAllocTiles * 2 * tile_rec_bytes(8)) +
     na_round(kNoAllocTiles * 2 * sizeof(TileSolve)) + na_round(kNoAllocTiles * sizeof(TileAux)) +
-    na_round(kNoAllocRent * 8 * 8) +
+    na_round(kNoAllocRent * 8) +
     na_round(8) + na_round(sizeof(Stats)) + na_round(4 * 8); // active flags, stats, result
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1271,7 +1271,7 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     ws.d_tex = take(kNoAllocTiles * 2 * tile_rec_bytes(8));
     ws.d_tsol = (TileSolve *)take(kNoAllocTiles * 2 * sizeof(TileSolve));
     ws.d_taux = (TileAux *)take(kNoAllocTiles * sizeof(TileAux));
-    ws.d_rscr = (double *)take(kNoAllocRent * 8 * 8);
+    ws.d_rscr = (double *)take(kNoAllocRent * 8);
     ws.d_active = (int32_t *)take(8);
     ws.d_stats = (Stats *)take(sizeof(Stats));
     double *d_result = (double *)take(4 * 8);

@@ -24,7 +24,7 @@ struct Workspace {
     void *base = nullptr;
     size_t bytes = 0;
     int tile = kTile;
-    int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0, max_ntiles = 0;
+    int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0, max_ntiles = 0; // cap_rentries: doubles of interface scratch
     int cap_inst = 0, cap_iters = 0;
     size_t elem_size = 0;
     void *h0 = nullptr, *h1 = nullptr;

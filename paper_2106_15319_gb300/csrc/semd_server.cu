@@ -95,7 +95,7 @@ static ReqLayout req_layout(int64_t L, size_t elem, int tile)
     q.tex = R((size_t)q.nt * 2 * tile_rec_bytes(elem));
     q.tsol = R((size_t)q.nt * 2 * sizeof(TileSolve));
     q.taux = R((size_t)q.nt * sizeof(TileAux));
-    q.rscr = R((size_t)q.rlen * 16 * 8);
+    q.rscr = R((size_t)(2 * rscr_env_doubles(q.rlen)) * 8);
     q.total = 2 * q.h + 2 * q.r + q.tex + q.tsol + q.taux + q.rscr;
     return q;
 }

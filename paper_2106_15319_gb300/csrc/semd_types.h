@@ -41,11 +41,12 @@ __host__ __device__ constexpr size_t tile_rec_bytes(size_t elem)
 // plans fill the single-precision values (read by the FP32 pass kernel), FP64 plans the
 // double ones.
 struct __align__(16) TileSolve {
-    float f[6];             // MF, ML, yp, Mp, yn, Mn in single precision
+    float f[8];             // MF, ML, yp, Mp, yn, Mn, M1, M2 in single precision
     int32_t tp, tn;         // outside bracket knots: last knot before the tile, first knot
-                            // after it (instance positions)
+    int32_t pad[2];         // after it (instance positions)
     double MF, ML;          // M at the tile's first and last knot
     double yp, Mp, yn, Mn;  // values and M at the bracket knots
+    double M1, M2;          // M at knots 1 and 2 (envelopes with at most 4 knots)
 };
 
 // Working precision, like TileExport.
@@ -69,7 +70,7 @@ struct Inst {
     TileSolve *tsol;        // 2 per tile
     TileAux *taux;          // 1 per tile
     double *rscr;           // interface-solve scratch when it does not fit shared memory:
-    int64_t rlen;           //   8 doubles per entry, rlen entries per envelope
+    int64_t rlen;           //   rlen entries per envelope, rscr_env_doubles(rlen) each
     const void *x;          // input (rows x cols, row-major), or null
     void *imf;              // IMF output base
     double *res;            // residue output (input shape), or null
@@ -128,6 +129,11 @@ __host__ __device__ constexpr size_t red_env_bytes(int64_t entries, size_t elem)
 {
     return ((size_t)entries * (6 * elem + 17) + 15) & ~(size_t)15;
 }
+// Global-memory scratch of one envelope, in doubles (sized for either precision).
+__host__ __device__ constexpr int64_t rscr_env_doubles(int64_t entries)
+{
+    return (int64_t)(red_env_bytes(entries, 8) / 8);
+}
 // Shared memory of one k_reduce CTA when its scratch lives there.
 __host__ __device__ constexpr size_t reduce_smem_bytes(int64_t entries, size_t elem)
 {
@@ -135,6 +141,9 @@ __host__ __device__ constexpr size_t reduce_smem_bytes(int64_t entries, size_t e
 }
 
 // Entries of the reduced system of an instance with nt tiles (per envelope).
-__host__ __device__ constexpr int64_t reduce_entries(int64_t nt) { return 2 * nt + 4; }
+// Envelopes of a tile with at most this many knots export all of them (no elimination of
+// an interior), so the interface solve yields every knot's second derivative.
+constexpr int kSparseKnots = 4;
+__host__ __device__ constexpr int64_t reduce_entries(int64_t nt) { return kSparseKnots * nt + 4; }
 
 } // namespace semd
