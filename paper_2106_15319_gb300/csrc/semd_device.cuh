@@ -950,6 +950,66 @@ struct RedScratch {
     }
 };
 
+// Segment elimination of rows [rs, re) of the reduced system in the scratch, in place:
+// rows rs..re-2 become (bp, b, cp, dp) in (A, B, C, D); returns the segment's reduced
+// form (first unknown in terms of x_{rs-1} and x_{re-1}, last row kept).
+template <typename R>
+__device__ __forceinline__ SegElim<R> seg_eliminate(const RedScratch<R> &X, int rs, int re)
+{
+    SegElim<R> g;
+    if (re - rs < 1)
+        return g;
+    R cprev = R(0), dprev = R(0), bprev = R(1);
+#pragma unroll 4
+    for (int j = rs; j < re - 1; ++j) {
+        const R A = X.A[j], B = X.B[j], C = X.C[j], D = X.D[j];
+        const R inv = rrcp(B - A * cprev);
+        cprev = C * inv;
+        dprev = (D - A * dprev) * inv;
+        bprev = -A * bprev * inv;
+        X.A[j] = bprev;
+        X.C[j] = cprev;
+        X.D[j] = dprev;
+    }
+    g.al = X.A[re - 1];
+    g.bl = X.B[re - 1];
+    g.cl = X.C[re - 1];
+    g.dl = X.D[re - 1];
+    if (re - rs >= 2) {
+        g.alE = dprev;
+        g.beE = bprev;
+        g.gaE = -cprev;
+        R xa = g.alE, xb = g.beE, xg = g.gaE;
+#pragma unroll 4
+        for (int j = re - 3; j >= rs; --j) {
+            const R c = X.C[j];
+            xa = X.D[j] - c * xa;
+            xb = X.A[j] - c * xb;
+            xg = -c * xg;
+        }
+        g.alS = xa;
+        g.beS = xb;
+        g.gaS = xg;
+    }
+    return g;
+}
+
+// Back-substitution of segment [rs, re) given x_{rs-1} = Zp and x_{re-1} = z; writes MV.
+template <typename R>
+__device__ __forceinline__ void seg_backsub(const RedScratch<R> &X, int rs, int re, R Zp, R z)
+{
+    if (re - rs < 1)
+        return;
+    X.MV[re - 1] = z;
+    R xn = z;
+#pragma unroll 4
+    for (int j = re - 2; j >= rs; --j) {
+        const R x = X.D[j] + X.A[j] * Zp - X.C[j] * xn;
+        X.MV[j] = x;
+        xn = x;
+    }
+}
+
 struct RedShared {
     double lev[14 * kRedThreads]; // level-1 results (10 arrays), level-1.5 scratch (4), in R
     int segq[kRedThreads];        // rows per level-1 segment
@@ -1026,9 +1086,10 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         X.carve(p0, cap);
     }
     pdl_wait();
+    // what the pass kernel wrote is read at once (the state and the tile counts; the
+    // counts of a finished instance are read and dropped)
     State *st = ra.state + ii;
-    if (st->mode == MODE_DONE)
-        return;
+    const int mode_now = st->mode;
     const int pm = st->pass_mode, psift = st->pass_sift, pimf = st->pass_imf;
     const int ppar = st->pass_par;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1039,7 +1100,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     // stride of the block, four per thread at a time, every load in flight before use.
     int sn = 0, so_ = 0;
     double a = 0.0, b = 0.0;
-    const bool want_sd = pm == MODE_SIFT && ra.stop == STOP_SD;
+    const bool want_sd = ra.stop == STOP_SD;
     for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
         int ne[4], no[4];
         double sa[4], sb[4];
@@ -1068,10 +1129,14 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
             b += sb[k];
         }
     }
+    if (mode_now == MODE_DONE)
+        return;
     sn = warp_sum(sn);
     so_ = warp_sum(so_);
-    a = warp_sum(a);
-    b = warp_sum(b);
+    if (want_sd) { // FP64 sums only when the stop rule reads them (the FP64 pipe is narrow)
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
     if (lane == 0) {
         S.wsn[warp][0] = sn;
         S.wsn[warp][1] = so_;
@@ -1104,9 +1169,11 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     if (tid == 0) {
         const int nmax = e == 0 ? ntot : nother, nmin = e == 0 ? nother : ntot;
         double sdn = 0.0, sdd = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            sdn += S.sd[w][0];
-            sdd += S.sd[w][1];
+        if (want_sd) {
+            for (int w = 0; w < NW; ++w) {
+                sdn += S.sd[w][0];
+                sdd += S.sd[w][1];
+            }
         }
         const bool ok = nmax >= 1 && nmin >= 1 && nmax + nmin >= 3;
         int imf_count = pimf, sift_count = psift, nm;
@@ -1344,138 +1411,116 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         X.D[p] = rd;
     }
     __syncthreads();
-    // level 1: every thread eliminates a contiguous segment of Q1 rows (Q1 odd, so the
-    // lanes of a warp hit distinct banks); its result goes to shared memory
     R *lev = reinterpret_cast<R *>(S.lev);
-    constexpr int NS = kRedThreads;      // level-1 segments
+    constexpr int NS = kRedThreads;      // level-1 segments of the large form
     constexpr int G = kRedThreads / 32;  // segments per lane of the level-1.5 warp
-    {
+    // transposed layout: lane l's k-th segment (j = G l + k) at k * 32 + l, so that the
+    // level-1.5 warp reads without bank conflicts
+    auto tj = [](int j) { return (j % G) * 32 + j / G; };
+    if (NR <= 24 * 32) {
+        // small systems: three levels in warp 0 (segments of Q1 rows per lane, the 32
+        // segment ends to FP64 accuracy, back-substitution)
+        if (warp == 0) {
+            const int Q1 = ((NR + 31) >> 5) | 1;
+            const int rs = min(lane * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
+            const SegElim<R> g = seg_eliminate(X, rs, re);
+            const double Zd = level2_solve(g, rq, (rq >= 1) && (re < NR));
+            const R z = (R)Zd;
+            R Zp = __shfl_up_sync(FULLMASK, z, 1);
+            if (lane == 0)
+                Zp = R(0);
+            seg_backsub(X, rs, re, Zp, z);
+        }
+        __syncthreads();
+    } else {
+        // level 1: every thread eliminates a contiguous segment of Q1 rows (Q1 odd, so
+        // the lanes of a warp hit distinct banks)
         const int Q1 = ((NR + NS - 1) / NS) | 1;
         const int rs = min(tid * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
-        SegElim<R> g;
-        if (rq >= 1) {
+        {
+            const SegElim<R> g = seg_eliminate(X, rs, re);
+            const R gv[10] = {g.alS, g.beS, g.gaS, g.alE, g.beE, g.gaE, g.al, g.bl, g.cl, g.dl};
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                lev[k * NS + tj(tid)] = gv[k];
+            S.segq[tj(tid)] = rq;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // level 1.5: the NS segment-end unknowns; lane l eliminates the reduced rows of
+            // segments G l .. G l + G - 1 (row j couples Z_{j-1}, Z_j, Z_{j+1})
+            R *cp2 = lev + 10 * NS, *dp2 = lev + 11 * NS, *bp2 = lev + 12 * NS, *Zs = lev + 13 * NS;
+            auto red_row = [&](int k, R &A, R &B, R &C, R &D) {
+                // reduced row of segment j = G lane + k; its successor is j + 1
+                const int i = k * 32 + lane;
+                SegElim<R> gj;
+                gj.alE = lev[3 * NS + i];
+                gj.beE = lev[4 * NS + i];
+                gj.gaE = lev[5 * NS + i];
+                gj.al = lev[6 * NS + i];
+                gj.bl = lev[7 * NS + i];
+                gj.cl = lev[8 * NS + i];
+                gj.dl = lev[9 * NS + i];
+                const int j = G * lane + k;
+                const int in_ = j + 1 < NS ? tj(j + 1) : 0;
+                const bool hn = j + 1 < NS && S.segq[in_] >= 1;
+                const R nalS = hn ? lev[in_] : R(0), nbeS = hn ? lev[NS + in_] : R(0);
+                const R ngaS = hn ? lev[2 * NS + in_] : R(0);
+                reduced_row(gj, S.segq[i], hn, nalS, nbeS, ngaS, A, B, C, D);
+            };
+            SegElim<R> g2;
             R cprev = R(0), dprev = R(0), bprev = R(1);
-#pragma unroll 4
-            for (int j = rs; j < re - 1; ++j) {
-                const R A = X.A[j], B = X.B[j], C = X.C[j], D = X.D[j];
+#pragma unroll
+            for (int k = 0; k < G - 1; ++k) {
+                R A, B, C, D;
+                red_row(k, A, B, C, D);
                 const R inv = rrcp(B - A * cprev);
                 cprev = C * inv;
                 dprev = (D - A * dprev) * inv;
                 bprev = -A * bprev * inv;
-                X.A[j] = bprev;
-                X.C[j] = cprev;
-                X.D[j] = dprev;
+                cp2[k * 32 + lane] = cprev;
+                dp2[k * 32 + lane] = dprev;
+                bp2[k * 32 + lane] = bprev;
             }
-            g.al = X.A[re - 1];
-            g.bl = X.B[re - 1];
-            g.cl = X.C[re - 1];
-            g.dl = X.D[re - 1];
-            if (rq >= 2) {
-                g.alE = dprev;
-                g.beE = bprev;
-                g.gaE = -cprev;
-                R xa = g.alE, xb = g.beE, xg = g.gaE;
-#pragma unroll 4
-                for (int j = re - 3; j >= rs; --j) {
-                    const R c = X.C[j];
-                    xa = X.D[j] - c * xa;
-                    xb = X.A[j] - c * xb;
-                    xg = -c * xg;
-                }
-                g.alS = xa;
-                g.beS = xb;
-                g.gaS = xg;
+            red_row(G - 1, g2.al, g2.bl, g2.cl, g2.dl);
+            g2.alE = dprev;
+            g2.beE = bprev;
+            g2.gaE = -cprev;
+            R xa = g2.alE, xb = g2.beE, xg = g2.gaE;
+#pragma unroll
+            for (int k = G - 3; k >= 0; --k) {
+                const R c = cp2[k * 32 + lane];
+                xa = dp2[k * 32 + lane] - c * xa;
+                xb = bp2[k * 32 + lane] - c * xb;
+                xg = -c * xg;
             }
-        }
-        const R gv[10] = {g.alS, g.beS, g.gaS, g.alE, g.beE, g.gaE, g.al, g.bl, g.cl, g.dl};
-#pragma unroll
-        for (int k = 0; k < 10; ++k)
-            lev[k * NS + tid] = gv[k];
-        S.segq[tid] = rq;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // level 1.5: the NS segment-end unknowns; lane l eliminates the reduced rows of
-        // segments G l .. G l + G - 1 (row j couples Z_{j-1}, Z_j, Z_{j+1})
-        R *cp2 = lev + 10 * NS, *dp2 = lev + 11 * NS, *bp2 = lev + 12 * NS, *Zs = lev + 13 * NS;
-        const int j0 = lane * G;
-        auto red_row = [&](int j, R &A, R &B, R &C, R &D) {
-            SegElim<R> gj;
-            gj.alE = lev[3 * NS + j];
-            gj.beE = lev[4 * NS + j];
-            gj.gaE = lev[5 * NS + j];
-            gj.al = lev[6 * NS + j];
-            gj.bl = lev[7 * NS + j];
-            gj.cl = lev[8 * NS + j];
-            gj.dl = lev[9 * NS + j];
-            const bool hn = j + 1 < NS && S.segq[j + 1] >= 1;
-            const R nalS = hn ? lev[j + 1] : R(0), nbeS = hn ? lev[NS + j + 1] : R(0);
-            const R ngaS = hn ? lev[2 * NS + j + 1] : R(0);
-            reduced_row(gj, S.segq[j], hn, nalS, nbeS, ngaS, A, B, C, D);
-        };
-        SegElim<R> g2;
-        R cprev = R(0), dprev = R(0), bprev = R(1);
-#pragma unroll
-        for (int k = 0; k < G - 1; ++k) {
-            R A, B, C, D;
-            red_row(j0 + k, A, B, C, D);
-            const R inv = rrcp(B - A * cprev);
-            cprev = C * inv;
-            dprev = (D - A * dprev) * inv;
-            bprev = -A * bprev * inv;
-            cp2[j0 + k] = cprev;
-            dp2[j0 + k] = dprev;
-            bp2[j0 + k] = bprev;
-        }
-        red_row(j0 + G - 1, g2.al, g2.bl, g2.cl, g2.dl);
-        g2.alE = dprev;
-        g2.beE = bprev;
-        g2.gaE = -cprev;
-        R xa = g2.alE, xb = g2.beE, xg = g2.gaE;
-#pragma unroll
-        for (int k = G - 3; k >= 0; --k) {
-            const R c = cp2[j0 + k];
-            xa = dp2[j0 + k] - c * xa;
-            xb = bp2[j0 + k] - c * xb;
-            xg = -c * xg;
-        }
-        g2.alS = xa;
-        g2.beS = xb;
-        g2.gaS = xg;
-        // level 2: the 32 group-end unknowns to FP64 accuracy
-        const double Zd = level2_solve(g2, G, lane < 31);
-        const R z = (R)Zd;
-        R Zp = __shfl_up_sync(FULLMASK, z, 1);
-        if (lane == 0)
-            Zp = R(0);
-        Zs[j0 + G - 1] = z;
-        R xn = z;
-#pragma unroll
-        for (int k = G - 2; k >= 0; --k) {
-            const R x = dp2[j0 + k] + bp2[j0 + k] * Zp - cp2[j0 + k] * xn;
-            Zs[j0 + k] = x;
-            xn = x;
-        }
-    }
-    __syncthreads();
-    {
-        // level 3: back-substitution of this thread's segment
-        const int Q1 = ((NR + NS - 1) / NS) | 1;
-        const int rs = min(tid * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
-        const R *Zs = lev + 13 * NS;
-        if (rq >= 1) {
-            const R z = Zs[tid], Zp = tid > 0 ? Zs[tid - 1] : R(0);
-            X.MV[re - 1] = z;
+            g2.alS = xa;
+            g2.beS = xb;
+            g2.gaS = xg;
+            // level 2: the 32 group-end unknowns to FP64 accuracy
+            const double Zd = level2_solve(g2, G, lane < 31);
+            const R z = (R)Zd;
+            R Zp = __shfl_up_sync(FULLMASK, z, 1);
+            if (lane == 0)
+                Zp = R(0);
+            Zs[(G - 1) * 32 + lane] = z;
             R xn = z;
-#pragma unroll 4
-            for (int j = re - 2; j >= rs; --j) {
-                const R x = X.D[j] + X.A[j] * Zp - X.C[j] * xn;
-                X.MV[j] = x;
+#pragma unroll
+            for (int k = G - 2; k >= 0; --k) {
+                const int i = k * 32 + lane;
+                const R x = dp2[i] + bp2[i] * Zp - cp2[i] * xn;
+                Zs[i] = x;
                 xn = x;
             }
         }
+        __syncthreads();
+        // level 3: back-substitution of this thread's segment
+        if (rq >= 1) {
+            const R *Zs = lev + 13 * NS;
+            seg_backsub(X, rs, re, tid > 0 ? Zs[tj(tid - 1)] : R(0), Zs[tj(tid)]);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int t = tid; t < nt; t += kRedThreads) {
         const int u = X.Tu[t], p = X.To[t];
         TileSolve *so = tsol + t;
