@@ -687,6 +687,16 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             prefetch_l2(rsrc + TW, (uint32_t)(((ncnt * 8) + 15) & ~15));
     }
 
+    // the tile's interface values (written by the interface solve just before), fetched
+    // with the signal so that their latency overlaps the extrema search
+    SolveVals<R> sv{};
+    int2 tpn = make_int2(0, 0);
+    if (sift) {
+        const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
+        sv = solve_vals(so, R(0));
+        tpn = *reinterpret_cast<const int2 *>(&so.tp);
+    }
+
     R pn = R(0), pd = R(0);
     R hnl = hcl, hnr = hcr; // the new signal at the halo samples
     if (sift) {
@@ -699,13 +709,11 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         uint32_t MX, MN;
         int bx, bn, m0, m1;
         warp_knots<R, SPL, TW>(P, v, left, right, k0, ts + k0, cnt, L, MX, MN, bx, bn, m0, m1);
-        const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
-        const SolveVals<R> sv = solve_vals(so, R(0));
         const int b1 = m0 + 2;
         const int base = eh ? b1 : 0, m = eh ? m1 : m0;
         if (hl == 0) {
-            P.ky[base] = KnotY<R>{so.tp - ts, sv.yp};
-            P.ky[base + m + 1] = KnotY<R>{so.tn - ts, sv.yn};
+            P.ky[base] = KnotY<R>{tpn.x - ts, sv.yp};
+            P.ky[base + m + 1] = KnotY<R>{tpn.y - ts, sv.yn};
         }
         __syncwarp();
         env_solve_any<R, TW>(P, base, m, hl, m0, m1, sv);
