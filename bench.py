@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "serialized samples sifted/s: batched FP32 vs plain FP64 on GB300; p99 request latency"
 UNIT = "samples*sifts/s"
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one k_pass launch of the default workload, from the ncu
+# capture summarized in profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu
+# replays); set to None when the kernel changes until it is captured again.
+PASS_TRAFFIC_TEXTURE = 398336
 
 
 def _peaks():
@@ -405,7 +409,9 @@ def arm_ours(args):
         "fp32_imf_rel_l2": None,
         "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": None,
+                     "peak_source": peak_kind,
+                     "traffic": PASS_TRAFFIC_TEXTURE if args.workload == "texture256" and
+                     not args.tile else None,
                      "avg_launch_us": pass_avg_ms * 1e3, "bytes_per_launch": bytes_per_launch,
                      "launches": prof["pass_n"], "reduce_avg_us":
                          prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
