@@ -61,7 +61,7 @@ def _rel(a, b, floor):
 
 def _check_imfs(imfs_g, res_g, n_g, imfs_o, res_o, n_o, x, prec, what=""):
     nx = np.linalg.norm(x)
-    floor = 1e-6 * nx
+    floor = max(1e-6 * nx, 1e-300)  # an all-zero input has a zero norm
     K = imfs_o.shape[0]
     errs = [_rel(imfs_g[k], imfs_o[k], floor) for k in range(K)]
     rerr = _rel(res_g, res_o, floor)
@@ -73,6 +73,7 @@ def _check_imfs(imfs_g, res_g, n_g, imfs_o, res_o, n_o, x, prec, what=""):
     tail0 = max(min(n_g, n_o) - 1, 0)
     lead = errs[:min(2, tail0)]
     assert max(lead, default=0.0) <= TOL[prec], f"{what}: leading IMFs {lead} (all {errs})"
+    nx = max(nx, 1e-300)
     absn = [np.linalg.norm(imfs_g[k] - imfs_o[k]) / nx for k in range(tail0)]
     tail = imfs_g[tail0:].sum(0) + res_g - imfs_o[tail0:].sum(0) - res_o
     absn.append(np.linalg.norm(tail) / nx)
@@ -118,7 +119,7 @@ def _check_fp32_given_input(imfs_g, res_g, n_g, x, K, what="", S=10):
     so the serialized signal is x flattened)."""
     x = np.asarray(x, np.float64).reshape(-1)
     c = np.asarray(imfs_g, np.float64).reshape(K, -1)
-    floor = 1e-6 * np.linalg.norm(x)
+    floor = max(1e-6 * np.linalg.norm(x), 1e-300)
     r = x.copy()
     errs, stable = [], []
     for k in range(n_g):
@@ -341,3 +342,94 @@ def test_tile_sizes_agree_fp64(D):
         plan.close()
     for tile in (128, 512):
         assert np.abs(res[tile] - res[256]).max() <= 1e-12 * np.abs(X).max()
+
+
+# ----------------------------------------------------------------------- edge cases
+
+def _degenerate(kind):
+    if kind == "constant":
+        return np.full((1, 700), 2.5)
+    if kind == "zeros":
+        return np.zeros((3, 300))
+    if kind == "ramp":
+        return np.linspace(-1.0, 3.0, 900)[None, :]
+    if kind == "one_bump":  # one maximum, no minimum: nmax + nmin < 3 (Sec. 2.1 end test)
+        t = np.linspace(0.0, 1.0, 500)
+        return np.exp(-((t - 0.4) / 0.1) ** 2)[None, :]
+    if kind == "one_sample":
+        return np.array([[1.25]])
+    if kind == "two_samples":
+        return np.array([[1.0, -2.0]])
+    if kind == "plateaus":  # flat tops and bottoms: the tie rule of Step 1 decides
+        t = np.arange(1500)
+        return np.round(3.0 * np.sin(t / 17.0) + np.sin(t / 5.0))[None, :] / 4.0
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+@pytest.mark.parametrize("kind", ["constant", "zeros", "ramp", "one_bump", "one_sample",
+                                  "two_samples", "plateaus"])
+def test_degenerate_inputs(prec, kind):
+    """Inputs the method leaves whole or decomposes only partly (no or too few extrema,
+    flat runs) and the shortest signals: IMF counts equal the oracle's, IMFs and the
+    residue match it (FP32 inputs are exact in single precision here, except the bump and
+    ramp, whose IMF-free decompositions leave the input as the residue)."""
+    X = np.asarray(_degenerate(kind), NP[prec])
+    g = _run(X, prec, transition_len=0, max_imfs=6)
+    o = _oracle(X, prec, transition_len=0, max_imfs=6)
+    if prec == capi.FP64:
+        _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, kind)
+    else:
+        _check_fp32_given_input(g[0], g[1], g[2], X.astype(np.float64), 6, kind)
+    assert np.abs(g[0].sum(0) + g[1] - X.astype(np.float64)).max() <= \
+        1e-12 * max(1.0, np.abs(X).max())
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_every_sample_an_extremum(prec):
+    """Alternating samples: every interior sample is a maximum or a minimum, so each tile
+    holds as many knots as samples (the knot pool's worst case), with ragged tiles."""
+    g0 = synth.rng(5151)
+    L = 3 * 256 + 77
+    x = np.where(np.arange(L) % 2 == 0, 1.0, -1.0) * (1.0 + 0.25 * g0.uniform(size=L))
+    x = x + 0.1 * np.sin(np.arange(L) / 40.0)
+    X = np.asarray(x[None, :], NP[prec])
+    g = _run(X, prec, transition_len=0, max_imfs=5)
+    if prec == capi.FP64:
+        o = _oracle(X, prec, transition_len=0, max_imfs=5)
+        _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, "alternating")
+    else:
+        _check_fp32_given_input(g[0], g[1], g[2], X.astype(np.float64), 5, "alternating")
+
+
+def test_long_signal_global_interface_scratch_fp64():
+    """A signal long enough that the interface solve's scratch leaves shared memory for
+    global memory (more than ~4500 reduced-system entries per envelope at 256-sample
+    tiles), with a ragged last tile."""
+    L = (1 << 19) + 123
+    g0 = synth.rng(777)
+    t = np.arange(L)
+    X = (np.sin(2 * np.pi * t / 9.0) + 0.5 * np.sin(2 * np.pi * t / 61.0) +
+         0.3 * np.sin(2 * np.pi * t / 1500.0) + 0.05 * g0.standard_normal(L))[None, :]
+    g = _run(X, capi.FP64, transition_len=0, max_imfs=6)
+    o = _oracle(X, capi.FP64, transition_len=0, max_imfs=6)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, "long")
+
+
+def test_largest_serving_image_fp32():
+    """A 2048 x 2048 image (4.2 M samples, the serving mix's largest request) in FP32:
+    exact FP64 reconstruction, the oracle's IMF count, and its two leading IMFs given the
+    same remainder."""
+    X = np.asarray(synth.grating_image(2048, 99), np.float32)
+    imfs, res, n, _ = _run(X, capi.FP32_MIXED, transition_len=0, max_imfs=10)
+    x = X.astype(np.float64)
+    assert np.abs(imfs.sum(0) + res - x).max() <= 1e-12 * np.abs(x).max()
+    r = x.reshape(-1).copy()
+    floor = 1e-6 * np.linalg.norm(x)
+    for k in range(2):
+        oi, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1)
+        assert on == 1
+        err = _rel(imfs[k].reshape(-1), oi[0], floor)
+        assert err <= TOL[capi.FP32_MIXED] or not _fp32_keeps_extrema(
+            r.astype(np.float32).astype(np.float64), 10), (k, err)
+        r = r - imfs[k].reshape(-1)
