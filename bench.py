@@ -429,6 +429,10 @@ def arm_ours(args):
             line["batched"] = batched_eemd(args, device, flush, peak, peak_kind, world)
             line["batched_images"] = batched_images(args, device, flush, peak, peak_kind,
                                                     world)
+        if not args.no_batched:
+            line["standard_slices"] = standard_slices(args, device, flush, world)
+            line["standard_slices"]["serial_over_slices_time"] = \
+                line["ms_per_step"] / line["standard_slices"]["ms_per_step"]
         if not args.no_serving:
             line["serving"] = serving(args, device)
         if not args.no_cpu_baseline:
@@ -577,6 +581,47 @@ def serving(args, device):
     finally:
         server.close()
     return out
+
+
+def standard_slices(args, device, flush, world):
+    """The paper's standard-version baseline (Sec. 4) on the default workload: the 256
+    rows of the 256 x 256 texture decomposed one by one (no serialization), all rows in
+    one batched run, against the serial form of the same input."""
+    import torch
+    from paper_2106_15319_gb300 import capi
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    wl = workload_inputs("texture256")
+    X = np.ascontiguousarray(wl["X"], np.float32)
+    rows, cols = X.shape
+    plan = Plan(make_params(1, cols, precision=capi.FP32_MIXED, transition_len=0,
+                            max_imfs=wl["K"], fixed_sifts=wl["S"]), max_batch=rows)
+    x = torch.from_numpy(X).to(device)
+    imfs, res = plan.outputs(rows, cols, device=device)
+    stream = torch.cuda.Stream(device)
+    steps = max(1, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        for _ in range(min(args.warmup, 3)):
+            plan.decompose_slices(x, imfs, res, stream=stream, wait=False)
+        stream.synchronize()
+        ms = []
+        for _ in range(steps):
+            _flush_l2(flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.decompose_slices(x, imfs, res, stream=stream, wait=False)
+            b.record(stream)
+            stream.synchronize()
+            ms.append(a.elapsed_time(b))
+    st = plan.stats()
+    n, _ = plan.counts(rows)
+    plan.close()
+    m = max_over_ranks(statistics.mean(ms), world)
+    return {"workload": f"{rows} rows of the 256x256 texture, each decomposed alone "
+                        f"(1 x {cols} signals, no transitions), one batched run, "
+                        f"{wl['S']} sifts/IMF, <={wl['K']} IMFs",
+            "value": world * st.sample_sifts / (m * 1e-3), "unit": UNIT, "ms_per_step": m,
+            "steps": steps, "dtype": "f32", "imfs_per_row_mean": float(np.mean(n))}
 
 
 def main():

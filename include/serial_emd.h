@@ -150,6 +150,22 @@ typedef struct semd_instance {
 semd_status serial_emd_decompose_batch(semd_plan_t plan, int count, const semd_instance *inst,
                                        int *n_imfs, void *stream);
 
+/*
+ * Slice-wise standard EMD, the baseline of the paper's experiments (Sec. 4: the standard
+ * one-dimensional EMD applied to the input as a collection of one-dimensional slices):
+ * each of the `rows` signals of a row-major rows x cols input (plan precision) is
+ * decomposed on its own, without serialization or transitions, all in one batched run
+ * with the same kernels. d_imfs: K x rows x cols (IMF k of signal i at
+ * k*rows*cols + i*cols, zero past the signal's IMF count); d_residue: rows x cols
+ * doubles, or NULL; n_imfs: host array of `rows`, or NULL (see decompose). The plan must
+ * be an EMD plan whose serialized length holds one signal (cols samples) and whose
+ * max_batch is at least `rows`; EBUDGET otherwise, EINVAL for EEMD plans. Results equal
+ * those of decompose_batch on the rows taken one by one.
+ */
+semd_status serial_emd_decompose_slices(semd_plan_t plan, const void *d_x, int64_t rows,
+                                        int64_t cols, void *d_imfs, double *d_residue,
+                                        int *n_imfs, void *stream);
+
 /* After the stream has finished: IMF counts (count entries) and sifts per IMF
  * (count x K entries, may be NULL) of the plan's last decompose call. */
 semd_status serial_emd_plan_counts(semd_plan_t plan, int count, int *n_imfs, int *sifts);

@@ -77,6 +77,10 @@ SIGNATURES = {
     "serial_emd_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                                   ctypes.POINTER(semd_instance),
                                                   ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "serial_emd_decompose_slices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_int64, ctypes.c_int64,
+                                                   ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "serial_emd_plan_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
@@ -191,6 +195,16 @@ def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True)
     n = (ctypes.c_int * len(items))()
     rc = load().serial_emd_decompose_batch(plan, len(items), arr, n if wait else None,
                                            _stream(stream))
+    _check(rc, plan)
+    return list(n) if wait else None
+
+
+def serial_emd_decompose_slices(plan: int, x, imfs, residue, stream=None, wait: bool = True):
+    """Slice-wise standard EMD of every row of x (rows, cols); imfs (K, rows, cols)."""
+    rows, cols = x.shape
+    n = (ctypes.c_int * rows)()
+    rc = load().serial_emd_decompose_slices(plan, _ptr(x), rows, cols, _ptr(imfs), _ptr(residue),
+                                            n if wait else None, _stream(stream))
     _check(rc, plan)
     return list(n) if wait else None
 

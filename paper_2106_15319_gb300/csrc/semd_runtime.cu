@@ -631,7 +631,8 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
 
 template <typename R>
 semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *insts,
-                           const void *d_noise, int *n_imfs, cudaStream_t s)
+                           const void *d_noise, int *n_imfs, cudaStream_t s,
+                           int64_t imf_stride_all)
 {
     Workspace &ws = pl.ws;
     std::string &err = pl.err;
@@ -664,7 +665,7 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
             }
         } else {
             in.imf = q.d_imfs;
-            in.imf_stride = q.rows * q.cols;
+            in.imf_stride = imf_stride_all > 0 ? imf_stride_all : q.rows * q.cols;
             in.imf_serialized = 0;
             in.res = q.d_residue;
         }
@@ -884,9 +885,9 @@ ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_s
 }
 
 template semd_status decompose_impl<float>(semd_plan_s &, int, const semd_instance *,
-                                           const void *, int *, cudaStream_t);
+                                           const void *, int *, cudaStream_t, int64_t);
 template semd_status decompose_impl<double>(semd_plan_s &, int, const semd_instance *,
-                                            const void *, int *, cudaStream_t);
+                                            const void *, int *, cudaStream_t, int64_t);
 
 } // namespace semd
 
@@ -1011,8 +1012,8 @@ semd_status serial_emd_decompose(semd_plan_t plan, const void *d_x, const void *
     semd_instance in{d_x, plan->p.rows, plan->p.cols, d_imfs, d_residue};
     cudaStream_t s = (cudaStream_t)stream;
     return plan->p.precision == SEMD_FP64
-               ? decompose_impl<double>(*plan, 1, &in, d_noise, n_imfs, s)
-               : decompose_impl<float>(*plan, 1, &in, d_noise, n_imfs, s);
+               ? decompose_impl<double>(*plan, 1, &in, d_noise, n_imfs, s, 0)
+               : decompose_impl<float>(*plan, 1, &in, d_noise, n_imfs, s, 0);
 }
 
 semd_status serial_emd_decompose_batch(semd_plan_t plan, int count, const semd_instance *inst,
@@ -1044,8 +1045,49 @@ semd_status serial_emd_decompose_batch(semd_plan_t plan, int count, const semd_i
     }
     cudaStream_t s = (cudaStream_t)stream;
     return plan->p.precision == SEMD_FP64
-               ? decompose_impl<double>(*plan, count, inst, nullptr, n_imfs, s)
-               : decompose_impl<float>(*plan, count, inst, nullptr, n_imfs, s);
+               ? decompose_impl<double>(*plan, count, inst, nullptr, n_imfs, s, 0)
+               : decompose_impl<float>(*plan, count, inst, nullptr, n_imfs, s, 0);
+}
+
+semd_status serial_emd_decompose_slices(semd_plan_t plan, const void *d_x, int64_t rows,
+                                        int64_t cols, void *d_imfs, double *d_residue,
+                                        int *n_imfs, void *stream)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (!d_x || !d_imfs) {
+        plan->err = "null input or output pointer";
+        return SEMD_EINVAL;
+    }
+    if (plan->p.ensemble_trials > 1) {
+        plan->err = "slice-wise decomposition takes EMD plans only";
+        return SEMD_EINVAL;
+    }
+    if (rows < 1 || cols < 1 || rows > plan->ws.cap_inst) {
+        plan->err = "rows must be in [1, max_batch] and cols >= 1";
+        return SEMD_EINVAL;
+    }
+    if (cols > plan->L) {
+        plan->err = "a slice is longer than the plan's serialized length";
+        return SEMD_EBUDGET;
+    }
+    // signal i = row i, decomposed alone (one row: no serialization, no transitions); IMF
+    // k of signal i lands at k * rows * cols + i * cols
+    const size_t elem = plan->p.precision == SEMD_FP64 ? 8 : 4;
+    std::vector<semd_instance> in((size_t)rows);
+    for (int64_t i = 0; i < rows; ++i)
+        in[(size_t)i] = semd_instance{(const char *)d_x + (size_t)(i * cols) * elem, 1, cols,
+                                      (char *)d_imfs + (size_t)(i * cols) * elem,
+                                      d_residue ? d_residue + i * cols : nullptr};
+    cudaStream_t s = (cudaStream_t)stream;
+    const semd_params saved = plan->p;
+    plan->p.order = SEMD_ORDER_ROWS;
+    const semd_status st =
+        plan->p.precision == SEMD_FP64
+            ? decompose_impl<double>(*plan, (int)rows, in.data(), nullptr, n_imfs, s, rows * cols)
+            : decompose_impl<float>(*plan, (int)rows, in.data(), nullptr, n_imfs, s, rows * cols);
+    plan->p = saved;
+    return st;
 }
 
 semd_status serial_emd_plan_counts(semd_plan_t plan, int count, int *n_imfs, int *sifts)

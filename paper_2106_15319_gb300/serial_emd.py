@@ -77,6 +77,16 @@ class Plan:
         n = capi.serial_emd_decompose_batch(self.handle, items, stream, wait)
         return outs, n
 
+    def decompose_slices(self, x: torch.Tensor, imfs=None, residue=None, stream=None,
+                         wait: bool = True):
+        """Slice-wise standard EMD: every row of x decomposed on its own (the plan must hold
+        one row, with max_batch >= rows). Returns (imfs, residue, n per row)."""
+        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous() and x.dim() == 2
+        if imfs is None:
+            imfs, residue = self.outputs(*x.shape, device=x.device)
+        n = capi.serial_emd_decompose_slices(self.handle, x, imfs, residue, stream, wait)
+        return imfs, residue, n
+
     @property
     def tile(self) -> int:
         return capi.serial_emd_plan_get_tile(self.handle)

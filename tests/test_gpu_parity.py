@@ -433,3 +433,35 @@ def test_largest_serving_image_fp32():
         assert err <= TOL[capi.FP32_MIXED] or not _fp32_keeps_extrema(
             r.astype(np.float32).astype(np.float64), 10), (k, err)
         r = r - imfs[k].reshape(-1)
+
+
+# ------------------------------------------------------- slice-wise standard version
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_slices_match_oracle_per_row_and_batch(prec):
+    """The standard-version baseline of Sec. 4 (each signal decomposed on its own):
+    every row against the oracle's EMD of that row (FP64; FP32 given the same remainder),
+    and bit for bit against decompose_batch on the rows taken one by one."""
+    X = np.asarray(synth.tone_chirp_series(9, 1500, 4711), NP[prec])
+    rows, cols = X.shape
+    K = 7
+    plan = Plan(make_params(1, cols, precision=prec, transition_len=0, max_imfs=K),
+                max_batch=rows)
+    x = torch.from_numpy(X).cuda()
+    imfs, res, ns = plan.decompose_slices(x)
+    torch.cuda.synchronize()
+    gi, gr = imfs.double().cpu().numpy(), res.cpu().numpy()
+    for i in range(rows):
+        xi = X[i].astype(np.float64)
+        if prec == capi.FP64:
+            oi, orr, on, _ = O.emd(xi, K)
+            _check_imfs(gi[:, i], gr[i], ns[i], oi, orr, on, xi, prec, f"slice {i}")
+        else:
+            _check_fp32_given_input(gi[:, i], gr[i], ns[i], xi, K, f"slice {i}")
+    xs = [x[i:i + 1].contiguous() for i in range(rows)]
+    outs, nb = plan.decompose_batch(xs)
+    torch.cuda.synchronize()
+    assert list(nb) == list(ns)
+    for i in range(rows):
+        assert torch.equal(outs[i][0][:, 0], imfs[:, i]) and torch.equal(outs[i][1][0], res[i])
+    plan.close()
