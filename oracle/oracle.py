@@ -5,7 +5,7 @@ of the benchmark use it. The CUDA library never imports or links anything here.
 
 Each wrapper names the paper passage its C function follows (Zhang et al.,
 arXiv 2106.15319): serialization Sec. 3.2, de-serialization Sec. 3.3, EMD Sec. 2.1
-(Eq. 1, Steps 1-5), EEMD Sec. 2.2.
+(Eq. 1, Steps 1-5), EEMD and CEEMDAN Sec. 2.2.
 """
 from __future__ import annotations
 
@@ -77,6 +77,17 @@ def lib():
                                             ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, _dp, _dp, _dp, _ipint, ctypes.c_int]
+            L.oracle_ceemdan.restype = ctypes.c_int
+            L.oracle_ceemdan.argtypes = [_dp, _i64, _dp, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _dp, _dp, ctypes.c_int]
+            L.oracle_serial_ceemdan.restype = ctypes.c_int
+            L.oracle_serial_ceemdan.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                                ctypes.c_int]
             _lib = L
     return _lib
 
@@ -216,3 +227,39 @@ def serial_emd(X, D: int, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
                                 boundary, mirror_knots, trials, noise_rel_std, wp, _d(imfs),
                                 _d(res), sifts.ctypes.data_as(_ipint), int(store_f32))
     return imfs, res, int(n), sifts
+
+
+def ceemdan(x, w, noise_rel_std: float, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
+            sd_threshold: float = 0.2, max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR,
+            mirror_knots: int = 2, store_f32: bool = False):
+    """Sec. 2.2 CEEMDAN (Steps 1-4; Reading 12 of the C source): w is (trials, L).
+
+    Returns (modes (K, L), residue (L), number of modes)."""
+    x, w = _f64(x), _f64(w)
+    trials, L = w.shape
+    assert L == x.size
+    modes = np.empty((K, L), np.float64)
+    res = np.empty(L, np.float64)
+    n = lib().oracle_ceemdan(_d(x), L, _d(w), trials, noise_rel_std, K, stop, fixed_sifts,
+                             sd_threshold, max_sifts, boundary, mirror_knots, _d(modes),
+                             _d(res), int(store_f32))
+    return modes, res, int(n)
+
+
+def serial_ceemdan(X, D: int, K: int, w, noise_rel_std: float, stop: int = STOP_FIXED,
+                   fixed_sifts: int = 10, sd_threshold: float = 0.2, max_sifts: int = 50,
+                   boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2,
+                   store_f32: bool = False):
+    """Sec. 3 with CEEMDAN as the decomposition: serialize, CEEMDAN, de-serialize.
+    X is (N, M), w is (trials, L). Returns (modes (K, N, M), residue (N, M), count)."""
+    X, w = _f64(X), _f64(w)
+    N, M = X.shape
+    L = serial_length(M, N, D)
+    trials = w.shape[0]
+    assert w.shape == (trials, L)
+    modes = np.empty((K, N, M), np.float64)
+    res = np.empty((N, M), np.float64)
+    n = lib().oracle_serial_ceemdan(_d(X), M, N, D, K, stop, fixed_sifts, sd_threshold,
+                                    max_sifts, boundary, mirror_knots, trials, noise_rel_std,
+                                    _d(w), _d(modes), _d(res), int(store_f32))
+    return modes, res, int(n)

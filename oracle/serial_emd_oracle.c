@@ -12,6 +12,7 @@
  *                          matrix T, t = vec(T), x = t_{1:(M+D)N-D})
  *   1D EMD ............... Sec. 2.1, Eq. (1) and sifting Steps 1-5
  *   EEMD ................. Sec. 2.2, Steps 1-3
+ *   CEEMDAN .............. Sec. 2.2, the second list of Steps 1-4
  *   de-serialization ..... Sec. 3.3 (pad R with Z, reshape, drop the last D rows)
  * Where the paper is silent (interpolant, stop rule, end effects, ties) the
  * readings are fixed in one place each and named "Reading n" below:
@@ -35,6 +36,15 @@
  *   Reading 11 EEMD noise is added to the serialized signal; beta is
  *              noise_rel_std times the population std of x; trials with fewer
  *              IMFs contribute zeros to the average.
+ *   Reading 12 CEEMDAN (Sec. 2.2, Steps 1-4): E_k(w) is the k-th EMD mode of the
+ *              noise realization w (zero past its IMF count). Stage k = 0, 1, ...
+ *              starts from the residue r_k (r_0 = x) and runs only if r_k passes
+ *              Reading 9; beta_k is noise_rel_std times the population std of
+ *              r_k. Mode k+1 is the trial average of the first EMD mode of
+ *              r_k + beta_k w^(m) for k = 0 (the first EEMD mode, Step 1) and of
+ *              r_k + beta_k E_k(w^(m)) for k >= 1 (Steps 2 and 4; Step 4's
+ *              "c_2" is read as the mode being built); r_{k+1} = r_k - mode
+ *              (Step 3). Trials whose input has no IMF contribute zeros.
  *
  * store_f32 (off for the reference decomposition): rounds the sifted signal to
  * single precision at IMF start and after every sift, the two points where the
@@ -396,6 +406,97 @@ int oracle_eemd(const double *x, int64_t L, const double *w, int trials, double 
     free(cm);
     free(rm);
     return nmax;
+}
+
+/* ---------------------------------------------------- Sec. 2.2, CEEMDAN */
+
+/*
+ * CEEMDAN of x (length L) with the noise realizations w (trials x L), Reading 12.
+ * modes is K x L (slots past the produced count are zero), residue is L. The EMD
+ * runs inside (noise modes, first modes) use the given stop rule and boundary.
+ * Returns the number of modes produced.
+ */
+int oracle_ceemdan(const double *x, int64_t L, const double *w, int trials, double rel, int K,
+                   int stop, int fixed_sifts, double sd_threshold, int max_sifts, int boundary,
+                   int mirror_knots, double *modes, double *residue, int store_f32)
+{
+    const int KE = K - 1; /* noise modes E_1 .. E_{K-1} */
+    size_t ne = (size_t)trials * (size_t)(KE > 0 ? KE : 1) * (size_t)L;
+    double *E = (double *)malloc(ne * sizeof(double));
+    double *wr = (double *)malloc((size_t)L * sizeof(double));
+    double *r = (double *)malloc((size_t)L * sizeof(double));
+    double *in = (double *)malloc((size_t)L * sizeof(double));
+    double *c1 = (double *)malloc((size_t)L * sizeof(double));
+    double *acc = (double *)malloc((size_t)L * sizeof(double));
+    int32_t *sa = (int32_t *)malloc((size_t)L * sizeof(int32_t));
+    int32_t *sb = (int32_t *)malloc((size_t)L * sizeof(int32_t));
+    int k, m, n = 0;
+    int64_t q;
+    memset(modes, 0, (size_t)K * (size_t)L * sizeof(double));
+    /* E_k(w^(m)) for k = 1 .. K-1: the EMD of each noise realization */
+    if (KE > 0)
+        for (m = 0; m < trials; ++m)
+            oracle_emd(w + (int64_t)m * L, L, KE, stop, fixed_sifts, sd_threshold, max_sifts,
+                       boundary, mirror_knots, E + (int64_t)m * KE * L, wr, NULL, store_f32);
+    memcpy(r, x, (size_t)L * sizeof(double));
+    for (k = 0; k < K; ++k) {
+        double beta;
+        if (!has_enough_extrema(r, L, sa, sb))
+            break; /* r_k is the final residue */
+        beta = rel * oracle_std(r, L);
+        memset(acc, 0, (size_t)L * sizeof(double));
+        for (m = 0; m < trials; ++m) {
+            const double *e = k == 0 ? w + (int64_t)m * L : E + ((int64_t)m * KE + (k - 1)) * L;
+            for (q = 0; q < L; ++q)
+                in[q] = r[q] + beta * e[q];
+            /* first mode of r_k + beta_k E_k(w^(m)); zero when it has no IMF */
+            oracle_emd(in, L, 1, stop, fixed_sifts, sd_threshold, max_sifts, boundary,
+                       mirror_knots, c1, wr, NULL, store_f32);
+            for (q = 0; q < L; ++q)
+                acc[q] += c1[q];
+        }
+        for (q = 0; q < L; ++q) {
+            const double c = acc[q] / (double)trials;
+            modes[(int64_t)k * L + q] = c;
+            r[q] = r[q] - c; /* Step 3 */
+        }
+        ++n;
+    }
+    memcpy(residue, r, (size_t)L * sizeof(double));
+    free(E);
+    free(wr);
+    free(r);
+    free(in);
+    free(c1);
+    free(acc);
+    free(sa);
+    free(sb);
+    return n;
+}
+
+/*
+ * Serial-CEEMDAN (Sec. 3 with CEEMDAN as the decomposition F): serialize X,
+ * CEEMDAN of x with w (trials x L), de-serialize. Returns the mode count.
+ */
+int oracle_serial_ceemdan(const double *X, int64_t M, int64_t N, int64_t D, int K, int stop,
+                          int fixed_sifts, double sd_threshold, int max_sifts, int boundary,
+                          int mirror_knots, int trials, double noise_rel_std, const double *w,
+                          double *modes_out, double *residue_out, int store_f32)
+{
+    int64_t L = oracle_serial_length(M, N, D);
+    double *x = (double *)malloc((size_t)L * sizeof(double));
+    double *R = (double *)malloc((size_t)K * (size_t)L * sizeof(double));
+    double *r = (double *)malloc((size_t)L * sizeof(double));
+    int n;
+    oracle_serialize(X, M, N, D, x);
+    n = oracle_ceemdan(x, L, w, trials, noise_rel_std, K, stop, fixed_sifts, sd_threshold,
+                       max_sifts, boundary, mirror_knots, R, r, store_f32);
+    oracle_deserialize(R, K, M, N, D, modes_out);
+    oracle_deserialize(r, 1, M, N, D, residue_out);
+    free(x);
+    free(R);
+    free(r);
+    return n;
 }
 
 /* ------------------------------------------------------ Sec. 3 end to end */

@@ -320,6 +320,109 @@ def test_eemd_average_and_reconstruction():
     np.testing.assert_allclose(recon, x + beta * w.mean(0), rtol=0, atol=1e-12)
 
 
+# --------------------------------------------------------------- Sec. 2.2 CEEMDAN
+
+@pytest.mark.parametrize("trials", [1, 2])
+def test_ceemdan_zero_noise_equals_emd(trials):
+    """With beta = 0 every trial's input is the residue itself, so mode k+1 is the first
+    EMD mode of r_k: the (k+1)-th IMF of plain EMD (averaging 1 or 2 equal values is
+    exact)."""
+    x = synth.workload_series_3x1024()[1]
+    w = synth.white_noise(trials, x.size, 21)
+    m, r, n = O.ceemdan(x, w, 0.0, 7)
+    imfs, res, n2, _ = O.emd(x, 7)
+    assert n == n2
+    assert np.array_equal(m, imfs) and np.array_equal(r, res)
+
+
+def test_ceemdan_first_mode_is_eemd_first_mode():
+    """Step 1: the first CEEMDAN mode is the first EEMD mode with beta = rel * std(x)."""
+    x = synth.grating_image(24, 3).reshape(-1)
+    w = synth.white_noise(5, x.size, 22)
+    m, r, n = O.ceemdan(x, w, 0.2, 5)
+    e, _, _ = O.eemd(x, w, 0.2 * O.std(x), 1)
+    assert n == 5
+    assert np.array_equal(m[0], e[0])
+    np.testing.assert_allclose(m.sum(0) + r, x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def test_alternating_sequence_is_its_own_imf():
+    """An alternating sequence with a power-of-two amplitude: every interior sample is an
+    extremum, both envelopes are constant (natural splines through equal values, exact in
+    binary floating point), their mean is zero, so the sequence is its only IMF."""
+    L = 301
+    for a in (1.0, 0.5, 4.0):
+        w = a * (-1.0) ** np.arange(L)
+        imfs, res, n, _ = O.emd(w, 4)
+        assert n == 1
+        assert np.array_equal(imfs[0], w) and not imfs[1:].any() and not res.any()
+
+
+def test_ceemdan_noise_modes_closed_form():
+    """Noise realizations whose EMD is known exactly: w^(m) = a_m (-1)^q has
+    E_1(w^(m)) = w^(m) and E_k(w^(m)) = 0 for k >= 2. So (Steps 1-4) mode 1 is the first
+    EEMD mode of x + beta_0 w, mode 2 the trial average of the first EMD mode of
+    r_1 + beta_1 w^(m) with beta_1 = rel * std(r_1), and every later mode the first EMD
+    mode of the residue alone. A wrong noise-mode index, noise reused at every stage or
+    beta taken from x instead of r_k each changes modes 2 or 3."""
+    x = synth.workload_series_3x1024()[0][:700]
+    L = x.size
+    amps = (1.0, 2.0, 0.5)
+    w = np.stack([a * (-1.0) ** np.arange(L) for a in amps])
+    rel, K = 0.3, 6
+    m, r, n = O.ceemdan(x, w, rel, K)
+    rk = x.copy()
+    expect = []
+    for k in range(K):
+        c = np.zeros(L)
+        if k >= 2:
+            ck, _, nk, _ = O.emd(rk, 1)
+            if nk == 0:
+                break
+            for _ in amps:  # the trial average of equal first modes, summed in trial order
+                c += ck[0]
+        else:
+            beta = rel * O.std(rk)
+            for wm in w:
+                ck, _, _, _ = O.emd(rk + beta * wm, 1)
+                c += ck[0]
+        c /= len(amps)
+        expect.append(c)
+        rk = rk - c
+    assert n == len(expect) >= 4
+    for k, c in enumerate(expect):
+        assert np.array_equal(m[k], c), k
+    assert np.array_equal(r, rk)
+    assert not m[n:].any()
+
+
+def test_ceemdan_no_extrema_and_one_mode():
+    """Stage 0 runs only if x passes the IMF-start test: a ramp gives no mode. K = 1
+    gives the first EEMD mode and residue x minus it."""
+    L = 200
+    ramp = np.linspace(-1.0, 3.0, L)
+    w = synth.white_noise(3, L, 23)
+    m, r, n = O.ceemdan(ramp, w, 0.2, 4)
+    assert n == 0 and not m.any() and np.array_equal(r, ramp)
+    x = synth.workload_series_3x1024()[2][:L]
+    m, r, n = O.ceemdan(x, w, 0.2, 1)
+    e, _, _ = O.eemd(x, w, 0.2 * O.std(x), 1)
+    assert n == 1 and np.array_equal(m[0], e[0]) and np.array_equal(r, x - e[0])
+
+
+def test_serial_ceemdan_serializes_and_deserializes():
+    X = synth.workload_series_3x1024()[:, :300]
+    D = 60
+    L = O.serial_length(300, 3, D)
+    w = synth.white_noise(3, L, 24)
+    modes, res, n = O.serial_ceemdan(X, D, 5, w, 0.2)
+    xs = O.serialize(X, D)
+    m1, r1, n1 = O.ceemdan(xs, w, 0.2, 5)
+    assert n == n1
+    assert np.array_equal(modes, O.deserialize(m1, 300, 3, D))
+    assert np.array_equal(res, O.deserialize(r1, 300, 3, D)[0])
+
+
 # ------------------------------------------------------------------ Sec. 3 end to end
 
 def test_serial_emd_single_signal_is_plain_emd():
