@@ -433,14 +433,18 @@ def arm_ours(args):
             line["standard_slices"] = standard_slices(args, device, flush, world)
             line["standard_slices"]["serial_over_slices_time"] = \
                 line["ms_per_step"] / line["standard_slices"]["ms_per_step"]
+        if not args.no_batched:
+            line["ceemdan"] = ceemdan_legs(args, device, flush, world)
         if not args.no_serving:
             line["serving"] = serving(args, device)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
-    elif not args.no_batched:
+    elif not args.no_batched:  # the same collective calls as rank 0 (max over ranks)
         batched_eemd(args, device, flush, peak, peak_kind, world)
         batched_images(args, device, flush, peak, peak_kind, world)
+        standard_slices(args, device, flush, world)
+        ceemdan_legs(args, device, flush, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -622,6 +626,60 @@ def standard_slices(args, device, flush, world):
                         f"{wl['S']} sifts/IMF, <={wl['K']} IMFs",
             "value": world * st.sample_sifts / (m * 1e-3), "unit": UNIT, "ms_per_step": m,
             "steps": steps, "dtype": "f32", "imfs_per_row_mean": float(np.mean(n))}
+
+
+def ceemdan_legs(args, device, flush, world):
+    """Serial-CEEMDAN (Sec. 2.2 Steps 1-4 inside Sec. 3) on stand-ins for the two inputs the
+    paper times it on: its 6-variate tone set (6 x 1000 samples, D = 50) and a 101 x 101
+    texture image (D = 20), with 100 noise realizations, noise_rel_std 0.2, 10 sifts per
+    mode, at most 10 modes. One step = one full CEEMDAN call (EMD of the noise
+    realizations, then every stage). The paper's CPU times are context only."""
+    import torch
+    from paper_2106_15319_gb300 import capi, synth
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    trials = 100
+    cases = [("mask6x1000_D50", synth.paper_mask_series(), 50, 1154.97),
+             ("texture101_D20", synth.grating_image(101, 2106), 20, 20580.0)]
+    out = {}
+    steps = max(1, min(args.steps, 5))
+    for name, X0, D, paper_ms in cases:
+        rows, cols = X0.shape
+        N, M = rows, cols
+        L = M * N + D * N - D
+        for prec, np_t in ((capi.FP32_MIXED, np.float32), (capi.FP64, np.float64)):
+            X = np.ascontiguousarray(X0, np_t)
+            w = synth.white_noise(trials, L, 9001).astype(np_t)
+            plan = Plan(make_params(rows, cols, precision=prec, transition_len=D, max_imfs=10,
+                                    ensemble_trials=trials, noise_rel_std=0.2))
+            x = torch.from_numpy(X).to(device)
+            wt = torch.from_numpy(w).to(device)
+            modes, res = plan.outputs(rows, cols, device=device)
+            stream = torch.cuda.Stream(device)
+            ms = []
+            with torch.cuda.stream(stream):
+                for _ in range(min(args.warmup, 3)):
+                    plan.ceemdan(x, wt, modes, res, stream=stream, wait=False)
+                stream.synchronize()
+                for _ in range(steps):
+                    _flush_l2(flush)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    plan.ceemdan(x, wt, modes, res, stream=stream, wait=False)
+                    b.record(stream)
+                    stream.synchronize()
+                    ms.append(a.elapsed_time(b))
+            st = plan.stats()
+            n = plan.counts(1)[0][0]
+            plan.close()
+            m = max_over_ranks(statistics.mean(ms), world)
+            key = f"{name}_{'fp32' if prec == capi.FP32_MIXED else 'fp64'}"
+            out[key] = {"ms_per_step": m, "value": world * st.sample_sifts / (m * 1e-3),
+                        "unit": UNIT, "modes": int(n), "L": L, "trials": trials,
+                        "launches_per_step": int(st.kernel_launches),
+                        "cuda_graph": bool(st.used_graph),
+                        "paper_cpu_ms_context": paper_ms}
+    return out
 
 
 def main():

@@ -74,8 +74,10 @@ typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precisio
  *  precision        SEMD_FP64: FP64 end to end. SEMD_FP32_MIXED: sifting in FP32,
  *                   FP64 in the cross-tile spline interface solve, the stop
  *                   reductions, the residue and the EEMD average.
- *  ensemble_trials  <= 1: EMD. > 1: EEMD with that many noise realizations (Sec. 2.2).
- *  noise_rel_std    EEMD beta = noise_rel_std * population std of the serialized x.
+ *  ensemble_trials  <= 1: EMD. > 1: EEMD with that many noise realizations (Sec. 2.2);
+ *                   such plans also run CEEMDAN (serial_emd_ceemdan).
+ *  noise_rel_std    EEMD beta = noise_rel_std * population std of the serialized x;
+ *                   CEEMDAN beta_k = noise_rel_std * population std of the residue r_k.
  */
 typedef struct semd_params {
     int64_t rows;
@@ -166,8 +168,31 @@ semd_status serial_emd_decompose_slices(semd_plan_t plan, const void *d_x, int64
                                         int64_t cols, void *d_imfs, double *d_residue,
                                         int *n_imfs, void *stream);
 
+/*
+ * Serial-CEEMDAN of one input of the plan's shape (Sec. 3 with the CEEMDAN of Sec. 2.2,
+ * Steps 1-4, as the decomposition), enqueued on `stream`. The plan must be an ensemble
+ * plan (ensemble_trials = T >= 2, max_batch 1); EINVAL otherwise. With r_0 the serialized
+ * input and E_k(w) the k-th EMD mode of a noise realization w (zero past its mode count;
+ * the EMD uses the plan's stop rule and boundary), stage k = 0 .. K-1 runs while r_k has
+ * at least one maximum, one minimum and three extrema: beta_k = noise_rel_std * population
+ * std of r_k, mode k+1 = the average over the T trials of the first EMD mode of
+ * r_k + beta_k w^(m) (k = 0: the first EEMD mode, Step 1) or of r_k + beta_k E_k(w^(m))
+ * (k >= 1, Steps 2 and 4), and r_{k+1} = r_k - mode (Step 3), in FP64.
+ *  d_x        input, rows x cols (plan precision).
+ *  d_noise    T x L white-noise realizations w^(m) (plan precision, L = MN + DN - D).
+ *  d_modes    output, K x rows x cols (plan precision), zero past the mode count.
+ *  d_residue  output, rows x cols doubles (the final r), or NULL.
+ *  n_modes    host; if not NULL the call waits for the stream and stores the mode count;
+ *             if NULL, serial_emd_plan_counts() gives it after the stream has finished.
+ * Inputs and outputs stay owned by the caller and must stay valid until the stream has
+ * finished. The plan may not be used by two calls at once. Errors: EINVAL, ECUDA.
+ */
+semd_status serial_emd_ceemdan(semd_plan_t plan, const void *d_x, const void *d_noise,
+                               void *d_modes, double *d_residue, int *n_modes, void *stream);
+
 /* After the stream has finished: IMF counts (count entries) and sifts per IMF
- * (count x K entries, may be NULL) of the plan's last decompose call. */
+ * (count x K entries, may be NULL) of the plan's last decompose call (for a CEEMDAN
+ * call: the mode count, and zero sifts). */
 semd_status serial_emd_plan_counts(semd_plan_t plan, int count, int *n_imfs, int *sifts);
 
 /*

@@ -81,6 +81,9 @@ SIGNATURES = {
                                                    ctypes.c_int64, ctypes.c_int64,
                                                    ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "serial_emd_ceemdan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "serial_emd_plan_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
@@ -207,6 +210,15 @@ def serial_emd_decompose_slices(plan: int, x, imfs, residue, stream=None, wait: 
                                             n if wait else None, _stream(stream))
     _check(rc, plan)
     return list(n) if wait else None
+
+
+def serial_emd_ceemdan(plan: int, x, noise, modes, residue, stream=None, wait: bool = True):
+    """Serial-CEEMDAN (Sec. 2.2 Steps 1-4 inside Sec. 3) of x with the noise (trials, L)."""
+    n = ctypes.c_int(-1)
+    rc = load().serial_emd_ceemdan(plan, _ptr(x), _ptr(noise), _ptr(modes), _ptr(residue),
+                                   ctypes.byref(n) if wait else None, _stream(stream))
+    _check(rc, plan)
+    return n.value if wait else None
 
 
 def serial_emd_plan_counts(plan: int, count: int, max_imfs: int):

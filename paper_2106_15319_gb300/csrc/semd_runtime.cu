@@ -23,6 +23,22 @@ static thread_local std::string g_plan_create_error;
 // x = (r+1)/(D+1) * X(i+1, D-1-r) + (D-r)/(D+1) * X(i, M-1-r). Written in FP64 to r0.
 // Only instances that have not started (state MODE_INIT) are serialized.
 template <typename R>
+__device__ __forceinline__ double serial_sample(const R *X, int64_t M, int64_t N, int64_t D,
+                                                int order, int64_t p)
+{
+    const int64_t i = p / (M + D), m = p - i * (M + D);
+    if (m < M)
+        return (double)X[order == 0 ? i * M + m : m * N + i];
+    const int64_t r = m - M;
+    const int64_t ma = D - 1 - r, mb = M - 1 - r;
+    const double xa = (double)X[order == 0 ? (i + 1) * M + ma : ma * N + (i + 1)];
+    const double xb = (double)X[order == 0 ? i * M + mb : mb * N + i];
+    const double a = (double)(r + 1) / (double)(D + 1);
+    const double af = (double)(D - r) / (double)(D + 1);
+    return __dadd_rn(__dmul_rn(xa, a), __dmul_rn(xb, af));
+}
+
+template <typename R>
 __global__ void k_serialize(const Inst *inst, const State *state, const int32_t *tile_inst,
                             int tile, int only_first)
 {
@@ -33,24 +49,8 @@ __global__ void k_serialize(const Inst *inst, const State *state, const int32_t 
     const int64_t ts = (int64_t)(gt - in.tile0) * tile;
     const int64_t cnt = min((int64_t)tile, in.L - ts);
     const R *X = (const R *)in.x;
-    const int64_t M = in.M, N = in.N, D = in.D;
-    for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-        const int64_t p = ts + idx;
-        const int64_t i = p / (M + D), m = p - i * (M + D);
-        double v;
-        if (m < M) {
-            v = (double)X[in.order == 0 ? i * M + m : m * N + i];
-        } else {
-            const int64_t r = m - M;
-            const int64_t ma = D - 1 - r, mb = M - 1 - r;
-            const double xa = (double)X[in.order == 0 ? (i + 1) * M + ma : ma * N + (i + 1)];
-            const double xb = (double)X[in.order == 0 ? i * M + mb : mb * N + i];
-            const double a = (double)(r + 1) / (double)(D + 1);
-            const double af = (double)(D - r) / (double)(D + 1);
-            v = __dadd_rn(__dmul_rn(xa, a), __dmul_rn(xb, af));
-        }
-        in.r[0][p] = v;
-    }
+    for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x)
+        in.r[0][ts + idx] = serial_sample<R>(X, in.M, in.N, in.D, in.order, ts + idx);
 }
 
 // EEMD beta = rel * population std of the serialized x (Sec. 2.2 Step 1), one CTA.
@@ -158,6 +158,166 @@ __global__ void k_eemd_average(const Inst *inst, const State *state, int trials,
                 acc += inst[m].r[state[m].rpar][p];
             res[dst] = acc / (double)trials;
         }
+    }
+}
+
+// ------------------------------------------------------------- CEEMDAN (Sec. 2.2)
+//
+// Stage k (k = 0 .. K-1) of a CEEMDAN call: the IMF-start test and beta_k on r_k, the
+// trials' inputs r_k + beta_k E_k(w^(m)) (E_0(w) = w), the first EMD mode of every trial
+// (the sifting kernels with one IMF), then mode k+1 = the trial average and
+// r_{k+1} = r_k - mode.
+
+// After the EMD of the noise realizations: keep each realization's mode count (its modes
+// past the count are zero) and point every trial's IMF output at the scratch slot K-1,
+// which no stage reads (stage k reads slot k-1 <= K-2), for the stages' first modes.
+__global__ void k_ce_setup(const CeArgs *ca, Inst *inst, const State *state, CeState *cs,
+                           int noise_ran, int elem)
+{
+    const CeArgs &a = *ca;
+    for (int m = threadIdx.x; m < a.trials; m += blockDim.x) {
+        a.ncount[m] = noise_ran ? state[m].imf_count : 0;
+        inst[m].imf = (char *)a.E + (size_t)((int64_t)m * a.K + (a.K - 1)) * a.slot * elem;
+    }
+    if (threadIdx.x == 0) {
+        cs->beta = 0.0;
+        cs->done = 0;
+        cs->n = 0;
+    }
+}
+
+// r_0 = the serialized input (Sec. 3.2).
+template <typename R>
+__global__ void k_ce_serialize(const CeArgs *ca)
+{
+    const CeArgs &a = *ca;
+    const R *X = (const R *)a.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.L;
+         p += (int64_t)gridDim.x * blockDim.x)
+        a.r[p] = serial_sample<R>(X, a.M, a.N, a.D, a.order, p);
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum_1024(T v, T *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULLMASK, v, o);
+    __syncthreads(); // sh may still be read by a previous call
+    if (lane == 0)
+        sh[warp] = v;
+    __syncthreads();
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULLMASK, v, o);
+    return v;
+}
+
+// Stage test, one CTA of 1024 threads: r_k must pass the IMF-start test (n_max >= 1,
+// n_min >= 1, n_max + n_min >= 3, extrema by the rule of Sec. 2.1 Step 1), else this and
+// every later stage is empty; beta_k = rel * population std of r_k.
+__global__ void __launch_bounds__(1024) k_ce_stage_test(const CeArgs *ca, CeState *cs)
+{
+    if (cs->done)
+        return;
+    const CeArgs &a = *ca;
+    const double *r = a.r;
+    const int64_t L = a.L;
+    __shared__ double shd[32];
+    __shared__ int shi[32];
+    double s = 0.0;
+    int nmax = 0, nmin = 0;
+    for (int64_t k = threadIdx.x; k < L; k += blockDim.x) {
+        const double c = r[k];
+        s += c;
+        if (k >= 1 && k + 1 < L) {
+            const double l = r[k - 1], rr = r[k + 1];
+            nmax += (l < c && c >= rr) ? 1 : 0;
+            nmin += (l > c && c <= rr) ? 1 : 0;
+        }
+    }
+    const double mean = block_sum_1024(s, shd) / (double)L;
+    nmax = block_sum_1024(nmax, shi);
+    nmin = block_sum_1024(nmin, shi);
+    double v = 0.0;
+    for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
+        v += (r[k] - mean) * (r[k] - mean);
+    v = block_sum_1024(v, shd);
+    if (threadIdx.x == 0) {
+        if (nmax >= 1 && nmin >= 1 && nmax + nmin >= 3) {
+            cs->n += 1;
+            cs->beta = a.rel * sqrt(v / (double)L);
+        } else {
+            cs->done = 1;
+        }
+    }
+}
+
+// The trials' stage inputs r_k + beta_k E_k(w^(m)) as their residues for the INIT pass;
+// for an empty stage every trial is marked done instead (its first mode counts as zero).
+template <typename R>
+__global__ void k_ce_stage_init(const CeArgs *ca, const Inst *inst, State *state,
+                                const CeState *cs, int stage)
+{
+    const CeArgs &a = *ca;
+    if (cs->done) {
+        if (blockIdx.x == 0)
+            for (int m = threadIdx.x; m < a.trials; m += blockDim.x)
+                state[m].mode = MODE_DONE;
+        return;
+    }
+    const double beta = cs->beta;
+    const R *w = (const R *)a.noise, *E = (const R *)a.E;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.L;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double rk = a.r[p];
+        for (int m = 0; m < a.trials; ++m) {
+            double e;
+            if (stage == 0)
+                e = (double)w[(int64_t)m * a.L + p];
+            else
+                e = stage - 1 < a.ncount[m]
+                        ? (double)E[((int64_t)m * a.K + (stage - 1)) * a.slot + p]
+                        : 0.0;
+            inst[m].r[0][p] = __dadd_rn(rk, __dmul_rn(beta, e));
+        }
+    }
+}
+
+// Mode k+1 = the average of the trials' first modes (zero for a trial without one), in
+// FP64 and trial order; r_{k+1} = r_k - mode (Step 3); the mode de-serialized (Sec. 3.3).
+template <typename R>
+__global__ void k_ce_average(const CeArgs *ca, const Inst *inst, const State *state, int stage)
+{
+    const CeArgs &a = *ca;
+    R *out = (R *)a.modes + (int64_t)stage * a.M * a.N;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.L;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int m = 0; m < a.trials; ++m)
+            if (state[m].imf_count >= 1)
+                acc += (double)((const R *)inst[m].imf)[p];
+        const double c = acc / (double)a.trials;
+        a.r[p] = a.r[p] - c;
+        int64_t dst;
+        if (deser_index(p, a.M, a.N, a.D, a.order, dst))
+            out[dst] = (R)c;
+    }
+}
+
+// The final residue, de-serialized (Sec. 3.3).
+__global__ void k_ce_finish(const CeArgs *ca)
+{
+    const CeArgs &a = *ca;
+    if (!a.res)
+        return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.L;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t dst;
+        if (deser_index(p, a.M, a.N, a.D, a.order, dst))
+            a.res[dst] = a.r[p];
     }
 }
 
@@ -404,8 +564,13 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
         {(void **)&d_stats, sizeof(Stats)},
     };
-    if (eemd_elems > 0)
+    if (eemd_elems > 0) {
         reqs.push_back({&eemd_scratch, (size_t)eemd_elems * elem});
+        reqs.push_back({(void **)&d_ce, sizeof(CeArgs)});
+        reqs.push_back({(void **)&d_cestate, sizeof(CeState)});
+        reqs.push_back({(void **)&d_cecount, (size_t)insts * 4});
+        reqs.push_back({(void **)&d_ce_r, (size_t)(samples / insts) * 8});
+    }
     size_t total = 0;
     for (auto &r : reqs)
         total += (r.bytes + 255) & ~(size_t)255;
@@ -435,6 +600,10 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         e = cudaMallocHost((void **)&h_misc, (size_t)tiles * 2 * 4 + 64);
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&h_stats, sizeof(Stats));
+    if (e == cudaSuccess && eemd_elems > 0)
+        e = cudaMallocHost((void **)&h_ce, sizeof(CeArgs));
+    if (e == cudaSuccess && eemd_elems > 0)
+        e = cudaMallocHost((void **)&h_cestate, sizeof(CeState));
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&staging_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -470,6 +639,10 @@ void Workspace::release()
         cudaFreeHost(h_misc);
     if (h_stats)
         cudaFreeHost(h_stats);
+    if (h_ce)
+        cudaFreeHost(h_ce);
+    if (h_cestate)
+        cudaFreeHost(h_cestate);
     *this = Workspace();
 }
 
@@ -572,6 +745,38 @@ struct LaunchTimer {
     }
 };
 
+// The sifting passes of one decomposition: `iters` pass + interface-solve launches (the
+// state machine idles finished instances). With the SD stop rule and no capture, every
+// eighth iteration reads the count of running instances and ends the loop at zero.
+template <typename R>
+static semd_status sift_loop(semd_plan_s &pl, ReduceArgs ra, int ninst, int64_t ntiles,
+                             int iters, cudaStream_t s, Profiler *prof, bool capture,
+                             int64_t &launches)
+{
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    const bool sd = ra.stop == SEMD_STOP_SD;
+    for (int it = 0; it < iters; ++it) {
+        {
+            LaunchTimer t(prof, s, 0);
+            launch_pass<R>(ws, ntiles, sd, s);
+        }
+        ra.active = ws.d_active + it;
+        {
+            LaunchTimer t(prof, s, 1);
+            launch_reduce<R>(ra, ninst, s);
+        }
+        launches += 2;
+        if (!capture && sd && (it % 8) == 7) {
+            SEMD_CU(cudaMemcpyAsync(ws.h_misc, ws.d_active + it, 4, cudaMemcpyDeviceToHost, s));
+            SEMD_CU(cudaStreamSynchronize(s));
+            if (((int32_t *)ws.h_misc)[0] == 0)
+                break;
+        }
+    }
+    return SEMD_OK;
+}
+
 // All device work of one decomposition after the descriptors are uploaded. Everything
 // here is stream-ordered and, for the fixed sift count, free of host synchronization,
 // so it can be captured into a CUDA graph.
@@ -598,24 +803,9 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
         launches += 2;
     }
     ReduceArgs ra = reduce_args(ws, p);
-    for (int it = 0; it < iters; ++it) {
-        {
-            LaunchTimer t(prof, s, 0);
-            launch_pass<R>(ws, ntiles, p.stop == SEMD_STOP_SD, s);
-        }
-        ra.active = ws.d_active + it;
-        {
-            LaunchTimer t(prof, s, 1);
-            launch_reduce<R>(ra, ninst, s);
-        }
-        launches += 2;
-        if (!capture && p.stop == SEMD_STOP_SD && (it % 8) == 7) {
-            SEMD_CU(cudaMemcpyAsync(ws.h_misc, ws.d_active + it, 4, cudaMemcpyDeviceToHost, s));
-            SEMD_CU(cudaStreamSynchronize(s));
-            if (((int32_t *)ws.h_misc)[0] == 0)
-                break;
-        }
-    }
+    semd_status st = sift_loop<R>(pl, ra, ninst, ntiles, iters, s, prof, capture, launches);
+    if (st != SEMD_OK)
+        return st;
     if (eemd) {
         k_eemd_average<R><<<ntiles0, 256, 0, s>>>(ws.d_inst, ws.d_state, ninst, p.max_imfs,
                                                   (const R *)ws.eemd_scratch, ws.tile);
@@ -721,9 +911,171 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     SEMD_CU(cudaMemcpyAsync(ws.h_stats, ws.d_stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
     pl.last_ninst = ninst;
     pl.last_count = eemd ? 1 : count;
+    pl.last_ceemdan = false;
     if (n_imfs) {
         SEMD_CU(cudaStreamSynchronize(s));
         pl.counts(pl.last_count, n_imfs, nullptr);
+    }
+    return SEMD_OK;
+}
+
+// All device work of one CEEMDAN call (Sec. 2.2, Steps 1-4) after the descriptors and
+// the call's arguments are uploaded: the EMD of the noise realizations, then K stages.
+// Stream-ordered and, for the fixed sift count, free of host synchronization.
+template <typename R>
+static semd_status enqueue_ceemdan(semd_plan_s &pl, int64_t ntiles, cudaStream_t s, bool capture)
+{
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    const semd_params &p = pl.p;
+    const int trials = p.ensemble_trials, K = p.max_imfs;
+    Profiler *prof = capture ? nullptr : &pl.prof;
+    int64_t launches = 0;
+    const int64_t L = ws.h_ce->L;
+    const unsigned eg = (unsigned)std::min<int64_t>((L + 255) / 256, 4 * 304);
+    SEMD_CU(cudaMemsetAsync(ws.d_stats, 0, sizeof(Stats), s));
+    ReduceArgs ra = reduce_args(ws, p);
+    semd_status st;
+    if (K >= 2) { // E_1 .. E_{K-1} of every realization: plain EMD with K-1 IMFs
+        semd_params pn = p;
+        pn.max_imfs = K - 1;
+        const int iters = max_iterations(pn);
+        SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)trials * sizeof(State), s));
+        SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
+        k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
+                                                          ws.tile, 0);
+        ++launches;
+        ra.K = K - 1;
+        st = sift_loop<R>(pl, ra, trials, ntiles, iters, s, prof, capture, launches);
+        if (st != SEMD_OK)
+            return st;
+    }
+    k_ce_setup<<<1, 256, 0, s>>>(ws.d_ce, ws.d_inst, ws.d_state, ws.d_cestate, K >= 2 ? 1 : 0,
+                                 (int)sizeof(R));
+    k_ce_serialize<R><<<eg, 256, 0, s>>>(ws.d_ce);
+    launches += 2;
+    semd_params p1 = p;
+    p1.max_imfs = 1;
+    const int iters1 = max_iterations(p1);
+    ra.K = 1;
+    for (int k = 0; k < K; ++k) {
+        k_ce_stage_test<<<1, 1024, 0, s>>>(ws.d_ce, ws.d_cestate);
+        SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)trials * sizeof(State), s));
+        SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters1 * 4, s));
+        k_ce_stage_init<R><<<eg, 256, 0, s>>>(ws.d_ce, ws.d_inst, ws.d_state, ws.d_cestate, k);
+        launches += 2;
+        st = sift_loop<R>(pl, ra, trials, ntiles, iters1, s, prof, capture, launches);
+        if (st != SEMD_OK)
+            return st;
+        k_ce_average<R><<<eg, 256, 0, s>>>(ws.d_ce, ws.d_inst, ws.d_state, k);
+        ++launches;
+    }
+    k_ce_finish<<<eg, 256, 0, s>>>(ws.d_ce);
+    ++launches;
+    SEMD_CU(cudaGetLastError());
+    pl.stat_launches = launches;
+    return SEMD_OK;
+}
+
+template <typename R>
+semd_status ceemdan_impl(semd_plan_s &pl, const void *d_x, const void *d_noise, void *d_modes,
+                         double *d_residue, int *n_imfs, cudaStream_t s)
+{
+    Workspace &ws = pl.ws;
+    std::string &err = pl.err;
+    const semd_params &p = pl.p;
+    const int trials = p.ensemble_trials, K = p.max_imfs;
+    SEMD_CU(cudaEventSynchronize(ws.staging_done)); // staging buffers are free again
+    int64_t M, N, D;
+    if (!geometry(p, p.rows, p.cols, p.order, M, N, D, err))
+        return SEMD_EINVAL;
+    const int64_t L = serial_length(M, N, D);
+    const int64_t slot = (L + 31) & ~(int64_t)31;
+    // the trials, first as the EMD of the noise realizations (one plain signal each)
+    for (int m = 0; m < trials; ++m) {
+        Inst in{};
+        in.L = L;
+        in.M = L;
+        in.N = 1;
+        in.D = 0;
+        in.order = 0;
+        in.x = (const char *)d_noise + (size_t)m * (size_t)L * sizeof(R);
+        in.imf = (char *)ws.eemd_scratch + (size_t)m * K * slot * sizeof(R);
+        in.imf_stride = slot;
+        in.imf_serialized = 1;
+        in.res = nullptr;
+        ws.h_inst[m] = in;
+    }
+    CeArgs &a = *ws.h_ce;
+    a = CeArgs{};
+    a.x = d_x;
+    a.noise = d_noise;
+    a.E = ws.eemd_scratch;
+    a.modes = d_modes;
+    a.res = d_residue;
+    a.r = ws.d_ce_r;
+    a.ncount = ws.d_cecount;
+    a.M = M;
+    a.N = N;
+    a.D = D;
+    a.L = L;
+    a.slot = slot;
+    a.order = p.order;
+    a.trials = trials;
+    a.K = K;
+    a.rel = p.noise_rel_std;
+    SEMD_CU(cudaMemcpyAsync(ws.d_ce, ws.h_ce, sizeof(CeArgs), cudaMemcpyHostToDevice, s));
+    int64_t ntiles;
+    semd_status st = ws.layout(trials, ntiles, s, err); // records staging_done
+    if (st != SEMD_OK)
+        return st;
+    const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
+    pl.prof.reset();
+    if (use_graph) {
+        const GraphKey key{trials, ntiles, ws.h_inst[0].ntiles, ws.max_ntiles, ws.tile};
+        if (!pl.ce_graph_exec || !(pl.ce_graph_key == key)) {
+            if (pl.ce_graph_exec) {
+                cudaGraphExecDestroy(pl.ce_graph_exec);
+                pl.ce_graph_exec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            SEMD_CU(cudaStreamBeginCapture(pl.gstream, cudaStreamCaptureModeThreadLocal));
+            st = enqueue_ceemdan<R>(pl, ntiles, pl.gstream, true);
+            cudaError_t ce = cudaStreamEndCapture(pl.gstream, &g);
+            if (st != SEMD_OK) {
+                if (g)
+                    cudaGraphDestroy(g);
+                return st;
+            }
+            SEMD_CU(ce);
+            ce = cudaGraphInstantiate(&pl.ce_graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            SEMD_CU(ce);
+            pl.ce_graph_key = key;
+            pl.ce_graph_launches = pl.stat_launches;
+        }
+        SEMD_CU(cudaEventRecord(pl.ev_in, s));
+        SEMD_CU(cudaStreamWaitEvent(pl.gstream, pl.ev_in, 0));
+        SEMD_CU(cudaGraphLaunch(pl.ce_graph_exec, pl.gstream));
+        SEMD_CU(cudaEventRecord(pl.ev_out, pl.gstream));
+        SEMD_CU(cudaStreamWaitEvent(s, pl.ev_out, 0));
+        pl.stat_launches = pl.ce_graph_launches;
+        pl.stat_graph = 1;
+    } else {
+        st = enqueue_ceemdan<R>(pl, ntiles, s, false);
+        if (st != SEMD_OK)
+            return st;
+        pl.stat_graph = 0;
+    }
+    SEMD_CU(cudaMemcpyAsync(ws.h_cestate, ws.d_cestate, sizeof(CeState), cudaMemcpyDeviceToHost,
+                            s));
+    SEMD_CU(cudaMemcpyAsync(ws.h_stats, ws.d_stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
+    pl.last_ninst = trials;
+    pl.last_count = 1;
+    pl.last_ceemdan = true;
+    if (n_imfs) {
+        SEMD_CU(cudaStreamSynchronize(s));
+        *n_imfs = ws.h_cestate->n;
     }
     return SEMD_OK;
 }
@@ -897,7 +1249,9 @@ void semd_plan_s::counts(int count, int *n_imfs, int *sifts) const
     const bool eemd = p.ensemble_trials > 1;
     for (int i = 0; i < count; ++i) {
         int n = 0;
-        if (eemd) {
+        if (last_ceemdan) {
+            n = ws.h_cestate->n;
+        } else if (eemd) {
             for (int m = 0; m < last_ninst; ++m)
                 n = std::max(n, (int)ws.h_state[m].imf_count);
         } else {
@@ -908,7 +1262,7 @@ void semd_plan_s::counts(int count, int *n_imfs, int *sifts) const
         if (sifts)
             for (int k = 0; k < p.max_imfs; ++k)
                 sifts[(int64_t)i * p.max_imfs + k] =
-                    eemd ? 0 : (k < n ? ws.h_state[i].sifts[k] : 0);
+                    (eemd || last_ceemdan) ? 0 : (k < n ? ws.h_state[i].sifts[k] : 0);
     }
 }
 
@@ -1090,6 +1444,25 @@ semd_status serial_emd_decompose_slices(semd_plan_t plan, const void *d_x, int64
     return st;
 }
 
+semd_status serial_emd_ceemdan(semd_plan_t plan, const void *d_x, const void *d_noise,
+                               void *d_modes, double *d_residue, int *n_modes, void *stream)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (plan->p.ensemble_trials < 2) {
+        plan->err = "CEEMDAN takes ensemble plans (ensemble_trials >= 2)";
+        return SEMD_EINVAL;
+    }
+    if (!d_x || !d_noise || !d_modes) {
+        plan->err = "null input, noise or output pointer";
+        return SEMD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return plan->p.precision == SEMD_FP64
+               ? ceemdan_impl<double>(*plan, d_x, d_noise, d_modes, d_residue, n_modes, s)
+               : ceemdan_impl<float>(*plan, d_x, d_noise, d_modes, d_residue, n_modes, s);
+}
+
 semd_status serial_emd_plan_counts(semd_plan_t plan, int count, int *n_imfs, int *sifts)
 {
     if (!plan || count < 0 || count > plan->last_count)
@@ -1128,6 +1501,8 @@ void serial_emd_destroy(semd_plan_t plan)
         cudaStreamSynchronize(plan->gstream);
     if (plan->graph_exec)
         cudaGraphExecDestroy(plan->graph_exec);
+    if (plan->ce_graph_exec)
+        cudaGraphExecDestroy(plan->ce_graph_exec);
     if (plan->ev_in)
         cudaEventDestroy(plan->ev_in);
     if (plan->ev_out)

@@ -41,12 +41,19 @@ struct Workspace {
     int32_t *d_misc = nullptr;
     Stats *d_stats = nullptr;
     void *eemd_scratch = nullptr;
+    // CEEMDAN (ensemble plans): call arguments, stage state, noise mode counts, r_k
+    CeArgs *d_ce = nullptr;
+    CeState *d_cestate = nullptr;
+    int32_t *d_cecount = nullptr;
+    double *d_ce_r = nullptr;
     // pinned host staging
     Inst *h_inst = nullptr;
     int32_t *h_tile_inst = nullptr;
     State *h_state = nullptr;
     void *h_misc = nullptr;
     Stats *h_stats = nullptr;
+    CeArgs *h_ce = nullptr;
+    CeState *h_cestate = nullptr;
     cudaEvent_t staging_done = nullptr;
 
     semd_status allocate(int64_t samples, int insts, int64_t tiles, int64_t rentries, int iters,
@@ -161,6 +168,11 @@ struct semd_plan_s {
     cudaGraphExec_t graph_exec = nullptr;
     semd::GraphKey graph_key;
     int64_t graph_launches = 0;
+    // the same for CEEMDAN calls
+    cudaGraphExec_t ce_graph_exec = nullptr;
+    semd::GraphKey ce_graph_key;
+    int64_t ce_graph_launches = 0;
+    bool last_ceemdan = false; // the last call was CEEMDAN (counts come from its state)
     // statistics of the last decomposition
     semd::Profiler prof;
     int64_t stat_launches = 0;

@@ -120,6 +120,29 @@ struct ReduceArgs {
     int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
 };
 
+// One CEEMDAN call (Sec. 2.2, Steps 1-4), in device memory so that a captured graph can be
+// replayed with other buffers. The trials are the plan's instances: first the EMD of every
+// noise realization (its modes E_1..E_{K-1} stay in the ensemble scratch), then per stage
+// the first EMD mode of r_k + beta_k E_k(w^(m)) for every trial.
+struct CeArgs {
+    const void *x;        // input, rows x cols (plan precision)
+    const void *noise;    // trials x L noise realizations w^(m) (plan precision)
+    const void *E;        // ensemble scratch: trial m's mode k at E + (m * K + k) * slot
+    void *modes;          // K x rows x cols output (plan precision)
+    double *res;          // residue output (input shape), or null
+    double *r;            // residue r_k of the current stage, serialized (L doubles)
+    int32_t *ncount;      // modes of each noise realization (trials)
+    int64_t M, N, D, L;   // geometry of the input (Sec. 3.2)
+    int64_t slot;         // elements between two mode slots of the scratch
+    int32_t order, trials, K, pad;
+    double rel;           // beta_k = rel * std(r_k)
+};
+struct CeState {
+    double beta;          // beta_k of the current stage
+    int32_t done;         // 1: a residue failed the IMF-start test, later stages are empty
+    int32_t n;            // modes produced
+};
+
 // Threads of the interface-solve kernel (one CTA per instance and envelope).
 constexpr int kRedThreads = 256;
 

@@ -70,6 +70,17 @@ class Plan:
         n = capi.serial_emd_decompose(self.handle, x, noise, imfs, residue, stream, wait)
         return imfs, residue, n
 
+    def ceemdan(self, x: torch.Tensor, noise: torch.Tensor, modes=None, residue=None,
+                stream=None, wait: bool = True):
+        """Serial-CEEMDAN of x with the noise realizations (trials, L) (an ensemble plan).
+        Returns (modes (K, rows, cols), residue, mode count or None when not waiting)."""
+        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous()
+        assert noise.is_cuda and noise.dtype == self.dtype and noise.is_contiguous()
+        if modes is None:
+            modes, residue = self.outputs(*x.shape, device=x.device)
+        n = capi.serial_emd_ceemdan(self.handle, x, noise, modes, residue, stream, wait)
+        return modes, residue, n
+
     def decompose_batch(self, xs, outs=None, stream=None, wait: bool = True):
         if outs is None:
             outs = [self.outputs(*x.shape, device=x.device) for x in xs]

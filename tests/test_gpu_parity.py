@@ -465,3 +465,90 @@ def test_slices_match_oracle_per_row_and_batch(prec):
     for i in range(rows):
         assert torch.equal(outs[i][0][:, 0], imfs[:, i]) and torch.equal(outs[i][1][0], res[i])
     plan.close()
+
+
+# --------------------------------------------------------------------- serial-CEEMDAN
+
+def _ceemdan_gpu(X, w, prec, **kw):
+    rows, cols = X.shape
+    trials = w.shape[0]
+    plan = Plan(make_params(rows, cols, precision=prec, ensemble_trials=trials, **kw))
+    modes, res, n = plan.ceemdan(torch.from_numpy(np.ascontiguousarray(X)).cuda(),
+                                 torch.from_numpy(np.ascontiguousarray(w)).cuda())
+    torch.cuda.synchronize()
+    out = modes.double().cpu().numpy(), res.cpu().numpy(), n
+    return out, plan
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+@pytest.mark.parametrize("case", ["image48", "series3x1024_D205"])
+def test_ceemdan_matches_oracle(prec, case):
+    """Serial-CEEMDAN (Sec. 2.2 Steps 1-4 inside Sec. 3) against the oracle on the same
+    rounded input and noise: every mode and the residue, FP64 within 1e-10; FP32 under the
+    bar of the unconditional FP32 checks (the noise modes E_k are themselves FP32 EMDs)."""
+    if case == "image48":
+        X = synth.grating_image(48, 5).astype(NP[prec])
+        D, K, trials = 0, 6, 4
+    else:
+        X = synth.workload_series_3x1024().astype(NP[prec])
+        D, K, trials = 205, 8, 3
+    N, M = X.shape
+    L = O.serial_length(M, N, D)
+    w = synth.white_noise(trials, L, 77).astype(NP[prec])
+    (gm, gr, gn), plan = _ceemdan_gpu(X, w, prec, transition_len=D, max_imfs=K,
+                                      noise_rel_std=0.2)
+    om, orr, on = O.serial_ceemdan(X.astype(np.float64), D, K, w.astype(np.float64), 0.2)
+    xd = X.astype(np.float64)
+    _check_imfs(gm.reshape(K, -1), gr.reshape(-1), gn, om.reshape(K, -1), orr.reshape(-1), on,
+                xd.reshape(-1), prec, f"ceemdan {case}")
+    # modes + residue reconstruct the input (Step 3 keeps r in FP64)
+    rec = gm.sum(0) + gr
+    assert np.abs(rec - xd).max() <= (1e-12 if prec == capi.FP64 else 1e-5) * np.abs(xd).max()
+    # a second call replays the captured graph; without graphs the same numbers come out
+    m2, r2, n2 = plan.ceemdan(torch.from_numpy(X).cuda(), torch.from_numpy(w).cuda())
+    plan.set_options(use_graphs=False)
+    m3, r3, n3 = plan.ceemdan(torch.from_numpy(X).cuda(), torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    assert n2 == n3 == gn
+    assert np.array_equal(m2.double().cpu().numpy(), gm) and np.array_equal(r2.cpu().numpy(), gr)
+    assert np.array_equal(m3.double().cpu().numpy(), gm) and np.array_equal(r3.cpu().numpy(), gr)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_ceemdan_one_mode_sd_stop_and_no_extrema(prec):
+    """K = 1 (no noise EMD: the first EEMD mode), the SD stop rule, and an input without
+    extrema (no stage runs: zero modes, the residue is the input)."""
+    X = synth.grating_image(40, 8).astype(NP[prec])
+    w = synth.white_noise(5, X.size, 78).astype(NP[prec])
+    (gm, gr, gn), plan = _ceemdan_gpu(X, w, prec, transition_len=0, max_imfs=1)
+    om, orr, on = O.serial_ceemdan(X.astype(np.float64), 0, 1, w.astype(np.float64), 0.2)
+    _check_imfs(gm.reshape(1, -1), gr.reshape(-1), gn, om.reshape(1, -1), orr.reshape(-1), on,
+                X.astype(np.float64).reshape(-1), prec, "ceemdan K=1")
+    plan.close()
+    (gm, gr, gn), plan = _ceemdan_gpu(X, w, prec, transition_len=0, max_imfs=5,
+                                      stop=capi.STOP_SD, max_sifts=30)
+    om, orr, on = O.serial_ceemdan(X.astype(np.float64), 0, 5, w.astype(np.float64), 0.2,
+                                   stop=O.STOP_SD, max_sifts=30)
+    if prec == capi.FP64:
+        _check_imfs(gm.reshape(5, -1), gr.reshape(-1), gn, om.reshape(5, -1), orr.reshape(-1),
+                    on, X.astype(np.float64).reshape(-1), prec, "ceemdan SD")
+    plan.close()
+    ramp = np.tile(np.linspace(-1.0, 2.0, 64), (2, 1)).astype(NP[prec])
+    ramp[1] += 3.0  # row 2 continues the rise of row 1: the serialized signal is monotone
+    wr = synth.white_noise(3, ramp.size, 79).astype(NP[prec])
+    (gm, gr, gn), plan = _ceemdan_gpu(ramp, wr, prec, transition_len=0, max_imfs=4)
+    assert gn == 0 and not gm.any() and np.array_equal(gr, ramp.astype(np.float64))
+    m, r, n = plan.ceemdan(torch.from_numpy(ramp).cuda(), torch.from_numpy(wr).cuda(),
+                           wait=False)
+    torch.cuda.synchronize()
+    assert n is None and plan.counts(1)[0][0] == 0
+    plan.close()
+
+
+def test_ceemdan_needs_an_ensemble_plan():
+    plan = Plan(make_params(8, 8, precision=capi.FP64, transition_len=0))
+    x = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):
+        plan.ceemdan(x, torch.zeros((2, 64), dtype=torch.float64, device="cuda"))
+    plan.close()
