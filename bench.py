@@ -435,6 +435,7 @@ def arm_ours(args):
                 line["ms_per_step"] / line["standard_slices"]["ms_per_step"]
         if not args.no_batched:
             line["ceemdan"] = ceemdan_legs(args, device, flush, world)
+            line["d_sweep"] = d_sweep(args, device, world)
         if not args.no_serving:
             line["serving"] = serving(args, device)
         if not args.no_cpu_baseline:
@@ -445,6 +446,7 @@ def arm_ours(args):
         batched_images(args, device, flush, peak, peak_kind, world)
         standard_slices(args, device, flush, world)
         ceemdan_legs(args, device, flush, world)
+        d_sweep(args, device, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -680,6 +682,84 @@ def ceemdan_legs(args, device, flush, world):
                         "cuda_graph": bool(st.used_graph),
                         "paper_cpu_ms_context": paper_ms}
     return out
+
+
+def _tone_similarity(imfs, tones, mask):
+    """IMF quality on the 6-variate tone set: for IMF k (k = 1, 2) and each variate, the
+    normalized correlation of the IMF with the k-th highest tone the mask puts into that
+    variate (the component an ideal decomposition would return), averaged over variates."""
+    out = []
+    for k in range(2):
+        cs = []
+        for v in range(mask.shape[1]):
+            present = [j for j in range(mask.shape[0]) if mask[j, v]]
+            if k >= len(present):
+                continue
+            c, ref = imfs[k, v], tones[present[k]]
+            den = np.linalg.norm(c) * np.linalg.norm(ref)
+            cs.append(float(np.dot(c, ref) / den) if den > 0 else 0.0)
+        out.append(float(np.mean(cs)))
+    return out
+
+
+def d_sweep(args, device, world):
+    """Transition length D (Sec. 3.2) from 1 to 500 (half a variate) on the paper's
+    6-variate tone set (6 x 1000), as in Sec. 4.1: device time of serial EMD (fixed 10
+    sifts and SD stop 0.2), serial EEMD and serial CEEMDAN (100 realizations, fixed 10
+    sifts), FP32-mixed, and the IMF-tone correlation of IMF 1 and 2 for both EMD stops."""
+    import torch
+    from paper_2106_15319_gb300 import capi, synth
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    tones, mask = synth.paper_mask_components()
+    X = np.ascontiguousarray(synth.paper_mask_series(), np.float32)
+    rows, cols = X.shape
+    x = torch.from_numpy(X).to(device)
+    trials = 100
+    stream = torch.cuda.Stream(device)
+
+    def timed(fn, steps):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+            stream.synchronize()
+            ms = []
+            for _ in range(steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                stream.synchronize()
+                ms.append(a.elapsed_time(b))
+        return max_over_ranks(statistics.mean(ms), world)
+
+    rows_out = []
+    for D in (1, 10, 20, 50, 100, 200, 500):
+        L = cols * rows + D * rows - D
+        rec = {"D": D, "L": L}
+        for tag, kw in (("emd_fixed10", {}), ("emd_sd0.2", {"stop": capi.STOP_SD})):
+            plan = Plan(make_params(rows, cols, transition_len=D, max_imfs=10, **kw))
+            imfs, res = plan.outputs(rows, cols, device=device)
+            rec[tag + "_ms"] = timed(lambda: plan.decompose(x, None, imfs, res, stream=stream,
+                                                            wait=False), 5)
+            n, sifts = plan.counts(1)
+            rec[tag + "_imfs"] = int(n[0])
+            rec[tag + "_sifts"] = int(sum(sifts[0]))
+            rec[tag + "_tone_corr"] = _tone_similarity(imfs.double().cpu().numpy(), tones, mask)
+            plan.close()
+        w = torch.from_numpy(synth.white_noise(trials, L, 9002).astype(np.float32)).to(device)
+        plan = Plan(make_params(rows, cols, transition_len=D, max_imfs=10,
+                                ensemble_trials=trials, noise_rel_std=0.2))
+        imfs, res = plan.outputs(rows, cols, device=device)
+        rec["eemd_ms"] = timed(lambda: plan.decompose(x, w, imfs, res, stream=stream,
+                                                      wait=False), 3)
+        rec["ceemdan_ms"] = timed(lambda: plan.ceemdan(x, w, imfs, res, stream=stream,
+                                                       wait=False), 3)
+        plan.close()
+        rows_out.append(rec)
+    return {"workload": "6-variate tone set (32/16/8/2 Hz by the pickup mask), 6 x 1000, "
+                        f"FP32-mixed, <= 10 IMFs; EEMD/CEEMDAN {trials} realizations",
+            "rows": rows_out}
 
 
 def main():

@@ -145,10 +145,10 @@ def workload_eemd_512(trials: int = 256):
     return img, w
 
 
-def paper_mask_series(samples: int = 1000, fs: float = 1000.0) -> np.ndarray:
-    """The 6-variate tone set of Sec. 4.1: tones 32/16/8/2 Hz picked by the mask of
-    Eq. (pickup) (rows = tones, columns = variates U..Z). The sample rate is not
-    printed in the paper; 1 kHz and 1000 samples are assumed."""
+def paper_mask_components(samples: int = 1000, fs: float = 1000.0):
+    """The parts of the 6-variate tone set of Sec. 4.1: the tones 32/16/8/2 Hz (4, samples)
+    and the pickup mask (4 tones x 6 variates U..Z). The sample rate is not printed in
+    the paper; 1 kHz and 1000 samples are assumed."""
     mask = np.array([[1, 1, 0, 1, 0, 0],
                      [1, 1, 1, 0, 1, 0],
                      [1, 1, 1, 1, 1, 1],
@@ -156,4 +156,11 @@ def paper_mask_series(samples: int = 1000, fs: float = 1000.0) -> np.ndarray:
     f = np.array([32.0, 16.0, 8.0, 2.0])
     t = np.arange(samples) / fs
     tones = np.sin(2 * np.pi * f[:, None] * t[None, :])
+    return tones, mask
+
+
+def paper_mask_series(samples: int = 1000, fs: float = 1000.0) -> np.ndarray:
+    """The 6-variate tone set of Sec. 4.1 (6, samples): variate v is the sum of the tones
+    the mask picks for it."""
+    tones, mask = paper_mask_components(samples, fs)
     return (mask.T @ tones).astype(np.float64)

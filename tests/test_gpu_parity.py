@@ -220,6 +220,20 @@ def test_series_3x1024(prec, D):
     assert list(g[3][:common]) == list(o[3][:common])
 
 
+@pytest.mark.parametrize("D", [1, 50, 500, 1000])
+@pytest.mark.parametrize("stop", [capi.STOP_FIXED, capi.STOP_SD])
+def test_mask_series_transition_lengths_fp64(D, stop):
+    """The transition-length sweep of Sec. 4.1 on the paper's 6-variate tone set: D from 1
+    to M (the largest D that Sec. 3.2 allows, where X_A covers a whole signal), with the
+    fixed sift count and the SD stop rule; every IMF and the sift counts against the
+    oracle."""
+    X = synth.paper_mask_series()
+    g = _run(X, capi.FP64, transition_len=D, max_imfs=10, stop=stop)
+    o = _oracle(X, capi.FP64, transition_len=D, max_imfs=10, stop=stop)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, f"mask D={D}")
+    assert list(g[3][:g[2]]) == list(o[3][:o[2]])
+
+
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
 def test_texture_256(prec):
     X = synth.workload_texture_256()
