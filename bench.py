@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_pass launch of the default workload, from the ncu
 # capture summarized in profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu
 # replays); set to None when the kernel changes until it is captured again.
-PASS_TRAFFIC_TEXTURE = 398336
+PASS_TRAFFIC_TEXTURE = None
 
 
 def _peaks():

@@ -53,7 +53,7 @@ typedef enum semd_status {
 } semd_status;
 
 typedef enum semd_order { SEMD_ORDER_ROWS = 0, SEMD_ORDER_COLS = 1 } semd_order;
-typedef enum semd_stop { SEMD_STOP_FIXED = 0, SEMD_STOP_SD = 1 } semd_stop;
+typedef enum semd_stop { SEMD_STOP_FIXED = 0, SEMD_STOP_SD = 1, SEMD_STOP_SNUMBER = 2 } semd_stop;
 typedef enum semd_boundary { SEMD_BOUNDARY_MIRROR = 0, SEMD_BOUNDARY_ENDPOINTS = 1 } semd_boundary;
 typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precision;
 
@@ -68,6 +68,10 @@ typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precisio
  *                   SEMD_STOP_SD: sift until sum (h_prev - h)^2 / sum h_prev^2 <
  *                   sd_threshold, at most max_sifts sifts. Sec. 2.1 Step 5 leaves the
  *                   criterion open ("some predefined stopping criterion").
+ *                   SEMD_STOP_SNUMBER: the S-number rule of the EMD literature: sift
+ *                   until s_number consecutive sifts have each left a signal whose
+ *                   extrema count (maxima + minima) and zero-crossing count differ by
+ *                   at most one, at most max_sifts sifts.
  *  boundary         envelope end rule (the paper is silent): MIRROR reflects the
  *                   first and last mirror_knots (1 or 2) extrema about the ends;
  *                   ENDPOINTS adds the two end samples as knots.
@@ -78,6 +82,7 @@ typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precisio
  *                   such plans also run CEEMDAN (serial_emd_ceemdan).
  *  noise_rel_std    EEMD beta = noise_rel_std * population std of the serialized x;
  *                   CEEMDAN beta_k = noise_rel_std * population std of the residue r_k.
+ *  s_number         S of SEMD_STOP_SNUMBER, 1 <= S <= 1000.
  */
 typedef struct semd_params {
     int64_t rows;
@@ -94,10 +99,13 @@ typedef struct semd_params {
     int32_t precision;
     int32_t ensemble_trials;
     double noise_rel_std;
+    int32_t s_number;
+    int32_t reserved; /* 0 */
 } semd_params;
 
 /* Fills p with the defaults: ROWS order, D = -1 (20 % rule), K = 10, fixed 10 sifts,
- * SD threshold 0.2 with at most 50 sifts, MIRROR with 2 knots, FP32_MIXED, EMD. */
+ * SD threshold 0.2 with at most 50 sifts, S-number 4, MIRROR with 2 knots, FP32_MIXED,
+ * EMD. */
 void serial_emd_default_params(semd_params *p);
 
 typedef struct semd_plan_s *semd_plan_t;

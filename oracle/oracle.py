@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-STOP_FIXED, STOP_SD = 0, 1
+STOP_FIXED, STOP_SD, STOP_SNUMBER = 0, 1, 2
 BOUNDARY_MIRROR, BOUNDARY_ENDPOINTS = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -65,6 +65,8 @@ def lib():
             L.oracle_emd.argtypes = [_dp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      _dp, _dp, _ipint, ctypes.c_int]
+            L.oracle_zero_crossings.restype = _i64
+            L.oracle_zero_crossings.argtypes = [_dp, _i64]
             L.oracle_std.restype = ctypes.c_double
             L.oracle_std.argtypes = [_dp, _i64]
             L.oracle_eemd.restype = ctypes.c_int
@@ -168,11 +170,14 @@ def sift(h, boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2):
 
 def emd(x, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10, sd_threshold: float = 0.2,
         max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2,
-        store_f32: bool = False):
+        store_f32: bool = False, s_number: int = 4):
     """Sec. 2.1: returns (imfs (K, L) zero-filled, residue (L,), n_imfs, sifts per IMF).
 
     store_f32 rounds the sifted signal to single precision where the FP32 form stores it.
+    Under the S-number rule (stop = STOP_SNUMBER) s_number is S.
     """
+    if stop == STOP_SNUMBER:
+        fixed_sifts = s_number
     x = _f64(x)
     L = x.size
     imfs = np.empty((K, L), np.float64)
@@ -206,11 +211,14 @@ def eemd(x, w, beta: float, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 1
 def serial_emd(X, D: int, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
                sd_threshold: float = 0.2, max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR,
                mirror_knots: int = 2, trials: int = 1, noise_rel_std: float = 0.0, w=None,
-               store_f32: bool = False):
+               store_f32: bool = False, s_number: int = 4):
     """Sec. 3: serialize, EMD/EEMD, de-serialize. X is (N, M).
 
     Returns (imfs (K, N, M), residue (N, M), n_imfs, sifts per IMF (EMD only)).
+    Under the S-number rule (stop = STOP_SNUMBER) s_number is S.
     """
+    if stop == STOP_SNUMBER:
+        fixed_sifts = s_number
     X = _f64(X)
     N, M = X.shape
     L = serial_length(M, N, D)
@@ -263,3 +271,9 @@ def serial_ceemdan(X, D: int, K: int, w, noise_rel_std: float, stop: int = STOP_
                                     max_sifts, boundary, mirror_knots, trials, noise_rel_std,
                                     _d(w), _d(modes), _d(res), int(store_f32))
     return modes, res, int(n)
+
+
+def zero_crossings(h) -> int:
+    """Reading 8b: pairs (k, k+1) of h with exactly one negative sample."""
+    h = _f64(h)
+    return int(lib().oracle_zero_crossings(_d(h), h.size))

@@ -29,6 +29,12 @@
  *              ENDPOINTS alternative: (0, h[0]) and (L-1, h[L-1]) become knots.
  *   Reading 8  SD stop: SD = sum (h_prev - h)^2 / sum h_prev^2 < threshold,
  *              tested after each sift, at most max_sifts sifts.
+ *   Reading 8b S-number stop (a plan option; the paper names no rule): after each
+ *              sift, count the sifted signal's extrema (maxima + minima, Reading 5)
+ *              and zero crossings (pairs k, k+1 where exactly one of the two samples
+ *              is negative); sifting stops once S consecutive sifts have each left
+ *              counts that differ by at most one, or after max_sifts sifts. S is
+ *              passed in fixed_sifts under this rule.
  *   Reading 9  an IMF is started only if n_max >= 1, n_min >= 1 and
  *              n_max + n_min >= 3; otherwise the decomposition ends and the
  *              remainder is the residue. The same test on the sifted signal
@@ -59,6 +65,7 @@
 
 #define OR_STOP_FIXED 0
 #define OR_STOP_SD 1
+#define OR_STOP_SNUMBER 2
 #define OR_BOUNDARY_MIRROR 0
 #define OR_BOUNDARY_ENDPOINTS 1
 
@@ -269,6 +276,16 @@ out:
     return rc;
 }
 
+/* Reading 8b: zero crossings of h, pairs (k, k+1) with exactly one negative sample. */
+int64_t oracle_zero_crossings(const double *h, int64_t L)
+{
+    int64_t k, n = 0;
+    for (k = 0; k + 1 < L; ++k)
+        if ((h[k] < 0.0) != (h[k + 1] < 0.0))
+            ++n;
+    return n;
+}
+
 /* Reading 9: may an IMF be started from (or sifting continue on) h? */
 static int has_enough_extrema(const double *h, int64_t L, int32_t *scratch_a,
                               int32_t *scratch_b)
@@ -283,9 +300,10 @@ static int has_enough_extrema(const double *h, int64_t L, int32_t *scratch_a,
 /*
  * Standard 1D EMD of x (length L): x = sum_i c_i + r (Eq. 1). imfs is K x L
  * (slots past the produced count are zero-filled), residue is L. The stop rule
- * is a fixed sift count (stop = OR_STOP_FIXED, fixed_sifts) or the SD rule of
- * Reading 8. sifts_per_imf (length K, may be NULL) receives each IMF's sift
- * count. store_f32: see the header. Returns the number of IMFs produced.
+ * is a fixed sift count (stop = OR_STOP_FIXED, fixed_sifts), the SD rule of
+ * Reading 8 or the S-number rule of Reading 8b (S in fixed_sifts). sifts_per_imf
+ * (length K, may be NULL) receives each IMF's sift count. store_f32: see the
+ * header. Returns the number of IMFs produced.
  */
 static void round_to_single(double *h, int64_t L)
 {
@@ -311,7 +329,7 @@ int oracle_emd(const double *x, int64_t L, int K, int stop, int fixed_sifts,
         for (k = 0; k < K; ++k)
             sifts_per_imf[k] = 0;
     for (i = 0; i < K; ++i) {
-        int sifts = 0;
+        int sifts = 0, scount = 0;
         if (!has_enough_extrema(r, L, sa, sb))
             break; /* Reading 9: r is the residue */
         memcpy(h, r, (size_t)L * sizeof(double));
@@ -334,6 +352,13 @@ int oracle_emd(const double *x, int64_t L, int K, int stop, int fixed_sifts,
             if (stop == OR_STOP_SD) {
                 if (num / den < sd_threshold || sifts >= max_sifts)
                     break; /* Reading 8 */
+            } else if (stop == OR_STOP_SNUMBER) {
+                int64_t nmax, nmin, d;
+                oracle_extrema(h, L, sa, &nmax, sb, &nmin);
+                d = nmax + nmin - oracle_zero_crossings(h, L);
+                scount = (d >= -1 && d <= 1) ? scount + 1 : 0;
+                if (scount >= fixed_sifts || sifts >= max_sifts)
+                    break; /* Reading 8b */
             }
         }
         /* Step 5: c_i = h, and the next IMF is sifted from r - c_i */

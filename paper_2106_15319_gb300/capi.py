@@ -16,7 +16,7 @@ SEMD_OK, SEMD_PENDING = 0, 1
 SEMD_EINVAL, SEMD_ENOMEM, SEMD_EBUDGET, SEMD_ECUDA = -1, -2, -3, -4
 SEMD_ETIMEOUT, SEMD_ECANCELED, SEMD_EUNSUPPORTED = -5, -6, -7
 ORDER_ROWS, ORDER_COLS = 0, 1
-STOP_FIXED, STOP_SD = 0, 1
+STOP_FIXED, STOP_SD, STOP_SNUMBER = 0, 1, 2
 BOUNDARY_MIRROR, BOUNDARY_ENDPOINTS = 0, 1
 FP64, FP32_MIXED = 0, 1
 
@@ -37,7 +37,8 @@ class semd_params(ctypes.Structure):
                 ("max_sifts", ctypes.c_int32), ("sd_threshold", ctypes.c_double),
                 ("boundary", ctypes.c_int32), ("mirror_knots", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("ensemble_trials", ctypes.c_int32),
-                ("noise_rel_std", ctypes.c_double)]
+                ("noise_rel_std", ctypes.c_double), ("s_number", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class semd_instance(ctypes.Structure):

@@ -651,6 +651,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         stp->pass_sift = stp->sift_count;
         stp->pass_imf = imfc;
         stp->pass_par = hpar | (rpar << 1);
+        stp->pass_scount = stp->scount;
     }
     const int ts = lt * TW;
     const int cnt = min(TW, L - ts);
@@ -698,6 +699,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     }
 
     R pn = R(0), pd = R(0);
+    int zc = 0;             // zero crossings of the sifted signal (S-number rule)
     R hnl = hcl, hnr = hcr; // the new signal at the halo samples
     if (sift) {
         R left = __shfl_up_sync(FULLMASK, v[SPL - 1], 1);
@@ -763,6 +765,22 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             const KnotY<R> a1 = P.ky[q + 1];
             const R e1 = a1.t == TW ? rmul(a1.y, R(0.5)) : horner(P.cf[q], R(TW - P.ky[q].t));
             hnr = rsub(hcr, radd(e0, e1));
+        }
+        if (pa.need_zc) {
+            // sign changes (negative vs not) between samples k and k+1 with k+1 in the tile;
+            // the pair across the left tile edge uses the halo value, which equals the
+            // neighbour's own result bit for bit
+            const R nx = __shfl_down_sync(FULLMASK, hn[0], 1);
+            int z = 0;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const R b = s + 1 < SPL ? hn[s + 1] : nx;
+                if (k0 + s + 1 < cnt && (lane < 31 || s + 1 < SPL))
+                    z += ((hn[s] < R(0)) != (b < R(0))) ? 1 : 0;
+            }
+            if (lane == 0 && hasL)
+                z += ((hnl < R(0)) != (hn[0] < R(0))) ? 1 : 0;
+            zc = warp_sum(z);
         }
         __syncwarp(); // the pool is reused for the new signal's knots
     } else {
@@ -868,6 +886,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             in.taux[lt].sd_den = (double)pd;
         }
     }
+    if (sift && pa.need_zc && lane == 0)
+        in.taux[lt].nzc = zc;
 }
 
 // One sifting pass over all tiles of every running instance. Persistent grid: warp w
@@ -1022,7 +1042,7 @@ struct RedShared {
     double lev[14 * kRedThreads]; // level-1 results (10 arrays), level-1.5 scratch (4), in R
     int segq[kRedThreads];        // rows per level-1 segment
     double sd[kRedThreads / 32][2];
-    int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2];
+    int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2], wzc[kRedThreads / 32];
     int next;
 };
 
@@ -1099,23 +1119,23 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     State *st = ra.state + ii;
     const int mode_now = st->mode;
     const int pm = st->pass_mode, psift = st->pass_sift, pimf = st->pass_imf;
-    const int ppar = st->pass_par;
+    const int ppar = st->pass_par, pscount = st->pass_scount;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int NW = kRedThreads / 32;
 
     // counts: knots of both envelopes, this envelope's reduced-system entries per tile
     // (first/last knot) and the SD sums of the pass that just ran. Tiles are taken in a
     // stride of the block, four per thread at a time, every load in flight before use.
-    int sn = 0, so_ = 0;
+    int sn = 0, so_ = 0, zs = 0;
     double a = 0.0, b = 0.0;
-    const bool want_sd = ra.stop == STOP_SD;
+    const bool want_sd = ra.stop == STOP_SD, want_zc = ra.stop == STOP_SNUMBER;
     for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
-        int ne[4], no[4];
+        int ne[4], no[4], nz[4];
         double sa[4], sb[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int t = t0 + tid + k * kRedThreads;
-            ne[k] = no[k] = 0;
+            ne[k] = no[k] = nz[k] = 0;
             sa[k] = sb[k] = 0.0;
             if (t < nt) {
                 ne[k] = texe[t].n;
@@ -1124,6 +1144,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                     sa[k] = taux[t].sd_num;
                     sb[k] = taux[t].sd_den;
                 }
+                if (want_zc)
+                    nz[k] = taux[t].nzc;
             }
         }
 #pragma unroll
@@ -1133,6 +1155,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 X.Tu[t] = (unsigned char)(ne[k] <= kSparseKnots ? ne[k] : 2);
             sn += ne[k];
             so_ += no[k];
+            zs += nz[k];
             a += sa[k];
             b += sb[k];
         }
@@ -1141,6 +1164,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         return;
     sn = warp_sum(sn);
     so_ = warp_sum(so_);
+    zs = warp_sum(zs);
     if (want_sd) { // FP64 sums only when the stop rule reads them (the FP64 pipe is narrow)
         a = warp_sum(a);
         b = warp_sum(b);
@@ -1148,6 +1172,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     if (lane == 0) {
         S.wsn[warp][0] = sn;
         S.wsn[warp][1] = so_;
+        S.wzc[warp] = zs;
         S.sd[warp][0] = a;
         S.sd[warp][1] = b;
     }
@@ -1184,7 +1209,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
             }
         }
         const bool ok = nmax >= 1 && nmin >= 1 && nmax + nmin >= 3;
-        int imf_count = pimf, sift_count = psift, nm;
+        int imf_count = pimf, sift_count = psift, scount = pscount, nm;
         int committed = -1; // IMF slot whose sift count is recorded
         double sd = 0.0;
         if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
@@ -1203,18 +1228,29 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
                 nm = MODE_COMMIT;
             } else if (ra.stop == STOP_FIXED) {
                 nm = (sift_count >= ra.fixed_sifts - 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
-            } else {
+            } else if (ra.stop == STOP_SD) {
                 sd = sdn / sdd;
                 nm = (sd < ra.sd_threshold || sift_count >= ra.max_sifts) ? MODE_COMMIT
                                                                           : MODE_SIFT;
+            } else { // S-number: extrema and zero crossings of the sifted signal
+                int nz = 0;
+                for (int w = 0; w < NW; ++w)
+                    nz += S.wzc[w];
+                const int d = nmax + nmin - nz;
+                scount = (d >= -1 && d <= 1) ? scount + 1 : 0;
+                nm = (scount >= ra.s_number || sift_count >= ra.max_sifts) ? MODE_COMMIT
+                                                                           : MODE_SIFT;
             }
         }
         S.next = nm;
         if (e == 0) {
             if (committed >= 0)
                 st->sifts[committed] = sift_count + (pm == MODE_SIFT_COMMIT ? 1 : 0);
-            if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
+            if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
                 sift_count = 0;
+                scount = 0;
+            }
+            st->scount = scount;
             st->hpar = (ppar & 1) ^ 1;
             st->rpar = ((ppar >> 1) & 1) ^ ((pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT) ? 1 : 0);
             if (pm == MODE_SIFT && ra.stop == STOP_SD)

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+static_assert(sizeof(semd_params) == 80, "semd_params is part of the C ABI");
+
 namespace semd {
 
 static thread_local std::string g_plan_create_error;
@@ -496,12 +498,15 @@ bool validate(const semd_params &p, std::string &err)
         return err = "order must be ROWS or COLS", false;
     if (p.max_imfs < 1 || p.max_imfs > KMAX)
         return err = "max_imfs must be in [1, 32]", false;
-    if (p.stop != SEMD_STOP_FIXED && p.stop != SEMD_STOP_SD)
-        return err = "stop must be FIXED or SD", false;
+    if (p.stop != SEMD_STOP_FIXED && p.stop != SEMD_STOP_SD && p.stop != SEMD_STOP_SNUMBER)
+        return err = "stop must be FIXED, SD or SNUMBER", false;
     if (p.stop == SEMD_STOP_FIXED && (p.fixed_sifts < 1 || p.fixed_sifts > 1000))
         return err = "fixed_sifts must be in [1, 1000]", false;
     if (p.stop == SEMD_STOP_SD && (p.max_sifts < 1 || p.max_sifts > 1000 || !(p.sd_threshold >= 0)))
         return err = "max_sifts must be in [1, 1000] and sd_threshold >= 0", false;
+    if (p.stop == SEMD_STOP_SNUMBER &&
+        (p.max_sifts < 1 || p.max_sifts > 1000 || p.s_number < 1 || p.s_number > 1000))
+        return err = "max_sifts and s_number must be in [1, 1000]", false;
     if (p.boundary != SEMD_BOUNDARY_MIRROR && p.boundary != SEMD_BOUNDARY_ENDPOINTS)
         return err = "boundary must be MIRROR or ENDPOINTS", false;
     if (p.boundary == SEMD_BOUNDARY_MIRROR && (p.mirror_knots < 1 || p.mirror_knots > 2))
@@ -693,7 +698,8 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
 }
 
 template <typename R>
-static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, cudaStream_t s)
+static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, bool need_zc,
+                        cudaStream_t s)
 {
     PassArgs pa;
     pa.inst = ws.d_inst;
@@ -701,7 +707,7 @@ static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, cudaStream_
     pa.tile_inst = ws.d_tile_inst;
     pa.ntiles = ntiles;
     pa.need_sd = need_sd ? 1 : 0;
-    pa.pad = 0;
+    pa.need_zc = need_zc ? 1 : 0;
     launch_pass_tiles<R>(ws.tile, pa, ntiles, s);
 }
 
@@ -721,7 +727,7 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.boundary = p.boundary;
     ra.mirror_knots = p.mirror_knots;
     ra.single = ws.elem_size == 4 ? 1 : 0;
-    ra.pad = 0;
+    ra.s_number = p.s_number;
     const int64_t entries = reduce_len(ws.max_ntiles);
     ra.smem_entries = reduce_smem_bytes(entries, ws.elem_size) <= kReduceSmemMax ? entries : 0;
     return ra;
@@ -746,8 +752,9 @@ struct LaunchTimer {
 };
 
 // The sifting passes of one decomposition: `iters` pass + interface-solve launches (the
-// state machine idles finished instances). With the SD stop rule and no capture, every
-// eighth iteration reads the count of running instances and ends the loop at zero.
+// state machine idles finished instances). With an adaptive stop rule (SD, S-number) and
+// no capture, every eighth iteration reads the count of running instances and ends the
+// loop at zero.
 template <typename R>
 static semd_status sift_loop(semd_plan_s &pl, ReduceArgs ra, int ninst, int64_t ntiles,
                              int iters, cudaStream_t s, Profiler *prof, bool capture,
@@ -755,11 +762,11 @@ static semd_status sift_loop(semd_plan_s &pl, ReduceArgs ra, int ninst, int64_t 
 {
     Workspace &ws = pl.ws;
     std::string &err = pl.err;
-    const bool sd = ra.stop == SEMD_STOP_SD;
+    const bool sd = ra.stop == SEMD_STOP_SD, zc = ra.stop == SEMD_STOP_SNUMBER;
     for (int it = 0; it < iters; ++it) {
         {
             LaunchTimer t(prof, s, 0);
-            launch_pass<R>(ws, ntiles, sd, s);
+            launch_pass<R>(ws, ntiles, sd, zc, s);
         }
         ra.active = ws.d_active + it;
         {
@@ -767,7 +774,7 @@ static semd_status sift_loop(semd_plan_s &pl, ReduceArgs ra, int ninst, int64_t 
             launch_reduce<R>(ra, ninst, s);
         }
         launches += 2;
-        if (!capture && sd && (it % 8) == 7) {
+        if (!capture && (sd || zc) && (it % 8) == 7) {
             SEMD_CU(cudaMemcpyAsync(ws.h_misc, ws.d_active + it, 4, cudaMemcpyDeviceToHost, s));
             SEMD_CU(cudaStreamSynchronize(s));
             if (((int32_t *)ws.h_misc)[0] == 0)
@@ -1144,9 +1151,9 @@ semd_status sift_impl(semd_plan_s &pl, const void *d_h, int64_t L, void *d_out, 
     p.max_imfs = 1;
     ReduceArgs ra = reduce_args(ws, p);
     SEMD_CU(cudaMemsetAsync(ws.d_active, 0, 8, s));
-    launch_pass<R>(ws, ntiles, true, s); // INIT: h = r, export
+    launch_pass<R>(ws, ntiles, true, false, s); // INIT: h = r, export
     launch_reduce<R>(ra, 1, s);
-    launch_pass<R>(ws, ntiles, true, s); // SIFT
+    launch_pass<R>(ws, ntiles, true, false, s); // SIFT
     SEMD_CU(cudaGetLastError());
     SEMD_CU(cudaMemcpyAsync(ws.h_state, ws.d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
     SEMD_CU(cudaStreamSynchronize(s));
@@ -1230,7 +1237,7 @@ ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_s
     ra.boundary = p.boundary;
     ra.mirror_knots = p.mirror_knots;
     ra.single = elem == 4 ? 1 : 0;
-    ra.pad = 0;
+    ra.s_number = p.s_number;
     const int64_t entries = reduce_len(max_ntiles);
     ra.smem_entries = reduce_smem_bytes(entries, elem) <= kReduceSmemMax ? entries : 0;
     return ra;
@@ -1288,6 +1295,7 @@ void serial_emd_default_params(semd_params *p)
     p->precision = SEMD_FP32_MIXED;
     p->ensemble_trials = 1;
     p->noise_rel_std = 0.2;
+    p->s_number = 4;
 }
 
 semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem_budget,
@@ -1710,9 +1718,9 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     q.fixed_sifts = 1000; // stay in SIFT mode
     q.max_imfs = 1;
     ReduceArgs ra = reduce_args(ws, q);
-    launch_pass<R>(ws, ntiles, true, s); // INIT: h = r, export
+    launch_pass<R>(ws, ntiles, true, false, s); // INIT: h = r, export
     launch_reduce<R>(ra, 1, s);
-    launch_pass<R>(ws, ntiles, true, s); // SIFT
+    launch_pass<R>(ws, ntiles, true, false, s); // SIFT
     k_noalloc_result<<<1, 32, 0, s>>>(ws.d_state, ws.d_taux, ntiles, d_result);
     SEMD_CU(cudaGetLastError());
     double res[3];

@@ -18,7 +18,7 @@ enum Mode : int32_t {
 };
 
 enum Boundary : int32_t { BND_MIRROR = 0, BND_ENDPOINTS = 1 };
-enum Stop : int32_t { STOP_FIXED = 0, STOP_SD = 1 };
+enum Stop : int32_t { STOP_FIXED = 0, STOP_SD = 1, STOP_SNUMBER = 2 };
 
 // Per tile and envelope (0 = maxima, 1 = minima): what the interface solve needs of the
 // tile's knots, after the tile has eliminated its interior knots, in the pass kernel's
@@ -53,6 +53,8 @@ struct __align__(16) TileSolve {
 struct TileAux {
     double sd_num, sd_den;  // sum (h - h')^2, sum h^2 over the tile
     double h_first, h_last; // h[0] / h[L-1] of the new signal (first / last tile)
+    int32_t nzc;            // zero crossings of the sifted signal: pairs (k, k+1) with
+    int32_t pad;            //   k + 1 in the tile and a sign change (S-number rule)
 };
 
 // Read-only description of one instance (one serialized signal) and its buffers. Every
@@ -88,13 +90,15 @@ struct Stats {
 
 // Mutable per-instance state of the sifting state machine.
 struct State {
-    int32_t mode, hpar, rpar, imf_count, sift_count, nmax, nmin, pad;
+    int32_t mode, hpar, rpar, imf_count, sift_count, nmax, nmin;
+    int32_t scount; // S-number rule: consecutive sifts that met the count condition
     double sd;
     int32_t sifts[KMAX];
     // written by the pass kernel (the instance's first tile): the mode, sift and IMF
     // counts the pass ran with, so that both interface-solve CTAs of an instance read
     // the same inputs while one of them updates the fields above
     int32_t pass_mode, pass_sift, pass_imf, pass_par; // pass_par: hpar | rpar << 1
+    int32_t pass_scount, pad;
 };
 
 struct PassArgs {
@@ -103,7 +107,7 @@ struct PassArgs {
     const int32_t *tile_inst; // launch tile -> instance index
     int64_t ntiles;           // tiles in the launch
     int32_t need_sd;          // 1: accumulate the SD sums (SD stop rule, single-sift calls)
-    int32_t pad;
+    int32_t need_zc;          // 1: count the sifted signal's zero crossings (S-number rule)
 };
 
 struct ReduceArgs {
@@ -116,7 +120,7 @@ struct ReduceArgs {
     double sd_threshold;
     int32_t boundary, mirror_knots;
     int32_t single;       // 1: tile records hold floats (FP32 pass kernel)
-    int32_t pad;
+    int32_t s_number;     // S of the S-number rule
     int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
 };
 

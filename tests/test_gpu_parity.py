@@ -156,7 +156,7 @@ def _run(X, prec, order=capi.ORDER_ROWS, **kw):
 
 def _oracle(X, prec, order=capi.ORDER_ROWS, transition_len=-1, max_imfs=10,
             stop=capi.STOP_FIXED, fixed_sifts=10, sd_threshold=0.2, max_sifts=50,
-            boundary=capi.BOUNDARY_MIRROR, mirror_knots=2):
+            boundary=capi.BOUNDARY_MIRROR, mirror_knots=2, s_number=4):
     Xd = np.asarray(np.asarray(X, NP[prec]), np.float64)
     Xs = Xd if order == capi.ORDER_ROWS else Xd.T
     N, M = Xs.shape
@@ -164,7 +164,8 @@ def _oracle(X, prec, order=capi.ORDER_ROWS, transition_len=-1, max_imfs=10,
     if N == 1:
         D = 0
     kw = dict(D=D, K=max_imfs, stop=stop, fixed_sifts=fixed_sifts, sd_threshold=sd_threshold,
-              max_sifts=max_sifts, boundary=boundary, mirror_knots=mirror_knots)
+              max_sifts=max_sifts, boundary=boundary, mirror_knots=mirror_knots,
+              s_number=s_number)
     imfs, res, n, sifts = O.serial_emd(Xs, **kw)
     if order == capi.ORDER_COLS:
         imfs = imfs.transpose(0, 2, 1)
@@ -235,6 +236,19 @@ def test_mask_series_transition_lengths_fp64(D, stop):
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_snumber_stop_texture(prec):
+    """The S-number stop rule on the 256 x 256 texture: the zero crossings are counted per
+    tile, across every tile edge, and summed by the interface solve; the sift counts and
+    IMFs against the oracle (FP64), the IMF counts and the unconditional bar (FP32)."""
+    X = synth.workload_texture_256()
+    g = _run(X, prec, transition_len=0, max_imfs=8, stop=capi.STOP_SNUMBER, s_number=3)
+    o = _oracle(X, prec, transition_len=0, max_imfs=8, stop=capi.STOP_SNUMBER, s_number=3)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, "texture S-number")
+    if prec == capi.FP64:
+        assert list(g[3]) == list(o[3]), (g[3], o[3])
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
 def test_texture_256(prec):
     X = synth.workload_texture_256()
     g = _run(X, prec, transition_len=0, max_imfs=10)
@@ -268,7 +282,10 @@ def test_ragged_sizes_fp64(shape):
                                 dict(mirror_knots=1),
                                 dict(order=capi.ORDER_COLS),
                                 dict(fixed_sifts=1),
-                                dict(stop=capi.STOP_SD, sd_threshold=0.2, max_sifts=50)])
+                                dict(stop=capi.STOP_SD, sd_threshold=0.2, max_sifts=50),
+                                dict(stop=capi.STOP_SNUMBER, s_number=1, max_sifts=50),
+                                dict(stop=capi.STOP_SNUMBER, s_number=4, max_sifts=50),
+                                dict(stop=capi.STOP_SNUMBER, s_number=3, max_sifts=5)])
 def test_options_fp64(kw):
     X = synth.tone_chirp_series(4, 900, 77)
     if kw.get("order") == capi.ORDER_COLS:

@@ -276,6 +276,46 @@ def test_emd_sd_stop_limits():
     assert n3 == 4 and np.all((s3[:n3] >= 1) & (s3[:n3] <= 50))
 
 
+def test_zero_crossings_definition():
+    """Reading 8b: a pair counts when exactly one sample is negative (0 is not negative);
+    against a direct loop, and 2f crossings of a sampled sinusoid with f whole periods."""
+    g = synth.rng(5)
+    h = np.round(g.standard_normal(999), 1)  # many exact zeros
+    direct = sum(1 for k in range(h.size - 1) if (h[k] < 0) != (h[k + 1] < 0))
+    assert O.zero_crossings(h) == direct
+    assert O.zero_crossings(np.array([0.0, -0.0, 0.0, 1.0])) == 0
+    assert O.zero_crossings(np.array([-1.0, 0.0, -1.0])) == 2
+    t = np.arange(4000)
+    assert O.zero_crossings(np.sin(2 * np.pi * 7 * t / 4000 + 0.3)) == 14
+
+
+@pytest.mark.parametrize("S", [1, 3, 5])
+def test_emd_snumber_stop_against_sift_chain(S):
+    """Reading 8b on tie-free data: replay each IMF's sifts with the single-sift step and
+    count extrema with scipy's argrelextrema and zero crossings with numpy; the IMF ends
+    at the first sift that completes S consecutive sifts whose counts differ by at most
+    one (or at max_sifts), and equals that sift's output."""
+    x = synth.workload_series_3x1024()[2]
+    K, cap = 5, 40
+    imfs, res, n, sifts = O.emd(x, K, stop=O.STOP_SNUMBER, s_number=S, max_sifts=cap)
+    r = x.copy()
+    for i in range(n):
+        h, run, j = r.copy(), 0, 0
+        while True:
+            h = O.sift(h)[0]
+            j += 1
+            ne = (scipy_signal.argrelextrema(h, np.greater)[0].size
+                  + scipy_signal.argrelextrema(h, np.less)[0].size)
+            nz = int(np.count_nonzero(np.diff((h < 0).astype(np.int8))))
+            run = run + 1 if abs(ne - nz) <= 1 else 0
+            if run >= S or j >= cap:
+                break
+        assert sifts[i] == j, (i, sifts[i], j)
+        assert np.array_equal(imfs[i], h)
+        r = r - h
+    assert np.array_equal(res, r)
+
+
 def test_emd_fixed_sifts_equals_repeated_sift():
     """A fixed sift count is exactly the sift step applied S times (Sec. 2.1 Step 5)."""
     x = synth.workload_series_3x1024()[1]
