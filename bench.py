@@ -125,7 +125,7 @@ def _flush_l2(buf):
     buf.add_(1)
 
 
-def run_ours(wl, precision, steps, warmup, device, flush, tile=0):
+def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
     import torch
     from paper_2106_15319_gb300 import capi
     from paper_2106_15319_gb300.serial_emd import Plan, make_params
@@ -142,6 +142,11 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0):
         else None
     imfs, res = plan.outputs(rows, cols, device=device)
     stream = torch.cuda.Stream(device)
+    shape = None
+    if tune and not tile:  # setup, before the warm-up: the autotuner picks the pass shape
+        r = plan.autotune(x, noise, outs=[(imfs, res)], repeats=3, stream=stream)
+        shape = {"tile": r.tile, "ctas_per_sm": r.ctas_per_sm, "tuned_ms": r.ms,
+                 "default_shape_ms": r.ms_default, "candidates": r.candidates}
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
@@ -161,7 +166,7 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0):
     st = plan.stats()
     out = {"ms": ms, "sample_sifts": st.sample_sifts, "launches": st.kernel_launches,
            "graph": st.used_graph, "plan": plan, "x": x, "noise": noise, "imfs": imfs, "res": res,
-           "stream": stream}
+           "stream": stream, "shape": shape or {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas}}
     return out
 
 
@@ -366,19 +371,22 @@ def arm_ours(args):
 
     barrier(world)
     with ClockSampler(local) as clk:
-        r32 = run_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device, flush, args.tile)
+        r32 = run_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device, flush, args.tile,
+                       tune=not args.no_tune)
     barrier(world)
     ms32 = statistics.mean(r32["ms"])
     ms32_max = max_over_ranks(ms32, world)
     value = world * r32["sample_sifts"] / (ms32_max * 1e-3)
 
     if "fp64" in args.forms:
-        r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush, args.tile)
+        r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush, args.tile,
+                       tune=not args.no_tune)
         ms64 = max_over_ranks(statistics.mean(r64["ms"]), world)
         v64 = world * r64["sample_sifts"] / (ms64 * 1e-3)
+        r64_shape = r64["shape"]
         r64["plan"].close()
     else:
-        ms64, v64 = None, None
+        ms64, v64, r64_shape = None, None, None
 
     prof = profile_pass(r32, args.steps, flush)
     pass_avg_ms = prof["pass_ms"] / max(1, prof["pass_n"])
@@ -401,10 +409,12 @@ def arm_ours(args):
         "config": {"workload": wl["desc"], "form": "FP32-mixed (FP64 interface solve, "
                    "stop reductions and residue)", "L": int(r32["x"].numel()),
                    "sample_sifts_per_step": r32["sample_sifts"], "cuda_graph": bool(r32["graph"]),
+                   "pass_shape": r32["shape"],
                    "l2": "flushed between timed steps (512 MB write); "
                          "the 65536-sample working set is L2-resident within a step",
                    "parallelism": f"replicas x{world}"},
-        "plain_fp64": {"value": v64, "ms_per_step": ms64, "dtype": "f64"},
+        "plain_fp64": {"value": v64, "ms_per_step": ms64, "dtype": "f64",
+                       "pass_shape": r64_shape},
         "speedup_fp32_vs_fp64": value / v64 if v64 else None,
         "fp32_imf_rel_l2": None,
         "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
@@ -457,7 +467,8 @@ def batched_eemd(args, device, flush, peak, peak_kind, world):
     from paper_2106_15319_gb300 import capi
     wl = workload_inputs("eemd512", args.trials)
     steps = max(1, min(args.steps, 5))
-    r = run_ours(wl, capi.FP32_MIXED, steps, min(args.warmup, 3), device, flush)
+    r = run_ours(wl, capi.FP32_MIXED, steps, min(args.warmup, 3), device, flush,
+                 tune=not args.no_tune)
     ms = max_over_ranks(statistics.mean(r["ms"]), world)
     prof = profile_pass(r, 1, flush)
     pass_avg_ms = prof["pass_ms"] / max(1, prof["pass_n"])
@@ -465,6 +476,7 @@ def batched_eemd(args, device, flush, peak, peak_kind, world):
     ach = bpl / (pass_avg_ms * 1e-3) / 1e9
     out = {"workload": wl["desc"], "value": world * r["sample_sifts"] / (ms * 1e-3),
            "unit": UNIT, "ms_per_step": ms, "steps": steps, "dtype": "f32",
+           "pass_shape": r["shape"],
            "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": ach,
                         "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "peak_source": peak_kind, "avg_launch_us": pass_avg_ms * 1e3,
@@ -780,6 +792,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 300.0, 1000.0])
     ap.add_argument("--serve-requests", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default pass shape (no autotuning before the warm-up)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -257,15 +257,68 @@ semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int pr
 
 /*
  * Tile of the sifting pass kernel: every pass cuts each serialized signal into tiles of
- * `tile` samples (512, 1024 or 2048; one thread block each, 8 samples per thread), and
- * the spline system is partitioned at tile edges. 0 restores the plan's own choice. The
- * tile changes rounding only (results agree to the precision's tolerance), and the
- * speed: small tiles spread short signals over more SMs, large ones shrink the
- * interface system. Takes effect at the next decompose call. Errors: EINVAL.
+ * `tile` samples (128, 256 or 512; one warp each, tile / 32 samples per lane), and the
+ * spline system is partitioned at tile edges. 0 restores the plan's own choice (the
+ * tuning table's entry for the plan, else 256). The tile changes rounding only (results
+ * agree to the precision's tolerance), and the speed: small tiles spread short signals
+ * over more warps, large ones shrink the interface system. Takes effect at the next
+ * decompose call. Errors: EINVAL.
  */
 semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile);
 /* The plan's current tile (0 for a NULL plan). */
 int serial_emd_plan_get_tile(semd_plan_t plan);
+
+/*
+ * CTAs per SM of the pass kernel's persistent grid: 0 (the default) keeps as many as fit,
+ * n > 0 at most n. Changes speed only. Takes effect at the next call. Errors: EINVAL
+ * (outside [0, 64]).
+ */
+semd_status serial_emd_plan_set_pass_ctas(semd_plan_t plan, int ctas_per_sm);
+/* The plan's current setting (0 for a NULL plan). */
+int serial_emd_plan_get_pass_ctas(semd_plan_t plan);
+
+/* ------------------------------------------------------------------ autotuner */
+
+typedef struct semd_tune_result {
+    int32_t tile;        /* chosen tile (samples per warp) */
+    int32_t ctas_per_sm; /* chosen CTAs per SM of the pass grid (0: as many as fit) */
+    double ms;           /* median device time of one decomposition with the choice */
+    double ms_default;   /* the same with the default shape (tile 256, all CTAs) */
+    int32_t candidates;  /* shapes timed */
+    int32_t _reserved;
+} semd_tune_result;
+
+/*
+ * Times the plan's decomposition of `count` inputs (as serial_emd_decompose_batch takes
+ * them; for an ensemble plan one input and its noise, as serial_emd_decompose) for every
+ * pass-kernel shape: tile 128, 256 or 512, and CTAs per SM of the persistent grid (as
+ * many as fit, or fewer). Each shape runs once untimed, then `repeats` times (1..100)
+ * with CUDA events on `stream`; the median counts. The fastest shape is kept on the plan
+ * and entered in the process-wide tuning table under the plan's key: precision, stop
+ * rule, ensemble or not, ceil(log2) of the instance count (trials for an ensemble) and
+ * of the longest serialized length. Plans created later with that key start with it.
+ * The outputs are overwritten; the call waits for the stream. out may be NULL.
+ * Errors: EINVAL, EBUDGET (an input larger than the plan), ECUDA.
+ */
+semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_instance *inst,
+                                     const void *d_noise, int repeats, semd_tune_result *out,
+                                     void *stream);
+
+/* The tuning table's shape for a plan of these params, longest serialized length L and
+ * ninst instances: SEMD_OK and *tile, *ctas_per_sm set, or SEMD_PENDING when the table
+ * has no entry. EINVAL for bad arguments. Host only. */
+semd_status serial_emd_tune_lookup(const semd_params *params, int64_t L, int ninst, int *tile,
+                                   int *ctas_per_sm);
+/* Empties the tuning table. */
+void serial_emd_tune_clear(void);
+/* Writes the table as JSON (an "entries" list of flat objects with the key fields,
+ * "tile", "ctas_per_sm" and "ms"). Errors: EINVAL (see serial_emd_tune_last_error). */
+semd_status serial_emd_tune_save(const char *path);
+/* Merges a file written by serial_emd_tune_save into the table; entries with missing
+ * fields or an invalid shape are skipped. Errors: EINVAL (unreadable, no "entries"). */
+semd_status serial_emd_tune_load(const char *path);
+/* Text of the last save/load error of this thread. */
+const char *serial_emd_tune_last_error(void);
 
 /* Statistics of the plan's last decompose call; valid once its stream has finished. */
 typedef struct semd_stats {

@@ -60,6 +60,12 @@ class semd_stats(ctypes.Structure):
                 ("_reserved", ctypes.c_int32)]
 
 
+class semd_tune_result(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("ms_default", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+
+
 class semd_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n_imfs", ctypes.c_int32),
                 ("sifts", ctypes.c_int64), ("queue_ms", ctypes.c_double),
@@ -101,6 +107,19 @@ SIGNATURES = {
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "serial_emd_plan_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "serial_emd_plan_get_tile": (ctypes.c_int, [ctypes.c_void_p]),
+    "serial_emd_plan_set_pass_ctas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "serial_emd_plan_get_pass_ctas": (ctypes.c_int, [ctypes.c_void_p]),
+    "serial_emd_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                                ctypes.POINTER(semd_instance), ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.POINTER(semd_tune_result),
+                                                ctypes.c_void_p]),
+    "serial_emd_tune_lookup": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_int64,
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
+    "serial_emd_tune_clear": (None, []),
+    "serial_emd_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "serial_emd_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "serial_emd_tune_last_error": (ctypes.c_char_p, []),
     "serial_emd_plan_set_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "serial_emd_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_stats)]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
@@ -264,6 +283,57 @@ def serial_emd_plan_get_tile(plan: int) -> int:
 
 def serial_emd_plan_set_options(plan: int, use_graphs: bool = True, profile: bool = False):
     _check(load().serial_emd_plan_set_options(plan, int(use_graphs), int(profile)), plan)
+
+
+def serial_emd_plan_set_pass_ctas(plan: int, ctas_per_sm: int) -> None:
+    _check(load().serial_emd_plan_set_pass_ctas(plan, ctas_per_sm), plan)
+
+
+def serial_emd_plan_get_pass_ctas(plan: int) -> int:
+    return int(load().serial_emd_plan_get_pass_ctas(plan))
+
+
+def serial_emd_plan_autotune(plan: int, items, noise=None, repeats: int = 3,
+                             stream=None) -> semd_tune_result:
+    """Times every pass-kernel shape on the inputs (list of (x, imfs, residue) tensors,
+    as decompose_batch takes them; one item plus noise for an ensemble plan), keeps the
+    fastest on the plan and in the process-wide tuning table."""
+    arr = (semd_instance * len(items))()
+    for i, (x, imfs, res) in enumerate(items):
+        arr[i] = semd_instance(_ptr(x), x.shape[0], x.shape[1], _ptr(imfs), _ptr(res))
+    out = semd_tune_result()
+    rc = load().serial_emd_plan_autotune(plan, len(items), arr, _ptr(noise), repeats,
+                                         ctypes.byref(out), _stream(stream))
+    _check(rc, plan)
+    return out
+
+
+def serial_emd_tune_lookup(params: semd_params, L: int, ninst: int):
+    """(tile, ctas_per_sm) of the tuning table's entry, or None."""
+    t, c = ctypes.c_int(), ctypes.c_int()
+    rc = load().serial_emd_tune_lookup(ctypes.byref(params), L, ninst, ctypes.byref(t),
+                                       ctypes.byref(c))
+    if rc == SEMD_PENDING:
+        return None
+    if rc != 0:
+        raise SemdError(rc, "bad arguments")
+    return t.value, c.value
+
+
+def serial_emd_tune_clear() -> None:
+    load().serial_emd_tune_clear()
+
+
+def serial_emd_tune_save(path: str) -> None:
+    rc = load().serial_emd_tune_save(path.encode())
+    if rc != 0:
+        raise SemdError(rc, load().serial_emd_tune_last_error().decode())
+
+
+def serial_emd_tune_load(path: str) -> None:
+    rc = load().serial_emd_tune_load(path.encode())
+    if rc != 0:
+        raise SemdError(rc, load().serial_emd_tune_last_error().decode())
 
 
 def serial_emd_plan_stats(plan: int) -> semd_stats:

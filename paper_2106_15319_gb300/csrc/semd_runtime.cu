@@ -392,26 +392,51 @@ static cudaError_t set_smem_attr()
     return e;
 }
 
-// CTAs of the pass kernel that fit on the current device at once (the persistent grid),
-// computed once per device.
+// CTAs of the pass kernel that fit on one SM of the current device at once, and the
+// device's SM count, computed once per device.
 template <typename R, int TILE>
-static int64_t pass_resident_ctas()
+static void pass_residency(int &per_sm, int &sms)
 {
     constexpr int kMaxDev = 64;
-    static int64_t cache[kMaxDev];
+    static int cache[kMaxDev][2];
     int dev = 0;
+    per_sm = 1;
+    sms = 152;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
-        return 152;
-    if (cache[dev] == 0) {
-        int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R, TILE / 32, kPassWarps>,
+        return;
+    if (cache[dev][0] == 0) {
+        int a = 0, b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass<R, TILE / 32, kPassWarps>,
                                                           32 * kPassWarps,
                                                           pass_smem<R, TILE>()) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return 152;
-        cache[dev] = (int64_t)std::max(per_sm, 1) * std::max(sms, 1);
+            cudaDeviceGetAttribute(&b, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return;
+        cache[dev][0] = std::max(a, 1);
+        cache[dev][1] = std::max(b, 1);
     }
-    return cache[dev];
+    per_sm = cache[dev][0];
+    sms = cache[dev][1];
+}
+
+int pass_ctas_per_sm_max(size_t elem, int tile)
+{
+    int per_sm, sms;
+    if (elem == 8) {
+        if (tile == 128)
+            pass_residency<double, 128>(per_sm, sms);
+        else if (tile == 512)
+            pass_residency<double, 512>(per_sm, sms);
+        else
+            pass_residency<double, 256>(per_sm, sms);
+    } else {
+        if (tile == 128)
+            pass_residency<float, 128>(per_sm, sms);
+        else if (tile == 512)
+            pass_residency<float, 512>(per_sm, sms);
+        else
+            pass_residency<float, 256>(per_sm, sms);
+    }
+    return per_sm;
 }
 
 // Launches with programmatic stream serialization: the kernel's CTAs may start while the
@@ -434,25 +459,32 @@ static void launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem, cud
     cudaLaunchKernelEx(&cfg, kernel, arg);
 }
 
+// The persistent pass grid: at most ctas_per_sm CTAs per SM (0 or more than fit: as many
+// as fit), and never more CTAs than the launch has tiles for.
 template <typename R, int TILE>
-static void launch_pass_t(PassArgs pa, int64_t ntiles, cudaStream_t s)
+static void launch_pass_t(PassArgs pa, int64_t ntiles, int ctas_per_sm, cudaStream_t s)
 {
     pa.ntiles = ntiles;
+    int per_sm, sms;
+    pass_residency<R, TILE>(per_sm, sms);
+    if (ctas_per_sm > 0)
+        per_sm = std::min(per_sm, ctas_per_sm);
     const int64_t grid =
-        std::min((ntiles + kPassWarps - 1) / kPassWarps, pass_resident_ctas<R, TILE>());
+        std::min((ntiles + kPassWarps - 1) / kPassWarps, (int64_t)per_sm * sms);
     launch_pdl(k_pass<R, TILE / 32, kPassWarps>, (unsigned)grid, 32 * kPassWarps,
                pass_smem<R, TILE>(), s, pa);
 }
 
 template <typename R>
-static void launch_pass_tiles(int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
+static void launch_pass_tiles(int tile, int ctas_per_sm, const PassArgs &pa, int64_t ntiles,
+                              cudaStream_t s)
 {
     if (tile == 128)
-        launch_pass_t<R, 128>(pa, ntiles, s);
+        launch_pass_t<R, 128>(pa, ntiles, ctas_per_sm, s);
     else if (tile == 512)
-        launch_pass_t<R, 512>(pa, ntiles, s);
+        launch_pass_t<R, 512>(pa, ntiles, ctas_per_sm, s);
     else
-        launch_pass_t<R, 256>(pa, ntiles, s);
+        launch_pass_t<R, 256>(pa, ntiles, ctas_per_sm, s);
 }
 
 static size_t reduce_smem(const ReduceArgs &ra)
@@ -521,7 +553,14 @@ bool validate(const semd_params &p, std::string &err)
 }
 
 // Tile of the pass kernel for a plan: 1024 samples (128 threads).
-int choose_tile(const semd_params &, int64_t, int) { return kTile; }
+// The plan's pass-kernel shape: the tuning table's entry for the plan's key when there is
+// one, else 256-sample tiles and as many CTAs per SM as fit.
+void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas)
+{
+    tile = kTile;
+    ctas = 0;
+    tune_lookup(p, L, ninst, tile, ctas);
+}
 
 int max_iterations(const semd_params &p)
 {
@@ -708,7 +747,7 @@ static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, bool need_z
     pa.ntiles = ntiles;
     pa.need_sd = need_sd ? 1 : 0;
     pa.need_zc = need_zc ? 1 : 0;
-    launch_pass_tiles<R>(ws.tile, pa, ntiles, s);
+    launch_pass_tiles<R>(ws.tile, ws.pass_ctas, pa, ntiles, s);
 }
 
 static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
@@ -876,7 +915,7 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile};
+        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile, ws.pass_ctas};
         if (!pl.graph_exec || !(pl.graph_key == key)) {
             if (pl.graph_exec) {
                 cudaGraphExecDestroy(pl.graph_exec);
@@ -1039,7 +1078,8 @@ semd_status ceemdan_impl(semd_plan_s &pl, const void *d_x, const void *d_noise, 
     const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{trials, ntiles, ws.h_inst[0].ntiles, ws.max_ntiles, ws.tile};
+        const GraphKey key{trials, ntiles, ws.h_inst[0].ntiles, ws.max_ntiles, ws.tile,
+                           ws.pass_ctas};
         if (!pl.ce_graph_exec || !(pl.ce_graph_key == key)) {
             if (pl.ce_graph_exec) {
                 cudaGraphExecDestroy(pl.ce_graph_exec);
@@ -1187,9 +1227,9 @@ cudaError_t setup_kernel_attrs(size_t elem)
 void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
 {
     if (elem == 8)
-        launch_pass_tiles<double>(tile, pa, ntiles, s);
+        launch_pass_tiles<double>(tile, 0, pa, ntiles, s);
     else
-        launch_pass_tiles<float>(tile, pa, ntiles, s);
+        launch_pass_tiles<float>(tile, 0, pa, ntiles, s);
 }
 
 void launch_reduce_any(size_t elem, const ReduceArgs &ra, int nblocks, cudaStream_t s)
@@ -1325,7 +1365,8 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     }
     const int64_t L = serial_length(M, N, D);
     const int ninst = eemd ? params->ensemble_trials : max_batch;
-    const int tile = choose_tile(*params, L, ninst);
+    int tile, ctas;
+    choose_pass_shape(*params, L, ninst, tile, ctas);
     // capacity for the smallest tile, so that the tile can be changed per plan
     const int64_t tiles_per = (L + kMinTile - 1) / kMinTile;
     const int64_t samples = (int64_t)ninst * ((L + 31) & ~(int64_t)31);
@@ -1342,6 +1383,7 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     pl->p = *params;
     pl->L = L;
     pl->ws.tile = tile;
+    pl->ws.pass_ctas = ctas;
     semd_status st = pl->ws.allocate(samples, ninst, tiles, rent, max_iterations(*params), elem,
                                       eemd_elems, mem_budget, err);
     if (st == SEMD_OK) {
@@ -1526,8 +1568,10 @@ semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile)
 {
     if (!plan)
         return SEMD_EINVAL;
-    if (tile == 0)
-        tile = choose_tile(plan->p, plan->L, plan->ws.cap_inst);
+    if (tile == 0) {
+        int ctas;
+        choose_pass_shape(plan->p, plan->L, plan->ws.cap_inst, tile, ctas);
+    }
     if (tile != 128 && tile != 256 && tile != 512) {
         plan->err = "tile must be 0, 128, 256 or 512";
         return SEMD_EINVAL;
@@ -1537,6 +1581,20 @@ semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile)
 }
 
 int serial_emd_plan_get_tile(semd_plan_t plan) { return plan ? plan->ws.tile : 0; }
+
+semd_status serial_emd_plan_set_pass_ctas(semd_plan_t plan, int ctas_per_sm)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 64) {
+        plan->err = "ctas_per_sm must be in [0, 64]";
+        return SEMD_EINVAL;
+    }
+    plan->ws.pass_ctas = ctas_per_sm;
+    return SEMD_OK;
+}
+
+int serial_emd_plan_get_pass_ctas(semd_plan_t plan) { return plan ? plan->ws.pass_ctas : 0; }
 
 semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int profile)
 {

@@ -106,6 +106,25 @@ class Plan:
     def tile(self, value: int):
         capi.serial_emd_plan_set_tile(self.handle, value)
 
+    @property
+    def pass_ctas(self) -> int:
+        return capi.serial_emd_plan_get_pass_ctas(self.handle)
+
+    @pass_ctas.setter
+    def pass_ctas(self, value: int):
+        capi.serial_emd_plan_set_pass_ctas(self.handle, value)
+
+    def autotune(self, xs, noise: torch.Tensor | None = None, outs=None, repeats: int = 3,
+                 stream=None):
+        """Picks the fastest pass-kernel shape for these inputs (one tensor or a list, as
+        decompose_batch takes them). Returns the tuning result."""
+        if isinstance(xs, torch.Tensor):
+            xs = [xs]
+        if outs is None:
+            outs = [self.outputs(*x.shape, device=x.device) for x in xs]
+        items = [(x, o[0], o[1]) for x, o in zip(xs, outs)]
+        return capi.serial_emd_plan_autotune(self.handle, items, noise, repeats, stream)
+
     def set_options(self, use_graphs: bool = True, profile: bool = False):
         capi.serial_emd_plan_set_options(self.handle, use_graphs, profile)
 

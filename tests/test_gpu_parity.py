@@ -583,3 +583,55 @@ def test_ceemdan_needs_an_ensemble_plan():
     with pytest.raises(RuntimeError):
         plan.ceemdan(x, torch.zeros((2, 64), dtype=torch.float64, device="cuda"))
     plan.close()
+
+
+# ------------------------------------------------------------------------- autotuner
+
+def test_autotune_keeps_results_and_seeds_new_plans(tmp_path):
+    """The autotuner times every pass-kernel shape, keeps the fastest (never slower than
+    the default shape, which is among the candidates), and the decomposition it leaves
+    agrees with the default shape's to rounding; a new plan with the same key starts from
+    the tuned shape, and the saved table holds it."""
+    capi.serial_emd_tune_clear()
+    X = synth.workload_texture_256()
+    p = make_params(256, 256, precision=capi.FP64, transition_len=0, max_imfs=6)
+    plan = Plan(p)
+    x = torch.from_numpy(X).cuda()
+    ref, rres, rn = plan.decompose(x)
+    ref, rres = ref.cpu().numpy(), rres.cpu().numpy()
+    r = plan.autotune(x, repeats=2)
+    assert r.tile in (128, 256, 512) and r.ctas_per_sm >= 0 and r.candidates >= 3
+    assert 0 < r.ms <= r.ms_default
+    assert (plan.tile, plan.pass_ctas) == (r.tile, r.ctas_per_sm)
+    imfs, res, n = plan.decompose(x)
+    assert n == rn
+    floor = 1e-6 * np.linalg.norm(X)
+    for k in range(6):
+        assert _rel(imfs[k].cpu().numpy(), ref[k], floor) <= 1e-12
+    plan2 = Plan(p)
+    assert (plan2.tile, plan2.pass_ctas) == (r.tile, r.ctas_per_sm)
+    out = tmp_path / "tune.json"
+    capi.serial_emd_tune_save(str(out))
+    assert f'"tile": {r.tile}' in out.read_text()
+    plan.close()
+    plan2.close()
+    capi.serial_emd_tune_clear()
+
+
+def test_autotune_ensemble_plan():
+    capi.serial_emd_tune_clear()
+    img = synth.grating_image(40, 5).astype(np.float32)
+    trials = 8
+    w = synth.white_noise(trials, img.size, 6).astype(np.float32)
+    plan = Plan(make_params(40, 40, transition_len=0, max_imfs=5, ensemble_trials=trials))
+    xi, wi = torch.from_numpy(img).cuda(), torch.from_numpy(w).cuda()
+    r = plan.autotune(xi, noise=wi, repeats=1)
+    assert r.tile in (128, 256, 512) and 0 < r.ms <= r.ms_default
+    a, _, _ = plan.decompose(xi, wi)
+    plan.tile, plan.pass_ctas = 256, 0
+    b, _, _ = plan.decompose(xi, wi)
+    floor = 1e-6 * np.linalg.norm(img)
+    for k in range(2):
+        assert _rel(a[k].double().cpu().numpy(), b[k].double().cpu().numpy(), floor) <= 1e-4
+    plan.close()
+    capi.serial_emd_tune_clear()
