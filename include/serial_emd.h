@@ -54,6 +54,7 @@ typedef enum semd_status {
 
 typedef enum semd_order { SEMD_ORDER_ROWS = 0, SEMD_ORDER_COLS = 1 } semd_order;
 typedef enum semd_stop { SEMD_STOP_FIXED = 0, SEMD_STOP_SD = 1, SEMD_STOP_SNUMBER = 2 } semd_stop;
+typedef enum semd_spline_end { SEMD_SPLINE_NATURAL = 0, SEMD_SPLINE_NOT_A_KNOT = 1 } semd_spline_end;
 typedef enum semd_boundary { SEMD_BOUNDARY_MIRROR = 0, SEMD_BOUNDARY_ENDPOINTS = 1 } semd_boundary;
 typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precision;
 
@@ -83,6 +84,12 @@ typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precisio
  *  noise_rel_std    EEMD beta = noise_rel_std * population std of the serialized x;
  *                   CEEMDAN beta_k = noise_rel_std * population std of the residue r_k.
  *  s_number         S of SEMD_STOP_SNUMBER, 1 <= S <= 1000.
+ *  spline_end       end conditions of the envelope splines: SEMD_SPLINE_NATURAL (zero
+ *                   second derivative at the first and last knot of the sequence,
+ *                   boundary knots included) or SEMD_SPLINE_NOT_A_KNOT (continuous third
+ *                   derivative at the second and second-to-last knot; sequences of fewer
+ *                   than four knots keep natural ends). The paper names the cubic spline
+ *                   of standard EMD (Sec. 1) without its end conditions.
  */
 typedef struct semd_params {
     int64_t rows;
@@ -100,12 +107,12 @@ typedef struct semd_params {
     int32_t ensemble_trials;
     double noise_rel_std;
     int32_t s_number;
-    int32_t reserved; /* 0 */
+    int32_t spline_end;
 } semd_params;
 
 /* Fills p with the defaults: ROWS order, D = -1 (20 % rule), K = 10, fixed 10 sifts,
- * SD threshold 0.2 with at most 50 sifts, S-number 4, MIRROR with 2 knots, FP32_MIXED,
- * EMD. */
+ * SD threshold 0.2 with at most 50 sifts, S-number 4, MIRROR with 2 knots, natural
+ * spline ends, FP32_MIXED, EMD. */
 void serial_emd_default_params(semd_params *p);
 
 typedef struct semd_plan_s *semd_plan_t;

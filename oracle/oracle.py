@@ -24,6 +24,7 @@ _lib = None
 
 STOP_FIXED, STOP_SD, STOP_SNUMBER = 0, 1, 2
 BOUNDARY_MIRROR, BOUNDARY_ENDPOINTS = 0, 1
+SPLINE_NOT_A_KNOT = 16  # added to a boundary code: not-a-knot spline ends (Reading 6b)
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip32 = ctypes.POINTER(ctypes.c_int32)
@@ -57,6 +58,7 @@ def lib():
             L.oracle_deserialize.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
             L.oracle_extrema.argtypes = [_dp, _i64, _ip32, _ip64, _ip32, _ip64]
             L.oracle_spline_second_derivs.argtypes = [_dp, _dp, _i64, _dp]
+            L.oracle_spline_second_derivs_nak.argtypes = [_dp, _dp, _i64, _dp]
             L.oracle_envelope.argtypes = [_dp, _i64, _ip32, _i64, ctypes.c_int, ctypes.c_int,
                                           _dp]
             L.oracle_sift.restype = ctypes.c_int
@@ -138,11 +140,14 @@ def extrema(h):
     return a[:na.value].copy(), b[:nb.value].copy()
 
 
-def spline_second_derivs(s, v) -> np.ndarray:
-    """Natural cubic spline second derivatives (Thomas algorithm)."""
+def spline_second_derivs(s, v, not_a_knot: bool = False) -> np.ndarray:
+    """Cubic spline second derivatives (Thomas algorithm): natural ends, or not-a-knot
+    ends (Reading 6b)."""
     s, v = _f64(s), _f64(v)
     out = np.empty(s.size, np.float64)
-    lib().oracle_spline_second_derivs(_d(s), _d(v), s.size, _d(out))
+    fn = lib().oracle_spline_second_derivs_nak if not_a_knot else \
+        lib().oracle_spline_second_derivs
+    fn(_d(s), _d(v), s.size, _d(out))
     return out
 
 

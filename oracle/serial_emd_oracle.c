@@ -24,6 +24,12 @@
  *   Reading 6  envelopes are natural cubic splines with knots at the integer
  *              sample indices of the extrema (Sec. 1 names the cubic spline of
  *              standard EMD).
+ *   Reading 6b not-a-knot ends (a plan option; Sec. 1 names the cubic spline
+ *              without its end conditions): the third derivative is continuous
+ *              at the second and the second-to-last knot, so the first two and
+ *              the last two intervals each carry one cubic. Knot sequences with
+ *              fewer than four knots keep the natural ends. Selected by adding
+ *              OR_SPLINE_NOT_A_KNOT to the boundary code.
  *   Reading 7  mirror boundary: the first p = min(P, n) knots are reflected to
  *              -t_j and the last p to 2(L-1) - t_j, with the same values.
  *              ENDPOINTS alternative: (0, h[0]) and (L-1, h[L-1]) become knots.
@@ -68,6 +74,7 @@
 #define OR_STOP_SNUMBER 2
 #define OR_BOUNDARY_MIRROR 0
 #define OR_BOUNDARY_ENDPOINTS 1
+#define OR_SPLINE_NOT_A_KNOT 16 /* flag added to the boundary code, Reading 6b */
 
 /* ---------------------------------------------------------------- Sec. 3.2 */
 
@@ -177,6 +184,61 @@ void oracle_spline_second_derivs(const double *s, const double *v, int64_t n, do
     free(dp);
 }
 
+/*
+ * Not-a-knot spline (Reading 6b): the same interior rows, with the two end conditions
+ *   (M_1 - M_0) / h_0 = (M_2 - M_1) / h_1 and
+ *   (M_{n-1} - M_{n-2}) / h_{n-2} = (M_{n-2} - M_{n-3}) / h_{n-3}.
+ * They give M_0 = ((h_0 + h_1) M_1 - h_0 M_2) / h_1 and the mirror image for M_{n-1};
+ * substituted into rows 1 and n-2 they leave a tridiagonal system in M_1..M_{n-2}
+ * (Thomas algorithm), after which M_0 and M_{n-1} follow. n < 4: natural ends.
+ */
+void oracle_spline_second_derivs_nak(const double *s, const double *v, int64_t n, double *Mj)
+{
+    int64_t j, m = n - 2;
+    double *cp, *dp;
+    if (n < 4) {
+        oracle_spline_second_derivs(s, v, n, Mj);
+        return;
+    }
+    cp = (double *)malloc((size_t)m * sizeof(double));
+    dp = (double *)malloc((size_t)m * sizeof(double));
+    for (j = 1; j <= n - 2; ++j) {
+        double hl = s[j] - s[j - 1], hr = s[j + 1] - s[j];
+        double a = hl, b = 2.0 * (hl + hr), c = hr;
+        double d = 6.0 * ((v[j + 1] - v[j]) / hr - (v[j] - v[j - 1]) / hl);
+        int64_t q = j - 1;
+        if (j == 1) { /* M_0 substituted */
+            b = b + hl * (hl + hr) / hr;
+            c = hr - hl * hl / hr;
+            a = 0.0;
+        }
+        if (j == n - 2) { /* M_{n-1} substituted */
+            b = b + hr * (hl + hr) / hl;
+            a = hl - hr * hr / hl;
+            c = 0.0;
+        }
+        if (q == 0) {
+            cp[q] = c / b;
+            dp[q] = d / b;
+        } else {
+            double den = b - a * cp[q - 1];
+            cp[q] = c / den;
+            dp[q] = (d - a * dp[q - 1]) / den;
+        }
+    }
+    Mj[n - 2] = dp[m - 1];
+    for (j = n - 3; j >= 1; --j)
+        Mj[j] = dp[j - 1] - cp[j - 1] * Mj[j + 1];
+    {
+        double h0 = s[1] - s[0], h1 = s[2] - s[1];
+        double ha = s[n - 2] - s[n - 3], hb = s[n - 1] - s[n - 2];
+        Mj[0] = ((h0 + h1) * Mj[1] - h0 * Mj[2]) / h1;
+        Mj[n - 1] = ((ha + hb) * Mj[n - 2] - hb * Mj[n - 3]) / ha;
+    }
+    free(cp);
+    free(dp);
+}
+
 /* Value of the natural cubic spline at abscissa u, with s_j <= u <= s_{j+1}. */
 static double spline_eval_interval(const double *s, const double *v, const double *Mj,
                                    int64_t j, double u)
@@ -195,8 +257,11 @@ static double spline_eval_interval(const double *s, const double *v, const doubl
 void oracle_envelope(const double *h, int64_t L, const int32_t *t, int64_t n,
                      int boundary, int mirror_knots, double *env)
 {
-    int64_t p = (boundary == OR_BOUNDARY_MIRROR) ? (n < mirror_knots ? n : mirror_knots) : 0;
-    int64_t nk = (boundary == OR_BOUNDARY_MIRROR) ? n + 2 * p : n + 2, j, k, q = 0;
+    const int nak = (boundary & OR_SPLINE_NOT_A_KNOT) != 0;
+    int64_t p, nk, j, k, q = 0;
+    boundary &= ~OR_SPLINE_NOT_A_KNOT;
+    p = (boundary == OR_BOUNDARY_MIRROR) ? (n < mirror_knots ? n : mirror_knots) : 0;
+    nk = (boundary == OR_BOUNDARY_MIRROR) ? n + 2 * p : n + 2;
     double *s = (double *)malloc((size_t)nk * sizeof(double));
     double *v = (double *)malloc((size_t)nk * sizeof(double));
     double *Mj = (double *)malloc((size_t)nk * sizeof(double));
@@ -223,7 +288,10 @@ void oracle_envelope(const double *h, int64_t L, const int32_t *t, int64_t n,
         s[q] = (double)(L - 1);
         v[q++] = h[L - 1];
     }
-    oracle_spline_second_derivs(s, v, nk, Mj);
+    if (nak)
+        oracle_spline_second_derivs_nak(s, v, nk, Mj);
+    else
+        oracle_spline_second_derivs(s, v, nk, Mj);
     j = 0;
     for (k = 0; k < L; ++k) {
         while (j + 2 < nk && s[j + 1] <= (double)k)

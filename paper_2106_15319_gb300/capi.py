@@ -18,6 +18,7 @@ SEMD_ETIMEOUT, SEMD_ECANCELED, SEMD_EUNSUPPORTED = -5, -6, -7
 ORDER_ROWS, ORDER_COLS = 0, 1
 STOP_FIXED, STOP_SD, STOP_SNUMBER = 0, 1, 2
 BOUNDARY_MIRROR, BOUNDARY_ENDPOINTS = 0, 1
+SPLINE_NATURAL, SPLINE_NOT_A_KNOT = 0, 1
 FP64, FP32_MIXED = 0, 1
 
 _STATUS = {0: "OK", 1: "PENDING", -1: "EINVAL", -2: "ENOMEM", -3: "EBUDGET", -4: "ECUDA",
@@ -38,7 +39,7 @@ class semd_params(ctypes.Structure):
                 ("boundary", ctypes.c_int32), ("mirror_knots", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("ensemble_trials", ctypes.c_int32),
                 ("noise_rel_std", ctypes.c_double), ("s_number", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("spline_end", ctypes.c_int32)]
 
 
 class semd_instance(ctypes.Structure):

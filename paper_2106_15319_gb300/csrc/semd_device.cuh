@@ -1044,6 +1044,7 @@ struct RedShared {
     double sd[kRedThreads / 32][2];
     int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2], wzc[kRedThreads / 32];
     int next;
+    double nakx[2][3]; // not-a-knot ends: the elimination data of rows 1 and NR - 2
 };
 
 // Level 2: the 32 segment-end unknowns (one reduced row per lane, no outside values: the
@@ -1289,6 +1290,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
     const int nl = ra.boundary == BND_MIRROR ? min(ra.mirror_knots, ntot) : 1;
     const int nr = nl;
     const int NR = nl + U + nr;
+    // not-a-knot ends need a sequence of at least four knots (boundary knots included)
+    const bool nak = ra.spline_end == SPLINE_NOT_A_KNOT && ntot + nl + nr >= 4;
     {
         int p = nl + ubase;
         for (int t = ca; t < cb; ++t) {
@@ -1435,18 +1438,41 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
             }
             const R hl = R(tc - tl), hr = R(tr - tc);
             const R d0 = R(6) * ((yr - yc) * rrcp(hr) - (yc - yl) * rrcp(hl));
-            ra_ = hl;
-            rb = R(2) * (hl + hr);
-            rc_ = hr;
+            R a = hl, b = R(2) * (hl + hr), c = hr;
+            if (nak && p == 1) {
+                // not-a-knot: M_0 = ((h_0 + h_1) M_1 - h_0 M_2) / h_1 substituted
+                b = b + hl * (hl + hr) * rrcp(hr);
+                c = hr - hl * hl * rrcp(hr);
+                a = R(0);
+                if (k == EK_FS) {
+                    S.nakx[0][0] = (double)x0;
+                    S.nakx[0][1] = (double)x1;
+                    S.nakx[0][2] = (double)x2;
+                }
+            }
+            if (nak && p == NR - 2) {
+                // M_{n-1} = ((h_{n-3} + h_{n-2}) M_{n-2} - h_{n-2} M_{n-3}) / h_{n-3}
+                b = b + hr * (hl + hr) * rrcp(hl);
+                a = hl - hr * hr * rrcp(hl);
+                c = R(0);
+                if (k == EK_LS) {
+                    S.nakx[1][0] = (double)x0;
+                    S.nakx[1][1] = (double)x1;
+                    S.nakx[1][2] = (double)x2;
+                }
+            }
+            ra_ = a;
+            rb = b;
+            rc_ = c;
             rd = d0;
             if (k == EK_FS) {
-                rb = rb + hr * x1;
-                rc_ = hr * x2;
-                rd = d0 - hr * x0;
+                rb = b + c * x1;
+                rc_ = c * x2;
+                rd = d0 - c * x0;
             } else if (k == EK_LS) {
-                rb = rb + hl * x2;
-                ra_ = hl * x1;
-                rd = d0 - hl * x0;
+                rb = b + a * x2;
+                ra_ = a * x1;
+                rd = d0 - a * x0;
             }
         }
         X.A[p] = ra_;
@@ -1562,6 +1588,28 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         if (rq >= 1) {
             const R *Zs = lev + 13 * NS;
             seg_backsub(X, rs, re, tid > 0 ? Zs[tj(tid - 1)] : R(0), Zs[tj(tid)]);
+        }
+        __syncthreads();
+    }
+    if (nak) {
+        // the end knots' second derivatives from the not-a-knot conditions (the solve
+        // held them at 0); the third knot (second-to-last) may be a tile interior knot,
+        // given by the tile's elimination
+        if (tid == 0) {
+            const bool sub = X.Ek[1] == EK_FS;
+            const R h0 = R(X.Et[1] - X.Et[0]), h1 = R((sub ? X.St[1] : X.Et[2]) - X.Et[1]);
+            const R M1 = X.MV[1];
+            const R M2 = sub ? (R)S.nakx[0][0] + (R)S.nakx[0][1] * M1 + (R)S.nakx[0][2] * X.MV[2]
+                             : X.MV[2];
+            X.MV[0] = ((h0 + h1) * M1 - h0 * M2) * rrcp(h1);
+        } else if (tid == 32) {
+            const int q = NR - 2;
+            const bool sub = X.Ek[q] == EK_LS;
+            const R hb = R(X.Et[q + 1] - X.Et[q]), ha = R(X.Et[q] - (sub ? X.St[q] : X.Et[q - 1]));
+            const R Mq = X.MV[q];
+            const R M3 = sub ? (R)S.nakx[1][0] + (R)S.nakx[1][1] * X.MV[q - 1] + (R)S.nakx[1][2] * Mq
+                             : X.MV[q - 1];
+            X.MV[NR - 1] = ((ha + hb) * Mq - hb * M3) * rrcp(ha);
         }
         __syncthreads();
     }

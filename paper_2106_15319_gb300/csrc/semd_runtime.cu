@@ -545,6 +545,8 @@ bool validate(const semd_params &p, std::string &err)
         return err = "mirror_knots must be 1 or 2", false;
     if (p.precision != SEMD_FP64 && p.precision != SEMD_FP32_MIXED)
         return err = "precision must be FP64 or FP32_MIXED", false;
+    if (p.spline_end != SEMD_SPLINE_NATURAL && p.spline_end != SEMD_SPLINE_NOT_A_KNOT)
+        return err = "spline_end must be NATURAL or NOT_A_KNOT", false;
     if (p.ensemble_trials > 1 && !(p.noise_rel_std >= 0))
         return err = "noise_rel_std must be >= 0", false;
     if (p.transition_len < -1)
@@ -767,6 +769,8 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.mirror_knots = p.mirror_knots;
     ra.single = ws.elem_size == 4 ? 1 : 0;
     ra.s_number = p.s_number;
+    ra.spline_end = p.spline_end;
+    ra.pad = 0;
     const int64_t entries = reduce_len(ws.max_ntiles);
     ra.smem_entries = reduce_smem_bytes(entries, ws.elem_size) <= kReduceSmemMax ? entries : 0;
     return ra;
@@ -1278,6 +1282,8 @@ ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_s
     ra.mirror_knots = p.mirror_knots;
     ra.single = elem == 4 ? 1 : 0;
     ra.s_number = p.s_number;
+    ra.spline_end = p.spline_end;
+    ra.pad = 0;
     const int64_t entries = reduce_len(max_ntiles);
     ra.smem_entries = reduce_smem_bytes(entries, elem) <= kReduceSmemMax ? entries : 0;
     return ra;

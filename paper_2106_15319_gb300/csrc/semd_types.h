@@ -18,6 +18,7 @@ enum Mode : int32_t {
 };
 
 enum Boundary : int32_t { BND_MIRROR = 0, BND_ENDPOINTS = 1 };
+enum SplineEnd : int32_t { SPLINE_NATURAL = 0, SPLINE_NOT_A_KNOT = 1 };
 enum Stop : int32_t { STOP_FIXED = 0, STOP_SD = 1, STOP_SNUMBER = 2 };
 
 // Per tile and envelope (0 = maxima, 1 = minima): what the interface solve needs of the
@@ -122,6 +123,8 @@ struct ReduceArgs {
     int32_t single;       // 1: tile records hold floats (FP32 pass kernel)
     int32_t s_number;     // S of the S-number rule
     int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
+    int32_t spline_end;   // SPLINE_NATURAL or SPLINE_NOT_A_KNOT
+    int32_t pad;
 };
 
 // One CEEMDAN call (Sec. 2.2, Steps 1-4), in device memory so that a captured graph can be

@@ -18,12 +18,14 @@ def make_params(rows: int, cols: int, *, order: int = capi.ORDER_ROWS, transitio
                 sd_threshold: float = 0.2, max_sifts: int = 50,
                 boundary: int = capi.BOUNDARY_MIRROR, mirror_knots: int = 2,
                 precision: int = capi.FP32_MIXED, ensemble_trials: int = 1,
-                noise_rel_std: float = 0.2, s_number: int = 4) -> capi.semd_params:
+                noise_rel_std: float = 0.2, s_number: int = 4,
+                spline_end: int = capi.SPLINE_NATURAL) -> capi.semd_params:
     return capi.serial_emd_default_params(
         rows=rows, cols=cols, order=order, transition_len=transition_len, max_imfs=max_imfs,
         stop=stop, fixed_sifts=fixed_sifts, sd_threshold=sd_threshold, max_sifts=max_sifts,
         boundary=boundary, mirror_knots=mirror_knots, precision=precision,
-        ensemble_trials=ensemble_trials, noise_rel_std=noise_rel_std, s_number=s_number)
+        ensemble_trials=ensemble_trials, noise_rel_std=noise_rel_std, s_number=s_number,
+        spline_end=spline_end)
 
 
 def serialized_length(rows: int, cols: int, order: int = capi.ORDER_ROWS,

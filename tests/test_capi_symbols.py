@@ -35,7 +35,7 @@ def test_params_struct_layout_and_defaults():
     p = capi.serial_emd_default_params()
     assert ctypes.sizeof(capi.semd_params) == 80
     assert (p.max_imfs, p.fixed_sifts, p.mirror_knots, p.transition_len) == (10, 10, 2, -1)
-    assert (p.s_number, p.reserved) == (4, 0)
+    assert (p.s_number, p.spline_end) == (4, capi.SPLINE_NATURAL)
     assert p.sd_threshold == pytest.approx(0.2)
 
 
@@ -53,7 +53,7 @@ def test_invalid_params_rejected_before_device_use():
     bad = [dict(max_imfs=0), dict(max_imfs=33), dict(fixed_sifts=0), dict(mirror_knots=3),
            dict(order=5), dict(precision=7), dict(transition_len=-2), dict(stop=3),
            dict(stop=capi.STOP_SNUMBER, s_number=0),
-           dict(stop=capi.STOP_SNUMBER, max_sifts=0)]
+           dict(stop=capi.STOP_SNUMBER, max_sifts=0), dict(spline_end=2)]
     for kw in bad:
         p = capi.serial_emd_default_params(rows=4, cols=64, **kw)
         with pytest.raises(capi.SemdError) as ei:

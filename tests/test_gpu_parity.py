@@ -156,13 +156,16 @@ def _run(X, prec, order=capi.ORDER_ROWS, **kw):
 
 def _oracle(X, prec, order=capi.ORDER_ROWS, transition_len=-1, max_imfs=10,
             stop=capi.STOP_FIXED, fixed_sifts=10, sd_threshold=0.2, max_sifts=50,
-            boundary=capi.BOUNDARY_MIRROR, mirror_knots=2, s_number=4):
+            boundary=capi.BOUNDARY_MIRROR, mirror_knots=2, s_number=4,
+            spline_end=capi.SPLINE_NATURAL):
     Xd = np.asarray(np.asarray(X, NP[prec]), np.float64)
     Xs = Xd if order == capi.ORDER_ROWS else Xd.T
     N, M = Xs.shape
     D = round(0.2 * M) if transition_len < 0 else transition_len
     if N == 1:
         D = 0
+    if spline_end == capi.SPLINE_NOT_A_KNOT:
+        boundary += O.SPLINE_NOT_A_KNOT
     kw = dict(D=D, K=max_imfs, stop=stop, fixed_sifts=fixed_sifts, sd_threshold=sd_threshold,
               max_sifts=max_sifts, boundary=boundary, mirror_knots=mirror_knots,
               s_number=s_number)
@@ -235,6 +238,28 @@ def test_mask_series_transition_lengths_fp64(D, stop):
     assert list(g[3][:g[2]]) == list(o[3][:o[2]])
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(boundary=capi.BOUNDARY_ENDPOINTS),
+                                dict(mirror_knots=1)])
+@pytest.mark.parametrize("tile", [128, 512])
+def test_not_a_knot_ends_texture_fp64(kw, tile):
+    """Not-a-knot spline ends on the texture: the first and last tiles are dense for the
+    leading IMFs (the third knot from an end is a tile-interior knot given by the tile's
+    elimination) and sparse for the later ones."""
+    X = synth.workload_texture_256()[:64]
+    Xr = np.asarray(X, np.float64)
+    p = make_params(64, 256, precision=capi.FP64, transition_len=0, max_imfs=8,
+                    spline_end=capi.SPLINE_NOT_A_KNOT, **kw)
+    plan = Plan(p)
+    plan.tile = tile
+    imfs, res, n = plan.decompose(torch.from_numpy(Xr).cuda())
+    torch.cuda.synchronize()
+    g = (imfs.cpu().numpy(), res.cpu().numpy(), n)
+    plan.close()
+    o = _oracle(X, capi.FP64, transition_len=0, max_imfs=8, spline_end=capi.SPLINE_NOT_A_KNOT,
+                **kw)
+    _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, f"not-a-knot {kw}")
+
+
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
 def test_snumber_stop_texture(prec):
     """The S-number stop rule on the 256 x 256 texture: the zero crossings are counted per
@@ -285,7 +310,11 @@ def test_ragged_sizes_fp64(shape):
                                 dict(stop=capi.STOP_SD, sd_threshold=0.2, max_sifts=50),
                                 dict(stop=capi.STOP_SNUMBER, s_number=1, max_sifts=50),
                                 dict(stop=capi.STOP_SNUMBER, s_number=4, max_sifts=50),
-                                dict(stop=capi.STOP_SNUMBER, s_number=3, max_sifts=5)])
+                                dict(stop=capi.STOP_SNUMBER, s_number=3, max_sifts=5),
+                                dict(spline_end=capi.SPLINE_NOT_A_KNOT),
+                                dict(spline_end=capi.SPLINE_NOT_A_KNOT, mirror_knots=1),
+                                dict(spline_end=capi.SPLINE_NOT_A_KNOT,
+                                     boundary=capi.BOUNDARY_ENDPOINTS)])
 def test_options_fp64(kw):
     X = synth.tone_chirp_series(4, 900, 77)
     if kw.get("order") == capi.ORDER_COLS:

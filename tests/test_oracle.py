@@ -155,6 +155,30 @@ def test_spline_linear_data_is_exact():
     np.testing.assert_allclose(O.spline_second_derivs(s, v), 0.0, atol=1e-14)
 
 
+@pytest.mark.parametrize("n", [4, 5, 6, 9, 17, 40])
+def test_not_a_knot_spline_vs_scipy(n):
+    """Reading 6b against scipy's not-a-knot CubicSpline on random knots and values."""
+    g = synth.rng(100 + n)
+    s = np.cumsum(g.integers(1, 12, n)).astype(float) - 7.0
+    v = g.standard_normal(n)
+    ref = scipy_interp.CubicSpline(s, v, bc_type="not-a-knot")(s, 2)
+    np.testing.assert_allclose(O.spline_second_derivs(s, v, not_a_knot=True), ref,
+                               rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+def test_not_a_knot_spline_reproduces_cubics_and_falls_back_below_four_knots():
+    """A not-a-knot spline through samples of a cubic polynomial is that cubic (its
+    M = p'' exactly, linear in s); with three knots the natural spline is kept."""
+    s = np.array([-3.0, -1.0, 0.0, 2.0, 5.0, 6.0, 9.0])
+    p = 0.3 * s ** 3 - 1.1 * s ** 2 + 0.5 * s - 2.0
+    np.testing.assert_allclose(O.spline_second_derivs(s, p, not_a_knot=True),
+                               1.8 * s - 2.2, rtol=0, atol=1e-11)
+    assert np.abs(O.spline_second_derivs(s, p) - (1.8 * s - 2.2)).max() > 1e-3
+    s3, v3 = np.array([0.0, 1.0, 3.0]), np.array([1.0, -2.0, 0.5])
+    assert np.array_equal(O.spline_second_derivs(s3, v3, not_a_knot=True),
+                          O.spline_second_derivs(s3, v3))
+
+
 def _mirror_knots(h, t, P=2):
     L = h.size
     p = min(P, t.size)
@@ -187,6 +211,22 @@ def test_envelope_endpoints_rule_vs_scipy():
     v = np.concatenate([[h[0]], h[tmax], [h[63]]])
     ref = scipy_interp.CubicSpline(s, v, bc_type="natural")(np.arange(64))
     got = O.envelope(h, tmax, boundary=O.BOUNDARY_ENDPOINTS)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_envelope_not_a_knot_vs_scipy(rule):
+    """Envelopes with not-a-knot ends (Reading 6b) over the mirrored (P = 2) or endpoint
+    knot sequence, against scipy's not-a-knot CubicSpline of the same knots."""
+    h = synth.rng(7 + rule).standard_normal(90)
+    tmax, _ = O.extrema(h)
+    if rule == O.BOUNDARY_MIRROR:
+        s, v = _mirror_knots(h, tmax)
+    else:
+        s = np.concatenate([[0.0], tmax.astype(float), [89.0]])
+        v = np.concatenate([[h[0]], h[tmax], [h[89]]])
+    ref = scipy_interp.CubicSpline(s, v, bc_type="not-a-knot")(np.arange(90))
+    got = O.envelope(h, tmax, boundary=rule + O.SPLINE_NOT_A_KNOT)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
 
 
