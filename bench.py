@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_pass launch of the default workload, from the ncu
 # capture summarized in profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu
 # replays); set to None when the kernel changes until it is captured again.
-PASS_TRAFFIC_TEXTURE = None
+PASS_TRAFFIC_TEXTURE = 398080
 
 
 def _peaks():
@@ -114,6 +114,14 @@ def workload_inputs(name: str, trials: int = 256):
         return {"X": img, "W": w, "K": 10, "S": 10, "D": 0, "trials": trials,
                 "desc": f"EEMD of a 512x512 grating image (L=262144), {trials} noise realizations "
                         "(beta = 0.2 std), one batched run, 10 sifts/IMF, <=10 IMFs"}
+    if name == "ceemdan_mask":
+        X = synth.paper_mask_series()
+        L = 6 * 1000 + 50 * 6 - 50
+        return {"X": X, "W": synth.white_noise(100, L, 9001), "K": 10, "S": 10, "D": 50,
+                "trials": 100, "method": "ceemdan",
+                "desc": "serial-CEEMDAN of the 6-variate tone set (6 x 1000, D=50, L=6250), "
+                        "100 noise realizations (beta_k = 0.2 std(r_k)), 10 sifts/mode, "
+                        "<=10 modes"}
     if name == "series3x1024":
         return {"X": synth.workload_series_3x1024(), "K": 8, "S": 10, "D": 0, "trials": 1,
                 "desc": "3-channel series x 1024 samples (tones + chirp + noise), D=0, L=3072, "
@@ -123,6 +131,14 @@ def workload_inputs(name: str, trials: int = 256):
 
 def _flush_l2(buf):
     buf.add_(1)
+
+
+def _call(plan, wl, x, noise, imfs, res, stream):
+    """One decomposition of the workload through the public API (enqueued, no wait)."""
+    if wl.get("method") == "ceemdan":
+        plan.ceemdan(x, noise, imfs, res, stream=stream, wait=False)
+    else:
+        plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
 
 
 def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
@@ -149,7 +165,7 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
                  "default_shape_ms": r.ms_default, "candidates": r.candidates}
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
+            _call(plan, wl, x, noise, imfs, res, stream)
         stream.synchronize()
         times = []
         for _ in range(steps):
@@ -158,7 +174,7 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
+            _call(plan, wl, x, noise, imfs, res, stream)
             b.record(stream)
             times.append((a, b))
         stream.synchronize()
@@ -166,7 +182,7 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
     st = plan.stats()
     out = {"ms": ms, "sample_sifts": st.sample_sifts, "launches": st.kernel_launches,
            "graph": st.used_graph, "plan": plan, "x": x, "noise": noise, "imfs": imfs, "res": res,
-           "stream": stream, "shape": shape or {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas}}
+           "stream": stream, "wl": wl, "shape": shape or {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas}}
     return out
 
 
@@ -180,8 +196,7 @@ def profile_pass(run, steps, flush):
         for _ in range(steps):
             if flush is not None:
                 _flush_l2(flush)
-            plan.decompose(run["x"], run["noise"], run["imfs"], run["res"], stream=stream,
-                           wait=False)
+            _call(plan, run["wl"], run["x"], run["noise"], run["imfs"], run["res"], stream)
             stream.synchronize()
             st = plan.stats()
             tot["pass_ms"] += st.pass_ms
@@ -221,7 +236,7 @@ def e2e_ours(wl, precision, steps, warmup, device):
         x.copy_(hx, non_blocking=True)
         if noise is not None:
             noise.copy_(hn, non_blocking=True)
-        plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
+        _call(plan, wl, x, noise, imfs, res, stream)
         h_imfs.copy_(imfs, non_blocking=True)
         h_res.copy_(res, non_blocking=True)
 
@@ -272,10 +287,22 @@ def fp32_imf_errors_given_input(wl, run):
     return errs
 
 
-def cpu_baseline(wl, budget_s: float = 12.0):
+def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
     from oracle import oracle as O
     X = np.asarray(wl["X"], np.float64)
+    if wl.get("method") == "ceemdan":
+        # whole CEEMDAN calls; the work per call is counted as the GPU counts it
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < budget_s or done == 0:
+            O.serial_ceemdan(X, wl["D"], wl["K"], wl["W"], 0.2, fixed_sifts=wl["S"])
+            done += 1
+        el = time.perf_counter() - t0
+        return {"value": ss_per_step * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{done} full serial-CEEMDAN calls of the workload, FP64, single "
+                          "thread (samples*sifts per call as counted by the GPU run)",
+                "ms_per_call": el / done * 1e3}
     if wl["trials"] > 1:
         x = O.serialize(X, wl["D"])
         beta = 0.2 * O.std(x)
@@ -337,6 +364,11 @@ def arm_reference(args):
     if rank != 0:
         return
     wl = workload_inputs(args.workload, args.trials)
+    if wl.get("method") == "ceemdan":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the EMD "
+                          "workloads; serial-CEEMDAN is timed beside the GPU run "
+                          "(cpu_baseline of --workload ceemdan_mask)"}), flush=True)
+        return
     from oracle import oracle as O
     X = np.asarray(wl["X"], np.float64)
     per_step_budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
@@ -420,8 +452,9 @@ def arm_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind,
+                     # the capture was of 256-sample tiles (64 CTAs); other tiles differ
                      "traffic": PASS_TRAFFIC_TEXTURE if args.workload == "texture256" and
-                     not args.tile else None,
+                     r32["shape"]["tile"] == 256 else None,
                      "avg_launch_us": pass_avg_ms * 1e3, "bytes_per_launch": bytes_per_launch,
                      "launches": prof["pass_n"], "reduce_avg_us":
                          prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
@@ -449,7 +482,7 @@ def arm_ours(args):
         if not args.no_serving:
             line["serving"] = serving(args, device)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl)
+            line["cpu_baseline"] = cpu_baseline(wl, ss_per_step=r32["sample_sifts"])
         print(json.dumps(line), flush=True)
     elif not args.no_batched:  # the same collective calls as rank 0 (max over ranks)
         batched_eemd(args, device, flush, peak, peak_kind, world)
@@ -781,7 +814,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="texture256",
-                    choices=["texture256", "eemd512", "series3x1024"])
+                    choices=["texture256", "eemd512", "series3x1024", "ceemdan_mask"])
     ap.add_argument("--trials", type=int, default=256, help="EEMD realizations (eemd512)")
     ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64")
     ap.add_argument("--no-e2e", action="store_true")
