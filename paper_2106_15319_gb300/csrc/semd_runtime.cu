@@ -185,6 +185,8 @@ __global__ void k_ce_setup(const CeArgs *ca, Inst *inst, const State *state, CeS
         cs->beta = 0.0;
         cs->done = 0;
         cs->n = 0;
+        cs->mean = 0.0;
+        cs->arrived[0] = cs->arrived[1] = 0;
     }
 }
 
@@ -200,7 +202,7 @@ __global__ void k_ce_serialize(const CeArgs *ca)
 }
 
 template <typename T>
-__device__ __forceinline__ T block_sum_1024(T v, T *sh)
+__device__ __forceinline__ T block_sum(T v, T *sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -217,96 +219,130 @@ __device__ __forceinline__ T block_sum_1024(T v, T *sh)
     return v;
 }
 
-// Stage test, one CTA of 1024 threads: r_k must pass the IMF-start test (n_max >= 1,
-// n_min >= 1, n_max + n_min >= 3, extrema by the rule of Sec. 2.1 Step 1), else this and
-// every later stage is empty; beta_k = rel * population std of r_k.
-__global__ void __launch_bounds__(1024) k_ce_stage_test(const CeArgs *ca, CeState *cs)
+// Stage test of r_k in two passes over blocks of kCeTestSpan samples, each ending in the
+// last block to finish (a counter, no waiting): pass 0 sums r_k and the last block forms
+// the mean; pass 1 sums (r_k - mean)^2 and counts extrema (the rule of Sec. 2.1 Step 1),
+// and its last block takes the IMF-start test (n_max >= 1, n_min >= 1, n_max + n_min >= 3;
+// when it fails this and every later stage is empty) and beta_k = rel * population std of
+// r_k. The partials are combined in block order, so the result does not depend on timing.
+__global__ void __launch_bounds__(256) k_ce_stage_test(const CeArgs *ca, CeState *cs,
+                                                       CePart *part, int pass)
 {
     if (cs->done)
         return;
     const CeArgs &a = *ca;
     const double *r = a.r;
     const int64_t L = a.L;
+    const int64_t b0 = (int64_t)blockIdx.x * kCeTestSpan;
+    const int64_t b1 = min(b0 + (int64_t)kCeTestSpan, L);
     __shared__ double shd[32];
     __shared__ int shi[32];
+    __shared__ bool last;
+    const double mean = pass == 0 ? 0.0 : cs->mean;
     double s = 0.0;
     int nmax = 0, nmin = 0;
-    for (int64_t k = threadIdx.x; k < L; k += blockDim.x) {
+    for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
         const double c = r[k];
-        s += c;
-        if (k >= 1 && k + 1 < L) {
-            const double l = r[k - 1], rr = r[k + 1];
-            nmax += (l < c && c >= rr) ? 1 : 0;
-            nmin += (l > c && c <= rr) ? 1 : 0;
+        if (pass == 0) {
+            s += c;
+        } else {
+            s += (c - mean) * (c - mean);
+            if (k >= 1 && k + 1 < L) {
+                const double l = r[k - 1], rr = r[k + 1];
+                nmax += (l < c && c >= rr) ? 1 : 0;
+                nmin += (l > c && c <= rr) ? 1 : 0;
+            }
         }
     }
-    const double mean = block_sum_1024(s, shd) / (double)L;
-    nmax = block_sum_1024(nmax, shi);
-    nmin = block_sum_1024(nmin, shi);
-    double v = 0.0;
-    for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
-        v += (r[k] - mean) * (r[k] - mean);
-    v = block_sum_1024(v, shd);
+    s = block_sum(s, shd);
+    if (pass == 1) {
+        nmax = block_sum(nmax, shi);
+        nmin = block_sum(nmin, shi);
+    }
     if (threadIdx.x == 0) {
-        if (nmax >= 1 && nmin >= 1 && nmax + nmin >= 3) {
+        part[blockIdx.x] = CePart{s, nmax, nmin};
+        __threadfence();
+        last = atomicAdd(&cs->arrived[pass], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        int64_t xa = 0, xb = 0;
+        for (unsigned q = 0; q < gridDim.x; ++q) { // L2 reads: other blocks wrote them
+            t += __ldcg(&part[q].s);
+            xa += __ldcg(&part[q].nmax);
+            xb += __ldcg(&part[q].nmin);
+        }
+        cs->arrived[pass] = 0;
+        if (pass == 0) {
+            cs->mean = t / (double)L;
+        } else if (xa >= 1 && xb >= 1 && xa + xb >= 3) {
             cs->n += 1;
-            cs->beta = a.rel * sqrt(v / (double)L);
+            cs->beta = a.rel * sqrt(t / (double)L);
         } else {
             cs->done = 1;
         }
     }
 }
 
-// The trials' stage inputs r_k + beta_k E_k(w^(m)) as their residues for the INIT pass;
-// for an empty stage every trial is marked done instead (its first mode counts as zero).
+// The trials' stage inputs r_k + beta_k E_k(w^(m)) as their residues for the INIT pass,
+// one trial per grid row; for an empty stage every trial is marked done instead (its
+// first mode counts as zero).
 template <typename R>
 __global__ void k_ce_stage_init(const CeArgs *ca, const Inst *inst, State *state,
                                 const CeState *cs, int stage)
 {
     const CeArgs &a = *ca;
+    const int m = blockIdx.y;
     if (cs->done) {
-        if (blockIdx.x == 0)
-            for (int m = threadIdx.x; m < a.trials; m += blockDim.x)
-                state[m].mode = MODE_DONE;
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            state[m].mode = MODE_DONE;
         return;
     }
     const double beta = cs->beta;
-    const R *w = (const R *)a.noise, *E = (const R *)a.E;
+    const R *e = stage == 0 ? (const R *)a.noise + (int64_t)m * a.L
+                 : stage - 1 < a.ncount[m]
+                     ? (const R *)a.E + ((int64_t)m * a.K + (stage - 1)) * a.slot
+                     : nullptr;
+    double *dst = inst[m].r[0];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.L;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const double rk = a.r[p];
-        for (int m = 0; m < a.trials; ++m) {
-            double e;
-            if (stage == 0)
-                e = (double)w[(int64_t)m * a.L + p];
-            else
-                e = stage - 1 < a.ncount[m]
-                        ? (double)E[((int64_t)m * a.K + (stage - 1)) * a.slot + p]
-                        : 0.0;
-            inst[m].r[0][p] = __dadd_rn(rk, __dmul_rn(beta, e));
-        }
-    }
+         p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = __dadd_rn(a.r[p], __dmul_rn(beta, e ? (double)e[p] : 0.0));
 }
 
 // Mode k+1 = the average of the trials' first modes (zero for a trial without one), in
-// FP64 and trial order; r_{k+1} = r_k - mode (Step 3); the mode de-serialized (Sec. 3.3).
+// FP64; r_{k+1} = r_k - mode (Step 3); the mode de-serialized (Sec. 3.3). A block covers
+// 32 samples with 8 warps: warp g sums the trials m = g, g + 8, ... in order, then the 8
+// partial sums are added in warp order (a fixed order, independent of timing).
+constexpr int kCeAvgGroups = 8;
 template <typename R>
-__global__ void k_ce_average(const CeArgs *ca, const Inst *inst, const State *state, int stage)
+__global__ void __launch_bounds__(32 * kCeAvgGroups)
+    k_ce_average(const CeArgs *ca, const Inst *inst, const State *state, int stage)
 {
     const CeArgs &a = *ca;
-    R *out = (R *)a.modes + (int64_t)stage * a.M * a.N;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.L;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int m = 0; m < a.trials; ++m)
+    __shared__ double part[kCeAvgGroups][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (p < a.L)
+        for (int m = g; m < a.trials; m += kCeAvgGroups)
             if (state[m].imf_count >= 1)
                 acc += (double)((const R *)inst[m].imf)[p];
-        const double c = acc / (double)a.trials;
-        a.r[p] = a.r[p] - c;
-        int64_t dst;
-        if (deser_index(p, a.M, a.N, a.D, a.order, dst))
-            out[dst] = (R)c;
-    }
+    part[g][lane] = acc;
+    __syncthreads();
+    if (g != 0 || p >= a.L)
+        return;
+#pragma unroll
+    for (int q = 1; q < kCeAvgGroups; ++q)
+        acc += part[q][lane];
+    const double c = acc / (double)a.trials;
+    a.r[p] = a.r[p] - c;
+    int64_t dst;
+    if (deser_index(p, a.M, a.N, a.D, a.order, dst))
+        ((R *)a.modes)[(int64_t)stage * a.M * a.N + dst] = (R)c;
 }
 
 // The final residue, de-serialized (Sec. 3.3).
@@ -616,6 +652,9 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         reqs.push_back({(void **)&d_cestate, sizeof(CeState)});
         reqs.push_back({(void **)&d_cecount, (size_t)insts * 4});
         reqs.push_back({(void **)&d_ce_r, (size_t)(samples / insts) * 8});
+        reqs.push_back({(void **)&d_cepart,
+                        (size_t)((samples / insts + kCeTestSpan - 1) / kCeTestSpan + 1) *
+                            sizeof(CePart)});
     }
     size_t total = 0;
     for (auto &r : reqs)
@@ -983,6 +1022,12 @@ static semd_status enqueue_ceemdan(semd_plan_s &pl, int64_t ntiles, cudaStream_t
     int64_t launches = 0;
     const int64_t L = ws.h_ce->L;
     const unsigned eg = (unsigned)std::min<int64_t>((L + 255) / 256, 4 * 304);
+    // stage test: one block per kCeTestSpan samples; stage inputs: one grid row per trial,
+    // about 4 x 152 blocks in all; average: one block per 32 samples
+    const unsigned tg = (unsigned)((L + kCeTestSpan - 1) / kCeTestSpan);
+    const unsigned ig = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((L + 255) / 256, (4 * 152 + trials - 1) / trials));
+    const unsigned ag = (unsigned)((L + 31) / 32);
     SEMD_CU(cudaMemsetAsync(ws.d_stats, 0, sizeof(Stats), s));
     ReduceArgs ra = reduce_args(ws, p);
     semd_status st;
@@ -1009,15 +1054,18 @@ static semd_status enqueue_ceemdan(semd_plan_s &pl, int64_t ntiles, cudaStream_t
     const int iters1 = max_iterations(p1);
     ra.K = 1;
     for (int k = 0; k < K; ++k) {
-        k_ce_stage_test<<<1, 1024, 0, s>>>(ws.d_ce, ws.d_cestate);
+        k_ce_stage_test<<<tg, 256, 0, s>>>(ws.d_ce, ws.d_cestate, ws.d_cepart, 0);
+        k_ce_stage_test<<<tg, 256, 0, s>>>(ws.d_ce, ws.d_cestate, ws.d_cepart, 1);
         SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)trials * sizeof(State), s));
         SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters1 * 4, s));
-        k_ce_stage_init<R><<<eg, 256, 0, s>>>(ws.d_ce, ws.d_inst, ws.d_state, ws.d_cestate, k);
-        launches += 2;
+        k_ce_stage_init<R><<<dim3(ig, (unsigned)trials), 256, 0, s>>>(ws.d_ce, ws.d_inst,
+                                                                      ws.d_state, ws.d_cestate,
+                                                                      k);
+        launches += 3;
         st = sift_loop<R>(pl, ra, trials, ntiles, iters1, s, prof, capture, launches);
         if (st != SEMD_OK)
             return st;
-        k_ce_average<R><<<eg, 256, 0, s>>>(ws.d_ce, ws.d_inst, ws.d_state, k);
+        k_ce_average<R><<<ag, 32 * kCeAvgGroups, 0, s>>>(ws.d_ce, ws.d_inst, ws.d_state, k);
         ++launches;
     }
     k_ce_finish<<<eg, 256, 0, s>>>(ws.d_ce);
@@ -1511,6 +1559,10 @@ semd_status serial_emd_ceemdan(semd_plan_t plan, const void *d_x, const void *d_
     }
     if (!d_x || !d_noise || !d_modes) {
         plan->err = "null input, noise or output pointer";
+        return SEMD_EINVAL;
+    }
+    if (plan->p.ensemble_trials > 65535) {
+        plan->err = "CEEMDAN takes at most 65535 realizations";
         return SEMD_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;

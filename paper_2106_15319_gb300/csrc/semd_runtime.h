@@ -47,6 +47,7 @@ struct Workspace {
     CeState *d_cestate = nullptr;
     int32_t *d_cecount = nullptr;
     double *d_ce_r = nullptr;
+    CePart *d_cepart = nullptr; // one per stage-test block
     // pinned host staging
     Inst *h_inst = nullptr;
     int32_t *h_tile_inst = nullptr;

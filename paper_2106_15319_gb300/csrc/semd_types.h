@@ -148,7 +148,16 @@ struct CeState {
     double beta;          // beta_k of the current stage
     int32_t done;         // 1: a residue failed the IMF-start test, later stages are empty
     int32_t n;            // modes produced
+    double mean;          // mean of r_k (first pass of the stage test)
+    uint32_t arrived[2];  // blocks of the two stage-test passes that have finished
 };
+// Per-block partial results of the stage test.
+struct CePart {
+    double s;             // sum of r (first pass) or of (r - mean)^2 (second pass)
+    int32_t nmax, nmin;   // extrema of r_k in the block's samples (second pass)
+};
+// Samples per block of the stage-test passes.
+constexpr int kCeTestSpan = 2048;
 
 // Threads of the interface-solve kernel (one CTA per instance and envelope).
 constexpr int kRedThreads = 256;
