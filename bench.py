@@ -34,10 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "serialized samples sifted/s: batched FP32 vs plain FP64 on GB300; p99 request latency"
 UNIT = "samples*sifts/s"
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one k_pass launch of the default workload, from the ncu
-# capture summarized in profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu
-# replays); set to None when the kernel changes until it is captured again.
-PASS_TRAFFIC_TEXTURE = 398080
+# DRAM bytes (read + write) of one k_pass launch of the default workload (256-sample tiles)
+# per register-budget variant, from the ncu captures summarized in
+# profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu replays); emptied when
+# the kernel changes until it is captured again.
+PASS_TRAFFIC_TEXTURE = {0: 397824, 1: 398592}
 
 
 def _peaks():
@@ -141,7 +142,7 @@ def _call(plan, wl, x, noise, imfs, res, stream):
         plan.decompose(x, noise, imfs, res, stream=stream, wait=False)
 
 
-def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
+def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False, variant=None):
     import torch
     from paper_2106_15319_gb300 import capi
     from paper_2106_15319_gb300.serial_emd import Plan, make_params
@@ -153,15 +154,19 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
     plan = Plan(p)
     if tile:
         plan.tile = tile
+    if variant is not None:
+        plan.pass_variant = variant
     x = torch.from_numpy(X).to(device)
     noise = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).to(device) if wl["trials"] > 1 \
         else None
     imfs, res = plan.outputs(rows, cols, device=device)
     stream = torch.cuda.Stream(device)
     shape = None
-    if tune and not tile:  # setup, before the warm-up: the autotuner picks the pass shape
+    if tune and not tile and variant is None:  # setup, before the warm-up: the autotuner
+        # picks the pass shape
         r = plan.autotune(x, noise, outs=[(imfs, res)], repeats=3, stream=stream)
-        shape = {"tile": r.tile, "ctas_per_sm": r.ctas_per_sm, "tuned_ms": r.ms,
+        shape = {"tile": r.tile, "ctas_per_sm": r.ctas_per_sm, "variant": r.variant,
+                 "tuned_ms": r.ms,
                  "default_shape_ms": r.ms_default, "candidates": r.candidates}
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -182,7 +187,9 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False):
     st = plan.stats()
     out = {"ms": ms, "sample_sifts": st.sample_sifts, "launches": st.kernel_launches,
            "graph": st.used_graph, "plan": plan, "x": x, "noise": noise, "imfs": imfs, "res": res,
-           "stream": stream, "wl": wl, "shape": shape or {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas}}
+           "stream": stream, "wl": wl,
+           "shape": shape or {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas,
+                              "variant": plan.pass_variant}}
     return out
 
 
@@ -404,7 +411,7 @@ def arm_ours(args):
     barrier(world)
     with ClockSampler(local) as clk:
         r32 = run_ours(wl, capi.FP32_MIXED, args.steps, args.warmup, device, flush, args.tile,
-                       tune=not args.no_tune)
+                       tune=not args.no_tune, variant=args.pass_variant)
     barrier(world)
     ms32 = statistics.mean(r32["ms"])
     ms32_max = max_over_ranks(ms32, world)
@@ -452,9 +459,10 @@ def arm_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind,
-                     # the capture was of 256-sample tiles (64 CTAs); other tiles differ
-                     "traffic": PASS_TRAFFIC_TEXTURE if args.workload == "texture256" and
-                     r32["shape"]["tile"] == 256 else None,
+                     # the captures were of 256-sample tiles (64 CTAs); other tiles differ
+                     "traffic": PASS_TRAFFIC_TEXTURE.get(r32["shape"]["variant"])
+                     if args.workload == "texture256" and r32["shape"]["tile"] == 256
+                     else None,
                      "avg_launch_us": pass_avg_ms * 1e3, "bytes_per_launch": bytes_per_launch,
                      "launches": prof["pass_n"], "reduce_avg_us":
                          prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
@@ -702,6 +710,8 @@ def ceemdan_legs(args, device, flush, world):
             wt = torch.from_numpy(w).to(device)
             modes, res = plan.outputs(rows, cols, device=device)
             stream = torch.cuda.Stream(device)
+            if not args.no_tune:  # setup: the pass shape of the ensemble's sifting
+                plan.autotune(x, wt, outs=[(modes, res)], repeats=2, stream=stream)
             ms = []
             with torch.cuda.stream(stream):
                 for _ in range(min(args.warmup, 3)):
@@ -718,6 +728,8 @@ def ceemdan_legs(args, device, flush, world):
                     ms.append(a.elapsed_time(b))
             st = plan.stats()
             n = plan.counts(1)[0][0]
+            shape = {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas,
+                     "variant": plan.pass_variant}
             plan.close()
             m = max_over_ranks(statistics.mean(ms), world)
             key = f"{name}_{'fp32' if prec == capi.FP32_MIXED else 'fp64'}"
@@ -725,6 +737,7 @@ def ceemdan_legs(args, device, flush, world):
                         "unit": UNIT, "modes": int(n), "L": L, "trials": trials,
                         "launches_per_step": int(st.kernel_launches),
                         "cuda_graph": bool(st.used_graph),
+                        "pass_shape": shape,
                         "paper_cpu_ms_context": paper_ms}
     return out
 
@@ -827,6 +840,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass shape (no autotuning before the warm-up)")
+    ap.add_argument("--pass-variant", type=int, default=None, choices=[0, 1],
+                    help="register budget of the FP32 pass kernel (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

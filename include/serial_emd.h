@@ -284,22 +284,31 @@ semd_status serial_emd_plan_set_pass_ctas(semd_plan_t plan, int ctas_per_sm);
 /* The plan's current setting (0 for a NULL plan). */
 int serial_emd_plan_get_pass_ctas(semd_plan_t plan);
 
+/*
+ * Register budget of the pass kernel where it is compiled in two (FP32, 256-sample tiles):
+ * variant 0 (default) keeps four CTAs per SM resident at the cost of a few spilled bytes,
+ * variant 1 keeps three with none (better for launches too small to fill the GPU). Other
+ * kernels ignore it. Changes speed only. Errors: EINVAL (not 0 or 1).
+ */
+semd_status serial_emd_plan_set_pass_variant(semd_plan_t plan, int variant);
+int serial_emd_plan_get_pass_variant(semd_plan_t plan);
+
 /* ------------------------------------------------------------------ autotuner */
 
 typedef struct semd_tune_result {
     int32_t tile;        /* chosen tile (samples per warp) */
     int32_t ctas_per_sm; /* chosen CTAs per SM of the pass grid (0: as many as fit) */
     double ms;           /* median device time of one decomposition with the choice */
-    double ms_default;   /* the same with the default shape (tile 256, all CTAs) */
+    double ms_default;   /* the same with the default shape (tile 256, variant 0, all CTAs) */
     int32_t candidates;  /* shapes timed */
-    int32_t _reserved;
+    int32_t variant;     /* chosen register budget (see serial_emd_plan_set_pass_variant) */
 } semd_tune_result;
 
 /*
  * Times the plan's decomposition of `count` inputs (as serial_emd_decompose_batch takes
  * them; for an ensemble plan one input and its noise, as serial_emd_decompose) for every
- * pass-kernel shape: tile 128, 256 or 512, and CTAs per SM of the persistent grid (as
- * many as fit, or fewer). Each shape runs once untimed, then `repeats` times (1..100)
+ * pass-kernel shape: tile 128, 256 or 512, the register budget where the kernel has two,
+ * and CTAs per SM of the persistent grid (as many as fit, or fewer). Each shape runs once untimed, then `repeats` times (1..100)
  * with CUDA events on `stream`; the median counts. The fastest shape is kept on the plan
  * and entered in the process-wide tuning table under the plan's key: precision, stop
  * rule, ensemble or not, ceil(log2) of the instance count (trials for an ensemble) and
@@ -312,14 +321,15 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
                                      void *stream);
 
 /* The tuning table's shape for a plan of these params, longest serialized length L and
- * ninst instances: SEMD_OK and *tile, *ctas_per_sm set, or SEMD_PENDING when the table
- * has no entry. EINVAL for bad arguments. Host only. */
+ * ninst instances: SEMD_OK and *tile, *ctas_per_sm, *variant set, or SEMD_PENDING when the
+ * table has no entry. EINVAL for bad arguments. Host only. */
 semd_status serial_emd_tune_lookup(const semd_params *params, int64_t L, int ninst, int *tile,
-                                   int *ctas_per_sm);
+                                   int *ctas_per_sm, int *variant);
 /* Empties the tuning table. */
 void serial_emd_tune_clear(void);
 /* Writes the table as JSON (an "entries" list of flat objects with the key fields,
- * "tile", "ctas_per_sm" and "ms"). Errors: EINVAL (see serial_emd_tune_last_error). */
+ * "tile", "ctas_per_sm", "variant" and "ms"). Errors: EINVAL (see
+ * serial_emd_tune_last_error). */
 semd_status serial_emd_tune_save(const char *path);
 /* Merges a file written by serial_emd_tune_save into the table; entries with missing
  * fields or an invalid shape are skipped. Errors: EINVAL (unreadable, no "entries"). */

@@ -64,7 +64,7 @@ class semd_stats(ctypes.Structure):
 class semd_tune_result(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("ms", ctypes.c_double), ("ms_default", ctypes.c_double),
-                ("candidates", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class semd_result(ctypes.Structure):
@@ -116,7 +116,10 @@ SIGNATURES = {
                                                 ctypes.c_void_p]),
     "serial_emd_tune_lookup": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_int64,
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
+    "serial_emd_plan_set_pass_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "serial_emd_plan_get_pass_variant": (ctypes.c_int, [ctypes.c_void_p]),
     "serial_emd_tune_clear": (None, []),
     "serial_emd_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "serial_emd_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
@@ -310,15 +313,23 @@ def serial_emd_plan_autotune(plan: int, items, noise=None, repeats: int = 3,
 
 
 def serial_emd_tune_lookup(params: semd_params, L: int, ninst: int):
-    """(tile, ctas_per_sm) of the tuning table's entry, or None."""
-    t, c = ctypes.c_int(), ctypes.c_int()
+    """(tile, ctas_per_sm, variant) of the tuning table's entry, or None."""
+    t, c, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     rc = load().serial_emd_tune_lookup(ctypes.byref(params), L, ninst, ctypes.byref(t),
-                                       ctypes.byref(c))
+                                       ctypes.byref(c), ctypes.byref(v))
     if rc == SEMD_PENDING:
         return None
     if rc != 0:
         raise SemdError(rc, "bad arguments")
-    return t.value, c.value
+    return t.value, c.value, v.value
+
+
+def serial_emd_plan_set_pass_variant(plan: int, variant: int) -> None:
+    _check(load().serial_emd_plan_set_pass_variant(plan, variant), plan)
+
+
+def serial_emd_plan_get_pass_variant(plan: int) -> int:
+    return int(load().serial_emd_plan_get_pass_variant(plan))
 
 
 def serial_emd_tune_clear() -> None:

@@ -1,12 +1,15 @@
 // Autotuner of the sifting pass kernel's launch shape (host code).
 //
-// The pass kernel has two free launch parameters: the tile (128, 256 or 512 samples per
-// warp, which moves work between the per-tile eliminations and the interface system)
-// and how many CTAs per SM its persistent grid keeps resident (fewer CTAs leave each one
-// a longer contiguous range of tiles and more cache per CTA). Neither changes what is
-// computed beyond rounding. serial_emd_plan_autotune times the plan's own decomposition
-// of a caller's input for every candidate shape, keeps the fastest on the plan and
-// records it in a process-wide table keyed by what decides the best shape: precision,
+// The pass kernel has three free launch parameters: the tile (128, 256 or 512 samples per
+// warp, which moves work between the per-tile eliminations and the interface system),
+// for the FP32 kernel of 256-sample tiles its register budget (variant 0 keeps four CTAs
+// per SM resident, variant 1 three with no spilled registers: latency-bound launches
+// prefer the latter), and how many CTAs per SM its persistent grid keeps resident (fewer
+// CTAs leave each one a longer contiguous range of tiles and more cache per CTA). None
+// changes what is computed beyond rounding. serial_emd_plan_autotune times the plan's own
+// decomposition of a caller's input for every candidate shape, keeps the fastest on the
+// plan and records it in a process-wide table keyed by what decides the best shape:
+// precision,
 // stop rule, ensemble or not, and the log2 buckets of the instance count and of the
 // longest serialized length. Plans created later with the same key start from the
 // table's entry. The table can be saved to and merged from a JSON file.
@@ -37,7 +40,7 @@ struct TuneKey {
 };
 
 struct TuneVal {
-    int tile = kTile, ctas = 0;
+    int tile = kTile, ctas = 0, variant = 0;
     double ms = 0.0;
 };
 
@@ -59,9 +62,10 @@ TuneKey make_key(const semd_params &p, int64_t L, int ninst)
                    ceil_log2(L)};
 }
 
-bool valid_shape(int tile, int ctas)
+bool valid_shape(int tile, int ctas, int variant)
 {
-    return (tile == 128 || tile == 256 || tile == 512) && ctas >= 0 && ctas <= 64;
+    return (tile == 128 || tile == 256 || tile == 512) && ctas >= 0 && ctas <= 64 &&
+           (variant == 0 || variant == 1);
 }
 
 // One decomposition of the tuning input, enqueued on s.
@@ -105,7 +109,8 @@ semd_status time_shape(semd_plan_s &pl, int count, const semd_instance *inst,
 
 } // namespace
 
-bool tune_lookup(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas)
+bool tune_lookup(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas,
+                 int &variant)
 {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(make_key(p, L, ninst));
@@ -113,6 +118,7 @@ bool tune_lookup(const semd_params &p, int64_t L, int ninst, int &tile, int &cta
         return false;
     tile = it->second.tile;
     ctas = it->second.ctas;
+    variant = it->second.variant;
     return true;
 }
 
@@ -161,7 +167,7 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
         pl.err = "autotune: event creation failed";
         return SEMD_ECUDA;
     }
-    const int tile0 = pl.ws.tile, ctas0 = pl.ws.pass_ctas;
+    const int tile0 = pl.ws.tile, ctas0 = pl.ws.pass_ctas, var0 = pl.ws.pass_variant;
     const bool prof0 = pl.prof.on;
     pl.prof.on = false;
     const size_t elem = pl.p.precision == SEMD_FP64 ? 8 : 4;
@@ -171,25 +177,30 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
     semd_status st = SEMD_OK;
     int tried = 0;
     for (int tile : {256, 128, 512}) {
-        const int fit = pass_ctas_per_sm_max(elem, tile);
-        std::vector<int> cand = {0};
-        for (int c : {1, 2, 3, 4, 6, 8})
-            if (c < fit)
-                cand.push_back(c);
-        for (int c : cand) {
-            pl.ws.tile = tile;
-            pl.ws.pass_ctas = c;
-            double ms = 0.0;
-            st = time_shape(pl, count, inst, d_noise, repeats, s, a, b, ms);
-            if (st != SEMD_OK)
-                break;
-            ++tried;
-            if (tile == kTile && c == 0)
-                res.ms_default = ms;
-            if (best.ms < 0.0 || ms < best.ms) {
-                best.tile = tile;
-                best.ctas = c;
-                best.ms = ms;
+        for (int var = 0; var < (pass_has_variants(elem, tile) ? 2 : 1) && st == SEMD_OK;
+             ++var) {
+            const int fit = pass_ctas_per_sm_max(elem, tile, var);
+            std::vector<int> cand = {0};
+            for (int c : {1, 2, 3, 4, 6, 8})
+                if (c < fit)
+                    cand.push_back(c);
+            for (int c : cand) {
+                pl.ws.tile = tile;
+                pl.ws.pass_ctas = c;
+                pl.ws.pass_variant = var;
+                double ms = 0.0;
+                st = time_shape(pl, count, inst, d_noise, repeats, s, a, b, ms);
+                if (st != SEMD_OK)
+                    break;
+                ++tried;
+                if (tile == kTile && c == 0 && var == 0)
+                    res.ms_default = ms;
+                if (best.ms < 0.0 || ms < best.ms) {
+                    best.tile = tile;
+                    best.ctas = c;
+                    best.variant = var;
+                    best.ms = ms;
+                }
             }
         }
         if (st != SEMD_OK)
@@ -201,16 +212,19 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
     if (st != SEMD_OK) {
         pl.ws.tile = tile0;
         pl.ws.pass_ctas = ctas0;
+        pl.ws.pass_variant = var0;
         return st;
     }
     pl.ws.tile = best.tile;
     pl.ws.pass_ctas = best.ctas;
+    pl.ws.pass_variant = best.variant;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune[make_key(pl.p, Lmax, eemd ? pl.p.ensemble_trials : count)] = best;
     }
     res.tile = best.tile;
     res.ctas_per_sm = best.ctas;
+    res.variant = best.variant;
     res.ms = best.ms;
     res.candidates = tried;
     if (out)
@@ -219,15 +233,16 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
 }
 
 semd_status serial_emd_tune_lookup(const semd_params *params, int64_t L, int ninst, int *tile,
-                                   int *ctas_per_sm)
+                                   int *ctas_per_sm, int *variant)
 {
-    if (!params || !tile || !ctas_per_sm || L < 1 || ninst < 1)
+    if (!params || !tile || !ctas_per_sm || !variant || L < 1 || ninst < 1)
         return SEMD_EINVAL;
-    int t = kTile, c = 0;
-    if (!tune_lookup(*params, L, ninst, t, c))
+    int t = kTile, c = 0, v = 0;
+    if (!tune_lookup(*params, L, ninst, t, c, v))
         return SEMD_PENDING;
     *tile = t;
     *ctas_per_sm = c;
+    *variant = v;
     return SEMD_OK;
 }
 
@@ -250,10 +265,10 @@ semd_status serial_emd_tune_save(const char *path)
             std::snprintf(line, sizeof line,
                           "%s\n    {\"precision\": %d, \"stop\": %d, \"ensemble\": %d, "
                           "\"batch_log2\": %d, \"len_log2\": %d, \"tile\": %d, "
-                          "\"ctas_per_sm\": %d, \"ms\": %.6f}",
+                          "\"ctas_per_sm\": %d, \"variant\": %d, \"ms\": %.6f}",
                           first ? "" : ",", kv.first.precision, kv.first.stop,
                           kv.first.ensemble, kv.first.batch_log2, kv.first.len_log2,
-                          kv.second.tile, kv.second.ctas, kv.second.ms);
+                          kv.second.tile, kv.second.ctas, kv.second.variant, kv.second.ms);
             txt += line;
             first = false;
         }
@@ -339,8 +354,10 @@ semd_status serial_emd_tune_load(const char *path)
         TuneVal v;
         v.tile = (int)fld["tile"];
         v.ctas = (int)fld["ctas_per_sm"];
+        v.variant = fld.count("variant") ? (int)fld["variant"] : 0;
         v.ms = fld.count("ms") ? fld["ms"] : 0.0;
-        if (!valid_shape(v.tile, v.ctas))
+        if (!valid_shape(v.tile, v.ctas, v.variant) ||
+            (fld.count("variant") && fld["variant"] != std::floor(fld["variant"])))
             continue;
         got.push_back({k, v});
     }

@@ -894,11 +894,10 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
 // takes the contiguous tile range [w C, w C + C) of the launch (C = tiles / warps,
 // rounded up), so its next tile is usually the next tile of the same instance, which
 // it prefetches into L2. Warps are independent (no block barrier).
-// The FP32 kernel of 256-sample tiles is shared-memory-limited to 5 CTAs per SM; its
-// register budget is held to that occupancy.
-template <typename R, int SPL, int NWARP>
-__global__ void __launch_bounds__(NWARP * 32, (sizeof(R) == 4 && SPL == 8) ? 5 : 1)
-    k_pass(PassArgs pa)
+// MINB is the register budget's target: the compiler keeps to the registers that let MINB
+// CTAs reside on an SM (1: no limit).
+template <typename R, int SPL, int NWARP, int MINB>
+__global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
 {
     constexpr int TW = 32 * SPL;
     extern __shared__ __align__(16) unsigned char smraw[];

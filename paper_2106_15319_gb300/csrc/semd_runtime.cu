@@ -402,14 +402,21 @@ __global__ void k_to_double(const R *h, int64_t L, double *r)
 // ------------------------------------------------------------------ plan helpers
 
 // The pass kernel for each supported tile: 128 / 256 / 512 samples per warp (4, 8, 16 per
-// lane), kPassWarps warps per CTA.
+// lane), kPassWarps warps per CTA. The FP32 kernel of 256-sample tiles comes in two
+// register budgets (variant 0: four resident CTAs per SM, a few spilled bytes; variant 1:
+// three, no spills); the other kernels have one, and take either variant number.
+template <typename R, int TILE, int VAR>
+static constexpr int pass_minb() { return (sizeof(R) == 4 && TILE == 256) ? (VAR == 0 ? 4 : 3) : 1; }
+template <typename R, int TILE, int VAR>
+static constexpr auto pass_kernel() { return k_pass<R, TILE / 32, kPassWarps, pass_minb<R, TILE, VAR>()>; }
+
 template <typename R, int TILE>
 static constexpr size_t pass_smem() { return kPassWarps * sizeof(WarpPool<R, TILE>); }
 
-template <typename R, int TILE>
+template <typename R, int TILE, int VAR>
 static cudaError_t pass_attr_one()
 {
-    return cudaFuncSetAttribute(k_pass<R, TILE / 32, kPassWarps>,
+    return cudaFuncSetAttribute(pass_kernel<R, TILE, VAR>(),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pass_smem<R, TILE>());
 }
@@ -417,20 +424,22 @@ static cudaError_t pass_attr_one()
 template <typename R>
 static cudaError_t set_smem_attr()
 {
-    cudaError_t e = pass_attr_one<R, 128>();
+    cudaError_t e = pass_attr_one<R, 128, 0>();
     if (e == cudaSuccess)
-        e = pass_attr_one<R, 256>();
+        e = pass_attr_one<R, 256, 0>();
     if (e == cudaSuccess)
-        e = pass_attr_one<R, 512>();
+        e = pass_attr_one<R, 256, 1>();
+    if (e == cudaSuccess)
+        e = pass_attr_one<R, 512, 0>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_reduce<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kReduceSmemMax);
     return e;
 }
 
-// CTAs of the pass kernel that fit on one SM of the current device at once, and the
+// CTAs of a pass kernel that fit on one SM of the current device at once, and the
 // device's SM count, computed once per device.
-template <typename R, int TILE>
+template <typename R, int TILE, int VAR>
 static void pass_residency(int &per_sm, int &sms)
 {
     constexpr int kMaxDev = 64;
@@ -442,7 +451,7 @@ static void pass_residency(int &per_sm, int &sms)
         return;
     if (cache[dev][0] == 0) {
         int a = 0, b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass<R, TILE / 32, kPassWarps>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, pass_kernel<R, TILE, VAR>(),
                                                           32 * kPassWarps,
                                                           pass_smem<R, TILE>()) != cudaSuccess ||
             cudaDeviceGetAttribute(&b, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -454,24 +463,26 @@ static void pass_residency(int &per_sm, int &sms)
     sms = cache[dev][1];
 }
 
-int pass_ctas_per_sm_max(size_t elem, int tile)
+template <typename R>
+static void pass_residency_of(int tile, int variant, int &per_sm, int &sms)
 {
-    int per_sm, sms;
-    if (elem == 8) {
-        if (tile == 128)
-            pass_residency<double, 128>(per_sm, sms);
-        else if (tile == 512)
-            pass_residency<double, 512>(per_sm, sms);
-        else
-            pass_residency<double, 256>(per_sm, sms);
-    } else {
-        if (tile == 128)
-            pass_residency<float, 128>(per_sm, sms);
-        else if (tile == 512)
-            pass_residency<float, 512>(per_sm, sms);
-        else
-            pass_residency<float, 256>(per_sm, sms);
-    }
+    if (tile == 128)
+        pass_residency<R, 128, 0>(per_sm, sms);
+    else if (tile == 512)
+        pass_residency<R, 512, 0>(per_sm, sms);
+    else if (variant == 1)
+        pass_residency<R, 256, 1>(per_sm, sms);
+    else
+        pass_residency<R, 256, 0>(per_sm, sms);
+}
+
+int pass_ctas_per_sm_max(size_t elem, int tile, int variant)
+{
+    int per_sm = 1, sms = 152;
+    if (elem == 8)
+        pass_residency_of<double>(tile, variant, per_sm, sms);
+    else
+        pass_residency_of<float>(tile, variant, per_sm, sms);
     return per_sm;
 }
 
@@ -497,30 +508,32 @@ static void launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem, cud
 
 // The persistent pass grid: at most ctas_per_sm CTAs per SM (0 or more than fit: as many
 // as fit), and never more CTAs than the launch has tiles for.
-template <typename R, int TILE>
+template <typename R, int TILE, int VAR>
 static void launch_pass_t(PassArgs pa, int64_t ntiles, int ctas_per_sm, cudaStream_t s)
 {
     pa.ntiles = ntiles;
     int per_sm, sms;
-    pass_residency<R, TILE>(per_sm, sms);
+    pass_residency<R, TILE, VAR>(per_sm, sms);
     if (ctas_per_sm > 0)
         per_sm = std::min(per_sm, ctas_per_sm);
     const int64_t grid =
         std::min((ntiles + kPassWarps - 1) / kPassWarps, (int64_t)per_sm * sms);
-    launch_pdl(k_pass<R, TILE / 32, kPassWarps>, (unsigned)grid, 32 * kPassWarps,
+    launch_pdl(pass_kernel<R, TILE, VAR>(), (unsigned)grid, 32 * kPassWarps,
                pass_smem<R, TILE>(), s, pa);
 }
 
 template <typename R>
-static void launch_pass_tiles(int tile, int ctas_per_sm, const PassArgs &pa, int64_t ntiles,
-                              cudaStream_t s)
+static void launch_pass_tiles(int tile, int variant, int ctas_per_sm, const PassArgs &pa,
+                              int64_t ntiles, cudaStream_t s)
 {
     if (tile == 128)
-        launch_pass_t<R, 128>(pa, ntiles, ctas_per_sm, s);
+        launch_pass_t<R, 128, 0>(pa, ntiles, ctas_per_sm, s);
     else if (tile == 512)
-        launch_pass_t<R, 512>(pa, ntiles, ctas_per_sm, s);
+        launch_pass_t<R, 512, 0>(pa, ntiles, ctas_per_sm, s);
+    else if (variant == 1)
+        launch_pass_t<R, 256, 1>(pa, ntiles, ctas_per_sm, s);
     else
-        launch_pass_t<R, 256>(pa, ntiles, ctas_per_sm, s);
+        launch_pass_t<R, 256, 0>(pa, ntiles, ctas_per_sm, s);
 }
 
 static size_t reduce_smem(const ReduceArgs &ra)
@@ -593,11 +606,13 @@ bool validate(const semd_params &p, std::string &err)
 // Tile of the pass kernel for a plan: 1024 samples (128 threads).
 // The plan's pass-kernel shape: the tuning table's entry for the plan's key when there is
 // one, else 256-sample tiles and as many CTAs per SM as fit.
-void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas)
+void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas,
+                       int &variant)
 {
     tile = kTile;
     ctas = 0;
-    tune_lookup(p, L, ninst, tile, ctas);
+    variant = 0;
+    tune_lookup(p, L, ninst, tile, ctas, variant);
 }
 
 int max_iterations(const semd_params &p)
@@ -788,7 +803,7 @@ static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, bool need_z
     pa.ntiles = ntiles;
     pa.need_sd = need_sd ? 1 : 0;
     pa.need_zc = need_zc ? 1 : 0;
-    launch_pass_tiles<R>(ws.tile, ws.pass_ctas, pa, ntiles, s);
+    launch_pass_tiles<R>(ws.tile, ws.pass_variant, ws.pass_ctas, pa, ntiles, s);
 }
 
 static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
@@ -958,7 +973,8 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile, ws.pass_ctas};
+        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile, ws.pass_ctas,
+                           ws.pass_variant};
         if (!pl.graph_exec || !(pl.graph_key == key)) {
             if (pl.graph_exec) {
                 cudaGraphExecDestroy(pl.graph_exec);
@@ -1131,7 +1147,7 @@ semd_status ceemdan_impl(semd_plan_s &pl, const void *d_x, const void *d_noise, 
     pl.prof.reset();
     if (use_graph) {
         const GraphKey key{trials, ntiles, ws.h_inst[0].ntiles, ws.max_ntiles, ws.tile,
-                           ws.pass_ctas};
+                           ws.pass_ctas, ws.pass_variant};
         if (!pl.ce_graph_exec || !(pl.ce_graph_key == key)) {
             if (pl.ce_graph_exec) {
                 cudaGraphExecDestroy(pl.ce_graph_exec);
@@ -1279,9 +1295,9 @@ cudaError_t setup_kernel_attrs(size_t elem)
 void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
 {
     if (elem == 8)
-        launch_pass_tiles<double>(tile, 0, pa, ntiles, s);
+        launch_pass_tiles<double>(tile, 0, 0, pa, ntiles, s);
     else
-        launch_pass_tiles<float>(tile, 0, pa, ntiles, s);
+        launch_pass_tiles<float>(tile, 0, 0, pa, ntiles, s);
 }
 
 void launch_reduce_any(size_t elem, const ReduceArgs &ra, int nblocks, cudaStream_t s)
@@ -1419,8 +1435,8 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     }
     const int64_t L = serial_length(M, N, D);
     const int ninst = eemd ? params->ensemble_trials : max_batch;
-    int tile, ctas;
-    choose_pass_shape(*params, L, ninst, tile, ctas);
+    int tile, ctas, variant;
+    choose_pass_shape(*params, L, ninst, tile, ctas, variant);
     // capacity for the smallest tile, so that the tile can be changed per plan
     const int64_t tiles_per = (L + kMinTile - 1) / kMinTile;
     const int64_t samples = (int64_t)ninst * ((L + 31) & ~(int64_t)31);
@@ -1438,6 +1454,7 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
     pl->L = L;
     pl->ws.tile = tile;
     pl->ws.pass_ctas = ctas;
+    pl->ws.pass_variant = variant;
     semd_status st = pl->ws.allocate(samples, ninst, tiles, rent, max_iterations(*params), elem,
                                       eemd_elems, mem_budget, err);
     if (st == SEMD_OK) {
@@ -1627,8 +1644,8 @@ semd_status serial_emd_plan_set_tile(semd_plan_t plan, int tile)
     if (!plan)
         return SEMD_EINVAL;
     if (tile == 0) {
-        int ctas;
-        choose_pass_shape(plan->p, plan->L, plan->ws.cap_inst, tile, ctas);
+        int ctas, variant;
+        choose_pass_shape(plan->p, plan->L, plan->ws.cap_inst, tile, ctas, variant);
     }
     if (tile != 128 && tile != 256 && tile != 512) {
         plan->err = "tile must be 0, 128, 256 or 512";
@@ -1653,6 +1670,20 @@ semd_status serial_emd_plan_set_pass_ctas(semd_plan_t plan, int ctas_per_sm)
 }
 
 int serial_emd_plan_get_pass_ctas(semd_plan_t plan) { return plan ? plan->ws.pass_ctas : 0; }
+
+semd_status serial_emd_plan_set_pass_variant(semd_plan_t plan, int variant)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (variant != 0 && variant != 1) {
+        plan->err = "variant must be 0 or 1";
+        return SEMD_EINVAL;
+    }
+    plan->ws.pass_variant = variant;
+    return SEMD_OK;
+}
+
+int serial_emd_plan_get_pass_variant(semd_plan_t plan) { return plan ? plan->ws.pass_variant : 0; }
 
 semd_status serial_emd_plan_set_options(semd_plan_t plan, int use_graphs, int profile)
 {

@@ -24,7 +24,8 @@ struct Workspace {
     void *base = nullptr;
     size_t bytes = 0;
     int tile = kTile;
-    int pass_ctas = 0; // CTAs per SM of the persistent pass grid (0: as many as fit)
+    int pass_ctas = 0;    // CTAs per SM of the persistent pass grid (0: as many as fit)
+    int pass_variant = 0; // register budget of the pass kernel, where it has two
     int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0, max_ntiles = 0; // cap_rentries: doubles of interface scratch
     int cap_inst = 0, cap_iters = 0;
     size_t elem_size = 0;
@@ -88,11 +89,15 @@ void launch_finalize_any(size_t elem, const Inst *d_inst, const State *d_state,
 ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_state,
                             const int32_t *inst_list, int32_t *active, size_t elem,
                             int64_t max_ntiles);
-void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas);
-// CTAs of the pass kernel that fit on one SM (working-precision size elem, tile).
-int pass_ctas_per_sm_max(size_t elem, int tile);
+void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas,
+                       int &variant);
+// CTAs of the pass kernel that fit on one SM (working-precision size elem, tile, variant).
+int pass_ctas_per_sm_max(size_t elem, int tile, int variant);
+// Pass kernels with two register budgets (variants 0 and 1): FP32 with 256-sample tiles.
+inline bool pass_has_variants(size_t elem, int tile) { return elem == 4 && tile == 256; }
 // The tuning table (semd_autotune.cu): the entry for this plan key, if any.
-bool tune_lookup(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas);
+bool tune_lookup(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas,
+                 int &variant);
 template <typename R>
 semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *insts,
                            const void *d_noise, int *n_imfs, cudaStream_t s,
@@ -157,10 +162,12 @@ struct GraphKey {
     int64_t max_ntiles = 0;
     int tile = 0;
     int pass_ctas = 0;
+    int pass_variant = 0;
     bool operator==(const GraphKey &o) const
     {
         return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0 &&
-               max_ntiles == o.max_ntiles && tile == o.tile && pass_ctas == o.pass_ctas;
+               max_ntiles == o.max_ntiles && tile == o.tile && pass_ctas == o.pass_ctas &&
+               pass_variant == o.pass_variant;
     }
 };
 

@@ -116,6 +116,14 @@ class Plan:
     def pass_ctas(self, value: int):
         capi.serial_emd_plan_set_pass_ctas(self.handle, value)
 
+    @property
+    def pass_variant(self) -> int:
+        return capi.serial_emd_plan_get_pass_variant(self.handle)
+
+    @pass_variant.setter
+    def pass_variant(self, value: int):
+        capi.serial_emd_plan_set_pass_variant(self.handle, value)
+
     def autotune(self, xs, noise: torch.Tensor | None = None, outs=None, repeats: int = 3,
                  stream=None):
         """Picks the fastest pass-kernel shape for these inputs (one tensor or a list, as

@@ -631,14 +631,15 @@ def test_autotune_keeps_results_and_seeds_new_plans(tmp_path):
     r = plan.autotune(x, repeats=2)
     assert r.tile in (128, 256, 512) and r.ctas_per_sm >= 0 and r.candidates >= 3
     assert 0 < r.ms <= r.ms_default
-    assert (plan.tile, plan.pass_ctas) == (r.tile, r.ctas_per_sm)
+    assert (plan.tile, plan.pass_ctas, plan.pass_variant) == (r.tile, r.ctas_per_sm, r.variant)
     imfs, res, n = plan.decompose(x)
     assert n == rn
     floor = 1e-6 * np.linalg.norm(X)
     for k in range(6):
         assert _rel(imfs[k].cpu().numpy(), ref[k], floor) <= 1e-12
     plan2 = Plan(p)
-    assert (plan2.tile, plan2.pass_ctas) == (r.tile, r.ctas_per_sm)
+    assert (plan2.tile, plan2.pass_ctas, plan2.pass_variant) == \
+        (r.tile, r.ctas_per_sm, r.variant)
     out = tmp_path / "tune.json"
     capi.serial_emd_tune_save(str(out))
     assert f'"tile": {r.tile}' in out.read_text()
@@ -664,3 +665,21 @@ def test_autotune_ensemble_plan():
         assert _rel(a[k].double().cpu().numpy(), b[k].double().cpu().numpy(), floor) <= 1e-4
     plan.close()
     capi.serial_emd_tune_clear()
+
+
+def test_pass_kernel_register_variants_agree_bit_for_bit():
+    """The two register budgets of the FP32 256-sample pass kernel compile the same
+    arithmetic: identical IMFs, residue and counts."""
+    X = synth.workload_texture_256().astype(np.float32)
+    plan = Plan(make_params(256, 256, transition_len=0, max_imfs=6))
+    x = torch.from_numpy(X).cuda()
+    out = []
+    for v in (0, 1):
+        plan.pass_variant = v
+        for c in (0, 2):
+            plan.pass_ctas = c
+            imfs, res, n = plan.decompose(x)
+            out.append((imfs.cpu(), res.cpu(), n))
+    plan.close()
+    for imfs, res, n in out[1:]:
+        assert n == out[0][2] and torch.equal(imfs, out[0][0]) and torch.equal(res, out[0][1])
