@@ -285,10 +285,12 @@ semd_status serial_emd_plan_set_pass_ctas(semd_plan_t plan, int ctas_per_sm);
 int serial_emd_plan_get_pass_ctas(semd_plan_t plan);
 
 /*
- * Register budget of the pass kernel where it is compiled in two (FP32, 256-sample tiles):
- * variant 0 (default) keeps four CTAs per SM resident at the cost of a few spilled bytes,
- * variant 1 keeps three with none (better for launches too small to fill the GPU). Other
- * kernels ignore it. Changes speed only. Errors: EINVAL (not 0 or 1).
+ * Variant of the pass kernel. 0 (default, throughput): each warp copies its next tile's
+ * signal and interface values into shared memory (asynchronous copies) while the current
+ * tile computes; for FP32 with 256-sample tiles it is compiled for four resident CTAs per
+ * SM. 1 (latency): no staging, a smaller kernel, for launches with about one tile per
+ * warp; for FP32 with 256-sample tiles compiled for three CTAs per SM without register
+ * spills. Changes speed only. Errors: EINVAL (not 0 or 1).
  */
 semd_status serial_emd_plan_set_pass_variant(semd_plan_t plan, int variant);
 int serial_emd_plan_get_pass_variant(semd_plan_t plan);

@@ -2,10 +2,10 @@
 //
 // The pass kernel has three free launch parameters: the tile (128, 256 or 512 samples per
 // warp, which moves work between the per-tile eliminations and the interface system),
-// for the FP32 kernel of 256-sample tiles its register budget (variant 0 keeps four CTAs
-// per SM resident, variant 1 three with no spilled registers: latency-bound launches
-// prefer the latter), and how many CTAs per SM its persistent grid keeps resident (fewer
-// CTAs leave each one a longer contiguous range of tiles and more cache per CTA). None
+// its variant (0 stages each warp's next tile in shared memory, 1 is a smaller kernel
+// without staging that latency-bound launches prefer), and how many CTAs per SM its
+// persistent grid keeps resident (fewer CTAs leave each one a longer contiguous range of
+// tiles and more cache per CTA). None
 // changes what is computed beyond rounding. serial_emd_plan_autotune times the plan's own
 // decomposition of a caller's input for every candidate shape, keeps the fastest on the
 // plan and records it in a process-wide table keyed by what decides the best shape:

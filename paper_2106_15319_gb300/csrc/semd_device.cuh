@@ -259,6 +259,15 @@ struct WarpPool {
     KnotY<R> ky[KP];
 };
 
+// A warp's next tile, copied in while the current one computes (staging kernels only,
+// placed after the warps' pools): the signal (zero past the tile's count), the halo
+// samples before and after it, and both envelopes' interface values.
+template <typename R, int TW>
+struct StageBuf {
+    R stage[TW + 16 / sizeof(R)];
+    TileSolve sts[2];
+};
+
 // The interface solution of one tile and envelope in the working precision (FP32 pass
 // kernels read the single-precision values, so they issue no FP64 conversions).
 template <typename R>
@@ -622,6 +631,29 @@ __device__ __forceinline__ TileRec<R> load_rec(const TileRec<R> *p)
     return u.r;
 }
 
+// Asynchronous global -> shared copies (no registers held while in flight): 16 bytes of
+// which the first src_bytes are read and the rest zero-filled (both addresses 16-byte
+// aligned; src is read only when src_bytes > 0), or one 4- or 8-byte element.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Asks L2 to fetch [p, p + bytes) ahead of use (p 16-byte aligned, bytes a multiple of
 // 16, the range inside one allocation). No completion is awaited.
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
@@ -629,11 +661,58 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Starts the copy of tile gt's inputs into the warp's stage buffer (all 32 lanes): the
+// signal (SPL samples per lane, 16-byte chunks, zero past the tile's count), the halo
+// samples next to it, and for a sifting mode both envelopes' interface values. Tiles
+// whose mode reads no signal (INIT, DONE) are not staged. Returns whether it copied.
+template <typename R, int SPL>
+__device__ __forceinline__ bool stage_tile(const PassArgs &pa, StageBuf<R, 32 * SPL> &P,
+                                           int64_t gt)
+{
+    constexpr int TW = 32 * SPL;
+    constexpr int PER = 16 / (int)sizeof(R); // samples per 16-byte chunk
+    const int lane = threadIdx.x & 31;
+    const int ii = pa.tile_inst[gt];
+    const State *stp = pa.state + ii;
+    const int mode = stp->mode;
+    if (mode == MODE_DONE || mode == MODE_INIT)
+        return false;
+    const Inst &in = pa.inst[ii];
+    const int L = (int)in.L;
+    const int lt = (int)(gt - in.tile0);
+    const int ts = lt * TW, cnt = min(TW, L - ts);
+    const R *hsrc = (const R *)in.h[stp->hpar] + ts;
+    const int k0 = lane * SPL;
+#pragma unroll
+    for (int c = 0; c < SPL / PER; ++c) {
+        const int k = k0 + c * PER;
+        const int valid = max(0, min(PER, cnt - k));
+        cp_async16(&P.stage[k], valid > 0 ? hsrc + k : hsrc, valid * (int)sizeof(R));
+    }
+    if (lane == 0 && ts > 0)
+        cp_async_elem(&P.stage[TW], hsrc - 1);
+    if (lane == 31 && ts + TW < L)
+        cp_async_elem(&P.stage[TW + 1], hsrc + TW);
+    if ((mode == MODE_SIFT || mode == MODE_SIFT_COMMIT) && lane < 14) {
+        constexpr int CH = (int)sizeof(TileSolve) / 16; // 7 chunks per envelope
+        const int e = lane / CH, q = lane - e * CH;
+        const char *src = reinterpret_cast<const char *>(in.tsol + (int64_t)e * in.ntiles + lt);
+        cp_async16(reinterpret_cast<char *>(&P.sts[e]) + 16 * q, src + 16 * q, 16);
+    }
+    cp_async_commit();
+    return true;
+}
+
 // ---------------------------------------------------------------------------------
 // One sifting pass over one warp tile (the body of k_pass).
-template <typename R, int SPL>
-__device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * SPL> &P, int64_t gt,
-                                          bool first, bool prefetch_next)
+// STAGE: the next tile's inputs are copied into the stage buffer while this one computes
+// (else only prefetched into L2: a smaller kernel, for launches with one tile per warp).
+// `staged`: this tile's inputs are in the stage buffer (copied by the previous tile);
+// returns whether the next tile's were started.
+template <typename R, int SPL, bool STAGE>
+__device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * SPL> &P,
+                                          StageBuf<R, 32 * SPL> &B, int64_t gt, bool first,
+                                          bool prefetch_next, bool staged)
 {
     constexpr int TW = 32 * SPL;
     const int lane = threadIdx.x & 31;
@@ -641,7 +720,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     State *stp = pa.state + ii;
     const int mode = stp->mode;
     if (mode == MODE_DONE)
-        return;
+        return false;
     const int hpar = stp->hpar, rpar = stp->rpar, imfc = stp->imf_count;
     const Inst &in = pa.inst[ii];
     const int L = (int)in.L;
@@ -668,34 +747,53 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
 
     R v[SPL], hn[SPL];
     R hcl = R(0), hcr = R(0); // current signal at the halo samples -1 and TW
-    if (mode != MODE_INIT) {
-        loadn<R, SPL>(hsrc, k0, cnt, v);
+    // the tile's interface values (written by the interface solve just before)
+    SolveVals<R> sv{};
+    int2 tpn = make_int2(0, 0);
+    if (STAGE && staged) {
+        // copied in while the previous tile computed
+        cp_async_wait_all();
+        __syncwarp();
+        vload<SPL>(B.stage + k0, v);
         if (lane == 0 && hasL)
-            hcl = hsrc[-1];
+            hcl = B.stage[TW];
         if (lane == 31 && hasR)
-            hcr = hsrc[TW];
+            hcr = B.stage[TW + 1];
+        if (sift) {
+            sv = solve_vals(B.sts[eh], R(0));
+            tpn = *reinterpret_cast<const int2 *>(&B.sts[eh].tp);
+        }
+        __syncwarp(); // the stage is refilled below
+    } else {
+        if (mode != MODE_INIT) {
+            loadn<R, SPL>(hsrc, k0, cnt, v);
+            if (lane == 0 && hasL)
+                hcl = hsrc[-1];
+            if (lane == 31 && hasR)
+                hcr = hsrc[TW];
+        }
+        if (sift) {
+            const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
+            sv = solve_vals(so, R(0));
+            tpn = *reinterpret_cast<const int2 *>(&so.tp);
+        }
     }
+    // the warp's next tile: its signal and interface values into the stage buffer (or
+    // its signal into L2), its residue (commit and INIT passes) into L2, while this one
+    // computes
+    bool nstaged = false;
+    if constexpr (STAGE)
+        nstaged = prefetch_next && stage_tile<R, SPL>(pa, B, gt + 1);
     // the residue of a commit (or INIT) pass into L2 now (a warp's first tile; the others
     // were prefetched by its previous tile), into registers when the sift is done
     if (first && use_r && lane == 0)
         prefetch_l2(rsrc, (uint32_t)(((cnt * 8) + 15) & ~15));
-    // the warp's next tile (the same instance and mode) into L2 while this one computes
     if (prefetch_next && lane == 0 && lt + 1 < in.ntiles) {
         const int ncnt = min(TW, L - ts - TW);
-        if (mode != MODE_INIT)
+        if (!STAGE && mode != MODE_INIT)
             prefetch_l2(hsrc + TW, (uint32_t)(((ncnt * (int)sizeof(R)) + 15) & ~15));
         if (use_r)
             prefetch_l2(rsrc + TW, (uint32_t)(((ncnt * 8) + 15) & ~15));
-    }
-
-    // the tile's interface values (written by the interface solve just before), fetched
-    // with the signal so that their latency overlaps the extrema search
-    SolveVals<R> sv{};
-    int2 tpn = make_int2(0, 0);
-    if (sift) {
-        const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
-        sv = solve_vals(so, R(0));
-        tpn = *reinterpret_cast<const int2 *>(&so.tp);
     }
 
     R pn = R(0), pd = R(0);
@@ -888,6 +986,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     }
     if (sift && pa.need_zc && lane == 0)
         in.taux[lt].nzc = zc;
+    return nstaged;
 }
 
 // One sifting pass over all tiles of every running instance. Persistent grid: warp w
@@ -895,8 +994,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
 // rounded up), so its next tile is usually the next tile of the same instance, which
 // it prefetches into L2. Warps are independent (no block barrier).
 // MINB is the register budget's target: the compiler keeps to the registers that let MINB
-// CTAs reside on an SM (1: no limit).
-template <typename R, int SPL, int NWARP, int MINB>
+// CTAs reside on an SM (1: no limit). STAGE: see pass_tile.
+template <typename R, int SPL, int NWARP, int MINB, bool STAGE>
 __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
 {
     constexpr int TW = 32 * SPL;
@@ -905,12 +1004,16 @@ __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
     pdl_wait();
     const int warp = threadIdx.x >> 5;
     WarpPool<R, TW> &P = reinterpret_cast<WarpPool<R, TW> *>(smraw)[warp];
+    // staging kernels: the stage buffers follow the NWARP pools (not touched otherwise)
+    StageBuf<R, TW> &B =
+        reinterpret_cast<StageBuf<R, TW> *>(smraw + NWARP * sizeof(WarpPool<R, TW>))[warp];
     const int64_t nw = (int64_t)gridDim.x * NWARP;
     const int64_t wid = (int64_t)blockIdx.x * NWARP + warp;
     const int64_t C = (pa.ntiles + nw - 1) / nw;
     const int64_t g0 = wid * C, g1 = min(g0 + C, pa.ntiles);
+    bool staged = false;
     for (int64_t gt = g0; gt < g1; ++gt)
-        pass_tile<R, SPL>(pa, P, gt, gt == g0, gt + 1 < g1);
+        staged = pass_tile<R, SPL, STAGE>(pa, P, B, gt, gt == g0, gt + 1 < g1, staged);
 }
 
 

@@ -402,23 +402,31 @@ __global__ void k_to_double(const R *h, int64_t L, double *r)
 // ------------------------------------------------------------------ plan helpers
 
 // The pass kernel for each supported tile: 128 / 256 / 512 samples per warp (4, 8, 16 per
-// lane), kPassWarps warps per CTA. The FP32 kernel of 256-sample tiles comes in two
-// register budgets (variant 0: four resident CTAs per SM, a few spilled bytes; variant 1:
-// three, no spills); the other kernels have one, and take either variant number.
+// lane), kPassWarps warps per CTA, in two variants. Variant 0 (throughput) stages each
+// warp's next tile in shared memory while the current one computes; for FP32 with
+// 256-sample tiles it is compiled for four resident CTAs per SM (a few spilled bytes).
+// Variant 1 (latency: launches with about one tile per warp) only prefetches into L2, a
+// smaller kernel; FP32 256-sample tiles compile it for three CTAs per SM (no spills).
 template <typename R, int TILE, int VAR>
 static constexpr int pass_minb() { return (sizeof(R) == 4 && TILE == 256) ? (VAR == 0 ? 4 : 3) : 1; }
 template <typename R, int TILE, int VAR>
-static constexpr auto pass_kernel() { return k_pass<R, TILE / 32, kPassWarps, pass_minb<R, TILE, VAR>()>; }
+static constexpr auto pass_kernel()
+{
+    return k_pass<R, TILE / 32, kPassWarps, pass_minb<R, TILE, VAR>(), VAR == 0>;
+}
 
-template <typename R, int TILE>
-static constexpr size_t pass_smem() { return kPassWarps * sizeof(WarpPool<R, TILE>); }
+template <typename R, int TILE, int VAR>
+static constexpr size_t pass_smem()
+{
+    return kPassWarps * (sizeof(WarpPool<R, TILE>) + (VAR == 0 ? sizeof(StageBuf<R, TILE>) : 0));
+}
 
 template <typename R, int TILE, int VAR>
 static cudaError_t pass_attr_one()
 {
     return cudaFuncSetAttribute(pass_kernel<R, TILE, VAR>(),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pass_smem<R, TILE>());
+                                (int)pass_smem<R, TILE, VAR>());
 }
 
 template <typename R>
@@ -426,11 +434,15 @@ static cudaError_t set_smem_attr()
 {
     cudaError_t e = pass_attr_one<R, 128, 0>();
     if (e == cudaSuccess)
+        e = pass_attr_one<R, 128, 1>();
+    if (e == cudaSuccess)
         e = pass_attr_one<R, 256, 0>();
     if (e == cudaSuccess)
         e = pass_attr_one<R, 256, 1>();
     if (e == cudaSuccess)
         e = pass_attr_one<R, 512, 0>();
+    if (e == cudaSuccess)
+        e = pass_attr_one<R, 512, 1>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_reduce<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kReduceSmemMax);
@@ -453,7 +465,7 @@ static void pass_residency(int &per_sm, int &sms)
         int a = 0, b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, pass_kernel<R, TILE, VAR>(),
                                                           32 * kPassWarps,
-                                                          pass_smem<R, TILE>()) != cudaSuccess ||
+                                                          pass_smem<R, TILE, VAR>()) != cudaSuccess ||
             cudaDeviceGetAttribute(&b, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return;
         cache[dev][0] = std::max(a, 1);
@@ -467,13 +479,11 @@ template <typename R>
 static void pass_residency_of(int tile, int variant, int &per_sm, int &sms)
 {
     if (tile == 128)
-        pass_residency<R, 128, 0>(per_sm, sms);
+        variant == 1 ? pass_residency<R, 128, 1>(per_sm, sms) : pass_residency<R, 128, 0>(per_sm, sms);
     else if (tile == 512)
-        pass_residency<R, 512, 0>(per_sm, sms);
-    else if (variant == 1)
-        pass_residency<R, 256, 1>(per_sm, sms);
+        variant == 1 ? pass_residency<R, 512, 1>(per_sm, sms) : pass_residency<R, 512, 0>(per_sm, sms);
     else
-        pass_residency<R, 256, 0>(per_sm, sms);
+        variant == 1 ? pass_residency<R, 256, 1>(per_sm, sms) : pass_residency<R, 256, 0>(per_sm, sms);
 }
 
 int pass_ctas_per_sm_max(size_t elem, int tile, int variant)
@@ -519,7 +529,7 @@ static void launch_pass_t(PassArgs pa, int64_t ntiles, int ctas_per_sm, cudaStre
     const int64_t grid =
         std::min((ntiles + kPassWarps - 1) / kPassWarps, (int64_t)per_sm * sms);
     launch_pdl(pass_kernel<R, TILE, VAR>(), (unsigned)grid, 32 * kPassWarps,
-               pass_smem<R, TILE>(), s, pa);
+               pass_smem<R, TILE, VAR>(), s, pa);
 }
 
 template <typename R>
@@ -527,13 +537,14 @@ static void launch_pass_tiles(int tile, int variant, int ctas_per_sm, const Pass
                               int64_t ntiles, cudaStream_t s)
 {
     if (tile == 128)
-        launch_pass_t<R, 128, 0>(pa, ntiles, ctas_per_sm, s);
+        variant == 1 ? launch_pass_t<R, 128, 1>(pa, ntiles, ctas_per_sm, s)
+                     : launch_pass_t<R, 128, 0>(pa, ntiles, ctas_per_sm, s);
     else if (tile == 512)
-        launch_pass_t<R, 512, 0>(pa, ntiles, ctas_per_sm, s);
-    else if (variant == 1)
-        launch_pass_t<R, 256, 1>(pa, ntiles, ctas_per_sm, s);
+        variant == 1 ? launch_pass_t<R, 512, 1>(pa, ntiles, ctas_per_sm, s)
+                     : launch_pass_t<R, 512, 0>(pa, ntiles, ctas_per_sm, s);
     else
-        launch_pass_t<R, 256, 0>(pa, ntiles, ctas_per_sm, s);
+        variant == 1 ? launch_pass_t<R, 256, 1>(pa, ntiles, ctas_per_sm, s)
+                     : launch_pass_t<R, 256, 0>(pa, ntiles, ctas_per_sm, s);
 }
 
 static size_t reduce_smem(const ReduceArgs &ra)

@@ -93,8 +93,9 @@ void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, in
                        int &variant);
 // CTAs of the pass kernel that fit on one SM (working-precision size elem, tile, variant).
 int pass_ctas_per_sm_max(size_t elem, int tile, int variant);
-// Pass kernels with two register budgets (variants 0 and 1): FP32 with 256-sample tiles.
-inline bool pass_has_variants(size_t elem, int tile) { return elem == 4 && tile == 256; }
+// Every pass kernel comes in two variants: 0 stages the next tile in shared memory, 1 does
+// not (smaller; for FP32 256-sample tiles also a larger register budget).
+inline bool pass_has_variants(size_t, int) { return true; }
 // The tuning table (semd_autotune.cu): the entry for this plan key, if any.
 bool tune_lookup(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas,
                  int &variant);
