@@ -487,6 +487,7 @@ def arm_ours(args):
         if not args.no_batched:
             line["ceemdan"] = ceemdan_legs(args, device, flush, world)
             line["d_sweep"] = d_sweep(args, device, world)
+            line["paper_context"] = paper_context(line)
         if not args.no_serving:
             line["serving"] = serving(args, device)
         if not args.no_cpu_baseline:
@@ -693,11 +694,12 @@ def ceemdan_legs(args, device, flush, world):
     from paper_2106_15319_gb300 import capi, synth
     from paper_2106_15319_gb300.serial_emd import Plan, make_params
     trials = 100
-    cases = [("mask6x1000_D50", synth.paper_mask_series(), 50, 1154.97),
-             ("texture101_D20", synth.grating_image(101, 2106), 20, 20580.0)]
+    # (name, input, D, the paper's serial-CEEMDAN and serial-EEMD CPU times in ms)
+    cases = [("mask6x1000_D50", synth.paper_mask_series(), 50, 1154.97, 397.92),
+             ("texture101_D20", synth.grating_image(101, 2106), 20, 20580.0, 6410.0)]
     out = {}
     steps = max(1, min(args.steps, 5))
-    for name, X0, D, paper_ms in cases:
+    for name, X0, D, paper_ms, paper_eemd_ms in cases:
         rows, cols = X0.shape
         N, M = rows, cols
         L = M * N + D * N - D
@@ -712,33 +714,71 @@ def ceemdan_legs(args, device, flush, world):
             stream = torch.cuda.Stream(device)
             if not args.no_tune:  # setup: the pass shape of the ensemble's sifting
                 plan.autotune(x, wt, outs=[(modes, res)], repeats=2, stream=stream)
-            ms = []
-            with torch.cuda.stream(stream):
-                for _ in range(min(args.warmup, 3)):
-                    plan.ceemdan(x, wt, modes, res, stream=stream, wait=False)
-                stream.synchronize()
-                for _ in range(steps):
-                    _flush_l2(flush)
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    plan.ceemdan(x, wt, modes, res, stream=stream, wait=False)
-                    b.record(stream)
+            def timed(call):
+                ms = []
+                with torch.cuda.stream(stream):
+                    for _ in range(min(args.warmup, 3)):
+                        call()
                     stream.synchronize()
-                    ms.append(a.elapsed_time(b))
+                    for _ in range(steps):
+                        _flush_l2(flush)
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        call()
+                        b.record(stream)
+                        stream.synchronize()
+                        ms.append(a.elapsed_time(b))
+                return max_over_ranks(statistics.mean(ms), world)
+
+            # serial-EEMD of the same input and noise (the paper times both)
+            eemd_ms = timed(lambda: plan.decompose(x, wt, modes, res, stream=stream, wait=False))
+            m = timed(lambda: plan.ceemdan(x, wt, modes, res, stream=stream, wait=False))
             st = plan.stats()
             n = plan.counts(1)[0][0]
             shape = {"tile": plan.tile, "ctas_per_sm": plan.pass_ctas,
                      "variant": plan.pass_variant}
             plan.close()
-            m = max_over_ranks(statistics.mean(ms), world)
             key = f"{name}_{'fp32' if prec == capi.FP32_MIXED else 'fp64'}"
             out[key] = {"ms_per_step": m, "value": world * st.sample_sifts / (m * 1e-3),
                         "unit": UNIT, "modes": int(n), "L": L, "trials": trials,
                         "launches_per_step": int(st.kernel_launches),
                         "cuda_graph": bool(st.used_graph),
                         "pass_shape": shape,
-                        "paper_cpu_ms_context": paper_ms}
+                        "paper_cpu_ms_context": paper_ms,
+                        "eemd_ms_per_step": eemd_ms,
+                        "paper_eemd_cpu_ms_context": paper_eemd_ms}
+    return out
+
+
+def paper_context(line):
+    """The paper's own timings (Sec. 4; one i7-6700HQ laptop CPU, language and precision
+    not stated) beside this run's GPU times of the same method on stand-in inputs. Context,
+    not a target."""
+    out = {"hardware": "paper: Intel i7-6700HQ laptop CPU (Sec. 4); here: one GB300",
+           "rows": []}
+    ds = {r["D"]: r for r in line.get("d_sweep", {}).get("rows", [])}
+    ce = line.get("ceemdan", {})
+    if 50 in ds:
+        out["rows"].append({"what": "serial-EMD, 6-variate tone set, D=50", "paper_ms": 10.96,
+                            "ours_ms_fp32": ds[50]["emd_fixed10_ms"]})
+    if "mask6x1000_D50_fp32" in ce:
+        c32, c64 = ce["mask6x1000_D50_fp32"], ce.get("mask6x1000_D50_fp64", {})
+        out["rows"].append({"what": "serial-EEMD, 6-variate tone set, D=50, 100 realizations",
+                            "paper_ms": 397.92, "ours_ms_fp32": c32["eemd_ms_per_step"],
+                            "ours_ms_fp64": c64.get("eemd_ms_per_step")})
+        out["rows"].append({"what": "serial-CEEMDAN, 6-variate tone set, D=50, "
+                                    "100 realizations", "paper_ms": 1154.97,
+                            "ours_ms_fp32": c32["ms_per_step"],
+                            "ours_ms_fp64": c64.get("ms_per_step")})
+    if "texture101_D20_fp32" in ce:
+        c32, c64 = ce["texture101_D20_fp32"], ce.get("texture101_D20_fp64", {})
+        out["rows"].append({"what": "serial-EEMD, 101x101 texture (ATI stand-in), D=20",
+                            "paper_ms": 6410.0, "ours_ms_fp32": c32["eemd_ms_per_step"],
+                            "ours_ms_fp64": c64.get("eemd_ms_per_step")})
+        out["rows"].append({"what": "serial-CEEMDAN, 101x101 texture (ATI stand-in), D=20",
+                            "paper_ms": 20580.0, "ours_ms_fp32": c32["ms_per_step"],
+                            "ours_ms_fp64": c64.get("ms_per_step")})
     return out
 
 
