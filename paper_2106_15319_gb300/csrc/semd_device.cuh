@@ -666,22 +666,14 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 // samples next to it, and for a sifting mode both envelopes' interface values. Tiles
 // whose mode reads no signal (INIT, DONE) are not staged. Returns whether it copied.
 template <typename R, int SPL>
-__device__ __forceinline__ bool stage_tile(const PassArgs &pa, StageBuf<R, 32 * SPL> &P,
-                                           int64_t gt)
+__device__ __forceinline__ void stage_issue(StageBuf<R, 32 * SPL> &P, int mode, const R *hsrc,
+                                            int ts, int L, const TileSolve *tsol, int ntiles,
+                                            int lt)
 {
     constexpr int TW = 32 * SPL;
     constexpr int PER = 16 / (int)sizeof(R); // samples per 16-byte chunk
     const int lane = threadIdx.x & 31;
-    const int ii = pa.tile_inst[gt];
-    const State *stp = pa.state + ii;
-    const int mode = stp->mode;
-    if (mode == MODE_DONE || mode == MODE_INIT)
-        return false;
-    const Inst &in = pa.inst[ii];
-    const int L = (int)in.L;
-    const int lt = (int)(gt - in.tile0);
-    const int ts = lt * TW, cnt = min(TW, L - ts);
-    const R *hsrc = (const R *)in.h[stp->hpar] + ts;
+    const int cnt = min(TW, L - ts);
     const int k0 = lane * SPL;
 #pragma unroll
     for (int c = 0; c < SPL / PER; ++c) {
@@ -696,10 +688,29 @@ __device__ __forceinline__ bool stage_tile(const PassArgs &pa, StageBuf<R, 32 * 
     if ((mode == MODE_SIFT || mode == MODE_SIFT_COMMIT) && lane < 14) {
         constexpr int CH = (int)sizeof(TileSolve) / 16; // 7 chunks per envelope
         const int e = lane / CH, q = lane - e * CH;
-        const char *src = reinterpret_cast<const char *>(in.tsol + (int64_t)e * in.ntiles + lt);
+        const char *src = reinterpret_cast<const char *>(tsol + (int64_t)e * ntiles + lt);
         cp_async16(reinterpret_cast<char *>(&P.sts[e]) + 16 * q, src + 16 * q, 16);
     }
     cp_async_commit();
+}
+
+// The same for a tile of another instance than the current one (its descriptor and state
+// read first).
+template <typename R, int SPL>
+__device__ __forceinline__ bool stage_tile(const PassArgs &pa, StageBuf<R, 32 * SPL> &P,
+                                           int64_t gt)
+{
+    constexpr int TW = 32 * SPL;
+    const int ii = pa.tile_inst[gt];
+    const State *stp = pa.state + ii;
+    const int mode = stp->mode;
+    if (mode == MODE_DONE || mode == MODE_INIT)
+        return false;
+    const Inst &in = pa.inst[ii];
+    const int lt = (int)(gt - in.tile0);
+    const int ts = lt * TW;
+    stage_issue<R, SPL>(P, mode, (const R *)in.h[stp->hpar] + ts, ts, (int)in.L, in.tsol,
+                        in.ntiles, lt);
     return true;
 }
 
@@ -782,8 +793,19 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     // its signal into L2), its residue (commit and INIT passes) into L2, while this one
     // computes
     bool nstaged = false;
-    if constexpr (STAGE)
-        nstaged = prefetch_next && stage_tile<R, SPL>(pa, B, gt + 1);
+    if constexpr (STAGE) {
+        if (prefetch_next) {
+            if (lt + 1 < in.ntiles) { // the same instance and mode: no descriptor reads
+                if (mode != MODE_INIT) {
+                    stage_issue<R, SPL>(B, mode, hsrc + TW, ts + TW, L, in.tsol, in.ntiles,
+                                        lt + 1);
+                    nstaged = true;
+                }
+            } else {
+                nstaged = stage_tile<R, SPL>(pa, B, gt + 1);
+            }
+        }
+    }
     // the residue of a commit (or INIT) pass into L2 now (a warp's first tile; the others
     // were prefetched by its previous tile), into registers when the sift is done
     if (first && use_r && lane == 0)
