@@ -134,6 +134,7 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
 {
     if (!plan)
         return SEMD_EINVAL;
+    NvtxRange nvtx("serial_emd_plan_autotune");
     semd_plan_s &pl = *plan;
     const bool eemd = pl.p.ensemble_trials > 1;
     if (!inst || count < 1 || count > (eemd ? 1 : pl.ws.cap_inst) || (eemd && !d_noise)) {

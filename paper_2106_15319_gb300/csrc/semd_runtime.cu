@@ -939,6 +939,7 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
                            const void *d_noise, int *n_imfs, cudaStream_t s,
                            int64_t imf_stride_all)
 {
+    NvtxRange nvtx("serial_emd_decompose");
     Workspace &ws = pl.ws;
     std::string &err = pl.err;
     const semd_params &p = pl.p;
@@ -1081,6 +1082,7 @@ static semd_status enqueue_ceemdan(semd_plan_s &pl, int64_t ntiles, cudaStream_t
     const int iters1 = max_iterations(p1);
     ra.K = 1;
     for (int k = 0; k < K; ++k) {
+        NvtxRange stage_range("ceemdan stage");
         k_ce_stage_test<<<tg, 256, 0, s>>>(ws.d_ce, ws.d_cestate, ws.d_cepart, 0);
         k_ce_stage_test<<<tg, 256, 0, s>>>(ws.d_ce, ws.d_cestate, ws.d_cepart, 1);
         SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)trials * sizeof(State), s));
@@ -1106,6 +1108,7 @@ template <typename R>
 semd_status ceemdan_impl(semd_plan_s &pl, const void *d_x, const void *d_noise, void *d_modes,
                          double *d_residue, int *n_imfs, cudaStream_t s)
 {
+    NvtxRange nvtx("serial_emd_ceemdan");
     Workspace &ws = pl.ws;
     std::string &err = pl.err;
     const semd_params &p = pl.p;

@@ -4,6 +4,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "semd_types.h"
 #include "serial_emd.h"
 
@@ -18,6 +20,16 @@ constexpr int kPassWarps = 4;
 // Largest dynamic shared-memory scratch of the interface solve; larger instances use
 // global memory.
 constexpr size_t kReduceSmemMax = 184 * 1024;
+
+// A named NVTX range over a host scope (decompositions, CEEMDAN stages, autotuning, server
+// rounds), so that a timeline profiler shows where the host enqueues which work. Without a
+// profiler attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Device workspace of a plan: one allocation carved up, plus pinned host staging.
 struct Workspace {

@@ -259,6 +259,7 @@ bool semd_server_s::round(std::string &e)
         waiting = !queue.empty();
     }
     const int passes = waiting ? 2 : 8;
+    NvtxRange nvtx("server round");
     PassArgs pa{d_inst, d_state, d_tiles, ntiles, p.stop == SEMD_STOP_SD ? 1 : 0,
                 p.stop == SEMD_STOP_SNUMBER ? 1 : 0};
     ReduceArgs ra = make_reduce_args(p, d_inst, d_state, d_list, d_active, elem, max_nt);
