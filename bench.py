@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 512 << 20
 # per register-budget variant, from the ncu captures summarized in
 # profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu replays); emptied when
 # the kernel changes until it is captured again.
-PASS_TRAFFIC_TEXTURE = {}
+PASS_TRAFFIC_TEXTURE = {0: 398592, 1: 397312}
 
 
 def _peaks():
@@ -407,6 +407,17 @@ def arm_ours(args):
     wl = workload_inputs(args.workload, args.trials)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     peak, peak_kind = _peaks()
+    if args.only_leg:  # one extra leg alone (for profiling it), no headline line
+        legs = {"batched": lambda: batched_eemd(args, device, flush, peak, peak_kind, world),
+                "images": lambda: batched_images(args, device, flush, peak, peak_kind, world),
+                "slices": lambda: standard_slices(args, device, flush, world),
+                "ceemdan": lambda: ceemdan_legs(args, device, flush, world),
+                "dsweep": lambda: d_sweep(args, device, world),
+                "serving": lambda: serving(args, device)}
+        out = legs[args.only_leg]()
+        if rank == 0:
+            print(json.dumps({"only_leg": args.only_leg, "result": out}), flush=True)
+        return
 
     barrier(world)
     with ClockSampler(local) as clk:
@@ -880,6 +891,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass shape (no autotuning before the warm-up)")
+    ap.add_argument("--only-leg", default=None,
+                    choices=["batched", "images", "slices", "ceemdan", "dsweep", "serving"],
+                    help="run one extra leg alone and print its result (for profiling)")
     ap.add_argument("--pass-variant", type=int, default=None, choices=[0, 1],
                     help="register budget of the FP32 pass kernel (no autotuning)")
     args = ap.parse_args()
