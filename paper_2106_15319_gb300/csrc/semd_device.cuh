@@ -1162,14 +1162,23 @@ __device__ __forceinline__ void seg_backsub(const RedScratch<R> &X, int rs, int 
     }
 }
 
-struct RedShared {
-    double lev[14 * kRedThreads]; // level-1 results (10 arrays), level-1.5 scratch (4), in R
-    int segq[kRedThreads];        // rows per level-1 segment
+struct RedCommon {
     double sd[kRedThreads / 32][2];
     int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2], wzc[kRedThreads / 32];
     int next;
     double nakx[2][3]; // not-a-knot ends: the elimination data of rows 1 and NR - 2
 };
+// The large form's level-1 and level-1.5 arrays exist only in the kernel that has it.
+template <bool SMALL>
+struct RedShared : RedCommon {
+    double lev[14 * kRedThreads]; // level-1 results (10 arrays), level-1.5 scratch (4), in R
+    int segq[kRedThreads];        // rows per level-1 segment
+};
+template <>
+struct RedShared<true> : RedCommon {
+};
+// Systems of at most this many rows are solved by warp 0 alone (three levels).
+constexpr int kRedSmallRows = 24 * 32;
 
 // Level 2: the 32 segment-end unknowns (one reduced row per lane, no outside values: the
 // first and last rows are natural ends). FP64 plans: cyclic reduction in FP64.
@@ -1214,10 +1223,14 @@ __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, b
     return z + (double)dZ[0];
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
+// SMALL: instances whose reduced systems have at most kRedSmallRows rows (the host
+// guarantees it from the tile count); only the small form is compiled, with a register
+// budget for three (FP32) or two (FP64) resident CTAs per SM instead of one or two, so
+// that batches of many short instances fill the GPU (0: no register budget).
+template <typename R, bool SMALL>
+__global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) : 0) k_reduce(ReduceArgs ra)
 {
-    __shared__ RedShared S;
+    __shared__ RedShared<SMALL> S;
     pdl_trigger();
     const int e = blockIdx.x & 1;
     const int ii = ra.inst_list ? ra.inst_list[blockIdx.x >> 1] : (int)(blockIdx.x >> 1);
@@ -1605,15 +1618,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         X.D[p] = rd;
     }
     __syncthreads();
-    R *lev = reinterpret_cast<R *>(S.lev);
-    constexpr int NS = kRedThreads;      // level-1 segments of the large form
-    constexpr int G = kRedThreads / 32;  // segments per lane of the level-1.5 warp
-    // transposed layout: lane l's k-th segment (j = G l + k) at k * 32 + l, so that the
-    // level-1.5 warp reads without bank conflicts
-    auto tj = [](int j) { return (j % G) * 32 + j / G; };
-    if (NR <= 24 * 32) {
-        // small systems: three levels in warp 0 (segments of Q1 rows per lane, the 32
-        // segment ends to FP64 accuracy, back-substitution)
+    // small systems: three levels in warp 0 (segments of Q1 rows per lane, the 32 segment
+    // ends to FP64 accuracy, back-substitution)
+    auto small_solve = [&]() {
         if (warp == 0) {
             const int Q1 = ((NR + 31) >> 5) | 1;
             const int rs = min(lane * Q1, NR), re = min(rs + Q1, NR), rq = re - rs;
@@ -1626,7 +1633,18 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
             seg_backsub(X, rs, re, Zp, z);
         }
         __syncthreads();
+    };
+    if constexpr (SMALL) {
+        small_solve();
+    } else if (NR <= kRedSmallRows) {
+        small_solve();
     } else {
+        R *lev = reinterpret_cast<R *>(S.lev);
+        constexpr int NS = kRedThreads;     // level-1 segments of the large form
+        constexpr int G = kRedThreads / 32; // segments per lane of the level-1.5 warp
+        // transposed layout: lane l's k-th segment (j = G l + k) at k * 32 + l, so
+        // that the level-1.5 warp reads without bank conflicts
+        auto tj = [](int j) { return (j % G) * 32 + j / G; };
         // level 1: every thread eliminates a contiguous segment of Q1 rows (Q1 odd, so
         // the lanes of a warp hit distinct banks)
         const int Q1 = ((NR + NS - 1) / NS) | 1;
@@ -1643,7 +1661,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
         if (warp == 0) {
             // level 1.5: the NS segment-end unknowns; lane l eliminates the reduced rows of
             // segments G l .. G l + G - 1 (row j couples Z_{j-1}, Z_j, Z_{j+1})
-            R *cp2 = lev + 10 * NS, *dp2 = lev + 11 * NS, *bp2 = lev + 12 * NS, *Zs = lev + 13 * NS;
+            R *cp2 = lev + 10 * NS, *dp2 = lev + 11 * NS, *bp2 = lev + 12 * NS;
+            R *Zs = lev + 13 * NS;
             auto red_row = [&](int k, R &A, R &B, R &C, R &D) {
                 // reduced row of segment j = G lane + k; its successor is j + 1
                 const int i = k * 32 + lane;
@@ -1714,6 +1733,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(ReduceArgs ra)
             seg_backsub(X, rs, re, tid > 0 ? Zs[tj(tid - 1)] : R(0), Zs[tj(tid)]);
         }
         __syncthreads();
+    
     }
     if (nak) {
         // the end knots' second derivatives from the not-a-knot conditions (the solve

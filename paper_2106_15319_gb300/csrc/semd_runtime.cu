@@ -444,8 +444,11 @@ static cudaError_t set_smem_attr()
     if (e == cudaSuccess)
         e = pass_attr_one<R, 512, 1>();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_reduce<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_reduce<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kReduceSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)reduce_smem_bytes(kRedSmallRows, sizeof(R)));
     return e;
 }
 
@@ -552,11 +555,17 @@ static size_t reduce_smem(const ReduceArgs &ra)
     return ra.smem_entries > 0 ? reduce_smem_bytes(ra.smem_entries, ra.single ? 4 : 8) : 0;
 }
 
-// One CTA per instance and envelope.
+// One CTA per instance and envelope. When the shared scratch holds every instance's
+// system (smem_entries, sized for the launch's longest instance, bounds each system's
+// rows) and that is at most kRedSmallRows rows, the small-system kernel runs.
 template <typename R>
 static void launch_reduce(const ReduceArgs &ra, int ninst, cudaStream_t s)
 {
-    launch_pdl(k_reduce<R>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s, ra);
+    if (ra.smem_entries > 0 && ra.smem_entries <= kRedSmallRows)
+        launch_pdl(k_reduce<R, true>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s, ra);
+    else
+        launch_pdl(k_reduce<R, false>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s,
+                   ra);
 }
 
 int64_t serial_length(int64_t M, int64_t N, int64_t D) { return M * N + D * N - D; }
