@@ -1228,7 +1228,8 @@ __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, b
 // budget for three (FP32) or two (FP64) resident CTAs per SM instead of one or two, so
 // that batches of many short instances fill the GPU (0: no register budget).
 template <typename R, bool SMALL>
-__global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) : 0) k_reduce(ReduceArgs ra)
+__global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) : 0)
+    k_reduce(ReduceArgs ra)
 {
     __shared__ RedShared<SMALL> S;
     pdl_trigger();

@@ -683,3 +683,20 @@ def test_pass_kernel_register_variants_agree_bit_for_bit():
     plan.close()
     for imfs, res, n in out[1:]:
         assert n == out[0][2] and torch.equal(imfs, out[0][0]) and torch.equal(res, out[0][1])
+
+
+def test_readme_example_runs():
+    """The usage example of the README: serial EMD, EEMD and CEEMDAN of a 6 x 1000 input."""
+    x = torch.randn(6, 1000, device="cuda")
+    plan = Plan(make_params(6, 1000, transition_len=50, max_imfs=10))
+    imfs, residue, n = plan.decompose(x)
+    assert imfs.shape == (10, 6, 1000) and residue.dtype == torch.float64 and 1 <= n <= 10
+    noise = torch.randn(100, 6 * 1000 + 50 * 5, device="cuda")
+    ens = Plan(make_params(6, 1000, transition_len=50, ensemble_trials=100))
+    eemd_imfs, _, _ = ens.decompose(x, noise)
+    modes, r, n_modes = ens.ceemdan(x, noise)
+    torch.cuda.synchronize()
+    rec = (modes.double().sum(0) + r - x.double()).abs().max().item()
+    assert 1 <= n_modes <= 10 and rec <= 1e-5 * x.abs().max().item()
+    for p in (plan, ens):
+        p.close()
