@@ -347,22 +347,30 @@ def dist_setup(args):
     return world, rank, local
 
 
-def max_over_ranks(v: float, world: int) -> float:
+def max_over_ranks(v: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (every rank calls it, in the same order)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def barrier(world):
+def whole_job_rate(world: int, work_per_rank: float, ms_max: float) -> float:
+    """Weak scaling, one replica per rank: the units all ranks processed over the slowest
+    rank's time."""
+    return world * work_per_rank / (ms_max * 1e-3)
+
+
+def barrier(world, cuda: bool = True):
     import torch
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
+    if cuda:
+        torch.cuda.synchronize()
 
 
 def arm_reference(args):
@@ -426,7 +434,7 @@ def arm_ours(args):
     barrier(world)
     ms32 = statistics.mean(r32["ms"])
     ms32_max = max_over_ranks(ms32, world)
-    value = world * r32["sample_sifts"] / (ms32_max * 1e-3)
+    value = whole_job_rate(world, r32["sample_sifts"], ms32_max)
 
     if "fp64" in args.forms:
         r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush, args.tile,
