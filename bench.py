@@ -294,6 +294,42 @@ def fp32_imf_errors_given_input(wl, run):
     return errs
 
 
+def _oracle_trial(args):
+    """One EEMD trial through the oracle (a process-pool task): its sample-sifts."""
+    x, w, beta, K, S = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    _, _, _, sifts = O.emd(x + beta * w, K, fixed_sifts=S)
+    return int(np.sum(sifts)) * x.size
+
+
+def cpu_pool_eemd(wl, budget_s: float = 10.0):
+    """The oracle on every host core: EEMD trials (independent EMDs) in a process pool
+    (spawned, as CUDA is already initialized in this process), as many whole trials as
+    about budget_s allows."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle import oracle as O
+    X = np.asarray(wl["X"], np.float64)
+    x = O.serialize(X, wl["D"])
+    beta = 0.2 * O.std(x)
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_trial, [(x[:4096], wl["W"][m][:4096], beta, wl["K"], wl["S"])
+                                    for m in range(cores)]))  # start every worker
+        t0 = time.perf_counter()
+        done, ss, m = 0, 0, 0
+        while time.perf_counter() - t0 < budget_s and m < wl["trials"]:
+            batch = range(m, min(m + cores, wl["trials"]))
+            ss += sum(ex.map(_oracle_trial, [(x, wl["W"][j], beta, wl["K"], wl["S"])
+                                             for j in batch]))
+            done += len(batch)
+            m += len(batch)
+        el = time.perf_counter() - t0
+    return {"value": ss / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {wl['trials']} EEMD trials, FP64, one process per core"}
+
+
 def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -544,6 +580,8 @@ def batched_eemd(args, device, flush, peak, peak_kind, world):
                         "bytes_per_launch": bpl, "launches": prof["pass_n"],
                         "reduce_avg_us": prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3}}
     r["plan"].close()
+    if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
+        out["cpu_baseline_all_cores"] = cpu_pool_eemd(wl)
     return out
 
 
