@@ -244,10 +244,12 @@ def serial_emd(X, D: int, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
 
 def ceemdan(x, w, noise_rel_std: float, K: int, stop: int = STOP_FIXED, fixed_sifts: int = 10,
             sd_threshold: float = 0.2, max_sifts: int = 50, boundary: int = BOUNDARY_MIRROR,
-            mirror_knots: int = 2, store_f32: bool = False):
+            mirror_knots: int = 2, store_f32: bool = False, s_number: int = 4):
     """Sec. 2.2 CEEMDAN (Steps 1-4; Reading 12 of the C source): w is (trials, L).
 
     Returns (modes (K, L), residue (L), number of modes)."""
+    if stop == STOP_SNUMBER:
+        fixed_sifts = s_number
     x, w = _f64(x), _f64(w)
     trials, L = w.shape
     assert L == x.size
@@ -262,9 +264,11 @@ def ceemdan(x, w, noise_rel_std: float, K: int, stop: int = STOP_FIXED, fixed_si
 def serial_ceemdan(X, D: int, K: int, w, noise_rel_std: float, stop: int = STOP_FIXED,
                    fixed_sifts: int = 10, sd_threshold: float = 0.2, max_sifts: int = 50,
                    boundary: int = BOUNDARY_MIRROR, mirror_knots: int = 2,
-                   store_f32: bool = False):
+                   store_f32: bool = False, s_number: int = 4):
     """Sec. 3 with CEEMDAN as the decomposition: serialize, CEEMDAN, de-serialize.
     X is (N, M), w is (trials, L). Returns (modes (K, N, M), residue (N, M), count)."""
+    if stop == STOP_SNUMBER:
+        fixed_sifts = s_number
     X, w = _f64(X), _f64(w)
     N, M = X.shape
     L = serial_length(M, N, D)

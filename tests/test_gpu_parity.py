@@ -700,3 +700,25 @@ def test_readme_example_runs():
     assert 1 <= n_modes <= 10 and rec <= 1e-5 * x.abs().max().item()
     for p in (plan, ens):
         p.close()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(stop=capi.STOP_SNUMBER, s_number=3, max_sifts=30),
+    dict(spline_end=capi.SPLINE_NOT_A_KNOT, boundary=capi.BOUNDARY_ENDPOINTS),
+    dict(spline_end=capi.SPLINE_NOT_A_KNOT, mirror_knots=1, stop=capi.STOP_SD, max_sifts=40)])
+def test_ceemdan_plan_options_fp64(kw):
+    """Serial-CEEMDAN with the plan options that change the inner EMDs (stop rules,
+    boundary rule, not-a-knot ends), FP64, against the oracle with the same options."""
+    X = synth.grating_image(40, 12)
+    trials, K = 4, 6
+    w = synth.white_noise(trials, X.size, 80)
+    (gm, gr, gn), plan = _ceemdan_gpu(X, w, capi.FP64, transition_len=0, max_imfs=K,
+                                      noise_rel_std=0.2, **kw)
+    plan.close()
+    okw = dict(stop=kw.get("stop", capi.STOP_FIXED), max_sifts=kw.get("max_sifts", 50),
+               s_number=kw.get("s_number", 4), mirror_knots=kw.get("mirror_knots", 2),
+               boundary=kw.get("boundary", capi.BOUNDARY_MIRROR) +
+               (O.SPLINE_NOT_A_KNOT if kw.get("spline_end") == capi.SPLINE_NOT_A_KNOT else 0))
+    om, orr, on = O.serial_ceemdan(X, 0, K, w, 0.2, **okw)
+    _check_imfs(gm.reshape(K, -1), gr.reshape(-1), gn, om.reshape(K, -1), orr.reshape(-1), on,
+                X.reshape(-1), capi.FP64, f"ceemdan {kw}")
