@@ -266,6 +266,7 @@ template <typename R, int TW>
 struct StageBuf {
     R stage[TW + 16 / sizeof(R)];
     TileSolve sts[2];
+    uint2 km[32]; // the signal's extremum masks and ranks, per lane
 };
 
 // The interface solution of one tile and envelope in the working precision (FP32 pass
@@ -360,6 +361,22 @@ __device__ __forceinline__ void storen(T *p, int k0, int cnt, const T (&v)[N])
     }
 }
 
+// Knots (tile position and value) of this lane's samples into the pool in rank order:
+// maxima at slots 1 + bx.., minima at slots m0 + 3 + bn...
+template <typename R, int SPL, int TW>
+__device__ __forceinline__ void knot_compact(WarpPool<R, TW> &P, const R (&v)[SPL], int k0,
+                                             uint32_t MX, uint32_t MN, int bx, int bn, int m0)
+{
+    int ix = 1 + bx, in = m0 + 3 + bn;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+        if ((MX >> s) & 1u)
+            P.ky[ix++] = KnotY<R>{k0 + s, v[s]};
+        if ((MN >> s) & 1u)
+            P.ky[in++] = KnotY<R>{k0 + s, v[s]};
+    }
+}
+
 // Step 1 on one warp tile: extremum masks of this lane's SPL samples (maximum:
 // h[k-1] < h[k] >= h[k+1]; minimum: h[k-1] > h[k] <= h[k+1]; never at the instance's
 // end samples), their warp-wide exclusive ranks (bx, bn), the counts (m0, m1), and the
@@ -399,14 +416,23 @@ __device__ __forceinline__ void warp_knots(WarpPool<R, TW> &P, const R (&v)[SPL]
     bn = (int)(before >> 16);
     m0 = (int)(total & 0xffffu);
     m1 = (int)(total >> 16);
-    int ix = 1 + bx, in = m0 + 3 + bn;
-#pragma unroll
-    for (int s = 0; s < SPL; ++s) {
-        if ((MX >> s) & 1u)
-            P.ky[ix++] = KnotY<R>{k0 + s, v[s]};
-        if ((MN >> s) & 1u)
-            P.ky[in++] = KnotY<R>{k0 + s, v[s]};
-    }
+    knot_compact<R, SPL, TW>(P, v, k0, MX, MN, bx, bn, m0);
+}
+
+// The same from masks and ranks a previous pass stored for this signal (packed per lane:
+// x = MX | MN << 16, y = bx | bn << 16), without the comparisons and the scan.
+template <typename R, int SPL, int TW>
+__device__ __forceinline__ void warp_knots_stored(WarpPool<R, TW> &P, const R (&v)[SPL], int k0,
+                                                  uint2 km, uint32_t &MX, uint32_t &MN, int &bx,
+                                                  int &bn, int &m0, int &m1)
+{
+    MX = km.x & 0xffffu;
+    MN = km.x >> 16;
+    bx = (int)(km.y & 0xffffu);
+    bn = (int)(km.y >> 16);
+    m0 = __shfl_sync(FULLMASK, bx + __popc(MX), 31);
+    m1 = __shfl_sync(FULLMASK, bn + __popc(MN), 31);
+    knot_compact<R, SPL, TW>(P, v, k0, MX, MN, bx, bn, m0);
 }
 
 // Forward elimination of the interior spline rows s..e-1 of one envelope (row i: knot
@@ -651,6 +677,11 @@ __device__ __forceinline__ void cp_async_elem(double *dst, const double *src)
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -667,8 +698,8 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 // whose mode reads no signal (INIT, DONE) are not staged. Returns whether it copied.
 template <typename R, int SPL>
 __device__ __forceinline__ void stage_issue(StageBuf<R, 32 * SPL> &P, int mode, const R *hsrc,
-                                            int ts, int L, const TileSolve *tsol, int ntiles,
-                                            int lt)
+                                            int ts, int L, const TileSolve *tsol,
+                                            const uint2 *kmask, int ntiles, int lt)
 {
     constexpr int TW = 32 * SPL;
     constexpr int PER = 16 / (int)sizeof(R); // samples per 16-byte chunk
@@ -685,11 +716,14 @@ __device__ __forceinline__ void stage_issue(StageBuf<R, 32 * SPL> &P, int mode, 
         cp_async_elem(&P.stage[TW], hsrc - 1);
     if (lane == 31 && ts + TW < L)
         cp_async_elem(&P.stage[TW + 1], hsrc + TW);
-    if ((mode == MODE_SIFT || mode == MODE_SIFT_COMMIT) && lane < 14) {
-        constexpr int CH = (int)sizeof(TileSolve) / 16; // 7 chunks per envelope
-        const int e = lane / CH, q = lane - e * CH;
-        const char *src = reinterpret_cast<const char *>(tsol + (int64_t)e * ntiles + lt);
-        cp_async16(reinterpret_cast<char *>(&P.sts[e]) + 16 * q, src + 16 * q, 16);
+    if (mode == MODE_SIFT || mode == MODE_SIFT_COMMIT) {
+        if (lane < 14) {
+            constexpr int CH = (int)sizeof(TileSolve) / 16; // 7 chunks per envelope
+            const int e = lane / CH, q = lane - e * CH;
+            const char *src = reinterpret_cast<const char *>(tsol + (int64_t)e * ntiles + lt);
+            cp_async16(reinterpret_cast<char *>(&P.sts[e]) + 16 * q, src + 16 * q, 16);
+        }
+        cp_async8(&P.km[lane], kmask + (int64_t)lt * 32 + lane);
     }
     cp_async_commit();
 }
@@ -710,7 +744,7 @@ __device__ __forceinline__ bool stage_tile(const PassArgs &pa, StageBuf<R, 32 * 
     const int lt = (int)(gt - in.tile0);
     const int ts = lt * TW;
     stage_issue<R, SPL>(P, mode, (const R *)in.h[stp->hpar] + ts, ts, (int)in.L, in.tsol,
-                        in.ntiles, lt);
+                        in.kmask, in.ntiles, lt);
     return true;
 }
 
@@ -761,6 +795,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     // the tile's interface values (written by the interface solve just before)
     SolveVals<R> sv{};
     int2 tpn = make_int2(0, 0);
+    uint2 km = make_uint2(0u, 0u); // the signal's extremum masks and ranks (sifting modes)
     if (STAGE && staged) {
         // copied in while the previous tile computed
         cp_async_wait_all();
@@ -773,6 +808,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         if (sift) {
             sv = solve_vals(B.sts[eh], R(0));
             tpn = *reinterpret_cast<const int2 *>(&B.sts[eh].tp);
+            km = B.km[lane];
         }
         __syncwarp(); // the stage is refilled below
     } else {
@@ -787,6 +823,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
             sv = solve_vals(so, R(0));
             tpn = *reinterpret_cast<const int2 *>(&so.tp);
+            km = in.kmask[(int64_t)lt * 32 + lane];
         }
     }
     // the warp's next tile: its signal and interface values into the stage buffer (or
@@ -797,8 +834,8 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         if (prefetch_next) {
             if (lt + 1 < in.ntiles) { // the same instance and mode: no descriptor reads
                 if (mode != MODE_INIT) {
-                    stage_issue<R, SPL>(B, mode, hsrc + TW, ts + TW, L, in.tsol, in.ntiles,
-                                        lt + 1);
+                    stage_issue<R, SPL>(B, mode, hsrc + TW, ts + TW, L, in.tsol, in.kmask,
+                                        in.ntiles, lt + 1);
                     nstaged = true;
                 }
             } else {
@@ -822,15 +859,11 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     int zc = 0;             // zero crossings of the sifted signal (S-number rule)
     R hnl = hcl, hnr = hcr; // the new signal at the halo samples
     if (sift) {
-        R left = __shfl_up_sync(FULLMASK, v[SPL - 1], 1);
-        R right = __shfl_down_sync(FULLMASK, v[0], 1);
-        if (lane == 0)
-            left = hcl;
-        if (lane == 31)
-            right = hcr;
+        // Step 1: the extrema of h were found when the previous pass wrote it (its masks
+        // and ranks, stored per lane); only the knots are gathered into the pool
         uint32_t MX, MN;
         int bx, bn, m0, m1;
-        warp_knots<R, SPL, TW>(P, v, left, right, k0, ts + k0, cnt, L, MX, MN, bx, bn, m0, m1);
+        warp_knots_stored<R, SPL, TW>(P, v, k0, km, MX, MN, bx, bn, m0, m1);
         const int b1 = m0 + 2;
         const int base = eh ? b1 : 0, m = eh ? m1 : m0;
         if (hl == 0) {
@@ -965,6 +998,9 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         uint32_t MX, MN;
         int bx, bn, m0, m1;
         warp_knots<R, SPL, TW>(P, hn, left, right, k0, ts + k0, cnt, L, MX, MN, bx, bn, m0, m1);
+        // the masks and ranks for the next pass, which sifts this signal
+        in.kmask[(int64_t)lt * 32 + lane] =
+            make_uint2(MX | (MN << 16), (uint32_t)bx | ((uint32_t)bn << 16));
         __syncwarp();
         const int base = eh ? m0 + 2 : 0, m = eh ? m1 : m0;
         R f[3] = {R(0), R(0), R(0)}, l[3] = {R(0), R(0), R(0)};

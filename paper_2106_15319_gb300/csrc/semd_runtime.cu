@@ -675,6 +675,7 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {&d_tex, (size_t)tiles * 2 * tile_rec_bytes(elem)},
         {(void **)&d_tsol, (size_t)tiles * 2 * sizeof(TileSolve)},
         {(void **)&d_taux, (size_t)tiles * sizeof(TileAux)},
+        {(void **)&d_kmask, (size_t)tiles * 32 * sizeof(uint2)},
         {(void **)&d_rscr, (size_t)rentries * 8},
         {(void **)&d_active, (size_t)iters * 4},
         {(void **)&d_beta, 8},
@@ -779,6 +780,7 @@ static void bind_instance(Workspace &ws, Inst &in, int64_t off, int64_t tiles, i
     in.tex = (char *)ws.d_tex + 2 * tiles * (int64_t)tile_rec_bytes(ws.elem_size);
     in.tsol = ws.d_tsol + 2 * tiles;
     in.taux = ws.d_taux + tiles;
+    in.kmask = ws.d_kmask + 32 * tiles;
     in.rlen = reduce_len(in.ntiles);
     in.rscr = ws.d_rscr + rent;
 }
@@ -1763,6 +1765,7 @@ constexpr size_t kNoAllocBytes =
     na_round(sizeof(Inst)) + na_round(sizeof(State)) + na_round(kNoAllocTiles * 4) +
     na_round(kNoAllocTiles * 2 * tile_rec_bytes(8)) +
     na_round(kNoAllocTiles * 2 * sizeof(TileSolve)) + na_round(kNoAllocTiles * sizeof(TileAux)) +
+    na_round(kNoAllocTiles * 32 * sizeof(uint2)) +
     na_round(kNoAllocRent * 8) +
     na_round(8) + na_round(sizeof(Stats)) + na_round(4 * 8); // active flags, stats, result
 
@@ -1866,6 +1869,7 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     ws.d_tex = take(kNoAllocTiles * 2 * tile_rec_bytes(8));
     ws.d_tsol = (TileSolve *)take(kNoAllocTiles * 2 * sizeof(TileSolve));
     ws.d_taux = (TileAux *)take(kNoAllocTiles * sizeof(TileAux));
+    ws.d_kmask = (uint2 *)take(kNoAllocTiles * 32 * sizeof(uint2));
     ws.d_rscr = (double *)take(kNoAllocRent * 8);
     ws.d_active = (int32_t *)take(8);
     ws.d_stats = (Stats *)take(sizeof(Stats));

@@ -49,6 +49,7 @@ struct Workspace {
     void *d_tex = nullptr;
     TileSolve *d_tsol = nullptr;
     TileAux *d_taux = nullptr;
+    uint2 *d_kmask = nullptr; // 32 per tile
     double *d_rscr = nullptr; // interface-solve scratch: 16 x rlen doubles per instance
     int32_t *d_active = nullptr;
     double *d_beta = nullptr;

@@ -80,7 +80,7 @@ class PoolAlloc {
 // Per-request device buffers, carved from one pool range.
 struct ReqLayout {
     int64_t Lp = 0, nt = 0, rlen = 0;
-    size_t h = 0, r = 0, tex = 0, tsol = 0, taux = 0, rscr = 0, total = 0;
+    size_t h = 0, r = 0, tex = 0, tsol = 0, taux = 0, rscr = 0, kmask = 0, total = 0;
 };
 
 static ReqLayout req_layout(int64_t L, size_t elem, int tile)
@@ -96,7 +96,8 @@ static ReqLayout req_layout(int64_t L, size_t elem, int tile)
     q.tsol = R((size_t)q.nt * 2 * sizeof(TileSolve));
     q.taux = R((size_t)q.nt * sizeof(TileAux));
     q.rscr = R((size_t)(2 * rscr_env_doubles(q.rlen)) * 8);
-    q.total = 2 * q.h + 2 * q.r + q.tex + q.tsol + q.taux + q.rscr;
+    q.kmask = R((size_t)q.nt * 32 * sizeof(uint2));
+    q.total = 2 * q.h + 2 * q.r + q.tex + q.tsol + q.taux + q.rscr + q.kmask;
     return q;
 }
 
@@ -226,6 +227,7 @@ bool semd_server_s::round(std::string &e)
         in.tsol = (TileSolve *)(c + q.tex);
         in.taux = (TileAux *)(c + q.tex + q.tsol);
         in.rscr = (double *)(c + q.tex + q.tsol + q.taux);
+        in.kmask = (uint2 *)(c + q.tex + q.tsol + q.taux + q.rscr);
         in.rlen = q.rlen;
         in.x = rq.req.d_x;
         in.imf = rq.req.d_imfs;

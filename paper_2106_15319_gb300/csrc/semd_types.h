@@ -72,6 +72,8 @@ struct Inst {
     void *tex;              // TileRec<R>, 2 per tile
     TileSolve *tsol;        // 2 per tile
     TileAux *taux;          // 1 per tile
+    uint2 *kmask;           // 32 per tile: per lane, the extremum masks and ranks of the
+                            //   signal the last pass wrote (read by the next sift)
     double *rscr;           // interface-solve scratch when it does not fit shared memory:
     int64_t rlen;           //   rlen entries per envelope, rscr_env_doubles(rlen) each
     const void *x;          // input (rows x cols, row-major), or null
