@@ -904,6 +904,21 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
                 pd += v[s] * v[s];
             }
         }
+        // the instance's last sample when it is a knot (the end-point rule puts one there,
+        // as the right bracket of both envelopes): the envelopes take the knot values there
+        // exactly, as at every other knot, instead of the cubic evaluated at the far end of
+        // its interval; the loop left this lane's last intervals in c0 / c1
+        if (!hasR && cnt - 1 >= k0 && cnt - 1 < k0 + SPL) {
+            const KnotY<R> a0 = P.ky[m0 + 1], a1 = P.ky[b1 + m1 + 1];
+            if (a0.t == cnt - 1 || a1.t == cnt - 1) {
+                const R e0 = a0.t == cnt - 1 ? rmul(a0.y, R(0.5)) : horner(c0, R(cnt - 1 - t0));
+                const R e1 = a1.t == cnt - 1 ? rmul(a1.y, R(0.5)) : horner(c1, R(cnt - 1 - t1));
+#pragma unroll
+                for (int s = 0; s < SPL; ++s)
+                    if (k0 + s == cnt - 1)
+                        hn[s] = rsub(v[s], radd(e0, e1));
+            }
+        }
         // halo samples: interval 0 before the tile, interval m after it (where the
         // bracket knot is the sample itself, the knot value, as the neighbour computes it)
         if (lane == 0 && hasL) {

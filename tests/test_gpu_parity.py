@@ -32,6 +32,8 @@ from the outputs, so there the unconditional bar applies: the two leading IMFs
 within 1e-4 of their norm, every later IMF and the tail sum within 1e-3 of
 ||x||, IMF counts at most one apart.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -722,3 +724,44 @@ def test_ceemdan_plan_options_fp64(kw):
     om, orr, on = O.serial_ceemdan(X, 0, K, w, 0.2, **okw)
     _check_imfs(gm.reshape(K, -1), gr.reshape(-1), gn, om.reshape(K, -1), orr.reshape(-1), on,
                 X.reshape(-1), capi.FP64, f"ceemdan {kw}")
+
+
+@pytest.mark.parametrize("seed", range(int(os.environ.get("SEMD_RANDOM_CASES", "24"))))
+def test_random_configurations_fp64(seed):
+    """Seeded random configurations (shape, order, transition length, IMF count, stop rule,
+    boundary rule, mirror knots, spline ends, tile), FP64 against the oracle."""
+    g = np.random.default_rng(7000 + seed)
+    rows, cols = int(g.integers(1, 6)), int(g.integers(40, 1500))
+    order = capi.ORDER_ROWS if g.random() < 0.7 else capi.ORDER_COLS
+    M = cols if order == capi.ORDER_ROWS else rows
+    D = int(g.integers(0, M + 1)) if g.random() < 0.5 else -1
+    kw = dict(transition_len=D, max_imfs=int(g.integers(1, 9)), order=order)
+    stop = int(g.integers(0, 3))
+    kw["stop"] = stop
+    if stop == capi.STOP_FIXED:
+        kw["fixed_sifts"] = int(g.integers(1, 12))
+    elif stop == capi.STOP_SD:
+        kw["sd_threshold"], kw["max_sifts"] = float(g.uniform(0.05, 0.5)), int(g.integers(2, 40))
+    else:
+        kw["s_number"], kw["max_sifts"] = int(g.integers(1, 6)), int(g.integers(2, 40))
+    kw["boundary"] = int(g.integers(0, 2))
+    kw["mirror_knots"] = int(g.integers(1, 3))
+    kw["spline_end"] = int(g.integers(0, 2))
+    tile = int(g.choice([128, 256, 512]))
+    t = np.arange(rows * cols).reshape(rows, cols) / 97.0
+    X = (np.sin(t * g.uniform(0.5, 3.0)) + 0.5 * np.sin(t * g.uniform(5.0, 20.0))
+         + 0.2 * g.standard_normal((rows, cols)))
+    plan = Plan(make_params(rows, cols, precision=capi.FP64, **kw))
+    plan.tile = tile
+    imfs, res, n = plan.decompose(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    gi, gr = imfs.cpu().numpy(), res.cpu().numpy()
+    sifts = plan.counts(1)[1][0]
+    plan.close()
+    okw = {k: v for k, v in kw.items() if k in ("stop", "fixed_sifts", "sd_threshold",
+                                                   "max_sifts", "boundary", "mirror_knots",
+                                                   "s_number", "spline_end", "transition_len",
+                                                   "max_imfs", "order")}
+    o = _oracle(X, capi.FP64, **okw)
+    _check_imfs(gi, gr, n, o[0], o[1], o[2], o[4], capi.FP64, f"seed {seed} {kw} tile {tile}")
+    assert list(sifts[:n]) == list(o[3][:n])
