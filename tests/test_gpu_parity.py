@@ -765,3 +765,80 @@ def test_random_configurations_fp64(seed):
     o = _oracle(X, capi.FP64, **okw)
     _check_imfs(gi, gr, n, o[0], o[1], o[2], o[4], capi.FP64, f"seed {seed} {kw} tile {tile}")
     assert list(sifts[:n]) == list(o[3][:n])
+
+
+def _random_plan_options(g):
+    kw = dict(max_imfs=int(g.integers(1, 8)))
+    stop = int(g.integers(0, 3))
+    kw["stop"] = stop
+    if stop == capi.STOP_FIXED:
+        kw["fixed_sifts"] = int(g.integers(1, 12))
+    elif stop == capi.STOP_SD:
+        kw["sd_threshold"], kw["max_sifts"] = float(g.uniform(0.05, 0.5)), int(g.integers(2, 30))
+    else:
+        kw["s_number"], kw["max_sifts"] = int(g.integers(1, 6)), int(g.integers(2, 30))
+    kw["boundary"] = int(g.integers(0, 2))
+    kw["mirror_knots"] = int(g.integers(1, 3))
+    kw["spline_end"] = int(g.integers(0, 2))
+    return kw
+
+
+def _oracle_kw(kw):
+    okw = dict(stop=kw["stop"], max_sifts=kw.get("max_sifts", 50),
+               fixed_sifts=kw.get("fixed_sifts", 10), sd_threshold=kw.get("sd_threshold", 0.2),
+               s_number=kw.get("s_number", 4), mirror_knots=kw["mirror_knots"],
+               boundary=kw["boundary"] +
+               (O.SPLINE_NOT_A_KNOT if kw["spline_end"] == capi.SPLINE_NOT_A_KNOT else 0))
+    if kw["stop"] == capi.STOP_SNUMBER:
+        okw.pop("fixed_sifts")
+    else:
+        okw.pop("s_number")
+    return okw
+
+
+@pytest.mark.parametrize("seed", range(int(os.environ.get("SEMD_RANDOM_CASES", "24")) // 3))
+def test_random_batches_fp64(seed):
+    """Seeded random batches of uneven inputs (one plan, random options and shapes, rows
+    order, D = 0), every input against the oracle alone, FP64."""
+    g = np.random.default_rng(8000 + seed)
+    kw = _random_plan_options(g)
+    count = int(g.integers(2, 7))
+    shapes = [(int(g.integers(1, 5)), int(g.integers(20, 700))) for _ in range(count)]
+    rmax = max(r for r, _ in shapes)
+    cmax = max(c for _, c in shapes)
+    plan = Plan(make_params(rmax, cmax, precision=capi.FP64, transition_len=0, **kw),
+                max_batch=len(shapes))
+    plan.tile = int(g.choice([128, 256, 512]))
+    Xs = [g.standard_normal(s).cumsum(axis=1) * 0.1 + np.sin(np.arange(s[1]) / 7.0)
+          for s in shapes]
+    xs = [torch.from_numpy(np.ascontiguousarray(X)).cuda() for X in Xs]
+    outs, ns = plan.decompose_batch(xs)
+    torch.cuda.synchronize()
+    plan.close()
+    K = kw["max_imfs"]
+    for X, (imfs, res), n in zip(Xs, outs, ns):
+        oi, orr, on, _ = O.serial_emd(X, 0, K, **_oracle_kw(kw))
+        _check_imfs(imfs.cpu().numpy(), res.cpu().numpy(), n, oi, orr, on, X, capi.FP64,
+                    f"batch seed {seed} {kw} shape {X.shape}")
+
+
+@pytest.mark.parametrize("seed", range(int(os.environ.get("SEMD_RANDOM_CASES", "24")) // 4))
+def test_random_ceemdan_fp64(seed):
+    """Seeded random serial-CEEMDAN configurations (shape, D, realizations, options), FP64
+    against the oracle."""
+    g = np.random.default_rng(9000 + seed)
+    kw = _random_plan_options(g)
+    rows, cols = int(g.integers(1, 4)), int(g.integers(30, 400))
+    D = int(g.integers(0, cols + 1)) if rows > 1 else 0
+    trials = int(g.integers(2, 6))
+    N, M = rows, cols
+    L = M * N + D * N - D
+    X = np.sin(np.arange(rows * cols).reshape(rows, cols) / g.uniform(3, 15)) + \
+        0.3 * g.standard_normal((rows, cols))
+    w = g.standard_normal((trials, L))
+    (gm, gr, gn), plan = _ceemdan_gpu(X, w, capi.FP64, transition_len=D, **kw)
+    plan.close()
+    K = kw["max_imfs"]
+    om, orr, on = O.serial_ceemdan(X, D, K, w, 0.2, **_oracle_kw(kw))
+    _check_imfs(gm.reshape(K, -1), gr.reshape(-1), gn, om.reshape(K, -1), orr.reshape(-1), on,
+                X.reshape(-1), capi.FP64, f"ceemdan seed {seed} {kw} D {D}")
