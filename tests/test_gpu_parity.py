@@ -95,7 +95,7 @@ def _fp32_fragile_step(h, tau=2.0 ** -20):
     return bool(np.any(np.abs(d) <= tau * np.abs(h).max()))
 
 
-def _fp32_keeps_extrema(h32, S):
+def _fp32_keeps_extrema(h32, S, boundary=O.BOUNDARY_MIRROR, mirror_knots=2):
     """Whether the oracle's FP64 sift chain from h32 keeps its extremum decisions in
     single precision: rounding each sifted signal to FP32 leaves every extremum set
     unchanged, and no sift input has an FP32-fragile near-flat step."""
@@ -109,14 +109,15 @@ def _fp32_keeps_extrema(h32, S):
             return False
         if a[0].size < 1 or a[1].size < 1 or a[0].size + a[1].size < 3:
             return True
-        out = O.sift(h)
+        out = O.sift(h, boundary=boundary, mirror_knots=mirror_knots)
         if out is None:
             return True
         h = out[0]
     return True
 
 
-def _check_fp32_given_input(imfs_g, res_g, n_g, x, K, what="", S=10):
+def _check_fp32_given_input(imfs_g, res_g, n_g, x, K, what="", S=10,
+                            boundary=O.BOUNDARY_MIRROR, mirror_knots=2):
     """FP32 parity of every IMF against the oracle's IMF of the same remainder (D = 0,
     so the serialized signal is x flattened)."""
     x = np.asarray(x, np.float64).reshape(-1)
@@ -126,16 +127,18 @@ def _check_fp32_given_input(imfs_g, res_g, n_g, x, K, what="", S=10):
     errs, stable = [], []
     for k in range(n_g):
         h32 = r.astype(np.float32).astype(np.float64)
-        oi, _, on, _ = O.emd(h32, 1, fixed_sifts=S)
+        oi, _, on, _ = O.emd(h32, 1, fixed_sifts=S, boundary=boundary,
+                             mirror_knots=mirror_knots)
         assert on == 1, f"{what}: the oracle finds no IMF {k + 1} in the GPU's remainder"
         errs.append(_rel(c[k], oi[0], floor))
-        stable.append(_fp32_keeps_extrema(h32, S))
+        stable.append(_fp32_keeps_extrema(h32, S, boundary, mirror_knots))
         r = r - c[k]
     msg = f"{what}: per-IMF given input {errs}, extremum decisions kept in FP32 {stable}"
     assert all(e <= TOL[capi.FP32_MIXED] for e, st in zip(errs[:2], stable[:2]) if st), msg
     assert all(e <= FP32_STABLE_TOL for e, st in zip(errs, stable) if st), msg
     if n_g < K:
-        _, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, fixed_sifts=S)
+        _, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, fixed_sifts=S,
+                            boundary=boundary, mirror_knots=mirror_knots)
         assert on == 0, f"{what}: the GPU stopped after {n_g} IMFs, the oracle continues"
     assert np.all(c[n_g:] == 0.0), f"{what}: IMF slots past the count are not zero"
     rn = np.asarray(res_g, np.float64).reshape(-1)
@@ -842,3 +845,28 @@ def test_random_ceemdan_fp64(seed):
     om, orr, on = O.serial_ceemdan(X, D, K, w, 0.2, **_oracle_kw(kw))
     _check_imfs(gm.reshape(K, -1), gr.reshape(-1), gn, om.reshape(K, -1), orr.reshape(-1), on,
                 X.reshape(-1), capi.FP64, f"ceemdan seed {seed} {kw} D {D}")
+
+
+
+@pytest.mark.parametrize("seed", range(int(os.environ.get("SEMD_RANDOM_CASES", "24")) // 3))
+def test_random_configurations_fp32(seed):
+    """Seeded random FP32-mixed configurations (shape, K, sift count, boundary rule, mirror
+    knots, spline ends, tile; D = 0), each IMF against the oracle's IMF of the same
+    remainder under the FP32 bar."""
+    g = np.random.default_rng(10000 + seed)
+    rows, cols = int(g.integers(1, 6)), int(g.integers(60, 1500))
+    K, S = int(g.integers(1, 8)), int(g.integers(1, 12))
+    b, mk, se = int(g.integers(0, 2)), int(g.integers(1, 3)), int(g.integers(0, 2))
+    t = np.arange(rows * cols).reshape(rows, cols) / 89.0
+    X = (np.sin(t * g.uniform(0.5, 3.0)) + 0.5 * np.sin(t * g.uniform(5.0, 20.0))
+         + 0.2 * g.standard_normal((rows, cols))).astype(np.float32)
+    plan = Plan(make_params(rows, cols, transition_len=0, max_imfs=K, fixed_sifts=S,
+                            boundary=b, mirror_knots=mk, spline_end=se))
+    plan.tile = int(g.choice([128, 256, 512]))
+    imfs, res, n = plan.decompose(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    _check_fp32_given_input(imfs.double().cpu().numpy(), res.cpu().numpy(), n,
+                            X.astype(np.float64), K, f"fp32 seed {seed} K {K} S {S} b {b} "
+                            f"mk {mk} se {se}", S=S,
+                            boundary=b + (O.SPLINE_NOT_A_KNOT if se else 0), mirror_knots=mk)
