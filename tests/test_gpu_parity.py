@@ -870,3 +870,25 @@ def test_random_configurations_fp32(seed):
                             X.astype(np.float64), K, f"fp32 seed {seed} K {K} S {S} b {b} "
                             f"mk {mk} se {se}", S=S,
                             boundary=b + (O.SPLINE_NOT_A_KNOT if se else 0), mirror_knots=mk)
+
+
+@pytest.mark.parametrize("seed", range(int(os.environ.get("SEMD_RANDOM_CASES", "24")) // 6))
+def test_random_long_signals_fp64(seed):
+    """Seeded random long single signals (20 k to 300 k samples, so that the interface
+    solve takes its large form and, past its shared-memory capacity, global scratch), with
+    random options and tile, FP64 against the oracle."""
+    g = np.random.default_rng(11000 + seed)
+    kw = _random_plan_options(g)
+    L = int(g.integers(20000, 300000))
+    t = np.arange(L)
+    x = (np.sin(t / g.uniform(3.0, 9.0)) + 0.7 * np.sin(t / g.uniform(40.0, 400.0))
+         + 0.3 * g.standard_normal(L))[None, :]
+    plan = Plan(make_params(1, L, precision=capi.FP64, transition_len=0, **kw))
+    plan.tile = int(g.choice([128, 256, 512]))
+    imfs, res, n = plan.decompose(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    K = kw["max_imfs"]
+    oi, orr, on, _ = O.serial_emd(x, 0, K, **_oracle_kw(kw))
+    _check_imfs(imfs.cpu().numpy(), res.cpu().numpy(), n, oi, orr, on, x, capi.FP64,
+                f"long seed {seed} L {L} {kw}")
