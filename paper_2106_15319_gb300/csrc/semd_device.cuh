@@ -1155,9 +1155,14 @@ struct RedScratch {
 
 // Segment elimination of rows [rs, re) of the reduced system in the scratch, in place:
 // rows rs..re-2 become (bp, b, cp, dp) in (A, B, C, D); returns the segment's reduced
-// form (first unknown in terms of x_{rs-1} and x_{re-1}, last row kept).
+// form (first unknown in terms of x_{rs-1} and x_{re-1}, last row kept). The scratch
+// arrays are disjoint (__restrict__), so the loads of later rows may be issued ahead of
+// the stores of earlier ones.
 template <typename R>
-__device__ __forceinline__ SegElim<R> seg_eliminate(const RedScratch<R> &X, int rs, int re)
+__device__ __forceinline__ SegElim<R> seg_eliminate_rows(R *__restrict__ XA,
+                                                         const R *__restrict__ XB,
+                                                         R *__restrict__ XC, R *__restrict__ XD,
+                                                         int rs, int re)
 {
     SegElim<R> g;
     if (re - rs < 1)
@@ -1165,19 +1170,19 @@ __device__ __forceinline__ SegElim<R> seg_eliminate(const RedScratch<R> &X, int 
     R cprev = R(0), dprev = R(0), bprev = R(1);
 #pragma unroll 4
     for (int j = rs; j < re - 1; ++j) {
-        const R A = X.A[j], B = X.B[j], C = X.C[j], D = X.D[j];
+        const R A = XA[j], B = XB[j], C = XC[j], D = XD[j];
         const R inv = rrcp(B - A * cprev);
         cprev = C * inv;
         dprev = (D - A * dprev) * inv;
         bprev = -A * bprev * inv;
-        X.A[j] = bprev;
-        X.C[j] = cprev;
-        X.D[j] = dprev;
+        XA[j] = bprev;
+        XC[j] = cprev;
+        XD[j] = dprev;
     }
-    g.al = X.A[re - 1];
-    g.bl = X.B[re - 1];
-    g.cl = X.C[re - 1];
-    g.dl = X.D[re - 1];
+    g.al = XA[re - 1];
+    g.bl = XB[re - 1];
+    g.cl = XC[re - 1];
+    g.dl = XD[re - 1];
     if (re - rs >= 2) {
         g.alE = dprev;
         g.beE = bprev;
@@ -1185,9 +1190,9 @@ __device__ __forceinline__ SegElim<R> seg_eliminate(const RedScratch<R> &X, int 
         R xa = g.alE, xb = g.beE, xg = g.gaE;
 #pragma unroll 4
         for (int j = re - 3; j >= rs; --j) {
-            const R c = X.C[j];
-            xa = X.D[j] - c * xa;
-            xb = X.A[j] - c * xb;
+            const R c = XC[j];
+            xa = XD[j] - c * xa;
+            xb = XA[j] - c * xb;
             xg = -c * xg;
         }
         g.alS = xa;
@@ -1196,21 +1201,34 @@ __device__ __forceinline__ SegElim<R> seg_eliminate(const RedScratch<R> &X, int 
     }
     return g;
 }
+template <typename R>
+__device__ __forceinline__ SegElim<R> seg_eliminate(const RedScratch<R> &X, int rs, int re)
+{
+    return seg_eliminate_rows<R>(X.A, X.B, X.C, X.D, rs, re);
+}
 
 // Back-substitution of segment [rs, re) given x_{rs-1} = Zp and x_{re-1} = z; writes MV.
 template <typename R>
-__device__ __forceinline__ void seg_backsub(const RedScratch<R> &X, int rs, int re, R Zp, R z)
+__device__ __forceinline__ void seg_backsub_rows(const R *__restrict__ XA,
+                                                 const R *__restrict__ XC,
+                                                 const R *__restrict__ XD, R *__restrict__ XMV,
+                                                 int rs, int re, R Zp, R z)
 {
     if (re - rs < 1)
         return;
-    X.MV[re - 1] = z;
+    XMV[re - 1] = z;
     R xn = z;
 #pragma unroll 4
     for (int j = re - 2; j >= rs; --j) {
-        const R x = X.D[j] + X.A[j] * Zp - X.C[j] * xn;
-        X.MV[j] = x;
+        const R x = XD[j] + XA[j] * Zp - XC[j] * xn;
+        XMV[j] = x;
         xn = x;
     }
+}
+template <typename R>
+__device__ __forceinline__ void seg_backsub(const RedScratch<R> &X, int rs, int re, R Zp, R z)
+{
+    seg_backsub_rows<R>(X.A, X.C, X.D, X.MV, rs, re, Zp, z);
 }
 
 struct RedCommon {
@@ -1316,10 +1334,27 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     // counts: knots of both envelopes, this envelope's reduced-system entries per tile
     // (first/last knot) and the SD sums of the pass that just ran. Tiles are taken in a
     // stride of the block, four per thread at a time, every load in flight before use.
+    // With at most one tile per thread, the thread loads its tile's whole record here and
+    // writes the tile's entries from registers once the offsets are known.
     int sn = 0, so_ = 0, zs = 0;
     double a = 0.0, b = 0.0;
     const bool want_sd = ra.stop == STOP_SD, want_zc = ra.stop == STOP_SNUMBER;
-    for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+    const bool one = nt <= kRedThreads;
+    TileRec<R> r1;
+    r1.n = 0;
+    if (one && tid < nt) {
+        r1 = load_rec(texe + tid);
+        so_ = texo[tid].n;
+        if (want_sd) {
+            a = taux[tid].sd_num;
+            b = taux[tid].sd_den;
+        }
+        if (want_zc)
+            zs = taux[tid].nzc;
+        sn = r1.n;
+        X.Tu[tid] = (unsigned char)(sn <= kSparseKnots ? sn : 2);
+    }
+    for (int t0 = 0; !one && t0 < nt; t0 += 4 * kRedThreads) {
         int ne[4], no[4], nz[4];
         double sa[4], sb[4];
 #pragma unroll
@@ -1389,6 +1424,15 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         ntot += S.wsn[w][0];
         nother += S.wsn[w][1];
     }
+    __syncthreads();
+    int ubase = incl - su, U = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        ubase += w < warp ? S.wsu[w] : 0;
+        U += S.wsu[w];
+    }
+    // the stop test and the next mode (thread 0, while the others write the entries; the
+    // entries of an instance that stops sifting are dropped)
     if (tid == 0) {
         const int nmax = e == 0 ? ntot : nother, nmin = e == 0 ? nother : ntot;
         double sdn = 0.0, sdd = 0.0;
@@ -1466,95 +1510,96 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
             }
         }
     }
-    __syncthreads();
-    int ubase = incl - su, U = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        ubase += w < warp ? S.wsu[w] : 0;
-        U += S.wsu[w];
-    }
-    const int nm = S.next;
-    if (nm != MODE_SIFT && nm != MODE_SIFT_COMMIT)
-        return;
     const int nl = ra.boundary == BND_MIRROR ? min(ra.mirror_knots, ntot) : 1;
     const int nr = nl;
     const int NR = nl + U + nr;
     // not-a-knot ends need a sequence of at least four knots (boundary knots included)
     const bool nak = ra.spline_end == SPLINE_NOT_A_KNOT && ntot + nl + nr >= 4;
-    {
-        int p = nl + ubase;
-        for (int t = ca; t < cb; ++t) {
-            X.To[t] = p;
-            p += X.Tu[t];
+    auto put_entries = [&](const TileRec<R> &rc, int p) {
+        const int n = rc.n;
+        if (n == 1) {
+            X.Et[p] = rc.t[0];
+            X.Ey[p] = rc.y[0];
+            X.Ek[p] = EK_FL;
+        } else if (n >= 2 && n <= kSparseKnots) {
+            // every knot an entry: t[0], t[1] (n >= 3), t[2] (n = 4), t[3]
+            X.Et[p] = rc.t[0];
+            X.Ey[p] = rc.y[0];
+            X.Ek[p] = EK_F;
+            int q = p + 1;
+            if (n >= 3) {
+                X.Et[q] = rc.t[1];
+                X.Ey[q] = rc.y[1];
+                X.Ek[q] = EK_FREE;
+                ++q;
+            }
+            if (n == 4) {
+                X.Et[q] = rc.t[2];
+                X.Ey[q] = rc.y[2];
+                X.Ek[q] = EK_FREE;
+                ++q;
+            }
+            X.Et[q] = rc.t[3];
+            X.Ey[q] = rc.y[3];
+            X.Ek[q] = EK_L;
+        } else if (n > kSparseKnots) {
+            X.Et[p] = rc.t[0];
+            X.Ey[p] = rc.y[0];
+            X.Et[p + 1] = rc.t[3];
+            X.Ey[p + 1] = rc.y[3];
+            {
+                X.Ek[p] = EK_FS;
+                X.St[p] = rc.t[1];
+                X.A[p] = rc.y[1];
+                X.B[p] = rc.xa[0];
+                X.C[p] = rc.xa[1];
+                X.D[p] = rc.xa[2];
+                X.Ek[p + 1] = EK_LS;
+                X.St[p + 1] = rc.t[2];
+                X.A[p + 1] = rc.y[2];
+                X.B[p + 1] = rc.xb[0];
+                X.C[p + 1] = rc.xb[1];
+                X.D[p + 1] = rc.xb[2];
+            }
         }
-    }
-    __syncthreads();
-    // entries, with the substitution data of their rows: tiles in a stride of the block,
-    // four records per thread in flight at a time
-    for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
-        TileRec<R> rb[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + tid + k * kRedThreads;
-            if (t < nt)
-                rb[k] = load_rec(texe + t);
+    };
+    if (one) {
+        if (tid < nt) {
+            X.To[tid] = nl + ubase;
+            put_entries(r1, nl + ubase);
         }
+    } else {
+        {
+            int p = nl + ubase;
+            for (int t = ca; t < cb; ++t) {
+                X.To[t] = p;
+                p += X.Tu[t];
+            }
+        }
+        __syncthreads();
+        // entries, with the substitution data of their rows: tiles in a stride of the
+        // block, four records per thread in flight at a time
+        for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+            TileRec<R> rb[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + tid + k * kRedThreads;
-            if (t >= nt)
-                break;
-            const TileRec<R> &rc = rb[k];
-            const int n = rc.n;
-            const int p = X.To[t];
-            if (n == 1) {
-                X.Et[p] = rc.t[0];
-                X.Ey[p] = rc.y[0];
-                X.Ek[p] = EK_FL;
-            } else if (n >= 2 && n <= kSparseKnots) {
-                // every knot an entry: t[0], t[1] (n >= 3), t[2] (n = 4), t[3]
-                X.Et[p] = rc.t[0];
-                X.Ey[p] = rc.y[0];
-                X.Ek[p] = EK_F;
-                int q = p + 1;
-                if (n >= 3) {
-                    X.Et[q] = rc.t[1];
-                    X.Ey[q] = rc.y[1];
-                    X.Ek[q] = EK_FREE;
-                    ++q;
-                }
-                if (n == 4) {
-                    X.Et[q] = rc.t[2];
-                    X.Ey[q] = rc.y[2];
-                    X.Ek[q] = EK_FREE;
-                    ++q;
-                }
-                X.Et[q] = rc.t[3];
-                X.Ey[q] = rc.y[3];
-                X.Ek[q] = EK_L;
-            } else if (n > kSparseKnots) {
-                X.Et[p] = rc.t[0];
-                X.Ey[p] = rc.y[0];
-                X.Et[p + 1] = rc.t[3];
-                X.Ey[p + 1] = rc.y[3];
-                {
-                    X.Ek[p] = EK_FS;
-                    X.St[p] = rc.t[1];
-                    X.A[p] = rc.y[1];
-                    X.B[p] = rc.xa[0];
-                    X.C[p] = rc.xa[1];
-                    X.D[p] = rc.xa[2];
-                    X.Ek[p + 1] = EK_LS;
-                    X.St[p + 1] = rc.t[2];
-                    X.A[p + 1] = rc.y[2];
-                    X.B[p + 1] = rc.xb[0];
-                    X.C[p + 1] = rc.xb[1];
-                    X.D[p + 1] = rc.xb[2];
-                }
+            for (int k = 0; k < 4; ++k) {
+                const int t = t0 + tid + k * kRedThreads;
+                if (t < nt)
+                    rb[k] = load_rec(texe + t);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int t = t0 + tid + k * kRedThreads;
+                if (t >= nt)
+                    break;
+                put_entries(rb[k], X.To[t]);
             }
         }
     }
     __syncthreads();
+    const int nm = S.next;
+    if (nm != MODE_SIFT && nm != MODE_SIFT_COMMIT)
+        return;
     if (tid == 0) {
         const int64_t L = in.L;
         if (ra.boundary == BND_MIRROR) {
