@@ -144,6 +144,50 @@ __device__ __forceinline__ void pcr_solve(R A, R B, R C, R (&D)[NCOL], R (&Z)[NC
         Z[k] = D[k] * invB;
 }
 
+// One column of pcr_solve that also keeps its elimination factors, so that a further
+// right-hand side of the same rows is solved by pcr_apply with the shuffles of D alone:
+// pcr_apply performs the same operations on D as pcr_solve, with the same result.
+template <typename R, int W>
+struct PcrFactors {
+    static constexpr int kSteps = W >= 32 ? 5 : W >= 16 ? 4 : W >= 8 ? 3 : W >= 4 ? 2 : 1;
+    R k1[kSteps], k2[kSteps], invB;
+};
+template <typename R, int W>
+__device__ __forceinline__ R pcr_solve_keep(R A, R B, R C, R D, PcrFactors<R, W> &f)
+{
+    int i = 0;
+#pragma unroll
+    for (int st = 1; st < W; st <<= 1, ++i) {
+        const R iB = rrcp(B);
+        const R Am = __shfl_up_sync(FULLMASK, A, st, W), iBm = __shfl_up_sync(FULLMASK, iB, st, W);
+        const R Cm = __shfl_up_sync(FULLMASK, C, st, W);
+        const R Ap = __shfl_down_sync(FULLMASK, A, st, W), iBp = __shfl_down_sync(FULLMASK, iB, st, W);
+        const R Cp = __shfl_down_sync(FULLMASK, C, st, W);
+        const R Dm = __shfl_up_sync(FULLMASK, D, st, W), Dp = __shfl_down_sync(FULLMASK, D, st, W);
+        const R k1 = A * iBm, k2 = C * iBp;
+        const R nA = -k1 * Am, nC = -k2 * Cp, nB = B - k1 * Cm - k2 * Ap;
+        D = D - k1 * Dm - k2 * Dp;
+        A = nA;
+        B = nB;
+        C = nC;
+        f.k1[i] = k1;
+        f.k2[i] = k2;
+    }
+    f.invB = rrcp(B);
+    return D * f.invB;
+}
+template <typename R, int W>
+__device__ __forceinline__ R pcr_apply(const PcrFactors<R, W> &f, R D)
+{
+    int i = 0;
+#pragma unroll
+    for (int st = 1; st < W; st <<= 1, ++i) {
+        const R Dm = __shfl_up_sync(FULLMASK, D, st, W), Dp = __shfl_down_sync(FULLMASK, D, st, W);
+        D = D - f.k1[i] * Dm - f.k2[i] * Dp;
+    }
+    return D * f.invB;
+}
+
 // Reduced row of a worker from its segment elimination g and the next worker's
 // first-unknown expression (nalS, nbeS, ngaS): A Z_{l-1} + B Z_l + C Z_{l+1} = D.
 // Workers without rows (q == 0) get the dummy row Z = 0.
@@ -1267,9 +1311,10 @@ __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, b
     const float nalS = __shfl_down_sync(FULLMASK, g.alS, 1);
     const float nbeS = __shfl_down_sync(FULLMASK, g.beS, 1);
     const float ngaS = __shfl_down_sync(FULLMASK, g.gaS, 1);
-    float A, B, C, D[1], Z[1];
-    reduced_row(g, q, has_next, nalS, nbeS, ngaS, A, B, C, D[0]);
-    pcr_solve<float, 1, 32>(A, B, C, D, Z);
+    float A, B, C, D;
+    reduced_row(g, q, has_next, nalS, nbeS, ngaS, A, B, C, D);
+    PcrFactors<float, 32> f;
+    const float Z = pcr_solve_keep<float, 32>(A, B, C, D, f);
     SegElim<double> gd;
     gd.alE = g.alE;
     gd.beE = g.beE;
@@ -1280,16 +1325,15 @@ __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, b
     gd.dl = g.dl;
     double Ad, Bd, Cd, Dd;
     reduced_row(gd, q, has_next, (double)nalS, (double)nbeS, (double)ngaS, Ad, Bd, Cd, Dd);
-    const double z = (double)Z[0];
+    const double z = (double)Z;
     double zm = __shfl_up_sync(FULLMASK, z, 1), zp = __shfl_down_sync(FULLMASK, z, 1);
     if (lane == 0)
         zm = 0.0;
     if (lane == 31)
         zp = 0.0;
     const double res = Dd - (Ad * zm + Bd * z + Cd * zp);
-    float Dr[1] = {(float)res}, dZ[1];
-    pcr_solve<float, 1, 32>(A, B, C, Dr, dZ);
-    return z + (double)dZ[0];
+    const float dZ = pcr_apply<float, 32>(f, (float)res);
+    return z + (double)dZ;
 }
 
 // SMALL: instances whose reduced systems have at most kRedSmallRows rows (the host
