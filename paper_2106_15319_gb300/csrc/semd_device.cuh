@@ -73,6 +73,11 @@ __device__ __forceinline__ T warp_sum(T v)
 // visible. Both are no-ops for a kernel launched without the attribute.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Hint: fetch the line holding p into L1 (no register result).
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 // De-serialized destination of serialized sample p (Sec. 3.3): returns false for
 // transition samples, which the de-serialization drops.
@@ -1118,7 +1123,6 @@ __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
     constexpr int TW = 32 * SPL;
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_trigger();
-    pdl_wait();
     const int warp = threadIdx.x >> 5;
     WarpPool<R, TW> &P = reinterpret_cast<WarpPool<R, TW> *>(smraw)[warp];
     // staging kernels: the stage buffers follow the NWARP pools (not touched otherwise)
@@ -1128,6 +1132,18 @@ __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
     const int64_t wid = (int64_t)blockIdx.x * NWARP + warp;
     const int64_t C = (pa.ntiles + nw - 1) / nw;
     const int64_t g0 = wid * C, g1 = min(g0 + C, pa.ntiles);
+    // The tile -> instance map and the instance descriptors are written only before a
+    // decomposition starts (host copies, or kernels that finished before the previous
+    // kernel of the stream began), never by the pass or the interface solve: bring the
+    // first tile's descriptor into L1 while the interface solve finishes. Nothing the
+    // interface solve writes is touched before pdl_wait.
+    if (g0 < g1 && (threadIdx.x & 31) < 2) {
+        const char *d = reinterpret_cast<const char *>(pa.inst + pa.tile_inst[g0]);
+        prefetch_l1(d + (threadIdx.x & 31) * (sizeof(Inst) - 1));
+        if ((threadIdx.x & 31) == 0 && sizeof(Inst) > 128)
+            prefetch_l1(d + 128);
+    }
+    pdl_wait();
     bool staged = false;
     for (int64_t gt = g0; gt < g1; ++gt)
         staged = pass_tile<R, SPL, STAGE>(pa, P, B, gt, gt == g0, gt + 1 < g1, staged);
