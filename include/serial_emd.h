@@ -49,7 +49,7 @@ typedef enum semd_status {
     SEMD_ECUDA = -4,       /* a CUDA call failed (no device, launch error, ...) */
     SEMD_ETIMEOUT = -5,    /* a bounded wait ran out */
     SEMD_ECANCELED = -6,   /* the server was destroyed before the request finished */
-    SEMD_EUNSUPPORTED = -7 /* a valid option this build does not implement */
+    SEMD_EUNSUPPORTED = -7 /* a valid option that the library does not implement */
 } semd_status;
 
 typedef enum semd_order { SEMD_ORDER_ROWS = 0, SEMD_ORDER_COLS = 1 } semd_order;
