@@ -303,6 +303,28 @@ def _oracle_trial(args):
     return int(np.sum(sifts)) * x.size
 
 
+def _cpu_model() -> str:
+    """The host CPU, for the oracle timings: /proc/cpuinfo's model name, else (Arm) its
+    implementer and part numbers, else the machine type."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    part = fields.get("CPU part")
+    if part:
+        names = {"0xd4f": "Neoverse V2"}
+        return (f"{platform.machine()} {names.get(part, 'CPU part ' + part)} "
+                f"(implementer {fields.get('CPU implementer', '?')})")
+    return platform.machine()
+
+
 def cpu_pool_eemd(wl, budget_s: float = 10.0):
     """The oracle on every host core: EEMD trials (independent EMDs) in a process pool
     (spawned, as CUDA is already initialized in this process), as many whole trials as
@@ -327,6 +349,7 @@ def cpu_pool_eemd(wl, budget_s: float = 10.0):
             m += len(batch)
         el = time.perf_counter() - t0
     return {"value": ss / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": f"{done} of {wl['trials']} EEMD trials, FP64, one process per core"}
 
 
@@ -343,6 +366,7 @@ def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
             done += 1
         el = time.perf_counter() - t0
         return {"value": ss_per_step * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "cpu_model": _cpu_model(),
                 "sample": f"{done} full serial-CEEMDAN calls of the workload, FP64, single "
                           "thread (samples*sifts per call as counted by the GPU run)",
                 "ms_per_call": el / done * 1e3}
@@ -357,6 +381,7 @@ def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
             done += 1
         el = time.perf_counter() - t0
         return {"value": ss / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "cpu_model": _cpu_model(),
                 "sample": f"{done} of {wl['trials']} EEMD trials, FP64, single thread"}
     t0 = time.perf_counter()
     done, ss = 0, 0
@@ -365,7 +390,7 @@ def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
         ss += int(np.sum(sifts)) * O.serial_length(X.shape[1], X.shape[0], wl["D"])
         done += 1
     el = time.perf_counter() - t0
-    return {"value": ss / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": ss / el, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
             "sample": f"{done} full decompositions of the workload, FP64, single thread"}
 
 
