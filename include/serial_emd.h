@@ -60,19 +60,21 @@ typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precisio
 
 /*
  * Parameters of the method, following the paper's statement of the problem:
- *  rows, cols       shape of one input (the plan's capacity unit, see serial_emd_plan).
+ *  rows, cols       shape of one input (the plan's capacity unit, see serial_emd_plan),
+ *                   both >= 1, with a serialized length MN + DN - D below 2^30.
  *  order            which axis holds the N signals (see conventions above).
  *  transition_len   D of Sec. 3.2, 0 <= D <= M; -1 selects round(0.2 M), the
- *                   20 % rule of Sec. 4.1.
+ *                   20 % rule of Sec. 4.1. A single signal (N = 1) takes D = 0.
  *  max_imfs         K, 1 <= K <= 32 (Sec. 3.3; the paper caps at 10 in Sec. 4.3).
- *  stop             SEMD_STOP_FIXED: exactly fixed_sifts sifts per IMF (>= 1).
+ *  stop             SEMD_STOP_FIXED: exactly fixed_sifts sifts per IMF (1 to 1000).
  *                   SEMD_STOP_SD: sift until sum (h_prev - h)^2 / sum h_prev^2 <
- *                   sd_threshold, at most max_sifts sifts. Sec. 2.1 Step 5 leaves the
- *                   criterion open ("some predefined stopping criterion").
+ *                   sd_threshold (>= 0), at most max_sifts sifts (1 to 1000). Sec. 2.1
+ *                   Step 5 leaves the criterion open ("some predefined stopping
+ *                   criterion").
  *                   SEMD_STOP_SNUMBER: the S-number rule of the EMD literature: sift
  *                   until s_number consecutive sifts have each left a signal whose
  *                   extrema count (maxima + minima) and zero-crossing count differ by
- *                   at most one, at most max_sifts sifts.
+ *                   at most one, at most max_sifts sifts (1 to 1000).
  *  boundary         envelope end rule (the paper is silent): MIRROR reflects the
  *                   first and last mirror_knots (1 or 2) extrema about the ends;
  *                   ENDPOINTS adds the two end samples as knots.
@@ -81,7 +83,8 @@ typedef enum semd_precision { SEMD_FP64 = 0, SEMD_FP32_MIXED = 1 } semd_precisio
  *                   reductions, the residue and the EEMD average.
  *  ensemble_trials  <= 1: EMD. > 1: EEMD with that many noise realizations (Sec. 2.2);
  *                   such plans also run CEEMDAN (serial_emd_ceemdan).
- *  noise_rel_std    EEMD beta = noise_rel_std * population std of the serialized x;
+ *  noise_rel_std    (>= 0 when ensemble_trials > 1) EEMD beta = noise_rel_std *
+ *                   population std of the serialized x;
  *                   CEEMDAN beta_k = noise_rel_std * population std of the residue r_k.
  *  s_number         S of SEMD_STOP_SNUMBER, 1 <= S <= 1000.
  *  spline_end       end conditions of the envelope splines: SEMD_SPLINE_NATURAL (zero
