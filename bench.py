@@ -35,10 +35,10 @@ METRIC = "serialized samples sifted/s: batched FP32 vs plain FP64 on GB300; p99 
 UNIT = "samples*sifts/s"
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_pass launch of the default workload (256-sample tiles)
-# per register-budget variant, from the ncu captures summarized in
-# profiles/k_pass_k_reduce_fp32_texture256.md (cold caches, as ncu replays); emptied when
-# the kernel changes until it is captured again.
-PASS_TRAFFIC_TEXTURE = {0: 465152, 1: 464384}
+# per pass-kernel variant, from an ncu capture of that launch with the dram__bytes counters
+# (cold caches, as ncu replays). Emptied whenever the pass kernel changes, until the changed
+# kernel is captured again; an empty entry is reported as null.
+PASS_TRAFFIC_TEXTURE = {}
 
 
 def _peaks():

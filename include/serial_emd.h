@@ -232,25 +232,29 @@ semd_status serial_emd_sift(semd_plan_t plan, const void *d_h, int64_t L, void *
 
 /*
  * Allocation-free form of serial_emd_sift, for callers that cannot reserve device
- * memory: code that runs while a CUDA graph is being captured into or replayed on a
- * pool it does not own, plug-ins hosted by a framework whose caching allocator owns
- * the device memory, or real-time paths that forbid allocation after start-up. The
+ * memory at the point where they sift: plug-ins hosted by a framework whose caching
+ * allocator owns the device memory (a cudaMalloc of their own would fight it for the
+ * same bytes), real-time paths that forbid allocation after start-up, and code that
+ * runs under a hard device-memory cap where an allocation could fail mid-stream. The
  * paper has no counterpart; it is a packaging of the same sift.
  * It performs exactly the sift of serial_emd_sift (same kernels, same results) on
  * d_h (L elements of the precision in params->precision) into d_out (L elements),
- * with the envelope rule of params->boundary / params->mirror_knots; the other
- * fields of params are ignored. The sums (h - h')^2 and h^2 are returned through the
- * host pointers, after the call has waited for the stream.
+ * with the envelope rule of params->boundary / params->mirror_knots and the spline
+ * end conditions of params->spline_end (each validated as serial_emd_plan validates
+ * it; SEMD_EINVAL otherwise); the other fields of params are ignored.
+ * The call waits for `stream`: it copies the sums (h - h')^2 and h^2 back to the host
+ * pointers and synchronizes the stream before it returns.
  * Scratch: one static device array of about 2.4 MB, compiled into the library, which
  * every GPU that loads the library holds until the process exits; nothing is
  * allocated per call (no cudaMalloc, cudaFree or allocating library routine). L
  * must be in [1, 65536]: a larger L returns SEMD_EINVAL with a message naming the
  * limit. The first call on a device looks up the array's device address and sets
- * kernel attributes for that device; make that first call outside any stream
- * capture. All calls share the one array and each call clears what it needs, so two
- * calls whose work overlaps on the GPU (different streams or threads) race and
- * give wrong results: serialize them. Errors (EINVAL, ECUDA) are described by
- * serial_emd_last_error(NULL).
+ * kernel attributes for that device; make that first call before any stream capture
+ * begins. All calls share the one array and each call clears what it needs, so two
+ * calls whose work overlaps on the GPU (different streams or threads) race and give
+ * wrong results: serialize them. Errors (EINVAL, ECUDA) are described by
+ * serial_emd_last_error(NULL) called on the same host thread: the message of a call
+ * without a plan is kept per thread.
  */
 semd_status serial_emd_sift_noalloc(const semd_params *params, const void *d_h, int64_t L,
                                     void *d_out, double *sd_num, double *sd_den, void *stream);
@@ -359,10 +363,23 @@ typedef struct semd_stats {
 
 semd_status serial_emd_plan_stats(semd_plan_t plan, semd_stats *out);
 
+/*
+ * Per-launch device times of the plan's last decompose call when it ran with profiling
+ * on (serial_emd_plan_set_options): kind 0 the sifting pass launches, kind 1 the interface
+ * solves, in launch order, in milliseconds (CUDA events around each launch on its stream).
+ * Writes at most cap values to the host array ms (may be NULL) and returns the number of
+ * launches of that kind, or -1 for a NULL plan, an unknown kind or cap < 0. Waits for the
+ * events. Pass launch i of a fixed-sift-count EMD runs, for i >= 1, IMF (i - 1) / S + 1
+ * and sift (i - 1) % S + 1 (S sifts per IMF; the last sift of an IMF also commits it);
+ * launch 0 reads the serialized input.
+ */
+int64_t serial_emd_plan_launch_times(semd_plan_t plan, int kind, float *ms, int64_t cap);
+
 /* Releases a plan and its workspaces (after its work on any stream has finished). */
 void serial_emd_destroy(semd_plan_t plan);
 
-/* Text of the last error on a plan (or of the last failed plan creation if NULL). */
+/* Text of the last error on a plan; with NULL, of the last failed call without a plan
+ * (plan creation, serial_emd_sift_noalloc) on the calling host thread. */
 const char *serial_emd_last_error(semd_plan_t plan);
 
 /* ------------------------------------------------------------------ serving */

@@ -126,6 +126,9 @@ SIGNATURES = {
     "serial_emd_tune_last_error": (ctypes.c_char_p, []),
     "serial_emd_plan_set_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "serial_emd_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_stats)]),
+    "serial_emd_plan_launch_times": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int,
+                                                      ctypes.POINTER(ctypes.c_float),
+                                                      ctypes.c_int64]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
     "serial_emd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "serial_emd_server_create": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_size_t,
@@ -159,6 +162,50 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+# handle -> the plan's parameters, for the argument checks below
+_PLAN_PARAMS: dict = {}
+
+_TORCH_DTYPES = None
+
+
+def _dtype_of(precision: int):
+    global _TORCH_DTYPES
+    if _TORCH_DTYPES is None:
+        import torch
+        _TORCH_DTYPES = {FP64: torch.float64, FP32_MIXED: torch.float32, "int32": torch.int32}
+    return _TORCH_DTYPES[precision]
+
+
+def _need(t, what: str, dtype, numel: int | None = None, optional: bool = False):
+    """Refuses (SEMD_EINVAL, before any library call) a buffer the C ABI would read or write
+    out of bounds or misinterpret: it must be a contiguous CUDA tensor on the current
+    device, of the element type the call uses, with at least `numel` elements."""
+    if t is None:
+        if optional:
+            return
+        raise SemdError(SEMD_EINVAL, f"{what}: a CUDA tensor is required")
+    if isinstance(t, int):  # a raw device pointer: the caller vouches for it
+        return
+    if not getattr(t, "is_cuda", False):
+        raise SemdError(SEMD_EINVAL, f"{what}: not a CUDA tensor")
+    import torch
+    if torch.cuda.is_available() and t.device.index != torch.cuda.current_device():
+        raise SemdError(SEMD_EINVAL, f"{what}: on cuda:{t.device.index}, not on the current "
+                                     f"device cuda:{torch.cuda.current_device()}")
+    if not t.is_contiguous():
+        raise SemdError(SEMD_EINVAL, f"{what}: not contiguous")
+    want = _dtype_of(dtype)
+    if t.dtype != want:
+        raise SemdError(SEMD_EINVAL, f"{what}: dtype {t.dtype}, the call needs {want}")
+    if numel is not None and t.numel() < numel:
+        raise SemdError(SEMD_EINVAL, f"{what}: {t.numel()} elements, the call needs {numel}")
+
+
+def _plan_precision(plan: int):
+    p = _PLAN_PARAMS.get(plan)
+    return p.precision if p is not None else None
 
 
 def _ptr(t) -> int | None:
@@ -199,6 +246,9 @@ def serial_emd_plan(params: semd_params, max_batch: int = 1, mem_budget: int = 0
     h = ctypes.c_void_p()
     rc = load().serial_emd_plan(ctypes.byref(params), max_batch, mem_budget, ctypes.byref(h))
     _check(rc, None)
+    kept = semd_params()
+    ctypes.pointer(kept)[0] = params
+    _PLAN_PARAMS[h.value] = kept
     return h.value
 
 
@@ -206,7 +256,26 @@ def serial_emd_plan_bytes(plan: int) -> int:
     return int(load().serial_emd_plan_bytes(plan))
 
 
+def _serial_len(p, rows: int, cols: int) -> int:
+    M, N = (cols, rows) if p.order == ORDER_ROWS else (rows, cols)
+    D = int(round(0.2 * M)) if p.transition_len < 0 else p.transition_len
+    return M * N if N == 1 else M * N + D * N - D
+
+
+def _need_decompose(plan: int, x, noise, imfs, residue, ensemble_needs_noise: bool):
+    p = _PLAN_PARAMS.get(plan)
+    if p is None:
+        return
+    rc = p.rows * p.cols
+    _need(x, "x", p.precision, rc)
+    _need(imfs, "imfs", p.precision, p.max_imfs * rc)
+    _need(residue, "residue", FP64, rc, optional=True)
+    if p.ensemble_trials > 1 and ensemble_needs_noise:
+        _need(noise, "noise", p.precision, p.ensemble_trials * _serial_len(p, p.rows, p.cols))
+
+
 def serial_emd_decompose(plan: int, x, noise, imfs, residue, stream=None, wait: bool = True):
+    _need_decompose(plan, x, noise, imfs, residue, True)
     n = ctypes.c_int(-1)
     rc = load().serial_emd_decompose(plan, _ptr(x), _ptr(noise), _ptr(imfs), _ptr(residue),
                                      ctypes.byref(n) if wait else None, _stream(stream))
@@ -216,8 +285,14 @@ def serial_emd_decompose(plan: int, x, noise, imfs, residue, stream=None, wait: 
 
 def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True):
     """items: list of (x, imfs, residue) CUDA tensors, x 2D (rows, cols)."""
+    p = _PLAN_PARAMS.get(plan)
     arr = (semd_instance * len(items))()
     for i, (x, imfs, res) in enumerate(items):
+        if p is not None:
+            rc = x.shape[0] * x.shape[1]
+            _need(x, f"items[{i}].x", p.precision, rc)
+            _need(imfs, f"items[{i}].imfs", p.precision, p.max_imfs * rc)
+            _need(res, f"items[{i}].residue", FP64, rc, optional=True)
         arr[i] = semd_instance(_ptr(x), x.shape[0], x.shape[1], _ptr(imfs), _ptr(res))
     n = (ctypes.c_int * len(items))()
     rc = load().serial_emd_decompose_batch(plan, len(items), arr, n if wait else None,
@@ -229,6 +304,11 @@ def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True)
 def serial_emd_decompose_slices(plan: int, x, imfs, residue, stream=None, wait: bool = True):
     """Slice-wise standard EMD of every row of x (rows, cols); imfs (K, rows, cols)."""
     rows, cols = x.shape
+    p = _PLAN_PARAMS.get(plan)
+    if p is not None:
+        _need(x, "x", p.precision, rows * cols)
+        _need(imfs, "imfs", p.precision, p.max_imfs * rows * cols)
+        _need(residue, "residue", FP64, rows * cols, optional=True)
     n = (ctypes.c_int * rows)()
     rc = load().serial_emd_decompose_slices(plan, _ptr(x), rows, cols, _ptr(imfs), _ptr(residue),
                                             n if wait else None, _stream(stream))
@@ -238,6 +318,7 @@ def serial_emd_decompose_slices(plan: int, x, imfs, residue, stream=None, wait: 
 
 def serial_emd_ceemdan(plan: int, x, noise, modes, residue, stream=None, wait: bool = True):
     """Serial-CEEMDAN (Sec. 2.2 Steps 1-4 inside Sec. 3) of x with the noise (trials, L)."""
+    _need_decompose(plan, x, noise, modes, residue, True)
     n = ctypes.c_int(-1)
     rc = load().serial_emd_ceemdan(plan, _ptr(x), _ptr(noise), _ptr(modes), _ptr(residue),
                                    ctypes.byref(n) if wait else None, _stream(stream))
@@ -253,6 +334,12 @@ def serial_emd_plan_counts(plan: int, count: int, max_imfs: int):
 
 
 def serial_emd_extrema(plan: int, h, tmax, tmin, stream=None):
+    prec = _plan_precision(plan)
+    if prec is not None:
+        _need(h, "h", prec)
+        n = h.numel() // 2 + 1 if not isinstance(h, int) else None
+        _need(tmax, "tmax", "int32", n)
+        _need(tmin, "tmin", "int32", n)
     a, b = ctypes.c_int64(), ctypes.c_int64()
     rc = load().serial_emd_extrema(plan, _ptr(h), h.numel(), _ptr(tmax), _ptr(tmin),
                                    ctypes.byref(a), ctypes.byref(b), _stream(stream))
@@ -261,6 +348,10 @@ def serial_emd_extrema(plan: int, h, tmax, tmin, stream=None):
 
 
 def serial_emd_sift(plan: int, h, out, stream=None):
+    prec = _plan_precision(plan)
+    if prec is not None:
+        _need(h, "h", prec)
+        _need(out, "out", prec, h.numel())
     a, b = ctypes.c_double(), ctypes.c_double()
     rc = load().serial_emd_sift(plan, _ptr(h), h.numel(), _ptr(out), ctypes.byref(a),
                                 ctypes.byref(b), _stream(stream))
@@ -270,6 +361,10 @@ def serial_emd_sift(plan: int, h, out, stream=None):
 
 def serial_emd_sift_noalloc(params: semd_params, h, out, stream=None):
     """Allocation-free single sift (no plan); returns (sum (h - h')^2, sum h^2)."""
+    if params.precision not in (FP64, FP32_MIXED):
+        raise SemdError(SEMD_EINVAL, "precision must be FP64 or FP32_MIXED")
+    _need(h, "h", params.precision)
+    _need(out, "out", params.precision, h.numel())
     a, b = ctypes.c_double(), ctypes.c_double()
     rc = load().serial_emd_sift_noalloc(ctypes.byref(params), _ptr(h), h.numel(), _ptr(out),
                                         ctypes.byref(a), ctypes.byref(b), _stream(stream))
@@ -354,8 +449,19 @@ def serial_emd_plan_stats(plan: int) -> semd_stats:
     return st
 
 
+def serial_emd_plan_launch_times(plan: int, kind: int) -> list[float]:
+    """Per-launch device times (ms) of the last profiled call: kind 0 passes, 1 solves."""
+    n = int(load().serial_emd_plan_launch_times(plan, kind, None, 0))
+    if n < 0:
+        raise SemdError(SEMD_EINVAL, "bad plan or kind")
+    buf = (ctypes.c_float * max(1, n))()
+    load().serial_emd_plan_launch_times(plan, kind, buf, n)
+    return list(buf[:n])
+
+
 def serial_emd_destroy(plan: int) -> None:
     if plan:
+        _PLAN_PARAMS.pop(plan, None)
         load().serial_emd_destroy(plan)
 
 
@@ -370,10 +476,19 @@ def serial_emd_server_create(params: semd_params, mem_budget: int, max_inflight:
                                          ctypes.byref(h))
     if rc < 0:
         raise SemdError(rc, serial_emd_server_last_error(None))
+    kept = semd_params()
+    ctypes.pointer(kept)[0] = params
+    _PLAN_PARAMS[("server", h.value)] = kept
     return h.value
 
 
 def serial_emd_submit(server: int, x, imfs, residue, order: int = ORDER_ROWS) -> int:
+    p = _PLAN_PARAMS.get(("server", server))
+    if p is not None:
+        rc = x.shape[0] * x.shape[1]
+        _need(x, "x", p.precision, rc)
+        _need(imfs, "imfs", p.precision, p.max_imfs * rc)
+        _need(residue, "residue", FP64, rc, optional=True)
     req = semd_request(_ptr(x), x.shape[0], x.shape[1], order, 0, _ptr(imfs), _ptr(residue))
     t = ctypes.c_uint64()
     rc = load().serial_emd_submit(server, ctypes.byref(req), ctypes.byref(t))
@@ -393,6 +508,7 @@ def serial_emd_poll(server: int, ticket: int):
 
 def serial_emd_server_destroy(server: int) -> None:
     if server:
+        _PLAN_PARAMS.pop(("server", server), None)
         load().serial_emd_server_destroy(server)
 
 

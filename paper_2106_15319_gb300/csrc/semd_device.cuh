@@ -30,6 +30,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "semd_convert.cuh"
 #include "semd_types.h"
 
 namespace semd {
@@ -1006,7 +1007,8 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             hn[s] = v[s];
     }
 
-    // Step 5 / Eq. (1): commit the IMF c, update the FP64 residue, restart from it
+    // Step 5 / Eq. (1): commit the IMF c, update the FP64 residue, restart from it (the
+    // conversions between the working precision and FP64 run on the integer pipes)
     if (use_r) {
         double r[SPL], rl = 0.0, rr = 0.0;
         loadn<double, SPL>(rsrc, k0, cnt, r);
@@ -1018,7 +1020,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             double rn[SPL];
 #pragma unroll
             for (int s = 0; s < SPL; ++s)
-                rn[s] = __dsub_rn(r[s], (double)hn[s]);
+                rn[s] = __dsub_rn(r[s], widen(hn[s]));
             storen<double, SPL>(rdst, k0, cnt, rn);
             R *imf = (R *)in.imf + (int64_t)imfc * in.imf_stride;
             if (in.imf_serialized) {
@@ -1039,16 +1041,16 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
             }
 #pragma unroll
             for (int s = 0; s < SPL; ++s)
-                hn[s] = (R)rn[s];
+                narrow_to(rn[s], hn[s]);
         } else {
 #pragma unroll
             for (int s = 0; s < SPL; ++s)
-                hn[s] = (R)r[s];
+                narrow_to(r[s], hn[s]);
         }
         if (lane == 0 && hasL)
-            hnl = (R)(commit ? __dsub_rn(rl, (double)hnl) : rl);
+            narrow_to(commit ? __dsub_rn(rl, widen(hnl)) : rl, hnl);
         if (lane == 31 && hasR)
-            hnr = (R)(commit ? __dsub_rn(rr, (double)hnr) : rr);
+            narrow_to(commit ? __dsub_rn(rr, widen(hnr)) : rr, hnr);
     }
 
     // Step 1 on the new signal and the per-tile elimination of its spline system

@@ -1738,6 +1738,13 @@ semd_status serial_emd_plan_stats(semd_plan_t plan, semd_stats *out)
     return SEMD_OK;
 }
 
+int64_t serial_emd_plan_launch_times(semd_plan_t plan, int kind, float *ms, int64_t cap)
+{
+    if (!plan || (kind != 0 && kind != 1) || cap < 0)
+        return -1;
+    return plan->prof.times(kind, ms, cap);
+}
+
 const char *serial_emd_last_error(semd_plan_t plan)
 {
     return plan ? plan->err.c_str() : g_plan_create_error.c_str();
@@ -1930,6 +1937,8 @@ extern "C" semd_status serial_emd_sift_noalloc(const semd_params *params, const 
     if (params->boundary == SEMD_BOUNDARY_MIRROR &&
         (params->mirror_knots < 1 || params->mirror_knots > 2))
         return err = "mirror_knots must be 1 or 2", SEMD_EINVAL;
+    if (params->spline_end != SEMD_SPLINE_NATURAL && params->spline_end != SEMD_SPLINE_NOT_A_KNOT)
+        return err = "spline_end must be NATURAL or NOT_A_KNOT", SEMD_EINVAL;
     if (L < 1 || L > semd::kNoAllocMaxL) {
         err = "L = " + std::to_string(L) + " is outside [1, " +
               std::to_string(semd::kNoAllocMaxL) + "], the size of the allocation-free scratch";

@@ -160,6 +160,25 @@ struct Profiler {
             }
         }
     }
+    // Device time of each profiled launch of one kind, in launch order (waits for the
+    // events); returns how many launches of that kind were recorded.
+    int64_t times(int kind, float *ms, int64_t cap) const
+    {
+        int64_t n = 0;
+        for (auto &r : rec) {
+            if (r.first != kind)
+                continue;
+            if (ms && n < cap) {
+                float t = 0.f;
+                cudaEventSynchronize(ev[r.second + 1]);
+                if (cudaEventElapsedTime(&t, ev[r.second], ev[r.second + 1]) != cudaSuccess)
+                    t = -1.f;
+                ms[n] = t;
+            }
+            ++n;
+        }
+        return n;
+    }
     void destroy()
     {
         for (auto e : ev)

@@ -316,6 +316,100 @@ def test_emd_sd_stop_limits():
     assert n3 == 4 and np.all((s3[:n3] >= 1) & (s3[:n3] <= 50))
 
 
+def _enough_extrema(h):
+    """Reading 9's test, written out: at least one maximum, one minimum and three extrema
+    under the tie rule of Reading 5 (maximum iff h[k-1] < h[k] >= h[k+1], 1 <= k <= L-2)."""
+    k = np.arange(1, h.size - 1)
+    nmax = int(np.sum((h[k - 1] < h[k]) & (h[k] >= h[k + 1])))
+    nmin = int(np.sum((h[k - 1] > h[k]) & (h[k] <= h[k + 1])))
+    return nmax >= 1 and nmin >= 1 and nmax + nmin >= 3
+
+
+def _sd_replay(r, thr, cap, denom_new=False, test_first=False):
+    """Sifts of one IMF under Reading 8, replayed with the single-sift step: after each
+    sift, SD = sum (h_prev - h)^2 / sum h_prev^2 in numpy; sifting ends when SD < thr, at
+    the cap, or when the sifted signal fails Reading 9's test. The two flags give the
+    plausible misreadings the pin must tell apart: the new signal's energy as the
+    denominator, and the ratio of the previous sift tested after the next one (the test
+    placed before the sift that it should follow)."""
+    h, j, prev_sd = r.copy(), 0, None
+    while True:
+        hn = O.sift(h)[0]
+        j += 1
+        sd = np.sum((h - hn) ** 2) / np.sum((hn if denom_new else h) ** 2)
+        h = hn
+        tested = prev_sd if test_first else sd
+        if (tested is not None and tested < thr) or j >= cap or not _enough_extrema(h):
+            break
+        prev_sd = sd
+    return h, j
+
+
+@pytest.mark.parametrize("thr", [0.2, 0.05])
+def test_emd_sd_stop_against_sift_chain(thr):
+    """Reading 8 (Sec. 2.1 Step 5): each IMF's sift count and value equal a replay of single
+    sifts whose SD ratio is computed here from the sift outputs; the misread rules (the
+    sifted signal's energy as the denominator, the test placed before the sift) give other
+    counts on the same input."""
+    cap, K = 50, 6
+    diffs = {"denom_new": 0, "test_first": 0}
+    for ch in range(3):
+        x = synth.workload_series_3x1024()[ch]
+        imfs, res, n, sifts = O.emd(x, K, stop=O.STOP_SD, sd_threshold=thr, max_sifts=cap)
+        assert n >= 3
+        r = x.copy()
+        for i in range(n):
+            h, j = _sd_replay(r, thr, cap)
+            assert sifts[i] == j, (ch, i, sifts[i], j)
+            assert np.array_equal(imfs[i], h)
+            for flag in diffs:
+                _, jj = _sd_replay(r, thr, cap, **{flag: True})
+                diffs[flag] += int(jj != j)
+            r = r - h
+        assert np.array_equal(res, r)
+    assert all(v > 0 for v in diffs.values()), diffs
+
+
+def test_emd_mid_sift_end_test():
+    """Reading 9 mid-sift: when a sift leaves a signal without a maximum, a minimum or three
+    extrema, sifting stops and that signal is the IMF, although the fixed count (10) is not
+    reached. Small seeded inputs (a tone, a ramp and sometimes noise) where this happens are
+    replayed with the single-sift step and the extremum rule written out here; without the
+    mid-sift test the replay would sift on, so the rule is what decides these cases."""
+    g = synth.rng(77)
+    cases, decisive = 0, 0
+    for _ in range(6000):
+        L = int(g.integers(8, 40))
+        t = np.arange(L)
+        x = (np.sin(t * g.uniform(0.1, 0.6)) + g.normal(0, 0.3, L) * (g.uniform() < 0.5)
+             + g.uniform(-1, 1) * t / L * 3)
+        imfs, res, n, sifts = O.emd(x, 3, fixed_sifts=10)
+        if n < 1 or sifts[0] >= 10:
+            continue
+        cases += 1
+        r = x.copy()
+        for i in range(n):
+            h, j = r.copy(), 0
+            while j < 10 and _enough_extrema(h):
+                out = O.sift(h)
+                if out is None:
+                    break
+                h, j = out[0], j + 1
+            assert sifts[i] == j, (i, sifts[i], j)
+            assert np.array_equal(imfs[i], h)
+            r = r - h
+        assert np.array_equal(res, r)
+        # without the mid-sift test the first IMF would take more sifts
+        h, j = x.copy(), 0
+        while j < 10:
+            out = O.sift(h)
+            if out is None:
+                break
+            h, j = out[0], j + 1
+        decisive += int(j != sifts[0])
+    assert cases >= 3 and decisive >= 3, (cases, decisive)
+
+
 def test_zero_crossings_definition():
     """Reading 8b: a pair counts when exactly one sample is negative (0 is not negative);
     against a direct loop, and 2f crossings of a sampled sinusoid with f whole periods."""
