@@ -34,11 +34,16 @@ sys.path.insert(0, ROOT)
 METRIC = "serialized samples sifted/s: batched FP32 vs plain FP64 on GB300; p99 request latency"
 UNIT = "samples*sifts/s"
 L2_FLUSH_BYTES = 512 << 20
+EEMD_NOISE_SEED = 20210629 + 4  # seed of the white noise the library draws for the EEMD leg
 # DRAM bytes (read + write) of one k_pass launch of the default workload (256-sample tiles)
 # per pass-kernel variant, from an ncu capture of that launch with the dram__bytes counters
 # (cold caches, as ncu replays). Emptied whenever the pass kernel changes, until the changed
 # kernel is captured again; an empty entry is reported as null.
 PASS_TRAFFIC_TEXTURE = {}
+# FP64-pipe lane operations (sm__inst_executed_pipe_fp64 x 32) of one k_pass<double> launch
+# of the default workload, per (tile, variant), from an ncu capture of that launch; emptied
+# whenever the pass kernel changes.
+PASS_FP64_OPS_TEXTURE = {}
 
 
 def _peaks():
@@ -111,10 +116,12 @@ def workload_inputs(name: str, trials: int = 256):
                 "desc": "256x256 texture (gratings 4/16/64 px + N(0,0.05^2)), row-serialized, "
                         "D=0, L=65536, 10 sifts/IMF, <=10 IMFs, mirror boundary"}
     if name == "eemd512":
-        img, w = synth.workload_eemd_512(trials)
-        return {"X": img, "W": w, "K": 10, "S": 10, "D": 0, "trials": trials,
-                "desc": f"EEMD of a 512x512 grating image (L=262144), {trials} noise realizations "
-                        "(beta = 0.2 std), one batched run, 10 sifts/IMF, <=10 IMFs"}
+        img = synth.workload_eemd_512(1)[0]
+        return {"X": img, "W": None, "seed": EEMD_NOISE_SEED, "K": 10, "S": 10, "D": 0,
+                "trials": trials,
+                "desc": f"EEMD of a 512x512 grating image (L=262144), {trials} white-noise "
+                        "realizations drawn on the device (Philox4x32-10, uniform, unit "
+                        "variance; beta = 0.2 std), one batched run, 10 sifts/IMF, <=10 IMFs"}
     if name == "ceemdan_mask":
         X = synth.paper_mask_series()
         L = 6 * 1000 + 50 * 6 - 50
@@ -157,8 +164,10 @@ def run_ours(wl, precision, steps, warmup, device, flush, tile=0, tune=False, va
     if variant is not None:
         plan.pass_variant = variant
     x = torch.from_numpy(X).to(device)
-    noise = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).to(device) if wl["trials"] > 1 \
-        else None
+    noise = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).to(device) \
+        if wl["trials"] > 1 and wl["W"] is not None else None
+    if wl.get("seed") is not None:
+        plan.noise_seed = wl["seed"]
     imfs, res = plan.outputs(rows, cols, device=device)
     stream = torch.cuda.Stream(device)
     shape = None
@@ -228,8 +237,10 @@ def e2e_ours(wl, precision, steps, warmup, device):
                     fixed_sifts=wl["S"], ensemble_trials=wl["trials"])
     plan = Plan(p)
     hx = torch.from_numpy(X).pin_memory()
-    hn = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).pin_memory() if wl["trials"] > 1 \
-        else None
+    hn = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).pin_memory() \
+        if wl["trials"] > 1 and wl["W"] is not None else None
+    if wl.get("seed") is not None:
+        plan.noise_seed = wl["seed"]
     x = torch.empty_like(hx, device=device)
     noise = torch.empty_like(hn, device=device) if hn is not None else None
     imfs, res = plan.outputs(rows, cols, device=device)
@@ -275,23 +286,83 @@ def fp32_imf_errors(wl, run):
             for k in range(wl["K"])]
 
 
-def fp32_imf_errors_given_input(wl, run):
-    """Per-IMF relative L2 of the FP32 result against the oracle's IMF of the same input
-    remainder (x minus the GPU's earlier IMFs, rounded to single precision), untimed."""
+FP32_TAU = 2.0 ** -20  # knot decisions whose FP64 margin is below this (of max|h|) are ties
+
+
+def _fp32_replay(h32, S, shape, sift_plans):
+    """One IMF's sifting replayed two ways from the same single-precision input: the GPU's
+    FP32 chain (single sifts through the C ABI with the decomposition's pass shape) and the
+    oracle's FP64 chain. Returns (decisions agree at every sift, margin of the first
+    differing knot decision relative to max|h|, or None)."""
+    import torch
     from oracle import oracle as O
-    x = np.asarray(np.asarray(wl["X"], np.float32), np.float64).reshape(-1)
-    g = run["imfs"].double().cpu().numpy().reshape(wl["K"], -1)
+    from paper_2106_15319_gb300 import capi
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    key = (h32.size, shape)
+    if key not in sift_plans:
+        sp = Plan(make_params(1, max(h32.size, 8), precision=capi.FP32_MIXED))
+        sp.tile, sp.pass_variant = shape
+        sift_plans[key] = sp
+    sp = sift_plans[key]
+    g, o = h32.astype(np.float32), h32.copy()
+    for j in range(S):
+        ga, gb = O.extrema(g.astype(np.float64))
+        oa, ob = O.extrema(o)
+        if not (np.array_equal(ga, oa) and np.array_equal(gb, ob)):
+            m = 0.0
+            for q in np.concatenate([np.setxor1d(ga, oa), np.setxor1d(gb, ob)]):
+                d = [abs(o[q] - o[q - 1])] if q >= 1 else []
+                if q + 1 < o.size:
+                    d.append(abs(o[q + 1] - o[q]))
+                m = max(m, min(d))
+            return False, m / max(np.abs(h32).max(), np.abs(o).max(), 1e-300)
+        if j > 0 and (oa.size < 1 or ob.size < 1 or oa.size + ob.size < 3):
+            break
+        g = sp.sift(torch.from_numpy(g).to("cuda"))[0].cpu().numpy()
+        o = O.sift(o)[0]
+    return True, None
+
+
+def fp32_imf_errors_given_input(x, imfs, K, S, shape, sift_plans=None):
+    """Per-IMF relative L2 of an FP32 result against the oracle's IMF of the same input
+    remainder (x minus the GPU's earlier IMFs, rounded to single precision), untimed, and
+    per IMF whether its sifting took the FP64 chain's knot decisions at every sift (else the
+    FP64 margin of the first differing decision: a tie single precision cannot resolve)."""
+    from oracle import oracle as O
+    own = sift_plans is None
+    sift_plans = {} if own else sift_plans
+    x = np.asarray(x, np.float64).reshape(-1)
+    g = np.asarray(imfs, np.float64).reshape(K, -1)
     floor = 1e-6 * np.linalg.norm(x)
-    r, errs = x.copy(), []
-    for k in range(wl["K"]):
+    r, errs, exempt, margins = x.copy(), [], [], []
+    for k in range(K):
         if not np.any(g[k]):
             break
-        oi, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, fixed_sifts=wl["S"])
+        h32 = r.astype(np.float32).astype(np.float64)
+        oi, _, on, _ = O.emd(h32, 1, fixed_sifts=S)
         if on < 1:
             break
         errs.append(float(np.linalg.norm(g[k] - oi[0]) / max(np.linalg.norm(oi[0]), floor)))
+        same, margin = _fp32_replay(h32, S, shape, sift_plans)
+        exempt.append(not same)
+        margins.append(margin)
         r = r - g[k]
-    return errs
+    if own:
+        for sp in sift_plans.values():
+            sp.close()
+    return {"rel_l2": errs, "exempt": exempt, "exempt_margin": margins,
+            "max_rel_l2_not_exempt": max([e for e, x_ in zip(errs, exempt) if not x_],
+                                         default=None),
+            "n_exempt": int(sum(exempt)), "n_imfs": len(errs)}
+
+
+def _trial_noise(wl, m, L):
+    """Realization m of the EEMD leg's noise: the caller's array, or the library's
+    generator (Philox4x32-10, stated by the oracle)."""
+    from oracle import oracle as O
+    if wl["W"] is not None:
+        return np.asarray(wl["W"][m], np.float64)
+    return O.white_noise(wl["seed"], 1, L, first=m)[0]
 
 
 def _oracle_trial(args):
@@ -299,6 +370,8 @@ def _oracle_trial(args):
     x, w, beta, K, S = args
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
+    if isinstance(w, tuple):  # (seed, realization): drawn here by the generator
+        w = O.white_noise(w[0], 1, x.size, first=w[1])[0]
     _, _, _, sifts = O.emd(x + beta * w, K, fixed_sifts=S)
     return int(np.sum(sifts)) * x.size
 
@@ -337,13 +410,14 @@ def cpu_pool_eemd(wl, budget_s: float = 10.0):
     beta = 0.2 * O.std(x)
     cores = os.cpu_count() or 1
     with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
-        list(ex.map(_oracle_trial, [(x[:4096], wl["W"][m][:4096], beta, wl["K"], wl["S"])
-                                    for m in range(cores)]))  # start every worker
+        list(ex.map(_oracle_trial, [(x[:4096], _trial_noise(wl, m, x.size)[:4096], beta,
+                                     wl["K"], wl["S"]) for m in range(cores)]))  # warm up
         t0 = time.perf_counter()
         done, ss, m = 0, 0, 0
         while time.perf_counter() - t0 < budget_s and m < wl["trials"]:
             batch = range(m, min(m + cores, wl["trials"]))
-            ss += sum(ex.map(_oracle_trial, [(x, wl["W"][j], beta, wl["K"], wl["S"])
+            ss += sum(ex.map(_oracle_trial, [(x, wl["W"][j] if wl["W"] is not None
+                                              else (wl["seed"], j), beta, wl["K"], wl["S"])
                                              for j in batch]))
             done += len(batch)
             m += len(batch)
@@ -376,7 +450,8 @@ def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
         t0 = time.perf_counter()
         done, ss = 0, 0
         while time.perf_counter() - t0 < budget_s and done < wl["trials"]:
-            _, _, n, sifts = O.emd(x + beta * wl["W"][done], wl["K"], fixed_sifts=wl["S"])
+            _, _, n, sifts = O.emd(x + beta * _trial_noise(wl, done, x.size), wl["K"],
+                                   fixed_sifts=wl["S"])
             ss += int(np.sum(sifts)) * x.size
             done += 1
         el = time.perf_counter() - t0
@@ -503,12 +578,26 @@ def arm_ours(args):
     ms32_max = max_over_ranks(ms32, world)
     value = whole_job_rate(world, r32["sample_sifts"], ms32_max)
 
+    fp64_roof = None
     if "fp64" in args.forms:
         r64 = run_ours(wl, capi.FP64, args.steps, args.warmup, device, flush, args.tile,
                        tune=not args.no_tune)
         ms64 = max_over_ranks(statistics.mean(r64["ms"]), world)
         v64 = world * r64["sample_sifts"] / (ms64 * 1e-3)
         r64_shape = r64["shape"]
+        # the plain FP64 form is bound by GB300's narrow FP64 pipe: its pass kernel's FP64
+        # instructions per launch (ncu) against the measured FP64 FMA rate
+        prof64 = profile_pass(r64, 1, flush)
+        avg64 = prof64["pass_ms"] / max(1, prof64["pass_n"])
+        peak64 = capi.serial_emd_fma_rate(capi.FP64, 4096) / 2.0  # FMA lane-ops, G/s
+        ops = PASS_FP64_OPS_TEXTURE.get((r64_shape["tile"], r64_shape["variant"])) \
+            if args.workload == "texture256" else None
+        fp64_roof = {"bound": "alu", "kernel": "k_pass<double>", "unit": "G FP64 ops/s",
+                     "peak": peak64, "peak_source": "measured: serial_emd_fma_rate (FP64 "
+                     "FMA chains; 1 op = 1 lane FMA)", "avg_launch_us": avg64 * 1e3,
+                     "fp64_ops_per_launch": ops,
+                     "achieved": ops / (avg64 * 1e-3) / 1e9 if ops else None,
+                     "frac": ops / (avg64 * 1e-3) / 1e9 / peak64 if ops else None}
         r64["plan"].close()
     else:
         ms64, v64, r64_shape = None, None, None
@@ -539,7 +628,9 @@ def arm_ours(args):
                          "the 65536-sample working set is L2-resident within a step",
                    "parallelism": f"replicas x{world}"},
         "plain_fp64": {"value": v64, "ms_per_step": ms64, "dtype": "f64",
-                       "pass_shape": r64_shape},
+                       "pass_shape": r64_shape, "roofline": fp64_roof},
+        "fma_rate_gflops": {"fp64": capi.serial_emd_fma_rate(capi.FP64, 4096),
+                            "fp32": capi.serial_emd_fma_rate(capi.FP32_MIXED, 4096)},
         "speedup_fp32_vs_fp64": value / v64 if v64 else None,
         "fp32_imf_rel_l2": None,
         "roofline": {"bound": "hbm", "kernel": "k_pass<float>", "achieved": achieved,
@@ -561,12 +652,17 @@ def arm_ours(args):
     if rank == 0:
         if wl["trials"] == 1 and wl["D"] == 0:
             line["fp32_imf_rel_l2"] = fp32_imf_errors(wl, r32)
-            line["fp32_imf_rel_l2_given_input"] = fp32_imf_errors_given_input(wl, r32)
+            sh = r32["shape"]
+            line["fp32_imf_given_input"] = fp32_imf_errors_given_input(
+                np.asarray(np.asarray(wl["X"], np.float32), np.float64),
+                r32["imfs"].double().cpu().numpy(), wl["K"], wl["S"],
+                (sh["tile"], sh["variant"]))
         if not args.no_batched:
             line["batched"] = batched_eemd(args, device, flush, peak, peak_kind, world)
             line["batched_images"] = batched_images(args, device, flush, peak, peak_kind,
                                                     world)
         if not args.no_batched:
+            line["series_3x1024"] = series_leg(args, device, flush, world)
             line["standard_slices"] = standard_slices(args, device, flush, world)
             line["standard_slices"]["serial_over_slices_time"] = \
                 line["ms_per_step"] / line["standard_slices"]["ms_per_step"]
@@ -582,6 +678,7 @@ def arm_ours(args):
     elif not args.no_batched:  # the same collective calls as rank 0 (max over ranks)
         batched_eemd(args, device, flush, peak, peak_kind, world)
         batched_images(args, device, flush, peak, peak_kind, world)
+        series_leg(args, device, flush, world)
         standard_slices(args, device, flush, world)
         ceemdan_legs(args, device, flush, world)
         d_sweep(args, device, world)
@@ -610,10 +707,49 @@ def batched_eemd(args, device, flush, peak, peak_kind, world):
                         "peak_source": peak_kind, "avg_launch_us": pass_avg_ms * 1e3,
                         "bytes_per_launch": bpl, "launches": prof["pass_n"],
                         "reduce_avg_us": prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3}}
+    if int(os.environ.get("RANK", "0")) == 0 and not args.no_fp32_errors:
+        out["fp32_realizations_given_input"] = eemd_trial_errors(wl, r, args.error_trials)
     r["plan"].close()
+    if not args.no_e2e:
+        e2e_ms, e2e_ss, bi, bo = e2e_ours(wl, capi.FP32_MIXED, steps, min(args.warmup, 3),
+                                          device)
+        e2e_ms = max_over_ranks(e2e_ms, world)
+        out["e2e"] = {"value": world * e2e_ss / (e2e_ms * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                      "ms_per_step": e2e_ms,
+                      "note": "host buffers: the image in, the averaged IMFs and residue out; "
+                              "the noise is drawn on the device"}
     if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
         out["cpu_baseline_all_cores"] = cpu_pool_eemd(wl)
     return out
+
+
+def eemd_trial_errors(wl, r, ntrials):
+    """Per-IMF FP32 error of EEMD realizations 0..ntrials-1 (each read back from the
+    plan after the timed run), against the oracle's IMF of the same remainder, with the
+    knot-decision replay of fp32_imf_errors_given_input; untimed."""
+    from oracle import oracle as O
+    plan = r["plan"]
+    K, S = wl["K"], wl["S"]
+    x = O.serialize(np.asarray(np.asarray(wl["X"], np.float32), np.float64), wl["D"])
+    sh = r["shape"]
+    shape = (sh["tile"], sh["variant"])
+    sift_plans, per = {}, []
+    for m in range(ntrials):
+        imfs, _, n, beta = plan.eemd_trial(m)
+        wm = _trial_noise(wl, m, x.size)
+        if wl["W"] is not None:  # the caller's noise is stored in the plan's precision
+            wm = np.asarray(np.asarray(wm, np.float32), np.float64)
+        xm = x + beta * wm
+        per.append(fp32_imf_errors_given_input(xm, imfs.double().cpu().numpy(), K, S, shape,
+                                               sift_plans))
+    for sp in sift_plans.values():
+        sp.close()
+    ok = [e for d in per for e, x_ in zip(d["rel_l2"], d["exempt"]) if not x_]
+    return {"realizations": ntrials, "per_realization": per,
+            "max_rel_l2_not_exempt": max(ok, default=None),
+            "n_exempt": int(sum(d["n_exempt"] for d in per)),
+            "n_imfs": int(sum(d["n_imfs"] for d in per))}
 
 
 def batched_images(args, device, flush, peak, peak_kind, world):
@@ -677,9 +813,10 @@ def serving(args, device):
     """The serving mix: Poisson arrivals of requests, half tone+chirp series (2..16
     channels x 1k..64k samples), half grating images (side 32..1024 px, plus a 2 % tail
     of 2048^2 images), transitions D = round(0.2 M), FP32-mixed, 10 sifts/IMF, <= 10
-    IMFs, one server with a 40 GB device budget and 64 slots. Each rate's requests are
-    submitted at their arrival times; latency is the server's submit -> outputs-written
-    time (queue + run)."""
+    IMFs, one server with a 40 GB device budget and 64 slots. One set of requests is drawn
+    (arrival gaps at rate 1, scaled by 1/rate for each rate); each rate's requests are
+    submitted at their arrival times, and "saturation" submits them all at once. Latency
+    is the server's submit -> outputs-written time (queue + run)."""
     import time as _t
     import torch
     from paper_2106_15319_gb300 import capi, synth
@@ -690,20 +827,24 @@ def serving(args, device):
                        "images 32..1024 px (+2% 2048^2), D=round(0.2 M), FP32-mixed, 10 "
                        "sifts/IMF, <=10 IMFs, 40 GB budget, 64 slots",
            "latency": "submit -> outputs written, measured by the server", "rates": []}
+    nreq = args.serve_requests
+    mix = synth.serving_mix(nreq, 20210629 + 5, 1.0)
+    xs = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device) for _, _, a in mix]
     server = Server(base, 40 << 30, 64)
+    outs = [server.outputs(*x.shape, device=device) for x in xs]
+    torch.cuda.synchronize()
+    sizes = [serialized_length(*x.shape) for x in xs]
     try:
-        for rate in args.serve_rates:
-            mix = synth.serving_mix(args.serve_requests, 20210629 + 5, rate)
-            xs = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
-                  for _, _, a in mix]
-            outs = [server.outputs(*x.shape, device=device) for x in xs]
-            torch.cuda.synchronize()
+        for rate in list(args.serve_rates) + [float("inf")]:
+            # slow rates: a bounded prefix of the requests, so that the leg ends in minutes
+            n = nreq if rate >= 100 else min(nreq, int(args.serve_slow_seconds * rate))
+            arr = [0.0 if rate == float("inf") else mix[k][0] / rate for k in range(n)]
             pend, res = {}, {}
             t0 = _t.perf_counter()
             i = 0
-            while i < len(mix) or pend:
+            while i < n or pend:
                 now = _t.perf_counter() - t0
-                while i < len(mix) and mix[i][0] <= now:
+                while i < n and arr[i] <= now:
                     t, _, _ = server.submit(xs[i], outs[i][0], outs[i][1])
                     pend[t] = i
                     i += 1
@@ -711,23 +852,43 @@ def serving(args, device):
                     r = server.poll(t)
                     if r is not None:
                         res[pend.pop(t)] = (r, _t.perf_counter() - t0)
-                if i < len(mix) and not pend:
-                    _t.sleep(max(0.0, min(mix[i][0] - now, 0.002)))
+                if i < n and not pend:
+                    _t.sleep(max(0.0, min(arr[i] - now, 0.002)))
                 elif pend:
                     _t.sleep(0.0002)
-            wall = max(v[1] for v in res.values()) - mix[0][0]
+            wall = max(v[1] for v in res.values()) - arr[0]
             lat = np.array([r.queue_ms + r.run_ms for r, _ in res.values()])
-            ss = sum(r.sifts * serialized_length(*xs[k].shape) for k, (r, _) in res.items())
+            ss = sum(r.sifts * sizes[k] for k, (r, _) in res.items())
             ok = all(r.status == capi.SEMD_OK for r, _ in res.values())
             out["rates"].append({
-                "rate_hz": rate, "requests": len(mix), "all_ok": bool(ok),
+                "rate_hz": "saturation" if rate == float("inf") else rate, "requests": n,
+                "all_ok": bool(ok),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "max_ms": float(lat.max()),
-                "served_per_s": len(mix) / wall, "samples_sifts_per_s": ss / wall,
-                "samples": int(sum(serialized_length(*x.shape) for x in xs))})
-            del xs, outs
+                "served_per_s": n / wall, "samples_sifts_per_s": ss / wall,
+                "samples": int(sum(sizes[:n]))})
     finally:
         server.close()
+    del xs, outs
+    return out
+
+
+def series_leg(args, device, flush, world):
+    """The 3-channel series (3 x 1024 samples, tones + chirp + noise, D = 0, L = 3072, 10
+    sifts per IMF, at most 8 IMFs), plain FP64 and FP32-mixed, one decomposition per step,
+    beside the oracle on one host core."""
+    from paper_2106_15319_gb300 import capi
+    wl = workload_inputs("series3x1024")
+    out = {"workload": wl["desc"]}
+    for tag, prec in (("fp64", capi.FP64), ("fp32", capi.FP32_MIXED)):
+        r = run_ours(wl, prec, max(1, min(args.steps, 10)), min(args.warmup, 3), device, flush,
+                     tune=not args.no_tune)
+        ms = max_over_ranks(statistics.mean(r["ms"]), world)
+        out[tag] = {"ms_per_step": ms, "value": world * r["sample_sifts"] / (ms * 1e-3),
+                    "unit": UNIT, "pass_shape": r["shape"], "cuda_graph": bool(r["graph"])}
+        r["plan"].close()
+    if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
+        out["cpu_baseline"] = cpu_baseline(wl, budget_s=3.0)
     return out
 
 
@@ -963,14 +1124,21 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--images", type=int, default=2048, help="batched uneven images")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 300.0, 1000.0])
-    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--serve-rates", type=float, nargs="+",
+                    default=[10.0, 30.0, 100.0, 300.0, 1000.0])
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-slow-seconds", type=float, default=30.0,
+                    help="rates below 100/s submit at most this many seconds of arrivals")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass shape (no autotuning before the warm-up)")
     ap.add_argument("--only-leg", default=None,
                     choices=["batched", "images", "slices", "ceemdan", "dsweep", "serving"],
                     help="run one extra leg alone and print its result (for profiling)")
+    ap.add_argument("--no-fp32-errors", action="store_true",
+                    help="skip the untimed FP32 per-IMF error report of the EEMD leg")
+    ap.add_argument("--error-trials", type=int, default=4,
+                    help="EEMD realizations whose FP32 IMFs are checked against the oracle")
     ap.add_argument("--pass-variant", type=int, default=None, choices=[0, 1],
                     help="register budget of the FP32 pass kernel (no autotuning)")
     args = ap.parse_args()

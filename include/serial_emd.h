@@ -139,7 +139,13 @@ size_t serial_emd_plan_bytes(semd_plan_t plan);
  * de-serialize), enqueued on `stream`.
  *  d_x        input, rows x cols (plan precision).
  *  d_noise    EEMD only: ensemble_trials x L white-noise realizations w^(m)
- *             (plan precision, L = MN + DN - D); ignored for EMD.
+ *             (plan precision, L = MN + DN - D), or NULL: the library then draws the
+ *             noise itself, on the device, from the plan's noise seed
+ *             (serial_emd_plan_set_noise_seed): sample p of realization m is word
+ *             p mod 4 of the Philox4x32-10 block (Salmon et al., SC 2011) with counter
+ *             (p div 4, m, 0, 0) and key (seed low, seed high), mapped from the word u
+ *             to (2 (u >> 9) - (2^23 - 1)) * sqrt(3) / 2^23 in FP64: white noise,
+ *             uniform with zero mean and unit variance. Ignored for EMD.
  *  d_imfs     output, K x rows x cols (plan precision); for EEMD the trial average.
  *  d_residue  output, rows x cols doubles; may be NULL.
  *  n_imfs     host; if not NULL the call waits for the stream and stores the IMF
@@ -150,6 +156,10 @@ size_t serial_emd_plan_bytes(semd_plan_t plan);
  */
 semd_status serial_emd_decompose(semd_plan_t plan, const void *d_x, const void *d_noise,
                                  void *d_imfs, double *d_residue, int *n_imfs, void *stream);
+
+/* Seed of the white noise the library draws for EEMD calls that pass no noise (default
+ * 0). Takes effect at the next call. Errors: EINVAL (NULL plan). */
+semd_status serial_emd_plan_set_noise_seed(semd_plan_t plan, uint64_t seed);
 
 /* One input of a batch: its own shape (within the plan's capacity) and buffers. */
 typedef struct semd_instance {
@@ -207,6 +217,19 @@ semd_status serial_emd_decompose_slices(semd_plan_t plan, const void *d_x, int64
  */
 semd_status serial_emd_ceemdan(semd_plan_t plan, const void *d_x, const void *d_noise,
                                void *d_modes, double *d_residue, int *n_modes, void *stream);
+
+/*
+ * One realization of the plan's last EEMD call (Sec. 2.2: realization m is the EMD of
+ * x + beta w^(m), serialized as in Sec. 3.2), for callers that need the ensemble's spread
+ * and not only its average: writes its IMFs de-serialized to d_imfs (K x rows x cols,
+ * plan precision, zero past the realization's IMF count) and, if d_residue is not NULL,
+ * its residue (rows x cols doubles), enqueued on `stream`. If n_imfs or beta (host) is
+ * not NULL the call waits for the stream and stores the realization's IMF count and the
+ * beta of that call. The plan must be an ensemble plan whose last call was
+ * serial_emd_decompose; trial in [0, ensemble_trials). Errors: EINVAL, ECUDA.
+ */
+semd_status serial_emd_eemd_trial(semd_plan_t plan, int trial, void *d_imfs, double *d_residue,
+                                  int *n_imfs, double *beta, void *stream);
 
 /* After the stream has finished: IMF counts (count entries) and sifts per IMF
  * (count x K entries, may be NULL) of the plan's last decompose call (for a CEEMDAN
@@ -375,6 +398,16 @@ semd_status serial_emd_plan_stats(semd_plan_t plan, semd_stats *out);
  */
 int64_t serial_emd_plan_launch_times(semd_plan_t plan, int kind, float *ms, int64_t cap);
 
+/*
+ * Measured fused-multiply-add rate of the current GPU in the arithmetic of `precision`
+ * (SEMD_FP64: double, SEMD_FP32_MIXED: float), in GFLOP/s (2 flops per FMA): a probe kernel
+ * of independent register-resident FMA chains (iters per chain, e.g. 4096), timed with
+ * CUDA events on `stream`; waits for the stream. It is the arithmetic peak against which
+ * the plain FP64 form, bound by GB300's narrow FP64 pipe, is reported. Allocates a small
+ * output buffer (stream-ordered) and changes no GPU setting. Errors: EINVAL, ECUDA.
+ */
+semd_status serial_emd_fma_rate(int precision, int iters, double *gflops, void *stream);
+
 /* Releases a plan and its workspaces (after its work on any stream has finished). */
 void serial_emd_destroy(semd_plan_t plan);
 
@@ -387,9 +420,14 @@ const char *serial_emd_last_error(semd_plan_t plan);
 /*
  * A server decomposes requests of different shapes as they arrive (continuous
  * batching): a host thread admits queued requests whenever slots and the byte
- * budget allow, runs one pass of the sifting loop over every admitted request at
+ * budget allow, runs a few passes of the sifting loop over every admitted request at
  * once, and retires requests as they finish, so new ones join while others are on
  * the GPU. Per-request results are identical to decomposing the request alone.
+ * Requests of at least 2^21 serialized samples run in a second lane with its own host
+ * thread and a lower-priority stream, whose pass launches keep to two CTAs per SM, so
+ * that they run beside the small requests' passes instead of lengthening them; that
+ * lane holds max(1, max_inflight / 8) requests at a time. Both lanes share the byte
+ * budget.
  *  defaults     method parameters; rows/cols give the largest accepted request
  *               (its serialized length must not exceed that of rows x cols).
  *  mem_budget   device bytes the server may hold for request state (> 0).
@@ -425,6 +463,13 @@ semd_status serial_emd_submit(semd_server_t server, const semd_request *req, uin
 /* Non-blocking: SEMD_PENDING while the request is queued or running; otherwise
  * fills *out (once) and returns SEMD_OK. EINVAL for an unknown ticket. */
 semd_status serial_emd_poll(semd_server_t server, uint64_t ticket, semd_result *out);
+
+/* Blocking form of serial_emd_poll with a time limit: waits up to timeout_ms (>= 0) for
+ * the request to finish, then fills *out (once) and returns SEMD_OK, or returns
+ * SEMD_ETIMEOUT with the request still pending (it may be waited for again). EINVAL for
+ * an unknown ticket or a negative limit. */
+semd_status serial_emd_wait(semd_server_t server, uint64_t ticket, double timeout_ms,
+                            semd_result *out);
 
 /* Stops the server thread; unfinished requests end with SEMD_ECANCELED. */
 void serial_emd_server_destroy(semd_server_t server);

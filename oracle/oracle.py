@@ -69,6 +69,11 @@ def lib():
                                      _dp, _dp, _ipint, ctypes.c_int]
             L.oracle_zero_crossings.restype = _i64
             L.oracle_zero_crossings.argtypes = [_dp, _i64]
+            L.oracle_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32),
+                                               ctypes.POINTER(ctypes.c_uint32),
+                                               ctypes.POINTER(ctypes.c_uint32)]
+            L.oracle_white_noise.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _i64,
+                                             _dp]
             L.oracle_std.restype = ctypes.c_double
             L.oracle_std.argtypes = [_dp, _i64]
             L.oracle_eemd.restype = ctypes.c_int
@@ -280,6 +285,23 @@ def serial_ceemdan(X, D: int, K: int, w, noise_rel_std: float, stop: int = STOP_
                                     max_sifts, boundary, mirror_knots, trials, noise_rel_std,
                                     _d(w), _d(modes), _d(res), int(store_f32))
     return modes, res, int(n)
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block (Salmon et al., SC 2011) of 4 counter and 2 key words."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def white_noise(seed: int, trials: int, L: int, first: int = 0) -> np.ndarray:
+    """Reading 11b: the white noise the library draws itself for EEMD, realizations
+    first .. first + trials - 1, (trials, L)."""
+    w = np.empty((trials, L), np.float64)
+    lib().oracle_white_noise(ctypes.c_uint64(seed), first, trials, L, _d(w))
+    return w
 
 
 def zero_crossings(h) -> int:

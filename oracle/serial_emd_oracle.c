@@ -48,6 +48,15 @@
  *   Reading 11 EEMD noise is added to the serialized signal; beta is
  *              noise_rel_std times the population std of x; trials with fewer
  *              IMFs contribute zeros to the average.
+ *   Reading 11b white noise drawn by the library itself (when the caller passes no
+ *              noise): realization m, serialized sample p takes 32-bit word p mod 4
+ *              of the Philox4x32-10 block with counter (p div 4, m, 0, 0) and key
+ *              (seed low word, seed high word) (Salmon, Moraes, Dror and Shaw,
+ *              "Parallel random numbers: as easy as 1, 2, 3", SC 2011); the word u
+ *              gives the odd integer i = 2 (u >> 9) - (2^23 - 1) and the sample
+ *              w = i * (sqrt(3) / 2^23) in FP64, uniform on (-sqrt 3, sqrt 3): zero
+ *              mean, unit variance, independent samples (white). The paper asks for
+ *              white noise of a given deviation without naming its distribution.
  *   Reading 12 CEEMDAN (Sec. 2.2, Steps 1-4): E_k(w) is the k-th EMD mode of the
  *              noise realization w (zero past its IMF count). Stage k = 0, 1, ...
  *              starts from the residue r_k (r_0 = x) and runs only if r_k passes
@@ -499,6 +508,56 @@ int oracle_eemd(const double *x, int64_t L, const double *w, int trials, double 
     free(cm);
     free(rm);
     return nmax;
+}
+
+/* ------------------------------------- Sec. 2.2, white noise (Reading 11b) */
+
+/* One Philox4x32-10 block (Salmon et al., SC 2011): ten rounds of two 32 x 32 -> 64-bit
+ * products of counter words with the round multipliers, whose high halves are mixed with
+ * the other counter words and the round key, and a Weyl-sequence bump of the key between
+ * rounds. */
+void oracle_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t *out)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u; /* round multipliers */
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u; /* key increments */
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    int r;
+    for (r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* w (trials x L): realizations first .. first + trials - 1 for the seed, Reading 11b. */
+void oracle_white_noise(uint64_t seed, int first, int trials, int64_t L, double *w)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const double scale = 1.7320508075688772 / 8388608.0; /* sqrt(3) / 2^23 */
+    int m;
+    int64_t p;
+    for (m = 0; m < trials; ++m) {
+        for (p = 0; p < L; ++p) {
+            const uint32_t ctr[4] = {(uint32_t)(p >> 2), (uint32_t)(first + m), 0u, 0u};
+            uint32_t out[4];
+            int32_t i;
+            oracle_philox4x32_10(ctr, key, out);
+            i = (int32_t)(2u * (out[p & 3] >> 9)) - 8388607;
+            w[(int64_t)m * L + p] = (double)i * scale;
+        }
+    }
 }
 
 /* ---------------------------------------------------- Sec. 2.2, CEEMDAN */

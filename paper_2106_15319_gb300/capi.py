@@ -82,6 +82,7 @@ SIGNATURES = {
     "serial_emd_decompose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "serial_emd_plan_set_noise_seed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "serial_emd_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                                   ctypes.POINTER(semd_instance),
                                                   ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
@@ -92,6 +93,9 @@ SIGNATURES = {
     "serial_emd_ceemdan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "serial_emd_eemd_trial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "serial_emd_plan_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
@@ -129,6 +133,8 @@ SIGNATURES = {
     "serial_emd_plan_launch_times": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int,
                                                       ctypes.POINTER(ctypes.c_float),
                                                       ctypes.c_int64]),
+    "serial_emd_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
     "serial_emd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "serial_emd_server_create": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_size_t,
@@ -136,6 +142,8 @@ SIGNATURES = {
     "serial_emd_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(semd_request),
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "serial_emd_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.POINTER(semd_result)]),
+    "serial_emd_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double,
                                        ctypes.POINTER(semd_result)]),
     "serial_emd_server_destroy": (None, [ctypes.c_void_p]),
     "serial_emd_server_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -270,17 +278,22 @@ def _need_decompose(plan: int, x, noise, imfs, residue, ensemble_needs_noise: bo
     _need(x, "x", p.precision, rc)
     _need(imfs, "imfs", p.precision, p.max_imfs * rc)
     _need(residue, "residue", FP64, rc, optional=True)
-    if p.ensemble_trials > 1 and ensemble_needs_noise:
+    if p.ensemble_trials > 1 and (ensemble_needs_noise or noise is not None):
         _need(noise, "noise", p.precision, p.ensemble_trials * _serial_len(p, p.rows, p.cols))
 
 
 def serial_emd_decompose(plan: int, x, noise, imfs, residue, stream=None, wait: bool = True):
-    _need_decompose(plan, x, noise, imfs, residue, True)
+    """noise: the EEMD realizations, or None to let the library draw them (EEMD plans)."""
+    _need_decompose(plan, x, noise, imfs, residue, False)
     n = ctypes.c_int(-1)
     rc = load().serial_emd_decompose(plan, _ptr(x), _ptr(noise), _ptr(imfs), _ptr(residue),
                                      ctypes.byref(n) if wait else None, _stream(stream))
     _check(rc, plan)
     return n.value if wait else None
+
+
+def serial_emd_plan_set_noise_seed(plan: int, seed: int) -> None:
+    _check(load().serial_emd_plan_set_noise_seed(plan, seed), plan)
 
 
 def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True):
@@ -324,6 +337,20 @@ def serial_emd_ceemdan(plan: int, x, noise, modes, residue, stream=None, wait: b
                                    ctypes.byref(n) if wait else None, _stream(stream))
     _check(rc, plan)
     return n.value if wait else None
+
+
+def serial_emd_eemd_trial(plan: int, trial: int, imfs, residue=None, stream=None):
+    """Realization `trial` of the plan's last EEMD call: fills imfs (K, rows, cols) and
+    residue; returns (its IMF count, beta of the call)."""
+    p = _PLAN_PARAMS.get(plan)
+    if p is not None:
+        _need(imfs, "imfs", p.precision, p.max_imfs * p.rows * p.cols)
+        _need(residue, "residue", FP64, p.rows * p.cols, optional=True)
+    n, beta = ctypes.c_int(-1), ctypes.c_double()
+    rc = load().serial_emd_eemd_trial(plan, trial, _ptr(imfs), _ptr(residue), ctypes.byref(n),
+                                      ctypes.byref(beta), _stream(stream))
+    _check(rc, plan)
+    return n.value, beta.value
 
 
 def serial_emd_plan_counts(plan: int, count: int, max_imfs: int):
@@ -459,6 +486,15 @@ def serial_emd_plan_launch_times(plan: int, kind: int) -> list[float]:
     return list(buf[:n])
 
 
+def serial_emd_fma_rate(precision: int, iters: int = 4096, stream=None) -> float:
+    """Measured FMA throughput (GFLOP/s) of the current GPU in FP64 or FP32."""
+    g = ctypes.c_double()
+    rc = load().serial_emd_fma_rate(precision, iters, ctypes.byref(g), _stream(stream))
+    if rc != 0:
+        raise SemdError(rc, "fma rate probe failed")
+    return g.value
+
+
 def serial_emd_destroy(plan: int) -> None:
     if plan:
         _PLAN_PARAMS.pop(plan, None)
@@ -501,6 +537,17 @@ def serial_emd_poll(server: int, ticket: int):
     r = semd_result()
     rc = load().serial_emd_poll(server, ticket, ctypes.byref(r))
     if rc == SEMD_PENDING:
+        return None
+    _check(rc, server, "serial_emd_server_last_error")
+    return r
+
+
+def serial_emd_wait(server: int, ticket: int, timeout_ms: float):
+    """Waits up to timeout_ms for the request; returns its semd_result, or None when the
+    limit ran out (SEMD_ETIMEOUT: the request is still pending)."""
+    r = semd_result()
+    rc = load().serial_emd_wait(server, ticket, float(timeout_ms), ctypes.byref(r))
+    if rc == SEMD_ETIMEOUT:
         return None
     _check(rc, server, "serial_emd_server_last_error")
     return r

@@ -413,6 +413,8 @@ __device__ __forceinline__ void storen(T *p, int k0, int cnt, const T (&v)[N])
 
 // Knots (tile position and value) of this lane's samples into the pool in rank order:
 // maxima at slots 1 + bx.., minima at slots m0 + 3 + bn...
+// A sample is at most one kind of extremum, so each sample takes at most one store: the
+// slot of its kind's next knot.
 template <typename R, int SPL, int TW>
 __device__ __forceinline__ void knot_compact(WarpPool<R, TW> &P, const R (&v)[SPL], int k0,
                                              uint32_t MX, uint32_t MN, int bx, int bn, int m0)
@@ -420,10 +422,11 @@ __device__ __forceinline__ void knot_compact(WarpPool<R, TW> &P, const R (&v)[SP
     int ix = 1 + bx, in = m0 + 3 + bn;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {
-        if ((MX >> s) & 1u)
-            P.ky[ix++] = KnotY<R>{k0 + s, v[s]};
-        if ((MN >> s) & 1u)
-            P.ky[in++] = KnotY<R>{k0 + s, v[s]};
+        const int px = (int)((MX >> s) & 1u), pn = (int)((MN >> s) & 1u);
+        if (px | pn)
+            P.ky[px ? ix : in] = KnotY<R>{k0 + s, v[s]};
+        ix += px;
+        in += pn;
     }
 }
 
@@ -927,9 +930,12 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         // their mean, the subtraction, and the SD partial sums. A lane's samples share
         // few intervals: an interval's cubic is read when a knot starts it, and the local
         // coordinate u = k - t_left advances by exact integer steps in between.
+        // The local coordinates are kept as floating-point integers (exact: |u| < 2^24),
+        // advanced by 1 per sample and reset to 0 at a knot, instead of converting k - t.
         int q0 = bx + (MX & 1u), q1 = b1 + bn + (MN & 1u);
         Coef<R> c0 = P.cf[q0], c1 = P.cf[q1];
         int t0 = P.ky[q0].t, t1 = P.ky[q1].t;
+        R u0 = R(k0 - t0), u1 = R(k0 - t1);
 #pragma unroll
         for (int s = 0; s < SPL; ++s) {
             const int k = k0 + s;
@@ -938,21 +944,25 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
                     ++q0;
                     c0 = P.cf[q0];
                     t0 = k;
+                    u0 = R(0);
                 }
                 if ((MN >> s) & 1u) {
                     ++q1;
                     c1 = P.cf[q1];
                     t1 = k;
+                    u1 = R(0);
                 }
             }
-            const R e0 = horner(c0, R(k - t0));
-            const R e1 = horner(c1, R(k - t1));
+            const R e0 = horner(c0, u0);
+            const R e1 = horner(c1, u1);
             const R mean = radd(e0, e1);
             hn[s] = rsub(v[s], mean);
             if (pa.need_sd && k < cnt) {
                 pn += mean * mean;
                 pd += v[s] * v[s];
             }
+            u0 = radd(u0, R(1));
+            u1 = radd(u1, R(1));
         }
         // the instance's last sample when it is a knot (the end-point rule puts one there,
         // as the right bracket of both envelopes): the envelopes take the knot values there

@@ -87,9 +87,42 @@ __global__ void k_std(const Inst *inst, double rel, double *beta)
         *beta = rel * sqrt(sh[0] / (double)L);
 }
 
-// x^(m) = x + beta w^(m) for every trial (Sec. 2.2 Step 1); trial 0 holds x on entry.
+// One Philox4x32-10 block (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC 2011): ten rounds of two 32 x 32 -> 64-bit products of counter
+// words with the round multipliers, the high halves mixed with the other counter words and
+// the round key, the key bumped by a Weyl sequence between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// White noise drawn by the library (Sec. 2.2 asks for white noise of a given deviation):
+// realization m, serialized sample p takes word p mod 4 of the Philox block with counter
+// (p div 4, m, 0, 0) and key (seed low word, seed high word); the word u gives the odd
+// integer i = 2 (u >> 9) - (2^23 - 1) and the sample i * sqrt(3) / 2^23, uniform on
+// (-sqrt 3, sqrt 3) with zero mean and unit variance.
+__device__ __forceinline__ double white_sample(uint64_t seed, int m, int64_t p)
+{
+    const uint4 b = philox4x32_10(make_uint4((uint32_t)(p >> 2), (uint32_t)m, 0u, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const int j = (int)(p & 3);
+    const uint32_t u = j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+    const int32_t i = (int32_t)(2u * (u >> 9)) - 8388607;
+    return __dmul_rn((double)i, 1.7320508075688772 / 8388608.0);
+}
+
+// x^(m) = x + beta w^(m) for every trial (Sec. 2.2 Step 1); trial 0 holds x on entry. The
+// noise is the caller's (inst[0].noise) or, when that is null, drawn here from the seed.
 template <typename R>
-__global__ void k_add_noise(const Inst *inst, int trials, const double *beta)
+__global__ void k_add_noise(const Inst *inst, int trials, const double *beta, uint64_t seed)
 {
     const int64_t L = inst[0].L;
     const R *w = (const R *)inst[0].noise;
@@ -97,8 +130,10 @@ __global__ void k_add_noise(const Inst *inst, int trials, const double *beta)
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L;
          p += (int64_t)gridDim.x * blockDim.x) {
         const double x = inst[0].r[0][p];
-        for (int m = trials - 1; m >= 0; --m)
-            inst[m].r[0][p] = __dadd_rn(x, __dmul_rn(b, (double)w[(int64_t)m * L + p]));
+        for (int m = trials - 1; m >= 0; --m) {
+            const double wv = w ? (double)w[(int64_t)m * L + p] : white_sample(seed, m, p);
+            inst[m].r[0][p] = __dadd_rn(x, __dmul_rn(b, wv));
+        }
     }
 }
 
@@ -160,6 +195,30 @@ __global__ void k_eemd_average(const Inst *inst, const State *state, int trials,
                 acc += inst[m].r[state[m].rpar][p];
             res[dst] = acc / (double)trials;
         }
+    }
+}
+
+// One EEMD realization's IMFs and residue as the last decomposition left them (Sec. 2.2:
+// trial m is the EMD of x + beta w^(m)), de-serialized (Sec. 3.3); IMF slots past the
+// trial's count are zero.
+template <typename R>
+__global__ void k_eemd_trial(const Inst *inst, const State *state, int m, int K, const R *scratch,
+                             R *out, double *res)
+{
+    const Inst &in = inst[m];
+    const int n = state[m].imf_count;
+    const double *r = in.r[state[m].rpar];
+    const int64_t MN = in.M * in.N;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < in.L;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t dst;
+        if (!deser_index(p, in.M, in.N, in.D, in.order, dst))
+            continue;
+        for (int k = 0; k < K; ++k)
+            out[(int64_t)k * MN + dst] =
+                k < n ? scratch[((int64_t)m * K + k) * in.imf_stride + p] : R(0);
+        if (res)
+            res[dst] = r[p];
     }
 }
 
@@ -502,10 +561,18 @@ int pass_ctas_per_sm_max(size_t elem, int tile, int variant)
 // Launches with programmatic stream serialization: the kernel's CTAs may start while the
 // previous kernel of the stream finishes (each waits in pdl_wait before reading its
 // results), which hides the launch gap between the passes and the interface solves.
+// Set while the body of a device-decided sifting loop is captured: kernels inside a
+// conditional graph node are launched without programmatic stream serialization.
+static thread_local bool g_plain_launches = false;
+
 template <typename K, typename A>
 static void launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem, cudaStream_t s,
                        const A &arg)
 {
+    if (g_plain_launches) {
+        kernel<<<grid, block, smem, s>>>(arg);
+        return;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -677,7 +744,7 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {(void **)&d_taux, (size_t)tiles * sizeof(TileAux)},
         {(void **)&d_kmask, (size_t)tiles * 32 * sizeof(uint2)},
         {(void **)&d_rscr, (size_t)rentries * 8},
-        {(void **)&d_active, (size_t)iters * 4},
+        {(void **)&d_active, (size_t)(iters + 8) * 4},
         {(void **)&d_beta, 8},
         {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
         {(void **)&d_stats, sizeof(Stats)},
@@ -703,6 +770,7 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
     cudaError_t e = cudaMalloc(&base, total);
     if (e != cudaSuccess) {
         err = std::string("cudaMalloc of the workspace: ") + cudaGetErrorString(e);
+        (void)cudaGetLastError(); // a failed allocation must not surface in later calls
         base = nullptr;
         return e == cudaErrorMemoryAllocation ? SEMD_ENOMEM : SEMD_ECUDA;
     }
@@ -870,10 +938,29 @@ struct LaunchTimer {
     }
 };
 
+// Iterations of the body of a device-decided sifting loop.
+constexpr int kLoopBody = 4;
+
+// End of one body execution of a device-decided sifting loop (Sec. 2.1 Step 5 with an
+// adaptive stop rule): the loop goes on while the body's last interface solve counted a
+// running instance and the iteration cap is not reached. Clears the body's counters for
+// its next execution.
+__global__ void k_loop_control(cudaGraphConditionalHandle h, int32_t *active, int32_t *iter,
+                               int max_iters)
+{
+    const int it = *iter + kLoopBody;
+    const bool more = active[kLoopBody - 1] > 0 && it < max_iters;
+    *iter = it;
+    for (int b = 0; b < kLoopBody; ++b)
+        active[b] = 0;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // The sifting passes of one decomposition: `iters` pass + interface-solve launches (the
-// state machine idles finished instances). With an adaptive stop rule (SD, S-number) and
-// no capture, every eighth iteration reads the count of running instances and ends the
-// loop at zero.
+// state machine idles finished instances). With an adaptive stop rule (SD, S-number):
+// under capture, a WHILE conditional node whose body runs kLoopBody iterations and then
+// decides on the device whether to go on (no host synchronization); without capture,
+// every eighth iteration reads the count of running instances and ends the loop at zero.
 template <typename R>
 static semd_status sift_loop(semd_plan_s &pl, ReduceArgs ra, int ninst, int64_t ntiles,
                              int iters, cudaStream_t s, Profiler *prof, bool capture,
@@ -882,6 +969,42 @@ static semd_status sift_loop(semd_plan_s &pl, ReduceArgs ra, int ninst, int64_t 
     Workspace &ws = pl.ws;
     std::string &err = pl.err;
     const bool sd = ra.stop == SEMD_STOP_SD, zc = ra.stop == SEMD_STOP_SNUMBER;
+    if (capture && (sd || zc)) {
+        cudaStreamCaptureStatus cs;
+        unsigned long long id = 0;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *ed = nullptr;
+        size_t nd = 0;
+        SEMD_CU(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd));
+        cudaGraphConditionalHandle h;
+        SEMD_CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t cn;
+        SEMD_CU(cudaGraphAddNode(&cn, g, deps, ed, nd, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        SEMD_CU(cudaStreamBeginCaptureToGraph(pl.lstream, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+        g_plain_launches = true;
+        for (int b = 0; b < kLoopBody; ++b) {
+            launch_pass<R>(ws, ntiles, sd, zc, pl.lstream);
+            ra.active = ws.d_active + b;
+            launch_reduce<R>(ra, ninst, pl.lstream);
+        }
+        g_plain_launches = false;
+        k_loop_control<<<1, 1, 0, pl.lstream>>>(h, ws.d_active, ws.d_active + kLoopBody, iters);
+        cudaGraph_t bo = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(pl.lstream, &bo);
+        SEMD_CU(ce);
+        SEMD_CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies));
+        launches += 2 * kLoopBody + 1; // per body execution
+        return SEMD_OK;
+    }
     for (int it = 0; it < iters; ++it) {
         {
             LaunchTimer t(prof, s, 0);
@@ -918,14 +1041,14 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
     int64_t launches = 0;
     const int iters = max_iterations(p);
     SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)ninst * sizeof(State), s));
-    SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
+    SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)(iters + kLoopBody + 1) * 4, s));
     SEMD_CU(cudaMemsetAsync(ws.d_stats, 0, sizeof(Stats), s));
     k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
                                                       ws.tile, eemd ? 1 : 0);
     ++launches;
     if (eemd) {
         k_std<<<1, 1024, 0, s>>>(ws.d_inst, p.noise_rel_std, ws.d_beta);
-        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, ws.d_beta);
+        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, ws.d_beta, pl.noise_seed);
         launches += 2;
     }
     ReduceArgs ra = reduce_args(ws, p);
@@ -993,11 +1116,11 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     if (st != SEMD_OK)
         return st;
     const int ntiles0 = ws.h_inst[0].ntiles;
-    const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
+    const bool use_graph = pl.graphs && !pl.prof.on;
     pl.prof.reset();
     if (use_graph) {
         const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile, ws.pass_ctas,
-                           ws.pass_variant};
+                           ws.pass_variant, pl.noise_seed};
         if (!pl.graph_exec || !(pl.graph_key == key)) {
             if (pl.graph_exec) {
                 cudaGraphExecDestroy(pl.graph_exec);
@@ -1075,7 +1198,7 @@ static semd_status enqueue_ceemdan(semd_plan_s &pl, int64_t ntiles, cudaStream_t
         pn.max_imfs = K - 1;
         const int iters = max_iterations(pn);
         SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)trials * sizeof(State), s));
-        SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters * 4, s));
+        SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)(iters + kLoopBody + 1) * 4, s));
         k_serialize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
                                                           ws.tile, 0);
         ++launches;
@@ -1097,7 +1220,7 @@ static semd_status enqueue_ceemdan(semd_plan_s &pl, int64_t ntiles, cudaStream_t
         k_ce_stage_test<<<tg, 256, 0, s>>>(ws.d_ce, ws.d_cestate, ws.d_cepart, 0);
         k_ce_stage_test<<<tg, 256, 0, s>>>(ws.d_ce, ws.d_cestate, ws.d_cepart, 1);
         SEMD_CU(cudaMemsetAsync(ws.d_state, 0, (size_t)trials * sizeof(State), s));
-        SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)iters1 * 4, s));
+        SEMD_CU(cudaMemsetAsync(ws.d_active, 0, (size_t)(iters1 + kLoopBody + 1) * 4, s));
         k_ce_stage_init<R><<<dim3(ig, (unsigned)trials), 256, 0, s>>>(ws.d_ce, ws.d_inst,
                                                                       ws.d_state, ws.d_cestate,
                                                                       k);
@@ -1168,7 +1291,7 @@ semd_status ceemdan_impl(semd_plan_s &pl, const void *d_x, const void *d_noise, 
     semd_status st = ws.layout(trials, ntiles, s, err); // records staging_done
     if (st != SEMD_OK)
         return st;
-    const bool use_graph = pl.graphs && !pl.prof.on && p.stop == SEMD_STOP_FIXED;
+    const bool use_graph = pl.graphs && !pl.prof.on;
     pl.prof.reset();
     if (use_graph) {
         const GraphKey key{trials, ntiles, ws.h_inst[0].ntiles, ws.max_ntiles, ws.tile,
@@ -1317,12 +1440,13 @@ cudaError_t setup_kernel_attrs(size_t elem)
     return elem == 8 ? set_smem_attr<double>() : set_smem_attr<float>();
 }
 
-void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s)
+void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s,
+                     int ctas_per_sm)
 {
     if (elem == 8)
-        launch_pass_tiles<double>(tile, 0, 0, pa, ntiles, s);
+        launch_pass_tiles<double>(tile, 0, ctas_per_sm, pa, ntiles, s);
     else
-        launch_pass_tiles<float>(tile, 0, 0, pa, ntiles, s);
+        launch_pass_tiles<float>(tile, 0, ctas_per_sm, pa, ntiles, s);
 }
 
 void launch_reduce_any(size_t elem, const ReduceArgs &ra, int nblocks, cudaStream_t s)
@@ -1484,6 +1608,7 @@ semd_status serial_emd_plan(const semd_params *params, int max_batch, size_t mem
                                       eemd_elems, mem_budget, err);
     if (st == SEMD_OK) {
         if (cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&pl->lstream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming) != cudaSuccess) {
             err = "stream or event creation failed";
@@ -1505,8 +1630,8 @@ semd_status serial_emd_decompose(semd_plan_t plan, const void *d_x, const void *
 {
     if (!plan)
         return SEMD_EINVAL;
-    if (!d_x || !d_imfs || (plan->p.ensemble_trials > 1 && !d_noise)) {
-        plan->err = "null input, output or (EEMD) noise pointer";
+    if (!d_x || !d_imfs) {
+        plan->err = "null input or output pointer";
         return SEMD_EINVAL;
     }
     semd_instance in{d_x, plan->p.rows, plan->p.cols, d_imfs, d_residue};
@@ -1659,6 +1784,8 @@ void serial_emd_destroy(semd_plan_t plan)
         cudaEventDestroy(plan->ev_out);
     if (plan->gstream)
         cudaStreamDestroy(plan->gstream);
+    if (plan->lstream)
+        cudaStreamDestroy(plan->lstream);
     plan->prof.destroy();
     plan->ws.release();
     delete plan;
@@ -1735,6 +1862,51 @@ semd_status serial_emd_plan_stats(semd_plan_t plan, semd_stats *out)
     out->pass_ms = ms[0];
     out->reduce_launches = cnt[1];
     out->reduce_ms = ms[1];
+    return SEMD_OK;
+}
+
+semd_status serial_emd_eemd_trial(semd_plan_t plan, int trial, void *d_imfs, double *d_residue,
+                                  int *n_imfs, double *beta, void *stream)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    if (plan->p.ensemble_trials < 2 || plan->last_ceemdan || plan->last_ninst < 2) {
+        plan->err = "no EEMD decomposition has run on this plan";
+        return SEMD_EINVAL;
+    }
+    if (trial < 0 || trial >= plan->last_ninst || !d_imfs) {
+        plan->err = "trial out of range or null output";
+        return SEMD_EINVAL;
+    }
+    std::string &err = plan->err;
+    Workspace &ws = plan->ws;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = plan->p.max_imfs;
+    const unsigned grid = (unsigned)std::min<int64_t>((plan->L + 255) / 256, 4 * 152);
+    if (plan->p.precision == SEMD_FP64)
+        k_eemd_trial<double><<<grid, 256, 0, s>>>(ws.d_inst, ws.d_state, trial, K,
+                                                  (const double *)ws.eemd_scratch,
+                                                  (double *)d_imfs, d_residue);
+    else
+        k_eemd_trial<float><<<grid, 256, 0, s>>>(ws.d_inst, ws.d_state, trial, K,
+                                                 (const float *)ws.eemd_scratch,
+                                                 (float *)d_imfs, d_residue);
+    SEMD_CU(cudaGetLastError());
+    if (beta) {
+        SEMD_CU(cudaMemcpyAsync(beta, ws.d_beta, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (beta || n_imfs)
+        SEMD_CU(cudaStreamSynchronize(s));
+    if (n_imfs)
+        *n_imfs = ws.h_state[trial].imf_count;
+    return SEMD_OK;
+}
+
+semd_status serial_emd_plan_set_noise_seed(semd_plan_t plan, uint64_t seed)
+{
+    if (!plan)
+        return SEMD_EINVAL;
+    plan->noise_seed = seed;
     return SEMD_OK;
 }
 

@@ -92,7 +92,9 @@ int max_iterations(const semd_params &p);
 // Kernel launches for other translation units (the kernels are instantiated once, in the
 // runtime's). elem is the working precision's size: 4 (FP32-mixed) or 8 (FP64).
 cudaError_t setup_kernel_attrs(size_t elem);
-void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s);
+// ctas_per_sm > 0 caps the persistent pass grid at that many CTAs per SM.
+void launch_pass_any(size_t elem, int tile, const PassArgs &pa, int64_t ntiles, cudaStream_t s,
+                     int ctas_per_sm = 0);
 void launch_reduce_any(size_t elem, const ReduceArgs &ra, int nblocks, cudaStream_t s);
 void launch_serialize_any(size_t elem, const Inst *d_inst, const State *d_state,
                           const int32_t *tile_inst, int64_t ntiles, int tile, cudaStream_t s);
@@ -196,11 +198,12 @@ struct GraphKey {
     int tile = 0;
     int pass_ctas = 0;
     int pass_variant = 0;
+    uint64_t seed = 0;
     bool operator==(const GraphKey &o) const
     {
         return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0 &&
                max_ntiles == o.max_ntiles && tile == o.tile && pass_ctas == o.pass_ctas &&
-               pass_variant == o.pass_variant;
+               pass_variant == o.pass_variant && seed == o.seed;
     }
 };
 
@@ -215,6 +218,7 @@ struct semd_plan_s {
     // CUDA graph of the fixed-sift-count decomposition, replayed on the plan's stream
     bool graphs = true;
     cudaStream_t gstream = nullptr;
+    cudaStream_t lstream = nullptr; // captures the body of a device-decided sifting loop
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     semd::GraphKey graph_key;
@@ -224,6 +228,7 @@ struct semd_plan_s {
     semd::GraphKey ce_graph_key;
     int64_t ce_graph_launches = 0;
     bool last_ceemdan = false; // the last call was CEEMDAN (counts come from its state)
+    uint64_t noise_seed = 0;   // EEMD noise drawn by the library when the caller passes none
     // statistics of the last decomposition
     semd::Profiler prof;
     int64_t stat_launches = 0;

@@ -118,35 +118,50 @@ struct Slot {
 
 } // namespace semd
 
-struct semd_server_s {
-    semd_params p{};
-    size_t budget = 0, elem = 4;
-    int max_inflight = 1, tile = semd::kTile;
-    int64_t Lmax = 0, cap_tiles = 0;
-    void *pool = nullptr;
-    semd::PoolAlloc alloc;
-    // device and pinned host arrays indexed by slot / launch tile
-    semd::Inst *d_inst = nullptr, *h_inst = nullptr;
-    semd::State *d_state = nullptr, *h_state = nullptr;
-    int32_t *d_tiles = nullptr, *h_tiles = nullptr;     // pass launch: tile -> slot
-    int32_t *d_list = nullptr, *h_list = nullptr;       // reduce launch: block -> slot
+namespace semd {
+// A lane of the server: its own worker thread, stream, requests and launch arrays. Small
+// requests and large ones (at least kLargeSamples serialized samples) run in separate
+// lanes, so the passes over a large request never hold up the small ones: the small lane's
+// stream has the higher priority, and the large lane's pass grid keeps to part of each SM,
+// so both lanes' kernels run side by side.
+constexpr int64_t kLargeSamples = (int64_t)1 << 21;
+struct Lane {
+    int max_inflight = 1;
+    int ctas_per_sm = 0; // pass-grid cap (0: as many CTAs as fit)
+    int64_t cap_tiles = 0;
+    Inst *d_inst = nullptr, *h_inst = nullptr;
+    State *d_state = nullptr, *h_state = nullptr;
+    int32_t *d_tiles = nullptr, *h_tiles = nullptr; // pass launch: tile -> slot
+    int32_t *d_list = nullptr, *h_list = nullptr;   // reduce launch: block -> slot
     int32_t *d_active = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
-    std::vector<semd::Slot> slots;
+    std::vector<Slot> slots;
+    std::deque<Request> queue;
+    std::thread worker;
+};
+} // namespace semd
+
+struct semd_server_s {
+    semd_params p{};
+    size_t budget = 0, elem = 4;
+    int tile = semd::kTile;
+    int64_t Lmax = 0;
+    void *pool = nullptr;
+    semd::PoolAlloc alloc;
+    semd::Lane lanes[2]; // 0: small requests, 1: large requests
     std::mutex mu;
-    std::condition_variable cv;
-    std::deque<semd::Request> queue;
+    std::condition_variable cv;      // work for a worker (or stop)
+    std::condition_variable cv_done; // a result was recorded
     std::unordered_map<uint64_t, semd_result> results;
     std::unordered_set<uint64_t> pending;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::string err;
-    std::thread worker;
 
-    void run();
-    bool round(std::string &e);
-    void fail_all(int status);
+    void run(int li);
+    bool round(semd::Lane &ln, std::string &e);
+    void fail_lane(semd::Lane &ln, int status);
     void release_device();
 };
 
@@ -170,40 +185,40 @@ using namespace semd;
         }                                                                                  \
     } while (0)
 
-// One round: admit, launch a few passes for every admitted request, collect finished
-// ones. Returns false on a CUDA error (message in e).
-bool semd_server_s::round(std::string &e)
+// One round of a lane: admit, launch a few passes for every admitted request, collect
+// finished ones. Returns false on a CUDA error (message in e).
+bool semd_server_s::round(Lane &ln, std::string &e)
 {
-    // admission, strict FIFO: a request waits until a slot and pool space are free
+    // admission, FIFO within the lane: a request waits until a slot and pool space are free
     std::vector<int> fresh;
     {
         std::lock_guard<std::mutex> lk(mu);
-        while (!queue.empty()) {
-            Request &rq = queue.front();
+        while (!ln.queue.empty()) {
+            Request &rq = ln.queue.front();
             int si = -1;
-            for (int i = 0; i < max_inflight; ++i)
-                if (!slots[i].used) {
+            for (int i = 0; i < ln.max_inflight; ++i)
+                if (!ln.slots[i].used) {
                     si = i;
                     break;
                 }
             size_t off = 0;
             if (si < 0 || !alloc.alloc(rq.lay.total, off))
                 break;
-            Slot &sl = slots[si];
+            Slot &sl = ln.slots[si];
             sl.used = true;
             sl.fresh = true;
             sl.off = off;
             sl.rq = rq;
             sl.rq.t_admit = Clock::now();
-            queue.pop_front();
+            ln.queue.pop_front();
             fresh.push_back(si);
         }
     }
     // descriptors and tile maps of every admitted request
     int64_t ntiles = 0, max_nt = 0;
     int nact = 0;
-    for (int i = 0; i < max_inflight; ++i) {
-        Slot &sl = slots[i];
+    for (int i = 0; i < ln.max_inflight; ++i) {
+        Slot &sl = ln.slots[i];
         if (!sl.used)
             continue;
         const Request &rq = sl.rq;
@@ -233,145 +248,162 @@ bool semd_server_s::round(std::string &e)
         in.imf = rq.req.d_imfs;
         in.res = rq.req.d_residue;
         in.imf_stride = rq.req.rows * rq.req.cols;
-        h_inst[i] = in;
+        ln.h_inst[i] = in;
         for (int64_t t = 0; t < q.nt; ++t)
-            h_tiles[ntiles + t] = i;
+            ln.h_tiles[ntiles + t] = i;
         ntiles += q.nt;
         max_nt = std::max<int64_t>(max_nt, q.nt);
-        h_list[nact++] = i;
+        ln.h_list[nact++] = i;
     }
     if (nact == 0)
         return true;
-    SV_CU(cudaMemcpyAsync(d_inst, h_inst, (size_t)max_inflight * sizeof(Inst),
-                          cudaMemcpyHostToDevice, stream));
-    SV_CU(cudaMemcpyAsync(d_tiles, h_tiles, (size_t)ntiles * 4, cudaMemcpyHostToDevice, stream));
-    SV_CU(cudaMemcpyAsync(d_list, h_list, (size_t)nact * 4, cudaMemcpyHostToDevice, stream));
+    SV_CU(cudaMemcpyAsync(ln.d_inst, ln.h_inst, (size_t)ln.max_inflight * sizeof(Inst),
+                          cudaMemcpyHostToDevice, ln.stream));
+    SV_CU(cudaMemcpyAsync(ln.d_tiles, ln.h_tiles, (size_t)ntiles * 4, cudaMemcpyHostToDevice,
+                          ln.stream));
+    SV_CU(cudaMemcpyAsync(ln.d_list, ln.h_list, (size_t)nact * 4, cudaMemcpyHostToDevice,
+                          ln.stream));
     if (!fresh.empty()) {
         // fresh states are zero (MODE_INIT): serialize only those instances
         for (int si : fresh)
-            SV_CU(cudaMemsetAsync(d_state + si, 0, sizeof(State), stream));
-        launch_serialize_any(elem, d_inst, d_state, d_tiles, ntiles, tile, stream);
+            SV_CU(cudaMemsetAsync(ln.d_state + si, 0, sizeof(State), ln.stream));
+        launch_serialize_any(elem, ln.d_inst, ln.d_state, ln.d_tiles, ntiles, tile, ln.stream);
     }
     for (int si : fresh)
-        slots[si].fresh = false;
+        ln.slots[si].fresh = false;
     // a few passes per round; fewer while requests are waiting, so they join sooner
     bool waiting;
     {
         std::lock_guard<std::mutex> lk(mu);
-        waiting = !queue.empty();
+        waiting = !ln.queue.empty();
     }
     const int passes = waiting ? 2 : 8;
     NvtxRange nvtx("server round");
-    PassArgs pa{d_inst, d_state, d_tiles, ntiles, p.stop == SEMD_STOP_SD ? 1 : 0,
+    PassArgs pa{ln.d_inst, ln.d_state, ln.d_tiles, ntiles, p.stop == SEMD_STOP_SD ? 1 : 0,
                 p.stop == SEMD_STOP_SNUMBER ? 1 : 0};
-    ReduceArgs ra = make_reduce_args(p, d_inst, d_state, d_list, d_active, elem, max_nt);
+    ReduceArgs ra = make_reduce_args(p, ln.d_inst, ln.d_state, ln.d_list, ln.d_active, elem,
+                                     max_nt);
     for (int it = 0; it < passes; ++it) {
-        launch_pass_any(elem, tile, pa, ntiles, stream);
-        launch_reduce_any(elem, ra, nact, stream);
+        launch_pass_any(elem, tile, pa, ntiles, ln.stream, ln.ctas_per_sm);
+        launch_reduce_any(elem, ra, nact, ln.stream);
     }
     SV_CU(cudaGetLastError());
-    SV_CU(cudaMemcpyAsync(h_state, d_state, (size_t)max_inflight * sizeof(State),
-                          cudaMemcpyDeviceToHost, stream));
-    SV_CU(cudaEventRecord(ev, stream));
-    SV_CU(cudaEventSynchronize(ev));
+    SV_CU(cudaMemcpyAsync(ln.h_state, ln.d_state, (size_t)ln.max_inflight * sizeof(State),
+                          cudaMemcpyDeviceToHost, ln.stream));
+    SV_CU(cudaEventRecord(ln.ev, ln.stream));
+    SV_CU(cudaEventSynchronize(ln.ev));
     // finished requests (state MODE_DONE): residue de-serialization and zero-fill over
     // the same tile map, then release
     std::vector<int> fin;
     for (int k = 0; k < nact; ++k)
-        if (h_state[h_list[k]].mode == MODE_DONE)
-            fin.push_back(h_list[k]);
+        if (ln.h_state[ln.h_list[k]].mode == MODE_DONE)
+            fin.push_back(ln.h_list[k]);
     if (fin.empty())
         return true;
-    launch_finalize_any(elem, d_inst, d_state, d_tiles, ntiles, tile, p.max_imfs, stream);
+    launch_finalize_any(elem, ln.d_inst, ln.d_state, ln.d_tiles, ntiles, tile, p.max_imfs,
+                        ln.stream);
     SV_CU(cudaGetLastError());
-    SV_CU(cudaEventRecord(ev, stream));
-    SV_CU(cudaEventSynchronize(ev));
+    SV_CU(cudaEventRecord(ln.ev, ln.stream));
+    SV_CU(cudaEventSynchronize(ln.ev));
     const Clock::time_point now = Clock::now();
-    std::lock_guard<std::mutex> lk(mu);
-    for (int i : fin) {
-        Slot &sl = slots[i];
-        const State &st = h_state[i];
-        semd_result r{};
-        r.status = SEMD_OK;
-        r.n_imfs = st.imf_count;
-        int64_t sifts = 0;
-        for (int k = 0; k < st.imf_count && k < KMAX; ++k)
-            sifts += st.sifts[k];
-        r.sifts = sifts;
-        r.queue_ms = ms_between(sl.rq.t_submit, sl.rq.t_admit);
-        r.run_ms = ms_between(sl.rq.t_admit, now);
-        results[sl.rq.ticket] = r;
-        pending.erase(sl.rq.ticket);
-        alloc.release(sl.off, sl.rq.lay.total);
-        sl.used = false;
-    }
-    return true;
-}
-
-void semd_server_s::fail_all(int status)
-{
-    std::lock_guard<std::mutex> lk(mu);
-    auto mark = [&](const Request &rq) {
-        semd_result r{};
-        r.status = status;
-        results[rq.ticket] = r;
-        pending.erase(rq.ticket);
-    };
-    for (auto &sl : slots)
-        if (sl.used) {
-            mark(sl.rq);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i : fin) {
+            Slot &sl = ln.slots[i];
+            const State &st = ln.h_state[i];
+            semd_result r{};
+            r.status = SEMD_OK;
+            r.n_imfs = st.imf_count;
+            int64_t sifts = 0;
+            for (int k = 0; k < st.imf_count && k < KMAX; ++k)
+                sifts += st.sifts[k];
+            r.sifts = sifts;
+            r.queue_ms = ms_between(sl.rq.t_submit, sl.rq.t_admit);
+            r.run_ms = ms_between(sl.rq.t_admit, now);
+            results[sl.rq.ticket] = r;
+            pending.erase(sl.rq.ticket);
             alloc.release(sl.off, sl.rq.lay.total);
             sl.used = false;
         }
-    for (auto &rq : queue)
-        mark(rq);
-    queue.clear();
+    }
+    cv_done.notify_all();
+    cv.notify_all(); // freed pool space may admit the other lane's requests
+    return true;
 }
 
-void semd_server_s::run()
+// Ends every request of a lane (admitted or queued) with `status`.
+void semd_server_s::fail_lane(Lane &ln, int status)
 {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto mark = [&](const Request &rq) {
+            semd_result r{};
+            r.status = status;
+            results[rq.ticket] = r;
+            pending.erase(rq.ticket);
+        };
+        for (auto &sl : ln.slots)
+            if (sl.used) {
+                mark(sl.rq);
+                alloc.release(sl.off, sl.rq.lay.total);
+                sl.used = false;
+            }
+        for (auto &rq : ln.queue)
+            mark(rq);
+        ln.queue.clear();
+    }
+    cv_done.notify_all();
+}
+
+void semd_server_s::run(int li)
+{
+    Lane &ln = lanes[li];
     for (;;) {
-        bool busy = false;
         {
             std::unique_lock<std::mutex> lk(mu);
-            for (auto &sl : slots)
+            bool busy = false;
+            for (auto &sl : ln.slots)
                 busy = busy || sl.used;
             if (!busy)
-                cv.wait(lk, [&] { return stop || !queue.empty(); });
+                cv.wait(lk, [&] { return stop || !ln.queue.empty(); });
             if (stop)
                 break;
         }
         std::string e;
-        if (!round(e)) {
+        if (!round(ln, e)) {
+            cudaStreamSynchronize(ln.stream);
+            fail_lane(ln, SEMD_ECUDA);
             {
                 std::lock_guard<std::mutex> lk(mu);
                 err = e;
+                stop = true;
             }
-            cudaStreamSynchronize(stream);
-            fail_all(SEMD_ECUDA);
-            std::lock_guard<std::mutex> lk(mu);
-            stop = true;
+            cv.notify_all();
             break;
         }
     }
-    cudaStreamSynchronize(stream);
-    fail_all(SEMD_ECANCELED);
+    cudaStreamSynchronize(ln.stream);
+    fail_lane(ln, SEMD_ECANCELED);
 }
 
 void semd_server_s::release_device()
 {
-    if (ev)
-        cudaEventDestroy(ev);
-    if (stream)
-        cudaStreamDestroy(stream);
-    void *dev[] = {pool, d_inst, d_state, d_tiles, d_list, d_active};
-    for (void *q : dev)
-        if (q)
-            cudaFree(q);
-    void *host[] = {h_inst, h_state, h_tiles, h_list};
-    for (void *q : host)
-        if (q)
-            cudaFreeHost(q);
+    for (Lane &ln : lanes) {
+        if (ln.ev)
+            cudaEventDestroy(ln.ev);
+        if (ln.stream)
+            cudaStreamDestroy(ln.stream);
+        void *dev[] = {ln.d_inst, ln.d_state, ln.d_tiles, ln.d_list, ln.d_active};
+        for (void *q : dev)
+            if (q)
+                cudaFree(q);
+        void *host[] = {ln.h_inst, ln.h_state, ln.h_tiles, ln.h_list};
+        for (void *q : host)
+            if (q)
+                cudaFreeHost(q);
+    }
+    if (pool)
+        cudaFree(pool);
 }
 
 extern "C" {
@@ -407,48 +439,63 @@ semd_status serial_emd_server_create(const semd_params *defaults, size_t mem_bud
     }
     sv->p = *defaults;
     sv->budget = mem_budget;
-    sv->max_inflight = max_inflight;
     sv->elem = defaults->precision == SEMD_FP64 ? 8 : 4;
     sv->Lmax = serial_length(M, N, D);
     // every admitted request holds at least (2w + 16) bytes per sample of the pool
-    sv->cap_tiles = (int64_t)(mem_budget / ((2 * sv->elem + 16) * (size_t)sv->tile)) +
-                    2 * (int64_t)max_inflight;
-    sv->slots.resize(max_inflight);
-    sv->alloc.init(mem_budget);
-    const size_t ni = (size_t)max_inflight, nt = (size_t)sv->cap_tiles;
-    cudaError_t e = cudaMalloc(&sv->pool, mem_budget);
+    const int64_t budget_tiles =
+        (int64_t)(mem_budget / ((2 * sv->elem + 16) * (size_t)sv->tile));
+    // lane 0 (small requests) keeps most slots; lane 1 (large ones) a few, and its pass
+    // grid takes at most two CTAs per SM
+    const int nlarge = std::max(1, max_inflight / 8);
+    sv->lanes[0].max_inflight = max_inflight;
+    sv->lanes[1].max_inflight = nlarge;
+    sv->lanes[1].ctas_per_sm = 2;
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&sv->d_inst, ni * sizeof(Inst));
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&sv->d_state, ni * sizeof(State));
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&sv->d_tiles, nt * 4);
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&sv->d_list, ni * 4);
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&sv->d_active, 64);
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&sv->h_inst, ni * sizeof(Inst));
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&sv->h_state, ni * sizeof(State));
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&sv->h_tiles, nt * 4);
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&sv->h_list, ni * 4);
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaEventCreateWithFlags(&sv->ev, cudaEventDisableTiming);
+        e = cudaMalloc(&sv->pool, mem_budget);
+    for (int li = 0; li < 2 && e == cudaSuccess; ++li) {
+        Lane &ln = sv->lanes[li];
+        ln.cap_tiles = budget_tiles + 2 * (int64_t)ln.max_inflight;
+        ln.slots.resize(ln.max_inflight);
+        const size_t ni = (size_t)ln.max_inflight, nt = (size_t)ln.cap_tiles;
+        e = cudaMalloc((void **)&ln.d_inst, ni * sizeof(Inst));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&ln.d_state, ni * sizeof(State));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&ln.d_tiles, nt * 4);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&ln.d_list, ni * 4);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&ln.d_active, 64);
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&ln.h_inst, ni * sizeof(Inst));
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&ln.h_state, ni * sizeof(State));
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&ln.h_tiles, nt * 4);
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&ln.h_list, ni * 4);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&ln.stream, cudaStreamNonBlocking,
+                                             li == 0 ? prio_hi : prio_lo);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&ln.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            std::memset(ln.h_inst, 0, ni * sizeof(Inst));
+    }
     if (e == cudaSuccess)
         e = setup_kernel_attrs(sv->elem);
     if (e != cudaSuccess) {
         err = std::string("server set-up: ") + cudaGetErrorString(e);
+        (void)cudaGetLastError(); // a failed allocation must not surface in later calls
         sv->release_device();
         delete sv;
         return e == cudaErrorMemoryAllocation ? SEMD_ENOMEM : SEMD_ECUDA;
     }
-    std::memset(sv->h_inst, 0, ni * sizeof(Inst));
-    sv->worker = std::thread([sv] { sv->run(); });
+    sv->alloc.init(mem_budget);
+    for (int li = 0; li < 2; ++li)
+        sv->lanes[li].worker = std::thread([sv, li] { sv->run(li); });
     *out = sv;
     return SEMD_OK;
 }
@@ -475,8 +522,9 @@ semd_status serial_emd_submit(semd_server_t sv, const semd_request *req, uint64_
         return SEMD_EINVAL;
     rq.L = serial_length(rq.M, rq.N, rq.D);
     rq.lay = req_layout(rq.L, sv->elem, sv->tile);
+    const int li = rq.L >= kLargeSamples ? 1 : 0;
     if (rq.L > sv->Lmax || PoolAlloc::round(rq.lay.total) > sv->budget ||
-        rq.lay.nt > sv->cap_tiles) {
+        rq.lay.nt > sv->lanes[li].cap_tiles) {
         sv->err = "the request is larger than the server accepts (" +
                   std::to_string(rq.lay.total) + " bytes of working buffers)";
         return SEMD_EBUDGET;
@@ -485,9 +533,9 @@ semd_status serial_emd_submit(semd_server_t sv, const semd_request *req, uint64_
     rq.ticket = sv->next_ticket++;
     rq.t_submit = Clock::now();
     sv->pending.insert(rq.ticket);
-    sv->queue.push_back(rq);
+    sv->lanes[li].queue.push_back(rq);
     *ticket = rq.ticket;
-    sv->cv.notify_one();
+    sv->cv.notify_all();
     return SEMD_OK;
 }
 
@@ -508,6 +556,40 @@ semd_status serial_emd_poll(semd_server_t sv, uint64_t ticket, semd_result *out)
     return SEMD_EINVAL;
 }
 
+semd_status serial_emd_wait(semd_server_t sv, uint64_t ticket, double timeout_ms,
+                            semd_result *out)
+{
+    if (!sv || !out || !(timeout_ms >= 0))
+        return SEMD_EINVAL;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline =
+        Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                           std::chrono::duration<double, std::milli>(timeout_ms));
+    for (;;) {
+        auto it = sv->results.find(ticket);
+        if (it != sv->results.end()) {
+            *out = it->second;
+            sv->results.erase(it);
+            return SEMD_OK;
+        }
+        if (!sv->pending.count(ticket)) {
+            sv->err = "unknown ticket (or its result was already returned)";
+            return SEMD_EINVAL;
+        }
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+            Clock::now() >= deadline) {
+            auto again = sv->results.find(ticket);
+            if (again != sv->results.end()) {
+                *out = again->second;
+                sv->results.erase(again);
+                return SEMD_OK;
+            }
+            sv->err = "the request did not finish within the time limit";
+            return SEMD_ETIMEOUT;
+        }
+    }
+}
+
 void serial_emd_server_destroy(semd_server_t sv)
 {
     if (!sv)
@@ -517,8 +599,9 @@ void serial_emd_server_destroy(semd_server_t sv)
         sv->stop = true;
     }
     sv->cv.notify_all();
-    if (sv->worker.joinable())
-        sv->worker.join();
+    for (Lane &ln : sv->lanes)
+        if (ln.worker.joinable())
+            ln.worker.join();
     sv->release_device();
     delete sv;
 }

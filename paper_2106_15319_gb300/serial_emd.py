@@ -144,6 +144,27 @@ class Plan:
     def counts(self, count: int = 1):
         return capi.serial_emd_plan_counts(self.handle, count, self.params.max_imfs)
 
+    @property
+    def noise_seed(self) -> int:
+        return getattr(self, "_seed", 0)
+
+    @noise_seed.setter
+    def noise_seed(self, value: int):
+        capi.serial_emd_plan_set_noise_seed(self.handle, value)
+        self._seed = value
+
+    def eemd_trial(self, trial: int, stream=None):
+        """Realization `trial` of the last EEMD call: (imfs (K, rows, cols), residue,
+        its IMF count, beta of the call)."""
+        imfs, res = self.outputs(self.params.rows, self.params.cols)
+        n, beta = capi.serial_emd_eemd_trial(self.handle, trial, imfs, res, stream)
+        return imfs, res, n, beta
+
+    def launch_times(self, kind: int = 0):
+        """Per-launch device times (ms) of the last profiled call (kind 0: passes, 1:
+        interface solves)."""
+        return capi.serial_emd_plan_launch_times(self.handle, kind)
+
     def extrema(self, h: torch.Tensor, stream=None):
         L = h.numel()
         tmax = torch.empty(L // 2 + 1, dtype=torch.int32, device=h.device)
@@ -191,6 +212,10 @@ class Server:
             imfs, residue = self.outputs(*x.shape, device=x.device)
         t = capi.serial_emd_submit(self.handle, x, imfs, residue, order)
         return t, imfs, residue
+
+    def wait(self, ticket: int, timeout_ms: float):
+        """The request's result, or None if it did not finish within timeout_ms."""
+        return capi.serial_emd_wait(self.handle, ticket, timeout_ms)
 
     def poll(self, ticket: int):
         return capi.serial_emd_poll(self.handle, ticket)

@@ -13,24 +13,18 @@ from that remainder rounded to single precision. The oracle starts from the same
 rounded values, so both sides decide from identical numbers whether another IMF
 exists (the IMF count must match exactly); the residue must equal the FP64
 sequence to rounding. The FP32 tolerance (1e-4 of the IMF's norm) presumes, like
-the FP64 one, that the extremum sets of every sift match. Single precision breaks
-that premise where the signal is slow enough that neighbouring samples round to
-equal values: the tie rule then fires on plateaus that FP64 resolves, and one
-knot more or less moves a slow IMF by far more than 1e-4. The test therefore
-replays the oracle's FP64 sift chain for each IMF and asks whether its extremum
-decisions survive single precision: rounding each sifted signal to FP32 must
-leave every extremum set unchanged, and no sift input may contain a neighbour
-difference within 2^-20 of max|h| (a near-flat step of a monotone run, where FP32
-noise can add or remove a maximum/minimum pair, or a near-flat extremum, where the
-tie rule's choice of knot depends on rounding). IMFs that pass the check must be
-within 1e-4 (the two leading IMFs, where knots are dense) or 1e-3 (later IMFs:
-besides rounding, FP32 arithmetic adds ~1e-6 of the signal scale per sift, the
-cubic evaluated over long intervals and the single-precision tile solve, which can
-still move a slow IMF's knot by a sample; observed effects up to ~3e-4); IMFs that
-fail the check are reported, not bounded. Inputs with transitions (D > 0) drop transition samples
-from the outputs, so there the unconditional bar applies: the two leading IMFs
-within 1e-4 of their norm, every later IMF and the tail sum within 1e-3 of
-||x||, IMF counts at most one apart.
+the FP64 one, that both sides sift with the same knots. So for every IMF the test
+replays the GPU's own FP32 sift chain (single sifts through the C ABI, with the
+decomposition's pass shape; the replay must reproduce the decomposition's IMF bit
+for bit) beside the oracle's FP64 chain from the same input, and compares their
+knot decisions sift by sift. Where every decision agrees, the IMF must be within
+1e-4. Where one differs, the test requires that the decision was one single
+precision cannot resolve: the comparison that decides it must differ by at most
+2^-20 of the IMF input's max|h| in the FP64 chain (a near-flat step or a near-flat extremum, where
+rounding picks the side). Such an IMF is exempt from the bar and counted. Inputs
+with transitions (D > 0) drop transition samples from the outputs, so there the
+unconditional bar applies: the two leading IMFs within 1e-4 of their norm, every
+later IMF and the tail sum within 1e-3 of ||x||, IMF counts at most one apart.
 """
 import os
 
@@ -45,8 +39,6 @@ from paper_2106_15319_gb300 import capi, synth  # noqa: E402
 from paper_2106_15319_gb300.serial_emd import Plan, make_params  # noqa: E402
 
 TOL = {capi.FP64: 1e-10, capi.FP32_MIXED: 1e-4}
-# FP32, IMFs after the two leading ones whose extremum decisions survive single precision
-FP32_STABLE_TOL = 1e-3
 NP = {capi.FP64: np.float64, capi.FP32_MIXED: np.float32}
 
 
@@ -83,67 +75,154 @@ def _check_imfs(imfs_g, res_g, n_g, imfs_o, res_o, n_o, x, prec, what=""):
     return errs
 
 
-def _fp32_fragile_step(h, tau=2.0 ** -20):
-    """A neighbour difference within tau * max|h|: a near-flat step of a monotone run
-    (single-precision noise can create or remove a maximum/minimum pair) or a near-flat
-    extremum (two almost equal samples at a peak or trough: which of them the tie rule
-    of Step 1 makes the knot then depends on rounding). Either moves a knot, and a knot
-    moved by one sample changes a slow IMF by far more than the FP32 bar."""
-    d = np.diff(h)
-    if d.size < 1:
-        return False
-    return bool(np.any(np.abs(d) <= tau * np.abs(h).max()))
+# Single-precision knot decisions. A knot decision of Step 1 at sample q rests on the two
+# comparisons (q-1, q) and (q, q+1). FP32 arithmetic and storage move every sample of a
+# sifted signal by a few units in the last place of the scale of the IMF's input; a
+# comparison whose FP64 difference is within FP32_TAU of that scale can therefore come out
+# either way, and the rounding decides it. When that happens the FP32 and FP64 sift chains use different knot
+# sets from that sift on, and the IMF may move by far more than the FP32 bar (a knot moved
+# by one sample changes a slow IMF at the percent level).
+FP32_TAU = 2.0 ** -20
+# The SD ratio's sums run in single precision per tile (about 1e-6 relative); a stop
+# decision may differ only where the FP64 ratio is within this relative distance of the
+# threshold.
+FP32_SD_TAU = 1e-4
+
+_SIFT_PLANS = {}
 
 
-def _fp32_keeps_extrema(h32, S, boundary=O.BOUNDARY_MIRROR, mirror_knots=2):
-    """Whether the oracle's FP64 sift chain from h32 keeps its extremum decisions in
-    single precision: rounding each sifted signal to FP32 leaves every extremum set
-    unchanged, and no sift input has an FP32-fragile near-flat step."""
-    h = h32.copy()
-    for _ in range(S):
-        a = O.extrema(h)
-        b = O.extrema(h.astype(np.float32).astype(np.float64))
-        if not (np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])):
-            return False
-        if _fp32_fragile_step(h):
-            return False
-        if a[0].size < 1 or a[1].size < 1 or a[0].size + a[1].size < 3:
-            return True
-        out = O.sift(h, boundary=boundary, mirror_knots=mirror_knots)
-        if out is None:
-            return True
-        h = out[0]
-    return True
+def _sift_plan(L, shape, boundary, mirror_knots):
+    """A single-sift FP32 plan with the decomposition's pass shape (tile, variant) and
+    envelope rule (the oracle's boundary code: rule + not-a-knot flag)."""
+    key = (L, shape, boundary, mirror_knots)
+    if key not in _SIFT_PLANS:
+        if len(_SIFT_PLANS) > 8:
+            for pl in _SIFT_PLANS.values():
+                pl.close()
+            _SIFT_PLANS.clear()
+        nak = boundary & O.SPLINE_NOT_A_KNOT
+        pl = Plan(make_params(1, max(L, 8), precision=capi.FP32_MIXED,
+                              boundary=boundary & ~O.SPLINE_NOT_A_KNOT,
+                              mirror_knots=mirror_knots,
+                              spline_end=capi.SPLINE_NOT_A_KNOT if nak else capi.SPLINE_NATURAL))
+        pl.tile, pl.pass_variant = shape
+        _SIFT_PLANS[key] = pl
+    return _SIFT_PLANS[key]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _close_sift_plans():
+    yield
+    for pl in _SIFT_PLANS.values():
+        pl.close()
+    _SIFT_PLANS.clear()
+
+
+def _enough_extrema(h):
+    """Reading 9's test: at least one maximum, one minimum and three extrema."""
+    a, b = O.extrema(h)
+    return a.size >= 1 and b.size >= 1 and a.size + b.size >= 3
+
+
+def _decision_margin(o, qs, scale):
+    """The largest, over the samples qs whose knot decisions differ, of the smaller FP64
+    difference of the two comparisons that decide the sample, relative to `scale`: the
+    magnitude of the IMF's single-precision input. The FP32 form's errors are absolute
+    errors of that scale (the first sift subtracts a mean envelope of the input's size, in
+    single precision), and they stay in the signal through the later sifts."""
+    m = 0.0
+    for q in qs:
+        d = [abs(o[q] - o[q - 1])] if q >= 1 else []
+        if q + 1 < o.size:
+            d.append(abs(o[q + 1] - o[q]))
+        m = max(m, min(d))
+    return m / max(scale, 1e-300)
+
+
+def _fp32_chain(h32, S, shape, boundary=O.BOUNDARY_MIRROR, mirror_knots=2, sd=None):
+    """Replays one IMF's sifting two ways from the same single-precision input: the GPU's
+    own FP32 chain (single sifts through the C ABI with the decomposition's pass shape) and
+    the oracle's FP64 chain. Returns (GPU result, sifts, None) when every sift of both
+    chains took the same knot decisions (and, with sd = (threshold, max_sifts), the same
+    stop decisions), else (None, sift index, (kind, margin)) for the first differing
+    decision: for a knot decision the relative FP64 difference of its deciding
+    comparison, for a stop decision the relative distance of the FP64 SD ratio from the
+    threshold."""
+    sp = _sift_plan(h32.size, shape, boundary, mirror_knots)
+    g = h32.astype(np.float32)
+    o = h32.copy()
+    cap = S if sd is None else sd[1]
+    j = 0
+    while j < cap:
+        gd = g.astype(np.float64)
+        ga, gb = O.extrema(gd)
+        oa, ob = O.extrema(o)
+        if not (np.array_equal(ga, oa) and np.array_equal(gb, ob)):
+            qs = np.concatenate([np.setxor1d(ga, oa), np.setxor1d(gb, ob)])
+            return None, j, ("knot", _decision_margin(o, qs, max(np.abs(h32).max(),
+                                                                  np.abs(o).max())))
+        if j > 0 and not _enough_extrema(o):
+            break
+        out, gnum, gden = sp.sift(torch.from_numpy(g).cuda())
+        g = out.cpu().numpy()
+        o_next, onum, oden = O.sift(o, boundary=boundary, mirror_knots=mirror_knots)
+        o = o_next
+        j += 1
+        if sd is not None:
+            gstop, ostop = gnum / gden < sd[0], onum / oden < sd[0]
+            if gstop != ostop:
+                return None, j, ("stop", abs(onum / oden / sd[0] - 1.0))
+            if ostop:
+                break
+    return g.astype(np.float64), j, None
 
 
 def _check_fp32_given_input(imfs_g, res_g, n_g, x, K, what="", S=10,
-                            boundary=O.BOUNDARY_MIRROR, mirror_knots=2):
+                            boundary=O.BOUNDARY_MIRROR, mirror_knots=2, shape=(256, 0),
+                            sd=None, sifts_g=None):
     """FP32 parity of every IMF against the oracle's IMF of the same remainder (D = 0,
-    so the serialized signal is x flattened)."""
+    so the serialized signal is x flattened). Per IMF, the GPU's FP32 sift chain is
+    replayed beside the oracle's FP64 chain from the same single-precision input:
+    - same knot (and stop) decisions at every sift: the replay must equal the
+      decomposition's IMF bit for bit, and the IMF must be within 1e-4 of the oracle's;
+    - a differing decision: allowed only where its FP64 margin is within FP32_TAU (a
+      comparison that single precision cannot resolve); the IMF is then reported as
+      exempt, and from that sift on the two chains sift different knot sets."""
     x = np.asarray(x, np.float64).reshape(-1)
     c = np.asarray(imfs_g, np.float64).reshape(K, -1)
     floor = max(1e-6 * np.linalg.norm(x), 1e-300)
     r = x.copy()
-    errs, stable = [], []
+    errs, exempt = [], []
+    stop_kw = {} if sd is None else dict(stop=O.STOP_SD, sd_threshold=sd[0], max_sifts=sd[1])
     for k in range(n_g):
         h32 = r.astype(np.float32).astype(np.float64)
-        oi, _, on, _ = O.emd(h32, 1, fixed_sifts=S, boundary=boundary,
-                             mirror_knots=mirror_knots)
+        oi, _, on, os_ = O.emd(h32, 1, fixed_sifts=S, boundary=boundary,
+                               mirror_knots=mirror_knots, **stop_kw)
         assert on == 1, f"{what}: the oracle finds no IMF {k + 1} in the GPU's remainder"
         errs.append(_rel(c[k], oi[0], floor))
-        stable.append(_fp32_keeps_extrema(h32, S, boundary, mirror_knots))
+        g, j, margin = _fp32_chain(h32, S, shape, boundary, mirror_knots, sd)
+        if margin is None:
+            exempt.append(False)
+            assert np.array_equal(g, c[k]), f"{what}: IMF {k + 1} replay differs"
+            if sifts_g is not None:
+                assert int(sifts_g[k]) == j == int(os_[0]), \
+                    f"{what}: IMF {k + 1} sifts {sifts_g[k]} / replay {j} / oracle {os_[0]}"
+            assert errs[-1] <= TOL[capi.FP32_MIXED], \
+                f"{what}: IMF {k + 1} error {errs[-1]} with matching decisions (all {errs})"
+        else:
+            exempt.append(True)
+            kind, m = margin
+            assert m <= (FP32_TAU if kind == "knot" else FP32_SD_TAU), \
+                f"{what}: IMF {k + 1} {kind} decisions differ at sift {j} with margin {m}"
         r = r - c[k]
-    msg = f"{what}: per-IMF given input {errs}, extremum decisions kept in FP32 {stable}"
-    assert all(e <= TOL[capi.FP32_MIXED] for e, st in zip(errs[:2], stable[:2]) if st), msg
-    assert all(e <= FP32_STABLE_TOL for e, st in zip(errs, stable) if st), msg
     if n_g < K:
         _, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, fixed_sifts=S,
-                            boundary=boundary, mirror_knots=mirror_knots)
+                            boundary=boundary, mirror_knots=mirror_knots, **stop_kw)
         assert on == 0, f"{what}: the GPU stopped after {n_g} IMFs, the oracle continues"
     assert np.all(c[n_g:] == 0.0), f"{what}: IMF slots past the count are not zero"
     rn = np.asarray(res_g, np.float64).reshape(-1)
     assert np.abs(rn - r).max() <= 1e-14 * np.abs(x).max(), f"{what}: residue"
-    return errs, stable
+    return errs, exempt
 
 
 def _run(X, prec, order=capi.ORDER_ROWS, **kw):
@@ -154,7 +233,8 @@ def _run(X, prec, order=capi.ORDER_ROWS, **kw):
     x = torch.from_numpy(Xr).cuda()
     imfs, res, n = plan.decompose(x)
     torch.cuda.synchronize()
-    out = imfs.double().cpu().numpy(), res.cpu().numpy(), n, plan.counts(1)[1][0]
+    out = (imfs.double().cpu().numpy(), res.cpu().numpy(), n, plan.counts(1)[1][0],
+           (plan.tile, plan.pass_variant))
     plan.close()
     return out
 
@@ -221,7 +301,7 @@ def test_series_3x1024(prec, D):
     g = _run(X, prec, transition_len=D, max_imfs=8)
     if prec == capi.FP32_MIXED and D == 0:
         x = np.asarray(X, np.float32).astype(np.float64)
-        _check_fp32_given_input(g[0], g[1], g[2], x, 8, "series D=0")
+        _check_fp32_given_input(g[0], g[1], g[2], x, 8, "series D=0", shape=g[4])
         return
     o = _oracle(X, prec, transition_len=D, max_imfs=8)
     _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, f"series D={D}")
@@ -287,7 +367,7 @@ def test_texture_256(prec):
         _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, "texture 256")
     else:
         x = np.asarray(X, np.float32).astype(np.float64)
-        _check_fp32_given_input(g[0], g[1], g[2], x, 10, "texture 256")
+        _check_fp32_given_input(g[0], g[1], g[2], x, 10, "texture 256", shape=g[4])
 
 
 def test_texture_256_with_transitions_fp64():
@@ -332,7 +412,7 @@ def test_options_fp64(kw):
 
 def test_reconstruction_on_gpu():
     X = synth.workload_texture_256()
-    imfs, res, n, _ = _run(X, capi.FP64, transition_len=0)
+    imfs, res, n, _, _ = _run(X, capi.FP64, transition_len=0)
     assert np.abs(imfs.sum(0) + res - X).max() <= 1e-12
 
 
@@ -351,7 +431,8 @@ def test_batch_uneven_images_match_oracle_and_alone(prec):
     for i, im in enumerate(imgs):
         gi, gr = outs[i][0].double().cpu().numpy(), outs[i][1].cpu().numpy()
         if prec == capi.FP32_MIXED:
-            _check_fp32_given_input(gi, gr, ns[i], im.astype(np.float64), 8, f"batch item {i}")
+            _check_fp32_given_input(gi, gr, ns[i], im.astype(np.float64), 8, f"batch item {i}",
+                                    shape=(plan.tile, plan.pass_variant))
         else:
             o = _oracle(im, prec, transition_len=0, max_imfs=8)
             _check_imfs(gi, gr, ns[i], o[0], o[1], o[2], o[4], prec, f"batch item {i}")
@@ -445,7 +526,7 @@ def test_degenerate_inputs(prec, kind):
     if prec == capi.FP64:
         _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, kind)
     else:
-        _check_fp32_given_input(g[0], g[1], g[2], X.astype(np.float64), 6, kind)
+        _check_fp32_given_input(g[0], g[1], g[2], X.astype(np.float64), 6, kind, shape=g[4])
     assert np.abs(g[0].sum(0) + g[1] - X.astype(np.float64)).max() <= \
         1e-12 * max(1.0, np.abs(X).max())
 
@@ -464,7 +545,8 @@ def test_every_sample_an_extremum(prec):
         o = _oracle(X, prec, transition_len=0, max_imfs=5)
         _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], prec, "alternating")
     else:
-        _check_fp32_given_input(g[0], g[1], g[2], X.astype(np.float64), 5, "alternating")
+        _check_fp32_given_input(g[0], g[1], g[2], X.astype(np.float64), 5, "alternating",
+                                shape=g[4])
 
 
 def test_long_signal_global_interface_scratch_fp64():
@@ -486,17 +568,22 @@ def test_largest_serving_image_fp32():
     exact FP64 reconstruction, the oracle's IMF count, and its two leading IMFs given the
     same remainder."""
     X = np.asarray(synth.grating_image(2048, 99), np.float32)
-    imfs, res, n, _ = _run(X, capi.FP32_MIXED, transition_len=0, max_imfs=10)
+    imfs, res, n, _, shape = _run(X, capi.FP32_MIXED, transition_len=0, max_imfs=10)
     x = X.astype(np.float64)
     assert np.abs(imfs.sum(0) + res - x).max() <= 1e-12 * np.abs(x).max()
     r = x.reshape(-1).copy()
     floor = 1e-6 * np.linalg.norm(x)
     for k in range(2):
-        oi, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1)
+        h32 = r.astype(np.float32).astype(np.float64)
+        oi, _, on, _ = O.emd(h32, 1)
         assert on == 1
         err = _rel(imfs[k].reshape(-1), oi[0], floor)
-        assert err <= TOL[capi.FP32_MIXED] or not _fp32_keeps_extrema(
-            r.astype(np.float32).astype(np.float64), 10), (k, err)
+        g, j, margin = _fp32_chain(h32, 10, shape)
+        if margin is None:
+            assert np.array_equal(g, imfs[k].reshape(-1)), k
+            assert err <= TOL[capi.FP32_MIXED], (k, err)
+        else:
+            assert margin[1] <= FP32_TAU, (k, j, margin)
         r = r - imfs[k].reshape(-1)
 
 
@@ -522,7 +609,8 @@ def test_slices_match_oracle_per_row_and_batch(prec):
             oi, orr, on, _ = O.emd(xi, K)
             _check_imfs(gi[:, i], gr[i], ns[i], oi, orr, on, xi, prec, f"slice {i}")
         else:
-            _check_fp32_given_input(gi[:, i], gr[i], ns[i], xi, K, f"slice {i}")
+            _check_fp32_given_input(gi[:, i], gr[i], ns[i], xi, K, f"slice {i}",
+                                    shape=(plan.tile, plan.pass_variant))
     xs = [x[i:i + 1].contiguous() for i in range(rows)]
     outs, nb = plan.decompose_batch(xs)
     torch.cuda.synchronize()
@@ -865,11 +953,13 @@ def test_random_configurations_fp32(seed):
     plan.tile = int(g.choice([128, 256, 512]))
     imfs, res, n = plan.decompose(torch.from_numpy(X).cuda())
     torch.cuda.synchronize()
+    shape = (plan.tile, plan.pass_variant)
     plan.close()
     _check_fp32_given_input(imfs.double().cpu().numpy(), res.cpu().numpy(), n,
                             X.astype(np.float64), K, f"fp32 seed {seed} K {K} S {S} b {b} "
                             f"mk {mk} se {se}", S=S,
-                            boundary=b + (O.SPLINE_NOT_A_KNOT if se else 0), mirror_knots=mk)
+                            boundary=b + (O.SPLINE_NOT_A_KNOT if se else 0), mirror_knots=mk,
+                            shape=shape)
 
 
 @pytest.mark.parametrize("seed", range(int(os.environ.get("SEMD_RANDOM_CASES", "24")) // 6))
@@ -896,41 +986,6 @@ def test_random_long_signals_fp64(seed):
 
 # ------------------------------------------------------------- full-size workloads
 
-def _check_fp32_given_input_sd(imfs_g, res_g, n_g, sifts_g, x, K, what="",
-                               sd_threshold=0.2, max_sifts=50):
-    """The SD-stop form of _check_fp32_given_input: for every IMF, the oracle's SD-stop
-    EMD of the GPU's remainder rounded to single precision. Where the extremum decisions
-    of the oracle's sift chain survive single precision, the sift counts must agree
-    exactly and the IMF must be within the FP32 bars."""
-    x = np.asarray(x, np.float64).reshape(-1)
-    c = np.asarray(imfs_g, np.float64).reshape(K, -1)
-    floor = max(1e-6 * np.linalg.norm(x), 1e-300)
-    r = x.copy()
-    errs, stable = [], []
-    for k in range(n_g):
-        h32 = r.astype(np.float32).astype(np.float64)
-        oi, _, on, os_ = O.emd(h32, 1, stop=O.STOP_SD, sd_threshold=sd_threshold,
-                               max_sifts=max_sifts)
-        assert on == 1, f"{what}: the oracle finds no IMF {k + 1} in the GPU's remainder"
-        st = _fp32_keeps_extrema(h32, int(max(os_[0], sifts_g[k])))
-        stable.append(st)
-        errs.append(_rel(c[k], oi[0], floor))
-        if st:
-            assert int(os_[0]) == int(sifts_g[k]), \
-                f"{what}: IMF {k + 1} sifts {sifts_g[k]} vs the oracle's {os_[0]}"
-            bar = TOL[capi.FP32_MIXED] if k < 2 else FP32_STABLE_TOL
-            assert errs[-1] <= bar, f"{what}: IMF {k + 1} error {errs[-1]} (all {errs})"
-        r = r - c[k]
-    if n_g < K:
-        _, _, on, _ = O.emd(r.astype(np.float32).astype(np.float64), 1, stop=O.STOP_SD,
-                            sd_threshold=sd_threshold, max_sifts=max_sifts)
-        assert on == 0, f"{what}: the GPU stopped after {n_g} IMFs, the oracle continues"
-    assert np.all(c[n_g:] == 0.0), f"{what}: IMF slots past the count are not zero"
-    rn = np.asarray(res_g, np.float64).reshape(-1)
-    assert np.abs(rn - r).max() <= 1e-14 * np.abs(x).max(), f"{what}: residue"
-    return errs, stable
-
-
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
 def test_uneven_images_2048_full_workload(prec):
     """The 2048 uneven blob-field images (side U{32..128}) in one batched run with the
@@ -947,6 +1002,7 @@ def test_uneven_images_2048_full_workload(prec):
     outs, ns = plan.decompose_batch(xs)
     torch.cuda.synchronize()
     n_all, sifts_all = plan.counts(len(imgs))
+    shape = (plan.tile, plan.pass_variant)
     plan.close()
     assert list(ns) == list(n_all)
     for i, im in enumerate(imgs):
@@ -967,7 +1023,8 @@ def test_uneven_images_2048_full_workload(prec):
             _check_imfs(gi, gr, ns[i], o[0], o[1], o[2], o[4], prec, what)
             assert list(sifts_all[i][:ns[i]]) == list(o[3][:o[2]]), what
         else:
-            _check_fp32_given_input_sd(gi, gr, ns[i], sifts_all[i], imgs[i], K, what)
+            _check_fp32_given_input(gi, gr, ns[i], imgs[i].astype(np.float64), K, what,
+                                    shape=shape, sd=(0.2, 50), sifts_g=sifts_all[i])
 
 
 def _pool_eemd(x, w, beta, K, S, workers):
@@ -994,15 +1051,17 @@ def test_eemd_512_256_trials_full_workload(prec):
     it, against the oracle's EEMD of the same inputs (its trials in a process pool on the
     host cores). FP64: every averaged IMF within 1e-10.
 
-    FP32: at this size single precision moves a few knots of the slower IMFs in some of
-    the 256 trials (a near-flat step of Step 1's comparisons that FP64 resolves the other
-    way), and the trial mean carries those moves at 1/256 of their size: observed 1.5e-4
-    of the second IMF's norm, 1e-4 to 6e-2 for IMFs 3 to 9, 0.24 for the tenth (relative
-    to their own, smaller norms). The element-wise bar
-    (1e-4 of the IMF's norm) is therefore asserted for the first IMF, where the knots are
-    dense; every later IMF and the tail sum must be within 1e-3 of ||x||, the IMF counts at
-    most one apart, and the trial mean must reconstruct: the averaged IMFs plus the
-    averaged residue equal x plus beta times the mean noise."""
+    FP32, per realization: realizations 0 to 15 are read back one by one
+    (serial_emd_eemd_trial) and each of their IMFs is held to the FP32 bar against the
+    oracle's IMF of the same remainder, with the per-decision exemption rule of
+    _check_fp32_given_input (the realization's input x + beta w^(m) is formed here from
+    the beta the call used, in the same FP64 operations as the library). FP32, the trial
+    mean: the first IMF within 1e-4 (its knots are dense and single precision keeps its
+    decisions); later averaged IMFs carry, at 1/256 of their size, the knot moves of the
+    realizations whose decisions single precision cannot resolve, so they and the tail sum
+    are held to 1e-3 of ||x||, the IMF counts at most one apart, and the trial mean must
+    reconstruct: the averaged IMFs plus the averaged residue equal x plus beta times the
+    mean noise."""
     K, S, trials = 10, 10, 256
     img, w = synth.workload_eemd_512(trials)
     img, w = np.ascontiguousarray(img, NP[prec]), np.ascontiguousarray(w, NP[prec])
@@ -1011,6 +1070,12 @@ def test_eemd_512_256_trials_full_workload(prec):
     plan = Plan(p)
     imfs, res, n = plan.decompose(torch.from_numpy(img).cuda(), torch.from_numpy(w).cuda())
     torch.cuda.synchronize()
+    trials_g = []
+    if prec == capi.FP32_MIXED:
+        for m in range(16):
+            ti, tr, tn, tbeta = plan.eemd_trial(m)
+            trials_g.append((ti.double().cpu().numpy(), tr.cpu().numpy(), tn, tbeta))
+    shape = (plan.tile, plan.pass_variant)
     plan.close()
     gi = imfs.double().cpu().numpy().reshape(K, -1)
     gr = res.cpu().numpy().reshape(-1)
@@ -1023,6 +1088,15 @@ def test_eemd_512_256_trials_full_workload(prec):
     if prec == capi.FP64:
         _check_imfs(gi, gr, n, oi, orr, on, x, prec, what)
         return
+    exempt = 0
+    for m, (ti, tr, tn, tbeta) in enumerate(trials_g):
+        assert abs(tbeta - beta) <= 1e-12 * beta, (tbeta, beta)
+        xm = x + tbeta * wd[m]  # one FP64 product, one FP64 sum: as the library forms it
+        _, ex = _check_fp32_given_input(ti, tr, tn, xm, K, f"{what} realization {m}",
+                                        shape=shape)
+        exempt += sum(ex)
+    print(f"{what}: {exempt} of the realizations' IMFs exempt (decisions FP32 cannot "
+          f"resolve)")
     nx = np.linalg.norm(x)
     errs = [_rel(gi[k], oi[k], 1e-6 * nx) for k in range(K)]
     assert abs(n - on) <= 1, f"{what}: IMF count {n} vs {on}"
@@ -1034,3 +1108,76 @@ def test_eemd_512_256_trials_full_workload(prec):
     target = x + beta * wd.mean(0)
     rec = gi.sum(0) + gr
     assert np.abs(rec - target).max() <= 1e-5 * np.abs(target).max(), f"{what}: mean"
+
+
+# --------------------------------------------- adaptive stop decided on the device
+
+@pytest.mark.parametrize("stop", [capi.STOP_SD, capi.STOP_SNUMBER])
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+def test_adaptive_stop_graph_equals_host_loop(prec, stop):
+    """With the SD or S-number stop (Sec. 2.1 Step 5) a batched decomposition runs as one
+    CUDA graph whose sifting loop is a conditional node: the device decides after every
+    few passes whether an instance is still running, with no host synchronization. Its
+    results equal the host-driven loop's (graphs off) bit for bit, over two replays, and
+    (FP64) the oracle's IMFs and sift counts."""
+    imgs = [np.asarray(im, NP[prec]) for im in synth.uneven_images(9, 5150, side_range=(20, 72))]
+    side = max(im.shape[0] for im in imgs)
+    p = make_params(side, side, precision=prec, transition_len=0, max_imfs=6, stop=stop,
+                    sd_threshold=0.2, max_sifts=40, s_number=3)
+    plan = Plan(p, max_batch=len(imgs))
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    outs_g, n_g = plan.decompose_batch(xs)
+    outs_g2, n_g2 = plan.decompose_batch(xs)
+    torch.cuda.synchronize()
+    assert plan.stats().used_graph == 1
+    cnt_g = plan.counts(len(imgs))
+    plan.set_options(use_graphs=False)
+    outs_h, n_h = plan.decompose_batch(xs)
+    torch.cuda.synchronize()
+    assert plan.stats().used_graph == 0
+    cnt_h = plan.counts(len(imgs))
+    plan.close()
+    assert list(n_g) == list(n_h) == list(n_g2)
+    assert cnt_g == cnt_h
+    for i in range(len(imgs)):
+        for a, b, c in ((outs_g[i][0], outs_h[i][0], outs_g2[i][0]),
+                        (outs_g[i][1], outs_h[i][1], outs_g2[i][1])):
+            assert torch.equal(a, b) and torch.equal(a, c), i
+    if prec == capi.FP64:
+        for i in (0, 4, 8):
+            o = _oracle(imgs[i], prec, transition_len=0, max_imfs=6, stop=stop,
+                        sd_threshold=0.2, max_sifts=40, s_number=3)
+            _check_imfs(outs_g[i][0].cpu().numpy(), outs_g[i][1].cpu().numpy(), n_g[i], o[0],
+                        o[1], o[2], o[4], prec, f"image {i}")
+            assert list(cnt_g[1][i][:n_g[i]]) == list(o[3][:o[2]])
+
+
+# ------------------------------------------------------- EEMD noise drawn on the device
+
+def test_eemd_device_noise_equals_oracle_generator_fp64():
+    """EEMD without caller noise: the library draws the realizations on the device
+    (Philox4x32-10, Reading 11b). The result equals, bit for bit, the same plan run with
+    the oracle's statement of the generator passed in as noise, and matches the oracle's
+    EEMD with that noise within 1e-10; another seed gives another result."""
+    K, trials, seed = 6, 5, 0xBEEF
+    X = synth.grating_image(48, 21)
+    L = X.size
+    p = make_params(48, 48, precision=capi.FP64, transition_len=0, max_imfs=K,
+                    ensemble_trials=trials, noise_rel_std=0.2)
+    plan = Plan(p)
+    plan.noise_seed = seed
+    x = torch.from_numpy(np.ascontiguousarray(X, np.float64)).cuda()
+    imfs_d, res_d, n_d = plan.decompose(x, None)
+    w = O.white_noise(seed, trials, L)
+    imfs_w, res_w, n_w = plan.decompose(x, torch.from_numpy(w).cuda())
+    plan.noise_seed = seed + 1
+    imfs_o2, _, _ = plan.decompose(x, None)
+    torch.cuda.synchronize()
+    plan.close()
+    assert n_d == n_w
+    assert torch.equal(imfs_d, imfs_w) and torch.equal(res_d, res_w)
+    assert not torch.equal(imfs_d, imfs_o2)
+    xs = X.reshape(-1).astype(np.float64)
+    oi, orr, on = O.eemd(xs, w, 0.2 * O.std(xs), K)
+    _check_imfs(imfs_d.cpu().numpy().reshape(K, -1), res_d.cpu().numpy().reshape(-1), n_d,
+                oi, orr, on, xs, capi.FP64, "device noise")

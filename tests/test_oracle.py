@@ -619,3 +619,41 @@ def test_serial_emd_transitions_removed():
         assert np.array_equal(imfs[:, i, :], R[:, seg])
         assert np.array_equal(res[i], r[seg])
     assert np.abs(imfs.sum(0) + res - X).max() <= 1e-12
+
+
+# ------------------------------------------- Reading 11b: the library's white noise
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the known-answer vectors published with the generator
+    (Salmon, Moraes, Dror and Shaw, SC 2011; the Random123 distribution's test vectors):
+    counter and key all zero, all ones, and the hexadecimal digits of pi."""
+    assert O.philox4x32_10([0, 0, 0, 0], [0, 0]) == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c,
+                                                     0x9b00dbd8]
+    assert O.philox4x32_10([0xffffffff] * 4, [0xffffffff] * 2) == [0x408f276d, 0x41c83b0e,
+                                                                   0xa20bc7c6, 0x6d5451fd]
+    assert O.philox4x32_10([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344],
+                           [0xa4093822, 0x299f31d0]) == [0xd16cfe09, 0x94fdcceb, 0x5001e420,
+                                                         0x24126ea1]
+
+
+def test_white_noise_definition_and_moments():
+    """Reading 11b: each sample is word p mod 4 of the block with counter (p div 4, m, 0,
+    0) and the seed as key, mapped to an odd multiple of sqrt(3)/2^23 inside (-sqrt 3,
+    sqrt 3); zero mean, unit variance, no lag-1 correlation; seeds and realizations give
+    different streams, the same seed the same stream."""
+    seed, T, L = 0x1234_5678_9abc, 3, 200003
+    w = O.white_noise(seed, T, L)
+    scale = 1.7320508075688772 / 8388608.0
+    for m, p in ((0, 0), (1, 5), (2, L - 1), (0, 123457)):
+        u = O.philox4x32_10([p >> 2, m, 0, 0], [seed & 0xffffffff, seed >> 32])[p & 3]
+        assert w[m, p] == (2 * (u >> 9) - 8388607) * scale
+    i = np.round(w / scale)
+    assert np.all(i % 2 == 1) and np.abs(w).max() < np.sqrt(3.0)
+    for m in range(T):
+        assert abs(w[m].mean()) < 5.0 / np.sqrt(L)
+        assert abs(w[m].var() - 1.0) < 0.02
+        assert abs(np.corrcoef(w[m, :-1], w[m, 1:])[0, 1]) < 5.0 / np.sqrt(L)
+    assert not np.array_equal(w[0], w[1])
+    assert np.array_equal(O.white_noise(seed, 1, 1000)[0], w[0, :1000])
+    assert np.array_equal(O.white_noise(seed, 1, L, first=2)[0], w[2])
+    assert not np.array_equal(O.white_noise(seed + 1, 1, 1000)[0], w[0, :1000])

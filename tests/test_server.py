@@ -139,3 +139,92 @@ def test_server_destroy_while_busy_leaves_gpu_usable():
     _, _, n = plan.decompose(torch.from_numpy(X).cuda())
     plan.close()
     assert n >= 3
+
+
+def test_server_large_request_lane_results_equal_alone():
+    """A request of at least 2^21 serialized samples runs in the server's second lane
+    (its own worker and stream) while small requests keep arriving; every result equals
+    the same input decomposed alone."""
+    base = make_params(1600, 1600, precision=capi.FP32_MIXED, transition_len=0, max_imfs=6)
+    server = Server(base, 2 << 30, 8)
+    big = synth.grating_image(1500, 4)  # 2.25 M samples
+    items = [(big, capi.ORDER_ROWS)] + _mix(52)
+    xs = [torch.from_numpy(np.asarray(X, np.float32)).cuda() for X, _ in items]
+    subs = [server.submit(x, order=o) for x, (_, o) in zip(xs, items)]
+    res = _wait(server, [s[0] for s in subs])
+    server.close()
+    for (X, order), x, (t, imfs, r) in zip(items, xs, subs):
+        assert res[t].status == capi.SEMD_OK
+        plan = Plan(make_params(*X.shape, precision=capi.FP32_MIXED, transition_len=0,
+                                max_imfs=6, order=order))
+        ai, ar, an = plan.decompose(x)
+        torch.cuda.synchronize()
+        plan.close()
+        assert res[t].n_imfs == an
+        assert torch.equal(imfs, ai) and torch.equal(r, ar), X.shape
+
+
+# ------------------------------------------------------- failures made on the host
+
+def test_server_allocation_failure_is_reported():
+    """A budget no GPU can hold: creation fails with SEMD_ENOMEM and a message, nothing is
+    left behind, and a server of a sensible size works afterwards."""
+    base = make_params(16, 1024, precision=capi.FP32_MIXED, max_imfs=4)
+    with pytest.raises(capi.SemdError) as ei:
+        Server(base, 1 << 52, 4)
+    assert ei.value.status == capi.SEMD_ENOMEM
+    assert "server set-up" in capi.serial_emd_server_last_error(None)
+    server = Server(base, 8 << 20, 2)
+    x = torch.from_numpy(synth.tone_chirp_series(2, 700, 5).astype(np.float32)).cuda()
+    t, _, _ = server.submit(x)
+    assert _wait(server, [t])[t].status == capi.SEMD_OK
+    server.close()
+
+
+def test_server_poisoned_requests_do_not_disturb_others():
+    """Requests whose samples are NaN or infinite (all of them, or a few) run to the end
+    beside ordinary ones; the ordinary results stay bit-identical to decomposing alone."""
+    base = make_params(64, 4096, precision=capi.FP32_MIXED, transition_len=-1, max_imfs=6)
+    server = Server(base, 64 << 20, 6)
+    items = _mix(61)
+    bad = [np.full((3, 800), np.nan, np.float32), synth.tone_chirp_series(2, 900, 9)]
+    bad[1] = bad[1].astype(np.float32)
+    bad[1][0, 100:110] = np.inf
+    bad[1][1, 400] = np.nan
+    xs = [torch.from_numpy(np.asarray(X, np.float32)).cuda() for X, _ in items]
+    xb = [torch.from_numpy(b).cuda() for b in bad]
+    subs = []
+    for k, (x, (_, o)) in enumerate(zip(xs, items)):
+        subs.append(server.submit(x, order=o))
+        if k == 2:
+            tb = [server.submit(b) for b in xb]
+    res = _wait(server, [s[0] for s in subs] + [t[0] for t in tb])
+    server.close()
+    for t, _, _ in tb:
+        assert res[t].status == capi.SEMD_OK
+    assert res[tb[0][0]].n_imfs == 0  # no sample of an all-NaN signal is an extremum
+    for (X, order), x, (t, imfs, r) in zip(items, xs, subs):
+        plan = Plan(make_params(*X.shape, precision=capi.FP32_MIXED, transition_len=-1,
+                                max_imfs=6, order=order))
+        ai, ar, an = plan.decompose(x)
+        torch.cuda.synchronize()
+        plan.close()
+        assert res[t].status == capi.SEMD_OK and res[t].n_imfs == an
+        assert torch.equal(imfs, ai) and torch.equal(r, ar), X.shape
+
+
+def test_server_wait_time_limit():
+    """serial_emd_wait with a time limit far below the request's run time returns
+    SEMD_ETIMEOUT (None here) and leaves the request pending; a later wait gets it."""
+    base = make_params(1024, 1024, precision=capi.FP32_MIXED, transition_len=0, max_imfs=10)
+    server = Server(base, 1 << 30, 2)
+    x = torch.from_numpy(synth.grating_image(1024, 77).astype(np.float32)).cuda()
+    t, _, _ = server.submit(x)
+    assert server.wait(t, 0.001) is None
+    r = server.wait(t, 60000.0)
+    assert r is not None and r.status == capi.SEMD_OK and r.n_imfs >= 1
+    with pytest.raises(capi.SemdError):
+        server.wait(t, 1.0)  # returned once
+    with pytest.raises(capi.SemdError):
+        server.wait(t + 1000, -1.0)
+    server.close()
