@@ -35,15 +35,17 @@ METRIC = "serialized samples sifted/s: batched FP32 vs plain FP64 on GB300; p99 
 UNIT = "samples*sifts/s"
 L2_FLUSH_BYTES = 512 << 20
 EEMD_NOISE_SEED = 20210629 + 4  # seed of the white noise the library draws for the EEMD leg
-# DRAM bytes (read + write) of one k_pass launch of the default workload (256-sample tiles)
-# per pass-kernel variant, from an ncu capture of that launch with the dram__bytes counters
-# (cold caches, as ncu replays). Emptied whenever the pass kernel changes, until the changed
-# kernel is captured again; an empty entry is reported as null.
-PASS_TRAFFIC_TEXTURE = {}
+# DRAM bytes (read + write) of one k_pass launch of the default workload (pass launch 6 of a
+# decomposition: an IMF-1 sift) per (tile, variant), from an ncu capture of that launch with
+# the dram__bytes counters (cold caches, as ncu replays). Emptied whenever the pass kernel
+# changes, until the changed kernel is captured again; an empty entry is reported as null.
+PASS_TRAFFIC_TEXTURE = {(128, 0): 588032, (128, 1): 585216, (256, 0): 470272,
+                        (256, 1): 466176, (512, 0): 412416, (512, 1): 413184}
 # FP64-pipe lane operations (sm__inst_executed_pipe_fp64 x 32) of one k_pass<double> launch
 # of the default workload, per (tile, variant), from an ncu capture of that launch; emptied
 # whenever the pass kernel changes.
-PASS_FP64_OPS_TEXTURE = {}
+PASS_FP64_OPS_TEXTURE = {(128, 0): 173952 * 32, (128, 1): 173952 * 32, (256, 0): 134356 * 32,
+                         (256, 1): 134356 * 32, (512, 0): 86475 * 32, (512, 1): 86475 * 32}
 
 
 def _peaks():
@@ -222,6 +224,36 @@ def profile_pass(run, steps, flush):
             tot["bytes"] += st.pass_bytes
     plan.set_options(use_graphs=True, profile=False)
     return tot
+
+
+def decompose_once(args, wl, device):
+    """One decomposition of the workload with no warm-up and without CUDA graphs, so that
+    every kernel is a separate launch in a fixed order (for ncu captures of one launch):
+    precision from --forms (its first entry), pass shape from --tile / --pass-variant."""
+    import torch
+    from paper_2106_15319_gb300 import capi
+    from paper_2106_15319_gb300.serial_emd import Plan, make_params
+    prec = capi.FP64 if args.forms.split(",")[0] == "fp64" else capi.FP32_MIXED
+    dt = np.float64 if prec == capi.FP64 else np.float32
+    X = np.ascontiguousarray(wl["X"], dt)
+    rows, cols = X.shape
+    plan = Plan(make_params(rows, cols, precision=prec, transition_len=wl["D"],
+                            max_imfs=wl["K"], fixed_sifts=wl["S"],
+                            ensemble_trials=wl["trials"]))
+    if args.tile:
+        plan.tile = args.tile
+    if args.pass_variant is not None:
+        plan.pass_variant = args.pass_variant
+    if wl.get("seed") is not None:
+        plan.noise_seed = wl["seed"]
+    noise = torch.from_numpy(np.ascontiguousarray(wl["W"], dt)).to(device) \
+        if wl["trials"] > 1 and wl["W"] is not None else None
+    plan.set_options(use_graphs=False, profile=False)
+    _, _, n = plan.decompose(torch.from_numpy(X).to(device), noise)
+    torch.cuda.synchronize()
+    out = {"imfs": n, "tile": plan.tile, "variant": plan.pass_variant}
+    plan.close()
+    return out
 
 
 def e2e_ours(wl, precision, steps, warmup, device):
@@ -557,6 +589,10 @@ def arm_ours(args):
     wl = workload_inputs(args.workload, args.trials)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     peak, peak_kind = _peaks()
+    if args.only_leg == "once":  # one decomposition of the workload, graphs off (profiling)
+        print(json.dumps({"only_leg": "once", "result": decompose_once(args, wl, device)}),
+              flush=True)
+        return
     if args.only_leg:  # one extra leg alone (for profiling it), no headline line
         legs = {"batched": lambda: batched_eemd(args, device, flush, peak, peak_kind, world),
                 "images": lambda: batched_images(args, device, flush, peak, peak_kind, world),
@@ -589,15 +625,18 @@ def arm_ours(args):
         # instructions per launch (ncu) against the measured FP64 FMA rate
         prof64 = profile_pass(r64, 1, flush)
         avg64 = prof64["pass_ms"] / max(1, prof64["pass_n"])
+        t64 = r64["plan"].launch_times(0)
+        l6 = t64[5] if len(t64) > 5 else avg64  # pass launch 6, the one ncu counted
         peak64 = capi.serial_emd_fma_rate(capi.FP64, 4096) / 2.0  # FMA lane-ops, G/s
         ops = PASS_FP64_OPS_TEXTURE.get((r64_shape["tile"], r64_shape["variant"])) \
             if args.workload == "texture256" else None
         fp64_roof = {"bound": "alu", "kernel": "k_pass<double>", "unit": "G FP64 ops/s",
                      "peak": peak64, "peak_source": "measured: serial_emd_fma_rate (FP64 "
                      "FMA chains; 1 op = 1 lane FMA)", "avg_launch_us": avg64 * 1e3,
+                     "launch": "pass launch 6 (an IMF-1 sift)", "launch_us": l6 * 1e3,
                      "fp64_ops_per_launch": ops,
-                     "achieved": ops / (avg64 * 1e-3) / 1e9 if ops else None,
-                     "frac": ops / (avg64 * 1e-3) / 1e9 / peak64 if ops else None}
+                     "achieved": ops / (l6 * 1e-3) / 1e9 if ops else None,
+                     "frac": ops / (l6 * 1e-3) / 1e9 / peak64 if ops else None}
         r64["plan"].close()
     else:
         ms64, v64, r64_shape = None, None, None
@@ -637,9 +676,10 @@ def arm_ours(args):
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind,
                      # the captures were of 256-sample tiles (64 CTAs); other tiles differ
-                     "traffic": PASS_TRAFFIC_TEXTURE.get(r32["shape"]["variant"])
-                     if args.workload == "texture256" and r32["shape"]["tile"] == 256
-                     else None,
+                     "traffic": PASS_TRAFFIC_TEXTURE.get((r32["shape"]["tile"],
+                                                          r32["shape"]["variant"]))
+                     if args.workload == "texture256" else None,
+                     "traffic_launch": "pass launch 6 (an IMF-1 sift), ncu, cold caches",
                      "avg_launch_us": pass_avg_ms * 1e3, "bytes_per_launch": bytes_per_launch,
                      "launches": prof["pass_n"], "reduce_avg_us":
                          prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
@@ -858,6 +898,10 @@ def serving(args, device):
                     _t.sleep(0.0002)
             wall = max(v[1] for v in res.values()) - arr[0]
             lat = np.array([r.queue_ms + r.run_ms for r, _ in res.values()])
+            lat_small = np.array([r.queue_ms + r.run_ms for k, (r, _) in res.items()
+                                  if sizes[k] < (1 << 21)])
+            lat_big = np.array([r.queue_ms + r.run_ms for k, (r, _) in res.items()
+                                if sizes[k] >= (1 << 21)])
             ss = sum(r.sifts * sizes[k] for k, (r, _) in res.items())
             ok = all(r.status == capi.SEMD_OK for r, _ in res.values())
             out["rates"].append({
@@ -865,6 +909,13 @@ def serving(args, device):
                 "all_ok": bool(ok),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "max_ms": float(lat.max()),
+                "small_requests": {"count": int(lat_small.size),
+                                   "p50_ms": float(np.percentile(lat_small, 50)),
+                                   "p99_ms": float(np.percentile(lat_small, 99))}
+                if lat_small.size else None,
+                "large_requests": {"count": int(lat_big.size),
+                                   "p50_ms": float(np.percentile(lat_big, 50)),
+                                   "max_ms": float(lat_big.max())} if lat_big.size else None,
                 "served_per_s": n / wall, "samples_sifts_per_s": ss / wall,
                 "samples": int(sum(sizes[:n]))})
     finally:
@@ -1133,8 +1184,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass shape (no autotuning before the warm-up)")
     ap.add_argument("--only-leg", default=None,
-                    choices=["batched", "images", "slices", "ceemdan", "dsweep", "serving"],
-                    help="run one extra leg alone and print its result (for profiling)")
+                    choices=["batched", "images", "slices", "ceemdan", "dsweep", "serving",
+                             "once"],
+                    help="run one extra leg alone and print its result (for profiling); "
+                         "once: one decomposition of --workload, graphs off, no warm-up")
     ap.add_argument("--no-fp32-errors", action="store_true",
                     help="skip the untimed FP32 per-IMF error report of the EEMD leg")
     ap.add_argument("--error-trials", type=int, default=4,

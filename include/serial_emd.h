@@ -338,7 +338,8 @@ typedef struct semd_tune_result {
 
 /*
  * Times the plan's decomposition of `count` inputs (as serial_emd_decompose_batch takes
- * them; for an ensemble plan one input and its noise, as serial_emd_decompose) for every
+ * them; for an ensemble plan one input and its noise, or NULL noise to let the library
+ * draw it, as serial_emd_decompose) for every
  * pass-kernel shape: tile 128, 256 or 512, the register budget where the kernel has two,
  * and CTAs per SM of the persistent grid (as many as fit, or fewer). Each shape runs once untimed, then `repeats` times (1..100)
  * with CUDA events on `stream`; the median counts. The fastest shape is kept on the plan

@@ -186,10 +186,21 @@ def _dtype_of(precision: int):
     return _TORCH_DTYPES[precision]
 
 
-def _need(t, what: str, dtype, numel: int | None = None, optional: bool = False):
+_NO_DEVICE = object()
+
+
+def _current_device():
+    """The current CUDA device index, or a marker when no device is present (the device
+    check is then skipped: nothing can run anyway)."""
+    import torch
+    return torch.cuda.current_device() if torch.cuda.is_available() else _NO_DEVICE
+
+
+def _need(t, what: str, dtype, numel: int | None = None, optional: bool = False, dev=None):
     """Refuses (SEMD_EINVAL, before any library call) a buffer the C ABI would read or write
     out of bounds or misinterpret: it must be a contiguous CUDA tensor on the current
-    device, of the element type the call uses, with at least `numel` elements."""
+    device, of the element type the call uses, with at least `numel` elements. dev: the
+    current device, when the caller checks many tensors (looked up here otherwise)."""
     if t is None:
         if optional:
             return
@@ -198,14 +209,15 @@ def _need(t, what: str, dtype, numel: int | None = None, optional: bool = False)
         return
     if not getattr(t, "is_cuda", False):
         raise SemdError(SEMD_EINVAL, f"{what}: not a CUDA tensor")
-    import torch
-    if torch.cuda.is_available() and t.device.index != torch.cuda.current_device():
+    if dev is None:
+        dev = _current_device()
+    if dev is not _NO_DEVICE and t.device.index != dev:
         raise SemdError(SEMD_EINVAL, f"{what}: on cuda:{t.device.index}, not on the current "
-                                     f"device cuda:{torch.cuda.current_device()}")
+                                     f"device cuda:{dev}")
     if not t.is_contiguous():
         raise SemdError(SEMD_EINVAL, f"{what}: not contiguous")
     want = _dtype_of(dtype)
-    if t.dtype != want:
+    if t.dtype is not want:
         raise SemdError(SEMD_EINVAL, f"{what}: dtype {t.dtype}, the call needs {want}")
     if numel is not None and t.numel() < numel:
         raise SemdError(SEMD_EINVAL, f"{what}: {t.numel()} elements, the call needs {numel}")
@@ -296,20 +308,50 @@ def serial_emd_plan_set_noise_seed(plan: int, seed: int) -> None:
     _check(load().serial_emd_plan_set_noise_seed(plan, seed), plan)
 
 
+_INSTANCE_DTYPE = None
+
+
+def _instance_array(items, p):
+    """The semd_instance array of a batch, built with vectorized numpy (a batch may hold
+    thousands of inputs), after the per-item buffer checks."""
+    global _INSTANCE_DTYPE
+    import numpy as np
+    if _INSTANCE_DTYPE is None:
+        _INSTANCE_DTYPE = np.dtype([("x", "<u8"), ("rows", "<i8"), ("cols", "<i8"),
+                                    ("imfs", "<u8"), ("res", "<u8")], align=True)
+        assert _INSTANCE_DTYPE.itemsize == ctypes.sizeof(semd_instance)
+    n = len(items)
+    if p is not None:
+        dev = _current_device()
+        want, wres = _dtype_of(p.precision), _dtype_of(FP64)
+        for i, (x, imfs, res) in enumerate(items):
+            rc = x.shape[0] * x.shape[1]
+            if isinstance(x, int) or isinstance(imfs, int) or not (
+                    x.is_cuda and imfs.is_cuda and x.dtype is want and imfs.dtype is want
+                    and x.is_contiguous() and imfs.is_contiguous()
+                    and imfs.numel() >= p.max_imfs * rc
+                    and (res is None or (res.is_cuda and res.dtype is wres
+                                         and res.is_contiguous() and res.numel() >= rc))
+                    and (i > 0 or dev is _NO_DEVICE or x.device.index == dev)):
+                _need(x, "items[%d].x" % i, p.precision, rc, dev=dev)
+                _need(imfs, "items[%d].imfs" % i, p.precision, p.max_imfs * rc, dev=dev)
+                _need(res, "items[%d].residue" % i, FP64, rc, optional=True, dev=dev)
+    a = np.zeros(n, _INSTANCE_DTYPE)
+    a["x"] = [_ptr(x) for x, _, _ in items]
+    a["rows"] = [x.shape[0] for x, _, _ in items]
+    a["cols"] = [x.shape[1] for x, _, _ in items]
+    a["imfs"] = [_ptr(m) for _, m, _ in items]
+    a["res"] = [_ptr(r) or 0 for _, _, r in items]
+    return a
+
+
 def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True):
     """items: list of (x, imfs, residue) CUDA tensors, x 2D (rows, cols)."""
-    p = _PLAN_PARAMS.get(plan)
-    arr = (semd_instance * len(items))()
-    for i, (x, imfs, res) in enumerate(items):
-        if p is not None:
-            rc = x.shape[0] * x.shape[1]
-            _need(x, f"items[{i}].x", p.precision, rc)
-            _need(imfs, f"items[{i}].imfs", p.precision, p.max_imfs * rc)
-            _need(res, f"items[{i}].residue", FP64, rc, optional=True)
-        arr[i] = semd_instance(_ptr(x), x.shape[0], x.shape[1], _ptr(imfs), _ptr(res))
+    a = _instance_array(items, _PLAN_PARAMS.get(plan))
     n = (ctypes.c_int * len(items))()
-    rc = load().serial_emd_decompose_batch(plan, len(items), arr, n if wait else None,
-                                           _stream(stream))
+    rc = load().serial_emd_decompose_batch(
+        plan, len(items), a.ctypes.data_as(ctypes.POINTER(semd_instance)), n if wait else None,
+        _stream(stream))
     _check(rc, plan)
     return list(n) if wait else None
 

@@ -137,8 +137,8 @@ semd_status serial_emd_plan_autotune(semd_plan_t plan, int count, const semd_ins
     NvtxRange nvtx("serial_emd_plan_autotune");
     semd_plan_s &pl = *plan;
     const bool eemd = pl.p.ensemble_trials > 1;
-    if (!inst || count < 1 || count > (eemd ? 1 : pl.ws.cap_inst) || (eemd && !d_noise)) {
-        pl.err = "autotune: count must be in [1, max_batch] (1 with noise for ensemble plans)";
+    if (!inst || count < 1 || count > (eemd ? 1 : pl.ws.cap_inst)) {
+        pl.err = "autotune: count must be in [1, max_batch] (1 for ensemble plans)";
         return SEMD_EINVAL;
     }
     if (repeats < 1 || repeats > 100) {

@@ -930,12 +930,11 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         // their mean, the subtraction, and the SD partial sums. A lane's samples share
         // few intervals: an interval's cubic is read when a knot starts it, and the local
         // coordinate u = k - t_left advances by exact integer steps in between.
-        // The local coordinates are kept as floating-point integers (exact: |u| < 2^24),
-        // advanced by 1 per sample and reset to 0 at a knot, instead of converting k - t.
+        // The local coordinate of each sample is converted from the integer k - t, so the
+        // samples' evaluations do not depend on one another (a short latency chain).
         int q0 = bx + (MX & 1u), q1 = b1 + bn + (MN & 1u);
         Coef<R> c0 = P.cf[q0], c1 = P.cf[q1];
         int t0 = P.ky[q0].t, t1 = P.ky[q1].t;
-        R u0 = R(k0 - t0), u1 = R(k0 - t1);
 #pragma unroll
         for (int s = 0; s < SPL; ++s) {
             const int k = k0 + s;
@@ -944,25 +943,21 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
                     ++q0;
                     c0 = P.cf[q0];
                     t0 = k;
-                    u0 = R(0);
                 }
                 if ((MN >> s) & 1u) {
                     ++q1;
                     c1 = P.cf[q1];
                     t1 = k;
-                    u1 = R(0);
                 }
             }
-            const R e0 = horner(c0, u0);
-            const R e1 = horner(c1, u1);
+            const R e0 = horner(c0, R(k - t0));
+            const R e1 = horner(c1, R(k - t1));
             const R mean = radd(e0, e1);
             hn[s] = rsub(v[s], mean);
             if (pa.need_sd && k < cnt) {
                 pn += mean * mean;
                 pd += v[s] * v[s];
             }
-            u0 = radd(u0, R(1));
-            u1 = radd(u1, R(1));
         }
         // the instance's last sample when it is a knot (the end-point rule puts one there,
         // as the right bracket of both envelopes): the envelopes take the knot values there
@@ -1177,9 +1172,9 @@ __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
 // warp: lane l eliminates its contiguous segment of rows in the working precision, the
 // 32 segment-end unknowns are solved to FP64 accuracy, and the segments are
 // back-substituted. GB300's FP64 pipe is narrow (a warp-wide FP64 instruction,
-// conversions included, occupies it for many cycles), so FP64 work is kept to O(1)
-// instructions per lane: FP32 plans solve the 32-unknown system by FP32 cyclic
-// reduction refined once with its residual evaluated in FP64; FP64 plans run the
+// conversions included, occupies it for many cycles), so FP32 plans keep FP64 out of the
+// solve: the 32-unknown system is solved by FP32 cyclic reduction refined once with its
+// residual evaluated in float-float arithmetic (FP64-accurate); FP64 plans run the
 // cyclic reduction in FP64.
 
 // Entry kinds of the reduced system.
@@ -1330,9 +1325,49 @@ __device__ __forceinline__ double level2_solve(const SegElim<double> &g, int q, 
     warp_reduced_solve<double, 1, 32>(g, q, has_next, zl, zr, Z);
     return Z[0];
 }
-// FP32 plans: cyclic reduction in FP32, the residual of the reduced rows formed and
-// evaluated in FP64, one FP32 correction solve: the FP64-accurate solution of the
-// system (it is diagonally dominant, condition number a few units).
+// Error-free transformations of single-precision arithmetic (Dekker, Knuth): a product
+// and a sum as an unevaluated pair hi + lo equal to the exact result.
+__device__ __forceinline__ float two_prod(float a, float b, float &lo)
+{
+    const float p = __fmul_rn(a, b);
+    lo = __fmaf_rn(a, b, -p);
+    return p;
+}
+__device__ __forceinline__ float two_sum(float a, float b, float &lo)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+// A running sum in float-float (hi + lo, about 48 significant bits).
+struct FFSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float h, float l)
+    {
+        float e;
+        const float s = two_sum(hi, h, e);
+        lo = __fadd_rn(__fadd_rn(lo, l), e);
+        hi = s;
+    }
+    // a * b * c with the two products error-free (the last one's error to first order)
+    __device__ __forceinline__ void add_prod3(float a, float b, float c)
+    {
+        float l1, l2;
+        const float p1 = two_prod(a, b, l1);
+        const float p2 = two_prod(p1, c, l2);
+        add(p2, __fmaf_rn(l1, c, l2));
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+// FP32 plans: cyclic reduction in FP32, then the residual of the reduced rows evaluated in
+// float-float arithmetic (error-free products and sums: about 48 significant bits, no FP64
+// instruction, which GB300's narrow FP64 pipe would serialize) and one FP32 correction
+// solve: the FP64-accurate solution of the system (it is diagonally dominant, condition
+// number a few units). The reduced row of a lane (reduced_row) is expanded in the
+// residual's terms: D - A z_{l-1} - B z_l - C z_{l+1} with A = al beE, B = bl + al gaE +
+// cl nbeS, C = cl ngaS, D = dl - al alE - cl nalS.
 __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, bool has_next)
 {
     const int lane = threadIdx.x & 31;
@@ -1343,25 +1378,28 @@ __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, b
     reduced_row(g, q, has_next, nalS, nbeS, ngaS, A, B, C, D);
     PcrFactors<float, 32> f;
     const float Z = pcr_solve_keep<float, 32>(A, B, C, D, f);
-    SegElim<double> gd;
-    gd.alE = g.alE;
-    gd.beE = g.beE;
-    gd.gaE = g.gaE;
-    gd.al = g.al;
-    gd.bl = g.bl;
-    gd.cl = g.cl;
-    gd.dl = g.dl;
-    double Ad, Bd, Cd, Dd;
-    reduced_row(gd, q, has_next, (double)nalS, (double)nbeS, (double)ngaS, Ad, Bd, Cd, Dd);
-    const double z = (double)Z;
-    double zm = __shfl_up_sync(FULLMASK, z, 1), zp = __shfl_down_sync(FULLMASK, z, 1);
+    float zm = __shfl_up_sync(FULLMASK, Z, 1), zp = __shfl_down_sync(FULLMASK, Z, 1);
     if (lane == 0)
-        zm = 0.0;
+        zm = 0.f;
     if (lane == 31)
-        zp = 0.0;
-    const double res = Dd - (Ad * zm + Bd * z + Cd * zp);
-    const float dZ = pcr_apply<float, 32>(f, (float)res);
-    return z + (double)dZ;
+        zp = 0.f;
+    FFSum r;
+    if (q >= 1) {
+        r.add(g.dl, 0.f);
+        r.add_prod3(-g.al, g.alE, 1.f);
+        r.add_prod3(-g.al, g.beE, zm);
+        r.add_prod3(-g.bl, 1.f, Z);
+        r.add_prod3(-g.al, g.gaE, Z);
+        if (has_next) {
+            r.add_prod3(-g.cl, nalS, 1.f);
+            r.add_prod3(-g.cl, nbeS, Z);
+            r.add_prod3(-g.cl, ngaS, zp);
+        }
+    } else { // the dummy row Z = 0
+        r.add_prod3(-1.f, 1.f, Z);
+    }
+    const float dZ = pcr_apply<float, 32>(f, r.value());
+    return (double)Z + (double)dZ;
 }
 
 // SMALL: instances whose reduced systems have at most kRedSmallRows rows (the host
