@@ -409,6 +409,20 @@ int64_t serial_emd_plan_launch_times(semd_plan_t plan, int kind, float *ms, int6
  */
 semd_status serial_emd_fma_rate(int precision, int iters, double *gflops, void *stream);
 
+/*
+ * How the interface solve (the reduced spline system of Sec. 2.1 Step 2, partitioned by
+ * tiles) is run on the current GPU for a precision and spline-end rule: instances of
+ * *min_tiles to *max_tiles tiles are solved by a thread-block cluster of *cluster CTAs per
+ * envelope (distributed shared memory), all others by one CTA per envelope (in shared
+ * memory while the system fits there, past *max_tiles with a global-memory scratch).
+ * *cluster = 0 (and the range 0..0) when clusters are not used (not-a-knot ends, or a
+ * device without clusters of 8 or 16 CTAs). The choice depends on an instance's tile
+ * count alone, never on the other instances of a batch. Sets the kernel attributes on the
+ * current device. Errors: EINVAL (NULL output, unknown precision or rule), ECUDA.
+ */
+semd_status serial_emd_interface_solve_shape(int precision, int spline_end, int *cluster,
+                                             int64_t *min_tiles, int64_t *max_tiles);
+
 /* Releases a plan and its workspaces (after its work on any stream has finished). */
 void serial_emd_destroy(semd_plan_t plan);
 

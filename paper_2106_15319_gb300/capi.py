@@ -135,6 +135,10 @@ SIGNATURES = {
                                                       ctypes.c_int64]),
     "serial_emd_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "serial_emd_interface_solve_shape": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                                        ctypes.POINTER(ctypes.c_int),
+                                                        ctypes.POINTER(ctypes.c_int64),
+                                                        ctypes.POINTER(ctypes.c_int64)]),
     "serial_emd_destroy": (None, [ctypes.c_void_p]),
     "serial_emd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "serial_emd_server_create": (ctypes.c_int, [ctypes.POINTER(semd_params), ctypes.c_size_t,
@@ -535,6 +539,17 @@ def serial_emd_fma_rate(precision: int, iters: int = 4096, stream=None) -> float
     if rc != 0:
         raise SemdError(rc, "fma rate probe failed")
     return g.value
+
+
+def serial_emd_interface_solve_shape(precision: int, spline_end: int = 0) -> tuple:
+    """(cluster CTAs per envelope, min tiles, max tiles) of the cluster interface solve on
+    the current GPU; cluster 0 when it is not used."""
+    c, lo, hi = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    rc = load().serial_emd_interface_solve_shape(precision, spline_end, ctypes.byref(c),
+                                                 ctypes.byref(lo), ctypes.byref(hi))
+    if rc != 0:
+        raise SemdError(rc, "interface solve shape query failed")
+    return c.value, lo.value, hi.value
 
 
 def serial_emd_destroy(plan: int) -> None:

@@ -411,6 +411,42 @@ __device__ __forceinline__ void storen(T *p, int k0, int cnt, const T (&v)[N])
     }
 }
 
+// The same loads cached in L2 only (not L1): for data another kernel wrote while this one
+// was already resident.
+template <int N>
+__device__ __forceinline__ void vload_cg(const float *p, float (&v)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const float4 a = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+        v[4 * i] = a.x;
+        v[4 * i + 1] = a.y;
+        v[4 * i + 2] = a.z;
+        v[4 * i + 3] = a.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void vload_cg(const double *p, double (&v)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(p) + i);
+        v[2 * i] = a.x;
+        v[2 * i + 1] = a.y;
+    }
+}
+template <typename T, int N>
+__device__ __forceinline__ void loadn_cg(const T *p, int k0, int cnt, T (&v)[N])
+{
+    if (k0 + N <= cnt) {
+        vload_cg<N>(p + k0, v);
+    } else {
+#pragma unroll
+        for (int s = 0; s < N; ++s)
+            v[s] = (k0 + s < cnt) ? __ldcg(p + k0 + s) : T(0);
+    }
+}
+
 // Knots (tile position and value) of this lane's samples into the pool in rank order:
 // maxima at slots 1 + bx.., minima at slots m0 + 3 + bn...
 // A sample is at most one kind of extremum, so each sample takes at most one store: the
@@ -801,28 +837,72 @@ __device__ __forceinline__ bool stage_tile(const PassArgs &pa, StageBuf<R, 32 * 
     return true;
 }
 
+// A warp's first tile, read before the pass kernel waits for the interface solve: the
+// signal, its halo samples and its stored extremum masks, which the previous pass wrote.
+// The interface solve, the kernel before this one, lets it start only once it has itself
+// waited for that pass (so those writes are complete); the loads bypass L1. The signal
+// buffer is predicted from the previous pass's parity (the interface solve flips it after
+// every pass); the pass uses these values only if the prediction holds and the tile sifts
+// or commits.
+template <typename R, int SPL>
+struct PreTile {
+    R v[SPL];
+    R hcl, hcr;
+    uint2 km;
+    int hpar;
+};
+template <typename R, int SPL>
+__device__ __forceinline__ void pre_tile(const PassArgs &pa, int64_t gt, PreTile<R, SPL> &pt)
+{
+    constexpr int TW = 32 * SPL;
+    const int lane = threadIdx.x & 31;
+    const int ii = pa.tile_inst[gt];
+    const Inst &in = pa.inst[ii];
+    const int ppar = __shfl_sync(FULLMASK, __ldcg(&pa.state[ii].pass_par), 0);
+    pt.hpar = (ppar & 1) ^ 1;
+    const int L = (int)in.L, lt = (int)(gt - in.tile0), ts = lt * TW;
+    const int cnt = min(TW, L - ts);
+    const R *hsrc = (const R *)in.h[pt.hpar] + ts;
+    loadn_cg<R, SPL>(hsrc, lane * SPL, cnt, pt.v);
+    pt.hcl = (lane == 0 && ts > 0) ? __ldcg(hsrc - 1) : R(0);
+    pt.hcr = (lane == 31 && ts + TW < L) ? __ldcg(hsrc + TW) : R(0);
+    pt.km = __ldcg(in.kmask + (int64_t)lt * 32 + lane);
+}
+
 // ---------------------------------------------------------------------------------
 // One sifting pass over one warp tile (the body of k_pass).
 // STAGE: the next tile's inputs are copied into the stage buffer while this one computes
 // (else only prefetched into L2: a smaller kernel, for launches with one tile per warp).
 // `staged`: this tile's inputs are in the stage buffer (copied by the previous tile);
-// returns whether the next tile's were started.
+// `pre`: the inputs read before the kernel's wait (a warp's first tile), or null.
+// Returns whether the next tile's were started.
 template <typename R, int SPL, bool STAGE>
 __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * SPL> &P,
                                           StageBuf<R, 32 * SPL> &B, int64_t gt, bool first,
-                                          bool prefetch_next, bool staged)
+                                          bool prefetch_next, bool staged,
+                                          const PreTile<R, SPL> *pre)
 {
     constexpr int TW = 32 * SPL;
     const int lane = threadIdx.x & 31;
+    const int eh = lane >> 4, hl = lane & 15; // half-warp = envelope in the spline phases
     const int ii = pa.tile_inst[gt];
     State *stp = pa.state + ii;
+    const Inst &in = pa.inst[ii];
+    const int lt = (int)(gt - in.tile0);
+    // the tile's interface values (written by the interface solve just before), read
+    // together with the state unless the previous tile staged them
+    SolveVals<R> sv{};
+    int2 tpn = make_int2(0, 0);
+    if (!(STAGE && staged)) {
+        const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
+        sv = solve_vals(so, R(0));
+        tpn = *reinterpret_cast<const int2 *>(&so.tp);
+    }
     const int mode = stp->mode;
     if (mode == MODE_DONE)
         return false;
     const int hpar = stp->hpar, rpar = stp->rpar, imfc = stp->imf_count;
-    const Inst &in = pa.inst[ii];
     const int L = (int)in.L;
-    const int lt = (int)(gt - in.tile0);
     if (lt == 0 && lane == 0) {
         stp->pass_mode = mode;
         stp->pass_sift = stp->sift_count;
@@ -841,13 +921,9 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     const bool commit = mode == MODE_SIFT_COMMIT || mode == MODE_COMMIT;
     const bool use_r = commit || mode == MODE_INIT;
     const int k0 = lane * SPL;
-    const int eh = lane >> 4, hl = lane & 15; // half-warp = envelope in the spline phases
 
     R v[SPL], hn[SPL];
     R hcl = R(0), hcr = R(0); // current signal at the halo samples -1 and TW
-    // the tile's interface values (written by the interface solve just before)
-    SolveVals<R> sv{};
-    int2 tpn = make_int2(0, 0);
     uint2 km = make_uint2(0u, 0u); // the signal's extremum masks and ranks (sifting modes)
     if (STAGE && staged) {
         // copied in while the previous tile computed
@@ -865,19 +941,24 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         }
         __syncwarp(); // the stage is refilled below
     } else {
+        const bool have = pre != nullptr && pre->hpar == hpar;
         if (mode != MODE_INIT) {
-            loadn<R, SPL>(hsrc, k0, cnt, v);
-            if (lane == 0 && hasL)
-                hcl = hsrc[-1];
-            if (lane == 31 && hasR)
-                hcr = hsrc[TW];
+            if (have) {
+#pragma unroll
+                for (int s = 0; s < SPL; ++s)
+                    v[s] = pre->v[s];
+                hcl = pre->hcl;
+                hcr = pre->hcr;
+            } else {
+                loadn<R, SPL>(hsrc, k0, cnt, v);
+                if (lane == 0 && hasL)
+                    hcl = hsrc[-1];
+                if (lane == 31 && hasR)
+                    hcr = hsrc[TW];
+            }
         }
-        if (sift) {
-            const TileSolve &so = in.tsol[(int64_t)eh * in.ntiles + lt];
-            sv = solve_vals(so, R(0));
-            tpn = *reinterpret_cast<const int2 *>(&so.tp);
-            km = in.kmask[(int64_t)lt * 32 + lane];
-        }
+        if (sift)
+            km = have ? pre->km : in.kmask[(int64_t)lt * 32 + lane];
     }
     // the warp's next tile: its signal and interface values into the stage buffer (or
     // its signal into L2), its residue (commit and INIT passes) into L2, while this one
@@ -1150,10 +1231,16 @@ __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
         if ((threadIdx.x & 31) == 0 && sizeof(Inst) > 128)
             prefetch_l1(d + 128);
     }
+    // latency kernels: the first tile's signal while the interface solve finishes (the
+    // staging kernels, with many tiles per warp, keep the registers for the tiles)
+    PreTile<R, SPL> pre;
+    if (!STAGE && g0 < g1)
+        pre_tile<R, SPL>(pa, g0, pre);
     pdl_wait();
     bool staged = false;
     for (int64_t gt = g0; gt < g1; ++gt)
-        staged = pass_tile<R, SPL, STAGE>(pa, P, B, gt, gt == g0, gt + 1 < g1, staged);
+        staged = pass_tile<R, SPL, STAGE>(pa, P, B, gt, gt == g0, gt + 1 < g1, staged,
+                                          (!STAGE && gt == g0) ? &pre : nullptr);
 }
 
 
@@ -1301,6 +1388,7 @@ __device__ __forceinline__ void seg_backsub(const RedScratch<R> &X, int rs, int 
 struct RedCommon {
     double sd[kRedThreads / 32][2];
     int wsu[kRedThreads / 32], wsn[kRedThreads / 32][2], wzc[kRedThreads / 32];
+    unsigned long long wpk[kRedThreads / 32];
     int next;
     double nakx[2][3]; // not-a-knot ends: the elimination data of rows 1 and NR - 2
 };
@@ -1402,6 +1490,86 @@ __device__ __forceinline__ double level2_solve(const SegElim<float> &g, int q, b
     return (double)Z + (double)dZ;
 }
 
+// The pass's snapshot of an instance's state (written by the pass kernel's first tile).
+struct PassSnap {
+    int pm, psift, pimf, ppar, pscount;
+};
+
+// Sec. 2.1 Step 5 and the IMF state machine, from the totals of the pass that just ran
+// (knots of envelope e and of the other one, the SD sums, the zero crossings): returns the
+// next mode. With `write` (one thread per instance) it also records the state, counts the
+// instance as running and adds the pass's algorithmic bytes to the statistics.
+template <typename R>
+__device__ __forceinline__ int stop_step(const ReduceArgs &ra, const Inst &in, State *st,
+                                         bool write, int e, int ntot, int nother, double sdn,
+                                         double sdd, int nz, const PassSnap &ps)
+{
+    const int pm = ps.pm;
+    const int nmax = e == 0 ? ntot : nother, nmin = e == 0 ? nother : ntot;
+    const bool ok = nmax >= 1 && nmin >= 1 && nmax + nmin >= 3;
+    int imf_count = ps.pimf, sift_count = ps.psift, scount = ps.pscount, nm;
+    int committed = -1; // IMF slot whose sift count is recorded
+    double sd = 0.0;
+    if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
+        if (pm != MODE_INIT) {
+            committed = imf_count;
+            imf_count += 1;
+        }
+        if (imf_count >= ra.K || !ok) {
+            nm = MODE_DONE;
+        } else {
+            nm = (ra.stop == STOP_FIXED && ra.fixed_sifts == 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
+        }
+    } else {
+        sift_count += 1;
+        if (!ok) {
+            nm = MODE_COMMIT;
+        } else if (ra.stop == STOP_FIXED) {
+            nm = (sift_count >= ra.fixed_sifts - 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
+        } else if (ra.stop == STOP_SD) {
+            sd = sdn / sdd;
+            nm = (sd < ra.sd_threshold || sift_count >= ra.max_sifts) ? MODE_COMMIT : MODE_SIFT;
+        } else { // S-number: extrema and zero crossings of the sifted signal
+            const int d = nmax + nmin - nz;
+            scount = (d >= -1 && d <= 1) ? scount + 1 : 0;
+            nm = (scount >= ra.s_number || sift_count >= ra.max_sifts) ? MODE_COMMIT : MODE_SIFT;
+        }
+    }
+    if (write) {
+        if (committed >= 0)
+            st->sifts[committed] = sift_count + (pm == MODE_SIFT_COMMIT ? 1 : 0);
+        if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
+            sift_count = 0;
+            scount = 0;
+        }
+        st->scount = scount;
+        st->hpar = (ps.ppar & 1) ^ 1;
+        st->rpar = ((ps.ppar >> 1) & 1) ^ ((pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT) ? 1 : 0);
+        if (pm == MODE_SIFT && ra.stop == STOP_SD)
+            st->sd = sd;
+        st->imf_count = imf_count;
+        st->sift_count = sift_count;
+        st->nmax = nmax;
+        st->nmin = nmin;
+        st->mode = nm;
+        if (nm != MODE_DONE)
+            atomicAdd(ra.active, 1);
+        if (ra.stats) {
+            // algorithmic bytes per sample of the pass that just ran: h in (w) unless
+            // INIT, h out (w), and for a commit the IMF out (w) and the residue in and
+            // out (16); INIT reads the residue (8)
+            const unsigned long long w = sizeof(R);
+            unsigned long long per = (pm == MODE_INIT) ? 8 + w : 2 * w;
+            if (pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
+                per += w + 16;
+            atomicAdd(&ra.stats->pass_bytes, per * (unsigned long long)in.L);
+            if (pm == MODE_SIFT || pm == MODE_SIFT_COMMIT)
+                atomicAdd(&ra.stats->sample_sifts, (unsigned long long)in.L);
+        }
+    }
+    return nm;
+}
+
 // SMALL: instances whose reduced systems have at most kRedSmallRows rows (the host
 // guarantees it from the tile count); only the small form is compiled, with a register
 // budget for three (FP32) or two (FP64) resident CTAs per SM instead of one or two, so
@@ -1411,13 +1579,14 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     k_reduce(ReduceArgs ra)
 {
     __shared__ RedShared<SMALL> S;
-    pdl_trigger();
     const int e = blockIdx.x & 1;
     const int ii = ra.inst_list ? ra.inst_list[blockIdx.x >> 1] : (int)(blockIdx.x >> 1);
     // the instance descriptor does not change during a decomposition: read it while the
     // pass kernel finishes
     const Inst &in = ra.inst[ii];
     const int nt = in.ntiles;
+    if (ra.cl > 0 && nt >= ra.cl_min_nt && nt <= ra.cl_max_nt)
+        return; // the cluster kernel's instance
     const TileRec<R> *texe = reinterpret_cast<const TileRec<R> *>(in.tex) + (int64_t)e * nt;
     const TileRec<R> *texo = reinterpret_cast<const TileRec<R> *>(in.tex) + (int64_t)(e ^ 1) * nt;
     TileSolve *tsol = in.tsol + (int64_t)e * nt;
@@ -1432,6 +1601,9 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         X.carve(p0, cap);
     }
     pdl_wait();
+    // the next pass may start now: the pass this solve waited for is complete, so the next
+    // one can read that pass's signal before its own wait
+    pdl_trigger();
     // what the pass kernel wrote is read at once (the state and the tile counts; the
     // counts of a finished instance are read and dropped)
     State *st = ra.state + ii;
@@ -1442,183 +1614,166 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     constexpr int NW = kRedThreads / 32;
 
     // counts: knots of both envelopes, this envelope's reduced-system entries per tile
-    // (first/last knot) and the SD sums of the pass that just ran. Tiles are taken in a
-    // stride of the block, four per thread at a time, every load in flight before use.
-    // With at most one tile per thread, the thread loads its tile's whole record here and
-    // writes the tile's entries from registers once the offsets are known.
+    // (first/last knot) and the SD sums of the pass that just ran. With at most one tile
+    // per thread, the thread loads its tile's whole record here and writes the tile's
+    // entries from registers once the offsets are known; the offsets and totals come from
+    // one block scan of (entries, knots, the other envelope's knots) packed in 64 bits
+    // (12, 19 and 33 bits: at most 4 x 256 entries and 256 x 512 knots). Otherwise tiles
+    // are taken in a stride of the block, four per thread at a time, every load in flight
+    // before use, and each thread then writes the entries of a contiguous chunk of tiles.
     int sn = 0, so_ = 0, zs = 0;
     double a = 0.0, b = 0.0;
     const bool want_sd = ra.stop == STOP_SD, want_zc = ra.stop == STOP_SNUMBER;
     const bool one = nt <= kRedThreads;
+    int ntot = 0, nother = 0, U = 0, ubase = 0, u1 = 0, ca = 0, cb = 0;
     TileRec<R> r1;
     r1.n = 0;
-    if (one && tid < nt) {
-        r1 = load_rec(texe + tid);
-        so_ = texo[tid].n;
-        if (want_sd) {
-            a = taux[tid].sd_num;
-            b = taux[tid].sd_den;
+    if (one) {
+        if (tid < nt) {
+            r1 = load_rec(texe + tid);
+            so_ = texo[tid].n;
+            if (want_sd) {
+                a = taux[tid].sd_num;
+                b = taux[tid].sd_den;
+            }
+            if (want_zc)
+                zs = taux[tid].nzc;
+            sn = r1.n;
         }
-        if (want_zc)
-            zs = taux[tid].nzc;
-        sn = r1.n;
-        X.Tu[tid] = (unsigned char)(sn <= kSparseKnots ? sn : 2);
-    }
-    for (int t0 = 0; !one && t0 < nt; t0 += 4 * kRedThreads) {
-        int ne[4], no[4], nz[4];
-        double sa[4], sb[4];
+        if (mode_now == MODE_DONE)
+            return;
+        u1 = sn <= kSparseKnots ? sn : 2;
+        const uint64_t pk = (uint64_t)u1 | ((uint64_t)sn << 12) | ((uint64_t)so_ << 31);
+        uint64_t incl = pk;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + tid + k * kRedThreads;
-            ne[k] = no[k] = nz[k] = 0;
-            sa[k] = sb[k] = 0.0;
-            if (t < nt) {
-                ne[k] = texe[t].n;
-                no[k] = texo[t].n;
-                if (want_sd) {
-                    sa[k] = taux[t].sd_num;
-                    sb[k] = taux[t].sd_den;
-                }
-                if (want_zc)
-                    nz[k] = taux[t].nzc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(FULLMASK, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            S.wpk[warp] = incl;
+        if (want_zc) {
+            zs = warp_sum(zs);
+            if (lane == 0)
+                S.wzc[warp] = zs;
+        }
+        if (want_sd) { // FP64 sums only when the stop rule reads them (the FP64 pipe is narrow)
+            a = warp_sum(a);
+            b = warp_sum(b);
+            if (lane == 0) {
+                S.sd[warp][0] = a;
+                S.sd[warp][1] = b;
             }
         }
+        if (tid < nt)
+            X.Tu[tid] = (unsigned char)u1;
+        __syncthreads();
+        uint64_t before = incl - pk, tot = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + tid + k * kRedThreads;
-            if (t < nt)
-                X.Tu[t] = (unsigned char)(ne[k] <= kSparseKnots ? ne[k] : 2);
-            sn += ne[k];
-            so_ += no[k];
-            zs += nz[k];
-            a += sa[k];
-            b += sb[k];
+        for (int w = 0; w < NW; ++w) {
+            const uint64_t v = S.wpk[w];
+            before += w < warp ? v : 0;
+            tot += v;
         }
-    }
-    if (mode_now == MODE_DONE)
-        return;
-    sn = warp_sum(sn);
-    so_ = warp_sum(so_);
-    zs = warp_sum(zs);
-    if (want_sd) { // FP64 sums only when the stop rule reads them (the FP64 pipe is narrow)
-        a = warp_sum(a);
-        b = warp_sum(b);
-    }
-    if (lane == 0) {
-        S.wsn[warp][0] = sn;
-        S.wsn[warp][1] = so_;
-        S.wzc[warp] = zs;
-        S.sd[warp][0] = a;
-        S.sd[warp][1] = b;
-    }
-    __syncthreads();
-    // entry offsets: each thread sums a contiguous chunk of tiles, a block scan of the
-    // chunk sums, then the chunk's per-tile offsets
-    const int CH = (nt + kRedThreads - 1) / kRedThreads;
-    const int ca = min(tid * CH, nt), cb = min(ca + CH, nt);
-    int su = 0;
-    for (int t = ca; t < cb; ++t)
-        su += X.Tu[t];
-    int incl = su;
+        ubase = (int)(before & 0xfffu);
+        U = (int)(tot & 0xfffu);
+        ntot = (int)((tot >> 12) & 0x7ffffu);
+        nother = (int)(tot >> 31);
+    } else {
+        for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+            int ne[4], no[4], nz[4];
+            double sa[4], sb[4];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULLMASK, incl, o);
-        if (lane >= o)
-            incl += y;
-    }
-    if (lane == 31)
-        S.wsu[warp] = incl;
-    int ntot = 0, nother = 0;
+            for (int k = 0; k < 4; ++k) {
+                const int t = t0 + tid + k * kRedThreads;
+                ne[k] = no[k] = nz[k] = 0;
+                sa[k] = sb[k] = 0.0;
+                if (t < nt) {
+                    ne[k] = texe[t].n;
+                    no[k] = texo[t].n;
+                    if (want_sd) {
+                        sa[k] = taux[t].sd_num;
+                        sb[k] = taux[t].sd_den;
+                    }
+                    if (want_zc)
+                        nz[k] = taux[t].nzc;
+                }
+            }
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        ntot += S.wsn[w][0];
-        nother += S.wsn[w][1];
-    }
-    __syncthreads();
-    int ubase = incl - su, U = 0;
+            for (int k = 0; k < 4; ++k) {
+                const int t = t0 + tid + k * kRedThreads;
+                if (t < nt)
+                    X.Tu[t] = (unsigned char)(ne[k] <= kSparseKnots ? ne[k] : 2);
+                sn += ne[k];
+                so_ += no[k];
+                zs += nz[k];
+                a += sa[k];
+                b += sb[k];
+            }
+        }
+        if (mode_now == MODE_DONE)
+            return;
+        sn = warp_sum(sn);
+        so_ = warp_sum(so_);
+        zs = warp_sum(zs);
+        if (want_sd) {
+            a = warp_sum(a);
+            b = warp_sum(b);
+        }
+        if (lane == 0) {
+            S.wsn[warp][0] = sn;
+            S.wsn[warp][1] = so_;
+            S.wzc[warp] = zs;
+            S.sd[warp][0] = a;
+            S.sd[warp][1] = b;
+        }
+        __syncthreads();
+        // entry offsets: each thread sums a contiguous chunk of tiles, a block scan of the
+        // chunk sums, then the chunk's per-tile offsets
+        const int CH = (nt + kRedThreads - 1) / kRedThreads;
+        ca = min(tid * CH, nt);
+        cb = min(ca + CH, nt);
+        int su = 0;
+        for (int t = ca; t < cb; ++t)
+            su += X.Tu[t];
+        int incl = su;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        ubase += w < warp ? S.wsu[w] : 0;
-        U += S.wsu[w];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULLMASK, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            S.wsu[warp] = incl;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            ntot += S.wsn[w][0];
+            nother += S.wsn[w][1];
+        }
+        __syncthreads();
+        ubase = incl - su;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            ubase += w < warp ? S.wsu[w] : 0;
+            U += S.wsu[w];
+        }
     }
     // the stop test and the next mode (thread 0, while the others write the entries; the
     // entries of an instance that stops sifting are dropped)
     if (tid == 0) {
-        const int nmax = e == 0 ? ntot : nother, nmin = e == 0 ? nother : ntot;
         double sdn = 0.0, sdd = 0.0;
-        if (want_sd) {
-            for (int w = 0; w < NW; ++w) {
+        int nz = 0;
+        for (int w = 0; w < NW; ++w) {
+            if (want_sd) {
                 sdn += S.sd[w][0];
                 sdd += S.sd[w][1];
             }
+            if (want_zc)
+                nz += S.wzc[w];
         }
-        const bool ok = nmax >= 1 && nmin >= 1 && nmax + nmin >= 3;
-        int imf_count = pimf, sift_count = psift, scount = pscount, nm;
-        int committed = -1; // IMF slot whose sift count is recorded
-        double sd = 0.0;
-        if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
-            if (pm != MODE_INIT) {
-                committed = imf_count;
-                imf_count += 1;
-            }
-            if (imf_count >= ra.K || !ok) {
-                nm = MODE_DONE;
-            } else {
-                nm = (ra.stop == STOP_FIXED && ra.fixed_sifts == 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
-            }
-        } else {
-            sift_count += 1;
-            if (!ok) {
-                nm = MODE_COMMIT;
-            } else if (ra.stop == STOP_FIXED) {
-                nm = (sift_count >= ra.fixed_sifts - 1) ? MODE_SIFT_COMMIT : MODE_SIFT;
-            } else if (ra.stop == STOP_SD) {
-                sd = sdn / sdd;
-                nm = (sd < ra.sd_threshold || sift_count >= ra.max_sifts) ? MODE_COMMIT
-                                                                          : MODE_SIFT;
-            } else { // S-number: extrema and zero crossings of the sifted signal
-                int nz = 0;
-                for (int w = 0; w < NW; ++w)
-                    nz += S.wzc[w];
-                const int d = nmax + nmin - nz;
-                scount = (d >= -1 && d <= 1) ? scount + 1 : 0;
-                nm = (scount >= ra.s_number || sift_count >= ra.max_sifts) ? MODE_COMMIT
-                                                                           : MODE_SIFT;
-            }
-        }
-        S.next = nm;
-        if (e == 0) {
-            if (committed >= 0)
-                st->sifts[committed] = sift_count + (pm == MODE_SIFT_COMMIT ? 1 : 0);
-            if (pm == MODE_INIT || pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT) {
-                sift_count = 0;
-                scount = 0;
-            }
-            st->scount = scount;
-            st->hpar = (ppar & 1) ^ 1;
-            st->rpar = ((ppar >> 1) & 1) ^ ((pm == MODE_SIFT_COMMIT || pm == MODE_COMMIT) ? 1 : 0);
-            if (pm == MODE_SIFT && ra.stop == STOP_SD)
-                st->sd = sd;
-            st->imf_count = imf_count;
-            st->sift_count = sift_count;
-            st->nmax = nmax;
-            st->nmin = nmin;
-            st->mode = nm;
-            if (nm != MODE_DONE)
-                atomicAdd(ra.active, 1);
-            if (ra.stats) {
-                // algorithmic bytes per sample of the pass that just ran: h in (w) unless
-                // INIT, h out (w), and for a commit the IMF out (w) and the residue in
-                // and out (16); INIT reads the residue (8)
-                const unsigned long long w = sizeof(R);
-                unsigned long long per = (pm == MODE_INIT) ? 8 + w : 2 * w;
-                if (pm == MODE_COMMIT || pm == MODE_SIFT_COMMIT)
-                    per += w + 16;
-                atomicAdd(&ra.stats->pass_bytes, per * (unsigned long long)in.L);
-                if (pm == MODE_SIFT || pm == MODE_SIFT_COMMIT)
-                    atomicAdd(&ra.stats->sample_sifts, (unsigned long long)in.L);
-            }
-        }
+        const PassSnap ps{pm, psift, pimf, ppar, pscount};
+        S.next = stop_step<R>(ra, in, st, e == 0, e, ntot, nother, sdn, sdd, nz, ps);
     }
     const int nl = ra.boundary == BND_MIRROR ? min(ra.mirror_knots, ntot) : 1;
     const int nr = nl;
@@ -1678,6 +1833,52 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
             X.To[tid] = nl + ubase;
             put_entries(r1, nl + ubase);
         }
+        // the end knots, written beside the entries: mirrored knots by the threads that hold
+        // the signal's first two and last two knots (a tile's first and second knots are
+        // t[0], t[1], its second-to-last and last t[2], t[3]; a tile with one knot has
+        // t[0] = t[3]); end samples by two threads of warp 1
+        if (ra.boundary == BND_MIRROR) {
+            if (tid < nt && u1 >= 1) {
+                const int n = r1.n, l = nl + U - 1;
+                const int Lm = (int)(2 * (in.L - 1));
+                if (ubase == 0) {
+                    X.Et[nl - 1] = -r1.t[0];
+                    X.Ey[nl - 1] = r1.y[0];
+                    X.Ek[nl - 1] = nl == 2 ? EK_FREE : EK_FIXED;
+                    if (nl == 2 && n >= 2) {
+                        X.Et[0] = -r1.t[1];
+                        X.Ey[0] = r1.y[1];
+                        X.Ek[0] = EK_FIXED;
+                    }
+                } else if (ubase == 1 && nl == 2) { // the first tile has one knot
+                    X.Et[0] = -r1.t[0];
+                    X.Ey[0] = r1.y[0];
+                    X.Ek[0] = EK_FIXED;
+                }
+                if (ubase + u1 == U) {
+                    X.Et[l + 1] = Lm - r1.t[3];
+                    X.Ey[l + 1] = r1.y[3];
+                    X.Ek[l + 1] = nr == 2 ? EK_FREE : EK_FIXED;
+                    if (nr == 2 && n >= 2) {
+                        X.Et[l + 2] = Lm - r1.t[2];
+                        X.Ey[l + 2] = r1.y[2];
+                        X.Ek[l + 2] = EK_FIXED;
+                    }
+                } else if (ubase + u1 == U - 1 && nr == 2) { // the last tile has one knot
+                    X.Et[l + 2] = Lm - r1.t[3];
+                    X.Ey[l + 2] = r1.y[3];
+                    X.Ek[l + 2] = EK_FIXED;
+                }
+            }
+        } else if (tid == 32) {
+            X.Et[0] = 0;
+            X.Ey[0] = (R)in.taux[0].h_first;
+            X.Ek[0] = EK_FIXED;
+        } else if (tid == 33) {
+            X.Et[nl + U] = (int)(in.L - 1);
+            X.Ey[nl + U] = (R)in.taux[nt - 1].h_last;
+            X.Ek[nl + U] = EK_FIXED;
+        }
     } else {
         {
             int p = nl + ubase;
@@ -1710,7 +1911,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     const int nm = S.next;
     if (nm != MODE_SIFT && nm != MODE_SIFT_COMMIT)
         return;
-    if (tid == 0) {
+    if (!one && tid == 0) {
         const int64_t L = in.L;
         if (ra.boundary == BND_MIRROR) {
             // first two and last two knots of the whole signal, reflected about the ends
@@ -1757,7 +1958,8 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
             X.Ek[nl + U] = EK_FIXED;
         }
     }
-    __syncthreads();
+    if (!one)
+        __syncthreads();
     // rows, every thread a strided share (reads the scratch only; writes its own rows)
     for (int p = tid; p < NR; p += kRedThreads) {
         const int k = X.Ek[p];

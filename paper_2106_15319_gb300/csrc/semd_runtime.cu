@@ -3,6 +3,7 @@
 // ensemble (Sec. 2.2). See semd_device.cuh for the sifting kernels.
 #include "semd_runtime.h"
 #include "semd_device.cuh"
+#include "semd_reduce_cl.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -55,27 +56,15 @@ __global__ void k_serialize(const Inst *inst, const State *state, const int32_t 
         in.r[0][ts + idx] = serial_sample<R>(X, in.M, in.N, in.D, in.order, ts + idx);
 }
 
-// EEMD beta = rel * population std of the serialized x (Sec. 2.2 Step 1), one CTA.
-__global__ void k_std(const Inst *inst, double rel, double *beta)
+// EEMD beta = rel * population std of the serialized x (Sec. 2.2 Step 1): the mean, then
+// the mean squared deviation from it, each a sum over kStdBlocks CTAs in a fixed order
+// (results do not depend on timing). part holds 2 kStdBlocks partial sums.
+constexpr int kStdBlocks = 256;
+constexpr int kStdThreads = 256;
+
+// Sum of the CTA's threads' values in a fixed tree order (every thread gets the total).
+__device__ double block_sum_fixed(double v, double *sh)
 {
-    const double *x = inst[0].r[0];
-    const int64_t L = inst[0].L;
-    __shared__ double sh[1024];
-    double s = 0.0;
-    for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
-        s += x[k];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    const double mean = sh[0] / (double)L;
-    __syncthreads();
-    double v = 0.0;
-    for (int64_t k = threadIdx.x; k < L; k += blockDim.x)
-        v += (x[k] - mean) * (x[k] - mean);
     sh[threadIdx.x] = v;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -83,8 +72,44 @@ __global__ void k_std(const Inst *inst, double rel, double *beta)
             sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
+    const double t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+// Stage 0: CTA b's share of sum x. Stage 1: the mean from the stage-0 partials, CTA b's
+// share of sum (x - mean)^2. Stage 2 (one CTA): beta from the stage-1 partials.
+__global__ void __launch_bounds__(kStdThreads) k_std(const Inst *inst, double rel, double *beta,
+                                                     double *part, int stage)
+{
+    __shared__ double sh[kStdThreads];
+    const double *x = inst[0].r[0];
+    const int64_t L = inst[0].L;
+    const int64_t stride = (int64_t)kStdBlocks * kStdThreads;
+    if (stage == 2) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < kStdBlocks; i += blockDim.x)
+            v += part[kStdBlocks + i];
+        const double t = block_sum_fixed(v, sh);
+        if (threadIdx.x == 0)
+            *beta = rel * sqrt(t / (double)L);
+        return;
+    }
+    double mean = 0.0;
+    if (stage == 1) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < kStdBlocks; i += blockDim.x)
+            v += part[i];
+        mean = block_sum_fixed(v, sh) / (double)L;
+    }
+    double s = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)kStdThreads + threadIdx.x; k < L; k += stride) {
+        const double d = stage == 1 ? x[k] - mean : x[k];
+        s += stage == 1 ? d * d : d;
+    }
+    const double t = block_sum_fixed(s, sh);
     if (threadIdx.x == 0)
-        *beta = rel * sqrt(sh[0] / (double)L);
+        part[stage * kStdBlocks + blockIdx.x] = t;
 }
 
 // One Philox4x32-10 block (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as
@@ -109,32 +134,79 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 // (p div 4, m, 0, 0) and key (seed low word, seed high word); the word u gives the odd
 // integer i = 2 (u >> 9) - (2^23 - 1) and the sample i * sqrt(3) / 2^23, uniform on
 // (-sqrt 3, sqrt 3) with zero mean and unit variance.
+__device__ __forceinline__ double white_value(uint32_t u)
+{
+    const int32_t i = (int32_t)(2u * (u >> 9)) - 8388607;
+    return __dmul_rn((double)i, 1.7320508075688772 / 8388608.0);
+}
 __device__ __forceinline__ double white_sample(uint64_t seed, int m, int64_t p)
 {
     const uint4 b = philox4x32_10(make_uint4((uint32_t)(p >> 2), (uint32_t)m, 0u, 0u),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
     const int j = (int)(p & 3);
-    const uint32_t u = j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
-    const int32_t i = (int32_t)(2u * (u >> 9)) - 8388607;
-    return __dmul_rn((double)i, 1.7320508075688772 / 8388608.0);
+    return white_value(j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w);
 }
 
-// x^(m) = x + beta w^(m) for every trial (Sec. 2.2 Step 1); trial 0 holds x on entry. The
-// noise is the caller's (inst[0].noise) or, when that is null, drawn here from the seed.
+// x^(m) = x + beta w^(m) for the trials m0 + blockIdx.y (Sec. 2.2 Step 1); trial 0 holds
+// x on entry, so the host runs trials 1.. first and trial 0 (in place) last. The noise is
+// the caller's (inst[0].noise) or, when that is null, drawn here from the seed: a warp
+// owns 128 consecutive samples of one trial, lane l computes the Philox block of samples
+// 128 g + 4 l .. + 3, and the words are passed by shuffles so that in round j lane l writes
+// sample 128 g + 32 j + l (coalesced).
 template <typename R>
-__global__ void k_add_noise(const Inst *inst, int trials, const double *beta, uint64_t seed)
+__global__ void k_add_noise(const Inst *inst, int m0, const double *beta, uint64_t seed)
 {
     const int64_t L = inst[0].L;
     const R *w = (const R *)inst[0].noise;
     const double b = *beta;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const double x = inst[0].r[0][p];
-        for (int m = trials - 1; m >= 0; --m) {
-            const double wv = w ? (double)w[(int64_t)m * L + p] : white_sample(seed, m, p);
-            inst[m].r[0][p] = __dadd_rn(x, __dmul_rn(b, wv));
+    const int m = m0 + (int)blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const int64_t nw = (L + 127) >> 7;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double *x0 = inst[0].r[0];
+    double *dst = inst[m].r[0];
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nw; g += stride) {
+        const int64_t p0 = (g << 7) + lane;
+        double x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            x[j] = p0 + 32 * j < L ? x0[p0 + 32 * j] : 0.0;
+        if (w) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t p = p0 + 32 * j;
+                if (p < L)
+                    dst[p] = __dadd_rn(x[j], __dmul_rn(b, (double)w[(int64_t)m * L + p]));
+            }
+            continue;
+        }
+        const uint4 blk =
+            philox4x32_10(make_uint4((uint32_t)((g << 5) + lane), (uint32_t)m, 0u, 0u), key);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            // sample 128 g + 32 j + lane: block 32 g + 8 j + lane / 4, word lane mod 4
+            const int src = 8 * j + (lane >> 2);
+            const uint32_t u0 = __shfl_sync(FULLMASK, blk.x, src);
+            const uint32_t u1 = __shfl_sync(FULLMASK, blk.y, src);
+            const uint32_t u2 = __shfl_sync(FULLMASK, blk.z, src);
+            const uint32_t u3 = __shfl_sync(FULLMASK, blk.w, src);
+            const int q = lane & 3;
+            const uint32_t u = q == 0 ? u0 : q == 1 ? u1 : q == 2 ? u2 : u3;
+            const int64_t p = p0 + 32 * j;
+            if (p < L)
+                dst[p] = __dadd_rn(x[j], __dmul_rn(b, white_value(u)));
         }
     }
+}
+
+// Grid of k_add_noise for a signal of ntiles tiles and `trials` trials: a warp per 128
+// samples (8 per CTA) in x, a trial per y.
+static dim3 noise_grid(int64_t ntiles, int tile, int trials)
+{
+    const int64_t warps = (ntiles * tile + 127) / 128;
+    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 1 << 16)),
+                (unsigned)trials);
 }
 
 // Sec. 3.3 for the residue, and zero-fill of the IMF slots past the produced count, for
@@ -164,37 +236,106 @@ __global__ void k_finalize(const Inst *inst, const State *state, const int32_t *
     }
 }
 
-// EEMD Step 3: average the trials' IMFs (zeros where a trial has fewer) and residues,
-// in FP64 and in trial order, then de-serialize (Sec. 3.3).
+// EEMD Step 3: average the trials' IMFs (zeros where a trial has fewer) and residues, in
+// trial order, then de-serialize (Sec. 3.3). FP64 plans sum in FP64. FP32 plans sum the
+// single-precision IMF values in float-float arithmetic (an unevaluated pair of floats,
+// about 48 significant bits: as accurate as the FP64 sum for these inputs, without the
+// narrow FP64 pipe); the residues are FP64 in both. A thread takes 4 consecutive samples
+// (16- or 32-byte loads of each trial's IMF row), a CTA 1024; the trials' IMF counts and
+// residue arrays are read once per CTA into shared memory (the first kAvgShared trials).
+constexpr int kAvgShared = 512;
+constexpr int kAvgPer = 4;
 template <typename R>
 __global__ void k_eemd_average(const Inst *inst, const State *state, int trials, int K,
-                               const R *scratch, int tile)
+                               const R *scratch)
 {
+    __shared__ int ncnt[kAvgShared];
+    __shared__ const double *rptr[kAvgShared];
+    for (int m = threadIdx.x; m < min(trials, kAvgShared); m += blockDim.x) {
+        ncnt[m] = state[m].imf_count;
+        rptr[m] = inst[m].r[state[m].rpar];
+    }
+    __syncthreads();
+    auto count_of = [&](int m) { return m < kAvgShared ? ncnt[m] : state[m].imf_count; };
     const Inst &in = inst[0];
     R *out = (R *)in.avg_imf;
     double *res = in.avg_res;
     const int64_t L = in.L;
-    const int64_t ts = (int64_t)blockIdx.x * tile;
-    const int64_t cnt = min((int64_t)tile, L - ts);
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kAvgPer;
+    if (p0 >= L)
+        return;
+    const int n = (int)min((int64_t)kAvgPer, L - p0); // the tail thread may have fewer
     const int64_t outstride = in.M * in.N;
-    for (int64_t idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-        const int64_t p = ts + idx;
-        int64_t dst;
-        if (!deser_index(p, in.M, in.N, in.D, in.order, dst))
-            continue;
-        for (int k = 0; k < K; ++k) {
-            double acc = 0.0;
-            for (int m = 0; m < trials; ++m)
-                if (k < state[m].imf_count)
-                    acc += (double)scratch[((int64_t)m * K + k) * in.imf_stride + p];
-            out[(int64_t)k * outstride + dst] = (R)(acc / (double)trials);
+    const int64_t step = (int64_t)K * in.imf_stride; // one trial's IMF block
+    int64_t dst[kAvgPer];
+    bool keep[kAvgPer];
+#pragma unroll
+    for (int j = 0; j < kAvgPer; ++j)
+        keep[j] = j < n && deser_index(p0 + j, in.M, in.N, in.D, in.order, dst[j]);
+    for (int k = 0; k < K; ++k) {
+        const R *src = scratch + (int64_t)k * in.imf_stride + p0;
+        double sum[kAvgPer];
+        if constexpr (sizeof(R) == 4) {
+            FFSum acc[kAvgPer];
+#pragma unroll 4
+            for (int m = 0; m < trials; ++m) {
+                float v[kAvgPer];
+                if (n == kAvgPer) {
+                    vload<kAvgPer>(src + m * step, v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kAvgPer; ++j)
+                        v[j] = j < n ? src[m * step + j] : 0.f;
+                }
+                if (k < count_of(m)) {
+#pragma unroll
+                    for (int j = 0; j < kAvgPer; ++j)
+                        acc[j].add(v[j], 0.f);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kAvgPer; ++j)
+                sum[j] = (double)acc[j].hi + (double)acc[j].lo;
+        } else {
+            double acc[kAvgPer] = {};
+#pragma unroll 4
+            for (int m = 0; m < trials; ++m) {
+                double v[kAvgPer];
+                if (n == kAvgPer) {
+                    vload<kAvgPer>(src + m * step, v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kAvgPer; ++j)
+                        v[j] = j < n ? src[m * step + j] : 0.0;
+                }
+                if (k < count_of(m)) {
+#pragma unroll
+                    for (int j = 0; j < kAvgPer; ++j)
+                        acc[j] += v[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kAvgPer; ++j)
+                sum[j] = acc[j];
         }
-        if (res) {
-            double acc = 0.0;
-            for (int m = 0; m < trials; ++m)
-                acc += inst[m].r[state[m].rpar][p];
-            res[dst] = acc / (double)trials;
+#pragma unroll
+        for (int j = 0; j < kAvgPer; ++j)
+            if (keep[j])
+                out[(int64_t)k * outstride + dst[j]] = (R)(sum[j] / (double)trials);
+    }
+    if (res) {
+        double acc[kAvgPer] = {};
+#pragma unroll 4
+        for (int m = 0; m < trials; ++m) {
+            const double *r = (m < kAvgShared ? rptr[m] : inst[m].r[state[m].rpar]) + p0;
+#pragma unroll
+            for (int j = 0; j < kAvgPer; ++j)
+                acc[j] += j < n ? r[j] : 0.0;
         }
+#pragma unroll
+        for (int j = 0; j < kAvgPer; ++j)
+            if (keep[j])
+                res[dst[j]] = acc[j] / (double)trials;
     }
 }
 
@@ -488,6 +629,50 @@ static cudaError_t pass_attr_one()
                                 (int)pass_smem<R, TILE, VAR>());
 }
 
+// Which cluster shapes of the interface solve the current device can hold: per precision,
+// device, cluster size (2, 4, 8, 16) and shared memory (up to 116 KB per CTA, or up to the
+// opt-in maximum): 0 not yet known, 1 yes, 2 no. Filled when the kernel attributes are set
+// (plan and server creation), so that no query runs while a stream is being captured.
+constexpr int kClDevMax = 64;
+static int g_cluster_fit[2][kClDevMax][4][2];
+
+template <typename R>
+static void query_cluster_fit(int dev)
+{
+    for (int lc = 0; lc < 4; ++lc) {
+        for (int big = 0; big < 2; ++big) {
+            const unsigned CL = 2u << lc;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(CL);
+            cfg.blockDim = dim3(kRedThreads);
+            cfg.dynamicSmemBytes = big ? kClSmemOptin - 1024 : 116 * 1024;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            const bool ok =
+                cudaOccupancyMaxActiveClusters(&n, k_reduce_cl<R>, &cfg) == cudaSuccess && n > 0;
+            cudaGetLastError(); // a refused query leaves no error behind
+            g_cluster_fit[sizeof(R) == 8][dev][lc][big] = ok ? 1 : 2;
+        }
+    }
+}
+
+// Whether a cluster of CL CTAs with `smem` bytes of shared memory each fits on the device.
+template <typename R>
+static bool cluster_fits(int CL, size_t smem)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kClDevMax)
+        return false;
+    const int lc = CL == 2 ? 0 : CL == 4 ? 1 : CL == 8 ? 2 : 3;
+    return g_cluster_fit[sizeof(R) == 8][dev][lc][smem > 116 * 1024 ? 1 : 0] == 1;
+}
+
 template <typename R>
 static cudaError_t set_smem_attr()
 {
@@ -508,6 +693,15 @@ static cudaError_t set_smem_attr()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_reduce<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)reduce_smem_bytes(kRedSmallRows, sizeof(R)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce_cl<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kClSmemOptin - 1024));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce_cl<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int dev = 0;
+    if (e == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kClDevMax &&
+        g_cluster_fit[sizeof(R) == 8][dev][0][0] == 0)
+        query_cluster_fit<R>(dev);
     return e;
 }
 
@@ -625,9 +819,33 @@ static size_t reduce_smem(const ReduceArgs &ra)
 // One CTA per instance and envelope. When the shared scratch holds every instance's
 // system (smem_entries, sized for the launch's longest instance, bounds each system's
 // rows) and that is at most kRedSmallRows rows, the small-system kernel runs.
+// The cluster kernel: ra.cl CTAs per instance and envelope, one cluster each (a plain
+// launch: it starts once the pass kernel has finished).
+template <typename R>
+static void launch_reduce_cl(const ReduceArgs &ra, int ninst, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * ninst * ra.cl));
+    cfg.blockDim = dim3(kRedThreads);
+    cfg.dynamicSmemBytes = cl_smem_bytes<R>(ra.cl_entries);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ra.cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_reduce_cl<R>, ra);
+}
+
 template <typename R>
 static void launch_reduce(const ReduceArgs &ra, int ninst, cudaStream_t s)
 {
+    if (ra.run_cl)
+        launch_reduce_cl<R>(ra, ninst, s);
+    if (!ra.run_single)
+        return;
     if (ra.smem_entries > 0 && ra.smem_entries <= kRedSmallRows)
         launch_pdl(k_reduce<R, true>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s, ra);
     else
@@ -745,7 +963,7 @@ semd_status Workspace::allocate(int64_t samples, int insts, int64_t tiles, int64
         {(void **)&d_kmask, (size_t)tiles * 32 * sizeof(uint2)},
         {(void **)&d_rscr, (size_t)rentries * 8},
         {(void **)&d_active, (size_t)(iters + 8) * 4},
-        {(void **)&d_beta, 8},
+        {(void **)&d_beta, (size_t)(1 + 2 * kStdBlocks) * 8},
         {(void **)&d_misc, (size_t)tiles * 2 * 4 + 64},
         {(void **)&d_stats, sizeof(Stats)},
     };
@@ -859,6 +1077,7 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
 {
     int64_t off = 0, tiles = 0, rent = 0;
     max_ntiles = 0;
+    min_ntiles = INT64_MAX;
     for (int i = 0; i < n; ++i) {
         Inst &in = h_inst[i];
         bind_instance(*this, in, off, tiles, rent);
@@ -866,6 +1085,7 @@ semd_status Workspace::layout(int n, int64_t &ntiles, cudaStream_t s, std::strin
         tiles += in.ntiles;
         rent += 2 * rscr_env_doubles(in.rlen);
         max_ntiles = std::max<int64_t>(max_ntiles, in.ntiles);
+        min_ntiles = std::min<int64_t>(min_ntiles, in.ntiles);
     }
     if (off > cap_samples || tiles > cap_tiles || rent > cap_rentries || n > cap_inst) {
         err = "batch exceeds the plan's capacity";
@@ -896,6 +1116,67 @@ static void launch_pass(Workspace &ws, int64_t ntiles, bool need_sd, bool need_z
     launch_pass_tiles<R>(ws.tile, ws.pass_variant, ws.pass_ctas, pa, ntiles, s);
 }
 
+// Shape of the interface solve of a launch whose instances have min_nt..max_nt tiles.
+// An instance whose system fits in one CTA's shared memory is solved by one CTA per
+// envelope. A longer one (natural spline ends) by a cluster of CLd CTAs per envelope, CLd
+// the largest size of 16 or 8 the device can hold at full shared memory, while a CTA's
+// share of its system fits; longer ones again by one CTA with a global-memory scratch.
+template <typename R>
+static void set_reduce_shape_t(ReduceArgs &ra, int64_t min_nt, int64_t max_nt)
+{
+    auto fits_one = [](int64_t nt) {
+        return reduce_smem_bytes(reduce_len(nt), sizeof(R)) <= kReduceSmemMax;
+    };
+    ra.cl = 0;
+    ra.cl_entries = 0;
+    ra.cl_min_nt = ra.cl_max_nt = 0;
+    ra.run_cl = 0;
+    ra.run_single = 1;
+    const int CLd = cluster_fits<R>(16, kClSmemOptin) ? 16 : cluster_fits<R>(8, kClSmemOptin) ? 8 : 0;
+    if (CLd > 0 && ra.spline_end == SPLINE_NATURAL) {
+        int64_t lo = 1;
+        while (fits_one(lo * 2))
+            lo *= 2;
+        int64_t hi = lo * 2; // fits_one(lo), !fits_one(hi): the boundary in between
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) / 2;
+            (fits_one(mid) ? lo : hi) = mid;
+        }
+        int64_t top = hi; // the largest count whose cluster share fits
+        while (cl_smem_bytes<R>(cl_entries((top * 2 + CLd - 1) / CLd)) <= kClSmemOptin - 1024)
+            top *= 2;
+        int64_t b = top * 2;
+        while (b - top > 1) {
+            const int64_t mid = (top + b) / 2;
+            (cl_smem_bytes<R>(cl_entries((mid + CLd - 1) / CLd)) <= kClSmemOptin - 1024 ? top : b) = mid;
+        }
+        if (top >= hi && top < (int64_t)1 << 30) {
+            ra.cl = CLd;
+            ra.cl_min_nt = (int32_t)hi;
+            ra.cl_max_nt = (int32_t)top;
+        }
+    }
+    if (ra.cl > 0) {
+        ra.run_cl = (max_nt >= ra.cl_min_nt && min_nt <= ra.cl_max_nt) ? 1 : 0;
+        ra.run_single = (min_nt < ra.cl_min_nt || max_nt > ra.cl_max_nt) ? 1 : 0;
+        const int64_t mc = std::min<int64_t>(max_nt, ra.cl_max_nt);
+        ra.cl_entries = cl_entries((mc + ra.cl - 1) / ra.cl);
+        // the one-CTA kernel's instances: below cl_min_nt (shared memory), or beyond
+        // cl_max_nt (global memory)
+        const int64_t ms = max_nt > ra.cl_max_nt ? max_nt : std::min<int64_t>(max_nt, ra.cl_min_nt - 1);
+        ra.smem_entries = fits_one(ms) ? reduce_len(ms) : 0;
+    } else {
+        ra.smem_entries = fits_one(max_nt) ? reduce_len(max_nt) : 0;
+    }
+}
+static void set_reduce_shape(ReduceArgs &ra, int64_t min_nt, int64_t max_nt, size_t elem)
+{
+    if (elem == 8)
+        set_reduce_shape_t<double>(ra, min_nt, max_nt);
+    else
+        set_reduce_shape_t<float>(ra, min_nt, max_nt);
+}
+
 static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
 {
     ReduceArgs ra;
@@ -914,9 +1195,7 @@ static ReduceArgs reduce_args(Workspace &ws, const semd_params &p)
     ra.single = ws.elem_size == 4 ? 1 : 0;
     ra.s_number = p.s_number;
     ra.spline_end = p.spline_end;
-    ra.pad = 0;
-    const int64_t entries = reduce_len(ws.max_ntiles);
-    ra.smem_entries = reduce_smem_bytes(entries, ws.elem_size) <= kReduceSmemMax ? entries : 0;
+    set_reduce_shape(ra, ws.min_ntiles, ws.max_ntiles, ws.elem_size);
     return ra;
 }
 
@@ -1047,17 +1326,26 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
                                                       ws.tile, eemd ? 1 : 0);
     ++launches;
     if (eemd) {
-        k_std<<<1, 1024, 0, s>>>(ws.d_inst, p.noise_rel_std, ws.d_beta);
-        k_add_noise<R><<<304, 256, 0, s>>>(ws.d_inst, ninst, ws.d_beta, pl.noise_seed);
-        launches += 2;
+        for (int stage = 0; stage < 3; ++stage)
+            k_std<<<stage == 2 ? 1 : kStdBlocks, kStdThreads, 0, s>>>(
+                ws.d_inst, p.noise_rel_std, ws.d_beta, ws.d_beta + 1, stage);
+        for (int m0 = 1; m0 < ninst; m0 += 65535) { // grid y is at most 65535
+            k_add_noise<R><<<noise_grid(ntiles0, ws.tile, std::min(ninst - m0, 65535)), 256, 0,
+                             s>>>(ws.d_inst, m0, ws.d_beta, pl.noise_seed);
+            ++launches;
+        }
+        k_add_noise<R><<<noise_grid(ntiles0, ws.tile, 1), 256, 0, s>>>(ws.d_inst, 0, ws.d_beta,
+                                                                      pl.noise_seed);
+        launches += 4;
     }
     ReduceArgs ra = reduce_args(ws, p);
     semd_status st = sift_loop<R>(pl, ra, ninst, ntiles, iters, s, prof, capture, launches);
     if (st != SEMD_OK)
         return st;
     if (eemd) {
-        k_eemd_average<R><<<ntiles0, 256, 0, s>>>(ws.d_inst, ws.d_state, ninst, p.max_imfs,
-                                                  (const R *)ws.eemd_scratch, ws.tile);
+        const int64_t L0 = (int64_t)ntiles0 * ws.tile; // at least the signal's length
+        k_eemd_average<R><<<(unsigned)((L0 + 256 * kAvgPer - 1) / (256 * kAvgPer)), 256, 0, s>>>(
+            ws.d_inst, ws.d_state, ninst, p.max_imfs, (const R *)ws.eemd_scratch);
     } else {
         k_finalize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
                                                          ws.tile, p.max_imfs);
@@ -1119,8 +1407,8 @@ semd_status decompose_impl(semd_plan_s &pl, int count, const semd_instance *inst
     const bool use_graph = pl.graphs && !pl.prof.on;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{ninst, ntiles, ntiles0, ws.max_ntiles, ws.tile, ws.pass_ctas,
-                           ws.pass_variant, pl.noise_seed};
+        const GraphKey key{ninst,         ntiles,         ntiles0,        ws.max_ntiles, ws.tile,
+                           ws.pass_ctas,  ws.pass_variant, pl.noise_seed, ws.min_ntiles};
         if (!pl.graph_exec || !(pl.graph_key == key)) {
             if (pl.graph_exec) {
                 cudaGraphExecDestroy(pl.graph_exec);
@@ -1294,8 +1582,9 @@ semd_status ceemdan_impl(semd_plan_s &pl, const void *d_x, const void *d_noise, 
     const bool use_graph = pl.graphs && !pl.prof.on;
     pl.prof.reset();
     if (use_graph) {
-        const GraphKey key{trials, ntiles, ws.h_inst[0].ntiles, ws.max_ntiles, ws.tile,
-                           ws.pass_ctas, ws.pass_variant};
+        const GraphKey key{trials,       ntiles,          ws.h_inst[0].ntiles, ws.max_ntiles,
+                           ws.tile,      ws.pass_ctas,    ws.pass_variant,     0,
+                           ws.min_ntiles};
         if (!pl.ce_graph_exec || !(pl.ce_graph_key == key)) {
             if (pl.ce_graph_exec) {
                 cudaGraphExecDestroy(pl.ce_graph_exec);
@@ -1478,7 +1767,7 @@ void launch_finalize_any(size_t elem, const Inst *d_inst, const State *d_state,
 
 ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_state,
                             const int32_t *inst_list, int32_t *active, size_t elem,
-                            int64_t max_ntiles)
+                            int64_t min_ntiles, int64_t max_ntiles)
 {
     ReduceArgs ra;
     ra.inst = d_inst;
@@ -1496,9 +1785,7 @@ ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_s
     ra.single = elem == 4 ? 1 : 0;
     ra.s_number = p.s_number;
     ra.spline_end = p.spline_end;
-    ra.pad = 0;
-    const int64_t entries = reduce_len(max_ntiles);
-    ra.smem_entries = reduce_smem_bytes(entries, elem) <= kReduceSmemMax ? entries : 0;
+    set_reduce_shape(ra, min_ntiles, max_ntiles, elem);
     return ra;
 }
 
@@ -1910,6 +2197,27 @@ semd_status serial_emd_plan_set_noise_seed(semd_plan_t plan, uint64_t seed)
     return SEMD_OK;
 }
 
+semd_status serial_emd_interface_solve_shape(int precision, int spline_end, int *cluster,
+                                             int64_t *min_tiles, int64_t *max_tiles)
+{
+    if (!cluster || !min_tiles || !max_tiles ||
+        (precision != SEMD_FP64 && precision != SEMD_FP32_MIXED) ||
+        (spline_end != SEMD_SPLINE_NATURAL && spline_end != SEMD_SPLINE_NOT_A_KNOT))
+        return SEMD_EINVAL;
+    const size_t elem = precision == SEMD_FP64 ? 8 : 4;
+    if (setup_kernel_attrs(elem) != cudaSuccess) {
+        cudaGetLastError();
+        return SEMD_ECUDA;
+    }
+    ReduceArgs ra{};
+    ra.spline_end = spline_end;
+    set_reduce_shape(ra, 1, 1, elem);
+    *cluster = ra.cl;
+    *min_tiles = ra.cl_min_nt;
+    *max_tiles = ra.cl_max_nt;
+    return SEMD_OK;
+}
+
 int64_t serial_emd_plan_launch_times(semd_plan_t plan, int kind, float *ms, int64_t cap)
 {
     if (!plan || (kind != 0 && kind != 1) || cap < 0)
@@ -2054,6 +2362,7 @@ static semd_status sift_noalloc_impl(const semd_params &p, const void *d_h, int6
     ws.d_stats = (Stats *)take(sizeof(Stats));
     double *d_result = (double *)take(4 * 8);
     ws.max_ntiles = ntiles;
+    ws.min_ntiles = ntiles;
     ws.tile = kTile;
     ws.elem_size = sizeof(R);
 

@@ -38,7 +38,8 @@ struct Workspace {
     int tile = kTile;
     int pass_ctas = 0;    // CTAs per SM of the persistent pass grid (0: as many as fit)
     int pass_variant = 0; // register budget of the pass kernel, where it has two
-    int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0, max_ntiles = 0; // cap_rentries: doubles of interface scratch
+    int64_t cap_samples = 0, cap_tiles = 0, cap_rentries = 0; // cap_rentries: doubles of interface scratch
+    int64_t max_ntiles = 0, min_ntiles = 0; // tile counts of the batch's longest / shortest instance
     int cap_inst = 0, cap_iters = 0;
     size_t elem_size = 0;
     void *h0 = nullptr, *h1 = nullptr;
@@ -103,7 +104,7 @@ void launch_finalize_any(size_t elem, const Inst *d_inst, const State *d_state,
                          cudaStream_t s);
 ReduceArgs make_reduce_args(const semd_params &p, const Inst *d_inst, State *d_state,
                             const int32_t *inst_list, int32_t *active, size_t elem,
-                            int64_t max_ntiles);
+                            int64_t min_ntiles, int64_t max_ntiles);
 void choose_pass_shape(const semd_params &p, int64_t L, int ninst, int &tile, int &ctas,
                        int &variant);
 // CTAs of the pass kernel that fit on one SM (working-precision size elem, tile, variant).
@@ -199,11 +200,12 @@ struct GraphKey {
     int pass_ctas = 0;
     int pass_variant = 0;
     uint64_t seed = 0;
+    int64_t min_ntiles = 0;
     bool operator==(const GraphKey &o) const
     {
         return ninst == o.ninst && ntiles == o.ntiles && ntiles0 == o.ntiles0 &&
                max_ntiles == o.max_ntiles && tile == o.tile && pass_ctas == o.pass_ctas &&
-               pass_variant == o.pass_variant && seed == o.seed;
+               pass_variant == o.pass_variant && seed == o.seed && min_ntiles == o.min_ntiles;
     }
 };
 

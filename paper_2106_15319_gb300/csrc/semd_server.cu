@@ -215,7 +215,7 @@ bool semd_server_s::round(Lane &ln, std::string &e)
         }
     }
     // descriptors and tile maps of every admitted request
-    int64_t ntiles = 0, max_nt = 0;
+    int64_t ntiles = 0, max_nt = 0, min_nt = INT64_MAX;
     int nact = 0;
     for (int i = 0; i < ln.max_inflight; ++i) {
         Slot &sl = ln.slots[i];
@@ -253,6 +253,7 @@ bool semd_server_s::round(Lane &ln, std::string &e)
             ln.h_tiles[ntiles + t] = i;
         ntiles += q.nt;
         max_nt = std::max<int64_t>(max_nt, q.nt);
+        min_nt = std::min<int64_t>(min_nt, q.nt);
         ln.h_list[nact++] = i;
     }
     if (nact == 0)
@@ -287,7 +288,7 @@ bool semd_server_s::round(Lane &ln, std::string &e)
     PassArgs pa{ln.d_inst, ln.d_state, ln.d_tiles, ntiles, p.stop == SEMD_STOP_SD ? 1 : 0,
                 p.stop == SEMD_STOP_SNUMBER ? 1 : 0};
     ReduceArgs ra = make_reduce_args(p, ln.d_inst, ln.d_state, ln.d_list, ln.d_active, elem,
-                                     max_nt);
+                                     min_nt, max_nt);
     for (int it = 0; it < passes; ++it) {
         launch_pass_any(elem, ln.tile, pa, ntiles, ln.stream, ctas);
         launch_reduce_any(elem, ra, nact, ln.stream);

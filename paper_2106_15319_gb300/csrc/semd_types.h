@@ -126,7 +126,15 @@ struct ReduceArgs {
     int32_t s_number;     // S of the S-number rule
     int64_t smem_entries; // > 0: per-envelope scratch of this many entries in shared memory
     int32_t spline_end;   // SPLINE_NATURAL or SPLINE_NOT_A_KNOT
-    int32_t pad;
+    // Instances of cl_min_nt..cl_max_nt tiles are solved by the cluster kernel (cl CTAs per
+    // envelope, cl_entries entries of scratch per CTA), all others by the one-CTA kernel;
+    // cl = 0: the one-CTA kernel for every instance. The choice depends on the instance's
+    // tile count alone, so an instance's results do not depend on its batch.
+    int32_t cl;
+    int64_t cl_entries;
+    int32_t cl_min_nt, cl_max_nt;
+    int32_t run_single; // host: some instance of the launch takes the one-CTA kernel
+    int32_t run_cl;     // host: some instance of the launch takes the cluster kernel
 };
 
 // One CEEMDAN call (Sec. 2.2, Steps 1-4), in device memory so that a captured graph can be

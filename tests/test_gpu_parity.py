@@ -563,6 +563,84 @@ def test_long_signal_global_interface_scratch_fp64():
     _check_imfs(g[0], g[1], g[2], o[0], o[1], o[2], o[4], capi.FP64, "long")
 
 
+def test_interface_solve_cluster_shape():
+    """On GB300 the interface solve of long instances (natural spline ends) runs on
+    thread-block clusters of 16 (else 8) CTAs per envelope, from the tile count where one
+    CTA's shared memory no longer holds the system; not-a-knot ends keep one CTA."""
+    for prec in (capi.FP64, capi.FP32_MIXED):
+        c, lo, hi = capi.serial_emd_interface_solve_shape(prec, capi.SPLINE_NATURAL)
+        assert c in (8, 16), (prec, c)
+        assert 256 < lo < hi, (prec, lo, hi)
+        assert capi.serial_emd_interface_solve_shape(prec, capi.SPLINE_NOT_A_KNOT) == (0, 0, 0)
+
+
+def _cluster_signal(nt, tile, seed, flat=True):
+    """A single signal of about nt tiles (ragged last tile) with tones, noise and, with
+    `flat`, a constant stretch of 40 tiles (tiles without knots)."""
+    g = synth.rng(seed)
+    L = nt * tile - 101
+    t = np.arange(L)
+    x = (np.sin(2 * np.pi * t / 7.3) + 0.6 * np.sin(2 * np.pi * t / 97.0) +
+         0.3 * np.sin(2 * np.pi * t / 2100.0) + 0.05 * g.standard_normal(L))
+    if flat:
+        a = L // 3
+        x[a:a + 40 * tile] = x[a]
+    return x[None, :]
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(mirror_knots=1),
+                                dict(boundary=capi.BOUNDARY_ENDPOINTS)])
+@pytest.mark.parametrize("where", ["low", "high"])
+def test_cluster_interface_solve_fp64(kw, where):
+    """Signals whose interface solve runs on a thread-block cluster (just above the tile
+    count where it starts, and at three times that, with tile 512), FP64 against the
+    oracle within 1e-10, with each boundary rule and a constant stretch."""
+    c, lo, hi = capi.serial_emd_interface_solve_shape(capi.FP64, capi.SPLINE_NATURAL)
+    tile = 256 if where == "low" else 512
+    nt = lo + 3 if where == "low" else min(3 * lo, hi)
+    X = _cluster_signal(nt, tile, 4100 + nt)
+    p = make_params(1, X.shape[1], precision=capi.FP64, transition_len=0, max_imfs=6, **kw)
+    plan = Plan(p)
+    plan.tile = tile
+    imfs, res, n = plan.decompose(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    o = _oracle(X, capi.FP64, transition_len=0, max_imfs=6, **kw)
+    _check_imfs(imfs.cpu().numpy(), res.cpu().numpy(), n, o[0], o[1], o[2], o[4], capi.FP64,
+                f"cluster {where} {kw}")
+
+
+def test_cluster_interface_solve_batch_independent_fp32():
+    """A batch holding a long signal (cluster interface solve) and short ones (one-CTA
+    solve) gives every instance the results it gets alone, bit for bit, in FP32: the
+    solver of an instance depends on its own tile count only. The long one also meets
+    the FP32 rule against the oracle."""
+    c, lo, hi = capi.serial_emd_interface_solve_shape(capi.FP32_MIXED, capi.SPLINE_NATURAL)
+    long_x = _cluster_signal(lo + 100, 256, 77)[0].astype(np.float32)
+    short = [np.asarray(synth.grating_image(s, 5 + s), np.float32).reshape(-1)
+             for s in (40, 96, 150)]
+    xs = [long_x] + short
+    L = max(len(v) for v in xs)
+    p = make_params(1, L, precision=capi.FP32_MIXED, transition_len=0, max_imfs=5)
+    plan = Plan(p, max_batch=len(xs))
+    outs, n = plan.decompose_batch([torch.from_numpy(v[None, :]).cuda() for v in xs])
+    torch.cuda.synchronize()
+    plan.close()
+    for i, v in enumerate(xs):
+        q = Plan(make_params(1, len(v), precision=capi.FP32_MIXED, transition_len=0,
+                             max_imfs=5))
+        ai, ar, an = q.decompose(torch.from_numpy(v[None, :]).cuda())
+        torch.cuda.synchronize()
+        shape = (q.tile, q.pass_variant)
+        q.close()
+        gi, gr = outs[i]
+        assert n[i] == an, i
+        assert torch.equal(gi, ai) and torch.equal(gr, ar), i
+        if i == 0:
+            _check_fp32_given_input(ai.double().cpu().numpy(), ar.cpu().numpy(), an,
+                                    v.astype(np.float64), 5, "cluster fp32", shape=shape)
+
+
 def test_largest_serving_image_fp32():
     """A 2048 x 2048 image (4.2 M samples, the serving mix's largest request) in FP32:
     exact FP64 reconstruction, the oracle's IMF count, and its two leading IMFs given the

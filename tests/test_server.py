@@ -143,8 +143,9 @@ def test_server_destroy_while_busy_leaves_gpu_usable():
 
 def test_server_large_request_lane_results_equal_alone():
     """A request of at least 2^21 serialized samples runs in the server's second lane
-    (its own worker and stream) while small requests keep arriving; every result equals
-    the same input decomposed alone."""
+    (its own worker and stream, 512-sample pass tiles) while small requests keep arriving;
+    every result equals the same input decomposed alone with the same tile (FP32 results
+    depend on the tile, which decides where the spline system is partitioned)."""
     base = make_params(1600, 1600, precision=capi.FP32_MIXED, transition_len=0, max_imfs=6)
     server = Server(base, 2 << 30, 8)
     big = synth.grating_image(1500, 4)  # 2.25 M samples
@@ -157,6 +158,8 @@ def test_server_large_request_lane_results_equal_alone():
         assert res[t].status == capi.SEMD_OK
         plan = Plan(make_params(*X.shape, precision=capi.FP32_MIXED, transition_len=0,
                                 max_imfs=6, order=order))
+        if X.size >= 1 << 21:
+            plan.tile = 512
         ai, ar, an = plan.decompose(x)
         torch.cuda.synchronize()
         plan.close()
