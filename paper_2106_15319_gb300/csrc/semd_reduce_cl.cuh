@@ -29,6 +29,11 @@ namespace cgc = cooperative_groups;
 
 constexpr int kClMax = 16;                  // CTAs per envelope at most (non-portable size)
 constexpr int kClGroups = kClMax * 32;      // level-1.5 groups of a cluster at most
+// Group arrays of CTA 0 are stored skewed (index j + j / 32), so that the lanes of the
+// level-1.75 warp, which walk runs of consecutive groups at a fixed stride, hit distinct
+// banks.
+constexpr int kClGroupSlots = kClGroups + kClGroups / 32;
+__host__ __device__ constexpr int gsk(int j) { return j + (j >> 5); }
 constexpr size_t kClSmemOptin = 232448;     // shared memory per CTA an SM can give (227 KB)
 
 // Counts of one CTA, published for the cluster-wide scan.
@@ -53,11 +58,10 @@ struct ClShared {
     int segq[kRedThreads];
     // level 1.5: per run of a group its elimination factors, then its end unknown
     R cp2[kRedThreads], dp2[kRedThreads], bp2[kRedThreads], zrun[kRedThreads];
-    // level 1.5 result per group (10 values) and its rows
-    R grp[10][32];
-    int grq[32];
-    // CTA 0: level 1.75 factors per group and every group's end unknown
-    R cp3[kClGroups], dp3[kClGroups], bp3[kClGroups], gz[kClGroups];
+    // CTA 0: every group's level-1.5 result (10 values, stored by the CTA that owns the
+    // group), the level-1.75 factors per group and every group's end unknown
+    R gg[10][kClGroupSlots];
+    R cp3[kClGroupSlots], dp3[kClGroupSlots], bp3[kClGroupSlots], gz[kClGroupSlots];
 };
 
 // Bytes of ClShared at the start of the dynamic shared memory (16-byte multiple), and the
@@ -112,12 +116,15 @@ __device__ __forceinline__ RedScratch<R> cl_remote(const cgc::cluster_group &cl,
 }
 
 // One entry of a tile record (its k-th, of u), stored at slot q of scratch Y; the same
-// entries as the single-CTA kernel's put_entries.
+// entries as the one-CTA kernel's put_entries. Record fields are picked with selects, so
+// that the record stays in registers.
 template <typename R>
 __device__ __forceinline__ void cl_put_entry(const RedScratch<R> &Y, int q, const TileRec<R> &rc,
                                              int k)
 {
     const int n = rc.n;
+    auto tk = [&](int i) { return i == 0 ? rc.t[0] : i == 1 ? rc.t[1] : i == 2 ? rc.t[2] : rc.t[3]; };
+    auto yk = [&](int i) { return i == 0 ? rc.y[0] : i == 1 ? rc.y[1] : i == 2 ? rc.y[2] : rc.y[3]; };
     if (n == 1) {
         Y.Et[q] = rc.t[0];
         Y.Ey[q] = rc.y[0];
@@ -125,20 +132,19 @@ __device__ __forceinline__ void cl_put_entry(const RedScratch<R> &Y, int q, cons
     } else if (n <= kSparseKnots) {
         // knots in order: t[0], (t[1] if n >= 3), (t[2] if n == 4), t[3]
         const int src = k == 0 ? 0 : (k == n - 1 ? 3 : k);
-        Y.Et[q] = rc.t[src];
-        Y.Ey[q] = rc.y[src];
+        Y.Et[q] = tk(src);
+        Y.Ey[q] = yk(src);
         Y.Ek[q] = k == 0 ? EK_F : (k == n - 1 ? EK_L : EK_FREE);
     } else {
-        const int src = k == 0 ? 0 : 3;
-        Y.Et[q] = rc.t[src];
-        Y.Ey[q] = rc.y[src];
-        Y.Ek[q] = k == 0 ? EK_FS : EK_LS;
-        Y.St[q] = rc.t[k == 0 ? 1 : 2];
-        Y.A[q] = rc.y[k == 0 ? 1 : 2];
-        const R *x = k == 0 ? rc.xa : rc.xb;
-        Y.B[q] = x[0];
-        Y.C[q] = x[1];
-        Y.D[q] = x[2];
+        const bool f = k == 0;
+        Y.Et[q] = f ? rc.t[0] : rc.t[3];
+        Y.Ey[q] = f ? rc.y[0] : rc.y[3];
+        Y.Ek[q] = f ? EK_FS : EK_LS;
+        Y.St[q] = f ? rc.t[1] : rc.t[2];
+        Y.A[q] = f ? rc.y[1] : rc.y[2];
+        Y.B[q] = f ? rc.xa[0] : rc.xb[0];
+        Y.C[q] = f ? rc.xa[1] : rc.xb[1];
+        Y.D[q] = f ? rc.xa[2] : rc.xb[2];
     }
 }
 
@@ -169,6 +175,9 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
     const int T = (nt + CL - 1) / CL; // tiles per CTA
     const int ta = min(c * T, nt), tb = min(ta + T, nt), ntc = tb - ta;
     pdl_wait();
+    // the next kernel may start now: the pass this solve waited for is complete, so the
+    // next pass can read that pass's signal before its own wait
+    pdl_trigger();
     State *st = ra.state + ii;
     const int mode_now = st->mode;
     const int pm = st->pass_mode, psift = st->pass_sift, pimf = st->pass_imf;
@@ -177,10 +186,42 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
     constexpr int NW = kRedThreads / 32;
     const bool want_sd = ra.stop == STOP_SD, want_zc = ra.stop == STOP_SNUMBER;
 
-    // ---- counts of this CTA's tiles, four records per thread in flight at a time
+    // ---- counts of this CTA's tiles. With at most two tiles per thread, the thread loads
+    // the whole records of its chunk of tiles here and keeps them for its entries;
+    // otherwise records are counted in a block stride, four in flight per thread at a
+    // time, and loaded again for the entries.
     int sn = 0, so_ = 0, zs = 0;
     double a = 0.0, b = 0.0;
-    for (int t0 = ta; t0 < tb; t0 += 4 * kRedThreads) {
+    constexpr int kKeep = 2;
+    const bool keep = ntc <= kKeep * kRedThreads;
+    const int CH = (ntc + kRedThreads - 1) / kRedThreads;
+    TileRec<R> rk[kKeep];
+    if (keep) {
+#pragma unroll
+        for (int k = 0; k < kKeep; ++k) {
+            const int t = tid * CH + k;
+            rk[k].n = 0;
+            if (k < CH && t < ntc) {
+                rk[k] = load_rec(texe + ta + t);
+                so_ += texo[ta + t].n;
+                if (want_sd) {
+                    a += taux[ta + t].sd_num;
+                    b += taux[ta + t].sd_den;
+                }
+                if (want_zc)
+                    zs += taux[ta + t].nzc;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kKeep; ++k) {
+            const int t = tid * CH + k;
+            if (k < CH && t < ntc) {
+                X.Tu[t] = (unsigned char)(rk[k].n <= kSparseKnots ? rk[k].n : 2);
+                sn += rk[k].n;
+            }
+        }
+    }
+    for (int t0 = ta; !keep && t0 < tb; t0 += 4 * kRedThreads) {
         int ne[4], no[4], nz[4];
         double sa[4], sb[4];
 #pragma unroll
@@ -227,7 +268,6 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
     }
     __syncthreads();
     // entry offsets within the CTA: a contiguous chunk of tiles per thread, a block scan
-    const int CH = (ntc + kRedThreads - 1) / kRedThreads;
     const int ca = min(tid * CH, ntc), cb = min(ca + CH, ntc);
     int su = 0;
     for (int t = ca; t < cb; ++t)
@@ -312,7 +352,20 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
         }
     }
     __syncthreads();
-    for (int t0 = 0; t0 < ntc; t0 += 4 * kRedThreads) {
+    if (keep) {
+#pragma unroll
+        for (int k = 0; k < kKeep; ++k) {
+            const int t = tid * CH + k;
+            if (k < CH && t < ntc) {
+                const int u = X.Tu[t], p = X.To[t];
+                for (int j = 0; j < u; ++j) {
+                    const int g = p + j, o = rows.owner(g);
+                    cl_put_entry(o == c ? X : cl_remote(cl, X, o), rows.slot(g), rk[k], j);
+                }
+            }
+        }
+    }
+    for (int t0 = 0; !keep && t0 < ntc; t0 += 4 * kRedThreads) {
         TileRec<R> rb[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -545,14 +598,15 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
                 g2.beS = xb;
                 g2.gaS = xg;
             }
+            // into CTA 0, which joins the groups of the whole cluster
             const R gv[10] = {g2.alS, g2.beS, g2.gaS, g2.alE, g2.beE, g2.gaE, g2.al, g2.bl, g2.cl, g2.dl};
+            ClShared<R> *S0 = cl.map_shared_rank(&S, 0);
 #pragma unroll
             for (int k = 0; k < 10; ++k)
-                S.grp[k][lane] = gv[k];
-            S.grq[lane] = sb - sa;
+                S0->gg[k][gsk(G0 + lane)] = gv[k];
         }
     }
-    cl.sync(); // (4) every CTA's groups
+    cl.sync(); // (4) every CTA's groups, in CTA 0
 
     // ---- levels 1.75 and 2 (CTA 0, warp 0): lane L joins groups [ja, jb) of the cluster;
     // the 32 lane-end unknowns are solved to FP64 accuracy; then every group's end unknown
@@ -561,40 +615,19 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
         int ja = 0, jb = 0;
         if (lane < NL)
             bsplit(NGT, NL, lane, ja, jb);
-        // group j of the cluster: its CTA and its index there
-        auto locate = [&](int j, int &r, int &i) {
-            r = 0;
-            int before = 0;
-            while (r + 1 < CL && before + groups_of(r) <= j) {
-                before += groups_of(r);
-                ++r;
-            }
-            i = j - before;
-        };
+        // reduced row of group j of the cluster (every group has at least one run)
         auto gred_row = [&](int j, R &A, R &B, R &C, R &D) {
-            int r, i;
-            locate(j, r, i);
-            const ClShared<R> *Sr = cl.map_shared_rank(&S, r);
             SegElim<R> gj;
-            gj.alE = Sr->grp[3][i];
-            gj.beE = Sr->grp[4][i];
-            gj.gaE = Sr->grp[5][i];
-            gj.al = Sr->grp[6][i];
-            gj.bl = Sr->grp[7][i];
-            gj.cl = Sr->grp[8][i];
-            gj.dl = Sr->grp[9][i];
-            const int q = Sr->grq[i];
+            gj.alE = S.gg[3][gsk(j)];
+            gj.beE = S.gg[4][gsk(j)];
+            gj.gaE = S.gg[5][gsk(j)];
+            gj.al = S.gg[6][gsk(j)];
+            gj.bl = S.gg[7][gsk(j)];
+            gj.cl = S.gg[8][gsk(j)];
+            gj.dl = S.gg[9][gsk(j)];
             const bool hn = j + 1 < NGT;
-            R nS[3] = {R(0), R(0), R(0)};
-            if (hn) {
-                int r2, i2;
-                locate(j + 1, r2, i2);
-                const ClShared<R> *S2 = cl.map_shared_rank(&S, r2);
-                nS[0] = S2->grp[0][i2];
-                nS[1] = S2->grp[1][i2];
-                nS[2] = S2->grp[2][i2];
-            }
-            reduced_row(gj, q, hn, nS[0], nS[1], nS[2], A, B, C, D);
+            reduced_row(gj, 1, hn, hn ? S.gg[0][gsk(j + 1)] : R(0), hn ? S.gg[1][gsk(j + 1)] : R(0),
+                        hn ? S.gg[2][gsk(j + 1)] : R(0), A, B, C, D);
         };
         SegElim<R> g3;
         if (lane < NL) {
@@ -606,9 +639,9 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
                 cprev = C * inv;
                 dprev = (D - A * dprev) * inv;
                 bprev = -A * bprev * inv;
-                S.cp3[j] = cprev;
-                S.dp3[j] = dprev;
-                S.bp3[j] = bprev;
+                S.cp3[gsk(j)] = cprev;
+                S.dp3[gsk(j)] = dprev;
+                S.bp3[gsk(j)] = bprev;
             }
             gred_row(jb - 1, g3.al, g3.bl, g3.cl, g3.dl);
             if (jb - ja >= 2) {
@@ -617,9 +650,9 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
                 g3.gaE = -cprev;
                 R xa = g3.alE, xb = g3.beE, xg = g3.gaE;
                 for (int j = jb - 3; j >= ja; --j) {
-                    const R cc = S.cp3[j];
-                    xa = S.dp3[j] - cc * xa;
-                    xb = S.bp3[j] - cc * xb;
+                    const R cc = S.cp3[gsk(j)];
+                    xa = S.dp3[gsk(j)] - cc * xa;
+                    xb = S.bp3[gsk(j)] - cc * xb;
                     xg = -cc * xg;
                 }
                 g3.alS = xa;
@@ -633,11 +666,11 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
         if (lane == 0)
             Zp = R(0);
         if (lane < NL) {
-            S.gz[jb - 1] = z;
+            S.gz[gsk(jb - 1)] = z;
             R xn = z;
             for (int j = jb - 2; j >= ja; --j) {
-                const R x = S.dp3[j] + S.bp3[j] * Zp - S.cp3[j] * xn;
-                S.gz[j] = x;
+                const R x = S.dp3[gsk(j)] + S.bp3[gsk(j)] * Zp - S.cp3[gsk(j)] * xn;
+                S.gz[gsk(j)] = x;
                 xn = x;
             }
         }
@@ -648,7 +681,7 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
     if (warp == 0 && lane < NG) {
         const R *gz = cl.map_shared_rank(S.gz, 0);
         const int J = G0 + lane;
-        const R z = gz[J], Zp = J > 0 ? gz[J - 1] : R(0);
+        const R z = gz[gsk(J)], Zp = J > 0 ? gz[gsk(J - 1)] : R(0);
         S.zrun[sb - 1] = z;
         R xn = z;
         for (int j = sb - 2; j >= sa; --j) {
@@ -662,7 +695,7 @@ __global__ void __launch_bounds__(kRedThreads, 1) k_reduce_cl(ReduceArgs ra)
         // the unknown before the run: the previous run's end (for a CTA's first run, the
         // previous CTA's last group's end)
         const R Zp = tid > 0 ? S.zrun[tid - 1]
-                             : (G0 > 0 ? cl.map_shared_rank(S.gz, 0)[G0 - 1] : R(0));
+                             : (G0 > 0 ? cl.map_shared_rank(S.gz, 0)[gsk(G0 - 1)] : R(0));
         seg_backsub_rows<R>(X.A + 1, X.C + 1, X.D + 1, X.MV + 1, rs, re, Zp, S.zrun[tid]);
     }
     cl.sync(); // (6) every row's second derivative

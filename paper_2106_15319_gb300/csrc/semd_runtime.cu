@@ -241,8 +241,9 @@ __global__ void k_finalize(const Inst *inst, const State *state, const int32_t *
 // single-precision IMF values in float-float arithmetic (an unevaluated pair of floats,
 // about 48 significant bits: as accurate as the FP64 sum for these inputs, without the
 // narrow FP64 pipe); the residues are FP64 in both. A thread takes 4 consecutive samples
-// (16- or 32-byte loads of each trial's IMF row), a CTA 1024; the trials' IMF counts and
-// residue arrays are read once per CTA into shared memory (the first kAvgShared trials).
+// (16- or 32-byte loads of each trial's IMF row) of one IMF k = blockIdx.y (k = K: the
+// residue), a CTA 1024 samples; the trials' IMF counts and residue arrays are read once per
+// CTA into shared memory (the first kAvgShared trials).
 constexpr int kAvgShared = 512;
 constexpr int kAvgPer = 4;
 template <typename R>
@@ -256,74 +257,22 @@ __global__ void k_eemd_average(const Inst *inst, const State *state, int trials,
         rptr[m] = inst[m].r[state[m].rpar];
     }
     __syncthreads();
-    auto count_of = [&](int m) { return m < kAvgShared ? ncnt[m] : state[m].imf_count; };
     const Inst &in = inst[0];
-    R *out = (R *)in.avg_imf;
-    double *res = in.avg_res;
+    const int k = blockIdx.y;
     const int64_t L = in.L;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kAvgPer;
     if (p0 >= L)
         return;
     const int n = (int)min((int64_t)kAvgPer, L - p0); // the tail thread may have fewer
-    const int64_t outstride = in.M * in.N;
-    const int64_t step = (int64_t)K * in.imf_stride; // one trial's IMF block
     int64_t dst[kAvgPer];
     bool keep[kAvgPer];
 #pragma unroll
     for (int j = 0; j < kAvgPer; ++j)
         keep[j] = j < n && deser_index(p0 + j, in.M, in.N, in.D, in.order, dst[j]);
-    for (int k = 0; k < K; ++k) {
-        const R *src = scratch + (int64_t)k * in.imf_stride + p0;
-        double sum[kAvgPer];
-        if constexpr (sizeof(R) == 4) {
-            FFSum acc[kAvgPer];
-#pragma unroll 4
-            for (int m = 0; m < trials; ++m) {
-                float v[kAvgPer];
-                if (n == kAvgPer) {
-                    vload<kAvgPer>(src + m * step, v);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kAvgPer; ++j)
-                        v[j] = j < n ? src[m * step + j] : 0.f;
-                }
-                if (k < count_of(m)) {
-#pragma unroll
-                    for (int j = 0; j < kAvgPer; ++j)
-                        acc[j].add(v[j], 0.f);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < kAvgPer; ++j)
-                sum[j] = (double)acc[j].hi + (double)acc[j].lo;
-        } else {
-            double acc[kAvgPer] = {};
-#pragma unroll 4
-            for (int m = 0; m < trials; ++m) {
-                double v[kAvgPer];
-                if (n == kAvgPer) {
-                    vload<kAvgPer>(src + m * step, v);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kAvgPer; ++j)
-                        v[j] = j < n ? src[m * step + j] : 0.0;
-                }
-                if (k < count_of(m)) {
-#pragma unroll
-                    for (int j = 0; j < kAvgPer; ++j)
-                        acc[j] += v[j];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < kAvgPer; ++j)
-                sum[j] = acc[j];
-        }
-#pragma unroll
-        for (int j = 0; j < kAvgPer; ++j)
-            if (keep[j])
-                out[(int64_t)k * outstride + dst[j]] = (R)(sum[j] / (double)trials);
-    }
-    if (res) {
+    if (k == K) { // the residues
+        double *res = in.avg_res;
+        if (!res)
+            return;
         double acc[kAvgPer] = {};
 #pragma unroll 4
         for (int m = 0; m < trials; ++m) {
@@ -336,7 +285,60 @@ __global__ void k_eemd_average(const Inst *inst, const State *state, int trials,
         for (int j = 0; j < kAvgPer; ++j)
             if (keep[j])
                 res[dst[j]] = acc[j] / (double)trials;
+        return;
     }
+    auto count_of = [&](int m) { return m < kAvgShared ? ncnt[m] : state[m].imf_count; };
+    R *out = (R *)in.avg_imf + (int64_t)k * in.M * in.N;
+    const int64_t step = (int64_t)K * in.imf_stride; // one trial's IMF block
+    const R *src = scratch + (int64_t)k * in.imf_stride + p0;
+    double sum[kAvgPer];
+    if constexpr (sizeof(R) == 4) {
+        FFSum acc[kAvgPer];
+#pragma unroll 4
+        for (int m = 0; m < trials; ++m) {
+            float v[kAvgPer];
+            if (n == kAvgPer) {
+                vload<kAvgPer>(src + m * step, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kAvgPer; ++j)
+                    v[j] = j < n ? src[m * step + j] : 0.f;
+            }
+            if (k < count_of(m)) {
+#pragma unroll
+                for (int j = 0; j < kAvgPer; ++j)
+                    acc[j].add(v[j], 0.f);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kAvgPer; ++j)
+            sum[j] = (double)acc[j].hi + (double)acc[j].lo;
+    } else {
+        double acc[kAvgPer] = {};
+#pragma unroll 4
+        for (int m = 0; m < trials; ++m) {
+            double v[kAvgPer];
+            if (n == kAvgPer) {
+                vload<kAvgPer>(src + m * step, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kAvgPer; ++j)
+                    v[j] = j < n ? src[m * step + j] : 0.0;
+            }
+            if (k < count_of(m)) {
+#pragma unroll
+                for (int j = 0; j < kAvgPer; ++j)
+                    acc[j] += v[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kAvgPer; ++j)
+            sum[j] = acc[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kAvgPer; ++j)
+        if (keep[j])
+            out[dst[j]] = (R)(sum[j] / (double)trials);
 }
 
 // One EEMD realization's IMFs and residue as the last decomposition left them (Sec. 2.2:
@@ -819,8 +821,9 @@ static size_t reduce_smem(const ReduceArgs &ra)
 // One CTA per instance and envelope. When the shared scratch holds every instance's
 // system (smem_entries, sized for the launch's longest instance, bounds each system's
 // rows) and that is at most kRedSmallRows rows, the small-system kernel runs.
-// The cluster kernel: ra.cl CTAs per instance and envelope, one cluster each (a plain
-// launch: it starts once the pass kernel has finished).
+// The cluster kernel: ra.cl CTAs per instance and envelope, one cluster each, launched
+// with programmatic dependent launch like the other kernels of the sifting loop (its CTAs
+// take the SMs the pass kernel leaves, and wait for it to finish before reading).
 template <typename R>
 static void launch_reduce_cl(const ReduceArgs &ra, int ninst, cudaStream_t s)
 {
@@ -829,13 +832,15 @@ static void launch_reduce_cl(const ReduceArgs &ra, int ninst, cudaStream_t s)
     cfg.blockDim = dim3(kRedThreads);
     cfg.dynamicSmemBytes = cl_smem_bytes<R>(ra.cl_entries);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)ra.cl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g_plain_launches ? 1 : 2;
     cudaLaunchKernelEx(&cfg, k_reduce_cl<R>, ra);
 }
 
@@ -1344,8 +1349,10 @@ static semd_status enqueue_decomposition(semd_plan_s &pl, int ninst, int64_t nti
         return st;
     if (eemd) {
         const int64_t L0 = (int64_t)ntiles0 * ws.tile; // at least the signal's length
-        k_eemd_average<R><<<(unsigned)((L0 + 256 * kAvgPer - 1) / (256 * kAvgPer)), 256, 0, s>>>(
-            ws.d_inst, ws.d_state, ninst, p.max_imfs, (const R *)ws.eemd_scratch);
+        const dim3 ag((unsigned)((L0 + 256 * kAvgPer - 1) / (256 * kAvgPer)),
+                      (unsigned)(p.max_imfs + 1));
+        k_eemd_average<R><<<ag, 256, 0, s>>>(ws.d_inst, ws.d_state, ninst, p.max_imfs,
+                                             (const R *)ws.eemd_scratch);
     } else {
         k_finalize<R><<<(unsigned)ntiles, 256, 0, s>>>(ws.d_inst, ws.d_state, ws.d_tile_inst,
                                                          ws.tile, p.max_imfs);
