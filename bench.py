@@ -132,6 +132,11 @@ def workload_inputs(name: str, trials: int = 256):
                 "desc": "serial-CEEMDAN of the 6-variate tone set (6 x 1000, D=50, L=6250), "
                         "100 noise realizations (beta_k = 0.2 std(r_k)), 10 sifts/mode, "
                         "<=10 modes"}
+    if name in ("image1024", "image2048"):
+        side = 1024 if name == "image1024" else 2048
+        return {"X": synth.grating_image(side, 99), "K": 10, "S": 10, "D": 0, "trials": 1,
+                "desc": f"{side}x{side} grating image (the serving mix's largest requests), "
+                        f"row-serialized, D=0, L={side * side}, 10 sifts/IMF, <=10 IMFs"}
     if name == "series3x1024":
         return {"X": synth.workload_series_3x1024(), "K": 8, "S": 10, "D": 0, "trials": 1,
                 "desc": "3-channel series x 1024 samples (tones + chirp + noise), D=0, L=3072, "
@@ -599,7 +604,8 @@ def arm_ours(args):
                 "slices": lambda: standard_slices(args, device, flush, world),
                 "ceemdan": lambda: ceemdan_legs(args, device, flush, world),
                 "dsweep": lambda: d_sweep(args, device, world),
-                "serving": lambda: serving(args, device)}
+                "serving": lambda: serving(args, device),
+                "large": lambda: large_images_leg(args, device, flush, world)}
         out = legs[args.only_leg]()
         if rank == 0:
             print(json.dumps({"only_leg": args.only_leg, "result": out}), flush=True)
@@ -703,6 +709,7 @@ def arm_ours(args):
                                                     world)
         if not args.no_batched:
             line["series_3x1024"] = series_leg(args, device, flush, world)
+            line["large_images"] = large_images_leg(args, device, flush, world)
             line["standard_slices"] = standard_slices(args, device, flush, world)
             line["standard_slices"]["serial_over_slices_time"] = \
                 line["ms_per_step"] / line["standard_slices"]["ms_per_step"]
@@ -719,6 +726,7 @@ def arm_ours(args):
         batched_eemd(args, device, flush, peak, peak_kind, world)
         batched_images(args, device, flush, peak, peak_kind, world)
         series_leg(args, device, flush, world)
+        large_images_leg(args, device, flush, world)
         standard_slices(args, device, flush, world)
         ceemdan_legs(args, device, flush, world)
         d_sweep(args, device, world)
@@ -940,6 +948,29 @@ def series_leg(args, device, flush, world):
         r["plan"].close()
     if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
         out["cpu_baseline"] = cpu_baseline(wl, budget_s=3.0)
+    return out
+
+
+def large_images_leg(args, device, flush, world):
+    """Single long instances, whose interface solve runs on a thread-block cluster: the
+    1024 x 1024 and 2048 x 2048 grating images in FP32-mixed (10 sifts per IMF, at most 10
+    IMFs), one decomposition per step (graph replay), and the per-launch device time of
+    the pass and interface-solve kernels from one profiled decomposition."""
+    from paper_2106_15319_gb300 import capi
+    out = {"shape": dict(zip(("cluster_ctas", "min_tiles", "max_tiles"),
+                             capi.serial_emd_interface_solve_shape(capi.FP32_MIXED)))}
+    for name in ("image1024", "image2048"):
+        wl = workload_inputs(name)
+        r = run_ours(wl, capi.FP32_MIXED, max(1, min(args.steps, 5)), min(args.warmup, 3),
+                     device, flush, tune=False)
+        ms = max_over_ranks(statistics.mean(r["ms"]), world)
+        prof = profile_pass(r, 1, flush)
+        out[name] = {"workload": wl["desc"], "ms_per_step": ms,
+                     "value": world * r["sample_sifts"] / (ms * 1e-3), "unit": UNIT,
+                     "pass_shape": r["shape"], "cuda_graph": bool(r["graph"]),
+                     "pass_avg_us": 1e3 * prof["pass_ms"] / max(1, prof["pass_n"]),
+                     "interface_solve_avg_us": 1e3 * prof["reduce_ms"] / max(1, prof["reduce_n"])}
+        r["plan"].close()
     return out
 
 
@@ -1167,7 +1198,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="texture256",
-                    choices=["texture256", "eemd512", "series3x1024", "ceemdan_mask"])
+                    choices=["texture256", "eemd512", "series3x1024", "ceemdan_mask",
+                             "image1024", "image2048"])
     ap.add_argument("--trials", type=int, default=256, help="EEMD realizations (eemd512)")
     ap.add_argument("--forms", default="fp32,fp64", help="comma list of fp32, fp64")
     ap.add_argument("--no-e2e", action="store_true")
@@ -1185,7 +1217,7 @@ def main():
                     help="keep the default pass shape (no autotuning before the warm-up)")
     ap.add_argument("--only-leg", default=None,
                     choices=["batched", "images", "slices", "ceemdan", "dsweep", "serving",
-                             "once"],
+                             "large", "once"],
                     help="run one extra leg alone and print its result (for profiling); "
                          "once: one decomposition of --workload, graphs off, no warm-up")
     ap.add_argument("--no-fp32-errors", action="store_true",
