@@ -39,8 +39,8 @@ EEMD_NOISE_SEED = 20210629 + 4  # seed of the white noise the library draws for 
 # decomposition: an IMF-1 sift) per (tile, variant), from an ncu capture of that launch with
 # the dram__bytes counters (cold caches, as ncu replays). Emptied whenever the pass kernel
 # changes, until the changed kernel is captured again; an empty entry is reported as null.
-PASS_TRAFFIC_TEXTURE = {(128, 0): 588032, (128, 1): 585216, (256, 0): 470272,
-                        (256, 1): 466176, (512, 0): 412416, (512, 1): 413184}
+PASS_TRAFFIC_TEXTURE = {(128, 0): 587776, (128, 1): 587008, (256, 0): 470272,
+                        (256, 1): 467456, (512, 0): 412160, (512, 1): 412928}
 # FP64-pipe lane operations (sm__inst_executed_pipe_fp64 x 32) of one k_pass<double> launch
 # of the default workload, per (tile, variant), from an ncu capture of that launch; emptied
 # whenever the pass kernel changes.
@@ -689,8 +689,8 @@ def arm_ours(args):
                      "avg_launch_us": pass_avg_ms * 1e3, "bytes_per_launch": bytes_per_launch,
                      "launches": prof["pass_n"], "reduce_avg_us":
                          prof["reduce_ms"] / max(1, prof["reduce_n"]) * 1e3,
-                     "note": "events around every pass launch over a replay of the timed steps "
-                             "(graphs off); working set L2-resident"},
+                     "note": "events around every kernel launch of the sifting loop over a "
+                             "replay of the timed steps (graphs off); working set L2-resident"},
         "e2e": e2e,
         "gpu_launches": int(r32["launches"]) * args.steps,
         "clocks": clk.summary(),
