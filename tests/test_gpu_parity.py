@@ -838,11 +838,13 @@ def test_autotune_ensemble_plan():
     capi.serial_emd_tune_clear()
 
 
-def test_pass_kernel_register_variants_agree_bit_for_bit():
-    """The two register budgets of the FP32 256-sample pass kernel compile the same
-    arithmetic: identical IMFs, residue and counts."""
-    X = synth.workload_texture_256().astype(np.float32)
-    plan = Plan(make_params(256, 256, transition_len=0, max_imfs=6))
+@pytest.mark.parametrize("prec", [capi.FP32_MIXED, capi.FP64])
+def test_pass_kernel_register_variants_agree_bit_for_bit(prec):
+    """The two variants of the 256-sample pass kernel (staging the next tile; a smaller
+    kernel without staging) compile the same arithmetic, with any CTA count per SM:
+    identical IMFs, residue and counts, in both precisions."""
+    X = synth.workload_texture_256().astype(NP[prec])
+    plan = Plan(make_params(256, 256, precision=prec, transition_len=0, max_imfs=6))
     x = torch.from_numpy(X).cuda()
     out = []
     for v in (0, 1):
