@@ -1322,9 +1322,12 @@ __device__ __forceinline__ SegElim<R> seg_eliminate_rows(R *__restrict__ XA,
     if (re - rs < 1)
         return g;
     R cprev = R(0), dprev = R(0), bprev = R(1);
-#pragma unroll 4
+    // the next row is loaded while the current one is eliminated (the loads do not wait
+    // for the chain of reciprocals)
+    R A = XA[rs], B = XB[rs], C = XC[rs], D = XD[rs];
+#pragma unroll 2
     for (int j = rs; j < re - 1; ++j) {
-        const R A = XA[j], B = XB[j], C = XC[j], D = XD[j];
+        const R An = XA[j + 1], Bn = XB[j + 1], Cn = XC[j + 1], Dn = XD[j + 1];
         const R inv = rrcp(B - A * cprev);
         cprev = C * inv;
         dprev = (D - A * dprev) * inv;
@@ -1332,11 +1335,15 @@ __device__ __forceinline__ SegElim<R> seg_eliminate_rows(R *__restrict__ XA,
         XA[j] = bprev;
         XC[j] = cprev;
         XD[j] = dprev;
+        A = An;
+        B = Bn;
+        C = Cn;
+        D = Dn;
     }
-    g.al = XA[re - 1];
-    g.bl = XB[re - 1];
-    g.cl = XC[re - 1];
-    g.dl = XD[re - 1];
+    g.al = A; // row re - 1, kept
+    g.bl = B;
+    g.cl = C;
+    g.dl = D;
     if (re - rs >= 2) {
         g.alE = dprev;
         g.beE = bprev;
