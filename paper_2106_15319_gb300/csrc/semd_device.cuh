@@ -46,14 +46,21 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
-// Reciprocals: the hardware approximation in FP32 (about 2 ulp); in FP64 a float seed
-// refined by two Newton steps (about 1 ulp), which avoids the long IEEE division
+// Reciprocals: the hardware approximation in FP32 (the PTX rcp.approx instruction, about
+// 1 ulp, denormal results flushed: every argument here is a knot spacing, a diagonal or a
+// pivot of a diagonally dominant spline system, far from the denormal range); in FP64 that
+// float seed refined by two Newton steps (about 1 ulp), which avoids the long IEEE division
 // sequence on the narrow FP64 pipe. Both are deterministic, which is what the halo
 // recomputation needs; neither is correctly rounded.
-__device__ __forceinline__ float rrcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ float rrcp(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ double rrcp(double a)
 {
-    double r = (double)__fdividef(1.0f, (float)a);
+    double r = (double)rrcp((float)a);
     double e = __fma_rn(-a, r, 1.0);
     r = __fma_rn(r, e, r);
     e = __fma_rn(-a, r, 1.0);
