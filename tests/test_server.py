@@ -167,6 +167,32 @@ def test_server_large_request_lane_results_equal_alone():
         assert torch.equal(imfs, ai) and torch.equal(r, ar), X.shape
 
 
+def test_server_mixed_interface_solvers_results_equal_alone():
+    """A small-lane request long enough for the cluster interface solve (a 700 x 700
+    image: 1914 tiles) beside short ones: every launch of the lane then runs both
+    interface-solve kernels, each on its own instances; every result equals the same
+    input decomposed alone, bit for bit."""
+    c, lo, hi = capi.serial_emd_interface_solve_shape(capi.FP32_MIXED, capi.SPLINE_NATURAL)
+    base = make_params(1000, 1000, precision=capi.FP32_MIXED, transition_len=0, max_imfs=5)
+    server = Server(base, 1 << 30, 8)
+    big = synth.grating_image(700, 8)
+    assert c == 0 or (700 * 700 + 255) // 256 >= lo
+    items = [(big, capi.ORDER_ROWS)] + _mix(61)
+    xs = [torch.from_numpy(np.asarray(X, np.float32)).cuda() for X, _ in items]
+    subs = [server.submit(x, order=o) for x, (_, o) in zip(xs, items)]
+    res = _wait(server, [s[0] for s in subs])
+    server.close()
+    for (X, order), x, (t, imfs, r) in zip(items, xs, subs):
+        assert res[t].status == capi.SEMD_OK
+        plan = Plan(make_params(*X.shape, precision=capi.FP32_MIXED, transition_len=0,
+                                max_imfs=5, order=order))
+        ai, ar, an = plan.decompose(x)
+        torch.cuda.synchronize()
+        plan.close()
+        assert res[t].n_imfs == an
+        assert torch.equal(imfs, ai) and torch.equal(r, ar), X.shape
+
+
 # ------------------------------------------------------- failures made on the host
 
 def test_server_allocation_failure_is_reported():
