@@ -857,9 +857,13 @@ struct PreTile {
     R hcl, hcr;
     uint2 km;
     int hpar;
+    // the knots compacted into the warp's pool from km (warp_knots_stored), and its results
+    uint32_t MX, MN;
+    int bx, bn, m0, m1;
 };
 template <typename R, int SPL>
-__device__ __forceinline__ void pre_tile(const PassArgs &pa, int64_t gt, PreTile<R, SPL> &pt)
+__device__ __forceinline__ void pre_tile(const PassArgs &pa, int64_t gt, PreTile<R, SPL> &pt,
+                                         WarpPool<R, 32 * SPL> &P)
 {
     constexpr int TW = 32 * SPL;
     const int lane = threadIdx.x & 31;
@@ -874,6 +878,9 @@ __device__ __forceinline__ void pre_tile(const PassArgs &pa, int64_t gt, PreTile
     pt.hcl = (lane == 0 && ts > 0) ? __ldcg(hsrc - 1) : R(0);
     pt.hcr = (lane == 31 && ts + TW < L) ? __ldcg(hsrc + TW) : R(0);
     pt.km = __ldcg(in.kmask + (int64_t)lt * 32 + lane);
+    // Step 1's knots of this signal into the pool now (used if the tile sifts)
+    warp_knots_stored<R, SPL, TW>(P, pt.v, lane * SPL, pt.km, pt.MX, pt.MN, pt.bx, pt.bn,
+                                  pt.m0, pt.m1);
 }
 
 // ---------------------------------------------------------------------------------
@@ -932,6 +939,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
     R v[SPL], hn[SPL];
     R hcl = R(0), hcr = R(0); // current signal at the halo samples -1 and TW
     uint2 km = make_uint2(0u, 0u); // the signal's extremum masks and ranks (sifting modes)
+    bool have = false;             // this tile's signal and knots came from `pre`
     if (STAGE && staged) {
         // copied in while the previous tile computed
         cp_async_wait_all();
@@ -948,7 +956,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         }
         __syncwarp(); // the stage is refilled below
     } else {
-        const bool have = pre != nullptr && pre->hpar == hpar;
+        have = pre != nullptr && pre->hpar == hpar;
         if (mode != MODE_INIT) {
             if (have) {
 #pragma unroll
@@ -1004,7 +1012,16 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         // and ranks, stored per lane); only the knots are gathered into the pool
         uint32_t MX, MN;
         int bx, bn, m0, m1;
-        warp_knots_stored<R, SPL, TW>(P, v, k0, km, MX, MN, bx, bn, m0, m1);
+        if (have) { // compacted before the kernel's wait
+            MX = pre->MX;
+            MN = pre->MN;
+            bx = pre->bx;
+            bn = pre->bn;
+            m0 = pre->m0;
+            m1 = pre->m1;
+        } else {
+            warp_knots_stored<R, SPL, TW>(P, v, k0, km, MX, MN, bx, bn, m0, m1);
+        }
         const int b1 = m0 + 2;
         const int base = eh ? b1 : 0, m = eh ? m1 : m0;
         if (hl == 0) {
@@ -1242,7 +1259,7 @@ __global__ void __launch_bounds__(NWARP * 32, MINB) k_pass(PassArgs pa)
     // staging kernels, with many tiles per warp, keep the registers for the tiles)
     PreTile<R, SPL> pre;
     if (!STAGE && g0 < g1)
-        pre_tile<R, SPL>(pa, g0, pre);
+        pre_tile<R, SPL>(pa, g0, pre, P);
     pdl_wait();
     bool staged = false;
     for (int64_t gt = g0; gt < g1; ++gt)
@@ -1773,9 +1790,10 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
             U += S.wsu[w];
         }
     }
-    // the stop test and the next mode (thread 0, while the others write the entries; the
-    // entries of an instance that stops sifting are dropped)
-    if (tid == 0) {
+    // the stop test and the next mode (a middle thread, while the others write the
+    // entries: thread 0 also writes the mirrored end rows of the first tile; the entries
+    // of an instance that stops sifting are dropped)
+    if (tid == kRedThreads / 2) {
         double sdn = 0.0, sdd = 0.0;
         int nz = 0;
         for (int w = 0; w < NW; ++w) {
