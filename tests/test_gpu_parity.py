@@ -589,12 +589,15 @@ def _cluster_signal(nt, tile, seed, flat=True):
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(mirror_knots=1),
-                                dict(boundary=capi.BOUNDARY_ENDPOINTS)])
+                                dict(boundary=capi.BOUNDARY_ENDPOINTS),
+                                dict(stop=capi.STOP_SD, sd_threshold=0.2, max_sifts=30),
+                                dict(stop=capi.STOP_SNUMBER, s_number=3, max_sifts=30)])
 @pytest.mark.parametrize("where", ["low", "high"])
 def test_cluster_interface_solve_fp64(kw, where):
     """Signals whose interface solve runs on a thread-block cluster (just above the tile
     count where it starts, and at three times that, with tile 512), FP64 against the
-    oracle within 1e-10, with each boundary rule and a constant stretch."""
+    oracle within 1e-10 (IMFs and sift counts), with each boundary rule, the SD and the
+    S-number stop (their totals summed over the cluster's CTAs) and a constant stretch."""
     c, lo, hi = capi.serial_emd_interface_solve_shape(capi.FP64, capi.SPLINE_NATURAL)
     tile = 256 if where == "low" else 512
     nt = lo + 3 if where == "low" else min(3 * lo, hi)
@@ -604,10 +607,12 @@ def test_cluster_interface_solve_fp64(kw, where):
     plan.tile = tile
     imfs, res, n = plan.decompose(torch.from_numpy(X).cuda())
     torch.cuda.synchronize()
+    sifts = plan.counts(1)[1][0]
     plan.close()
     o = _oracle(X, capi.FP64, transition_len=0, max_imfs=6, **kw)
     _check_imfs(imfs.cpu().numpy(), res.cpu().numpy(), n, o[0], o[1], o[2], o[4], capi.FP64,
                 f"cluster {where} {kw}")
+    assert list(sifts[:n]) == list(o[3][:n]), (sifts, o[3])
 
 
 def test_cluster_interface_solve_batch_independent_fp32():
