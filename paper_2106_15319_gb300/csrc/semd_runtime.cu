@@ -29,7 +29,9 @@ template <typename R>
 __device__ __forceinline__ double serial_sample(const R *X, int64_t M, int64_t N, int64_t D,
                                                 int order, int64_t p)
 {
-    const int64_t i = p / (M + D), m = p - i * (M + D);
+    // serialized lengths are below 2^30 (plan validation): 32-bit division
+    const uint32_t md = (uint32_t)(M + D);
+    const int64_t i = (uint32_t)p / md, m = p - i * (int64_t)md;
     if (m < M)
         return (double)X[order == 0 ? i * M + m : m * N + i];
     const int64_t r = m - M;
