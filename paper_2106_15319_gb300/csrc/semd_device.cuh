@@ -92,7 +92,9 @@ __device__ __forceinline__ void prefetch_l1(const void *p)
 __device__ __forceinline__ bool deser_index(int64_t p, int64_t M, int64_t N, int64_t D, int order,
                                             int64_t &dst)
 {
-    const int64_t i = p / (M + D), m = p - i * (M + D);
+    // serialized lengths are below 2^30 (plan validation): 32-bit division
+    const uint32_t md = (uint32_t)(M + D);
+    const int64_t i = (uint32_t)p / md, m = p - i * (int64_t)md;
     if (m >= M)
         return false;
     dst = order == 0 ? i * M + m : m * N + i;
