@@ -859,9 +859,11 @@ struct PreTile {
     R hcl, hcr;
     uint2 km;
     int hpar;
-    // the knots compacted into the warp's pool from km (warp_knots_stored), and its results
+    // the knots compacted into the warp's pool from km (warp_knots_stored), and its results;
+    // ok: the compaction ran (every slot the masks imply lies inside the pool)
     uint32_t MX, MN;
     int bx, bn, m0, m1;
+    bool ok;
 };
 template <typename R, int SPL>
 __device__ __forceinline__ void pre_tile(const PassArgs &pa, int64_t gt, PreTile<R, SPL> &pt,
@@ -880,9 +882,19 @@ __device__ __forceinline__ void pre_tile(const PassArgs &pa, int64_t gt, PreTile
     pt.hcl = (lane == 0 && ts > 0) ? __ldcg(hsrc - 1) : R(0);
     pt.hcr = (lane == 31 && ts + TW < L) ? __ldcg(hsrc + TW) : R(0);
     pt.km = __ldcg(in.kmask + (int64_t)lt * 32 + lane);
-    // Step 1's knots of this signal into the pool now (used if the tile sifts)
-    warp_knots_stored<R, SPL, TW>(P, pt.v, lane * SPL, pt.km, pt.MX, pt.MN, pt.bx, pt.bn,
-                                  pt.m0, pt.m1);
+    // Step 1's knots of this signal into the pool now (used if the tile sifts). Before the
+    // wait the stored masks may belong to another signal (an instance that starts with
+    // this pass, an earlier call with another tile size) or may never have been written,
+    // so the knots are compacted only if every slot the masks and ranks imply lies inside
+    // the pool, which masks of this signal always satisfy (bx + |MX| <= m0 and
+    // m0 + bn + |MN| <= m0 + m1 <= TW); otherwise the pass compacts after its wait.
+    const uint32_t MX = pt.km.x & 0xffffu, MN = pt.km.x >> 16;
+    const int bx = (int)(pt.km.y & 0xffffu), bn = (int)(pt.km.y >> 16);
+    const int m0 = __shfl_sync(FULLMASK, bx + __popc(MX), 31);
+    pt.ok = __all_sync(FULLMASK, bx + __popc(MX) <= TW && m0 + bn + __popc(MN) <= TW);
+    if (pt.ok)
+        warp_knots_stored<R, SPL, TW>(P, pt.v, lane * SPL, pt.km, pt.MX, pt.MN, pt.bx, pt.bn,
+                                      pt.m0, pt.m1);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1014,7 +1026,7 @@ __device__ __forceinline__ bool pass_tile(const PassArgs &pa, WarpPool<R, 32 * S
         // and ranks, stored per lane); only the knots are gathered into the pool
         uint32_t MX, MN;
         int bx, bn, m0, m1;
-        if (have) { // compacted before the kernel's wait
+        if (have && pre->ok) { // compacted before the kernel's wait
             MX = pre->MX;
             MN = pre->MN;
             bx = pre->bx;

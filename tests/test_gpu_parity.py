@@ -863,6 +863,31 @@ def test_pass_kernel_register_variants_agree_bit_for_bit(prec):
         assert n == out[0][2] and torch.equal(imfs, out[0][0]) and torch.equal(res, out[0][1])
 
 
+@pytest.mark.parametrize("prec", [capi.FP32_MIXED, capi.FP64])
+def test_pass_after_another_tile_size_equals_fresh_plan(prec):
+    """The latency variant of the pass kernel reads a warp's first tile, with the extremum
+    masks stored for it, before it waits for the interface solve, when those masks may
+    still be another signal's. A plan that ran with 512-sample tiles (its stored masks
+    index up to 512 samples per tile) and then with 256-sample tiles gives the IMFs of a
+    fresh 256-sample-tile plan bit for bit, in both precisions."""
+    X = synth.workload_texture_256().astype(NP[prec])
+    x = torch.from_numpy(X).cuda()
+    out = []
+    for first in (512, None):
+        plan = Plan(make_params(256, 256, precision=prec, transition_len=0, max_imfs=4))
+        if first is not None:
+            plan.tile = first
+            plan.pass_variant = 1
+            plan.decompose(x)
+        plan.tile = 256
+        plan.pass_variant = 1
+        imfs, res, n = plan.decompose(x)
+        out.append((imfs.cpu(), res.cpu(), n))
+        plan.close()
+    assert out[0][2] == out[1][2]
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
 def test_readme_example_runs():
     """The usage example of the README: serial EMD, EEMD and CEEMDAN of a 6 x 1000 input."""
     x = torch.randn(6, 1000, device="cuda")
