@@ -39,8 +39,8 @@ EEMD_NOISE_SEED = 20210629 + 4  # seed of the white noise the library draws for 
 # decomposition: an IMF-1 sift) per (tile, variant), from an ncu capture of that launch with
 # the dram__bytes counters (cold caches, as ncu replays). Emptied whenever the pass kernel
 # changes, until the changed kernel is captured again; an empty entry is reported as null.
-PASS_TRAFFIC_TEXTURE = {(128, 0): 582912, (128, 1): 581888, (256, 0): 467456,
-                        (256, 1): 465920, (512, 0): 412672, (512, 1): 412416}
+PASS_TRAFFIC_TEXTURE = {(128, 0): 583168, (128, 1): 583680, (256, 0): 467456,
+                        (256, 1): 465920, (512, 0): 412672, (512, 1): 412160}
 # FP64-pipe lane operations (sm__inst_executed_pipe_fp64 x 32) of one k_pass<double> launch
 # of the default workload, per (tile, variant), from an ncu capture of that launch; emptied
 # whenever the pass kernel changes.
