@@ -464,6 +464,70 @@ def cpu_pool_eemd(wl, budget_s: float = 10.0):
             "sample": f"{done} of {wl['trials']} EEMD trials, FP64, one process per core"}
 
 
+def _oracle_instance(args):
+    """One independent instance of a batched workload through the oracle (also a
+    process-pool task): its sample-sifts. args = (X (N, M), D, K, stop, fixed sifts)."""
+    X, D, K, stop, S = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    _, _, _, sifts = O.serial_emd(X, D, K, stop=stop, fixed_sifts=S, sd_threshold=0.2,
+                                  max_sifts=50)
+    return int(np.sum(sifts)) * O.serial_length(X.shape[1], X.shape[0], D)
+
+
+def _oracle_group(tasks):
+    """Consecutive instances through the oracle in one process-pool task (fewer round
+    trips for short instances): their sample-sifts."""
+    return sum(_oracle_instance(a) for a in tasks)
+
+
+def cpu_instances(tasks, what: str, budget_s: float = 10.0, group: int = 1):
+    """The oracle on the independent instances of a batched workload (tasks: arguments of
+    _oracle_instance in the workload's order), single-threaded in this process and then
+    in a process pool with one process per host core (spawned, as CUDA is already
+    initialized here), each over the leading instances that about budget_s allows; the
+    pool hands out `group` consecutive instances at a time. Returns (single thread, all
+    cores)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    done, ss = 0, 0
+    while done < len(tasks) and (time.perf_counter() - t0 < budget_s or done == 0):
+        ss += _oracle_instance(tasks[done])
+        done += 1
+    el = time.perf_counter() - t0
+    one = {"value": ss / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_model": _cpu_model(),
+           "sample": f"the first {done} of {len(tasks)} {what}, FP64, single thread"}
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        # start-up on the smallest instances
+        list(ex.map(_oracle_instance, sorted(tasks, key=lambda a: a[0].size)[:cores]))
+        # one group per process at a time; a process that finishes takes the next group
+        # while the budget lasts, and the time runs until the last one finishes
+        groups = [tasks[i:i + group] for i in range(0, len(tasks), group)]
+        t0 = time.perf_counter()
+        done, ss, nxt, run = 0, 0, 0, {}
+        while nxt < len(groups) and len(run) < cores:
+            run[ex.submit(_oracle_group, groups[nxt])] = len(groups[nxt])
+            nxt += 1
+        while run:
+            fin, _ = cf.wait(set(run), return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                ss += f.result()
+                done += run.pop(f)
+            while (nxt < len(groups) and len(run) < cores
+                   and time.perf_counter() - t0 < budget_s):
+                run[ex.submit(_oracle_group, groups[nxt])] = len(groups[nxt])
+                nxt += 1
+        el = time.perf_counter() - t0
+    take = "the next one" if group == 1 else f"the next {group}"
+    return one, {"value": ss / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                 "cpu_model": _cpu_model(),
+                 "sample": f"the first {done} of {len(tasks)} {what}, FP64, one process "
+                           f"per core, each taking {take} when it finishes"}
+
+
 def cpu_baseline(wl, budget_s: float = 12.0, ss_per_step: int = 0):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -768,6 +832,7 @@ def batched_eemd(args, device, flush, peak, peak_kind, world):
                       "note": "host buffers: the image in, the averaged IMFs and residue out; "
                               "the noise is drawn on the device"}
     if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
+        out["cpu_baseline"] = cpu_baseline(wl, 10.0)
         out["cpu_baseline_all_cores"] = cpu_pool_eemd(wl)
     return out
 
@@ -844,6 +909,13 @@ def batched_images(args, device, flush, peak, peak_kind, world):
     ach = bpl / (pass_avg_ms * 1e-3) / 1e9
     n_imfs, sifts = plan.counts(len(xs))
     plan.close()
+    cpu = {}
+    if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
+        from oracle import oracle as O
+        tasks = [(np.asarray(im, np.float32).astype(np.float64), 0, 8, O.STOP_SD, 10)
+                 for im in imgs]
+        one, allc = cpu_instances(tasks, "images (SD stop 0.2, <= 8 IMFs)", group=8)
+        cpu = {"cpu_baseline": one, "cpu_baseline_all_cores": allc}
     return {"workload": f"{len(xs)} uneven blob-field images, side U{{32..128}} "
                         f"({samples} samples), row-serialized D=0, SD stop 0.2 (max 50 "
                         "sifts), <=8 IMFs, all instances in every pass launch",
@@ -854,7 +926,8 @@ def batched_images(args, device, flush, peak, peak_kind, world):
                          "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "peak_source": peak_kind, "avg_launch_us": pass_avg_ms * 1e3,
                          "bytes_per_launch": bpl, "launches": pr.pass_launches,
-                         "reduce_avg_us": pr.reduce_ms / max(1, pr.reduce_launches) * 1e3}}
+                         "reduce_avg_us": pr.reduce_ms / max(1, pr.reduce_launches) * 1e3},
+            **cpu}
 
 
 def serving(args, device):
@@ -929,6 +1002,18 @@ def serving(args, device):
     finally:
         server.close()
     del xs, outs
+    if not args.no_cpu_baseline and int(os.environ.get("RANK", "0")) == 0:
+        # the requests in arrival order, each decomposed alone (D = round(0.2 M), one
+        # signal: D = 0), as the server decomposes them
+        from oracle import oracle as O
+        tasks = []
+        for _, _, a in mix:
+            X = np.asarray(a, np.float32).astype(np.float64)
+            X = X.reshape(1, -1) if X.ndim == 1 else X
+            D = 0 if X.shape[0] == 1 else int(round(0.2 * X.shape[1]))
+            tasks.append((X, D, 10, O.STOP_FIXED, 10))
+        out["cpu_baseline"], out["cpu_baseline_all_cores"] = cpu_instances(
+            tasks, "requests of the mix, in arrival order")
     return out
 
 
