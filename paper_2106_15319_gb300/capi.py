@@ -360,6 +360,56 @@ def serial_emd_decompose_batch(plan: int, items, stream=None, wait: bool = True)
     return list(n) if wait else None
 
 
+def _packed_instance_array(plan: int, x, shapes, imfs, residue):
+    """The semd_instance array of a packed batch: instance i's (rows_i, cols_i) input at
+    element offset o_i = sum of the earlier rows * cols in x, its K IMFs at K o_i in imfs
+    and its residue at o_i in residue, with one buffer check per tensor."""
+    global _INSTANCE_DTYPE
+    import numpy as np
+    p = _PLAN_PARAMS.get(plan)
+    if p is None:
+        raise SemdError(SEMD_EINVAL, "a packed batch needs a plan created by this binding")
+    sh = np.asarray(shapes, dtype=np.int64).reshape(-1, 2)
+    if sh.shape[0] < 1 or (sh < 1).any():
+        raise SemdError(SEMD_EINVAL, "shapes: one (rows, cols) pair of positive sizes per input")
+    size = sh[:, 0] * sh[:, 1]
+    off = np.concatenate(([0], np.cumsum(size)[:-1]))
+    total = int(size.sum())
+    dev = _current_device()
+    _need(x, "x", p.precision, total, dev=dev)
+    _need(imfs, "imfs", p.precision, p.max_imfs * total, dev=dev)
+    _need(residue, "residue", FP64, total, optional=True, dev=dev)
+    if _INSTANCE_DTYPE is None:
+        _INSTANCE_DTYPE = np.dtype([("x", "<u8"), ("rows", "<i8"), ("cols", "<i8"),
+                                    ("imfs", "<u8"), ("res", "<u8")], align=True)
+    elem = 8 if p.precision == FP64 else 4
+    a = np.zeros(sh.shape[0], _INSTANCE_DTYPE)
+    a["x"] = np.uint64(_ptr(x)) + (off * elem).astype(np.uint64)
+    a["rows"] = sh[:, 0]
+    a["cols"] = sh[:, 1]
+    a["imfs"] = np.uint64(_ptr(imfs)) + (off * (p.max_imfs * elem)).astype(np.uint64)
+    if residue is not None:
+        a["res"] = np.uint64(_ptr(residue)) + (off * 8).astype(np.uint64)
+    return a
+
+
+def serial_emd_decompose_packed(plan: int, x, shapes, imfs, residue=None, stream=None,
+                                wait: bool = True):
+    """serial_emd_decompose_batch of inputs stored back to back in one tensor: x holds
+    input i, (rows_i, cols_i) row-major, at element offset o_i (the sum of the earlier
+    inputs' sizes); its K IMFs are written at K o_i in imfs (K x rows_i x cols_i) and its
+    residue at o_i in residue. The per-input pointers are computed from the offsets, so a
+    batch of thousands of inputs costs one buffer check per tensor instead of three per
+    input."""
+    a = _packed_instance_array(plan, x, shapes, imfs, residue)
+    n = (ctypes.c_int * len(a))()
+    rc = load().serial_emd_decompose_batch(
+        plan, len(a), a.ctypes.data_as(ctypes.POINTER(semd_instance)), n if wait else None,
+        _stream(stream))
+    _check(rc, plan)
+    return list(n) if wait else None
+
+
 def serial_emd_decompose_slices(plan: int, x, imfs, residue, stream=None, wait: bool = True):
     """Slice-wise standard EMD of every row of x (rows, cols); imfs (K, rows, cols)."""
     rows, cols = x.shape

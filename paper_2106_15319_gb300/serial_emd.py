@@ -90,6 +90,20 @@ class Plan:
         n = capi.serial_emd_decompose_batch(self.handle, items, stream, wait)
         return outs, n
 
+    def decompose_packed(self, x: torch.Tensor, shapes, imfs=None, residue=None, stream=None,
+                         wait: bool = True):
+        """decompose_batch of inputs stored back to back in one flat tensor x (input i,
+        shapes[i] = (rows, cols), at the sum of the earlier inputs' sizes); imfs holds each
+        input's K IMFs back to back (K * rows * cols elements each), residue each input's
+        residue. Returns (imfs, residue, IMF count per input, or None without wait)."""
+        import numpy as np
+        total = int(np.prod(np.asarray(shapes, dtype=np.int64).reshape(-1, 2), axis=1).sum())
+        if imfs is None:
+            imfs = torch.empty(self.params.max_imfs * total, dtype=self.dtype, device=x.device)
+            residue = torch.empty(total, dtype=torch.float64, device=x.device)
+        n = capi.serial_emd_decompose_packed(self.handle, x, shapes, imfs, residue, stream, wait)
+        return imfs, residue, n
+
     def decompose_slices(self, x: torch.Tensor, imfs=None, residue=None, stream=None,
                          wait: bool = True):
         """Slice-wise standard EMD: every row of x decomposed on its own (the plan must hold

@@ -90,3 +90,36 @@ def test_plan_calls_refuse_mismatched_buffers(no_library):
                  [(x, FakeCuda(2559, f32), None)], msg="imfs")
     finally:
         capi._PLAN_PARAMS.pop(plan, None)
+
+
+def test_packed_batch_layout_and_refusals(no_library):
+    """A packed batch: input i at the sum of the earlier inputs' sizes, its K IMFs at K
+    times that offset, its residue at that offset (8-byte elements); buffers shorter than
+    the batch, or shapes with a zero size, are refused before any library call."""
+    f32, f64 = torch.float32, torch.float64
+    plan = 0x4321
+    capi._PLAN_PARAMS[plan] = capi.semd_params(rows=64, cols=64, max_imfs=3,
+                                               precision=capi.FP32_MIXED, transition_len=0,
+                                               order=capi.ORDER_ROWS, ensemble_trials=1)
+    try:
+        shapes = [(2, 3), (1, 5), (7, 1)]
+        a = capi._packed_instance_array(plan, 1000, shapes, 50000, 90000)  # raw pointers
+        assert list(a["x"]) == [1000, 1000 + 6 * 4, 1000 + 11 * 4]
+        assert list(a["rows"]) == [2, 1, 7] and list(a["cols"]) == [3, 5, 1]
+        assert list(a["imfs"]) == [50000, 50000 + 3 * 6 * 4, 50000 + 3 * 11 * 4]
+        assert list(a["res"]) == [90000, 90000 + 6 * 8, 90000 + 11 * 8]
+        assert list(capi._packed_instance_array(plan, 1000, shapes, 50000, None)["res"]) == \
+            [0, 0, 0]
+        total = 18
+        _refused(capi.serial_emd_decompose_packed, plan, FakeCuda(total - 1, f32), shapes,
+                 FakeCuda(3 * total, f32), None, msg="x")
+        _refused(capi.serial_emd_decompose_packed, plan, FakeCuda(total, f32), shapes,
+                 FakeCuda(3 * total - 1, f32), None, msg="imfs")
+        _refused(capi.serial_emd_decompose_packed, plan, FakeCuda(total, f32), shapes,
+                 FakeCuda(3 * total, f32), FakeCuda(total, f32), msg="residue")
+        _refused(capi.serial_emd_decompose_packed, plan, FakeCuda(total, f64), shapes,
+                 FakeCuda(3 * total, f32), None, msg="dtype")
+        _refused(capi.serial_emd_decompose_packed, plan, FakeCuda(total, f32), [(2, 0)],
+                 FakeCuda(3 * total, f32), None, msg="shapes")
+    finally:
+        capi._PLAN_PARAMS.pop(plan, None)

@@ -445,6 +445,35 @@ def test_batch_uneven_images_match_oracle_and_alone(prec):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
+@pytest.mark.parametrize("stop", [capi.STOP_FIXED, capi.STOP_SD])
+def test_packed_batch_equals_tensor_list_batch(prec, stop):
+    """A batch stored back to back in one tensor (odd sizes, so that most inputs start at
+    element offsets that are not 16-byte aligned) gives the IMFs, residues and counts of
+    the same batch passed as separate tensors, bit for bit."""
+    g = np.random.default_rng(7)
+    imgs = [np.asarray(synth.grating_image(int(s), int(g.integers(0, 1000))), NP[prec])
+            for s in g.integers(17, 90, size=23)]
+    imgs += [np.asarray(synth.tone_chirp_series(3, 1001, 5), NP[prec])]
+    p = make_params(90, 90, precision=prec, transition_len=0, max_imfs=6, stop=stop,
+                    sd_threshold=0.2, max_sifts=50)
+    plan = Plan(p, max_batch=len(imgs))
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    outs, ns = plan.decompose_batch(xs)
+    shapes = [im.shape for im in imgs]
+    flat = torch.cat([x.reshape(-1) for x in xs])
+    pim, pres, pn = plan.decompose_packed(flat, shapes)
+    torch.cuda.synchronize()
+    assert pn == ns
+    o = 0
+    for i, im in enumerate(imgs):
+        sz = im.size
+        assert torch.equal(pim[6 * o:6 * (o + sz)].reshape(outs[i][0].shape), outs[i][0])
+        assert torch.equal(pres[o:o + sz].reshape(outs[i][1].shape), outs[i][1])
+        o += sz
+    plan.close()
+
+
 # ----------------------------------------------------------------------------- EEMD
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
