@@ -1618,9 +1618,14 @@ __device__ __forceinline__ int stop_step(const ReduceArgs &ra, const Inst &in, S
 // SMALL: instances whose reduced systems have at most kRedSmallRows rows (the host
 // guarantees it from the tile count); only the small form is compiled, with a register
 // budget for three (FP32) or two (FP64) resident CTAs per SM instead of one or two, so
-// that batches of many short instances fill the GPU (0: no register budget).
-template <typename R, bool SMALL>
-__global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) : 0)
+// that batches of many short instances fill the GPU (0: no register budget). NT: threads
+// per CTA; the host launches NT = kRedThreadsTiny (with the same per-thread register
+// budget, four times the CTAs per SM) when every instance has at most that many tiles.
+// For such instances both thread counts perform the same operations in the same order
+// (one tile per thread; the SD sums of warps past the tiles are exact zeros), so the
+// results do not depend on which form ran.
+template <typename R, bool SMALL, int NT = kRedThreads>
+__global__ void __launch_bounds__(NT, SMALL ? (sizeof(R) == 4 ? 3 : 2) * (kRedThreads / NT) : 0)
     k_reduce(ReduceArgs ra)
 {
     __shared__ RedShared<SMALL> S;
@@ -1656,7 +1661,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     const int pm = st->pass_mode, psift = st->pass_sift, pimf = st->pass_imf;
     const int ppar = st->pass_par, pscount = st->pass_scount;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int NW = kRedThreads / 32;
+    constexpr int NW = NT / 32;
 
     // counts: knots of both envelopes, this envelope's reduced-system entries per tile
     // (first/last knot) and the SD sums of the pass that just ran. With at most one tile
@@ -1669,7 +1674,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     int sn = 0, so_ = 0, zs = 0;
     double a = 0.0, b = 0.0;
     const bool want_sd = ra.stop == STOP_SD, want_zc = ra.stop == STOP_SNUMBER;
-    const bool one = nt <= kRedThreads;
+    const bool one = nt <= NT;
     int ntot = 0, nother = 0, U = 0, ubase = 0, u1 = 0, ca = 0, cb = 0;
     TileRec<R> r1;
     r1.n = 0;
@@ -1726,12 +1731,12 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         ntot = (int)((tot >> 12) & 0x7ffffu);
         nother = (int)(tot >> 31);
     } else {
-        for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+        for (int t0 = 0; t0 < nt; t0 += 4 * NT) {
             int ne[4], no[4], nz[4];
             double sa[4], sb[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int t = t0 + tid + k * kRedThreads;
+                const int t = t0 + tid + k * NT;
                 ne[k] = no[k] = nz[k] = 0;
                 sa[k] = sb[k] = 0.0;
                 if (t < nt) {
@@ -1747,7 +1752,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int t = t0 + tid + k * kRedThreads;
+                const int t = t0 + tid + k * NT;
                 if (t < nt)
                     X.Tu[t] = (unsigned char)(ne[k] <= kSparseKnots ? ne[k] : 2);
                 sn += ne[k];
@@ -1776,7 +1781,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         __syncthreads();
         // entry offsets: each thread sums a contiguous chunk of tiles, a block scan of the
         // chunk sums, then the chunk's per-tile offsets
-        const int CH = (nt + kRedThreads - 1) / kRedThreads;
+        const int CH = (nt + NT - 1) / NT;
         ca = min(tid * CH, nt);
         cb = min(ca + CH, nt);
         int su = 0;
@@ -1807,7 +1812,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     // the stop test and the next mode (a middle thread, while the others write the
     // entries: thread 0 also writes the mirrored end rows of the first tile; the entries
     // of an instance that stops sifting are dropped)
-    if (tid == kRedThreads / 2) {
+    if (tid == NT / 2) {
         double sdn = 0.0, sdd = 0.0;
         int nz = 0;
         for (int w = 0; w < NW; ++w) {
@@ -1936,17 +1941,17 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         __syncthreads();
         // entries, with the substitution data of their rows: tiles in a stride of the
         // block, four records per thread in flight at a time
-        for (int t0 = 0; t0 < nt; t0 += 4 * kRedThreads) {
+        for (int t0 = 0; t0 < nt; t0 += 4 * NT) {
             TileRec<R> rb[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int t = t0 + tid + k * kRedThreads;
+                const int t = t0 + tid + k * NT;
                 if (t < nt)
                     rb[k] = load_rec(texe + t);
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int t = t0 + tid + k * kRedThreads;
+                const int t = t0 + tid + k * NT;
                 if (t >= nt)
                     break;
                 put_entries(rb[k], X.To[t]);
@@ -2007,7 +2012,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
     if (!one)
         __syncthreads();
     // rows, every thread a strided share (reads the scratch only; writes its own rows)
-    for (int p = tid; p < NR; p += kRedThreads) {
+    for (int p = tid; p < NR; p += NT) {
         const int k = X.Ek[p];
         R ra_ = R(0), rb = R(1), rc_ = R(0), rd = R(0);
         if (k != EK_FIXED) {
@@ -2095,8 +2100,8 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         small_solve();
     } else {
         R *lev = reinterpret_cast<R *>(S.lev);
-        constexpr int NS = kRedThreads;     // level-1 segments of the large form
-        constexpr int G = kRedThreads / 32; // segments per lane of the level-1.5 warp
+        constexpr int NS = NT;     // level-1 segments of the large form
+        constexpr int G = NT / 32; // segments per lane of the level-1.5 warp
         // transposed layout: lane l's k-th segment (j = G l + k) at k * 32 + l, so
         // that the level-1.5 warp reads without bank conflicts
         auto tj = [](int j) { return (j % G) * 32 + j / G; };
@@ -2212,7 +2217,7 @@ __global__ void __launch_bounds__(kRedThreads, SMALL ? (sizeof(R) == 4 ? 3 : 2) 
         }
         __syncthreads();
     }
-    for (int t = tid; t < nt; t += kRedThreads) {
+    for (int t = tid; t < nt; t += NT) {
         const int u = X.Tu[t], p = X.To[t];
         TileSolve *so = tsol + t;
         const R yp = X.Ey[p - 1], Mp = X.MV[p - 1], yn = X.Ey[p + u], Mn = X.MV[p + u];

@@ -698,6 +698,10 @@ static cudaError_t set_smem_attr()
         e = cudaFuncSetAttribute(k_reduce<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)reduce_smem_bytes(kRedSmallRows, sizeof(R)));
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_reduce<R, true, kRedThreadsTiny>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)reduce_smem_bytes(reduce_len(kRedThreadsTiny), sizeof(R)));
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_reduce_cl<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kClSmemOptin - 1024));
     if (e == cudaSuccess)
@@ -822,7 +826,9 @@ static size_t reduce_smem(const ReduceArgs &ra)
 
 // One CTA per instance and envelope. When the shared scratch holds every instance's
 // system (smem_entries, sized for the launch's longest instance, bounds each system's
-// rows) and that is at most kRedSmallRows rows, the small-system kernel runs.
+// rows) and that is at most kRedSmallRows rows, the small-system kernel runs; when the
+// longest instance has at most kRedThreadsTiny tiles, its 64-thread form (one thread per
+// tile, four times the resident CTAs per SM).
 // The cluster kernel: ra.cl CTAs per instance and envelope, one cluster each, launched
 // with programmatic dependent launch like the other kernels of the sifting loop (its CTAs
 // take the SMs the pass kernel leaves, and wait for it to finish before reading).
@@ -853,7 +859,10 @@ static void launch_reduce(const ReduceArgs &ra, int ninst, cudaStream_t s)
         launch_reduce_cl<R>(ra, ninst, s);
     if (!ra.run_single)
         return;
-    if (ra.smem_entries > 0 && ra.smem_entries <= kRedSmallRows)
+    if (ra.smem_entries > 0 && ra.smem_entries <= reduce_len(kRedThreadsTiny))
+        launch_pdl(k_reduce<R, true, kRedThreadsTiny>, (unsigned)(2 * ninst), kRedThreadsTiny,
+                   reduce_smem(ra), s, ra);
+    else if (ra.smem_entries > 0 && ra.smem_entries <= kRedSmallRows)
         launch_pdl(k_reduce<R, true>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s, ra);
     else
         launch_pdl(k_reduce<R, false>, (unsigned)(2 * ninst), kRedThreads, reduce_smem(ra), s,

@@ -169,8 +169,10 @@ struct CePart {
 // Samples per block of the stage-test passes.
 constexpr int kCeTestSpan = 2048;
 
-// Threads of the interface-solve kernel (one CTA per instance and envelope).
+// Threads of the interface-solve kernel (one CTA per instance and envelope), and of its
+// form for launches whose instances all have at most kRedThreadsTiny tiles.
 constexpr int kRedThreads = 256;
+constexpr int kRedThreadsTiny = 64;
 
 // Scratch of k_reduce for one envelope of `entries` entries: six arrays in the working
 // precision, four of 32-bit integers and one of bytes, rounded to 16 bytes.
