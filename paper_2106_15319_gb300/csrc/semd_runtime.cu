@@ -824,11 +824,31 @@ static size_t reduce_smem(const ReduceArgs &ra)
     return ra.smem_entries > 0 ? reduce_smem_bytes(ra.smem_entries, ra.single ? 4 : 8) : 0;
 }
 
+// SM count of the current device, looked up once per device.
+static int device_sms()
+{
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return 152;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 152;
+        cache[dev] = std::max(n, 1);
+    }
+    return cache[dev];
+}
+
 // One CTA per instance and envelope. When the shared scratch holds every instance's
 // system (smem_entries, sized for the launch's longest instance, bounds each system's
-// rows) and that is at most kRedSmallRows rows, the small-system kernel runs; when the
-// longest instance has at most kRedThreadsTiny tiles, its 64-thread form (one thread per
-// tile, four times the resident CTAs per SM).
+// rows) and that is at most kRedSmallRows rows, the small-system kernel runs. When the
+// longest instance has at most kRedThreadsTiny tiles and the launch has more CTAs than the
+// 256-thread small form keeps resident at once (its register budget: 3 per SM in FP32, 2
+// in FP64), its 64-thread form runs instead (one thread per tile, four times the resident
+// CTAs); a launch that fits in one wave keeps the 256-thread form, whose phases over the
+// rows of a system have more threads.
 // The cluster kernel: ra.cl CTAs per instance and envelope, one cluster each, launched
 // with programmatic dependent launch like the other kernels of the sifting loop (its CTAs
 // take the SMs the pass kernel leaves, and wait for it to finish before reading).
@@ -859,7 +879,8 @@ static void launch_reduce(const ReduceArgs &ra, int ninst, cudaStream_t s)
         launch_reduce_cl<R>(ra, ninst, s);
     if (!ra.run_single)
         return;
-    if (ra.smem_entries > 0 && ra.smem_entries <= reduce_len(kRedThreadsTiny))
+    const int64_t wave = (int64_t)(sizeof(R) == 4 ? 3 : 2) * device_sms();
+    if (ra.smem_entries > 0 && ra.smem_entries <= reduce_len(kRedThreadsTiny) && 2 * ninst > wave)
         launch_pdl(k_reduce<R, true, kRedThreadsTiny>, (unsigned)(2 * ninst), kRedThreadsTiny,
                    reduce_smem(ra), s, ra);
     else if (ra.smem_entries > 0 && ra.smem_entries <= kRedSmallRows)

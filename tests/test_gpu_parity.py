@@ -446,24 +446,27 @@ def test_batch_uneven_images_match_oracle_and_alone(prec):
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.FP32_MIXED])
-@pytest.mark.parametrize("stop", [capi.STOP_SD, capi.STOP_SNUMBER])
-def test_interface_solve_thread_counts_agree(prec, stop):
-    """Instances of at most 64 tiles are solved by the 64-thread form of the interface
-    solve when the launch holds only such instances, and by the 256-thread form when a
-    longer instance shares the launch: the same results bit for bit, adaptive stop rules
-    (sums over the tiles) included."""
-    small = [np.asarray(synth.grating_image(s, 11 + s), NP[prec]) for s in (40, 71, 127)]
+@pytest.mark.parametrize("stop,boundary", [(capi.STOP_SD, capi.BOUNDARY_MIRROR),
+                                           (capi.STOP_SNUMBER, capi.BOUNDARY_ENDPOINTS)])
+def test_interface_solve_thread_counts_agree(prec, stop, boundary):
+    """A launch of more short instances (at most 64 tiles each) than the 256-thread
+    interface solve keeps resident runs its 64-thread form; with one longer instance added,
+    the launch runs the 256-thread form. The short instances' results are the same bit for
+    bit, adaptive stop rules (sums over the tiles) and both boundary rules included."""
+    g = np.random.default_rng(5)
+    small = [np.asarray(synth.grating_image(int(s), int(s) + 7), NP[prec])
+             for s in g.integers(16, 128, size=240)]
     big = np.asarray(synth.grating_image(160, 3), NP[prec])  # 100 tiles of 256 samples
-    p = make_params(160, 160, precision=prec, transition_len=0, max_imfs=6, stop=stop,
-                    sd_threshold=0.2, max_sifts=50, s_number=3)
-    plan = Plan(p, max_batch=4)
+    p = make_params(160, 160, precision=prec, transition_len=0, max_imfs=5, stop=stop,
+                    sd_threshold=0.2, max_sifts=30, s_number=3, boundary=boundary)
+    plan = Plan(p, max_batch=len(small) + 1)
     plan.tile = 256
     xs = [torch.from_numpy(im).cuda() for im in small]
     alone, n_alone = plan.decompose_batch(xs)
     mixed, n_mixed = plan.decompose_batch(xs + [torch.from_numpy(big).cuda()])
     torch.cuda.synchronize()
-    assert n_alone == n_mixed[:3]
-    for i in range(3):
+    assert n_alone == n_mixed[:len(small)]
+    for i in range(len(small)):
         assert torch.equal(alone[i][0], mixed[i][0]) and torch.equal(alone[i][1], mixed[i][1])
     plan.close()
 
