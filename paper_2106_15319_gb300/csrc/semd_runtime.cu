@@ -6,6 +6,7 @@
 #include "semd_reduce_cl.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -635,10 +636,13 @@ static cudaError_t pass_attr_one()
 
 // Which cluster shapes of the interface solve the current device can hold: per precision,
 // device, cluster size (2, 4, 8, 16) and shared memory (up to 116 KB per CTA, or up to the
-// opt-in maximum): 0 not yet known, 1 yes, 2 no. Filled when the kernel attributes are set
-// (plan and server creation), so that no query runs while a stream is being captured.
+// opt-in maximum): 1 yes, 2 no. Filled once per precision and device, under a lock, when
+// the kernel attributes are set (plan and server creation), so that no query runs while a
+// stream is being captured; the ready flag is published after every entry.
 constexpr int kClDevMax = 64;
-static int g_cluster_fit[2][kClDevMax][4][2];
+static std::atomic<int> g_cluster_fit[2][kClDevMax][4][2];
+static std::atomic<int> g_cluster_fit_ready[2][kClDevMax];
+static std::mutex g_cluster_fit_mu;
 
 template <typename R>
 static void query_cluster_fit(int dev)
@@ -661,7 +665,8 @@ static void query_cluster_fit(int dev)
             const bool ok =
                 cudaOccupancyMaxActiveClusters(&n, k_reduce_cl<R>, &cfg) == cudaSuccess && n > 0;
             cudaGetLastError(); // a refused query leaves no error behind
-            g_cluster_fit[sizeof(R) == 8][dev][lc][big] = ok ? 1 : 2;
+            g_cluster_fit[sizeof(R) == 8][dev][lc][big].store(ok ? 1 : 2,
+                                                               std::memory_order_relaxed);
         }
     }
 }
@@ -673,8 +678,11 @@ static bool cluster_fits(int CL, size_t smem)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kClDevMax)
         return false;
+    if (!g_cluster_fit_ready[sizeof(R) == 8][dev].load(std::memory_order_acquire))
+        return false;
     const int lc = CL == 2 ? 0 : CL == 4 ? 1 : CL == 8 ? 2 : 3;
-    return g_cluster_fit[sizeof(R) == 8][dev][lc][smem > 116 * 1024 ? 1 : 0] == 1;
+    return g_cluster_fit[sizeof(R) == 8][dev][lc][smem > 116 * 1024 ? 1 : 0].load(
+               std::memory_order_relaxed) == 1;
 }
 
 template <typename R>
@@ -708,8 +716,13 @@ static cudaError_t set_smem_attr()
         e = cudaFuncSetAttribute(k_reduce_cl<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     int dev = 0;
     if (e == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kClDevMax &&
-        g_cluster_fit[sizeof(R) == 8][dev][0][0] == 0)
-        query_cluster_fit<R>(dev);
+        !g_cluster_fit_ready[sizeof(R) == 8][dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lk(g_cluster_fit_mu);
+        if (!g_cluster_fit_ready[sizeof(R) == 8][dev].load(std::memory_order_relaxed)) {
+            query_cluster_fit<R>(dev);
+            g_cluster_fit_ready[sizeof(R) == 8][dev].store(1, std::memory_order_release);
+        }
+    }
     return e;
 }
 
@@ -719,24 +732,27 @@ template <typename R, int TILE, int VAR>
 static void pass_residency(int &per_sm, int &sms)
 {
     constexpr int kMaxDev = 64;
-    static int cache[kMaxDev][2];
+    // [1] (SMs) is stored before [0] (CTAs per SM), which a reader checks first
+    static std::atomic<int> cache[kMaxDev][2];
     int dev = 0;
     per_sm = 1;
     sms = 152;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
         return;
-    if (cache[dev][0] == 0) {
+    int ps = cache[dev][0].load(std::memory_order_acquire);
+    if (ps == 0) {
         int a = 0, b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, pass_kernel<R, TILE, VAR>(),
                                                           32 * kPassWarps,
                                                           pass_smem<R, TILE, VAR>()) != cudaSuccess ||
             cudaDeviceGetAttribute(&b, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return;
-        cache[dev][0] = std::max(a, 1);
-        cache[dev][1] = std::max(b, 1);
+        cache[dev][1].store(std::max(b, 1), std::memory_order_relaxed);
+        cache[dev][0].store(std::max(a, 1), std::memory_order_release);
+        ps = std::max(a, 1);
     }
-    per_sm = cache[dev][0];
-    sms = cache[dev][1];
+    per_sm = ps;
+    sms = cache[dev][1].load(std::memory_order_relaxed);
 }
 
 template <typename R>
@@ -828,17 +844,18 @@ static size_t reduce_smem(const ReduceArgs &ra)
 static int device_sms()
 {
     constexpr int kMaxDev = 64;
-    static int cache[kMaxDev];
+    static std::atomic<int> cache[kMaxDev];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
         return 152;
-    if (cache[dev] == 0) {
-        int n = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 152;
-        cache[dev] = std::max(n, 1);
+        n = std::max(n, 1);
+        cache[dev].store(n, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return n;
 }
 
 // One CTA per instance and envelope. When the shared scratch holds every instance's
